@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the SG Helmholtz GMRES hot path on GB300.
+
+Headline (`value`): SG-GMRES solves per second to relative residual 1e-8
+(||b - A x|| / ||b|| computed in FP64) on the 2D workload: 127 x 127 nodes
+(h = 1/126), absorbing boundary, k = 30 (1 + 0.15 sum_{l<=3} l^-1 cos(l pi x)
+cos(l pi y) xi_l), Legendre chaos of total degree 3 (P = 20), Gaussian source
+at the centre: 322,580 complex unknowns; restarted GMRES(50), mean-value
+preconditioner, zero initial guess.  The timed step is one full solve of the
+mixed-precision path (complex64 Arnoldi inside FP64 iterative refinement)
+with b resident in HBM.  The preconditioner factorisation (done once per
+system in sg_assemble) is reported separately as setup_ms.
+
+Beside it the line reports: the plain FP64 GPU GMRES on the same workload,
+the end-to-end number through the C ABI with host buffers (host_io), the SG
+matvec bandwidth on the 511 x 511, s = 6, degree 3 workload (21.9 M unknowns,
+complex64), the roofline of the dominant kernel, clocks sampled during the
+timed region, and the CPU oracle timed on the host (cpu_baseline).
+
+--impl reference times the CPU oracle (oracle/, plain FP64 NumPy/SciPy) on the
+same workload, one solve per step.
+
+Multi-GPU: the solves are independent (replicas only): each rank solves its
+own copy, value = total solves / max rank time, scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SG-GMRES solves/s to rel.res 1e-8 (mixed precision, GMRES(50), mean-value preconditioner)"
+UNIT = "solves/s"
+WORKLOAD = {"workload": "helmholtz_2d_127x127_s3_deg3", "nodes": "127x127", "h": "1/126", "P": 20,
+            "unknowns": 322580, "kbar": 30.0, "sigma": 0.15, "restart": 50, "tol": 1e-8,
+            "preconditioner": "mean-value I(x)S(xi_bar)", "source": "gaussian w=0.02 at (0.5,0.5)"}
+MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_solve_seconds(repeats: int = 1):
+    """The CPU oracle on the same workload: GMRES(50) with the mean-value
+    block preconditioner (SuperLU of S(xi_bar) factored once, as the GPU
+    path's sg_assemble does), zero initial guess, tol 1e-8."""
+    from oracle import krylov, sg
+    from paper_2209_14740_gb300 import inputs
+    pr = inputs.config_2d_127()
+    S = sg.assemble_problem(pr)
+    M = krylov.BlockPrecond(S.S0, S.P)
+    times, its = [], []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        res = krylov.gmres(S.A, S.b, M, restart=50, tol=1e-8, maxit=2000)
+        times.append(time.perf_counter() - t0)
+        its.append(res.iters)
+        assert res.converged
+    return times, its
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_solve_seconds(1)
+    times, its = oracle_solve_seconds(args.steps)
+    ms = 1000.0 * statistics.mean(times)
+    value = 1000.0 / ms
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": dict(WORKLOAD, oracle="NumPy/SciPy FP64 GMRES(50) + SuperLU block preconditioner",
+                           world_size=world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d full oracle solves of the workload (%s iterations each)"
+                                       % (args.steps, its[0])},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2209_14740_gb300 import binding, inputs
+
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    B = binding
+    B.load()
+
+    # ---------------------------------------------------------------- set-up
+    pr = inputs.config_2d_127()
+    t0 = time.perf_counter()
+    op = B.SG(pr)
+    torch.cuda.synchronize()
+    setup_ms = 1000 * (time.perf_counter() - t0)
+    N = op.N
+    b = torch.empty(N, dtype=torch.complex128, device=dev)
+    op.rhs(b, B.FP64)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2 (129 MB)
+    solve = dict(restart=50, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED)
+
+    for _ in range(args.warmup):
+        op.gmres(b, x, **solve)
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- timed region
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    if rank == 0:
+        clk.start()
+    l0 = B.kernel_launches()
+    times, infos = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = op.gmres(b, x, **solve)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+    launches = B.kernel_launches() - l0
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop() if rank == 0 else None
+    ms = max_over_ranks(statistics.mean(times), world)
+    value = world * 1000.0 / ms
+    ok = all(i["status"] == B.SG_OK and i["relres"] <= 1e-8 for i in infos)
+
+    # ---------------------------------------------------------------- plain FP64 GPU GMRES, same workload
+    fp64 = dict(solve, mode=B.FP64)
+    op.gmres(b, x, **fp64)
+    t64, i64 = [], None
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i64 = op.gmres(b, x, **fp64)
+        e1.record(stream)
+        e1.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    fp64_ms = statistics.mean(t64)
+
+    # ---------------------------------------------------------------- end to end with host buffers
+    bh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+    bh.copy_(b)
+    xh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+    torch.cuda.synchronize()
+    te = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ie = op.gmres(bh.numpy(), xh.numpy(), host_io=True, **solve)
+        te.append(time.perf_counter() - t1)
+        assert ie["status"] == B.SG_OK
+    e2e_ms = 1000 * statistics.mean(te)
+    op.close()
+
+    # ---------------------------------------------------------------- matvec bandwidth (dominant HBM kernel)
+    mv = None
+    if rank == 0 and not args.skip_matvec:
+        pr3 = inputs.config_2d_511()
+        op3 = B.SG(pr3)
+        N3, n3, s3 = op3.N, op3.n, pr3.s
+        g = torch.Generator(device=dev).manual_seed(0)
+        X = torch.randn(N3, dtype=torch.complex64, device=dev, generator=g)
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            op3.matvec(X, Y, B.FP32)
+        torch.cuda.synchronize()
+        reps = 20
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for k in range(reps):
+            flush.zero_()
+            ev[2 * k].record(stream)
+            op3.matvec(X, Y, B.FP32)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        t_mv = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
+        bytes_mv = N3 * 8 * 2 + (s3 + 1) * n3 * 4
+        peak, peak_kind = load_peaks()
+        mv = {"workload": MATVEC_WORKLOAD, "dtype": "c64", "ms": t_mv, "bytes": bytes_mv,
+              "gbs": bytes_mv / (t_mv * 1e-3) / 1e9, "peak_gbs": peak, "peak_kind": peak_kind}
+        # FP64 operator on the same grid
+        X64 = X.to(torch.complex128)
+        Y64 = torch.empty_like(X64)
+        op3.matvec(X64, Y64, B.FP64)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        op3.matvec(X64, Y64, B.FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mv["fp64_ms"] = e0.elapsed_time(e1)
+        mv["fp64_gbs"] = (N3 * 16 * 2 + (s3 + 1) * n3 * 8) / (mv["fp64_ms"] * 1e-3) / 1e9
+        del X, Y, X64, Y64
+        op3.close()
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single", l2="flushed (256 MB write) "
+                       "before every timed solve", iterations=infos[-1]["iters"], outer=infos[-1]["outer"],
+                       relres=infos[-1]["relres"], all_converged=ok, setup_ms=setup_ms),
+        "fp64": {"solves_per_s": 1000.0 / fp64_ms, "ms": fp64_ms, "iterations": i64["iters"],
+                 "relres": i64["relres"], "mixed_speedup": fp64_ms / ms * world},
+        "e2e": {"value": 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if mv:
+        line["matvec"] = mv
+        line["roofline"] = {"kernel": "k_matvec (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
+                            "achieved": mv["gbs"], "peak": mv["peak_gbs"], "unit": "GB/s",
+                            "frac": mv["gbs"] / mv["peak_gbs"], "traffic": None,
+                            "peak_kind": mv["peak_kind"]}
+    if world == 1 and not args.skip_cpu:
+        times_c, its_c = oracle_solve_seconds(1)
+        line["cpu_baseline"] = {"value": 1.0 / times_c[0], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "1 full oracle solve of the workload (%d iterations), SuperLU single "
+                                          "threaded, NumPy BLAS on all cores" % its_c[0]}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-matvec", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

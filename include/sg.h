@@ -1,0 +1,196 @@
+/*
+ * sg.h -- C ABI of the GB300 stochastic Galerkin Helmholtz solver.
+ *
+ * The library solves the linear system A V = b that a finite-difference
+ * (FD) discretisation in space and a stochastic Galerkin (SG) projection in
+ * the random variables produce for
+ *
+ *     -Laplace(u) - k(x, xi)^2 u = f,    k(x, xi) = k_0(x) + sum_l xi_l k_l(x),
+ *
+ * with homogeneous Dirichlet or absorbing (d_n u - i k u = 0) boundary
+ * conditions and independent xi_l ~ U[-1, 1] (Pulch & Sete, "The Helmholtz
+ * equation with uncertainties in the wavenumber", Sec. 2 and Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named X, Y, R, Z, b, x, x0 are caller-owned buffers of
+ *     N = n * P complex numbers stored as interleaved (re, im) pairs,
+ *     complex128 for SG_FP64 and complex64 for SG_FP32.  They live in device
+ *     memory unless an entry point says otherwise.  Ordering is the paper's:
+ *     V = [V_0; V_1; ...; V_{P-1}] (mode-major, Sec. 3.1), each V_i over the
+ *     n grid unknowns with x fastest (Theorems A.5/A.6).
+ *   - n = number of grid unknowns (Dirichlet nodes are eliminated, absorbing
+ *     boundary nodes are kept), P = (s+r)!/(s! r!) chaos modes (Sec. 2.3).
+ *   - Chaos modes are ordered by total degree; inside one degree by
+ *     descending lexicographic order of the multi-index (alpha_1..alpha_s).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream unless stated.
+ *   - Every call returns an sg_status.  On failure sg_last_error() returns
+ *     a thread-local message; outputs are left unspecified.  No entry point
+ *     falls back to the CPU.
+ *   - The library owns the handle, its device fields, factors and
+ *     workspace (allocated by sg_assemble / the first sg_gmres call, freed by
+ *     sg_destroy).  Handles are not thread-safe; use one per host thread.
+ */
+#ifndef SG_GB300_H
+#define SG_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_handle sg_handle;
+
+typedef enum {
+  SG_OK = 0,
+  SG_EINVAL = 1,        /* bad argument (size, NULL pointer, NaN, k <= 0 ...) */
+  SG_ENOMEM = 2,        /* device or host allocation failed */
+  SG_ECUDA = 3,         /* a CUDA runtime call failed */
+  SG_ENOTCONV = 4,      /* GMRES stopped at maxit above tol (x = best iterate) */
+  SG_EBREAKDOWN = 5,    /* Arnoldi breakdown or non-finite value in the solve */
+  SG_ESINGULAR = 6,     /* zero pivot in a preconditioner factorisation */
+  SG_ETIMEOUT = 7,      /* device iteration watchdog fired */
+  SG_EUNSUPPORTED = 8   /* valid input the library does not implement */
+} sg_status;
+
+typedef enum { SG_BC_DIRICHLET = 0, SG_BC_ABSORBING = 1 } sg_bc;
+
+/* Preconditioners (Sec. 4, Sec. 5, Sec. 6.3):
+ *   SG_PREC_MEAN      mean-value A_0 = I_P (x) S(xi_bar), xi_bar = 0 for
+ *                     uniform variables, so S(xi_bar) is the FD matrix of the
+ *                     wavenumber k_0 (Sec. 5, Remark 6.1);
+ *   SG_PREC_CSL_MEAN  mean-value complex shifted Laplace
+ *                     M_0 = I_P (x) (S(xi_bar) - i beta D_2(k_0^2)) (Sec. 6.3). */
+typedef enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_CSL_MEAN = 2 } sg_prec;
+
+/* SG_FP64: complex128 operands and arithmetic.
+ * SG_FP32: complex64 operands and arithmetic (reductions accumulate in FP64
+ *          across thread blocks).
+ * SG_MIXED (sg_gmres only): complex64 inner GMRES inside an FP64 iterative
+ *          refinement loop; b, x, x0 are complex128. */
+typedef enum { SG_FP64 = 0, SG_FP32 = 1, SG_MIXED = 2 } sg_precision;
+
+/* Problem description (Sec. 2.2 wavenumber model; Appendix A grids).
+ *   dim    1 or 2 (unit interval / unit square).
+ *   nx,ny  grid nodes per direction INCLUDING boundary nodes (q+2 in the
+ *          paper's notation); ny = 1 when dim = 1.  h = mesh width.
+ *   bc     {left x=0, right x=1, bottom y=0, top y=1}; dim = 1 reads bc[0],
+ *          bc[1] (they may differ); dim = 2 requires all four equal
+ *          (Theorem A.5 all Dirichlet or Theorem A.6 all absorbing).
+ *   s, r   number of random variables and total chaos degree.
+ *   k0     host, nx*ny doubles: k_0 at every node, x fastest.
+ *   kl     host, s*nx*ny doubles, layout [l][node]: k_1..k_s (may be NULL
+ *          when s = 0).  k_0 - sum_l |k_l| must be > 0 at every node, the
+ *          positivity the paper assumes in Sec. 3.2.
+ *   f      host, nx*ny doubles: source values at the nodes (before FD
+ *          weights).  May be NULL (zero source).
+ *   beta   CSL shift for SG_PREC_CSL_MEAN (Sec. 4; the paper uses 1/2).
+ * The host arrays are read during sg_assemble only. */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double h;
+  int bc[4];
+  int s, r;
+  const double* k0;
+  const double* kl;
+  const double* f;
+  double beta;
+} sg_desc;
+
+typedef struct {
+  int dim;
+  int mx, my;          /* unknown grid (x, y); n = mx * my */
+  int n;               /* grid unknowns */
+  int P;               /* chaos modes */
+  long long N;         /* n * P */
+  int s, r;
+  int terms;           /* distinct coefficient fields of the coupling (2s + s(s-1)/2) */
+  int coupling_nnz;    /* nonzeros of the union P x P coupling pattern (incl. diagonal) */
+  int separable;       /* 1 if k_0 is constant: 2D preconditioners available */
+  int specialised;     /* 1 if a register-resident matvec kernel serves (s, r) */
+} sg_info;
+
+/* Builds the SG operator of Theorem 3.4 / Theorems A.1, A.2, A.5, A.6:
+ * chaos tables, node fields on the device, and the factorisations of the
+ * mean-value and CSL blocks (1D: tridiagonal LU with partial pivoting;
+ * 2D with constant k_0: eigenvectors of the 1D pencil in x plus tridiagonal
+ * LU with partial pivoting along y, all pivots in FP64).
+ * Returns SG_EINVAL on inconsistent sizes, NaN/Inf fields or k <= 0,
+ * SG_ESINGULAR if a factorisation meets a zero pivot.  *out is set only on
+ * success. */
+sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out);
+
+/* Frees everything the handle owns (synchronises the device first).  NULL
+ * is ignored. */
+void sg_destroy(sg_handle* h);
+
+sg_status sg_get_info(const sg_handle* h, sg_info* info);
+
+/* Writes the SG right-hand side b = e_0 (x) b_0 of Sec. 3.1, b_0 = D_2
+ * weights times f on the unknowns (F_0 of Theorem A.2, b_0 of Theorem A.6),
+ * into the device buffer b (N complex, precision prec: FP64 or FP32). */
+sg_status sg_rhs(sg_handle* h, sg_precision prec, void* b, void* stream);
+
+/* Y = A X, the SG matrix A = I_P (x) L - i[B_ij] - [C_ij] of Theorem 3.4,
+ * applied matrix-free: per grid point, the FD stencil of L on every mode
+ * plus the P x P coupling sum_t c_t(x) G_t (Sec. 3.2, c_ij and b_ij of the
+ * SG-then-FD route).  X and Y: device, N complex each, precision FP64 or
+ * FP32, must not overlap. */
+sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, void* stream);
+
+/* Z = (I_P (x) S_blk)^-1 R for the chosen block (see sg_prec), one
+ * factorisation applied to all P modes at once (the reshape of Sec. 6.3).
+ * SG_PREC_NONE copies R to Z.  R and Z: device, N complex; Z may equal R
+ * (in place).  Returns SG_EUNSUPPORTED for 2D problems whose k_0 varies in
+ * space (no separable factorisation). */
+sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
+                     void* stream);
+
+typedef struct {
+  int restart;          /* Krylov basis length per cycle; <= 0 means full GMRES (no restart) */
+  int maxit;            /* cap on total Arnoldi steps; <= 0 means N (FP64/FP32) */
+  int max_outer;        /* SG_MIXED: cap on refinement steps; <= 0 means 20 */
+  double tol;           /* stop when ||b - A x||_2 / ||b||_2 <= tol (Sec. 6.3) */
+  double inner_tol;     /* SG_MIXED: inner relative reduction per refinement step; <= 0 means 1e-4 */
+  sg_prec prec;         /* right preconditioner M: A M^-1 y = b, x = M^-1 y (Sec. 6.3) */
+  sg_precision mode;    /* SG_FP64, SG_FP32 or SG_MIXED */
+  const void* x0;       /* initial guess (same memory space and precision as x); NULL = zero */
+  int host_io;          /* 1: b, x0, x are HOST buffers (copied in and out inside the call) */
+  int check_every;      /* steps between host reads of the convergence flag; <= 0 means 8 */
+} sg_gmres_opts;
+
+typedef struct {
+  int iters;            /* Arnoldi steps over all cycles (and refinement steps) */
+  int outer;            /* SG_MIXED refinement steps (0 otherwise) */
+  int cycles;           /* restart cycles */
+  double relres;        /* final ||b - A x|| / ||b|| computed in FP64 (FP32 for SG_FP32) */
+  sg_status status;
+} sg_gmres_info;
+
+/* Solves A x = b with restarted, right-preconditioned GMRES: Arnoldi by
+ * classical Gram-Schmidt applied twice, complex Givens rotations in FP64 on
+ * the device, lazy normalisation of the basis (Sec. 6.3 names GMRES, this
+ * library fixes the variant).  b and x: N complex (complex128 for FP64 and
+ * MIXED, complex64 for FP32), device memory unless opts->host_io.  Blocks
+ * the calling host thread until the solve ends.  Returns SG_OK when relres
+ * <= tol, SG_ENOTCONV with the last iterate in x otherwise, SG_EBREAKDOWN on
+ * non-finite values.  info may be NULL. */
+sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void* x,
+                   sg_gmres_info* info, void* stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* sg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles, all threads; a diagnostic for benchmarks). */
+long long sg_kernel_launches(void);
+
+/* ABI version: 100 * major + minor. */
+int sg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

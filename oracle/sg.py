@@ -121,6 +121,46 @@ def realisation_matrix(sys: SGSystem, k0, kl, xi) -> sp.csr_matrix:
     return fd.deterministic_matrix(sys.grid, k)
 
 
+def apply_rows(prob, x, rows, absolute: bool = False) -> np.ndarray:
+    """Selected entries (A x)[rows] without assembling A, for sizes where the
+    explicit matrix does not fit: row (a, u) of A is the row u of the FD
+    Laplacian L applied to V_a plus row a of the per-node coupling
+    -i w1(u) <k phi phi> - w2(u) <k^2 phi phi> applied to (V_0(u), ..., V_{P-1}(u))
+    (Theorem 3.4; Sec. 3.2, c_ij and b_ij).  With absolute=True returns the
+    sum of |term| over the Laplacian part and the coupling part taken
+    separately (>= (|A| |x|)[rows]), the scale of the rounding error of a
+    row computed as those two parts.
+
+    Pinned by tests/test_oracle_sg.py against the explicit assembly."""
+    grid = fd.make_grid(prob.dim, prob.nx, prob.ny, prob.h, prob.bc)
+    n = len(grid.unknowns)
+    s, r = prob.s, prob.r
+    P = pc.num_modes(s, r)
+    X = np.asarray(x).reshape(P, n)
+    if absolute:
+        X = np.abs(X)
+    k0 = np.asarray(prob.k0, dtype=float).reshape(-1)[grid.unknowns]
+    kl = np.asarray(prob.kl, dtype=float).reshape(s, -1)[:, grid.unknowns] if s else np.zeros((0, n))
+    G1, G2 = pc.expectation_matrices(s, r)
+    L = grid.L.tocsr()
+    if absolute:
+        L = abs(L)
+    out = np.zeros(len(rows), dtype=complex if not absolute else float)
+    for t, row in enumerate(np.asarray(rows)):
+        a, u = divmod(int(row), n)
+        lap = (L.getrow(u) @ X[a])[0]
+        K1 = k0[u] * np.eye(P) + sum(kl[l, u] * G1[l] for l in range(s))
+        K2 = k0[u] ** 2 * np.eye(P) + sum(2 * k0[u] * kl[l, u] * G1[l] for l in range(s))
+        for (l, lp), G in G2.items():
+            K2 = K2 + (1.0 if l == lp else 2.0) * kl[l, u] * kl[lp, u] * G
+        M = -1j * grid.w1[u] * K1 - grid.w2[u] * K2
+        if absolute:
+            out[t] = abs(lap) + np.abs(M[a]) @ X[:, u]
+        else:
+            out[t] = lap + M[a] @ X[:, u]
+    return out
+
+
 def modes(sys: SGSystem, x: np.ndarray) -> np.ndarray:
     """Reshape an SG vector into (P, n): row i is V_i (Sec. 3.1)."""
     return np.asarray(x).reshape(sys.P, -1)

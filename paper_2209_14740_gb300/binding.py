@@ -1,0 +1,180 @@
+"""Thin Python binding of the C ABI in include/sg.h (argument marshalling only).
+
+Every computation runs in libsg_gb300.so.  Device buffers are passed as raw
+pointers taken from torch tensors (torch supplies device memory and streams,
+nothing else).  If the shared library is missing this module raises at once:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsg_gb300.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ENOTCONV, SG_EBREAKDOWN, SG_ESINGULAR, SG_ETIMEOUT, SG_EUNSUPPORTED = range(9)
+STATUS_NAMES = ["SG_OK", "SG_EINVAL", "SG_ENOMEM", "SG_ECUDA", "SG_ENOTCONV", "SG_EBREAKDOWN",
+                "SG_ESINGULAR", "SG_ETIMEOUT", "SG_EUNSUPPORTED"]
+BC_DIRICHLET, BC_ABSORBING = 0, 1
+PREC_NONE, PREC_MEAN, PREC_CSL_MEAN = 0, 1, 2
+FP64, FP32, MIXED = 0, 1, 2
+
+# every symbol include/sg.h declares
+EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "sg_precond", "sg_gmres",
+            "sg_last_error", "sg_version", "sg_kernel_launches"]
+
+
+class SgDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("h", C.c_double),
+                ("bc", C.c_int * 4), ("s", C.c_int), ("r", C.c_int),
+                ("k0", C.POINTER(C.c_double)), ("kl", C.POINTER(C.c_double)), ("f", C.POINTER(C.c_double)),
+                ("beta", C.c_double)]
+
+
+class SgInfo(C.Structure):
+    _fields_ = [("dim", C.c_int), ("mx", C.c_int), ("my", C.c_int), ("n", C.c_int), ("P", C.c_int),
+                ("N", C.c_longlong), ("s", C.c_int), ("r", C.c_int), ("terms", C.c_int),
+                ("coupling_nnz", C.c_int), ("separable", C.c_int), ("specialised", C.c_int)]
+
+
+class SgGmresOpts(C.Structure):
+    _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("max_outer", C.c_int), ("tol", C.c_double),
+                ("inner_tol", C.c_double), ("prec", C.c_int), ("mode", C.c_int), ("x0", C.c_void_p),
+                ("host_io", C.c_int), ("check_every", C.c_int)]
+
+
+class SgGmresInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("cycles", C.c_int), ("relres", C.c_double),
+                ("status", C.c_int)]
+
+
+class SgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load the shared library (raises OSError if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("libsg_gb300.so not built (run __graft_entry__.build()): %s" % path)
+    lib = C.CDLL(path)
+    vp, i = C.c_void_p, C.c_int
+    lib.sg_assemble.argtypes = [C.POINTER(SgDesc), vp, C.POINTER(vp)]
+    lib.sg_assemble.restype = i
+    lib.sg_destroy.argtypes = [vp]
+    lib.sg_destroy.restype = None
+    lib.sg_get_info.argtypes = [vp, C.POINTER(SgInfo)]
+    lib.sg_get_info.restype = i
+    lib.sg_rhs.argtypes = [vp, i, vp, vp]
+    lib.sg_rhs.restype = i
+    lib.sg_matvec.argtypes = [vp, i, vp, vp, vp]
+    lib.sg_matvec.restype = i
+    lib.sg_precond.argtypes = [vp, i, i, vp, vp, vp]
+    lib.sg_precond.restype = i
+    lib.sg_gmres.argtypes = [vp, C.POINTER(SgGmresOpts), vp, vp, C.POINTER(SgGmresInfo), vp]
+    lib.sg_gmres.restype = i
+    lib.sg_last_error.argtypes = []
+    lib.sg_last_error.restype = C.c_char_p
+    lib.sg_version.argtypes = []
+    lib.sg_version.restype = i
+    lib.sg_kernel_launches.argtypes = []
+    lib.sg_kernel_launches.restype = C.c_longlong
+    _lib = lib
+    return lib
+
+
+def kernel_launches() -> int:
+    return int(load().sg_kernel_launches())
+
+
+def _check(st):
+    if st != SG_OK:
+        raise SgError(st, load().sg_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """Raw data pointer of a torch tensor or a numpy array."""
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+class SG:
+    """One assembled SG Helmholtz system (owns an sg_handle)."""
+
+    def __init__(self, prob, stream=None):
+        lib = load()
+        self._keep = []
+        k0 = np.ascontiguousarray(prob.k0, dtype=np.float64)
+        kl = np.ascontiguousarray(np.asarray(prob.kl, dtype=np.float64).reshape(-1))
+        f = np.ascontiguousarray(prob.f, dtype=np.float64)
+        self._keep += [k0, kl, f]
+        d = SgDesc()
+        d.dim, d.nx, d.ny, d.h = prob.dim, prob.nx, prob.ny, prob.h
+        for k in range(4):
+            d.bc[k] = int(prob.bc[k])
+        d.s, d.r = prob.s, prob.r
+        dp = C.POINTER(C.c_double)
+        d.k0 = k0.ctypes.data_as(dp)
+        d.kl = kl.ctypes.data_as(dp) if kl.size else None
+        d.f = f.ctypes.data_as(dp)
+        d.beta = float(getattr(prob, "beta", 0.5))
+        h = C.c_void_p()
+        _check(lib.sg_assemble(C.byref(d), _stream(stream), C.byref(h)))
+        self.h = h
+        inf = SgInfo()
+        _check(lib.sg_get_info(h, C.byref(inf)))
+        self.info = {k: getattr(inf, k) for k, _ in SgInfo._fields_}
+        self.n, self.P, self.N = inf.n, inf.P, inf.N
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rhs(self, b, prec=FP64, stream=None):
+        _check(load().sg_rhs(self.h, prec, _ptr(b), _stream(stream)))
+
+    def matvec(self, X, Y, prec=FP64, stream=None):
+        _check(load().sg_matvec(self.h, prec, _ptr(X), _ptr(Y), _stream(stream)))
+
+    def precond(self, R, Z, kind=PREC_MEAN, prec=FP64, stream=None):
+        _check(load().sg_precond(self.h, kind, prec, _ptr(R), _ptr(Z), _stream(stream)))
+
+    def gmres(self, b, x, *, restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, x0=None, max_outer=0,
+              inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False):
+        o = SgGmresOpts()
+        o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
+        o.prec, o.mode = prec, mode
+        o.x0 = _ptr(x0) if x0 is not None else None
+        o.host_io = 1 if host_io else 0
+        o.check_every = check_every
+        inf = SgGmresInfo()
+        st = load().sg_gmres(self.h, C.byref(o), _ptr(b), _ptr(x), C.byref(inf),
+                             None if host_io and stream is None else _stream(stream))
+        if st not in (SG_OK, SG_ENOTCONV) or (raise_on_notconv and st == SG_ENOTCONV):
+            _check(st)
+        return dict(iters=inf.iters, outer=inf.outer, cycles=inf.cycles, relres=inf.relres, status=st)

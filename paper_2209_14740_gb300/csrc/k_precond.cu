@@ -1,0 +1,297 @@
+// Block preconditioners of Sec. 5 and Sec. 6.3 applied to all P chaos modes
+// with one factorisation:  Z = (I_P (x) S_blk)^-1 R.
+//
+// 1D: S_blk is tridiagonal (Theorems A.1/A.2); LU with partial pivoting in
+//     FP64 (LAPACK gttrf scheme) and a forward/back substitution per mode.
+// 2D with constant k_0 (Theorems A.5/A.6): S_blk = D_y (x) H_x + H_y (x) D_x
+//     with H = T - i (k_0/h) E - (k_0^2/2) D per direction.  With
+//     G = D^-1/2 H D^-1/2 = Q Lambda Q^T (complex symmetric, Q^T Q = I) the
+//     Sylvester form G_x W + W G_y = D_x^-1/2 R D_y^-1/2 is solved by
+//       (1) Z' = R Qhat            (Qhat = D_x^-1/2 Q; one complex GEMM over
+//                                   all P*my lines of length mx),
+//       (2) per eigen-index i: ((lambda_i + shift) I + G_y) z_i = d_y^-1/2 z'_i
+//           (tridiagonal along y, LU with partial pivoting in FP64),
+//       (3) Z = (d_y^-1/2 z) Qhat^T (second GEMM).
+//     The CSL block adds -i beta k_0^2 D_2, i.e. shift = -i beta k_0^2.
+#include <cuda_runtime.h>
+
+#include "sg_internal.h"
+
+namespace sgi {
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double zabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  // Smith's algorithm
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, den = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / den, (a.y - a.x * r) / den);
+  } else {
+    double r = b.x / b.y, den = b.x * r + b.y;
+    return make_double2((a.x * r + a.y) / den, (a.y * r - a.x) / den);
+  }
+}
+
+// One thread per system: LU with partial pivoting of the tridiagonal matrix
+// with diagonal diag[j] + lam_shift[sys] and symmetric off-diagonal off[j]
+// (real).  Writes FP64 factors and FP32 copies; sets *bad on a zero pivot.
+__global__ void k_tri_factor(int nsys, int len, const double2* __restrict__ diag,
+                             const double2* __restrict__ lam_shift, const double* __restrict__ off,
+                             TriFactors<double> F, TriFactors<float> G, int* bad) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= nsys) return;
+  const double2 sh = lam_shift ? lam_shift[sys] : make_double2(0, 0);
+  auto at = [&](int j) { return (size_t)j * nsys + sys; };
+  // d_j, du_j, dl_j of the current (partially eliminated) rows
+  double2 dcur = make_double2(diag[0].x + sh.x, diag[0].y + sh.y);
+  double2 ducur = make_double2(len > 1 ? off[0] : 0.0, 0.0);
+  double2 du2prev = make_double2(0, 0);
+  bool zero = false;
+  for (int j = 0; j < len; ++j) {
+    if (j == len - 1) {
+      if (dcur.x == 0.0 && dcur.y == 0.0) zero = true;
+      const double2 di = zero ? make_double2(0, 0) : zdiv(make_double2(1, 0), dcur);
+      F.dinv[at(j)] = di;
+      F.du[at(j)] = make_double2(0, 0);
+      F.du2[at(j)] = make_double2(0, 0);
+      F.dl[at(j)] = make_double2(0, 0);
+      F.piv[at(j)] = 0;
+      break;
+    }
+    const double2 dl = make_double2(off[j], 0.0);             // sub-diagonal entry (row j+1, col j)
+    const double2 dnext = make_double2(diag[j + 1].x + sh.x, diag[j + 1].y + sh.y);
+    const double2 dunext = make_double2(j + 2 < len ? off[j + 1] : 0.0, 0.0);
+    double2 fact, d_j, du_j, du2_j, d_n, du_n;
+    uint8_t p;
+    if (zabs1(dcur) >= zabs1(dl)) {
+      if (dcur.x == 0.0 && dcur.y == 0.0) { zero = true; fact = make_double2(0, 0); }
+      else fact = zdiv(dl, dcur);
+      d_j = dcur; du_j = ducur; du2_j = make_double2(0, 0);
+      d_n = zsub(dnext, zmul(fact, ducur));
+      du_n = dunext;
+      p = 0;
+    } else {
+      fact = zdiv(dcur, dl);
+      d_j = dl;
+      du_j = dnext;
+      d_n = zsub(ducur, zmul(fact, dnext));
+      du2_j = dunext;
+      du_n = make_double2(-(fact.x * dunext.x - fact.y * dunext.y), -(fact.x * dunext.y + fact.y * dunext.x));
+      p = 1;
+    }
+    (void)du2prev;
+    F.dl[at(j)] = fact;
+    F.dinv[at(j)] = zdiv(make_double2(1, 0), d_j);
+    F.du[at(j)] = du_j;
+    F.du2[at(j)] = du2_j;
+    F.piv[at(j)] = p;
+    dcur = d_n;
+    ducur = du_n;
+  }
+  for (int j = 0; j < len; ++j) {
+    const size_t k = at(j);
+    G.dl[k] = make_float2((float)F.dl[k].x, (float)F.dl[k].y);
+    G.dinv[k] = make_float2((float)F.dinv[k].x, (float)F.dinv[k].y);
+    G.du[k] = make_float2((float)F.du[k].x, (float)F.du[k].y);
+    G.du2[k] = make_float2((float)F.du2[k].x, (float)F.du2[k].y);
+  }
+  if (zero) atomicExch(bad, 1);
+}
+
+cudaError_t launch_tri_factor(int nsys, int len, const double2* diag, const double2* lam_shift, const double* off,
+                              TriFactors<double> f64, TriFactors<float> f32, int* d_bad, cudaStream_t st) {
+  const int blk = 128;
+  k_tri_factor<<<(nsys + blk - 1) / blk, blk, 0, st>>>(nsys, len, diag, lam_shift, off, f64, f32, d_bad); note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- complex helpers
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  C2<T> r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) {
+  C2<T> r;
+  r.x = a.x - b.x;
+  r.y = a.y - b.y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cscale(C2<T> a, T s) {
+  C2<T> r;
+  r.x = a.x * s;
+  r.y = a.y * s;
+  return r;
+}
+
+// Multi-RHS tridiagonal solve with gttrf factors.  Thread (sys, rhs) walks
+// j = 0..len-1; element address rhs*sR + j*sJ + sys*sS; factors at
+// j*nsys + sys.  Optional row scaling s_j applied to the input and the output
+// (2D: d_y^-1/2).  In place on Z (Z may alias R).
+template <typename T>
+__global__ void k_tri_solve(int nsys, int nrhs, int len, long long sR, long long sJ, long long sS,
+                            TriFactors<T> F, const T* __restrict__ rowscale, const C2<T>* R, C2<T>* Z,
+                            const int* skip, const double* in_scale) {
+  if (skip && *skip) return;
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
+  if (sys >= nsys || rhs >= nrhs) return;
+  const C2<T>* r = R + rhs * sR + sys * sS;
+  C2<T>* z = Z + rhs * sR + sys * sS;
+  auto f = [&](int j) { return (size_t)j * nsys + sys; };
+  // forward: apply row interchanges and L
+  // optional scalar factor on the input (the solve is linear)
+  const T s0 = in_scale ? (T)*in_scale : T(1);
+  C2<T> cur = cscale<T>(r[0], rowscale ? rowscale[0] * s0 : s0);
+  for (int j = 0; j + 1 < len; ++j) {
+    const C2<T> nxt = cscale<T>(r[(j + 1) * sJ], rowscale ? rowscale[j + 1] * s0 : s0);
+    const C2<T> l = F.dl[f(j)];
+    if (!F.piv[f(j)]) {
+      z[j * sJ] = cur;
+      cur = csub<T>(nxt, cmul<T>(l, cur));
+    } else {
+      z[j * sJ] = nxt;
+      cur = csub<T>(cur, cmul<T>(l, nxt));
+    }
+  }
+  // back substitution with U (diagonal, du, du2)
+  C2<T> x1 = cmul<T>(cur, F.dinv[f(len - 1)]);  // x_{j+1}
+  C2<T> x2;                                        // x_{j+2}
+  x2.x = T(0);
+  x2.y = T(0);
+  {
+    C2<T> o = rowscale ? cscale<T>(x1, rowscale[len - 1]) : x1;
+    z[(len - 1) * sJ] = o;
+  }
+  for (int j = len - 2; j >= 0; --j) {
+    C2<T> b = z[j * sJ];
+    b = csub<T>(b, cmul<T>(F.du[f(j)], x1));
+    b = csub<T>(b, cmul<T>(F.du2[f(j)], x2));
+    const C2<T> xj = cmul<T>(b, F.dinv[f(j)]);
+    z[j * sJ] = rowscale ? cscale<T>(xj, rowscale[j]) : xj;
+    x2 = x1;
+    x1 = xj;
+  }
+}
+
+// C[M][Nn] = A[M][K] * B[K][Nn], complex, row-major, CUDA cores.
+// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>* __restrict__ A,
+                                              const C2<T>* __restrict__ B, C2<T>* __restrict__ C,
+                                              const int* skip) {
+  if (skip && *skip) return;
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ C2<T> As[BK][BM + 1];
+  __shared__ C2<T> Bs[BK][BN];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  T accr[4][4], acci[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      const int mm = e / BK, kk = e % BK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      C2<T> v;
+      v.x = T(0);
+      v.y = T(0);
+      if (gm < M && gk < K) v = A[(size_t)gm * K + gk];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < BK * BN; e += 256) {
+      const int kk = e / BN, nn = e % BN;
+      const int gk = k0 + kk, gn = n0 + nn;
+      C2<T> v;
+      v.x = T(0);
+      v.y = T(0);
+      if (gk < K && gn < Nn) v = B[(size_t)gk * Nn + gn];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      C2<T> a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] += a[i].x * b[j].x - a[i].y * b[j].y;
+          acci[i][j] += a[i].x * b[j].y + a[i].y * b[j].x;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn < Nn) {
+        C2<T> v;
+        v.x = accr[i][j];
+        v.y = acci[i][j];
+        C[(size_t)gm * Nn + gn] = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+static cudaError_t cgemm(int M, int Nn, int K, const C2<T>* A, const C2<T>* B, C2<T>* C, cudaStream_t st,
+                         const int* skip) {
+  dim3 grid((Nn + 63) / 64, (M + 63) / 64);
+  k_cgemm<T><<<grid, 256, 0, st>>>(M, Nn, K, A, B, C, skip); note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
+                           const int* skip, const double* in_scale) {
+  const PrecBlock& blk = h->blk[which];
+  TriFactors<T> F;
+  if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;
+  if (h->dim == 1) {
+    // one system of length n, P right-hand sides (the modes)
+    dim3 b(1, 64), g(1, (h->P + 63) / 64);
+    k_tri_solve<T><<<g, b, 0, st>>>(1, h->P, h->n, h->n, 1, 0, F, nullptr, R, Z, skip, in_scale); note_launch();
+    return cudaGetLastError();
+  }
+  const int mx = h->mx, my = h->my, P = h->P;
+  const C2<T>* Q;
+  const C2<T>* Qt;
+  const T* dyinv;
+  if constexpr (sizeof(T) == 8) { Q = h->d_Q; Qt = h->d_Qt; dyinv = h->d_dyinv; }
+  else { Q = h->d_Q32; Qt = h->d_Qt32; dyinv = h->d_dyinv32; }
+  C2<T>* tmp = reinterpret_cast<C2<T>*>(h->d_tmp);
+  cudaError_t e = cgemm<T>(P * my, mx, mx, R, Q, tmp, st, skip);      // (1)
+  if (e != cudaSuccess) return e;
+  dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);                  // (2) sys = i, rhs = mode, j = y line
+  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, (long long)mx * my, mx, 1, F, dyinv, tmp, tmp, skip,
+                                  in_scale); note_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cgemm<T>(P * my, mx, mx, tmp, Qt, Z, st, skip);               // (3)
+}
+
+template cudaError_t launch_precond<double>(const sg_handle*, int, const double2*, double2*, cudaStream_t,
+                                           const int*, const double*);
+template cudaError_t launch_precond<float>(const sg_handle*, int, const float2*, float2*, cudaStream_t, const int*,
+                                          const double*);
+
+}  // namespace sgi

@@ -1,0 +1,617 @@
+// Host side of the SG Helmholtz library: problem validation, chaos tables,
+// node fields, preconditioner set-up and the operator entry points of the
+// C ABI (include/sg.h).
+//
+// Paper sections implemented here:
+//  * Sec. 2.2/2.3: multi-indices of total degree <= r, orthonormal Legendre
+//    chaos; Galerkin products of the wavenumber model k = k_0 + sum xi_l k_l.
+//  * Lemma 3.2 / Lemma A.3: the coupling of modes a, b is a sum of
+//    coefficient fields times <xi_l phi_a phi_b> or <xi_l xi_l' phi_a phi_b>;
+//    only pairs whose multi-indices differ by e_l, 2 e_l or e_l +- e_l' couple.
+//  * Appendix A: FD weights; the right-hand side b_0 = D_2-weights * f.
+//  * Sec. 5 / Sec. 6.3: mean-value and CSL-mean blocks and their one-time
+//    factorisation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <atomic>
+
+#include "sg_internal.h"
+
+namespace sgi {
+
+static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_err = msg; }
+sg_status fail(sg_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+// ------------------------------------------------------------------ chaos tables
+// Recurrence coefficient of the orthonormal Legendre polynomials under the
+// uniform density on [-1, 1]: xi p_n = b_{n+1} p_{n+1} + b_n p_{n-1}.
+static double leg_b(int n) { return n <= 0 ? 0.0 : n / std::sqrt(4.0 * n * n - 1.0); }
+
+// Multi-indices of total degree <= r: graded, descending lexicographic inside
+// a degree (the ordering the ABI documents).
+static void enumerate_level(int s, int left, std::vector<int>& cur, std::vector<int>& out) {
+  int pos = (int)cur.size();
+  if (pos == s - 1) {
+    cur.push_back(left);
+    out.insert(out.end(), cur.begin(), cur.end());
+    cur.pop_back();
+    return;
+  }
+  for (int a = left; a >= 0; --a) {
+    cur.push_back(a);
+    enumerate_level(s, left - a, cur, out);
+    cur.pop_back();
+  }
+}
+
+static std::vector<int> multi_indices(int s, int r) {
+  std::vector<int> out;
+  if (s == 0) return out;
+  std::vector<int> cur;
+  for (int d = 0; d <= r; ++d) enumerate_level(s, d, cur, out);
+  return out;
+}
+
+static int pair_index(int s, int l, int lp) {  // l < lp
+  int idx = 0;
+  for (int a = 0; a < l; ++a) idx += s - 1 - a;
+  return idx + (lp - l - 1);
+}
+
+// Coupling of mode a with mode b != a.  Returns false if they do not couple.
+// Term ids: [0, s) <xi_l phi phi> (coefficient -2 w2 k0 k_l - i w1 k_l);
+// [s, 2s) <xi_l^2 phi phi> off the diagonal (coefficient -w2 k_l^2);
+// [2s, 2s + s(s-1)/2) <xi_l xi_l' phi phi>, l < l' (coefficient -2 w2 k_l k_l').
+static bool coupling(int s, const int* aa, const int* bb, int* term, double* g) {
+  int nd = 0, l1 = -1, l2 = -1, dmax = 0;
+  for (int t = 0; t < s; ++t) {
+    int d = std::abs(aa[t] - bb[t]);
+    if (d) {
+      ++nd;
+      if (l1 < 0) l1 = t; else l2 = t;
+      dmax = std::max(dmax, d);
+    }
+  }
+  if (nd == 1 && dmax == 1) {
+    *term = l1;
+    *g = leg_b(std::max(aa[l1], bb[l1]));
+    return true;
+  }
+  if (nd == 1 && dmax == 2) {
+    int m = std::min(aa[l1], bb[l1]);
+    *term = s + l1;
+    *g = leg_b(m + 1) * leg_b(m + 2);
+    return true;
+  }
+  if (nd == 2 && dmax == 1) {
+    *term = 2 * s + pair_index(s, l1, l2);
+    *g = leg_b(std::max(aa[l1], bb[l1])) * leg_b(std::max(aa[l2], bb[l2]));
+    return true;
+  }
+  return false;
+}
+
+static int binom(int n, int k) {
+  long long v = 1;
+  for (int i = 1; i <= k; ++i) v = v * (n - k + i) / i;
+  return (int)v;
+}
+
+// ------------------------------------------------------------------ eigenpairs
+// Eigenvalues of a complex symmetric tridiagonal matrix by implicit QL with
+// complex orthogonal rotations (c^2 + s^2 = 1), eigenvectors by inverse
+// iteration, normalised so that v^T v = 1 (then Q^T Q = I for distinct
+// eigenvalues and Q^-1 = Q^T).
+static bool csym_ql(int n, std::vector<cd>& d, std::vector<cd> e) {
+  e.resize(n, 0.0);
+  const double eps = 2.2e-16;
+  for (int l = 0; l < n; ++l) {
+    int iter = 0, m;
+    do {
+      for (m = l; m < n - 1; ++m) {
+        double dd = std::abs(d[m]) + std::abs(d[m + 1]);
+        if (std::abs(e[m]) <= eps * dd) break;
+      }
+      if (m != l) {
+        if (iter++ == 80) return false;
+        cd g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        cd r = std::sqrt(g * g + 1.0);
+        cd den = (std::abs(g + r) >= std::abs(g - r)) ? g + r : g - r;
+        g = d[m] - d[l] + e[l] / den;
+        cd s = 1.0, c = 1.0, p = 0.0;
+        int i;
+        bool underflow = false;
+        for (i = m - 1; i >= l; --i) {
+          cd f = s * e[i], b = c * e[i];
+          r = std::sqrt(f * f + g * g);
+          e[i + 1] = r;
+          if (std::abs(r) < 1e-300 * (std::abs(f) + std::abs(g) + 1e-300)) {
+            d[i + 1] -= p;
+            e[m] = 0.0;
+            underflow = true;
+            break;
+          }
+          s = f / r;
+          c = g / r;
+          g = d[i + 1] - p;
+          r = (d[i] - g) * s + 2.0 * c * b;
+          p = s * r;
+          d[i + 1] = g + p;
+          g = c * r - b;
+        }
+        if (underflow && i >= l) continue;
+        d[l] -= p;
+        e[l] = g;
+        e[m] = 0.0;
+      }
+    } while (m != l);
+  }
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(d[i].real()) || !std::isfinite(d[i].imag())) return false;
+  return true;
+}
+
+// Solve (T - mu I) x = b for tridiagonal complex symmetric T with partial
+// pivoting (in place on b).
+static void tri_shift_solve(int n, const std::vector<cd>& diag, const std::vector<cd>& off, cd mu,
+                            std::vector<cd>& b) {
+  std::vector<cd> d(n), dl(n > 1 ? n - 1 : 1), du(n > 1 ? n - 1 : 1), du2(n > 2 ? n - 2 : 1, 0.0);
+  std::vector<int> piv(n, 0);
+  for (int i = 0; i < n; ++i) d[i] = diag[i] - mu;
+  for (int i = 0; i + 1 < n; ++i) dl[i] = du[i] = off[i];
+  double tiny = 1e-300;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (std::abs(d[i]) >= std::abs(dl[i])) {
+      if (std::abs(d[i]) < tiny) d[i] = tiny;
+      cd fact = dl[i] / d[i];
+      dl[i] = fact;
+      d[i + 1] -= fact * du[i];
+      piv[i] = 0;
+    } else {
+      cd fact = d[i] / dl[i];
+      d[i] = dl[i];
+      dl[i] = fact;
+      cd temp = du[i];
+      du[i] = d[i + 1];
+      d[i + 1] = temp - fact * d[i + 1];
+      if (i + 2 < n) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -fact * du[i + 1];
+      }
+      piv[i] = 1;
+    }
+  }
+  if (std::abs(d[n - 1]) < 1e-250) d[n - 1] = 1e-250;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (!piv[i]) {
+      b[i + 1] -= dl[i] * b[i];
+    } else {
+      cd t = b[i];
+      b[i] = b[i + 1];
+      b[i + 1] = t - dl[i] * b[i];
+    }
+  }
+  b[n - 1] /= d[n - 1];
+  if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / d[n - 2];
+  for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / d[i];
+}
+
+bool csym_tridiag_eig(int n, const std::vector<cd>& diag, const std::vector<cd>& off,
+                      std::vector<cd>& lam, std::vector<cd>& Q, double* orth_err) {
+  lam = diag;
+  if (!csym_ql(n, lam, off)) return false;
+  std::sort(lam.begin(), lam.end(), [](cd a, cd b) { return a.real() < b.real(); });
+  Q.assign((size_t)n * n, 0.0);   // column k = eigenvector k, row-major Q[i*n + k]
+  double scale = 0;
+  for (int i = 0; i < n; ++i) scale = std::max(scale, std::abs(diag[i]) + 2 * (i < n - 1 ? std::abs(off[i]) : 0));
+  std::vector<cd> v(n);
+  for (int k = 0; k < n; ++k) {
+    cd mu = lam[k] + cd(1e-13 * scale, 1e-13 * scale);
+    for (int i = 0; i < n; ++i) v[i] = cd(1.0 + 0.37 * std::sin(1.7 * i + 0.3 * k), 0.11 * std::cos(0.9 * i));
+    for (int it = 0; it < 3; ++it) {
+      tri_shift_solve(n, diag, off, mu, v);
+      double m = 0;
+      for (int i = 0; i < n; ++i) m = std::max(m, std::abs(v[i]));
+      for (int i = 0; i < n; ++i) v[i] /= m;
+    }
+    cd vtv = 0;
+    for (int i = 0; i < n; ++i) vtv += v[i] * v[i];
+    cd nrm = std::sqrt(vtv);
+    if (std::abs(nrm) < 1e-200) return false;
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + k] = v[i] / nrm;
+  }
+  // complex-symmetric orthogonality check Q^T Q = I
+  double err = 0;
+  for (int a = 0; a < n; ++a)
+    for (int b = a; b < n; ++b) {
+      cd sacc = 0;
+      for (int i = 0; i < n; ++i) sacc += Q[(size_t)i * n + a] * Q[(size_t)i * n + b];
+      err = std::max(err, std::abs(sacc - (a == b ? 1.0 : 0.0)));
+    }
+  if (orth_err) *orth_err = err;
+  return err < 1e-6;
+}
+
+}  // namespace sgi
+
+using namespace sgi;
+
+// ------------------------------------------------------------------ handle helpers
+OpParams<double> sg_handle::op64() const {
+  OpParams<double> p{};
+  p.dim = dim; p.mx = mx; p.my = my; p.n = n; p.P = P; p.s = s; p.T_terms = T_terms;
+  p.absL = bc[0] == SG_BC_ABSORBING; p.absR = bc[1] == SG_BC_ABSORBING;
+  p.absB = dim == 2 && bc[2] == SG_BC_ABSORBING; p.absT = dim == 2 && bc[3] == SG_BC_ABSORBING;
+  p.h = h; p.inv_h = 1.0 / h; p.inv_h2 = 1.0 / (h * h);
+  p.rowptr = d_rowptr; p.col = d_col; p.term = d_term; p.gval = d_gval; p.gdiag = d_gdiag;
+  p.fields = d_fields;
+  p.skip = nullptr;
+  return p;
+}
+
+OpParams<float> sg_handle::op32() const {
+  OpParams<float> p{};
+  p.dim = dim; p.mx = mx; p.my = my; p.n = n; p.P = P; p.s = s; p.T_terms = T_terms;
+  p.absL = bc[0] == SG_BC_ABSORBING; p.absR = bc[1] == SG_BC_ABSORBING;
+  p.absB = dim == 2 && bc[2] == SG_BC_ABSORBING; p.absT = dim == 2 && bc[3] == SG_BC_ABSORBING;
+  p.h = (float)h; p.inv_h = (float)(1.0 / h); p.inv_h2 = (float)(1.0 / (h * h));
+  p.rowptr = d_rowptr; p.col = d_col; p.term = d_term; p.gval = d_gval32; p.gdiag = d_gdiag32;
+  p.fields = d_fields32;
+  p.skip = nullptr;
+  return p;
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const T* src, size_t count) {
+  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (count) e = cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+static void free_factors(PrecBlock& b) {
+  cudaFree(b.f64.dl); cudaFree(b.f64.dinv); cudaFree(b.f64.du); cudaFree(b.f64.du2); cudaFree(b.f64.piv);
+  cudaFree(b.f32.dl); cudaFree(b.f32.dinv); cudaFree(b.f32.du); cudaFree(b.f32.du2);
+  b = PrecBlock{};
+}
+
+static cudaError_t alloc_factors(PrecBlock& b, size_t cnt) {
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&b.f64.dl, cnt * sizeof(double2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f64.dinv, cnt * sizeof(double2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f64.du, cnt * sizeof(double2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f64.du2, cnt * sizeof(double2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f64.piv, cnt))) return e;
+  if ((e = cudaMalloc((void**)&b.f32.dl, cnt * sizeof(float2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f32.dinv, cnt * sizeof(float2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f32.du, cnt * sizeof(float2)))) return e;
+  if ((e = cudaMalloc((void**)&b.f32.du2, cnt * sizeof(float2)))) return e;
+  b.f32.piv = b.f64.piv;
+  return cudaSuccess;
+}
+
+void sgi_free_gmres_work(sg_handle* h);  // solver.cu
+
+static void destroy_impl(sg_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  cudaFree(h->d_rowptr); cudaFree(h->d_col); cudaFree(h->d_term);
+  cudaFree(h->d_gval); cudaFree(h->d_gdiag); cudaFree(h->d_fields); cudaFree(h->d_b0);
+  cudaFree(h->d_gval32); cudaFree(h->d_gdiag32); cudaFree(h->d_fields32);
+  for (auto& b : h->blk) if (b.f64.dl) free_factors(b);
+  cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
+  cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp);
+  sgi_free_gmres_work(h);
+  delete h;
+}
+
+// 1D pencil of one grid direction on its unknowns: T (Theorems A.1/A.2),
+// end weights d (1/2 at an absorbing end) and absorbing-end indicator e.
+struct Pencil1D {
+  std::vector<double> tdiag, toff, d, e;
+};
+
+static Pencil1D pencil(int m, double h, int left_abs, int right_abs) {
+  Pencil1D p;
+  p.tdiag.assign(m, 2.0 / (h * h));
+  p.toff.assign(m > 1 ? m - 1 : 0, -1.0 / (h * h));
+  p.d.assign(m, 1.0);
+  p.e.assign(m, 0.0);
+  if (left_abs) { p.tdiag[0] = 1.0 / (h * h); p.d[0] = 0.5; p.e[0] = 1.0; }
+  if (right_abs) { p.tdiag[m - 1] = 1.0 / (h * h); p.d[m - 1] = 0.5; p.e[m - 1] = 1.0; }
+  return p;
+}
+
+static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
+  const int n = h->n;
+  int* d_bad = nullptr;
+  SG_CUDA_TRY(cudaMalloc((void**)&d_bad, sizeof(int)));
+  SG_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+  sg_status status = SG_OK;
+  if (h->dim == 1) {
+    // S_blk = T - i D_1(k_0) - (1 + i beta_c) D_2(k_0^2), one tridiagonal system.
+    Pencil1D px = pencil(h->mx, h->h, h->bc[0] == SG_BC_ABSORBING, h->bc[1] == SG_BC_ABSORBING);
+    std::vector<double> off(px.toff);
+    off.resize(std::max(n, 1), 0.0);
+    double* d_off = nullptr;
+    double2* d_diag = nullptr;
+    if (upload(&d_off, off.data(), off.size())) return fail(SG_ENOMEM, "precond upload");
+    for (int which = 0; which < 2; ++which) {
+      double bc_ = which == 0 ? 0.0 : h->beta;
+      std::vector<double2> diag(n);
+      for (int i = 0; i < n; ++i) {
+        double w1 = px.e[i] / h->h, w2 = px.d[i], k = h->k0u[i];
+        diag[i] = make_double2(px.tdiag[i] - w2 * k * k, -w1 * k - bc_ * w2 * k * k);
+      }
+      if (upload(&d_diag, diag.data(), diag.size())) return fail(SG_ENOMEM, "precond upload");
+      if (alloc_factors(h->blk[which], (size_t)n)) return fail(SG_ENOMEM, "factor alloc");
+      SG_CUDA_TRY(launch_tri_factor(1, n, d_diag, nullptr, d_off, h->blk[which].f64, h->blk[which].f32,
+                                    d_bad, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(d_diag);
+      d_diag = nullptr;
+      h->blk[which].ready = true;
+    }
+    cudaFree(d_off);
+  } else if (h->separable) {
+    const double kb = h->kbar, hh = h->h;
+    Pencil1D px = pencil(h->mx, hh, h->bc[0] == SG_BC_ABSORBING, h->bc[1] == SG_BC_ABSORBING);
+    Pencil1D py = pencil(h->my, hh, h->bc[2] == SG_BC_ABSORBING, h->bc[3] == SG_BC_ABSORBING);
+    // G = D^-1/2 (T - i (kbar/h) E - (kbar^2/2) D) D^-1/2, per direction.
+    auto gmat = [&](const Pencil1D& p, std::vector<cd>& gd, std::vector<cd>& go) {
+      int m = (int)p.d.size();
+      gd.resize(m);
+      go.resize(m > 1 ? m - 1 : 0);
+      for (int i = 0; i < m; ++i)
+        gd[i] = cd(p.tdiag[i] - 0.5 * kb * kb * p.d[i], -(kb / hh) * p.e[i]) / p.d[i];
+      for (int i = 0; i + 1 < m; ++i) go[i] = p.toff[i] / std::sqrt(p.d[i] * p.d[i + 1]);
+    };
+    std::vector<cd> gxd, gxo, gyd, gyo, lam, Q;
+    gmat(px, gxd, gxo);
+    gmat(py, gyd, gyo);
+    double oerr = 0;
+    if (!csym_tridiag_eig(h->mx, gxd, gxo, lam, Q, &oerr))
+      return fail(SG_ESINGULAR, "eigen-decomposition of the x pencil failed (orthogonality " +
+                                    std::to_string(oerr) + ")");
+    h->eig_orth_err = oerr;
+    const int mx = h->mx, my = h->my;
+    std::vector<double2> Qh((size_t)mx * mx), Qt((size_t)mx * mx);
+    std::vector<float2> Qh32((size_t)mx * mx), Qt32((size_t)mx * mx);
+    for (int i = 0; i < mx; ++i)
+      for (int k = 0; k < mx; ++k) {
+        cd v = Q[(size_t)i * mx + k] / std::sqrt(px.d[i]);
+        Qh[(size_t)i * mx + k] = make_double2(v.real(), v.imag());
+        Qt[(size_t)k * mx + i] = make_double2(v.real(), v.imag());
+        Qh32[(size_t)i * mx + k] = make_float2((float)v.real(), (float)v.imag());
+        Qt32[(size_t)k * mx + i] = make_float2((float)v.real(), (float)v.imag());
+      }
+    std::vector<double> dyinv(my);
+    std::vector<float> dyinv32(my);
+    for (int j = 0; j < my; ++j) { dyinv[j] = 1.0 / std::sqrt(py.d[j]); dyinv32[j] = (float)dyinv[j]; }
+    if (upload(&h->d_Q, Qh.data(), Qh.size()) || upload(&h->d_Qt, Qt.data(), Qt.size()) ||
+        upload(&h->d_Q32, Qh32.data(), Qh32.size()) || upload(&h->d_Qt32, Qt32.data(), Qt32.size()) ||
+        upload(&h->d_dyinv, dyinv.data(), dyinv.size()) || upload(&h->d_dyinv32, dyinv32.data(), dyinv32.size()))
+      return fail(SG_ENOMEM, "precond upload");
+    // y-direction systems: (lam_i + shift) I + G_y, shift 0 (mean) or -i beta kbar^2 (CSL).
+    std::vector<double2> gdiag(my), lsh(mx);
+    std::vector<double> goff(std::max(my, 1), 0.0);
+    for (int j = 0; j < my; ++j) gdiag[j] = make_double2(gyd[j].real(), gyd[j].imag());
+    for (int j = 0; j + 1 < my; ++j) goff[j] = gyo[j].real();
+    double2* d_gd = nullptr;
+    double2* d_ls = nullptr;
+    double* d_go = nullptr;
+    if (upload(&d_gd, gdiag.data(), gdiag.size()) || upload(&d_go, goff.data(), goff.size()))
+      return fail(SG_ENOMEM, "precond upload");
+    SG_CUDA_TRY(cudaMalloc((void**)&d_ls, sizeof(double2) * mx));
+    for (int which = 0; which < 2; ++which) {
+      cd shift = which == 0 ? cd(0, 0) : cd(0, -h->beta * kb * kb);
+      for (int i = 0; i < mx; ++i) {
+        cd v = lam[i] + shift;
+        lsh[i] = make_double2(v.real(), v.imag());
+      }
+      SG_CUDA_TRY(cudaMemcpy(d_ls, lsh.data(), sizeof(double2) * mx, cudaMemcpyHostToDevice));
+      if (alloc_factors(h->blk[which], (size_t)mx * my)) return fail(SG_ENOMEM, "factor alloc");
+      SG_CUDA_TRY(launch_tri_factor(mx, my, d_gd, d_ls, d_go, h->blk[which].f64, h->blk[which].f32, d_bad, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+      h->blk[which].ready = true;
+    }
+    cudaFree(d_gd); cudaFree(d_ls); cudaFree(d_go);
+    SG_CUDA_TRY(cudaMalloc(&h->d_tmp, (size_t)h->N * sizeof(double2)));
+  }
+  int bad = 0;
+  SG_CUDA_TRY(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaFree(d_bad);
+  if (bad) {
+    for (auto& b : h->blk) b.ready = false;
+    status = fail(SG_ESINGULAR, "zero pivot in a preconditioner factorisation");
+  }
+  return status;
+}
+
+extern "C" {
+
+const char* sg_last_error(void) { return sgi::g_err.c_str(); }
+int sg_version(void) { return 100; }
+long long sg_kernel_launches(void) { return sgi::g_launches.load(); }
+
+sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
+  g_err.clear();
+  if (!desc || !out) return fail(SG_EINVAL, "NULL desc or out");
+  const sg_desc& D = *desc;
+  if (D.dim != 1 && D.dim != 2) return fail(SG_EINVAL, "dim must be 1 or 2");
+  if (D.nx < 3 || (D.dim == 2 && D.ny < 3) || (D.dim == 1 && D.ny != 1))
+    return fail(SG_EINVAL, "grid too small (nx, ny >= 3; ny = 1 in 1D)");
+  if (!(D.h > 0) || !std::isfinite(D.h)) return fail(SG_EINVAL, "h must be positive");
+  if (D.s < 0 || D.s > 16 || D.r < 0 || D.r > 12) return fail(SG_EINVAL, "s in [0,16], r in [0,12]");
+  for (int i = 0; i < (D.dim == 2 ? 4 : 2); ++i)
+    if (D.bc[i] != SG_BC_DIRICHLET && D.bc[i] != SG_BC_ABSORBING) return fail(SG_EINVAL, "bad bc");
+  if (D.dim == 2 && !(D.bc[0] == D.bc[1] && D.bc[1] == D.bc[2] && D.bc[2] == D.bc[3]))
+    return fail(SG_EINVAL, "2D needs all-Dirichlet or all-absorbing boundaries (Theorems A.5/A.6)");
+  if (!D.k0 || (D.s > 0 && !D.kl)) return fail(SG_EINVAL, "NULL wavenumber field");
+  if (!std::isfinite(D.beta)) return fail(SG_EINVAL, "beta not finite");
+
+  auto* h = new sg_handle();
+  h->dim = D.dim; h->nx = D.nx; h->ny = D.dim == 2 ? D.ny : 1; h->h = D.h; h->beta = D.beta;
+  for (int i = 0; i < 4; ++i) h->bc[i] = (D.dim == 1 && i >= 2) ? SG_BC_DIRICHLET : D.bc[i];
+  h->s = D.s; h->r = D.r;
+  h->offx = h->bc[0] == SG_BC_DIRICHLET ? 1 : 0;
+  h->mx = D.nx - h->offx - (h->bc[1] == SG_BC_DIRICHLET ? 1 : 0);
+  if (D.dim == 2) {
+    h->offy = h->bc[2] == SG_BC_DIRICHLET ? 1 : 0;
+    h->my = D.ny - h->offy - (h->bc[3] == SG_BC_DIRICHLET ? 1 : 0);
+  }
+  h->n = h->mx * h->my;
+  h->P = D.s == 0 ? 1 : binom(D.s + D.r, D.s);
+  h->N = (long long)h->n * h->P;
+  h->T_terms = 2 * D.s + D.s * (D.s - 1) / 2;
+  if (h->P > 4096) { delete h; return fail(SG_EINVAL, "too many chaos modes"); }
+
+  // node fields restricted to the unknowns, validation k > 0 (Sec. 3.2)
+  const int n = h->n, s = h->s, P = h->P;
+  const size_t nodes = (size_t)D.nx * h->ny;
+  std::vector<double> fields((size_t)(s + 1) * n);
+  h->b0.assign(n, 0.0);
+  double kmin = 1e300, kmax = -1e300, k0min = 1e300, k0max = -1e300;
+  for (int ju = 0; ju < h->my; ++ju)
+    for (int iu = 0; iu < h->mx; ++iu) {
+      size_t node = (size_t)(iu + h->offx) + (size_t)D.nx * (ju + h->offy);
+      int u = iu + h->mx * ju;
+      double k0 = D.k0[node], spread = 0;
+      fields[u] = k0;
+      for (int l = 0; l < s; ++l) {
+        double kl = D.kl[(size_t)l * nodes + node];
+        fields[(size_t)(l + 1) * n + u] = kl;
+        spread += std::fabs(kl);
+        if (!std::isfinite(kl)) { delete h; return fail(SG_EINVAL, "non-finite k_l"); }
+      }
+      if (!std::isfinite(k0)) { delete h; return fail(SG_EINVAL, "non-finite k_0"); }
+      kmin = std::min(kmin, k0 - spread);
+      kmax = std::max(kmax, k0 + spread);
+      k0min = std::min(k0min, k0);
+      k0max = std::max(k0max, k0);
+      double f = D.f ? D.f[node] : 0.0;
+      if (!std::isfinite(f)) { delete h; return fail(SG_EINVAL, "non-finite f"); }
+      bool xabs = (iu == 0 && h->bc[0] == SG_BC_ABSORBING) || (iu == h->mx - 1 && h->bc[1] == SG_BC_ABSORBING);
+      bool yabs = D.dim == 2 && ((ju == 0 && h->bc[2] == SG_BC_ABSORBING) ||
+                                 (ju == h->my - 1 && h->bc[3] == SG_BC_ABSORBING));
+      h->b0[u] = (xabs ? 0.5 : 1.0) * (yabs ? 0.5 : 1.0) * f;
+    }
+  if (!(kmin > 0)) { delete h; return fail(SG_EINVAL, "k(x, xi) must be positive for all xi (k_0 - sum|k_l| <= 0)"); }
+  h->kbar = 0.5 * (k0min + k0max);
+  h->separable = (k0max - k0min) <= 1e-13 * k0max;
+  h->k0u.assign(fields.begin(), fields.begin() + n);
+
+  // chaos tables
+  h->alpha = multi_indices(s, h->r);
+  if (s == 0) h->alpha.clear();
+  h->rowptr.assign(P + 1, 0);
+  for (int a = 0; a < P; ++a) {
+    for (int b = 0; b < P; ++b) {
+      if (a == b) continue;
+      int t;
+      double g;
+      if (coupling(s, &h->alpha[(size_t)a * s], &h->alpha[(size_t)b * s], &t, &g)) {
+        h->col.push_back(b);
+        h->term.push_back(t);
+        h->gval.push_back(g);
+      }
+    }
+    h->rowptr[a + 1] = (int)h->col.size();
+  }
+  h->gdiag.assign((size_t)std::max(s, 1) * P, 0.0);
+  for (int l = 0; l < s; ++l)
+    for (int a = 0; a < P; ++a) {
+      int al = h->alpha[(size_t)a * s + l];
+      h->gdiag[(size_t)l * P + a] = leg_b(al) * leg_b(al) + leg_b(al + 1) * leg_b(al + 1);
+    }
+
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) { delete h; return fail(SG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)); }
+
+  std::vector<float> gval32(h->gval.begin(), h->gval.end()), gdiag32(h->gdiag.begin(), h->gdiag.end()),
+      fields32(fields.begin(), fields.end());
+  if (upload(&h->d_rowptr, h->rowptr.data(), h->rowptr.size()) ||
+      upload(&h->d_col, h->col.data(), h->col.size()) || upload(&h->d_term, h->term.data(), h->term.size()) ||
+      upload(&h->d_gval, h->gval.data(), h->gval.size()) || upload(&h->d_gdiag, h->gdiag.data(), h->gdiag.size()) ||
+      upload(&h->d_fields, fields.data(), fields.size()) || upload(&h->d_b0, h->b0.data(), h->b0.size()) ||
+      upload(&h->d_gval32, gval32.data(), gval32.size()) ||
+      upload(&h->d_gdiag32, gdiag32.data(), gdiag32.size()) ||
+      upload(&h->d_fields32, fields32.data(), fields32.size())) {
+    destroy_impl(h);
+    return fail(SG_ENOMEM, "device allocation for fields/tables failed");
+  }
+  sg_status ps = setup_preconditioners(h, st);
+  if (ps != SG_OK && ps != SG_ESINGULAR) {
+    destroy_impl(h);
+    return ps;
+  }
+  if (ps == SG_ESINGULAR) {
+    destroy_impl(h);
+    return ps;
+  }
+  *out = h;
+  return SG_OK;
+}
+
+void sg_destroy(sg_handle* h) { destroy_impl(h); }
+
+sg_status sg_get_info(const sg_handle* h, sg_info* info) {
+  if (!h || !info) return fail(SG_EINVAL, "NULL handle or info");
+  info->dim = h->dim; info->mx = h->mx; info->my = h->my; info->n = h->n; info->P = h->P;
+  info->N = h->N; info->s = h->s; info->r = h->r; info->terms = h->T_terms;
+  info->coupling_nnz = (int)h->col.size() + h->P;
+  info->separable = h->separable ? 1 : 0;
+  info->specialised = h->specialised;
+  return SG_OK;
+}
+
+sg_status sg_rhs(sg_handle* h, sg_precision prec, void* b, void* stream) {
+  if (!h || !b) return fail(SG_EINVAL, "NULL handle or b");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == SG_FP64) SG_CUDA_TRY(launch_rhs<double>(h, (double2*)b, st));
+  else if (prec == SG_FP32) SG_CUDA_TRY(launch_rhs<float>(h, (float2*)b, st));
+  else return fail(SG_EINVAL, "sg_rhs precision must be SG_FP64 or SG_FP32");
+  return SG_OK;
+}
+
+sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, void* stream) {
+  if (!h || !X || !Y) return fail(SG_EINVAL, "NULL handle or vector");
+  if (X == Y) return fail(SG_EINVAL, "sg_matvec: X and Y must not overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == SG_FP64) SG_CUDA_TRY(launch_matvec<double>(h, (const double2*)X, (double2*)Y, st));
+  else if (prec == SG_FP32) SG_CUDA_TRY(launch_matvec<float>(h, (const float2*)X, (float2*)Y, st));
+  else return fail(SG_EINVAL, "sg_matvec precision must be SG_FP64 or SG_FP32");
+  return SG_OK;
+}
+
+sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z, void* stream) {
+  if (!h || !R || !Z) return fail(SG_EINVAL, "NULL handle or vector");
+  if (prec != SG_FP64 && prec != SG_FP32) return fail(SG_EINVAL, "sg_precond precision must be SG_FP64 or SG_FP32");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = (size_t)h->N * (prec == SG_FP64 ? sizeof(double2) : sizeof(float2));
+  if (kind == SG_PREC_NONE) {
+    if (R != Z) SG_CUDA_TRY(cudaMemcpyAsync(Z, R, bytes, cudaMemcpyDeviceToDevice, st));
+    return SG_OK;
+  }
+  if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN) return fail(SG_EINVAL, "unknown preconditioner");
+  int which = kind == SG_PREC_MEAN ? 0 : 1;
+  if (!h->blk[which].ready)
+    return fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
+  if (prec == SG_FP64) SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));
+  else SG_CUDA_TRY(launch_precond<float>(h, which, (const float2*)R, (float2*)Z, st));
+  return SG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations of the GB300 SG Helmholtz library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/sg.h"
+
+namespace sgi {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+sg_status fail(sg_status st, const std::string& msg);
+#define SG_CUDA_TRY(expr)                                                       \
+  do {                                                                          \
+    cudaError_t e_ = (expr);                                                    \
+    if (e_ != cudaSuccess)                                                      \
+      return ::sgi::fail(SG_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------- device complex helpers
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> using C2 = typename Vec2<T>::type;
+
+// ---------------------------------------------------------------- operator description
+// Parameters every operator kernel needs: unknown-grid geometry and the
+// chaos coupling tables (device pointers).
+template <typename T>
+struct OpParams {
+  int dim, mx, my, n, P, s, T_terms;
+  int absL, absR, absB, absT;      // 1 if that side is absorbing
+  T h, inv_h, inv_h2;
+  const int* rowptr;               // P+1, off-diagonal coupling rows
+  const int* col;                  // nnz_off
+  const int* term;                 // nnz_off, term id in [0, T_terms)
+  const T* gval;                   // nnz_off, Galerkin product value
+  const T* gdiag;                  // s*P, <xi_l^2 phi_a phi_a>, layout [l][a]
+  const T* fields;                 // (s+1)*n: k_0, k_1..k_s on the unknowns
+  const int* skip;                 // optional device flag: kernel returns at once if *skip != 0
+};
+
+// Tridiagonal LU factors with partial pivoting (LAPACK gttrf layout) for
+// `nsys` systems of length `len`; element (j, sys) at j*nsys + sys.
+template <typename T>
+struct TriFactors {
+  C2<T>* dl = nullptr;    // multipliers
+  C2<T>* dinv = nullptr;  // 1 / U diagonal
+  C2<T>* du = nullptr;    // U first superdiagonal
+  C2<T>* du2 = nullptr;   // U second superdiagonal (fill from pivoting)
+  uint8_t* piv = nullptr; // 1 if rows j, j+1 were swapped
+};
+
+struct PrecBlock {
+  bool ready = false;
+  TriFactors<double> f64;
+  TriFactors<float> f32;
+};
+
+struct GmresWork {
+  int restart = 0;         // basis capacity (columns restart+1)
+  int prec_bytes = 0;      // 8 (c64) or 16 (c128) per element of V
+  void* V = nullptr;       // (restart+1) * N inner precision
+  void* Z = nullptr;       // N inner precision
+  void* R64 = nullptr;     // N complex128 (mixed: outer residual; fp64: A x)
+  void* X64 = nullptr;     // N complex128 staging for host_io / x0
+  void* B64 = nullptr;     // N complex128 staging for host_io
+  double* dscal = nullptr; // device scalars (see solver.cu)
+  int* dctl = nullptr;     // device control words
+  double* part = nullptr;  // partial sums [nblk][2*(restart+2)]
+  unsigned* counter = nullptr;
+  int nblk = 0;
+};
+
+}  // namespace sgi
+
+struct sg_handle {
+  int dim = 1, nx = 0, ny = 1, mx = 0, my = 1, offx = 0, offy = 0, n = 0, P = 0, s = 0, r = 0;
+  int T_terms = 0;
+  long long N = 0;
+  double h = 0, beta = 0.5, kbar = 0;
+  int bc[4] = {0, 0, 0, 0};
+  bool separable = false;
+  int specialised = 0;
+  int num_sms = 0;
+  int device = 0;
+
+  // host tables
+  std::vector<int> alpha;            // P*s multi-indices
+  std::vector<int> rowptr, col, term;
+  std::vector<double> gval, gdiag;   // off-diagonal values, diagonal moments [l][a]
+  std::vector<double> b0;            // n, FD-weighted source on the unknowns
+  std::vector<double> k0u;           // n, k_0 on the unknowns
+
+  // device tables
+  int *d_rowptr = nullptr, *d_col = nullptr, *d_term = nullptr;
+  double *d_gval = nullptr, *d_gdiag = nullptr, *d_fields = nullptr, *d_b0 = nullptr;
+  float *d_gval32 = nullptr, *d_gdiag32 = nullptr, *d_fields32 = nullptr;
+
+  // preconditioner data
+  sgi::PrecBlock blk[2];             // [0] mean value S(xi_bar), [1] CSL M_0 block
+  double2* d_Q = nullptr;            // 2D: Qhat = D_x^-1/2 Q, row-major mx x mx
+  double2* d_Qt = nullptr;           // 2D: Qhat^T
+  float2* d_Q32 = nullptr;
+  float2* d_Qt32 = nullptr;
+  double* d_dyinv = nullptr;         // 2D: d_y^-1/2 per y line
+  float* d_dyinv32 = nullptr;
+  void* d_tmp = nullptr;             // N complex128 scratch (2D precond intermediate)
+  double eig_orth_err = 0.0;         // max |Q^T Q - I| of the host eigenvectors
+
+  sgi::GmresWork gw;
+
+  sgi::OpParams<double> op64() const;
+  sgi::OpParams<float> op32() const;
+};
+
+namespace sgi {
+// kernels / launchers (defined in the .cu files)
+template <typename T>
+cudaError_t launch_matvec(const sg_handle* h, const C2<T>* X, C2<T>* Y, cudaStream_t st,
+                          const int* skip = nullptr);
+template <typename T>
+cudaError_t launch_rhs(const sg_handle* h, C2<T>* b, cudaStream_t st);
+
+cudaError_t launch_tri_factor(int nsys, int len, const double2* diag, const double2* lam_shift,
+                              const double* off, TriFactors<double> f64, TriFactors<float> f32,
+                              int* d_bad, cudaStream_t st);
+template <typename T>
+cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
+                           const int* skip = nullptr, const double* in_scale = nullptr);
+
+// launch bookkeeping (sg_kernel_launches)
+void note_launch();
+
+// host helpers
+bool csym_tridiag_eig(int n, const std::vector<cd>& diag, const std::vector<cd>& off,
+                      std::vector<cd>& lam, std::vector<cd>& Q, double* orth_err);
+}  // namespace sgi

@@ -1,0 +1,707 @@
+// Restarted, right-preconditioned GMRES for the SG system (Sec. 6.3: GMRES
+// with A M^-1 y = b, x = M^-1 y and relres = ||b - A x|| / ||b||), kept on
+// the device:
+//
+//  * Arnoldi step j:  z = M^-1 v_j,  w = A z,  classical Gram-Schmidt applied
+//    twice (d1 = V^H w; w -= V c1; d2 = V^H w; w -= V c2), ||w||.
+//  * Lazy normalisation: the basis is stored raw, v_i = vscale_i * V_i; the
+//    factor is applied where a vector is read (inside the preconditioner's
+//    tridiagonal solve, in the CGS coefficients, in the final combination),
+//    so no separate scaling pass is needed.
+//  * Complex Givens rotations, the Hessenberg matrix, the residual estimate
+//    |g_{j+1}| and the least-squares solve stay in FP64 on the device; one
+//    thread updates them.
+//  * Every step kernel returns at once when the device flag `done` is set, so
+//    the host reads that flag only every `check_every` steps.
+//  * SG_MIXED: FP64 iterative refinement around a complex64 GMRES cycle:
+//    r = b - A x (FP64 matvec), inner solve A d = r in complex64, x += d.
+//
+// Reductions: per thread in the vector precision, across warps and blocks in
+// FP64, blocks combined by the last block to finish (fixed order, so results
+// are bitwise reproducible).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "sg_internal.h"
+
+namespace sgi {
+
+constexpr int RED_THREADS = 256;
+constexpr int MAXV = 512;   // maximum basis vectors handled by the coefficient kernels (restart + 1)
+
+// ------------------------------------------------------------------ device scalar layout
+struct DevLayout {
+  int m;                    // restart capacity
+  size_t H, cs, sn, g, vscale, d1, c1, d2, c2, yc, sc;   // offsets in doubles
+  size_t total;
+  // Every array starts on a 16-byte boundary (an even double offset) because
+  // the complex ones are accessed as double2.
+  explicit DevLayout(int m_ = 0) : m(m_) {
+    size_t o = 0;
+    auto take = [&o](size_t count) {
+      const size_t at = o;
+      o += (count + 1) & ~(size_t)1;
+      return at;
+    };
+    H = take(2 * (size_t)(m + 1) * m);
+    cs = take(m);
+    sn = take(2 * (size_t)m);
+    g = take(2 * (size_t)(m + 1));
+    vscale = take(m + 1);
+    d1 = take(2 * (size_t)(m + 1));
+    c1 = take(2 * (size_t)(m + 1));
+    d2 = take(2 * (size_t)(m + 1));
+    c2 = take(2 * (size_t)(m + 1));
+    yc = take(2 * (size_t)(m + 1));
+    sc = take(16);
+    total = o;
+  }
+};
+// sc[] slots
+enum { SC_NORMSQ = 0, SC_BNORM = 1, SC_RNORM2 = 2, SC_EST = 3, SC_TOL = 4, SC_REF = 5, SC_WORK = 6 };
+// ctl[] slots
+enum { CTL_DONE = 0, CTL_ITERS = 1, CTL_K = 2, CTL_FLAGS = 3, CTL_MAXIT = 4 };
+enum { FL_CONV = 1, FL_BREAK = 2, FL_NAN = 4, FL_MAXIT = 8 };
+
+template <typename T>
+__device__ __forceinline__ C2<T> mkc(T a, T b) {
+  C2<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+
+// ------------------------------------------------------------------ block reduction
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV * 32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[k * 32 + warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nw ? sm[k * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;  // valid in thread 0
+    }
+  }
+  __syncthreads();
+}
+
+// Called by every thread after it stored its block partials; returns true in
+// the last block (all partials visible).  The counter is reset by that block.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last;
+}
+
+// ------------------------------------------------------------------ kernels
+// d_i = V_i^H w for i < nv (raw vectors); last block writes d and
+// c_i = vscale_i^2 d_i (the update coefficient for the raw basis).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const C2<T>* __restrict__ V, long long N, int nv,
+                                                     const C2<T>* __restrict__ w, double* part, int pstride,
+                                                     unsigned* counter, const double* vscale, double* d_out,
+                                                     double* c_out, const int* ctl) {
+  if (ctl[CTL_DONE]) return;
+  __shared__ double sm[8 * 32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int g0 = 0; g0 < nv; g0 += 4) {
+    T acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = T(0);
+    const int ng = min(4, nv - g0);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+      const C2<T> we = w[e];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (q < ng) {
+          const C2<T> v = V[(size_t)(g0 + q) * N + e];
+          acc[2 * q] += v.x * we.x + v.y * we.y;
+          acc[2 * q + 1] += v.x * we.y - v.y * we.x;
+        }
+      }
+    }
+    double dv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dv[k] = (double)acc[k];
+    block_sum<8>(dv, sm);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 2 * ng; ++k) part[(size_t)blockIdx.x * pstride + 2 * g0 + k] = dv[k];
+  }
+  if (last_block(counter)) {
+    for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) {
+      double s = 0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * pstride + k);
+      d_out[k] = s;
+      const double vs = vscale[k >> 1];
+      c_out[k] = vs * vs * s;
+    }
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+// w -= sum_i c_i V_i ; optionally ||w||^2 (last block writes *norm_out).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_update(const C2<T>* __restrict__ V, long long N, int nv,
+                                                       C2<T>* __restrict__ w, const double* __restrict__ c,
+                                                       double* part, int pstride, unsigned* counter,
+                                                       double* norm_out, const int* ctl) {
+  if (ctl[CTL_DONE]) return;
+  __shared__ C2<T> cs[MAXV];
+  __shared__ double sm[32];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = mkc<T>((T)c[2 * i], (T)c[2 * i + 1]);
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  T nacc = T(0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    C2<T> we = w[e];
+    for (int i = 0; i < nv; ++i) {
+      const C2<T> v = V[(size_t)i * N + e];
+      const C2<T> ci = cs[i];
+      we.x -= ci.x * v.x - ci.y * v.y;
+      we.y -= ci.x * v.y + ci.y * v.x;
+    }
+    w[e] = we;
+    nacc += we.x * we.x + we.y * we.y;
+  }
+  if (norm_out) {
+    double dv[1] = {(double)nacc};
+    block_sum<1>(dv, sm);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * pstride] = dv[0];
+    if (last_block(counter)) {
+      if (threadIdx.x == 0) {
+        double s = 0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * pstride);
+        *norm_out = s;
+        *counter = 0;
+      }
+    }
+  }
+}
+
+// r = b - Ax (or r = b when Ax == nullptr) written in the inner precision;
+// ||r||^2 accumulated in the outer precision, last block writes *norm_out.
+template <typename TO, typename TI>
+__global__ void __launch_bounds__(RED_THREADS) k_residual(const C2<TO>* __restrict__ b, const C2<TO>* __restrict__ Ax,
+                                                         C2<TI>* __restrict__ r, long long N, double* part,
+                                                         int pstride, unsigned* counter, double* norm_out) {
+  __shared__ double sm[32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  TO nacc = TO(0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    C2<TO> v = b[e];
+    if (Ax) {
+      const C2<TO> a = Ax[e];
+      v.x -= a.x;
+      v.y -= a.y;
+    }
+    if (r) r[e] = mkc<TI>((TI)v.x, (TI)v.y);
+    nacc += v.x * v.x + v.y * v.y;
+  }
+  double dv[1] = {(double)nacc};
+  block_sum<1>(dv, sm);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.x * pstride] = dv[0];
+  if (last_block(counter)) {
+    if (threadIdx.x == 0) {
+      double s = 0;
+      for (int b2 = 0; b2 < (int)gridDim.x; ++b2) s += __ldcg(part + (size_t)b2 * pstride);
+      *norm_out = s;
+      *counter = 0;
+    }
+  }
+}
+
+// Start of a cycle: vscale_0 = 1/||r||, g = (||r||, 0, ...), k = 0.
+// Sets done if ||r|| / ref <= tol already (or r is zero / not finite).
+__global__ void k_cycle_init(double* D, int* ctl, DevLayout L, double tol_est, double ref) {
+  const double rn = sqrt(D[L.sc + SC_RNORM2]);
+  for (int i = 0; i < 2 * (L.m + 1); ++i) D[L.g + i] = 0.0;
+  D[L.g] = rn;
+  D[L.vscale] = rn > 0 ? 1.0 / rn : 0.0;
+  D[L.sc + SC_TOL] = tol_est;
+  D[L.sc + SC_REF] = ref;
+  D[L.sc + SC_EST] = rn / ref;
+  ctl[CTL_K] = 0;
+  ctl[CTL_DONE] = 0;
+  ctl[CTL_FLAGS] = 0;
+  if (!(rn == rn) || rn > 1e300) {
+    ctl[CTL_DONE] = 1;
+    ctl[CTL_FLAGS] |= FL_NAN;
+  } else if (rn / ref <= tol_est || rn == 0.0) {
+    ctl[CTL_DONE] = 1;
+    ctl[CTL_FLAGS] |= FL_CONV;
+  }
+}
+
+// Givens update for column j (one thread).  w = A M^-1 v_j was formed from
+// the normalised v_j, so H[i][j] = v_i^H w = vscale_i (d1_i + d2_i) and
+// H[j+1][j] = ||w||.
+__global__ void k_givens(double* D, int* ctl, DevLayout L, int j) {
+  if (ctl[CTL_DONE]) return;
+  const int m = L.m;
+  double2* H = reinterpret_cast<double2*>(D + L.H);     // column-major, ld m+1
+  double* cs = D + L.cs;
+  double2* sn = reinterpret_cast<double2*>(D + L.sn);
+  double2* g = reinterpret_cast<double2*>(D + L.g);
+  double* vs = D + L.vscale;
+  const double2* d1 = reinterpret_cast<const double2*>(D + L.d1);
+  const double2* d2 = reinterpret_cast<const double2*>(D + L.d2);
+  const double om = 1.0;
+  double2* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) {
+    const double f = om * vs[i];
+    col[i] = make_double2(f * (d1[i].x + d2[i].x), f * (d1[i].y + d2[i].y));
+  }
+  const double wn = sqrt(D[L.sc + SC_NORMSQ]);
+  const double hn = om * wn;
+  col[j + 1] = make_double2(hn, 0.0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = col[i], b = col[i + 1];
+    const double c = cs[i];
+    const double2 s = sn[i];
+    // t = c a + s b ; b' = -conj(s) a + c b
+    const double2 t = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    const double2 bb = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    col[i] = t;
+    col[i + 1] = bb;
+  }
+  // new rotation zeroing col[j+1]
+  const double2 a = col[j], b = col[j + 1];
+  const double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
+  double c;
+  double2 s;
+  if (ab == 0.0) {
+    c = 1.0;
+    s = make_double2(0, 0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(b.x / ab, -b.y / ab);
+  } else {
+    const double rr = hypot(aa, ab);
+    c = aa / rr;
+    // s = (a/|a|) conj(b) / rr
+    const double2 u = make_double2(a.x / aa, a.y / aa);
+    s = make_double2((u.x * b.x + u.y * b.y) / rr, (u.y * b.x - u.x * b.y) / rr);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+  col[j + 1] = make_double2(0, 0);
+  const double2 gj = g[j];
+  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  const double est = hypot(g[j + 1].x, g[j + 1].y) / D[L.sc + SC_REF];
+  D[L.sc + SC_EST] = est;
+  vs[j + 1] = wn > 0 ? 1.0 / wn : 0.0;
+  ctl[CTL_ITERS] += 1;
+  ctl[CTL_K] = j + 1;
+  const bool bad = !(est == est) || !(hn == hn) || !(col[j].x == col[j].x);
+  if (bad) {
+    ctl[CTL_FLAGS] |= FL_NAN;
+    ctl[CTL_DONE] = 1;
+  } else if (est <= D[L.sc + SC_TOL]) {
+    ctl[CTL_FLAGS] |= FL_CONV;
+    ctl[CTL_DONE] = 1;
+  } else if (hn <= 1e-300 * (aa + ab + 1e-300) || wn == 0.0) {
+    ctl[CTL_FLAGS] |= FL_BREAK;   // (lucky) breakdown: Krylov space invariant
+    ctl[CTL_DONE] = 1;
+  } else if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT] || j + 1 >= m) {
+    if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT]) ctl[CTL_FLAGS] |= FL_MAXIT;
+    ctl[CTL_DONE] = 1;
+  }
+}
+
+// y = R^-1 g (k x k upper triangle of the rotated Hessenberg matrix);
+// yc_i = y_i * vscale_i for the raw-basis linear combination.
+__global__ void k_lsq(double* D, const int* ctl, DevLayout L) {
+  const int k = ctl[CTL_K];
+  const int m = L.m;
+  const double2* H = reinterpret_cast<const double2*>(D + L.H);
+  const double2* g = reinterpret_cast<const double2*>(D + L.g);
+  double2* yc = reinterpret_cast<double2*>(D + L.yc);
+  const double* vs = D + L.vscale;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i];
+    for (int l = i + 1; l < k; ++l) {
+      const double2 h = H[(size_t)l * (m + 1) + i];
+      const double2 y = yc[l];   // still unscaled y_l here
+      s.x -= h.x * y.x - h.y * y.y;
+      s.y -= h.x * y.y + h.y * y.x;
+    }
+    const double2 d = H[(size_t)i * (m + 1) + i];
+    const double den = d.x * d.x + d.y * d.y;
+    yc[i] = den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
+                    : make_double2(0, 0);
+  }
+  for (int i = 0; i < k; ++i) yc[i] = make_double2(yc[i].x * vs[i], yc[i].y * vs[i]);
+  for (int i = k; i <= m; ++i) yc[i] = make_double2(0, 0);
+}
+
+// u = sum_{i<k} yc_i V_i  (k read on the device).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_lincomb(const C2<T>* __restrict__ V, long long N,
+                                                        const double* __restrict__ yc, const int* ctl,
+                                                        C2<T>* __restrict__ u) {
+  __shared__ C2<T> cs[MAXV];
+  const int k = ctl[CTL_K];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = mkc<T>((T)yc[2 * i], (T)yc[2 * i + 1]);
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    C2<T> acc = mkc<T>(T(0), T(0));
+    for (int i = 0; i < k; ++i) {
+      const C2<T> v = V[(size_t)i * N + e];
+      const C2<T> c = cs[i];
+      acc.x += c.x * v.x - c.y * v.y;
+      acc.y += c.x * v.y + c.y * v.x;
+    }
+    u[e] = acc;
+  }
+}
+
+// x += z (z may be lower precision); skipped if k == 0.
+template <typename TX, typename TZ>
+__global__ void k_axpy(C2<TX>* __restrict__ x, const C2<TZ>* __restrict__ z, long long N, const int* ctl) {
+  if (ctl && ctl[CTL_K] == 0) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    const C2<TZ> v = z[e];
+    C2<TX> a = x[e];
+    a.x += (TX)v.x;
+    a.y += (TX)v.y;
+    x[e] = a;
+  }
+}
+
+// z = s * v, s read on the device.
+template <typename T>
+__global__ void k_scale_copy(const C2<T>* __restrict__ v, C2<T>* __restrict__ z, long long N,
+                             const double* __restrict__ s, const int* skip) {
+  if (skip && *skip) return;
+  const T f = (T)*s;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride)
+    z[e] = mkc<T>(v[e].x * f, v[e].y * f);
+}
+
+template <typename TA, typename TB>
+__global__ void k_convert(const C2<TA>* __restrict__ a, C2<TB>* __restrict__ b, long long N) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride)
+    b[e] = mkc<TB>((TB)a[e].x, (TB)a[e].y);
+}
+
+}  // namespace sgi
+
+using namespace sgi;
+
+void sgi_free_gmres_work(sg_handle* h) {
+  GmresWork& w = h->gw;
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
+  cudaFree(w.dscal); cudaFree(w.dctl); cudaFree(w.part); cudaFree(w.counter);
+  w = GmresWork{};
+}
+
+static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
+  GmresWork& w = h->gw;
+  if (w.V && w.restart >= m && w.prec_bytes == elem_bytes) return SG_OK;
+  sgi_free_gmres_work(h);
+  const size_t N = (size_t)h->N;
+  DevLayout L(m);
+  w.nblk = std::max(1, std::min(h->num_sms * 4, (int)((N + RED_THREADS - 1) / RED_THREADS)));
+  cudaError_t e = cudaSuccess;
+  if (!e) e = cudaMalloc(&w.V, (size_t)(m + 1) * N * elem_bytes);
+  if (!e) e = cudaMalloc(&w.Z, N * elem_bytes);
+  if (!e) e = cudaMalloc(&w.R64, N * sizeof(double2));
+  if (!e) e = cudaMalloc(&w.X64, N * sizeof(double2));
+  if (!e) e = cudaMalloc(&w.B64, N * sizeof(double2));
+  if (!e) e = cudaMalloc((void**)&w.dscal, L.total * sizeof(double));
+  if (!e) e = cudaMalloc((void**)&w.dctl, 16 * sizeof(int));
+  if (!e) e = cudaMalloc((void**)&w.part, (size_t)w.nblk * 2 * (MAXV + 2) * sizeof(double));
+  if (!e) e = cudaMalloc((void**)&w.counter, sizeof(unsigned));
+  if (!e) e = cudaMemset(w.counter, 0, sizeof(unsigned));
+  if (e) {
+    sgi_free_gmres_work(h);
+    return fail(SG_ENOMEM, std::string("GMRES workspace: ") + cudaGetErrorString(e));
+  }
+  w.restart = m;
+  w.prec_bytes = elem_bytes;
+  return SG_OK;
+}
+
+namespace {
+
+struct Ctx {
+  sg_handle* h;
+  cudaStream_t st;
+  DevLayout L;
+  int grid;
+  int pstride;
+};
+
+// Z = M^-1 (s R) with s = *in_scale (1 if null).
+template <typename T>
+cudaError_t precond_apply(Ctx& c, sg_prec prec, const C2<T>* R, C2<T>* Z, const int* skip,
+                          const double* in_scale = nullptr) {
+  if (prec == SG_PREC_NONE) {
+    if (in_scale) {
+      k_scale_copy<T><<<c.grid, RED_THREADS, 0, c.st>>>(R, Z, c.h->N, in_scale, skip);
+      note_launch();
+      return cudaGetLastError();
+    }
+    if (R != Z) return cudaMemcpyAsync(Z, R, (size_t)c.h->N * sizeof(C2<T>), cudaMemcpyDeviceToDevice, c.st);
+    return cudaSuccess;
+  }
+  return launch_precond<T>(c.h, prec == SG_PREC_MEAN ? 0 : 1, R, Z, c.st, skip, in_scale);
+}
+
+// One Arnoldi step j with CGS2 on the inner-precision basis.
+template <typename T>
+cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
+  GmresWork& w = c.h->gw;
+  const long long N = c.h->N;
+  C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
+  C2<T>* Z = reinterpret_cast<C2<T>*>(w.Z);
+  C2<T>* vj = V + (size_t)j * N;
+  C2<T>* wv = V + (size_t)(j + 1) * N;
+  double* D = w.dscal;
+  cudaError_t e;
+  // z = M^-1 v_j with v_j = vscale_j V_j (normalised on the fly, so the raw
+  // basis norms stay of the size of h_{j+1,j})
+  if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
+  if ((e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
+  const int nv = j + 1;
+  k_dots<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, c.pstride, w.counter, D + c.L.vscale,
+                                              D + c.L.d1, D + c.L.c1, w.dctl); note_launch();
+  k_update<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, c.pstride, w.counter, nullptr,
+                                                w.dctl); note_launch();
+  k_dots<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, c.pstride, w.counter, D + c.L.vscale,
+                                              D + c.L.d2, D + c.L.c2, w.dctl); note_launch();
+  k_update<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c2, w.part, c.pstride, w.counter,
+                                                D + c.L.sc + SC_NORMSQ, w.dctl); note_launch();
+  k_givens<<<1, 1, 0, c.st>>>(D, w.dctl, c.L, j); note_launch();
+  return cudaGetLastError();
+}
+
+// Runs one restart cycle whose starting residual is already in V[0] with its
+// squared norm in sc[RNORM2].  Leaves the correction u = M^-1 (V y) in Z.
+template <typename T>
+sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int check_every, bool* any_step) {
+  GmresWork& w = c.h->gw;
+  k_cycle_init<<<1, 1, 0, c.st>>>(w.dscal, w.dctl, c.L, tol_est, ref); note_launch();
+  int done = 0;
+  SG_CUDA_TRY(cudaMemcpyAsync(&done, w.dctl + CTL_DONE, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  SG_CUDA_TRY(cudaStreamSynchronize(c.st));
+  *any_step = false;
+  if (done) return SG_OK;
+  for (int j = 0; j < m; ++j) {
+    SG_CUDA_TRY(arnoldi_step<T>(c, prec, j));
+    if ((j + 1) % check_every == 0 || j == m - 1) {
+      SG_CUDA_TRY(cudaMemcpyAsync(&done, w.dctl + CTL_DONE, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+      SG_CUDA_TRY(cudaStreamSynchronize(c.st));
+      if (done) break;
+    }
+  }
+  *any_step = true;
+  C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
+  C2<T>* Z = reinterpret_cast<C2<T>*>(w.Z);
+  k_lsq<<<1, 1, 0, c.st>>>(w.dscal, w.dctl, c.L); note_launch();
+  k_lincomb<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
+  SG_CUDA_TRY(cudaGetLastError());
+  SG_CUDA_TRY(precond_apply<T>(c, prec, Z, Z, nullptr));
+  return SG_OK;
+}
+
+template <typename TX>
+sg_status residual_norm(Ctx& c, const C2<TX>* b, const C2<TX>* x, bool x_zero, C2<TX>* Ax, void* rout_inner,
+                        bool inner_f32, double* rnorm2_host) {
+  GmresWork& w = c.h->gw;
+  const C2<TX>* axp = nullptr;
+  if (!x_zero) {
+    SG_CUDA_TRY(launch_matvec<TX>(c.h, x, Ax, c.st));
+    axp = Ax;
+  }
+  double* out = w.dscal + c.L.sc + SC_RNORM2;
+  if (inner_f32)
+    k_residual<TX, float><<<c.grid, RED_THREADS, 0, c.st>>>(b, axp, (float2*)rout_inner, c.h->N, w.part, c.pstride,
+                                                           w.counter, out);
+  else
+    k_residual<TX, double><<<c.grid, RED_THREADS, 0, c.st>>>(b, axp, (double2*)rout_inner, c.h->N, w.part,
+                                                            c.pstride, w.counter, out);
+  note_launch();
+  SG_CUDA_TRY(cudaGetLastError());
+  SG_CUDA_TRY(cudaMemcpyAsync(rnorm2_host, out, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  SG_CUDA_TRY(cudaStreamSynchronize(c.st));
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void* x,
+                              sg_gmres_info* info, void* stream) {
+  if (!h || !opts || !b || !x) return fail(SG_EINVAL, "NULL argument to sg_gmres");
+  if (opts->mode != SG_FP64 && opts->mode != SG_FP32 && opts->mode != SG_MIXED)
+    return fail(SG_EINVAL, "bad mode");
+  if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN)
+    return fail(SG_EINVAL, "bad preconditioner");
+  if (!(opts->tol > 0) || !std::isfinite(opts->tol)) return fail(SG_EINVAL, "tol must be positive");
+  if (opts->prec != SG_PREC_NONE && !h->blk[opts->prec == SG_PREC_MEAN ? 0 : 1].ready)
+    return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (2D needs a constant k_0)");
+  const long long N = h->N;
+  int m = opts->restart <= 0 ? (int)std::min<long long>(N, MAXV - 1) : opts->restart;
+  if (m > MAXV - 1) return fail(SG_EINVAL, "restart must be <= 511");
+  m = (int)std::min<long long>(m, N);
+  const int maxit = opts->maxit <= 0 ? (int)std::min<long long>(N, 1 << 30) : opts->maxit;
+  const int check_every = opts->check_every <= 0 ? 8 : opts->check_every;
+  const bool mixed = opts->mode == SG_MIXED;
+  const bool f32 = opts->mode == SG_FP32;
+  const bool inner32 = mixed || f32;
+  sg_status st0 = ensure_work(h, m, inner32 ? 8 : 16);
+  if (st0 != SG_OK) return st0;
+  GmresWork& w = h->gw;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2)};
+  c.L = DevLayout(w.restart);
+  // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
+  const size_t obytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
+
+  // outer vectors (x, b) in the outer precision
+  void* xd = x;
+  const void* bd = b;
+  if (opts->host_io) {
+    SG_CUDA_TRY(cudaMemcpyAsync(w.B64, b, obytes, cudaMemcpyHostToDevice, st));
+    bd = w.B64;
+    xd = w.X64;
+  }
+  bool x_zero = opts->x0 == nullptr;
+  if (opts->x0 && opts->x0 != xd) {
+    SG_CUDA_TRY(cudaMemcpyAsync(xd, opts->x0, obytes, opts->host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  } else if (!opts->x0) {
+    SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
+  }
+  int ctl0[16] = {0};
+  ctl0[CTL_MAXIT] = maxit;
+  SG_CUDA_TRY(cudaMemcpyAsync(w.dctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, st));
+
+  // ||b||
+  double bn2 = 0;
+  {
+    double* out = w.dscal + c.L.sc + SC_BNORM;
+    if (f32)
+      k_residual<float, float><<<c.grid, RED_THREADS, 0, st>>>((const float2*)bd, nullptr, nullptr, N, w.part,
+                                                               c.pstride, w.counter, out);
+    else
+      k_residual<double, double><<<c.grid, RED_THREADS, 0, st>>>((const double2*)bd, nullptr, nullptr, N, w.part,
+                                                                 c.pstride, w.counter, out);
+    note_launch();
+    SG_CUDA_TRY(cudaGetLastError());
+    SG_CUDA_TRY(cudaMemcpyAsync(&bn2, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  const double bnorm = std::sqrt(bn2);
+  sg_gmres_info inf{};
+  sg_status status = SG_ENOTCONV;
+  if (!std::isfinite(bnorm)) {
+    status = fail(SG_EINVAL, "right-hand side is not finite");
+    if (info) { inf.status = status; *info = inf; }
+    return status;
+  }
+  if (bnorm == 0.0) {
+    SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
+    if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    inf.status = SG_OK;
+    if (info) *info = inf;
+    return SG_OK;
+  }
+  const int max_outer = mixed ? (opts->max_outer <= 0 ? 20 : opts->max_outer) : 1 << 30;
+  const double inner_tol = opts->inner_tol <= 0 ? 1e-4 : opts->inner_tol;
+  int iters = 0, cycles = 0, outer = 0;
+  double relres = 1.0;
+  int ctl[16];
+  for (;;) {
+    double rn2 = 0;
+    sg_status s;
+    if (f32)
+      s = residual_norm<float>(c, (const float2*)bd, (const float2*)xd, x_zero, (float2*)w.Z, w.V, true, &rn2);
+    else
+      s = residual_norm<double>(c, (const double2*)bd, (const double2*)xd, x_zero, (double2*)w.R64, w.V, inner32,
+                                &rn2);
+    if (s != SG_OK) return s;
+    relres = std::sqrt(rn2) / bnorm;
+    if (!std::isfinite(relres)) { status = SG_EBREAKDOWN; break; }
+    if (relres <= opts->tol) { status = SG_OK; break; }
+    if (iters >= maxit) { status = SG_ENOTCONV; break; }
+    if (mixed && outer >= max_outer) { status = SG_ENOTCONV; break; }
+    // inner tolerance on |g| relative to ref
+    double tol_est, ref;
+    if (mixed) {
+      ref = std::sqrt(rn2);
+      tol_est = std::max(inner_tol, 0.5 * opts->tol * bnorm / ref);
+    } else {
+      ref = bnorm;
+      tol_est = opts->tol;
+    }
+    bool any = false;
+    s = inner32 ? run_cycle<float>(c, opts->prec, m, tol_est, ref, check_every, &any)
+                : run_cycle<double>(c, opts->prec, m, tol_est, ref, check_every, &any);
+    if (s != SG_OK) return s;
+    SG_CUDA_TRY(cudaMemcpyAsync(ctl, w.dctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ctl[CTL_FLAGS] & FL_NAN) { status = SG_EBREAKDOWN; break; }
+    if (any) {
+      if (f32)
+        k_axpy<float, float><<<c.grid, RED_THREADS, 0, st>>>((float2*)xd, (const float2*)w.Z, N, w.dctl);
+      else if (mixed)
+        k_axpy<double, float><<<c.grid, RED_THREADS, 0, st>>>((double2*)xd, (const float2*)w.Z, N, w.dctl);
+      else
+        k_axpy<double, double><<<c.grid, RED_THREADS, 0, st>>>((double2*)xd, (const double2*)w.Z, N, w.dctl);
+      note_launch();
+      SG_CUDA_TRY(cudaGetLastError());
+      x_zero = false;
+    }
+    iters = ctl[CTL_ITERS];
+    ++cycles;
+    if (mixed) ++outer;
+    if (!any && !(ctl[CTL_FLAGS] & FL_CONV)) { status = SG_ENOTCONV; break; }
+    if (!any && (ctl[CTL_FLAGS] & FL_CONV)) {
+      // estimate says converged at zero steps but the true residual disagrees
+      status = SG_ENOTCONV;
+      break;
+    }
+    if ((ctl[CTL_FLAGS] & FL_BREAK) && !(ctl[CTL_FLAGS] & FL_CONV)) {
+      // invariant subspace: the update solved the system up to rounding; one more residual check
+      ctl[CTL_FLAGS] &= ~FL_BREAK;
+    }
+  }
+  if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(cudaStreamSynchronize(st));
+  inf.iters = iters;
+  inf.cycles = cycles;
+  inf.outer = outer;
+  inf.relres = relres;
+  inf.status = status;
+  if (info) *info = inf;
+  if (status == SG_ENOTCONV) set_error("GMRES did not reach tol within maxit");
+  if (status == SG_EBREAKDOWN) set_error("GMRES breakdown: non-finite values");
+  return status;
+}

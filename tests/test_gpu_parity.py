@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (derived from the arithmetic):
+* matvec FP64: each output sums <= ~25 terms, so the rounding error is at
+  most ~25 u64 (|terms|) -> 1e-13 relative to the row's absolute scale.
+* matvec FP32: same count with u32 = 6e-8 -> 3e-6 relative to the row scale
+  (inputs rounded to complex64 first, so only arithmetic error is measured).
+* preconditioner FP64: a backward-stable direct solve has forward error
+  <= kappa(S_blk) * n * u64; with kappa <= 1e5 here -> 1e-9 relative.
+* GMRES FP64 at tol 1e-10: ||x - x*|| <= kappa(A) * tol; kappa(A) <= ~1e4 on
+  these grids -> 1e-5 relative to the direct solution; the true relres is
+  re-computed by the oracle (FP64) and must be <= tol.
+* mixed: relres <= 1e-8 computed by the oracle in FP64 (the target of the
+  mixed-precision path); the error against the direct solution is reported.
+"""
+import numpy as np
+import pytest
+
+from oracle import krylov, sg
+from paper_2209_14740_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2209_14740_gb300 import binding
+    binding.load()
+    return binding
+
+
+def problems():
+    D, A = inputs.DIRICHLET, inputs.ABSORBING
+    return [
+        inputs.helmholtz_1d_c1(n_unknowns=37, r=5),
+        inputs.paper_1d(10.0, 0.1, 3),
+        inputs.random_problem(31, dim=1, g=150, s=1, r=8, bc=(A, A, D, D)),
+        inputs.random_problem(32, dim=2, g=13, s=2, r=2),
+        inputs.random_problem(33, dim=2, g=11, s=3, r=3, bc=(D, D, D, D)),
+        inputs.random_problem(34, dim=2, g=9, s=6, r=2),
+        inputs.random_problem(35, dim=2, g=17, s=0, r=0),
+        inputs.helmholtz_2d(21, 3, 3, 12.0, 0.15),
+        inputs.helmholtz_2d(19, 2, 4, 8.0, 0.2),
+        _dirichlet_2d(),
+        _rect_2d(),
+    ]
+
+
+def _dirichlet_2d():
+    p = inputs.helmholtz_2d(15, 2, 2, 9.0, 0.1)
+    p.bc = (inputs.DIRICHLET,) * 4
+    return p
+
+
+def _rect_2d():
+    """Non-square absorbing grid (13 x 9 nodes) with constant k_0: mx != my."""
+    rng = np.random.default_rng(77)
+    nx, ny, s = 13, 9, 2
+    k0 = np.full(nx * ny, 7.0)
+    kl = 0.8 * (2 * rng.random((s, nx * ny)) - 1)
+    f = rng.standard_normal(nx * ny)
+    return inputs.Problem("rect_13x9", 2, nx, ny, 1.0 / 12, (inputs.ABSORBING,) * 4, s, 3, k0, kl, f, beta=0.5)
+
+
+def rand_vec(N, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(N) + 1j * rng.standard_normal(N)
+
+
+@pytest.mark.parametrize("idx", range(len(problems())))
+def test_matvec_fp64_fp32(B, idx):
+    pr = problems()[idx]
+    ref = sg.assemble_problem(pr)
+    op = B.SG(pr)
+    N = op.N
+    assert N == ref.A.shape[0]
+    x = rand_vec(N, idx)
+    X = torch.from_numpy(x).to(DEV)
+    Y = torch.empty_like(X)
+    op.matvec(X, Y, B.FP64)
+    y = Y.cpu().numpy()
+    yr = ref.A @ x
+    scale = abs(ref.A) @ np.abs(x) + abs(ref.Lbig) @ np.abs(x)
+    assert np.all(np.abs(y - yr) <= 1e-13 * scale + 1e-300), np.max(np.abs(y - yr) / scale)
+    x32 = x.astype(np.complex64)
+    X32 = torch.from_numpy(x32).to(DEV)
+    Y32 = torch.empty_like(X32)
+    op.matvec(X32, Y32, B.FP32)
+    y32 = Y32.cpu().numpy().astype(np.complex128)
+    yr32 = ref.A @ x32.astype(np.complex128)
+    assert np.all(np.abs(y32 - yr32) <= 3e-6 * scale), np.max(np.abs(y32 - yr32) / scale)
+    op.close()
+
+
+def test_rhs(B):
+    pr = inputs.helmholtz_2d(21, 3, 3, 12.0, 0.15)
+    ref = sg.assemble_problem(pr)
+    op = B.SG(pr)
+    b = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+    op.rhs(b, B.FP64)
+    np.testing.assert_array_equal(b.cpu().numpy(), ref.b)
+    b32 = torch.empty(op.N, dtype=torch.complex64, device=DEV)
+    op.rhs(b32, B.FP32)
+    np.testing.assert_array_equal(b32.cpu().numpy(), ref.b.astype(np.complex64))
+
+
+PREC_CASES = [0, 1, 2, 3, 7, 8, 9, 10]   # 1D, or 2D with constant k_0 (index 3 is skipped)
+
+
+@pytest.mark.parametrize("idx", PREC_CASES)
+@pytest.mark.parametrize("kind", [1, 2])
+def test_precond(B, idx, kind):
+    pr = problems()[idx]
+    if pr.dim == 2 and np.ptp(pr.k0) > 0:
+        pytest.skip("2D preconditioner needs constant k_0")
+    ref = sg.assemble_problem(pr)
+    blk = ref.S0 if kind == 1 else sg.csl_mean_block(ref, pr.beta)
+    M = krylov.BlockPrecond(blk, ref.P)
+    op = B.SG(pr)
+    x = rand_vec(op.N, 100 + idx)
+    zr = M(x)
+    X = torch.from_numpy(x).to(DEV)
+    Z = torch.empty_like(X)
+    op.precond(X, Z, kind, B.FP64)
+    z = Z.cpu().numpy()
+    assert np.linalg.norm(z - zr) / np.linalg.norm(zr) < 1e-9
+    # in place
+    op.precond(X, X, kind, B.FP64)
+    assert np.linalg.norm(X.cpu().numpy() - zr) / np.linalg.norm(zr) < 1e-9
+    # FP32: forward error of a stable solve ~ kappa * u32
+    x32 = x.astype(np.complex64)
+    zr32 = M(x32.astype(np.complex128))
+    X32 = torch.from_numpy(x32).to(DEV)
+    Z32 = torch.empty_like(X32)
+    op.precond(X32, Z32, kind, B.FP32)
+    e32 = np.linalg.norm(Z32.cpu().numpy() - zr32) / np.linalg.norm(zr32)
+    assert e32 < 2e-4, e32
+    op.close()
+
+
+def test_precond_unsupported_for_varying_k0(B):
+    pr = problems()[3]
+    assert np.ptp(pr.k0) > 0
+    op = B.SG(pr)
+    X = torch.zeros(op.N, dtype=torch.complex128, device=DEV)
+    with pytest.raises(B.SgError) as ei:
+        op.precond(X, X, B.PREC_MEAN, B.FP64)
+    assert ei.value.status == B.SG_EUNSUPPORTED
+    op.close()
+
+
+GMRES_CASES = [(0, 0, 1), (0, 0, 2), (0, 0, 0), (1, 0, 1), (7, 20, 1), (7, 20, 2), (8, 10, 1), (4, 15, 0)]
+
+
+@pytest.mark.parametrize("idx,restart,prec", GMRES_CASES)
+def test_gmres_fp64_against_oracle(B, idx, restart, prec):
+    pr = problems()[idx]
+    ref = sg.assemble_problem(pr)
+    xd = krylov.direct(ref.A, ref.b)
+    Mo = None
+    if prec:
+        blk = ref.S0 if prec == 1 else sg.csl_mean_block(ref, pr.beta)
+        Mo = krylov.BlockPrecond(blk, ref.P)
+    tol = 1e-10
+    ro = krylov.gmres(ref.A, ref.b, Mo, restart=restart or None, tol=tol, maxit=4000)
+    op = B.SG(pr)
+    b = torch.from_numpy(ref.b).to(DEV)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=restart, tol=tol, prec=prec, mode=B.FP64, maxit=4000)
+    xg = x.cpu().numpy()
+    relres = np.linalg.norm(ref.b - ref.A @ xg) / np.linalg.norm(ref.b)
+    assert info["status"] == B.SG_OK, info
+    assert relres <= tol * 1.01, relres
+    assert abs(info["relres"] - relres) <= 1e-3 * tol + 1e-13
+    assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) < 1e-5
+    assert abs(info["iters"] - ro.iters) <= max(2, ro.iters // 20), (info["iters"], ro.iters)
+    op.close()
+
+
+@pytest.mark.parametrize("idx,restart,prec", [(0, 0, 1), (7, 20, 1), (7, 20, 2), (8, 10, 1), (2, 40, 0)])
+def test_gmres_mixed_reaches_1e8(B, idx, restart, prec):
+    pr = problems()[idx]
+    ref = sg.assemble_problem(pr)
+    xd = krylov.direct(ref.A, ref.b)
+    op = B.SG(pr)
+    b = torch.from_numpy(ref.b).to(DEV)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=restart, tol=1e-8, prec=prec, mode=B.MIXED, maxit=20000)
+    xg = x.cpu().numpy()
+    relres = np.linalg.norm(ref.b - ref.A @ xg) / np.linalg.norm(ref.b)
+    err = np.linalg.norm(xg - xd) / np.linalg.norm(xd)
+    print("mixed case %d: relres %.3e err vs direct %.3e iters %d outer %d" % (idx, relres, err, info["iters"],
+                                                                             info["outer"]))
+    assert info["status"] == B.SG_OK, info
+    assert relres <= 1e-8
+    assert abs(info["relres"] - relres) <= 1e-3 * relres + 1e-14
+    op.close()
+
+
+def test_gmres_fp32_mode(B):
+    pr = problems()[7]
+    ref = sg.assemble_problem(pr)
+    op = B.SG(pr)
+    b = torch.from_numpy(ref.b.astype(np.complex64)).to(DEV)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=20, tol=1e-5, prec=B.PREC_MEAN, mode=B.FP32)
+    xg = x.cpu().numpy().astype(np.complex128)
+    relres = np.linalg.norm(ref.b - ref.A @ xg) / np.linalg.norm(ref.b)
+    assert info["status"] == B.SG_OK and relres < 2e-5, (info, relres)
+    op.close()
+
+
+def test_gmres_edge_cases(B):
+    pr = problems()[7]
+    ref = sg.assemble_problem(pr)
+    xd = krylov.direct(ref.A, ref.b)
+    op = B.SG(pr)
+    b = torch.from_numpy(ref.b).to(DEV)
+    # exact initial guess: zero iterations
+    x0 = torch.from_numpy(xd).to(DEV)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=20, tol=1e-8, prec=B.PREC_MEAN, mode=B.FP64, x0=x0)
+    assert info["iters"] == 0 and info["status"] == B.SG_OK
+    # zero right-hand side: x = 0
+    z = torch.zeros_like(b)
+    x.fill_(1.0)
+    info = op.gmres(z, x, restart=20, tol=1e-8, prec=B.PREC_MEAN, mode=B.FP64)
+    assert info["status"] == B.SG_OK and float(x.abs().max()) == 0.0
+    # maxit too small: not converged, best iterate returned
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=20, tol=1e-12, prec=B.PREC_NONE, mode=B.FP64, maxit=3)
+    assert info["status"] == B.SG_ENOTCONV and info["iters"] == 3
+    # restart 1 still converges (slowly) with the mean-value preconditioner
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=1, tol=1e-6, prec=B.PREC_MEAN, mode=B.FP64, maxit=5000)
+    assert info["status"] == B.SG_OK
+    # NaN right-hand side is rejected
+    bn = b.clone()
+    bn[3] = float("nan")
+    with pytest.raises(B.SgError) as ei:
+        op.gmres(bn, x, restart=20, tol=1e-8, prec=B.PREC_MEAN, mode=B.FP64)
+    assert ei.value.status == B.SG_EINVAL
+    # host buffers (host_io) give the same answer as device buffers
+    bh = ref.b.copy()
+    xh = np.zeros_like(bh)
+    info_h = op.gmres(bh, xh, restart=20, tol=1e-10, prec=B.PREC_MEAN, mode=B.FP64, host_io=True)
+    xdev = torch.zeros_like(b)
+    info_d = op.gmres(b, xdev, restart=20, tol=1e-10, prec=B.PREC_MEAN, mode=B.FP64)
+    assert info_h["iters"] == info_d["iters"]
+    np.testing.assert_array_equal(xh, xdev.cpu().numpy())
+    op.close()
+
+
+def test_assemble_rejects_bad_input(B):
+    pr = inputs.random_problem(40, dim=2, g=9, s=2, r=2)
+    pr.kl = pr.kl * 50.0          # k(x, xi) < 0 for some xi
+    with pytest.raises(B.SgError) as ei:
+        B.SG(pr)
+    assert ei.value.status == B.SG_EINVAL
+    pr = inputs.random_problem(41, dim=2, g=9, s=2, r=2)
+    pr.k0[5] = float("nan")
+    with pytest.raises(B.SgError):
+        B.SG(pr)
+    pr = inputs.random_problem(42, dim=2, g=9, s=2, r=2, bc=(1, 0, 1, 1))
+    with pytest.raises(B.SgError):
+        B.SG(pr)
+
+
+def test_complex_symmetry_property_fp64(B):
+    """A^T = A (Theorem 3.4): x^T (A y) = y^T (A x) for random x, y."""
+    pr = inputs.helmholtz_2d(61, 4, 3, 20.0, 0.15)
+    op = B.SG(pr)
+    x = torch.from_numpy(rand_vec(op.N, 1)).to(DEV)
+    y = torch.from_numpy(rand_vec(op.N, 2)).to(DEV)
+    Ax = torch.empty_like(x)
+    Ay = torch.empty_like(y)
+    op.matvec(x, Ax, B.FP64)
+    op.matvec(y, Ay, B.FP64)
+    lhs = complex((x * Ay).sum())
+    rhs = complex((y * Ax).sum())
+    assert abs(lhs - rhs) <= 1e-12 * float((x.abs() * Ay.abs()).sum())
+    op.close()

@@ -166,3 +166,28 @@ def test_sg_mean_against_quadrature():
         errs.append(np.abs(V[0] - mean).max() / np.abs(mean).max())
     assert errs[-1] < 1e-7
     assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+
+
+@pytest.mark.parametrize("seed,dim,bc", [(21, 1, None), (22, 2, None), (23, 2, (0, 0, 0, 0)),
+                                          (24, 1, (0, 1, 0, 0))])
+def test_apply_rows_matches_explicit_matrix(seed, dim, bc):
+    """The row-by-row evaluation used for full-size sampled parity equals the
+    explicit Kronecker assembly; its absolute form (sum of |term| over the
+    Laplacian and coupling terms separately) bounds |A| |x| from above and
+    equals it on rows without a diagonal overlap of the two parts."""
+    pr = inputs.random_problem(seed, dim=dim, g=9 if dim == 2 else 17, s=3, r=2, bc=bc)
+    S = sg.assemble_problem(pr)
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(S.A.shape[0]) + 1j * rng.standard_normal(S.A.shape[0])
+    rows = rng.choice(S.A.shape[0], size=40, replace=False)
+    got = sg.apply_rows(pr, x, rows)
+    np.testing.assert_allclose(got, (S.A @ x)[rows], rtol=1e-13, atol=1e-13 * np.abs(S.A @ x).max())
+    gabs = sg.apply_rows(pr, x, rows, absolute=True)
+    ref = (abs(S.A) @ np.abs(x))[rows]
+    assert np.all(gabs >= ref * (1 - 1e-13))
+    L = sg.fd.make_grid(pr.dim, pr.nx, pr.ny, pr.h, pr.bc).L
+    n = L.shape[0]
+    # the gap is exactly |L_uu| + |M_aa| - |L_uu + M_aa| times |x_au|
+    u = rows % n
+    gap = gabs - ref
+    assert np.all(gap <= 2 * np.abs(L.diagonal()[u]) * np.abs(x[rows]) * (1 + 1e-12) + 1e-9 * ref)

@@ -10,8 +10,12 @@ import concurrent.futures as cf
 import os
 import shutil
 import subprocess
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
@@ -27,13 +31,15 @@ def nvcc_path() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
+    from paper_2209_14740_gb300 import codegen_matvec
+    gen = codegen_matvec.generate(os.path.join(BUILD, "gen", "k_matvec_special.cu"))
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp"))) + [gen]
 
 
 def _compile(nvcc, src, verbose_ptxas=False):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     cmd = [nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-           "-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
+           "-I", os.path.join(HERE, "..", "include"), "-I", CSRC, "-c", src, "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
         if verbose_ptxas:
@@ -71,5 +77,4 @@ def build(verbose_ptxas: bool = False, jobs: int | None = None) -> str:
 
 
 if __name__ == "__main__":
-    import sys
     print(build(verbose_ptxas="-v" in sys.argv))

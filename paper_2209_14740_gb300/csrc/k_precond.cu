@@ -134,31 +134,48 @@ __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) {
 // Multi-RHS tridiagonal solve with gttrf factors.  Thread (sys, rhs) walks
 // j = 0..len-1; element address rhs*sR + j*sJ + sys*sS; factors at
 // j*nsys + sys.  Optional row scaling s_j applied to the input and the output
-// (2D: d_y^-1/2).  In place on Z (Z may alias R).
+// (2D: d_y^-1/2) and an optional scalar on the input (the solve is linear).
+// R and Z must not overlap: the sweeps load CH rows ahead of the dependent
+// recurrence so the loads of a chunk overlap each other.
 template <typename T>
 __global__ void k_tri_solve(int nsys, int nrhs, int len, long long sR, long long sJ, long long sS,
-                            TriFactors<T> F, const T* __restrict__ rowscale, const C2<T>* R, C2<T>* Z,
-                            const int* skip, const double* in_scale) {
+                            TriFactors<T> F, const T* __restrict__ rowscale, const C2<T>* __restrict__ R,
+                            C2<T>* __restrict__ Z, const int* skip, const double* in_scale) {
   if (skip && *skip) return;
+  constexpr int CH = 8;
   const int sys = blockIdx.x * blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
   if (sys >= nsys || rhs >= nrhs) return;
   const C2<T>* r = R + rhs * sR + sys * sS;
   C2<T>* z = Z + rhs * sR + sys * sS;
   auto f = [&](int j) { return (size_t)j * nsys + sys; };
-  // forward: apply row interchanges and L
-  // optional scalar factor on the input (the solve is linear)
   const T s0 = in_scale ? (T)*in_scale : T(1);
+  // forward: row interchanges and L
   C2<T> cur = cscale<T>(r[0], rowscale ? rowscale[0] * s0 : s0);
-  for (int j = 0; j + 1 < len; ++j) {
-    const C2<T> nxt = cscale<T>(r[(j + 1) * sJ], rowscale ? rowscale[j + 1] * s0 : s0);
-    const C2<T> l = F.dl[f(j)];
-    if (!F.piv[f(j)]) {
-      z[j * sJ] = cur;
-      cur = csub<T>(nxt, cmul<T>(l, cur));
-    } else {
-      z[j * sJ] = nxt;
-      cur = csub<T>(cur, cmul<T>(l, nxt));
+  for (int j0 = 0; j0 + 1 < len; j0 += CH) {
+    C2<T> rv[CH], lv[CH];
+    uint8_t pv[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int j = j0 + q;
+      if (j + 1 < len) {
+        rv[q] = cscale<T>(r[(j + 1) * sJ], rowscale ? rowscale[j + 1] * s0 : s0);
+        lv[q] = F.dl[f(j)];
+        pv[q] = F.piv[f(j)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int j = j0 + q;
+      if (j + 1 < len) {
+        if (!pv[q]) {
+          z[j * sJ] = cur;
+          cur = csub<T>(rv[q], cmul<T>(lv[q], cur));
+        } else {
+          z[j * sJ] = rv[q];
+          cur = csub<T>(cur, cmul<T>(lv[q], rv[q]));
+        }
+      }
     }
   }
   // back substitution with U (diagonal, du, du2)
@@ -166,38 +183,52 @@ __global__ void k_tri_solve(int nsys, int nrhs, int len, long long sR, long long
   C2<T> x2;                                        // x_{j+2}
   x2.x = T(0);
   x2.y = T(0);
-  {
-    C2<T> o = rowscale ? cscale<T>(x1, rowscale[len - 1]) : x1;
-    z[(len - 1) * sJ] = o;
-  }
-  for (int j = len - 2; j >= 0; --j) {
-    C2<T> b = z[j * sJ];
-    b = csub<T>(b, cmul<T>(F.du[f(j)], x1));
-    b = csub<T>(b, cmul<T>(F.du2[f(j)], x2));
-    const C2<T> xj = cmul<T>(b, F.dinv[f(j)]);
-    z[j * sJ] = rowscale ? cscale<T>(xj, rowscale[j]) : xj;
-    x2 = x1;
-    x1 = xj;
+  z[(len - 1) * sJ] = rowscale ? cscale<T>(x1, rowscale[len - 1]) : x1;
+  for (int j0 = len - 2; j0 >= 0; j0 -= CH) {
+    C2<T> bv[CH], uv[CH], u2v[CH], dv[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int j = j0 - q;
+      if (j >= 0) {
+        bv[q] = z[j * sJ];
+        uv[q] = F.du[f(j)];
+        u2v[q] = F.du2[f(j)];
+        dv[q] = F.dinv[f(j)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int j = j0 - q;
+      if (j >= 0) {
+        C2<T> b = csub<T>(bv[q], cmul<T>(uv[q], x1));
+        b = csub<T>(b, cmul<T>(u2v[q], x2));
+        const C2<T> xj = cmul<T>(b, dv[q]);
+        z[j * sJ] = rowscale ? cscale<T>(xj, rowscale[j]) : xj;
+        x2 = x1;
+        x1 = xj;
+      }
+    }
   }
 }
 
 // C[M][Nn] = A[M][K] * B[K][Nn], complex, row-major, CUDA cores.
-// 64 x 64 output tile per CTA, 256 threads, 4 x 4 outputs per thread.
-template <typename T>
+// (16*TM) x (16*TN) output tile per CTA, 256 threads, TM x TN outputs per
+// thread; the launcher picks the tile so that the grid fills the GPU.
+template <typename T, int TM, int TN>
 __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>* __restrict__ A,
                                               const C2<T>* __restrict__ B, C2<T>* __restrict__ C,
                                               const int* skip) {
   if (skip && *skip) return;
-  constexpr int BM = 64, BN = 64, BK = 16;
+  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
   __shared__ C2<T> As[BK][BM + 1];
   __shared__ C2<T> Bs[BK][BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  T accr[4][4], acci[4][4];
+  T accr[TM][TN], acci[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = T(0);
+    for (int j = 0; j < TN; ++j) accr[i][j] = acci[i][j] = T(0);
   for (int k0 = 0; k0 < K; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       const int mm = e / BK, kk = e % BK;
@@ -220,15 +251,15 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      C2<T> a[4], b[4];
+      C2<T> a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           accr[i][j] += a[i].x * b[j].x - a[i].y * b[j].y;
           acci[i][j] += a[i].x * b[j].y + a[i].y * b[j].x;
         }
@@ -236,11 +267,11 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn < Nn) {
         C2<T> v;
@@ -253,10 +284,17 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>
 }
 
 template <typename T>
-static cudaError_t cgemm(int M, int Nn, int K, const C2<T>* A, const C2<T>* B, C2<T>* C, cudaStream_t st,
-                         const int* skip) {
-  dim3 grid((Nn + 63) / 64, (M + 63) / 64);
-  k_cgemm<T><<<grid, 256, 0, st>>>(M, Nn, K, A, B, C, skip); note_launch();
+static cudaError_t cgemm(const sg_handle* h, int M, int Nn, int K, const C2<T>* A, const C2<T>* B, C2<T>* C,
+                         cudaStream_t st, const int* skip) {
+  const long long tiles64 = (long long)((Nn + 63) / 64) * ((M + 63) / 64);
+  if (tiles64 >= 2LL * h->num_sms) {
+    dim3 grid((Nn + 63) / 64, (M + 63) / 64);
+    k_cgemm<T, 4, 4><<<grid, 256, 0, st>>>(M, Nn, K, A, B, C, skip);
+  } else {
+    dim3 grid((Nn + 31) / 32, (M + 31) / 32);
+    k_cgemm<T, 2, 2><<<grid, 256, 0, st>>>(M, Nn, K, A, B, C, skip);
+  }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -266,11 +304,17 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
   const PrecBlock& blk = h->blk[which];
   TriFactors<T> F;
   if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;
+  C2<T>* tmp = reinterpret_cast<C2<T>*>(h->d_tmp);
   if (h->dim == 1) {
-    // one system of length n, P right-hand sides (the modes)
+    // one system of length n, P right-hand sides (the modes); out of place
     dim3 b(1, 64), g(1, (h->P + 63) / 64);
-    k_tri_solve<T><<<g, b, 0, st>>>(1, h->P, h->n, h->n, 1, 0, F, nullptr, R, Z, skip, in_scale); note_launch();
-    return cudaGetLastError();
+    C2<T>* out = (R == Z) ? tmp : Z;
+    k_tri_solve<T><<<g, b, 0, st>>>(1, h->P, h->n, h->n, 1, 0, F, nullptr, R, out, skip, in_scale);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && out != Z)
+      e = cudaMemcpyAsync(Z, out, (size_t)h->N * sizeof(C2<T>), cudaMemcpyDeviceToDevice, st);
+    return e;
   }
   const int mx = h->mx, my = h->my, P = h->P;
   const C2<T>* Q;
@@ -278,15 +322,15 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
   const T* dyinv;
   if constexpr (sizeof(T) == 8) { Q = h->d_Q; Qt = h->d_Qt; dyinv = h->d_dyinv; }
   else { Q = h->d_Q32; Qt = h->d_Qt32; dyinv = h->d_dyinv32; }
-  C2<T>* tmp = reinterpret_cast<C2<T>*>(h->d_tmp);
-  cudaError_t e = cgemm<T>(P * my, mx, mx, R, Q, tmp, st, skip);      // (1)
+  C2<T>* tmp2 = reinterpret_cast<C2<T>*>(h->d_tmp2);
+  cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, Q, tmp, st, skip);   // (1)
   if (e != cudaSuccess) return e;
-  dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);                  // (2) sys = i, rhs = mode, j = y line
-  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, (long long)mx * my, mx, 1, F, dyinv, tmp, tmp, skip,
-                                  in_scale); note_launch();
+  dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);                     // (2) sys = i, rhs = mode, j = y line
+  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, (long long)mx * my, mx, 1, F, dyinv, tmp, tmp2, skip, in_scale);
+  note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return cgemm<T>(P * my, mx, mx, tmp, Qt, Z, st, skip);               // (3)
+  return cgemm<T>(h, P * my, mx, mx, tmp2, Qt, Z, st, skip);        // (3)
 }
 
 template cudaError_t launch_precond<double>(const sg_handle*, int, const double2*, double2*, cudaStream_t,

@@ -310,7 +310,7 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_gval32); cudaFree(h->d_gdiag32); cudaFree(h->d_fields32);
   for (auto& b : h->blk) if (b.f64.dl) free_factors(b);
   cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
-  cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp);
+  cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
   sgi_free_gmres_work(h);
   delete h;
 }
@@ -426,8 +426,9 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
       h->blk[which].ready = true;
     }
     cudaFree(d_gd); cudaFree(d_ls); cudaFree(d_go);
-    SG_CUDA_TRY(cudaMalloc(&h->d_tmp, (size_t)h->N * sizeof(double2)));
+    SG_CUDA_TRY(cudaMalloc(&h->d_tmp2, (size_t)h->N * sizeof(double2)));
   }
+  SG_CUDA_TRY(cudaMalloc(&h->d_tmp, (size_t)h->N * sizeof(double2)));
   int bad = 0;
   SG_CUDA_TRY(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
   cudaFree(d_bad);
@@ -508,6 +509,7 @@ sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
     }
   if (!(kmin > 0)) { delete h; return fail(SG_EINVAL, "k(x, xi) must be positive for all xi (k_0 - sum|k_l| <= 0)"); }
   h->kbar = 0.5 * (k0min + k0max);
+  h->specialised = matvec_is_specialised(h->s, h->r) ? 1 : 0;
   h->separable = (k0max - k0min) <= 1e-13 * k0max;
   h->k0u.assign(fields.begin(), fields.begin() + n);
 

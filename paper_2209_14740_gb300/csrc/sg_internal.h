@@ -112,7 +112,8 @@ struct sg_handle {
   float2* d_Qt32 = nullptr;
   double* d_dyinv = nullptr;         // 2D: d_y^-1/2 per y line
   float* d_dyinv32 = nullptr;
-  void* d_tmp = nullptr;             // N complex128 scratch (2D precond intermediate)
+  void* d_tmp = nullptr;             // N complex128 scratch (preconditioner intermediate)
+  void* d_tmp2 = nullptr;            // N complex128 scratch (2D: second intermediate)
   double eig_orth_err = 0.0;         // max |Q^T Q - I| of the host eigenvectors
 
   sgi::GmresWork gw;
@@ -138,6 +139,9 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
 
 // launch bookkeeping (sg_kernel_launches)
 void note_launch();
+
+// true if a register-resident complex64 matvec kernel exists for (s, r)
+bool matvec_is_specialised(int s, int r);
 
 // host helpers
 bool csym_tridiag_eig(int n, const std::vector<cd>& diag, const std::vector<cd>& off,

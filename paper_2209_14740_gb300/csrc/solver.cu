@@ -98,6 +98,29 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm /* NV * 32
   __syncthreads();
 }
 
+// Sum over all blocks of the partials part[b * pstride + k], k < nvals, done
+// by the warps of one block in parallel: lanes stride over the blocks, then a
+// shuffle tree (fixed order, so the result is reproducible).  emit(k, sum) is
+// called by lane 0 of the warp that owns k.
+template <typename F>
+__device__ __forceinline__ void sum_block_partials(const double* part, int pstride, int nvals, F&& emit) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x;
+  for (int k = warp; k < nvals; k += nw) {
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nb; b += 64) {
+      s0 += __ldcg(part + (size_t)b * pstride + k);
+      s1 += __ldcg(part + (size_t)(b + 32) * pstride + k);
+    }
+    if (b < nb) s0 += __ldcg(part + (size_t)b * pstride + k);
+    double s = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) emit(k, s);
+  }
+}
+
 // Called by every thread after it stored its block partials; returns true in
 // the last block (all partials visible).  The counter is reset by that block.
 __device__ __forceinline__ bool last_block(unsigned* counter) {
@@ -122,39 +145,40 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const C2<T>* __restrict__ 
                                                      unsigned* counter, const double* vscale, double* d_out,
                                                      double* c_out, const int* ctl) {
   if (ctl[CTL_DONE]) return;
-  __shared__ double sm[8 * 32];
+  constexpr int G = 8;   // vectors per pass over this block's elements
+  __shared__ double sm[2 * G * 32];
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int g0 = 0; g0 < nv; g0 += 4) {
-    T acc[8];
+  for (int g0 = 0; g0 < nv; g0 += G) {
+    T acc[2 * G];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = T(0);
-    const int ng = min(4, nv - g0);
+    for (int k = 0; k < 2 * G; ++k) acc[k] = T(0);
+    const int ng = min(G, nv - g0);
+    const C2<T>* Vg = V + (size_t)g0 * N;
+#pragma unroll 2
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
       const C2<T> we = w[e];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < G; ++q) {
         if (q < ng) {
-          const C2<T> v = V[(size_t)(g0 + q) * N + e];
+          const C2<T> v = Vg[(size_t)q * N + e];
           acc[2 * q] += v.x * we.x + v.y * we.y;
           acc[2 * q + 1] += v.x * we.y - v.y * we.x;
         }
       }
     }
-    double dv[8];
+    double dv[2 * G];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) dv[k] = (double)acc[k];
-    block_sum<8>(dv, sm);
+    for (int k = 0; k < 2 * G; ++k) dv[k] = (double)acc[k];
+    block_sum<2 * G>(dv, sm);
     if (threadIdx.x == 0)
       for (int k = 0; k < 2 * ng; ++k) part[(size_t)blockIdx.x * pstride + 2 * g0 + k] = dv[k];
   }
   if (last_block(counter)) {
-    for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) {
-      double s = 0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * pstride + k);
+    sum_block_partials(part, pstride, 2 * nv, [&](int k, double s) {
       d_out[k] = s;
       const double vs = vscale[k >> 1];
       c_out[k] = vs * vs * s;
-    }
+    });
     if (threadIdx.x == 0) *counter = 0;
   }
 }
@@ -172,8 +196,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C2<T>* __restrict_
   __syncthreads();
   const long long stride = (long long)gridDim.x * blockDim.x;
   T nacc = T(0);
+#pragma unroll 2
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
     C2<T> we = w[e];
+#pragma unroll 8
     for (int i = 0; i < nv; ++i) {
       const C2<T> v = V[(size_t)i * N + e];
       const C2<T> ci = cs[i];
@@ -188,12 +214,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const C2<T>* __restrict_
     block_sum<1>(dv, sm);
     if (threadIdx.x == 0) part[(size_t)blockIdx.x * pstride] = dv[0];
     if (last_block(counter)) {
-      if (threadIdx.x == 0) {
-        double s = 0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * pstride);
-        *norm_out = s;
-        *counter = 0;
-      }
+      sum_block_partials(part, pstride, 1, [&](int, double s) { *norm_out = s; });
+      if (threadIdx.x == 0) *counter = 0;
     }
   }
 }
@@ -221,12 +243,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual(const C2<TO>* __restri
   block_sum<1>(dv, sm);
   if (threadIdx.x == 0) part[(size_t)blockIdx.x * pstride] = dv[0];
   if (last_block(counter)) {
-    if (threadIdx.x == 0) {
-      double s = 0;
-      for (int b2 = 0; b2 < (int)gridDim.x; ++b2) s += __ldcg(part + (size_t)b2 * pstride);
-      *norm_out = s;
-      *counter = 0;
-    }
+    sum_block_partials(part, pstride, 1, [&](int, double s) { *norm_out = s; });
+    if (threadIdx.x == 0) *counter = 0;
   }
 }
 
@@ -427,7 +445,7 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   sgi_free_gmres_work(h);
   const size_t N = (size_t)h->N;
   DevLayout L(m);
-  w.nblk = std::max(1, std::min(h->num_sms * 4, (int)((N + RED_THREADS - 1) / RED_THREADS)));
+  w.nblk = std::max(1, std::min(h->num_sms * 2, (int)((N + 2 * RED_THREADS - 1) / (2 * RED_THREADS))));
   cudaError_t e = cudaSuccess;
   if (!e) e = cudaMalloc(&w.V, (size_t)(m + 1) * N * elem_bytes);
   if (!e) e = cudaMalloc(&w.Z, N * elem_bytes);

@@ -180,7 +180,7 @@ def test_gmres_fp64_against_oracle(B, idx, restart, prec):
     op.close()
 
 
-@pytest.mark.parametrize("idx,restart,prec", [(0, 0, 1), (7, 20, 1), (7, 20, 2), (8, 10, 1), (2, 40, 0)])
+@pytest.mark.parametrize("idx,restart,prec", [(0, 0, 1), (7, 20, 1), (7, 20, 2), (8, 10, 1), (2, 40, 1), (4, 0, 0)])
 def test_gmres_mixed_reaches_1e8(B, idx, restart, prec):
     pr = problems()[idx]
     ref = sg.assemble_problem(pr)

@@ -37,7 +37,9 @@ SPECIALISED = [(1, 5), (2, 2), (2, 3), (3, 2), (3, 3), (4, 2), (4, 3), (6, 3)]
 BLOCK = 128          # threads per CTA (64 unknowns)
 OPAQUE = False       # per-row opaque zero in the products (blocks cross-row merging)
 MINBLOCKS = 0        # __launch_bounds__ min blocks per SM (0 = none)
-STENCIL = "split"    # "split": coupling phase then stencil loop; "inline": stencil inside each row
+STENCIL = "tile"     # "tile": 2D tile staged in shared memory; "split": coupling then stencil loop; "inline"
+SERIAL = True        # rows evaluated one after another (bounded register pressure)
+ROWS_PER_FENCE = 4   # tile mode: rows between register fences
 
 
 def _multi_indices(s, r):
@@ -81,10 +83,29 @@ def gen_kernel(s, r):
     w("  const long long n2 = 2ll * p.n;")
     w("  const float* __restrict__ xp = X + 2ll * u + c;")
     w("  float* __restrict__ yp = Y + 2ll * u + c;")
-    for a in range(P):
-        w("  const float x%d = __ldg(xp + %d * n2);" % (a, a))
     w("  const int iu = u % p.mx, ju = u / p.mx;")
     w("  const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
+    if STENCIL == "smem_first":
+        # Phase 0: Laplacian neighbours of every mode into shared memory (a
+        # streaming loop with many loads in flight, few registers).
+        w("  __shared__ float lap[%d * %d];" % (P, BLOCK))
+        w("  {")
+        w("    const float wxm0 = g.hxm ? g.wxm : 0.0f, wxp0 = g.hxp ? g.wxp : 0.0f;")
+        w("    const float wym0 = g.hym ? g.wym : 0.0f, wyp0 = g.hyp ? g.wyp : 0.0f;")
+        w("    const long long oy0 = 2ll * p.mx;")
+        w("#pragma unroll 6")
+        w("    for (int a = 0; a < %d; ++a) {" % P)
+        w("      const float* q = xp + a * n2;")
+        w("      float t = 0.0f;")
+        w("      if (g.hxm) t = fmaf(-wxm0, q[-2], t);")
+        w("      if (g.hxp) t = fmaf(-wxp0, q[2], t);")
+        w("      if (g.hym) t = fmaf(-wym0, q[-oy0], t);")
+        w("      if (g.hyp) t = fmaf(-wyp0, q[oy0], t);")
+        w("      lap[a * %d + threadIdx.x] = t;" % BLOCK)
+        w("    }")
+        w("  }")
+    for a in range(P):
+        w("  const float x%d = __ldg(xp + %d * n2);" % (a, a))
     w("  const float k0 = __ldg(p.fields + u);")
     for l in range(s):
         w("  const float k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
@@ -115,8 +136,14 @@ def gen_kernel(s, r):
             w("  asm volatile(\"\" ::: \"memory\");")
         w("  {  // row %d, alpha = %s" % (a, alpha))
         # diagonal
-        w("    const float z = %s;" % ("opaque_zero()" if OPAQUE else "0.0f"))
-        w("    float y = dbase * x%d;" % a)
+        w("    const float z = %s;" % ("opaque_zero()" if (OPAQUE or SERIAL) else "0.0f"))
+        if SERIAL:
+            w("    float y = fmaf(dbase, x%d, z);" % a)
+        else:
+            w("    float y = dbase * x%d;" % a)
+        if STENCIL == "smem_first":
+            # the address depends on the row's opaque zero, so the load stays in its row
+            w("    y += lap[%d * %d + threadIdx.x + __float_as_int(z)];" % (a, BLOCK))
         for l in range(s):
             if alpha[l] > 0:
                 gd = _b(alpha[l]) ** 2 + _b(alpha[l] + 1) ** 2
@@ -193,6 +220,10 @@ def gen_kernel(s, r):
         w("      const float tk = %s;" % t)
         w("      y = fmaf(sw1, __shfl_xor_sync(0xffffffffu, tk, 1), y);")
         w("    }")
+        if SERIAL:
+            # row end marker: the row is complete before the next row's opaque
+            # start value is produced, so rows are evaluated one after another
+            w("    asm volatile(\"\" : \"+f\"(y));")
         w("    if (valid) yp[%d * n2] = y;" % a)
         w("  }")
     if STENCIL == "split":
@@ -216,6 +247,306 @@ def gen_kernel(s, r):
     return name, P, "\n".join(L)
 
 
+def gen_kernel_tile(s, r):
+    """Tiled variant: the CTA owns TX x TY grid unknowns (two threads each,
+    one per component).  Each thread loads its component of all P modes once
+    (all loads in flight together), publishes them to shared memory, the CTA
+    loads the one-node halo of the tile, and after one barrier every row takes
+    its four stencil neighbours from shared memory.  Rows are evaluated one
+    after another (row-start opaque zero, row-end register fence), which
+    bounds the live registers to the P mode values plus the coefficients."""
+    al = _multi_indices(s, r)
+    P = len(al)
+    idx = {a: i for i, a in enumerate(al)}
+    name = "k_mvt_s%dr%d" % (s, r)
+    L = []
+    w = L.append
+    w("template <int TX, int TY>")
+    w("__global__ void __launch_bounds__(2 * TX * TY) %s(OpParams<float> p, const float* __restrict__ X, "
+      "float* __restrict__ Y) {" % name)
+    w("  constexpr int NT = 2 * TX * TY;            // threads = (unknown, component) pairs")
+    w("  constexpr int NH = 2 * (2 * TX + 2 * TY);  // halo entries per mode")
+    w("  constexpr int ST = NT + NH;                // shared-memory row stride per mode")
+    w("  extern __shared__ float xs[];              // [P][ST]: tile values, then halo values")
+    w("  if (p.skip && *p.skip) return;")
+    w("  const int t = threadIdx.x, c = t & 1, nid = t >> 1;")
+    w("  const int lx = nid % TX, ly = nid / TX;")
+    w("  const int iu0 = blockIdx.x * TX + lx, ju0 = blockIdx.y * TY + ly;")
+    w("  const bool valid = iu0 < p.mx && ju0 < p.my;")
+    w("  const int iu = min(iu0, p.mx - 1), ju = min(ju0, p.my - 1);")
+    w("  const int u = iu + p.mx * ju;")
+    w("  const long long n2 = 2ll * p.n;")
+    w("  const float* __restrict__ xp = X + 2ll * u + c;")
+    for a in range(P):
+        w("  float x%d = __ldg(xp + %d * n2);" % (a, a))
+    # halo: top row (ly=-1), bottom row (ly=TY), left col (lx=-1), right col (lx=TX)
+    # the whole halo is loaded in one batch (all loads in flight together),
+    # then written to shared memory
+    w("  {")
+    w("    constexpr int HALO_PER_THREAD = (%d * NH + NT - 1) / NT;" % P)
+    w("    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;")
+    w("    float hv[HALO_PER_THREAD];")
+    w("#pragma unroll")
+    w("    for (int i = 0; i < HALO_PER_THREAD; ++i) {")
+    w("      const int k = t + i * NT;")
+    w("      const int a = k / NH, e = k - a * NH, hc = e & 1, h = e >> 1;")
+    w("      int hx, hy;")
+    w("      if (h < TX) { hx = bx0 + h; hy = by0 - 1; }")
+    w("      else if (h < 2 * TX) { hx = bx0 + h - TX; hy = by0 + TY; }")
+    w("      else if (h < 2 * TX + TY) { hx = bx0 - 1; hy = by0 + h - 2 * TX; }")
+    w("      else { hx = bx0 + TX; hy = by0 + h - 2 * TX - TY; }")
+    w("      hv[i] = 0.0f;")
+    w("      if (k < %d * NH && hx >= 0 && hx < p.mx && hy >= 0 && hy < p.my)" % P)
+    w("        hv[i] = __ldg(X + (long long)a * n2 + 2ll * (hx + (long long)p.mx * hy) + hc);")
+    w("    }")
+    w("#pragma unroll")
+    w("    for (int i = 0; i < HALO_PER_THREAD; ++i) {")
+    w("      const int k = t + i * NT;")
+    w("      if (k < %d * NH) {" % P)
+    w("        const int a = k / NH, e = k - a * NH;")
+    w("        xs[a * ST + NT + e] = hv[i];")
+    w("      }")
+    w("    }")
+    w("  }")
+    for a in range(P):
+        w("  xs[%d * ST + t] = x%d;" % (a, a))
+    w("  const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
+    # neighbour offsets inside a mode row of xs
+    w("  const int oxm = lx > 0 ? t - 2 : NT + 2 * (2 * TX + ly) + c;")
+    w("  const int oxp = lx < TX - 1 ? t + 2 : NT + 2 * (2 * TX + TY + ly) + c;")
+    w("  const int oym = ly > 0 ? t - 2 * TX : NT + 2 * lx + c;")
+    w("  const int oyp = ly < TY - 1 ? t + 2 * TX : NT + 2 * (TX + lx) + c;")
+    w("  const float wxm = g.hxm ? g.wxm : 0.0f, wxp = g.hxp ? g.wxp : 0.0f;")
+    w("  const float wym = g.hym ? g.wym : 0.0f, wyp = g.hyp ? g.wyp : 0.0f;")
+    w("  const float k0 = __ldg(p.fields + u);")
+    for l in range(s):
+        w("  const float k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
+    w("  const float w2 = g.w2;")
+    for l in range(s):
+        w("  const float cl%d = -2.0f * w2 * k0 * k%d;" % (l + 1, l + 1))
+        w("  const float cq%d = -w2 * k%d * k%d;" % (l + 1, l + 1, l + 1))
+    for l in range(s):
+        for lp in range(l + 1, s):
+            w("  const float cp%d_%d = -2.0f * w2 * k%d * k%d;" % (l + 1, lp + 1, l + 1, lp + 1))
+    gd0 = _b(1) ** 2
+    base = "g.ldiag - w2 * k0 * k0"
+    for l in range(s):
+        base += " + cq%d * %s" % (l + 1, _f(gd0))
+    w("  const float dbase = %s;" % base)
+    w("  const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0f);")
+    w("  const float sw1 = c ? -g.w1 : g.w1;")
+    w("  float* __restrict__ yp = Y + 2ll * u + c;")
+    w("  __syncthreads();")
+
+    def fence():
+        # Empty asm that "redefines" every mode register and clobbers memory:
+        # nothing computed from X or shared memory moves across it, so at most
+        # ROWS_PER_FENCE rows are in flight and the live registers stay the
+        # P mode values plus the coefficients.  It emits no instruction.
+        for i0 in range(0, P, 28):
+            ops = ", ".join('"+f"(x%d)' % i for i in range(i0, min(P, i0 + 28)))
+            w('  asm volatile("" : %s :: "memory");' % ops)
+
+    for a, alpha in enumerate(al):
+        if a % ROWS_PER_FENCE == 0:
+            fence()
+        w("  {  // row %d, alpha = %s" % (a, alpha))
+        w("    float y = dbase * x%d;" % a)
+        w("    {")
+        w("      const float* q = xs + %d * ST;" % a)
+        w("      y = fmaf(-wxm, q[oxm], y);")
+        w("      y = fmaf(-wxp, q[oxp], y);")
+        w("      y = fmaf(-wym, q[oym], y);")
+        w("      y = fmaf(-wyp, q[oyp], y);")
+        w("    }")
+        for l in range(s):
+            if alpha[l] > 0:
+                gd = _b(alpha[l]) ** 2 + _b(alpha[l] + 1) ** 2
+                w("    y = fmaf(cq%d, %s * x%d, y);" % (l + 1, _f(gd - gd0), a))
+        k1terms = []
+
+        def group(coef, parts):
+            if not parts:
+                return
+            t = "%s * x%d" % (_f(parts[0][0]), parts[0][1])
+            for gv, bb in parts[1:]:
+                t = "fmaf(%s, x%d, %s)" % (_f(gv), bb, t)
+            w("    y = fmaf(%s, %s, y);" % (coef, t))
+
+        for l in range(s):
+            parts = []
+            for sg in (+1, -1):
+                beta = list(alpha)
+                beta[l] += sg
+                beta = tuple(beta)
+                if beta in idx:
+                    parts.append((_b(max(alpha[l], beta[l])), idx[beta]))
+            k1terms.append((l, parts))
+            group("cl%d" % (l + 1), parts)
+        for l in range(s):
+            parts = []
+            for sg in (+2, -2):
+                beta = list(alpha)
+                beta[l] += sg
+                beta = tuple(beta)
+                if beta in idx:
+                    m = min(alpha[l], beta[l])
+                    parts.append((_b(m + 1) * _b(m + 2), idx[beta]))
+            group("cq%d" % (l + 1), parts)
+        for l in range(s):
+            for lp in range(l + 1, s):
+                parts = []
+                for s1 in (+1, -1):
+                    for s2 in (+1, -1):
+                        beta = list(alpha)
+                        beta[l] += s1
+                        beta[lp] += s2
+                        beta = tuple(beta)
+                        if beta in idx:
+                            parts.append((_b(max(alpha[l], beta[l])) * _b(max(alpha[lp], beta[lp])), idx[beta]))
+                group("cp%d_%d" % (l + 1, lp + 1), parts)
+        t = "k0 * x%d" % a
+        for l, parts in k1terms:
+            for gv, bb in parts:
+                t = "fmaf(k%d, %s * x%d, %s)" % (l + 1, _f(gv), bb, t)
+        w("    if (bnd) {")
+        w("      const float tk = %s;" % t)
+        w("      y = fmaf(sw1, __shfl_xor_sync(0xffffffffu, tk, 1), y);")
+        w("    }")
+        w("    if (valid) yp[%d * n2] = y;" % a)
+        w("  }")
+    w("}")
+    return name, P, "\n".join(L)
+
+
+def gen_kernel_packed(s, r):
+    """One thread per grid unknown holding both components (float2) of all P
+    modes; the coupling uses packed FP32x2 FMAs (__ffma2_rn: the real
+    coefficient acts on re and im at once).  CTAs are 2D tiles (TX x TY
+    unknowns), so the stencil's neighbours inside the tile are L1 hits."""
+    al = _multi_indices(s, r)
+    P = len(al)
+    idx = {a: i for i, a in enumerate(al)}
+    name = "k_mv2_s%dr%d" % (s, r)
+    L = []
+    w = L.append
+
+    def f2(v):
+        return "make_float2(%s, %s)" % (_f(v), _f(v))
+
+    w("template <int TX, int TY>")
+    w("__global__ void __launch_bounds__(TX * TY) %s(OpParams<float> p, const float2* __restrict__ X, "
+      "float2* __restrict__ Y) {" % name)
+    w("  if (p.skip && *p.skip) return;")
+    w("  const int iu0 = blockIdx.x * TX + (int)(threadIdx.x % TX);")
+    w("  const int ju0 = blockIdx.y * TY + (int)(threadIdx.x / TX);")
+    w("  const bool valid = iu0 < p.mx && ju0 < p.my;")
+    w("  const int iu = min(iu0, p.mx - 1), ju = min(ju0, p.my - 1);")
+    w("  const int u = iu + p.mx * ju;")
+    w("  const long long n = p.n;")
+    w("  const float2* __restrict__ xp = X + u;")
+    w("  float2* __restrict__ yp = Y + u;")
+    for a in range(P):
+        w("  const float2 x%d = __ldg(xp + %d * n);" % (a, a))
+    w("  const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
+    w("  const float k0 = __ldg(p.fields + u);")
+    for l in range(s):
+        w("  const float k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
+    w("  const float w2 = g.w2;")
+    for l in range(s):
+        w("  const float cl%d_ = -2.0f * w2 * k0 * k%d;" % (l + 1, l + 1))
+        w("  const float2 cl%d = make_float2(cl%d_, cl%d_);" % (l + 1, l + 1, l + 1))
+        w("  const float cq%d_ = -w2 * k%d * k%d;" % (l + 1, l + 1, l + 1))
+        w("  const float2 cq%d = make_float2(cq%d_, cq%d_);" % (l + 1, l + 1, l + 1))
+    for l in range(s):
+        for lp in range(l + 1, s):
+            w("  const float cp%d_%d_ = -2.0f * w2 * k%d * k%d;" % (l + 1, lp + 1, l + 1, lp + 1))
+            w("  const float2 cp%d_%d = make_float2(cp%d_%d_, cp%d_%d_);" % ((l + 1, lp + 1) * 3))
+    gd0 = _b(1) ** 2
+    base = "g.ldiag - w2 * k0 * k0"
+    for l in range(s):
+        base += " + cq%d_ * %s" % (l + 1, _f(gd0))
+    w("  const float dbase_ = %s;" % base)
+    w("  const float2 dbase = make_float2(dbase_, dbase_);")
+    w("  const bool bnd = g.w1 != 0.0f;")
+    w("  const float2 mwxm = make_float2(-g.wxm, -g.wxm), mwxp = make_float2(-g.wxp, -g.wxp);")
+    w("  const float2 mwym = make_float2(-g.wym, -g.wym), mwyp = make_float2(-g.wyp, -g.wyp);")
+    w("  const float2* xq = X + u;   // plain loads, kept inside their row by the barrier")
+    for a, alpha in enumerate(al):
+        w("  asm volatile(\"\" ::: \"memory\");")
+        w("  {  // row %d, alpha = %s" % (a, alpha))
+        w("    float2 y = __fmul2_rn(dbase, x%d);" % a)
+        for l in range(s):
+            if alpha[l] > 0:
+                gd = _b(alpha[l]) ** 2 + _b(alpha[l] + 1) ** 2
+                w("    y = __ffma2_rn(cq%d, __fmul2_rn(%s, x%d), y);" % (l + 1, f2(gd - gd0), a))
+        k1terms = []
+
+        def group(coef, parts):
+            if not parts:
+                return
+            t = "__fmul2_rn(%s, x%d)" % (f2(parts[0][0]), parts[0][1])
+            for gv, bb in parts[1:]:
+                t = "__ffma2_rn(%s, x%d, %s)" % (f2(gv), bb, t)
+            w("    y = __ffma2_rn(%s, %s, y);" % (coef, t))
+
+        for l in range(s):
+            parts = []
+            for sg in (+1, -1):
+                beta = list(alpha)
+                beta[l] += sg
+                beta = tuple(beta)
+                if beta in idx:
+                    parts.append((_b(max(alpha[l], beta[l])), idx[beta]))
+            k1terms.append((l, parts))
+            group("cl%d" % (l + 1), parts)
+        for l in range(s):
+            parts = []
+            for sg in (+2, -2):
+                beta = list(alpha)
+                beta[l] += sg
+                beta = tuple(beta)
+                if beta in idx:
+                    m = min(alpha[l], beta[l])
+                    parts.append((_b(m + 1) * _b(m + 2), idx[beta]))
+            group("cq%d" % (l + 1), parts)
+        for l in range(s):
+            for lp in range(l + 1, s):
+                parts = []
+                for s1 in (+1, -1):
+                    for s2 in (+1, -1):
+                        beta = list(alpha)
+                        beta[l] += s1
+                        beta[lp] += s2
+                        beta = tuple(beta)
+                        if beta in idx:
+                            parts.append((_b(max(alpha[l], beta[l])) * _b(max(alpha[lp], beta[lp])), idx[beta]))
+                group("cp%d_%d" % (l + 1, lp + 1), parts)
+        w("    {")
+        w("      const float2* q = xq + %d * n;" % a)
+        w("      if (g.hxm) y = __ffma2_rn(mwxm, q[-1], y);")
+        w("      if (g.hxp) y = __ffma2_rn(mwxp, q[1], y);")
+        w("      if (g.hym) y = __ffma2_rn(mwym, q[-p.mx], y);")
+        w("      if (g.hyp) y = __ffma2_rn(mwyp, q[p.mx], y);")
+        w("    }")
+        t = "k0 * x%d.x" % a
+        ti = "k0 * x%d.y" % a
+        for l, parts in k1terms:
+            for gv, bb in parts:
+                t = "fmaf(k%d * %s, x%d.x, %s)" % (l + 1, _f(gv), bb, t)
+                ti = "fmaf(k%d * %s, x%d.y, %s)" % (l + 1, _f(gv), bb, ti)
+        w("    if (bnd) {   // -i w1 <k phi phi>: y += w1 * (i^-1 times K1 x) componentwise")
+        w("      const float tr = %s;" % t)
+        w("      const float ti = %s;" % ti)
+        w("      y.x = fmaf(g.w1, ti, y.x);")
+        w("      y.y = fmaf(-g.w1, tr, y.y);")
+        w("    }")
+        w("    if (valid) yp[%d * n] = y;" % a)
+        w("  }")
+    w("}")
+    return name, P, "\n".join(L)
+
+
 def generate(path: str) -> str:
     parts = ["// GENERATED by paper_2209_14740_gb300/codegen_matvec.py -- do not edit.",
              "#include <cuda_runtime.h>",
@@ -231,25 +562,51 @@ def generate(path: str) -> str:
              "}"]
     table = []
     for s, r in SPECIALISED:
-        name, P, src = gen_kernel(s, r)
+        name, P, src = gen_kernel_tile(s, r) if STENCIL == "tile" else gen_kernel(s, r)
         parts.append(src)
-        table.append((s, r, name))
+        table.append((s, r, name, P))
+    if STENCIL == "tile":
+        parts += [
+            "// Launch of a tiled kernel: 2D problems use 16 x 4 unknowns per CTA,",
+            "// 1D problems 64 x 1; dynamic shared memory holds P rows of",
+            "// (tile + halo) values.",
+            "template <int TX, int TY>",
+            "static cudaError_t launch_tile(void (*kern)(OpParams<float>, const float*, float*), int P,",
+            "                               const sg_handle* h, const OpParams<float>& p, const float2* X, float2* Y,",
+            "                               cudaStream_t st) {",
+            "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
+            "  const size_t smem = (size_t)P * (nt + nh) * sizeof(float);",
+            "  if (smem > 48 * 1024) {",
+            "    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
+            "    if (e != cudaSuccess) return e;",
+            "  }",
+            "  dim3 grid((h->mx + TX - 1) / TX, (h->my + TY - 1) / TY);",
+            "  kern<<<grid, nt, smem, st>>>(p, (const float*)X, (float*)Y);",
+            "  note_launch();",
+            "  return cudaGetLastError();",
+            "}",
+        ]
     parts.append("cudaError_t matvec_special_f32(const sg_handle* h, const float2* X, float2* Y, cudaStream_t st,")
     parts.append("                               const int* skip, bool* handled) {")
     parts.append("  *handled = false;")
     parts.append("  OpParams<float> p = h->op32();")
     parts.append("  p.skip = skip;")
     parts.append("  const int grid = (h->n + %d - 1) / %d;" % (BLOCK // 2, BLOCK // 2))
-    for s, r, name in table:
+    parts.append("  (void)grid;")
+    for s, r, name, P in table:
         parts.append("  if (h->s == %d && h->r == %d) {" % (s, r))
-        parts.append("    %s<<<grid, %d, 0, st>>>(p, (const float*)X, (float*)Y); note_launch();" % (name, BLOCK))
         parts.append("    *handled = true;")
-        parts.append("    return cudaGetLastError();")
+        if STENCIL == "tile":
+            parts.append("    if (h->dim == 2) return launch_tile<16, 4>(%s<16, 4>, %d, h, p, X, Y, st);" % (name, P))
+            parts.append("    return launch_tile<64, 1>(%s<64, 1>, %d, h, p, X, Y, st);" % (name, P))
+        else:
+            parts.append("    %s<<<grid, %d, 0, st>>>(p, (const float*)X, (float*)Y); note_launch();" % (name, BLOCK))
+            parts.append("    return cudaGetLastError();")
         parts.append("  }")
     parts.append("  return cudaSuccess;")
     parts.append("}")
     parts.append("bool matvec_is_specialised(int s, int r) {")
-    for s, r, _ in table:
+    for s, r, _, _ in table:
         parts.append("  if (s == %d && r == %d) return true;" % (s, r))
     parts.append("  return false;")
     parts.append("}")

@@ -148,6 +148,29 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
 sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                      void* stream);
 
+/* Largest N (= n * P complex values) sg_precond_noalloc accepts. */
+#define SG_NOALLOC_MAX_N 524288
+
+/* Allocation-free form of sg_precond (the paper has no counterpart: this is
+ * an interface for callers, not part of the method).  Same result as
+ * sg_precond for SG_PREC_MEAN and SG_PREC_CSL_MEAN, but the intermediate
+ * vectors live in a fixed array inside the library image instead of the
+ * handle's scratch, and the call allocates no device or host memory.  It is
+ * meant for callers that cannot call cudaMalloc while they run (allocation
+ * forbidden or too slow in their context, or device memory owned by another
+ * allocator's pool); the handle itself must still come from sg_assemble.
+ *   - N must be <= SG_NOALLOC_MAX_N, else SG_EINVAL with a message.
+ *   - The array holds 2 * SG_NOALLOC_MAX_N complex128 values (16 MiB) on every
+ *     device that loads the library, until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (several
+ *     streams or host threads) race.  Each call overwrites what it reads, so
+ *     no clearing is needed between calls.
+ * R, Z: device, N complex of precision prec (FP64 or FP32); Z may equal R. */
+sg_status sg_precond_noalloc(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
+                             void* stream);
+
 typedef struct {
   int restart;          /* Krylov basis length per cycle; <= 0 means full GMRES (no restart) */
   int maxit;            /* cap on total Arnoldi steps; <= 0 means N (FP64/FP32) */

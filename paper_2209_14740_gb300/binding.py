@@ -24,7 +24,8 @@ FP64, FP32, MIXED = 0, 1, 2
 
 # every symbol include/sg.h declares
 EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "sg_precond", "sg_gmres",
-            "sg_last_error", "sg_version", "sg_kernel_launches"]
+            "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc"]
+NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
 class SgDesc(C.Structure):
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_version.restype = i
     lib.sg_kernel_launches.argtypes = []
     lib.sg_kernel_launches.restype = C.c_longlong
+    lib.sg_precond_noalloc.argtypes = [vp, i, i, vp, vp, vp]
+    lib.sg_precond_noalloc.restype = i
     _lib = lib
     return lib
 
@@ -163,6 +166,11 @@ class SG:
 
     def precond(self, R, Z, kind=PREC_MEAN, prec=FP64, stream=None):
         _check(load().sg_precond(self.h, kind, prec, _ptr(R), _ptr(Z), _stream(stream)))
+
+    def precond_noalloc(self, R, Z, kind=PREC_MEAN, prec=FP64, stream=None):
+        """sg_precond_noalloc: the same apply with the library's static scratch
+        (no device memory is allocated by the call)."""
+        _check(load().sg_precond_noalloc(self.h, kind, prec, _ptr(R), _ptr(Z), _stream(stream)))
 
     def gmres(self, b, x, *, restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, x0=None, max_outer=0,
               inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False):

@@ -333,6 +333,46 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
   return cgemm<T>(h, P * my, mx, mx, tmp2, Qt, Z, st, skip);        // (3)
 }
 
+// Same preconditioner apply with caller-provided scratch: tmp and tmp2 hold
+// at least N complex values of type T each (tmp2 is used by 2D problems only).
+// Used by the allocation-free entry point.
+template <typename T>
+cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
+                                   C2<T>* tmp, C2<T>* tmp2) {
+  const PrecBlock& blk = h->blk[which];
+  TriFactors<T> F;
+  if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;
+  if (h->dim == 1) {
+    dim3 b(1, 64), g(1, (h->P + 63) / 64);
+    C2<T>* out = (R == Z) ? tmp : Z;
+    k_tri_solve<T><<<g, b, 0, st>>>(1, h->P, h->n, h->n, 1, 0, F, nullptr, R, out, nullptr, nullptr);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && out != Z)
+      e = cudaMemcpyAsync(Z, out, (size_t)h->N * sizeof(C2<T>), cudaMemcpyDeviceToDevice, st);
+    return e;
+  }
+  const int mx = h->mx, my = h->my, P = h->P;
+  const C2<T>* Q;
+  const C2<T>* Qt;
+  const T* dyinv;
+  if constexpr (sizeof(T) == 8) { Q = h->d_Q; Qt = h->d_Qt; dyinv = h->d_dyinv; }
+  else { Q = h->d_Q32; Qt = h->d_Qt32; dyinv = h->d_dyinv32; }
+  cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, Q, tmp, st, nullptr);
+  if (e != cudaSuccess) return e;
+  dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);
+  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, (long long)mx * my, mx, 1, F, dyinv, tmp, tmp2, nullptr, nullptr);
+  note_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cgemm<T>(h, P * my, mx, mx, tmp2, Qt, Z, st, nullptr);
+}
+
+template cudaError_t launch_precond_scratch<double>(const sg_handle*, int, const double2*, double2*, cudaStream_t,
+                                                    double2*, double2*);
+template cudaError_t launch_precond_scratch<float>(const sg_handle*, int, const float2*, float2*, cudaStream_t,
+                                                   float2*, float2*);
+
 template cudaError_t launch_precond<double>(const sg_handle*, int, const double2*, double2*, cudaStream_t,
                                            const int*, const double*);
 template cudaError_t launch_precond<float>(const sg_handle*, int, const float2*, float2*, cudaStream_t, const int*,

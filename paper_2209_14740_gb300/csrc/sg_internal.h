@@ -137,6 +137,10 @@ template <typename T>
 cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                            const int* skip = nullptr, const double* in_scale = nullptr);
 
+template <typename T>
+cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
+                                   C2<T>* tmp, C2<T>* tmp2);
+
 // launch bookkeeping (sg_kernel_launches)
 void note_launch();
 

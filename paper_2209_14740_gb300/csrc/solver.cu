@@ -139,48 +139,75 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 // ------------------------------------------------------------------ kernels
 // d_i = V_i^H w for i < nv (raw vectors); last block writes d and
 // c_i = vscale_i^2 d_i (the update coefficient for the raw basis).
+// Grid: blockIdx.x = element chunk (gridDim.x chunks), blockIdx.y = group of
+// DG vectors; every block reduces its DG dot products once and stores them at
+// part[(group * chunks + chunk) * 2 * DG + k].
+constexpr int DG = 4;
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_dots(const C2<T>* __restrict__ V, long long N, int nv,
-                                                     const C2<T>* __restrict__ w, double* part, int pstride,
+                                                     const C2<T>* __restrict__ w, double* part,
                                                      unsigned* counter, const double* vscale, double* d_out,
                                                      double* c_out, const int* ctl) {
   if (ctl[CTL_DONE]) return;
-  constexpr int G = 8;   // vectors per pass over this block's elements
-  __shared__ double sm[2 * G * 32];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int g0 = 0; g0 < nv; g0 += G) {
-    T acc[2 * G];
+  __shared__ double sm[2 * DG * 32];
+  const int chunks = gridDim.x, grp = blockIdx.y;
+  const long long per = (N + chunks - 1) / chunks;
+  const long long e0 = blockIdx.x * per, e1 = min(N, e0 + per);
+  const int q0 = grp * DG, ng = min(DG, nv - q0);
+  const C2<T>* Vg = V + (size_t)q0 * N;
+  T acc[2 * DG];
 #pragma unroll
-    for (int k = 0; k < 2 * G; ++k) acc[k] = T(0);
-    const int ng = min(G, nv - g0);
-    const C2<T>* Vg = V + (size_t)g0 * N;
-#pragma unroll 2
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-      const C2<T> we = w[e];
+  for (int k = 0; k < 2 * DG; ++k) acc[k] = T(0);
+#pragma unroll 4
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const C2<T> we = w[e];
 #pragma unroll
-      for (int q = 0; q < G; ++q) {
-        if (q < ng) {
-          const C2<T> v = Vg[(size_t)q * N + e];
-          acc[2 * q] += v.x * we.x + v.y * we.y;
-          acc[2 * q + 1] += v.x * we.y - v.y * we.x;
-        }
+    for (int q = 0; q < DG; ++q) {
+      if (q < ng) {
+        const C2<T> v = Vg[(size_t)q * N + e];
+        acc[2 * q] += v.x * we.x + v.y * we.y;
+        acc[2 * q + 1] += v.x * we.y - v.y * we.x;
       }
     }
-    double dv[2 * G];
+  }
+  double dv[2 * DG];
 #pragma unroll
-    for (int k = 0; k < 2 * G; ++k) dv[k] = (double)acc[k];
-    block_sum<2 * G>(dv, sm);
-    if (threadIdx.x == 0)
-      for (int k = 0; k < 2 * ng; ++k) part[(size_t)blockIdx.x * pstride + 2 * g0 + k] = dv[k];
+  for (int k = 0; k < 2 * DG; ++k) dv[k] = (double)acc[k];
+  block_sum<2 * DG>(dv, sm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 2 * DG; ++k) part[((size_t)grp * chunks + blockIdx.x) * 2 * DG + k] = dv[k];
+  // last block of the whole grid: sum the chunks of every value, warps in parallel
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x * gridDim.y - 1);
   }
-  if (last_block(counter)) {
-    sum_block_partials(part, pstride, 2 * nv, [&](int k, double s) {
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < 2 * nv; k += nw) {
+    const int i = k >> 1, g = i / DG, kk = 2 * (i - g * DG) + (k & 1);
+    const double* pk = part + (size_t)g * chunks * 2 * DG + kk;
+    double s0 = 0.0, s1 = 0.0;
+    int c = lane;
+    for (; c + 32 < chunks; c += 64) {
+      s0 += __ldcg(pk + (size_t)c * 2 * DG);
+      s1 += __ldcg(pk + (size_t)(c + 32) * 2 * DG);
+    }
+    if (c < chunks) s0 += __ldcg(pk + (size_t)c * 2 * DG);
+    double s = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
       d_out[k] = s;
-      const double vs = vscale[k >> 1];
+      const double vs = vscale[i];
       c_out[k] = vs * vs * s;
-    });
-    if (threadIdx.x == 0) *counter = 0;
+    }
   }
+  if (threadIdx.x == 0) *counter = 0;
 }
 
 // w -= sum_i c_i V_i ; optionally ||w||^2 (last block writes *norm_out).
@@ -270,11 +297,17 @@ __global__ void k_cycle_init(double* D, int* ctl, DevLayout L, double tol_est, d
   }
 }
 
-// Givens update for column j (one thread).  w = A M^-1 v_j was formed from
-// the normalised v_j, so H[i][j] = v_i^H w = vscale_i (d1_i + d2_i) and
-// H[j+1][j] = ||w||.
+// Givens update for column j, one warp.  w = A M^-1 v_j was formed from the
+// normalised v_j, so H[i][j] = v_i^H w = vscale_i (d1_i + d2_i) and
+// H[j+1][j] = ||w||.  The column and the previous rotations are read and
+// written by all lanes in parallel through shared memory; lane 0 applies the
+// rotations (a sequential recurrence) and forms the new one.
 __global__ void k_givens(double* D, int* ctl, DevLayout L, int j) {
   if (ctl[CTL_DONE]) return;
+  __shared__ double2 col[MAXV + 1];
+  __shared__ double2 snr[MAXV];
+  __shared__ double csr[MAXV];
+  const int lane = threadIdx.x;
   const int m = L.m;
   double2* H = reinterpret_cast<double2*>(D + L.H);     // column-major, ld m+1
   double* cs = D + L.cs;
@@ -283,69 +316,80 @@ __global__ void k_givens(double* D, int* ctl, DevLayout L, int j) {
   double* vs = D + L.vscale;
   const double2* d1 = reinterpret_cast<const double2*>(D + L.d1);
   const double2* d2 = reinterpret_cast<const double2*>(D + L.d2);
-  const double om = 1.0;
-  double2* col = H + (size_t)j * (m + 1);
-  for (int i = 0; i <= j; ++i) {
-    const double f = om * vs[i];
-    col[i] = make_double2(f * (d1[i].x + d2[i].x), f * (d1[i].y + d2[i].y));
+  for (int i = lane; i <= j; i += 32) {
+    const double f = vs[i];
+    const double2 a = d1[i], b = d2[i];
+    col[i] = make_double2(f * (a.x + b.x), f * (a.y + b.y));
+    if (i < j) {
+      csr[i] = cs[i];
+      snr[i] = sn[i];
+    }
   }
-  const double wn = sqrt(D[L.sc + SC_NORMSQ]);
-  const double hn = om * wn;
-  col[j + 1] = make_double2(hn, 0.0);
-  for (int i = 0; i < j; ++i) {
-    const double2 a = col[i], b = col[i + 1];
-    const double c = cs[i];
-    const double2 s = sn[i];
-    // t = c a + s b ; b' = -conj(s) a + c b
-    const double2 t = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-    const double2 bb = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
-    col[i] = t;
-    col[i + 1] = bb;
+  __syncwarp();
+  double aa = 0, ab = 0, hn = 0, wn = 0;
+  if (lane == 0) {
+    wn = sqrt(D[L.sc + SC_NORMSQ]);
+    hn = wn;
+    col[j + 1] = make_double2(hn, 0.0);
+    double2 a = col[0];
+    for (int i = 0; i < j; ++i) {
+      const double2 b = col[i + 1];
+      const double c = csr[i];
+      const double2 s = snr[i];
+      // t = c a + s b ; b' = -conj(s) a + c b
+      col[i] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+      a = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    }
+    // new rotation zeroing the subdiagonal entry
+    const double2 b = col[j + 1];
+    aa = hypot(a.x, a.y);
+    ab = hypot(b.x, b.y);
+    double c;
+    double2 s;
+    if (ab == 0.0) {
+      c = 1.0;
+      s = make_double2(0, 0);
+    } else if (aa == 0.0) {
+      c = 0.0;
+      s = make_double2(b.x / ab, -b.y / ab);
+    } else {
+      const double rr = hypot(aa, ab);
+      c = aa / rr;
+      // s = (a/|a|) conj(b) / rr
+      const double2 u = make_double2(a.x / aa, a.y / aa);
+      s = make_double2((u.x * b.x + u.y * b.y) / rr, (u.y * b.x - u.x * b.y) / rr);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
+    col[j + 1] = make_double2(0, 0);
+    const double2 gj = g[j];
+    const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    g[j + 1] = g1;
+    g[j] = make_double2(c * gj.x, c * gj.y);
+    const double est = hypot(g1.x, g1.y) / D[L.sc + SC_REF];
+    D[L.sc + SC_EST] = est;
+    vs[j + 1] = wn > 0 ? 1.0 / wn : 0.0;
+    ctl[CTL_ITERS] += 1;
+    ctl[CTL_K] = j + 1;
+    const bool bad = !(est == est) || !(hn == hn) || !(col[j].x == col[j].x);
+    if (bad) {
+      ctl[CTL_FLAGS] |= FL_NAN;
+      ctl[CTL_DONE] = 1;
+    } else if (est <= D[L.sc + SC_TOL]) {
+      ctl[CTL_FLAGS] |= FL_CONV;
+      ctl[CTL_DONE] = 1;
+    } else if (hn <= 1e-300 * (aa + ab + 1e-300) || wn == 0.0) {
+      ctl[CTL_FLAGS] |= FL_BREAK;   // (lucky) breakdown: Krylov space invariant
+      ctl[CTL_DONE] = 1;
+    } else if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT] || j + 1 >= m) {
+      if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT]) ctl[CTL_FLAGS] |= FL_MAXIT;
+      ctl[CTL_DONE] = 1;
+    }
   }
-  // new rotation zeroing col[j+1]
-  const double2 a = col[j], b = col[j + 1];
-  const double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
-  double c;
-  double2 s;
-  if (ab == 0.0) {
-    c = 1.0;
-    s = make_double2(0, 0);
-  } else if (aa == 0.0) {
-    c = 0.0;
-    s = make_double2(b.x / ab, -b.y / ab);
-  } else {
-    const double rr = hypot(aa, ab);
-    c = aa / rr;
-    // s = (a/|a|) conj(b) / rr
-    const double2 u = make_double2(a.x / aa, a.y / aa);
-    s = make_double2((u.x * b.x + u.y * b.y) / rr, (u.y * b.x - u.x * b.y) / rr);
-  }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = make_double2(c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x));
-  col[j + 1] = make_double2(0, 0);
-  const double2 gj = g[j];
-  g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-  g[j] = make_double2(c * gj.x, c * gj.y);
-  const double est = hypot(g[j + 1].x, g[j + 1].y) / D[L.sc + SC_REF];
-  D[L.sc + SC_EST] = est;
-  vs[j + 1] = wn > 0 ? 1.0 / wn : 0.0;
-  ctl[CTL_ITERS] += 1;
-  ctl[CTL_K] = j + 1;
-  const bool bad = !(est == est) || !(hn == hn) || !(col[j].x == col[j].x);
-  if (bad) {
-    ctl[CTL_FLAGS] |= FL_NAN;
-    ctl[CTL_DONE] = 1;
-  } else if (est <= D[L.sc + SC_TOL]) {
-    ctl[CTL_FLAGS] |= FL_CONV;
-    ctl[CTL_DONE] = 1;
-  } else if (hn <= 1e-300 * (aa + ab + 1e-300) || wn == 0.0) {
-    ctl[CTL_FLAGS] |= FL_BREAK;   // (lucky) breakdown: Krylov space invariant
-    ctl[CTL_DONE] = 1;
-  } else if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT] || j + 1 >= m) {
-    if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT]) ctl[CTL_FLAGS] |= FL_MAXIT;
-    ctl[CTL_DONE] = 1;
-  }
+  __syncwarp();
+  double2* hcol = H + (size_t)j * (m + 1);
+  for (int i = lane; i <= j + 1; i += 32) hcol[i] = col[i];
 }
 
 // y = R^-1 g (k x k upper triangle of the rotated Hessenberg matrix);
@@ -454,7 +498,11 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   if (!e) e = cudaMalloc(&w.B64, N * sizeof(double2));
   if (!e) e = cudaMalloc((void**)&w.dscal, L.total * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.dctl, 16 * sizeof(int));
-  if (!e) e = cudaMalloc((void**)&w.part, (size_t)w.nblk * 2 * (MAXV + 2) * sizeof(double));
+  // block partials: the reduction kernels use nblk * 2 (MAXV + 2) doubles, k_dots
+  // at most (4 * SMs + MAXV / DG) * 2 * DG
+  const size_t part_doubles = std::max((size_t)w.nblk * 2 * (MAXV + 2),
+                                       ((size_t)4 * h->num_sms + MAXV / DG + 1) * 2 * DG);
+  if (!e) e = cudaMalloc((void**)&w.part, part_doubles * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.counter, sizeof(unsigned));
   if (!e) e = cudaMemset(w.counter, 0, sizeof(unsigned));
   if (e) {
@@ -475,6 +523,17 @@ struct Ctx {
   int grid;
   int pstride;
 };
+
+// k_dots grid: element chunks x groups of DG vectors, about 4 blocks per SM in
+// total, at least 1024 elements per chunk.  Partials: chunks * groups * 2 * DG
+// doubles (fits the workspace, see ensure_work).
+dim3 dots_grid(const Ctx& c, int nv) {
+  const int groups = (nv + DG - 1) / DG;
+  const long long by_size = (c.h->N + 1023) / 1024;
+  const long long by_fill = (4LL * c.h->num_sms + groups - 1) / groups;
+  const int chunks = (int)std::max(1LL, std::min(by_size, by_fill));
+  return dim3(chunks, groups);
+}
 
 // Z = M^-1 (s R) with s = *in_scale (1 if null).
 template <typename T>
@@ -508,15 +567,16 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
   if ((e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
   const int nv = j + 1;
-  k_dots<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, c.pstride, w.counter, D + c.L.vscale,
-                                              D + c.L.d1, D + c.L.c1, w.dctl); note_launch();
+  const dim3 dg = dots_grid(c, nv);
+  k_dots<T><<<dg, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale, D + c.L.d1,
+                                          D + c.L.c1, w.dctl); note_launch();
   k_update<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, c.pstride, w.counter, nullptr,
                                                 w.dctl); note_launch();
-  k_dots<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, c.pstride, w.counter, D + c.L.vscale,
-                                              D + c.L.d2, D + c.L.c2, w.dctl); note_launch();
+  k_dots<T><<<dg, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale, D + c.L.d2,
+                                          D + c.L.c2, w.dctl); note_launch();
   k_update<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c2, w.part, c.pstride, w.counter,
                                                 D + c.L.sc + SC_NORMSQ, w.dctl); note_launch();
-  k_givens<<<1, 1, 0, c.st>>>(D, w.dctl, c.L, j); note_launch();
+  k_givens<<<1, 32, 0, c.st>>>(D, w.dctl, c.L, j); note_launch();
   return cudaGetLastError();
 }
 

@@ -203,6 +203,21 @@ typedef struct {
 sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void* x,
                    sg_gmres_info* info, void* stream);
 
+/* Solves `count` independent SG systems (different grids, chaos sizes and
+ * wavenumbers allowed) with the same options, concurrently: each system runs
+ * the sg_gmres algorithm on its own internal CUDA stream, and up to
+ * `concurrency` systems (<= 0 means min(count, 16)) are in flight at once,
+ * driven by a pool of host threads.  Workspaces are allocated for all handles
+ * before any solve starts.  The solves wait for work already queued on
+ * `stream` and are complete when the call returns.  h[k], b[k], x[k] as in
+ * sg_gmres (opts->host_io is honoured per system); infos (may be NULL) gets
+ * one record per system.  Returns SG_OK if every system converged,
+ * SG_ENOTCONV if some did not, otherwise the first error met.  The handles
+ * must be distinct.  (The paper solves one system at a time; batching is
+ * this library's throughput mode.) */
+sg_status sg_gmres_batched(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b,
+                           void* const* x, sg_gmres_info* infos, int concurrency, void* stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* sg_last_error(void);
 

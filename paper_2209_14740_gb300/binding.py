@@ -24,7 +24,7 @@ FP64, FP32, MIXED = 0, 1, 2
 
 # every symbol include/sg.h declares
 EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "sg_precond", "sg_gmres",
-            "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc"]
+            "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -92,6 +92,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_kernel_launches.restype = C.c_longlong
     lib.sg_precond_noalloc.argtypes = [vp, i, i, vp, vp, vp]
     lib.sg_precond_noalloc.restype = i
+    lib.sg_gmres_batched.argtypes = [C.POINTER(vp), i, C.POINTER(SgGmresOpts), C.POINTER(vp), C.POINTER(vp),
+                                     C.POINTER(SgGmresInfo), i, vp]
+    lib.sg_gmres_batched.restype = i
     _lib = lib
     return lib
 
@@ -186,3 +189,31 @@ class SG:
         if st not in (SG_OK, SG_ENOTCONV) or (raise_on_notconv and st == SG_ENOTCONV):
             _check(st)
         return dict(iters=inf.iters, outer=inf.outer, cycles=inf.cycles, relres=inf.relres, status=st)
+
+
+def _opts(restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, max_outer=0, inner_tol=0.0, host_io=False,
+          check_every=0):
+    o = SgGmresOpts()
+    o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
+    o.prec, o.mode = prec, mode
+    o.x0 = None
+    o.host_io = 1 if host_io else 0
+    o.check_every = check_every
+    return o
+
+
+def gmres_batched(ops, bs, xs, *, concurrency=0, stream=None, **kw):
+    """sg_gmres_batched over SG objects `ops` with right-hand sides `bs` and
+    solutions `xs` (torch tensors or numpy arrays with host_io=True)."""
+    n = len(ops)
+    hs = (C.c_void_p * n)(*[op.h.value for op in ops])
+    bp = (C.c_void_p * n)(*[_ptr(v) for v in bs])
+    xp = (C.c_void_p * n)(*[_ptr(v) for v in xs])
+    infos = (SgGmresInfo * n)()
+    o = _opts(**kw)
+    st = load().sg_gmres_batched(hs, n, C.byref(o), bp, xp, infos, concurrency,
+                                 None if kw.get("host_io") and stream is None else _stream(stream))
+    if st not in (SG_OK, SG_ENOTCONV):
+        _check(st)
+    return st, [dict(iters=f.iters, outer=f.outer, cycles=f.cycles, relres=f.relres, status=f.status)
+                for f in infos]

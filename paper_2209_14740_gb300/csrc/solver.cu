@@ -634,6 +634,17 @@ sg_status residual_norm(Ctx& c, const C2<TX>* b, const C2<TX>* x, bool x_zero, C
 
 }  // namespace
 
+// Allocates the GMRES workspace sg_gmres will need for these options (used by
+// the batched solver so that no allocation happens while solves run).
+sg_status sgi_prepare_workspace(sg_handle* h, const sg_gmres_opts* opts) {
+  if (!h || !opts) return fail(SG_EINVAL, "NULL argument");
+  int m = opts->restart <= 0 ? (int)std::min<long long>(h->N, MAXV - 1) : opts->restart;
+  if (m > MAXV - 1) return fail(SG_EINVAL, "restart must be <= 511");
+  m = (int)std::min<long long>(m, h->N);
+  const bool inner32 = opts->mode == SG_MIXED || opts->mode == SG_FP32;
+  return ensure_work(h, m, inner32 ? 8 : 16);
+}
+
 extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void* x,
                               sg_gmres_info* info, void* stream) {
   if (!h || !opts || !b || !x) return fail(SG_EINVAL, "NULL argument to sg_gmres");

@@ -174,6 +174,85 @@ def run_reference(args):
     return 0
 
 
+def learned_leg(args, B, torch, dev):
+    """Warm-start workload: (kbar, sigma, lc, x_s, y_s) uniform in [10,40] x
+    [0.05,0.2] x [0.1,0.5] x [0.2,0.8]^2 on 127x127, s=3, degree 3 (N=322,580).
+    Trains on `--learned-train` solved problems, then solves `--learned-test`
+    held-out problems: mixed + learned guess + batched against plain FP64 one
+    at a time."""
+    import numpy as np
+
+    from paper_2209_14740_gb300 import inputs, warmstart
+
+    ptrain = inputs.warmstart_params(1, args.learned_train)
+    ptest = inputs.warmstart_params(2, args.learned_test)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S, its_train = warmstart.solve_batch(ptrain, torch, dev, tol=1e-10)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ws = warmstart.build(ptrain, S, torch, dev, rank=64, n_snapshots=min(1024, len(ptrain)), epochs=300, batch=64)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del S
+    ops = [B.SG(inputs.warmstart_problem(p)) for p in ptest]
+    bs = []
+    for op in ops:
+        bb = torch.empty(op.N, dtype=torch.complex128, device=dev)
+        op.rhs(bb, B.FP64)
+        bs.append(bb)
+    xs = [torch.zeros_like(bb) for bb in bs]
+    kw = dict(restart=50, tol=1e-8, prec=B.PREC_MEAN, maxit=20000)
+
+    def zero_batched():
+        return B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)
+
+    def learned_batched():
+        x0 = ws.predict(ptest, torch, dev)
+        return B.gmres_batched(ops, bs, xs, x0s=[x0[k] for k in range(len(ops))], x0_policy=B.X0_SCALED, mode=B.MIXED,
+                               **kw), x0
+
+    zero_batched()                                                 # workspaces
+    learned_batched()                                              # first use of the inference kernels
+    timings = {}
+    for name, fn in (("zero", zero_batched), ("learned", learned_batched)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        timings[name] = (time.perf_counter() - t1, out)
+    (st_z, inf_z) = timings["zero"][1]
+    (st_l, inf_l), x0 = timings["learned"][1]
+    rel = [float(torch.linalg.norm(x0[k] - xs[k]) / torch.linalg.norm(xs[k])) for k in range(len(ops))]
+    del x0
+    for op, bb in zip(ops, bs):                                    # FP64 workspaces (one iteration each)
+        op.gmres(bb, torch.zeros_like(bb), mode=B.FP64, restart=50, tol=1e-8, prec=B.PREC_MEAN, maxit=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    inf_s = [op.gmres(bb, torch.zeros_like(bb), mode=B.FP64, **kw) for op, bb in zip(ops, bs)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t1
+    for op in ops:
+        op.close()
+    n = len(ops)
+    return {"workload": "warm-start family: kbar~U[10,40], sigma~U[0.05,0.2], lc~U[0.1,0.5], source~U[0.2,0.8]^2; "
+                        "127x127, s=3, degree 3 (N=322,580); GMRES(50), mean-value, tol 1e-8",
+            "train_problems": len(ptrain), "test_problems": n,
+            "train_data_s": t_data, "train_iterations_mean": float(np.mean(its_train)),
+            "fit_s": t_train, "fit_breakdown_s": ws.timings, "pod_rank": ws.rank, "pod_energy": ws.energy_captured,
+            "loss_first_last": [ws.loss_history[0], ws.loss_history[-1]],
+            "guess_relerr_median": float(np.median(rel)),
+            "iterations_mean_zero": float(np.mean([i["iters"] for i in inf_z])),
+            "iterations_mean_learned": float(np.mean([i["iters"] for i in inf_l])),
+            "mixed_batched_zero_solves_per_s": n / timings["zero"][0],
+            "mixed_batched_learned_solves_per_s": n / timings["learned"][0],
+            "fp64_sequential_solves_per_s": n / t_seq,
+            "speedup_vs_fp64_sequential": t_seq / timings["learned"][0],
+            "all_converged": bool(st_z == B.SG_OK and st_l == B.SG_OK and all(i["status"] == B.SG_OK for i in inf_s)
+                                  and all(i["relres"] <= 1e-8 for i in inf_l))}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -342,6 +421,11 @@ def run_ours(args):
             op.close()
         del bs, xs
 
+    # ---------------------------------------------------------------- learned initial guess + batched + mixed
+    learned = None
+    if rank == 0 and not args.skip_learned:
+        learned = learned_leg(args, B, torch, dev)
+
     if rank != 0:
         return 0
     line = {
@@ -359,6 +443,8 @@ def run_ours(args):
     }
     if batched:
         line["batched"] = batched
+    if learned:
+        line["learned"] = learned
     if mv:
         line["matvec"] = mv
         line["roofline"] = {"kernel": "k_matvec (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
@@ -383,6 +469,9 @@ def main():
     ap.add_argument("--skip-matvec", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-learned", action="store_true")
+    ap.add_argument("--learned-train", type=int, default=4096, help="training solves of the warm-start network")
+    ap.add_argument("--learned-test", type=int, default=256, help="held-out solves of the warm-start leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

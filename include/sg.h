@@ -171,6 +171,18 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
 sg_status sg_precond_noalloc(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                              void* stream);
 
+/* Use of a supplied initial guess (not in the paper, which starts from zero).
+ *   SG_X0_AS_GIVEN:  start from x0.
+ *   SG_X0_FALLBACK:  start from x0 unless ||b - A x0|| > ||b|| (or is not
+ *                    finite); then start from zero.
+ *   SG_X0_SCALED:    start from zeta x0 with zeta = (A x0)^H b / ||A x0||^2,
+ *                    the multiple of x0 with the smallest residual (the
+ *                    initial-guess scaling of Hegedus), so the starting
+ *                    residual never exceeds ||b|| up to rounding; falls back
+ *                    to zero like SG_X0_FALLBACK if it does.  Costs one extra
+ *                    operator application and one reduction. */
+typedef enum { SG_X0_AS_GIVEN = 0, SG_X0_FALLBACK = 1, SG_X0_SCALED = 2 } sg_x0_policy;
+
 typedef struct {
   int restart;          /* Krylov basis length per cycle; <= 0 means full GMRES (no restart) */
   int maxit;            /* cap on total Arnoldi steps; <= 0 means N (FP64/FP32) */
@@ -182,6 +194,7 @@ typedef struct {
   const void* x0;       /* initial guess (same memory space and precision as x); NULL = zero */
   int host_io;          /* 1: b, x0, x are HOST buffers (copied in and out inside the call) */
   int check_every;      /* steps between host reads of the convergence flag; <= 0 means 8 */
+  int x0_policy;        /* sg_x0_policy: how a supplied x0 is used (0 = as given) */
 } sg_gmres_opts;
 
 typedef struct {
@@ -210,13 +223,58 @@ sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void*
  * driven by a pool of host threads.  Workspaces are allocated for all handles
  * before any solve starts.  The solves wait for work already queued on
  * `stream` and are complete when the call returns.  h[k], b[k], x[k] as in
- * sg_gmres (opts->host_io is honoured per system); infos (may be NULL) gets
- * one record per system.  Returns SG_OK if every system converged,
- * SG_ENOTCONV if some did not, otherwise the first error met.  The handles
- * must be distinct.  (The paper solves one system at a time; batching is
- * this library's throughput mode.) */
+ * sg_gmres (opts->host_io is honoured per system); x0 (may be NULL): per
+ * system initial guesses overriding opts->x0 (entries may be NULL = zero).
+ * infos (may be NULL) gets one record per system.  Returns SG_OK if every
+ * system converged, SG_ENOTCONV if some did not, otherwise the first error
+ * met.  The handles must be distinct.  (The paper solves one system at a
+ * time; batching is this library's throughput mode.) */
 sg_status sg_gmres_batched(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b,
-                           void* const* x, sg_gmres_info* infos, int concurrency, void* stream);
+                           void* const* x, const void* const* x0, sg_gmres_info* infos, int concurrency,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial guess (not in the paper: a throughput aid whose result is
+ * always finished by sg_gmres to the same tolerance; the zero guess remains
+ * the fallback).  A multilayer perceptron maps workload parameters to the
+ * coefficients c of a rank-R basis U (rows U_i of N complex64 values, from a
+ * POD of training solutions), and the guess is x0 = sum_i c_i U_i.
+ * ------------------------------------------------------------------------- */
+typedef struct sg_mlp sg_mlp;
+
+/* in_dim -> width (tanh) x hidden -> out_dim (linear).  Parameters start at
+ * zero; set them with sg_mlp_set_params.  Flat FP32 parameter layout:
+ * for each layer l: W_l (d_{l+1} x d_l, row-major) then b_l (d_{l+1}). */
+sg_status sg_mlp_create(int in_dim, int width, int hidden, int out_dim, sg_mlp** out);
+void sg_mlp_destroy(sg_mlp* m);
+long long sg_mlp_num_params(const sg_mlp* m);
+/* src/dst: device, num_params FP32 values.  set also resets the Adam state. */
+sg_status sg_mlp_set_params(sg_mlp* m, const float* src, void* stream);
+sg_status sg_mlp_get_params(const sg_mlp* m, float* dst, void* stream);
+/* Y = net(X); X: device batch x in_dim FP32, Y: device batch x out_dim FP32.
+ * Products read bf16 copies of the weights and accumulate in FP32. */
+sg_status sg_mlp_forward(sg_mlp* m, const float* X, int batch, float* Y, void* stream);
+/* Mean squared error against T (batch x out_dim) and its gradient with
+ * respect to every parameter (grad: device, num_params FP32; may be NULL).
+ * *loss (host, may be NULL) is written after the call synchronises. */
+sg_status sg_mlp_loss_grad(sg_mlp* m, const float* X, const float* T, int batch, double* loss, float* grad,
+                           void* stream);
+/* `epochs` passes over the nsamples rows of X, T (device) in mini-batches of
+ * `batch` rows taken in order, one Adam step (lr; beta 0.9 / 0.999; eps
+ * 1e-8) per mini-batch.  loss_history (host, epochs entries, may be NULL):
+ * mean loss per epoch. */
+sg_status sg_mlp_train(sg_mlp* m, const float* X, const float* T, int nsamples, int batch, int epochs, float lr,
+                       double* loss_history, void* stream);
+
+/* C[i][j] = sum_t conj(A[i][t]) B[j][t] for complex64 rows A_i (m rows,
+ * stride lda) and B_j (n rows, stride ldb) of length k; C: m x n complex64
+ * row-major.  workspace: device, m * n complex128 (FP64 accumulation of the
+ * split long dimension).  Gram matrices and projections onto a basis. */
+sg_status sg_cgemm_hn(const void* A, long long lda, const void* B, long long ldb, int m, int n, long long k, void* C,
+                      void* workspace, void* stream);
+/* C = A B for row-major complex64 A (m x k), B (k x n); C row-major m x n,
+ * complex128 if out_c128 else complex64.  Expansion x = c U of a basis. */
+sg_status sg_cgemm_nn(const void* A, const void* B, int m, int n, int k, void* C, int out_c128, void* stream);
 
 /* Message of the last failing call on this host thread ("" if none). */
 const char* sg_last_error(void);

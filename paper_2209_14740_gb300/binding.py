@@ -21,10 +21,13 @@ STATUS_NAMES = ["SG_OK", "SG_EINVAL", "SG_ENOMEM", "SG_ECUDA", "SG_ENOTCONV", "S
 BC_DIRICHLET, BC_ABSORBING = 0, 1
 PREC_NONE, PREC_MEAN, PREC_CSL_MEAN = 0, 1, 2
 FP64, FP32, MIXED = 0, 1, 2
+X0_AS_GIVEN, X0_FALLBACK, X0_SCALED = 0, 1, 2
 
 # every symbol include/sg.h declares
 EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "sg_precond", "sg_gmres",
-            "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched"]
+            "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched",
+            "sg_mlp_create", "sg_mlp_destroy", "sg_mlp_num_params", "sg_mlp_set_params", "sg_mlp_get_params",
+            "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -44,7 +47,7 @@ class SgInfo(C.Structure):
 class SgGmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("max_outer", C.c_int), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("prec", C.c_int), ("mode", C.c_int), ("x0", C.c_void_p),
-                ("host_io", C.c_int), ("check_every", C.c_int)]
+                ("host_io", C.c_int), ("check_every", C.c_int), ("x0_policy", C.c_int)]
 
 
 class SgGmresInfo(C.Structure):
@@ -93,14 +96,87 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_precond_noalloc.argtypes = [vp, i, i, vp, vp, vp]
     lib.sg_precond_noalloc.restype = i
     lib.sg_gmres_batched.argtypes = [C.POINTER(vp), i, C.POINTER(SgGmresOpts), C.POINTER(vp), C.POINTER(vp),
-                                     C.POINTER(SgGmresInfo), i, vp]
+                                     C.POINTER(vp), C.POINTER(SgGmresInfo), i, vp]
     lib.sg_gmres_batched.restype = i
+    fp, dp = C.POINTER(C.c_float), C.POINTER(C.c_double)
+    lib.sg_mlp_create.argtypes = [i, i, i, i, C.POINTER(vp)]
+    lib.sg_mlp_create.restype = i
+    lib.sg_mlp_destroy.argtypes = [vp]
+    lib.sg_mlp_destroy.restype = None
+    lib.sg_mlp_num_params.argtypes = [vp]
+    lib.sg_mlp_num_params.restype = C.c_longlong
+    lib.sg_mlp_set_params.argtypes = [vp, vp, vp]
+    lib.sg_mlp_set_params.restype = i
+    lib.sg_mlp_get_params.argtypes = [vp, vp, vp]
+    lib.sg_mlp_get_params.restype = i
+    lib.sg_mlp_forward.argtypes = [vp, vp, i, vp, vp]
+    lib.sg_mlp_forward.restype = i
+    lib.sg_mlp_loss_grad.argtypes = [vp, vp, vp, i, dp, vp, vp]
+    lib.sg_mlp_loss_grad.restype = i
+    lib.sg_mlp_train.argtypes = [vp, vp, vp, i, i, i, C.c_float, dp, vp]
+    lib.sg_mlp_train.restype = i
+    lib.sg_cgemm_hn.argtypes = [vp, C.c_longlong, vp, C.c_longlong, i, i, C.c_longlong, vp, vp, vp]
+    lib.sg_cgemm_hn.restype = i
+    lib.sg_cgemm_nn.argtypes = [vp, vp, i, i, i, vp, i, vp]
+    lib.sg_cgemm_nn.restype = i
+    del fp
     _lib = lib
     return lib
 
 
 def kernel_launches() -> int:
     return int(load().sg_kernel_launches())
+
+
+class MLP:
+    """sg_mlp: the warm-start network (device parameters, native kernels)."""
+
+    def __init__(self, in_dim, width, hidden, out_dim):
+        h = C.c_void_p()
+        _check(load().sg_mlp_create(in_dim, width, hidden, out_dim, C.byref(h)))
+        self.h = h
+        self.nparams = int(load().sg_mlp_num_params(h))
+        self.in_dim, self.out_dim = in_dim, out_dim
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p, stream=None):
+        _check(load().sg_mlp_set_params(self.h, _ptr(p), _stream(stream)))
+
+    def get_params(self, p, stream=None):
+        _check(load().sg_mlp_get_params(self.h, _ptr(p), _stream(stream)))
+
+    def forward(self, X, Y, stream=None):
+        _check(load().sg_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), _stream(stream)))
+
+    def loss_grad(self, X, T, grad=None, stream=None):
+        loss = C.c_double()
+        _check(load().sg_mlp_loss_grad(self.h, _ptr(X), _ptr(T), X.shape[0], C.byref(loss),
+                                       _ptr(grad) if grad is not None else None, _stream(stream)))
+        return loss.value
+
+    def train(self, X, T, batch, epochs, lr, stream=None):
+        hist = (C.c_double * max(epochs, 1))()
+        _check(load().sg_mlp_train(self.h, _ptr(X), _ptr(T), X.shape[0], batch, epochs, C.c_float(lr), hist,
+                                   _stream(stream)))
+        return list(hist)[:epochs]
+
+
+def cgemm_hn(A, lda, B, ldb, m, n, k, Cout, work, stream=None):
+    _check(load().sg_cgemm_hn(_ptr(A), lda, _ptr(B), ldb, m, n, k, _ptr(Cout), _ptr(work), _stream(stream)))
+
+
+def cgemm_nn(A, B, m, n, k, Cout, out_c128=False, stream=None):
+    _check(load().sg_cgemm_nn(_ptr(A), _ptr(B), m, n, k, _ptr(Cout), 1 if out_c128 else 0, _stream(stream)))
 
 
 def _check(st):
@@ -176,8 +252,10 @@ class SG:
         _check(load().sg_precond_noalloc(self.h, kind, prec, _ptr(R), _ptr(Z), _stream(stream)))
 
     def gmres(self, b, x, *, restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, x0=None, max_outer=0,
-              inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False):
+              inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False,
+              x0_policy=0):
         o = SgGmresOpts()
+        o.x0_policy = x0_policy
         o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
         o.prec, o.mode = prec, mode
         o.x0 = _ptr(x0) if x0 is not None else None
@@ -192,26 +270,29 @@ class SG:
 
 
 def _opts(restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, max_outer=0, inner_tol=0.0, host_io=False,
-          check_every=0):
+          check_every=0, x0_policy=0):
     o = SgGmresOpts()
     o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
     o.prec, o.mode = prec, mode
     o.x0 = None
     o.host_io = 1 if host_io else 0
     o.check_every = check_every
+    o.x0_policy = x0_policy
     return o
 
 
-def gmres_batched(ops, bs, xs, *, concurrency=0, stream=None, **kw):
-    """sg_gmres_batched over SG objects `ops` with right-hand sides `bs` and
-    solutions `xs` (torch tensors or numpy arrays with host_io=True)."""
+def gmres_batched(ops, bs, xs, *, x0s=None, concurrency=0, stream=None, **kw):
+    """sg_gmres_batched over SG objects `ops` with right-hand sides `bs`,
+    solutions `xs` (torch tensors, or numpy arrays with host_io=True) and
+    optional per-system initial guesses `x0s`."""
     n = len(ops)
     hs = (C.c_void_p * n)(*[op.h.value for op in ops])
     bp = (C.c_void_p * n)(*[_ptr(v) for v in bs])
     xp = (C.c_void_p * n)(*[_ptr(v) for v in xs])
+    x0p = (C.c_void_p * n)(*[_ptr(v) if v is not None else None for v in x0s]) if x0s is not None else None
     infos = (SgGmresInfo * n)()
     o = _opts(**kw)
-    st = load().sg_gmres_batched(hs, n, C.byref(o), bp, xp, infos, concurrency,
+    st = load().sg_gmres_batched(hs, n, C.byref(o), bp, xp, x0p, infos, concurrency,
                                  None if kw.get("host_io") and stream is None else _stream(stream))
     if st not in (SG_OK, SG_ENOTCONV):
         _check(st)

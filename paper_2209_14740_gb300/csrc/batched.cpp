@@ -19,8 +19,8 @@
 sg_status sgi_prepare_workspace(sg_handle* h, const sg_gmres_opts* opts);   // solver.cu
 
 extern "C" sg_status sg_gmres_batched(sg_handle* const* h, int count, const sg_gmres_opts* opts,
-                                      const void* const* b, void* const* x, sg_gmres_info* infos,
-                                      int concurrency, void* stream) {
+                                      const void* const* b, void* const* x, const void* const* x0,
+                                      sg_gmres_info* infos, int concurrency, void* stream) {
   if (count < 0 || (count > 0 && (!h || !b || !x)) || !opts) return sgi::fail(SG_EINVAL, "bad batch arguments");
   if (count == 0) return SG_OK;
   for (int k = 0; k < count; ++k) {
@@ -59,7 +59,9 @@ extern "C" sg_status sg_gmres_batched(sg_handle* const* h, int count, const sg_g
     for (;;) {
       const int k = next.fetch_add(1);
       if (k >= count) break;
-      status[k] = sg_gmres(h[k], opts, b[k], x[k], &inf[k], streams[t]);
+      sg_gmres_opts ok = *opts;
+      if (x0) ok.x0 = x0[k];
+      status[k] = sg_gmres(h[k], &ok, b[k], x[k], &inf[k], streams[t]);
       if (status[k] != SG_OK) errs[k] = sg_last_error();
     }
   };

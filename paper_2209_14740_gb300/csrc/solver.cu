@@ -61,7 +61,7 @@ struct DevLayout {
   }
 };
 // sc[] slots
-enum { SC_NORMSQ = 0, SC_BNORM = 1, SC_RNORM2 = 2, SC_EST = 3, SC_TOL = 4, SC_REF = 5, SC_WORK = 6 };
+enum { SC_NORMSQ = 0, SC_BNORM = 1, SC_RNORM2 = 2, SC_EST = 3, SC_TOL = 4, SC_REF = 5, SC_WORK = 6, SC_ZETA = 8 };
 // ctl[] slots
 enum { CTL_DONE = 0, CTL_ITERS = 1, CTL_K = 2, CTL_FLAGS = 3, CTL_MAXIT = 4 };
 enum { FL_CONV = 1, FL_BREAK = 2, FL_NAN = 4, FL_MAXIT = 8 };
@@ -465,6 +465,51 @@ __global__ void k_scale_copy(const C2<T>* __restrict__ v, C2<T>* __restrict__ z,
     z[e] = mkc<T>(v[e].x * f, v[e].y * f);
 }
 
+// zeta = (Ax)^H b / ||Ax||^2 (zero when Ax = 0): the multiple of the initial
+// guess with the smallest residual.  Partial sums in FP64, last block writes
+// zeta (complex, two doubles).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_x0_zeta(const C2<T>* __restrict__ b, const C2<T>* __restrict__ Ax,
+                                                        long long N, double* part, int pstride, unsigned* counter,
+                                                        double* zeta) {
+  __shared__ double sm[3 * 32];
+  __shared__ double tot[3];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    const C2<T> a = Ax[e], v = b[e];
+    acc[0] += (double)a.x * v.x + (double)a.y * v.y;
+    acc[1] += (double)a.x * v.y - (double)a.y * v.x;
+    acc[2] += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  block_sum<3>(acc, sm);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) part[(size_t)blockIdx.x * pstride + k] = acc[k];
+  if (last_block(counter)) {
+    sum_block_partials(part, pstride, 3, [&](int k, double v) { tot[k] = v; });
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const bool ok = tot[2] > 0.0;
+      zeta[0] = ok ? tot[0] / tot[2] : 0.0;
+      zeta[1] = ok ? tot[1] / tot[2] : 0.0;
+      *counter = 0;
+    }
+  }
+}
+
+// x *= zeta and Ax *= zeta (complex zeta read on the device).
+template <typename T>
+__global__ void k_cscale2(C2<T>* __restrict__ x, C2<T>* __restrict__ Ax, long long N,
+                          const double* __restrict__ zeta) {
+  const double zr = zeta[0], zi = zeta[1];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+    const C2<T> v = x[e], a = Ax[e];
+    x[e] = mkc<T>((T)(zr * v.x - zi * v.y), (T)(zr * v.y + zi * v.x));
+    Ax[e] = mkc<T>((T)(zr * a.x - zi * a.y), (T)(zr * a.y + zi * a.x));
+  }
+}
+
 template <typename TA, typename TB>
 __global__ void k_convert(const C2<TA>* __restrict__ a, C2<TB>* __restrict__ b, long long N) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -609,13 +654,30 @@ sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int
   return SG_OK;
 }
 
+// x <- zeta x with zeta the minimal-residual multiple of x (SG_X0_SCALED);
+// Ax (N outer-precision values) is left holding A (zeta x) for the first
+// residual.
+template <typename TX>
+sg_status scale_guess(Ctx& c, const C2<TX>* b, C2<TX>* x, C2<TX>* Ax) {
+  GmresWork& w = c.h->gw;
+  SG_CUDA_TRY(launch_matvec<TX>(c.h, x, Ax, c.st));
+  double* zeta = w.dscal + c.L.sc + SC_ZETA;
+  k_x0_zeta<TX><<<c.grid, RED_THREADS, 0, c.st>>>(b, Ax, c.h->N, w.part, c.pstride, w.counter, zeta);
+  note_launch();
+  SG_CUDA_TRY(cudaGetLastError());
+  k_cscale2<TX><<<c.grid, RED_THREADS, 0, c.st>>>(x, Ax, c.h->N, zeta);
+  note_launch();
+  SG_CUDA_TRY(cudaGetLastError());
+  return SG_OK;
+}
+
 template <typename TX>
 sg_status residual_norm(Ctx& c, const C2<TX>* b, const C2<TX>* x, bool x_zero, C2<TX>* Ax, void* rout_inner,
-                        bool inner_f32, double* rnorm2_host) {
+                        bool inner_f32, double* rnorm2_host, bool ax_ready = false) {
   GmresWork& w = c.h->gw;
   const C2<TX>* axp = nullptr;
   if (!x_zero) {
-    SG_CUDA_TRY(launch_matvec<TX>(c.h, x, Ax, c.st));
+    if (!ax_ready) SG_CUDA_TRY(launch_matvec<TX>(c.h, x, Ax, c.st));
     axp = Ax;
   }
   double* out = w.dscal + c.L.sc + SC_RNORM2;
@@ -653,6 +715,7 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
   if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN)
     return fail(SG_EINVAL, "bad preconditioner");
   if (!(opts->tol > 0) || !std::isfinite(opts->tol)) return fail(SG_EINVAL, "tol must be positive");
+  if (opts->x0_policy < SG_X0_AS_GIVEN || opts->x0_policy > SG_X0_SCALED) return fail(SG_EINVAL, "bad x0_policy");
   if (opts->prec != SG_PREC_NONE && !h->blk[opts->prec == SG_PREC_MEAN ? 0 : 1].ready)
     return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (2D needs a constant k_0)");
   const long long N = h->N;
@@ -727,16 +790,31 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
   int iters = 0, cycles = 0, outer = 0;
   double relres = 1.0;
   int ctl[16];
+  bool ax_ready = false;   // A x already in the residual scratch (scaled guess)
+  if (!x_zero && opts->x0_policy == SG_X0_SCALED) {
+    sg_status s = f32 ? scale_guess<float>(c, (const float2*)bd, (float2*)xd, (float2*)w.Z)
+                      : scale_guess<double>(c, (const double2*)bd, (double2*)xd, (double2*)w.R64);
+    if (s != SG_OK) return s;
+    ax_ready = true;
+  }
   for (;;) {
     double rn2 = 0;
     sg_status s;
     if (f32)
-      s = residual_norm<float>(c, (const float2*)bd, (const float2*)xd, x_zero, (float2*)w.Z, w.V, true, &rn2);
+      s = residual_norm<float>(c, (const float2*)bd, (const float2*)xd, x_zero, (float2*)w.Z, w.V, true, &rn2,
+                               ax_ready);
     else
       s = residual_norm<double>(c, (const double2*)bd, (const double2*)xd, x_zero, (double2*)w.R64, w.V, inner32,
-                                &rn2);
+                                &rn2, ax_ready);
+    ax_ready = false;
     if (s != SG_OK) return s;
     relres = std::sqrt(rn2) / bnorm;
+    if (cycles == 0 && !x_zero && opts->x0_policy != SG_X0_AS_GIVEN && !(relres <= 1.0)) {
+      // the supplied guess is worse than zero: start from zero instead
+      SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
+      x_zero = true;
+      continue;
+    }
     if (!std::isfinite(relres)) { status = SG_EBREAKDOWN; break; }
     if (relres <= opts->tol) { status = SG_OK; break; }
     if (iters >= maxit) { status = SG_ENOTCONV; break; }

@@ -13,6 +13,11 @@
 //           (tridiagonal along y, LU with partial pivoting in FP64),
 //       (3) Z = (d_y^-1/2 z) Qhat^T (second GEMM).
 //     The CSL block adds -i beta k_0^2 D_2, i.e. shift = -i beta k_0^2.
+//     FP32 applies on grids with lines of at most 320 unknowns diagonalise
+//     the y direction too (G_y = Q_y Lambda_y Q_y^T; the fast diagonalisation
+//     of Lynch, Rice and Thomas, 1964): four GEMMs and an elementwise
+//     division by lambda_y,j + lambda_x,i + shift, which keeps every step
+//     parallel instead of mx * P sequential sweeps of length my.
 #include <cuda_runtime.h>
 
 #include "sg_internal.h"
@@ -211,51 +216,80 @@ __global__ void k_tri_solve(int nsys, int nrhs, int len, long long sR, long long
   }
 }
 
-// C[M][Nn] = A[M][K] * B[K][Nn], complex, row-major, CUDA cores.
-// (16*TM) x (16*TN) output tile per CTA, 256 threads, TM x TN outputs per
-// thread; the launcher picks the tile so that the grid fills the GPU.
-template <typename T, int TM, int TN>
-__global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>* __restrict__ A,
-                                              const C2<T>* __restrict__ B, C2<T>* __restrict__ C,
+// ---------------------------------------------------------------- batched complex GEMM
+// C_b = A_b B_b for b = blockIdx.z, complex, row-major with row strides lda,
+// ldb, ldc and batch strides sA, sB, sC (0: operand shared by the batch).
+// Optional epilogue: C *= E[m * N + n] * (*escale).  CUDA cores, FP32 or FP64
+// accumulation in the element type.  (16*TM) x (16*TN) output tile per CTA,
+// 256 threads with TM x TN outputs each; K in chunks of KC staged in shared
+// memory by cp.async, two chunks in flight.
+__device__ __forceinline__ void cp_async_zfill(void* smem, const void* gmem, int bytes_valid, int size) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  if (size == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(bytes_valid));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(bytes_valid));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND)); }
+
+template <typename T, int TM, int TN, bool EPI>
+__global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>* __restrict__ A, long long lda,
+                                              long long sA, const C2<T>* __restrict__ B, long long ldb, long long sB,
+                                              C2<T>* __restrict__ C, long long ldc, long long sC,
+                                              const C2<T>* __restrict__ E, const double* __restrict__ escale,
                                               const int* skip) {
   if (skip && *skip) return;
-  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
-  __shared__ C2<T> As[BK][BM + 1];
-  __shared__ C2<T> Bs[BK][BN];
+  constexpr int BM = 16 * TM, BN = 16 * TN, KC = sizeof(T) == 4 ? 16 : 8;   // 33 KB of shared memory at 4 x 4
+  constexpr int ES = (int)sizeof(C2<T>);
+  __shared__ C2<T> As[2][KC][BM + 1];
+  __shared__ C2<T> Bs[2][KC][BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  A += blockIdx.z * sA;
+  B += blockIdx.z * sB;
+  C += blockIdx.z * sC;
+  auto load = [&](int buf, int k0) {
+    for (int e = threadIdx.x; e < BM * KC; e += 256) {
+      const int mm = e / KC, kk = e % KC;
+      const int gm = m0 + mm, gk = k0 + kk;
+      const bool ok = gm < M && gk < K;
+      cp_async_zfill(&As[buf][kk][mm], ok ? (const void*)(A + (size_t)gm * lda + gk) : (const void*)A, ok ? ES : 0,
+                     ES);
+    }
+    for (int e = threadIdx.x; e < KC * BN; e += 256) {
+      const int kk = e / BN, nn = e % BN;
+      const int gk = k0 + kk, gn = n0 + nn;
+      const bool ok = gk < K && gn < Nn;
+      cp_async_zfill(&Bs[buf][kk][nn], ok ? (const void*)(B + (size_t)gk * ldb + gn) : (const void*)B, ok ? ES : 0,
+                     ES);
+    }
+    cp_async_commit();
+  };
   T accr[TM][TN], acci[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) accr[i][j] = acci[i][j] = T(0);
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += 256) {
-      const int mm = e / BK, kk = e % BK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      C2<T> v;
-      v.x = T(0);
-      v.y = T(0);
-      if (gm < M && gk < K) v = A[(size_t)gm * K + gk];
-      As[kk][mm] = v;
-    }
-    for (int e = threadIdx.x; e < BK * BN; e += 256) {
-      const int kk = e / BN, nn = e % BN;
-      const int gk = k0 + kk, gn = n0 + nn;
-      C2<T> v;
-      v.x = T(0);
-      v.y = T(0);
-      if (gk < K && gn < Nn) v = B[(size_t)gk * Nn + gn];
-      Bs[kk][nn] = v;
+  const int nch = (K + KC - 1) / KC;
+  load(0, 0);
+  for (int c = 0; c < nch; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nch) {
+      load(buf ^ 1, (c + 1) * KC);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < BK; ++kk) {
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
       C2<T> a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -266,6 +300,8 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>
     }
     __syncthreads();
   }
+  T es = T(1);
+  if (EPI && escale) es = (T)*escale;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int gm = m0 + ty + 16 * i;
@@ -277,34 +313,49 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>
         C2<T> v;
         v.x = accr[i][j];
         v.y = acci[i][j];
-        C[(size_t)gm * Nn + gn] = v;
+        if (EPI) {
+          const C2<T> w = E[(size_t)gm * Nn + gn];
+          C2<T> u;
+          u.x = (v.x * w.x - v.y * w.y) * es;
+          u.y = (v.x * w.y + v.y * w.x) * es;
+          v = u;
+        }
+        C[(size_t)gm * ldc + gn] = v;
       }
     }
   }
 }
 
+// C_b = A_b B_b (+ epilogue E, escale) over `batch` problems; picks the
+// larger tile when it still gives two CTAs per SM.
 template <typename T>
-static cudaError_t cgemm(const sg_handle* h, int M, int Nn, int K, const C2<T>* A, const C2<T>* B, C2<T>* C,
-                         cudaStream_t st, const int* skip) {
-  const long long tiles64 = (long long)((Nn + 63) / 64) * ((M + 63) / 64);
-  if (tiles64 >= 2LL * h->num_sms) {
-    dim3 grid((Nn + 63) / 64, (M + 63) / 64);
-    k_cgemm<T, 4, 4><<<grid, 256, 0, st>>>(M, Nn, K, A, B, C, skip);
+static cudaError_t cgemm(const sg_handle* h, int M, int Nn, int K, const C2<T>* A, long long lda, long long sA,
+                         const C2<T>* B, long long ldb, long long sB, C2<T>* C, long long ldc, long long sC,
+                         int batch, cudaStream_t st, const int* skip, const C2<T>* E = nullptr,
+                         const double* escale = nullptr) {
+  const long long tiles64 = (long long)((Nn + 63) / 64) * ((M + 63) / 64) * batch;
+  const bool big = tiles64 >= 2LL * h->num_sms;
+  const int bm = big ? 64 : 32, bn = big ? 64 : 32;
+  dim3 grid((Nn + bn - 1) / bn, (M + bm - 1) / bm, batch);
+  if (big) {
+    if (E) k_cgemm<T, 4, 4, true><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, sA, B, ldb, sB, C, ldc, sC, E, escale, skip);
+    else k_cgemm<T, 4, 4, false><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, sA, B, ldb, sB, C, ldc, sC, E, escale, skip);
   } else {
-    dim3 grid((Nn + 31) / 32, (M + 31) / 32);
-    k_cgemm<T, 2, 2><<<grid, 256, 0, st>>>(M, Nn, K, A, B, C, skip);
+    if (E) k_cgemm<T, 2, 2, true><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, sA, B, ldb, sB, C, ldc, sC, E, escale, skip);
+    else k_cgemm<T, 2, 2, false><<<grid, 256, 0, st>>>(M, Nn, K, A, lda, sA, B, ldb, sB, C, ldc, sC, E, escale, skip);
   }
   note_launch();
   return cudaGetLastError();
 }
 
+// Z = M^-1 R for block `which`; tmp and tmp2 hold N complex values of type T
+// each (tmp2 only for 2D).  R and Z may be the same vector.
 template <typename T>
-cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
-                           const int* skip, const double* in_scale) {
+static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
+                                 const int* skip, const double* in_scale, C2<T>* tmp, C2<T>* tmp2) {
   const PrecBlock& blk = h->blk[which];
   TriFactors<T> F;
   if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;
-  C2<T>* tmp = reinterpret_cast<C2<T>*>(h->d_tmp);
   if (h->dim == 1) {
     // one system of length n, P right-hand sides (the modes); out of place
     dim3 b(1, 64), g(1, (h->P + 63) / 64);
@@ -317,20 +368,42 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
     return e;
   }
   const int mx = h->mx, my = h->my, P = h->P;
+  const long long plane = (long long)mx * my;
+  if constexpr (sizeof(T) == 4) {
+    if (h->fd) {
+      // (1) T1 = R Qhat_x over all P*my lines; (2) T2_p = L^-1 o (Qhat_y^T T1_p);
+      // (3) T3_p = Qhat_y T2_p; (4) Z = T3 Qhat_x^T.
+      cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, mx, 0, h->d_Q32, mx, 0, tmp, mx, 0, 1, st, skip);
+      if (e == cudaSuccess)
+        e = cgemm<T>(h, my, mx, my, h->d_Qyt32, my, 0, tmp, mx, plane, tmp2, mx, plane, P, st, skip,
+                     h->d_Linv32[which], in_scale);
+      if (e == cudaSuccess)
+        e = cgemm<T>(h, my, mx, my, h->d_Qy32, my, 0, tmp2, mx, plane, tmp, mx, plane, P, st, skip);
+      if (e == cudaSuccess)
+        e = cgemm<T>(h, P * my, mx, mx, tmp, mx, 0, h->d_Qt32, mx, 0, Z, mx, 0, 1, st, skip);
+      return e;
+    }
+  }
   const C2<T>* Q;
   const C2<T>* Qt;
   const T* dyinv;
   if constexpr (sizeof(T) == 8) { Q = h->d_Q; Qt = h->d_Qt; dyinv = h->d_dyinv; }
   else { Q = h->d_Q32; Qt = h->d_Qt32; dyinv = h->d_dyinv32; }
-  C2<T>* tmp2 = reinterpret_cast<C2<T>*>(h->d_tmp2);
-  cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, Q, tmp, st, skip);   // (1)
+  cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, mx, 0, Q, mx, 0, tmp, mx, 0, 1, st, skip);   // (1)
   if (e != cudaSuccess) return e;
   dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);                     // (2) sys = i, rhs = mode, j = y line
-  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, (long long)mx * my, mx, 1, F, dyinv, tmp, tmp2, skip, in_scale);
+  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, plane, mx, 1, F, dyinv, tmp, tmp2, skip, in_scale);
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return cgemm<T>(h, P * my, mx, mx, tmp2, Qt, Z, st, skip);        // (3)
+  return cgemm<T>(h, P * my, mx, mx, tmp2, mx, 0, Qt, mx, 0, Z, mx, 0, 1, st, skip);        // (3)
+}
+
+template <typename T>
+cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
+                           const int* skip, const double* in_scale) {
+  return precond_apply<T>(h, which, R, Z, st, skip, in_scale, reinterpret_cast<C2<T>*>(h->d_tmp),
+                          reinterpret_cast<C2<T>*>(h->d_tmp2));
 }
 
 // Same preconditioner apply with caller-provided scratch: tmp and tmp2 hold
@@ -339,33 +412,7 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                    C2<T>* tmp, C2<T>* tmp2) {
-  const PrecBlock& blk = h->blk[which];
-  TriFactors<T> F;
-  if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;
-  if (h->dim == 1) {
-    dim3 b(1, 64), g(1, (h->P + 63) / 64);
-    C2<T>* out = (R == Z) ? tmp : Z;
-    k_tri_solve<T><<<g, b, 0, st>>>(1, h->P, h->n, h->n, 1, 0, F, nullptr, R, out, nullptr, nullptr);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && out != Z)
-      e = cudaMemcpyAsync(Z, out, (size_t)h->N * sizeof(C2<T>), cudaMemcpyDeviceToDevice, st);
-    return e;
-  }
-  const int mx = h->mx, my = h->my, P = h->P;
-  const C2<T>* Q;
-  const C2<T>* Qt;
-  const T* dyinv;
-  if constexpr (sizeof(T) == 8) { Q = h->d_Q; Qt = h->d_Qt; dyinv = h->d_dyinv; }
-  else { Q = h->d_Q32; Qt = h->d_Qt32; dyinv = h->d_dyinv32; }
-  cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, Q, tmp, st, nullptr);
-  if (e != cudaSuccess) return e;
-  dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);
-  k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, (long long)mx * my, mx, 1, F, dyinv, tmp, tmp2, nullptr, nullptr);
-  note_launch();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cgemm<T>(h, P * my, mx, mx, tmp2, Qt, Z, st, nullptr);
+  return precond_apply<T>(h, which, R, Z, st, nullptr, nullptr, tmp, tmp2);
 }
 
 template cudaError_t launch_precond_scratch<double>(const sg_handle*, int, const double2*, double2*, cudaStream_t,

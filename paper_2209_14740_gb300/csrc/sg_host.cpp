@@ -311,6 +311,7 @@ static void destroy_impl(sg_handle* h) {
   for (auto& b : h->blk) if (b.f64.dl) free_factors(b);
   cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
   cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
+  cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
   sgi_free_gmres_work(h);
   delete h;
 }
@@ -331,6 +332,10 @@ static Pencil1D pencil(int m, double h, int left_abs, int right_abs) {
   if (right_abs) { p.tdiag[m - 1] = 1.0 / (h * h); p.d[m - 1] = 0.5; p.e[m - 1] = 1.0; }
   return p;
 }
+
+// Longest grid line for which the FP32 2D preconditioner uses the fast
+// diagonalisation instead of the tridiagonal solves along y.
+constexpr int kFdMaxLine = 320;
 
 static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
   const int n = h->n;
@@ -427,6 +432,42 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
     }
     cudaFree(d_gd); cudaFree(d_ls); cudaFree(d_go);
     SG_CUDA_TRY(cudaMalloc(&h->d_tmp2, (size_t)h->N * sizeof(double2)));
+    // Fast diagonalisation for the FP32 applies: also diagonalise the y
+    // pencil (the same matrix as x on a square grid).  Four GEMMs replace
+    // two GEMMs and mx * P sequential tridiagonal solves; worth it while
+    // the lines are short (the GEMM work grows with mx^2).
+    if (mx <= kFdMaxLine && my <= kFdMaxLine) {
+      std::vector<cd> lamy, Qy;
+      bool ok = true;
+      if (my == mx) {
+        lamy = lam;
+        Qy = Q;
+      } else {
+        double oerr_y = 0;
+        ok = csym_tridiag_eig(my, gyd, gyo, lamy, Qy, &oerr_y);
+      }
+      if (ok) {
+        std::vector<float2> Qy32((size_t)my * my), Qyt32((size_t)my * my), Linv((size_t)my * mx);
+        for (int j = 0; j < my; ++j)
+          for (int k = 0; k < my; ++k) {
+            const cd v = Qy[(size_t)j * my + k] / std::sqrt(py.d[j]);
+            Qy32[(size_t)j * my + k] = make_float2((float)v.real(), (float)v.imag());
+            Qyt32[(size_t)k * my + j] = make_float2((float)v.real(), (float)v.imag());
+          }
+        if (upload(&h->d_Qy32, Qy32.data(), Qy32.size()) || upload(&h->d_Qyt32, Qyt32.data(), Qyt32.size()))
+          return fail(SG_ENOMEM, "precond upload");
+        for (int which = 0; which < 2; ++which) {
+          const cd shift = which == 0 ? cd(0, 0) : cd(0, -h->beta * kb * kb);
+          for (int j = 0; j < my; ++j)
+            for (int i = 0; i < mx; ++i) {
+              const cd v = 1.0 / (lamy[j] + lam[i] + shift);
+              Linv[(size_t)j * mx + i] = make_float2((float)v.real(), (float)v.imag());
+            }
+          if (upload(&h->d_Linv32[which], Linv.data(), Linv.size())) return fail(SG_ENOMEM, "precond upload");
+        }
+        h->fd = true;
+      }
+    }
   }
   SG_CUDA_TRY(cudaMalloc(&h->d_tmp, (size_t)h->N * sizeof(double2)));
   int bad = 0;

@@ -115,6 +115,12 @@ struct sg_handle {
   void* d_tmp = nullptr;             // N complex128 scratch (preconditioner intermediate)
   void* d_tmp2 = nullptr;            // N complex128 scratch (2D: second intermediate)
   double eig_orth_err = 0.0;         // max |Q^T Q - I| of the host eigenvectors
+  // 2D fast diagonalisation (FP32 applies): both directions transformed,
+  // S^-1 = (Qhat_y (x) Qhat_x) diag(1 / (lambda_y,j + lambda_x,i + shift)) (Qhat_y (x) Qhat_x)^T
+  bool fd = false;
+  float2* d_Qy32 = nullptr;          // Qhat_y = D_y^-1/2 Q_y, row-major my x my
+  float2* d_Qyt32 = nullptr;         // Qhat_y^T
+  float2* d_Linv32[2] = {nullptr, nullptr};   // [block] my x mx: 1 / (lambda_y,j + lambda_x,i + shift)
 
   sgi::GmresWork gw;
 

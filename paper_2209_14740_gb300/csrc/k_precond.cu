@@ -234,6 +234,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND)); }
 
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename T, int TM, int TN, bool EPI>
 __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>* __restrict__ A, long long lda,
                                               long long sA, const C2<T>* __restrict__ B, long long ldb, long long sB,
@@ -294,8 +297,9 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int Nn, int K, const C2<T>
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
-          accr[i][j] += a[i].x * b[j].x - a[i].y * b[j].y;
-          acci[i][j] += a[i].x * b[j].y + a[i].y * b[j].x;
+          // four fused multiply-adds per complex product
+          accr[i][j] = fmat(a[i].x, b[j].x, fmat(-a[i].y, b[j].y, accr[i][j]));
+          acci[i][j] = fmat(a[i].x, b[j].y, fmat(a[i].y, b[j].x, acci[i][j]));
         }
     }
     __syncthreads();

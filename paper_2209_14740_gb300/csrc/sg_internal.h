@@ -76,7 +76,8 @@ struct GmresWork {
   int* dctl = nullptr;     // device control words
   double* part = nullptr;  // partial sums [nblk][2*(restart+2)]
   unsigned* counter = nullptr;
-  int nblk = 0;
+  int nblk = 0;            // blocks of the reduction kernels
+  int cg_nblk = 0;         // blocks of the CGS2 passes
 };
 
 }  // namespace sgi

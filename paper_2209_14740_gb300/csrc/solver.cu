@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "sg_internal.h"
@@ -137,114 +138,186 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 }
 
 // ------------------------------------------------------------------ kernels
-// d_i = V_i^H w for i < nv (raw vectors); last block writes d and
-// c_i = vscale_i^2 d_i (the update coefficient for the raw basis).
-// Grid: blockIdx.x = element chunk (gridDim.x chunks), blockIdx.y = group of
-// DG vectors; every block reduces its DG dot products once and stores them at
-// part[(group * chunks + chunk) * 2 * DG + k].
-constexpr int DG = 4;
+// ------------------------------------------------------------------ CGS2 passes
+// The Arnoldi step orthogonalises w against the raw basis V_0..V_{nv-1} in
+// three passes over V:
+//   k_cgs_dots             d1 = V^H w                      (c1 = vscale^2 d1)
+//   k_cgs_update<DOTS>     w -= V c1, then d2 = V^H w      (c2 = vscale^2 d2)
+//   k_cgs_update<GIVENS>   w -= V c2, ||w||^2, then the Givens update of
+//                          column j in the last block to finish.
+// Each block walks chunks of RED_THREADS * CG_EPT consecutive elements (grid
+// stride), a thread keeps its CG_EPT elements of w in registers, and every
+// pass reads each V_i element once (the DOTS re-read of the chunk it just
+// updated comes from L1).  Per-warp sums go to a [warp][value] table in
+// shared memory, block sums to part[value * gridDim.x + block], and the last
+// block adds the blocks in a fixed order (bitwise reproducible).
+constexpr int CG_EPT = 4;
+constexpr int CG_WARPS = RED_THREADS / 32;
+
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_dots(const C2<T>* __restrict__ V, long long N, int nv,
-                                                     const C2<T>* __restrict__ w, double* part,
-                                                     unsigned* counter, const double* vscale, double* d_out,
-                                                     double* c_out, const int* ctl) {
-  if (ctl[CTL_DONE]) return;
-  __shared__ double sm[2 * DG * 32];
-  const int chunks = gridDim.x, grp = blockIdx.y;
-  const long long per = (N + chunks - 1) / chunks;
-  const long long e0 = blockIdx.x * per, e1 = min(N, e0 + per);
-  const int q0 = grp * DG, ng = min(DG, nv - q0);
-  const C2<T>* Vg = V + (size_t)q0 * N;
-  T acc[2 * DG];
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-  for (int k = 0; k < 2 * DG; ++k) acc[k] = T(0);
-#pragma unroll 4
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const C2<T> we = w[e];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// red[warp * nv + i] += warp sum of conj(V_i[e]) w_e over the thread's
+// elements of the chunk starting at `base`.
+template <typename T>
+__device__ __forceinline__ void chunk_dots(const C2<T>* __restrict__ V, long long N, int nv, long long base,
+                                           const C2<T> (&wk)[CG_EPT], double2* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 2
+  for (int i = 0; i < nv; ++i) {
+    const C2<T>* Vi = V + (size_t)i * N;
+    T ax = T(0), ay = T(0);
 #pragma unroll
-    for (int q = 0; q < DG; ++q) {
-      if (q < ng) {
-        const C2<T> v = Vg[(size_t)q * N + e];
-        acc[2 * q] += v.x * we.x + v.y * we.y;
-        acc[2 * q + 1] += v.x * we.y - v.y * we.x;
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      if (e < N) {
+        const C2<T> v = __ldg(Vi + e);
+        ax += v.x * wk[k].x + v.y * wk[k].y;
+        ay += v.x * wk[k].y - v.y * wk[k].x;
       }
     }
-  }
-  double dv[2 * DG];
-#pragma unroll
-  for (int k = 0; k < 2 * DG; ++k) dv[k] = (double)acc[k];
-  block_sum<2 * DG>(dv, sm);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 2 * DG; ++k) part[((size_t)grp * chunks + blockIdx.x) * 2 * DG + k] = dv[k];
-  // last block of the whole grid: sum the chunks of every value, warps in parallel
-  __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned t = atomicAdd(counter, 1u);
-    is_last = (t == gridDim.x * gridDim.y - 1);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = warp; k < 2 * nv; k += nw) {
-    const int i = k >> 1, g = i / DG, kk = 2 * (i - g * DG) + (k & 1);
-    const double* pk = part + (size_t)g * chunks * 2 * DG + kk;
-    double s0 = 0.0, s1 = 0.0;
-    int c = lane;
-    for (; c + 32 < chunks; c += 64) {
-      s0 += __ldcg(pk + (size_t)c * 2 * DG);
-      s1 += __ldcg(pk + (size_t)(c + 32) * 2 * DG);
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) {
+      double2& r = red[warp * nv + i];
+      r.x += (double)ax;
+      r.y += (double)ay;
     }
-    if (c < chunks) s0 += __ldcg(pk + (size_t)c * 2 * DG);
+  }
+}
+
+// Block sums of the per-warp table into part, then (last block only) the
+// sums over blocks: d_out[k] and c_out[k] = vscale_i^2 d_out[k], k < 2 nv.
+// Returns true in the last block.
+__device__ __forceinline__ bool finish_dots(int nv, const double2* red, double* part, unsigned* counter,
+                                            const double* vscale, double* d_out, double* c_out) {
+  const int G = gridDim.x;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int w = 0; w < CG_WARPS; ++w) {
+      sx += red[w * nv + i].x;
+      sy += red[w * nv + i].y;
+    }
+    part[(size_t)(2 * i) * G + blockIdx.x] = sx;
+    part[(size_t)(2 * i + 1) * G + blockIdx.x] = sy;
+  }
+  if (!last_block(counter)) return false;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k < 2 * nv; k += CG_WARPS) {
+    const double* pk = part + (size_t)k * G;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < G; b += 64) {
+      s0 += __ldcg(pk + b);
+      s1 += __ldcg(pk + b + 32);
+    }
+    if (b < G) s0 += __ldcg(pk + b);
     double s = s0 + s1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) {
       d_out[k] = s;
-      const double vs = vscale[i];
+      const double vs = vscale[k >> 1];
       c_out[k] = vs * vs * s;
     }
   }
   if (threadIdx.x == 0) *counter = 0;
+  return true;
 }
 
-// w -= sum_i c_i V_i ; optionally ||w||^2 (last block writes *norm_out).
+// Pass 1: d = V^H w, c = vscale^2 d.  Dynamic shared memory: CG_WARPS * nv double2.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_update(const C2<T>* __restrict__ V, long long N, int nv,
-                                                       C2<T>* __restrict__ w, const double* __restrict__ c,
-                                                       double* part, int pstride, unsigned* counter,
-                                                       double* norm_out, const int* ctl) {
+__global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(const C2<T>* __restrict__ V, long long N, int nv,
+                                                         const C2<T>* __restrict__ w, double* part,
+                                                         unsigned* counter, const double* vscale, double* d_out,
+                                                         double* c_out, const int* ctl) {
   if (ctl[CTL_DONE]) return;
+  extern __shared__ double2 red[];
+  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const long long chunk = (long long)RED_THREADS * CG_EPT;
+  for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
+    C2<T> wk[CG_EPT];
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
+    }
+    chunk_dots<T>(V, N, nv, base, wk, red);
+  }
+  finish_dots(nv, red, part, counter, vscale, d_out, c_out);
+}
+
+__device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j);
+
+// Passes 2 and 3: w -= sum_i c_i V_i, then either d2 = V^H w (DOTS) or
+// ||w||^2 and the Givens update of column j (GIVENS).
+// Dynamic shared memory (DOTS): CG_WARPS * nv double2.
+template <typename T, bool DOTS>
+__global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restrict__ V, long long N, int nv,
+                                                           C2<T>* __restrict__ w, const double* __restrict__ c,
+                                                           double* part, unsigned* counter, const double* vscale,
+                                                           double* d_out, double* c_out, double* D, int* ctl,
+                                                           DevLayout L, int j) {
+  if (ctl[CTL_DONE]) return;
+  extern __shared__ double2 red[];
   __shared__ C2<T> cs[MAXV];
   __shared__ double sm[32];
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = mkc<T>((T)c[2 * i], (T)c[2 * i + 1]);
+  if (DOTS)
+    for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
   __syncthreads();
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long chunk = (long long)RED_THREADS * CG_EPT;
   T nacc = T(0);
-#pragma unroll 2
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    C2<T> we = w[e];
-#pragma unroll 8
+  for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
+    C2<T> wk[CG_EPT];
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
+    }
+#pragma unroll 4
     for (int i = 0; i < nv; ++i) {
-      const C2<T> v = V[(size_t)i * N + e];
+      const C2<T>* Vi = V + (size_t)i * N;
       const C2<T> ci = cs[i];
-      we.x -= ci.x * v.x - ci.y * v.y;
-      we.y -= ci.x * v.y + ci.y * v.x;
+#pragma unroll
+      for (int k = 0; k < CG_EPT; ++k) {
+        const long long e = base + k * RED_THREADS;
+        if (e < N) {
+          const C2<T> v = __ldg(Vi + e);
+          wk[k].x -= ci.x * v.x - ci.y * v.y;
+          wk[k].y -= ci.x * v.y + ci.y * v.x;
+        }
+      }
     }
-    w[e] = we;
-    nacc += we.x * we.x + we.y * we.y;
-  }
-  if (norm_out) {
-    double dv[1] = {(double)nacc};
-    block_sum<1>(dv, sm);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * pstride] = dv[0];
-    if (last_block(counter)) {
-      sum_block_partials(part, pstride, 1, [&](int, double s) { *norm_out = s; });
-      if (threadIdx.x == 0) *counter = 0;
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      if (e < N) {
+        w[e] = wk[k];
+        nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
+      }
     }
+    if (DOTS) chunk_dots<T>(V, N, nv, base, wk, red);
   }
+  if (DOTS) {
+    finish_dots(nv, red, part, counter, vscale, d_out, c_out);
+    return;
+  }
+  double dv[1] = {(double)nacc};
+  block_sum<1>(dv, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = dv[0];
+  if (!last_block(counter)) return;
+  sum_block_partials(part, 1, 1, [&](int, double s) { D[L.sc + SC_NORMSQ] = s; });
+  if (threadIdx.x == 0) *counter = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) givens_column(D, ctl, L, j);
 }
 
 // r = b - Ax (or r = b when Ax == nullptr) written in the inner precision;
@@ -297,13 +370,13 @@ __global__ void k_cycle_init(double* D, int* ctl, DevLayout L, double tol_est, d
   }
 }
 
-// Givens update for column j, one warp.  w = A M^-1 v_j was formed from the
+// Givens update for column j, by one warp (lanes 0-31 of the calling block;
+// the memory it reads was written before a block-wide fence).  w = A M^-1 v_j was formed from the
 // normalised v_j, so H[i][j] = v_i^H w = vscale_i (d1_i + d2_i) and
 // H[j+1][j] = ||w||.  The column and the previous rotations are read and
 // written by all lanes in parallel through shared memory; lane 0 applies the
 // rotations (a sequential recurrence) and forms the new one.
-__global__ void k_givens(double* D, int* ctl, DevLayout L, int j) {
-  if (ctl[CTL_DONE]) return;
+__device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j) {
   __shared__ double2 col[MAXV + 1];
   __shared__ double2 snr[MAXV];
   __shared__ double csr[MAXV];
@@ -528,6 +601,19 @@ void sgi_free_gmres_work(sg_handle* h) {
   w = GmresWork{};
 }
 
+// The CGS2 passes keep CG_WARPS * nv double2 per-warp sums in dynamic shared
+// memory: up to 64 KB at nv = MAXV, above the default 48 KB limit.
+static void cgs_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int bytes = CG_WARPS * MAXV * (int)sizeof(double2);
+    cudaFuncSetAttribute(k_cgs_dots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_cgs_dots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_cgs_update<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_cgs_update<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  });
+}
+
 static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   GmresWork& w = h->gw;
   if (w.V && w.restart >= m && w.prec_bytes == elem_bytes) return SG_OK;
@@ -535,6 +621,9 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   const size_t N = (size_t)h->N;
   DevLayout L(m);
   w.nblk = std::max(1, std::min(h->num_sms * 2, (int)((N + 2 * RED_THREADS - 1) / (2 * RED_THREADS))));
+  w.cg_nblk = (int)std::max<long long>(
+      1, std::min<long long>(4LL * h->num_sms, ((long long)N + RED_THREADS * CG_EPT - 1) / (RED_THREADS * CG_EPT)));
+  cgs_attributes();
   cudaError_t e = cudaSuccess;
   if (!e) e = cudaMalloc(&w.V, (size_t)(m + 1) * N * elem_bytes);
   if (!e) e = cudaMalloc(&w.Z, N * elem_bytes);
@@ -543,10 +632,9 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   if (!e) e = cudaMalloc(&w.B64, N * sizeof(double2));
   if (!e) e = cudaMalloc((void**)&w.dscal, L.total * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.dctl, 16 * sizeof(int));
-  // block partials: the reduction kernels use nblk * 2 (MAXV + 2) doubles, k_dots
-  // at most (4 * SMs + MAXV / DG) * 2 * DG
-  const size_t part_doubles = std::max((size_t)w.nblk * 2 * (MAXV + 2),
-                                       ((size_t)4 * h->num_sms + MAXV / DG + 1) * 2 * DG);
+  // block partials: the reduction kernels use nblk * 2 (MAXV + 2) doubles, the
+  // CGS2 passes 2 * MAXV * cg_nblk
+  const size_t part_doubles = std::max((size_t)w.nblk * 2 * (MAXV + 2), (size_t)2 * MAXV * w.cg_nblk);
   if (!e) e = cudaMalloc((void**)&w.part, part_doubles * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.counter, sizeof(unsigned));
   if (!e) e = cudaMemset(w.counter, 0, sizeof(unsigned));
@@ -567,18 +655,8 @@ struct Ctx {
   DevLayout L;
   int grid;
   int pstride;
+  int cg_grid;   // blocks of the CGS2 passes
 };
-
-// k_dots grid: element chunks x groups of DG vectors, about 4 blocks per SM in
-// total, at least 1024 elements per chunk.  Partials: chunks * groups * 2 * DG
-// doubles (fits the workspace, see ensure_work).
-dim3 dots_grid(const Ctx& c, int nv) {
-  const int groups = (nv + DG - 1) / DG;
-  const long long by_size = (c.h->N + 1023) / 1024;
-  const long long by_fill = (4LL * c.h->num_sms + groups - 1) / groups;
-  const int chunks = (int)std::max(1LL, std::min(by_size, by_fill));
-  return dim3(chunks, groups);
-}
 
 // Z = M^-1 (s R) with s = *in_scale (1 if null).
 template <typename T>
@@ -612,16 +690,16 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
   if ((e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
   const int nv = j + 1;
-  const dim3 dg = dots_grid(c, nv);
-  k_dots<T><<<dg, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale, D + c.L.d1,
-                                          D + c.L.c1, w.dctl); note_launch();
-  k_update<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, c.pstride, w.counter, nullptr,
-                                                w.dctl); note_launch();
-  k_dots<T><<<dg, RED_THREADS, 0, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale, D + c.L.d2,
-                                          D + c.L.c2, w.dctl); note_launch();
-  k_update<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c2, w.part, c.pstride, w.counter,
-                                                D + c.L.sc + SC_NORMSQ, w.dctl); note_launch();
-  k_givens<<<1, 32, 0, c.st>>>(D, w.dctl, c.L, j); note_launch();
+  const size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
+  const int G = c.cg_grid;
+  k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
+                                                    D + c.L.d1, D + c.L.c1, w.dctl); note_launch();
+  k_cgs_update<T, true><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, w.counter,
+                                                            D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl,
+                                                            c.L, j); note_launch();
+  k_cgs_update<T, false><<<G, RED_THREADS, 0, c.st>>>(V, N, nv, wv, D + c.L.c2, w.part, w.counter,
+                                                     D + c.L.vscale, nullptr, nullptr, D, w.dctl, c.L, j);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -731,7 +809,7 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
   if (st0 != SG_OK) return st0;
   GmresWork& w = h->gw;
   cudaStream_t st = (cudaStream_t)stream;
-  Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2)};
+  Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
   c.L = DevLayout(w.restart);
   // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
   const size_t obytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
@@ -822,8 +900,13 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     // inner tolerance on |g| relative to ref
     double tol_est, ref;
     if (mixed) {
+      // reduce by inner_tol per refinement step, but finish in this step when
+      // the remaining reduction is within 20x of it (saves a refinement step
+      // that would only cover the last factor)
       ref = std::sqrt(rn2);
-      tol_est = std::max(inner_tol, 0.5 * opts->tol * bnorm / ref);
+      const double need = 0.5 * opts->tol * bnorm / ref;
+      tol_est = need >= 0.05 * inner_tol ? need : inner_tol;
+      tol_est = std::min(tol_est, 0.5);
     } else {
       ref = bnorm;
       tol_est = opts->tol;

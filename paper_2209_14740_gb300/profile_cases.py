@@ -50,6 +50,7 @@ def main(argv=None):
     ap.add_argument("--mode", choices=["mixed", "fp64", "fp32"], default="mixed", help="solve precision")
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="mixed solve: inner reduction per refinement")
     a = ap.parse_args(argv)
 
     B.load()
@@ -69,7 +70,7 @@ def main(argv=None):
 
         def call():
             return op.gmres(b, x, restart=a.restart, tol=1e-8 if mode != B.FP32 else 1e-5, prec=B.PREC_MEAN,
-                            mode=mode)
+                            mode=mode, inner_tol=a.inner_tol)
     else:
         X = torch.randn(op.N, dtype=cdt, device=dev, generator=gen)
         Y = torch.empty_like(X)
@@ -93,7 +94,7 @@ def main(argv=None):
     line = {"case": a.case, "g": a.g, "s": a.s, "r": a.r, "P": op.P, "N": op.N, "reps": a.reps,
             "ms_per_rep": e0.elapsed_time(e1) / max(a.reps, 1)}
     if isinstance(out, dict):
-        line.update(iters=out["iters"], relres=out["relres"])
+        line.update(iters=out["iters"], outer=out["outer"], relres=out["relres"])
     print(json.dumps(line))
     op.close()
     return 0

@@ -189,7 +189,7 @@ typedef struct {
   int max_outer;        /* SG_MIXED: cap on refinement steps; <= 0 means 20 */
   double tol;           /* stop when ||b - A x||_2 / ||b||_2 <= tol (Sec. 6.3) */
   double inner_tol;     /* SG_MIXED: inner relative reduction per refinement step (a step that can
-                           reach tol within 20x of it aims at tol directly); <= 0 means 1e-4 */
+                           reach tol within 20x of it aims at tol directly); <= 0 means 1e-5 */
   sg_prec prec;         /* right preconditioner M: A M^-1 y = b, x = M^-1 y (Sec. 6.3) */
   sg_precision mode;    /* SG_FP64, SG_FP32 or SG_MIXED */
   const void* x0;       /* initial guess (same memory space and precision as x); NULL = zero */

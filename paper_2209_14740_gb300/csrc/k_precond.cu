@@ -375,16 +375,21 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
   const long long plane = (long long)mx * my;
   if constexpr (sizeof(T) == 4) {
     if (h->fd) {
-      // (1) T1 = R Qhat_x over all P*my lines; (2) T2_p = L^-1 o (Qhat_y^T T1_p);
-      // (3) T3_p = Qhat_y T2_p; (4) Z = T3 Qhat_x^T.
-      cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, mx, 0, h->d_Q32, mx, 0, tmp, mx, 0, 1, st, skip);
+      // Tensor-core transforms, each a GEMM with a constant right factor; the
+      // per-batch transposes in (1) and (3) move the direction being
+      // transformed into the rows' contiguous index:
+      //   (1) T1'_p = (R_p Qhat_x)^T          [p][i][y]
+      //   (2) T2'_p = L^-1 o (T1'_p Qhat_y)   [p][i][j], L^-1 indexed (j, i)
+      //   (3) T3_p  = (T2'_p Qhat_y^T)^T      [p][y][i]
+      //   (4) Z_p   = T3_p Qhat_x^T           [p][y][x]
+      cudaError_t e = tc_cgemm(h->tcB[0], R, mx, P * my, tmp, 0, 1, my, nullptr, 0, 1, nullptr, skip, h->d_err, st);
       if (e == cudaSuccess)
-        e = cgemm<T>(h, my, mx, my, h->d_Qyt32, my, 0, tmp, mx, plane, tmp2, mx, plane, P, st, skip,
-                     h->d_Linv32[which], in_scale);
+        e = tc_cgemm(h->tcB[1], tmp, my, P * mx, tmp2, my, 0, 0, h->d_Linv32[which], mx, mx, in_scale, skip,
+                     h->d_err, st);
       if (e == cudaSuccess)
-        e = cgemm<T>(h, my, mx, my, h->d_Qy32, my, 0, tmp2, mx, plane, tmp, mx, plane, P, st, skip);
+        e = tc_cgemm(h->tcB[2], tmp2, my, P * mx, tmp, 0, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st);
       if (e == cudaSuccess)
-        e = cgemm<T>(h, P * my, mx, mx, tmp, mx, 0, h->d_Qt32, mx, 0, Z, mx, 0, 1, st, skip);
+        e = tc_cgemm(h->tcB[3], tmp, mx, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st);
       return e;
     }
   }

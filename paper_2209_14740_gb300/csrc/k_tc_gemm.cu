@@ -1,0 +1,453 @@
+// Complex GEMM with a constant right factor on the 5th-generation tensor
+// cores (tcgen05, TF32 inputs, FP32 accumulation in tensor memory), used by
+// the fast-diagonalisation transforms of the 2D preconditioner.
+//
+//   C = X Q,  X: M x K complex64 rows (the data), Q: K x N complex (constant)
+//
+// The complex product is the real product of X viewed as an M x 2K real
+// matrix (re, im interleaved, as stored) with the real embedding
+//   B[2k][2n] = Re Q[k][n],   B[2k][2n+1] = Im Q[k][n],
+//   B[2k+1][2n] = -Im Q[k][n], B[2k+1][2n+1] = Re Q[k][n],
+// so C viewed as M x 2N real comes out interleaved as well.
+//
+// FP32 accuracy from TF32 inputs (the 3xTF32 split): every operand is
+// x = hi + lo with hi = tf32(x), lo = x - hi, and C = Xhi Bhi + Xhi Blo +
+// Xlo Bhi; the dropped Xlo Blo term is below FP32 rounding.  B's split is
+// precomputed on the host, X's is formed per tile in shared memory.
+//
+// One CTA owns 128 rows and 64 real output columns; the accumulator (128
+// lanes x 64 columns FP32) lives in tensor memory.  K is walked in stages
+// of 32 real values.  Eight loader warps copy raw X rows by cp.async (two
+// stages ahead), split them into hi/lo in the canonical K-major layout
+// (8-row x 16-byte core matrices, no swizzle) and copy the pre-laid-out B
+// tiles; one lane of a ninth warp issues the 12 MMAs of each stage (M=128,
+// N=64, K=8) and commits them to an mbarrier.  Every wait is bounded: on a
+// timeout the kernel records it, drains its copies, frees tensor memory and
+// returns.
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sg_internal.h"
+
+namespace sgi {
+namespace tc {
+
+constexpr int BM = 128;                 // rows per CTA = TMEM lanes
+constexpr int BN = 64;                  // real output columns per CTA = TMEM columns
+constexpr int BK = 32;                  // real K values per stage (128 bytes of FP32)
+constexpr int NLOAD = 256;              // loader / splitter threads (warps 0-7)
+constexpr int THREADS = NLOAD + 32;     // + one MMA warp
+constexpr int NRAW = 3;                 // raw X slots: stages s, s+1, s+2 in flight
+constexpr int NBS = 4;                  // B slots: stage s-1 may still be read by its MMAs
+constexpr int NAS = 2;                  // split A (hi, lo) slots
+constexpr int RAW_PITCH = 144;          // bytes per raw X row (128 + 16: conflict-free split reads)
+constexpr int RAW_TILE = BM * RAW_PITCH;
+constexpr int A_TILE = BM * BK * 4;     // 16 KB, core-matrix layout
+constexpr int B_TILE = BN * BK * 4;     // 8 KB, core-matrix layout
+constexpr int OFF_RAW = 0;
+constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;              // [slot][hi, lo]
+constexpr int OFF_A = ((OFF_B + NBS * 2 * B_TILE + 1023) / 1024) * 1024;   // [slot][hi, lo]
+constexpr int OFF_BAR = OFF_A + NAS * 2 * A_TILE;             // full[NAS], done[NBS], TMEM address, abort flag
+constexpr int SMEM_BYTES = OFF_BAR + 128 + 1024;              // + slack for 1024-byte alignment
+constexpr int OUT_PITCH = BN / 2 + 1;                         // float2 per staged output row
+static_assert(BM * OUT_PITCH * 8 <= NRAW * RAW_TILE, "output staging must fit in the raw slots");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+constexpr uint32_t TMEM_COLS = 64;
+
+// Byte offset of element (row, k) of a tile with 32 K values per row in the
+// no-swizzle K-major layout: core matrix (row / 8, k / 4) at 128-byte
+// granularity, K-adjacent core matrices 128 bytes apart (leading byte
+// offset), 8-row groups 1024 bytes apart (stride byte offset).
+__host__ __device__ constexpr int core_off(int row, int k) {
+  return ((row >> 3) * 8 + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared memory matrix descriptor: start address, leading byte offset 128,
+// stride byte offset 1024, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         (1ull << 46);
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
+// N = BN, M = BM.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase with the given parity of an mbarrier; false after
+// about 0.5 s (the MMAs of one stage take well under a microsecond).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = now_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255u) == 255u && now_ns() - t0 > 500000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+}  // namespace tc
+
+// Output placement of C (complex, Nc columns):
+//   mode 0: C[m * ldc + n]
+//   mode 1: row m = p * MB + r goes to C[(p * Nc + n) * MB + r] (the
+//           per-batch transpose used to switch the transformed direction)
+// With E: C *= E[n * e_ld + m % e_mod] * (*escale).
+struct TcArgs {
+  const float* X;      // M rows of 2K floats, row stride ldx floats
+  long long ldx;
+  int M, K2;           // rows, real K (2K)
+  int nks;             // K stages (ceil(K2 / 32)); B is laid out for nks stages
+  const float* Bhi;    // [n tile][stage][64 x 32 core-matrix tile]
+  const float* Blo;
+  int Nc;              // complex output columns
+  float2* C;
+  long long ldc;
+  int mode, MB;
+  const float2* E;
+  int e_ld, e_mod;
+  const double* escale;
+  const int* skip;
+  int* err;            // set to 1 on a wait timeout
+};
+
+// Named barrier of the loader warps (the MMA warp does not take part).
+__device__ __forceinline__ void loader_sync() { asm volatile("bar.sync 1, %0;" ::"n"(tc::NLOAD) : "memory"); }
+
+// Loader barrier that also ORs a flag over the loaders, so that every loader
+// takes the same branch afterwards.
+__device__ __forceinline__ bool loader_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(tc::NLOAD)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+// Pipeline (stage s = 32 real K values):
+//   loaders:  wait raw/B of s landed -> wait MMA(s-2) (frees A slot s%2)
+//             -> split raw -> A slot, arrive full[s%2] -> issue copies of s+2
+//   MMA lane: wait full[s%2] -> 12 MMAs (3xTF32 x 4 K steps) -> commit done[s%4]
+// so the split of stage s+1 and the copies of later stages overlap the MMAs
+// of stage s.
+__global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
+  using namespace tc;
+  if (a.skip && *a.skip) return;
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t s_base = smem_u32(sm);
+  const uint32_t full0 = s_base + OFF_BAR;              // NAS barriers, count NLOAD
+  const uint32_t done0 = full0 + 8 * NAS;               // NBS barriers, count 1 (MMA commit)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8 * (NAS + NBS));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_BAR + 8 * (NAS + NBS) + 8);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < NAS; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * i), "n"(NLOAD) : "memory");
+    for (int i = 0; i < NBS; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done0 + 8 * i) : "memory");
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int m0 = blockIdx.x * BM;
+  const int nks = a.nks;
+
+  if (warp < NLOAD / 32) {
+    // ---------------------------------------------------------------- loaders
+    const float* Bh = a.Bhi + (size_t)blockIdx.y * nks * (BN * BK);
+    const float* Bl = a.Blo + (size_t)blockIdx.y * nks * (BN * BK);
+    auto issue = [&](int t) {
+      const uint32_t raw = s_base + OFF_RAW + (t % NRAW) * RAW_TILE;
+      const int k0 = t * BK;
+#pragma unroll
+      for (int q = 0; q < (BM * BK / 2) / NLOAD; ++q) {
+        const int idx = tid + q * NLOAD;
+        const int r = idx >> 4, kp = idx & 15;
+        const int m = m0 + r, k = k0 + 2 * kp;
+        const bool ok = m < a.M && k < a.K2;
+        const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
+        cp_async8(raw + r * RAW_PITCH + kp * 8, src, ok ? 8 : 0);
+      }
+      const uint32_t bh = s_base + OFF_B + (t % NBS) * 2 * B_TILE;
+      const float* gh = Bh + (size_t)t * (BN * BK);
+      const float* gl = Bl + (size_t)t * (BN * BK);
+#pragma unroll
+      for (int q = 0; q < (BN * BK / 4) / NLOAD; ++q) {
+        const int c = tid + q * NLOAD;
+        cp_async16(bh + c * 16, gh + 4 * c);
+        cp_async16(bh + B_TILE + c * 16, gl + 4 * c);
+      }
+    };
+    for (int t = 0; t < 2; ++t) {
+      if (t < nks) issue(t);
+      cp_commit();
+    }
+    bool bad = false;
+    for (int s = 0; s < nks; ++s) {
+      cp_wait<1>();
+      bool to = false;
+      if (s >= 2) to = !mbar_wait(done0 + 8 * ((s - 2) % NBS), ((s - 2) / NBS) & 1);
+      if (loader_sync_or(to || *abort_flag != 0)) { bad = true; break; }
+      // split X into hi / lo: two threads per row, four 16-byte chunks each
+      {
+        const int row = tid & (BM - 1), half = tid >> 7;
+        const unsigned char* raw = sm + OFF_RAW + (s % NRAW) * RAW_TILE + row * RAW_PITCH;
+        unsigned char* ahi = sm + OFF_A + (s % NAS) * 2 * A_TILE;
+        unsigned char* alo = ahi + A_TILE;
+#pragma unroll
+        for (int cc = 0; cc < BK / 8; ++cc) {
+          const int c = half * (BK / 8) + cc;
+          const float4 v = *reinterpret_cast<const float4*>(raw + 16 * c);
+          float4 h, l;
+          h.x = tf32_hi(v.x); l.x = v.x - h.x;
+          h.y = tf32_hi(v.y); l.y = v.y - h.y;
+          h.z = tf32_hi(v.z); l.z = v.z - h.z;
+          h.w = tf32_hi(v.w); l.w = v.w - h.w;
+          *reinterpret_cast<float4*>(ahi + core_off(row, 4 * c)) = h;
+          *reinterpret_cast<float4*>(alo + core_off(row, 4 * c)) = l;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(full0 + 8 * (s % NAS));
+      // the raw slot of stage s+2 was split at s-1; its B slot was read by
+      // MMA(s-2), waited for above
+      if (s + 2 < nks) issue(s + 2);
+      cp_commit();
+    }
+    // all MMAs done before the accumulator is read
+    if (!bad && nks > 0 && !mbar_wait(done0 + 8 * ((nks - 1) % NBS), ((nks - 1) / NBS) & 1)) bad = true;
+    cp_wait<0>();
+    bad = loader_sync_or(bad || *abort_flag != 0);
+    if (bad) {
+      *abort_flag = 1;
+      if (tid == 0) atomicExch(a.err, 1);
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int n0 = blockIdx.y * (BN / 2);   // first complex column of the tile
+      float2* stage = reinterpret_cast<float2*>(sm + OFF_RAW);
+      if (warp < 4) {
+        // warps 0-3 read TMEM lanes 32w..32w+31 (rows of the tile)
+        const int row = warp * 32 + lane, m = m0 + row;
+        float2 e[BN / 2];
+        if (a.E) {
+          const int mr = (m < a.M ? m : 0) % a.e_mod;
+#pragma unroll
+          for (int q = 0; q < BN / 2; ++q)
+            e[q] = (n0 + q < a.Nc) ? a.E[(size_t)(n0 + q) * a.e_ld + mr] : make_float2(0.f, 0.f);
+        }
+        const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
+        uint32_t v[BN];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int j0 = 0; j0 < BN; j0 += 16)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+              "%13, %14, %15}, [%16];"
+              : "=r"(v[j0 + 0]), "=r"(v[j0 + 1]), "=r"(v[j0 + 2]), "=r"(v[j0 + 3]), "=r"(v[j0 + 4]),
+                "=r"(v[j0 + 5]), "=r"(v[j0 + 6]), "=r"(v[j0 + 7]), "=r"(v[j0 + 8]), "=r"(v[j0 + 9]),
+                "=r"(v[j0 + 10]), "=r"(v[j0 + 11]), "=r"(v[j0 + 12]), "=r"(v[j0 + 13]), "=r"(v[j0 + 14]),
+                "=r"(v[j0 + 15])
+              : "r"(taddr + (uint32_t)j0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float2 c[BN / 2];
+#pragma unroll
+        for (int q = 0; q < BN / 2; ++q) {
+          c[q] = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+          if (a.E)
+            c[q] = make_float2(es * (c[q].x * e[q].x - c[q].y * e[q].y), es * (c[q].x * e[q].y + c[q].y * e[q].x));
+        }
+        if (a.mode == 1) {
+          // per-batch transpose: lanes hold consecutive rows r, so each
+          // store instruction writes consecutive addresses
+          if (m < a.M) {
+            const int p = m / a.MB, r = m - p * a.MB;
+#pragma unroll
+            for (int q = 0; q < BN / 2; ++q)
+              if (n0 + q < a.Nc) a.C[((size_t)p * a.Nc + n0 + q) * a.MB + r] = c[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < BN / 2; ++q) stage[row * OUT_PITCH + q] = c[q];
+        }
+      }
+      if (a.mode == 0) {
+        // row-major: all loader warps write the staged rows, consecutive
+        // lanes on consecutive columns
+        loader_sync();
+        for (int idx = tid; idx < BM * (BN / 2); idx += NLOAD) {
+          const int rr = idx / (BN / 2), q = idx % (BN / 2);
+          const int mm = m0 + rr, n = n0 + q;
+          if (mm < a.M && n < a.Nc) a.C[(size_t)mm * a.ldc + n] = stage[rr * OUT_PITCH + q];
+        }
+      }
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- MMA issue
+    for (int s = 0; s < nks; ++s) {
+      if (!mbar_wait(full0 + 8 * (s % NAS), (s / NAS) & 1)) { *abort_flag = 1; break; }
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ahi = s_base + OFF_A + (s % NAS) * 2 * A_TILE, alo = ahi + A_TILE;
+      const uint32_t bhi = s_base + OFF_B + (s % NBS) * 2 * B_TILE, blo = bhi + B_TILE;
+#pragma unroll
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        const uint32_t o = 256u * ks;   // 8 TF32 = two core matrices along K
+        mma_tf32(tmem, sdesc(ahi + o), sdesc(bhi + o), (s > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), 1u);
+        mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), 1u);
+      }
+      mma_commit(done0 + 8 * (s % NBS));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------ host side
+// B layout for C = X Q with Q (kdim x ndim complex, row-major, FP64 on the
+// host): nt = ceil(2 ndim / 64) column tiles, nks = ceil(2 kdim / 32) K
+// stages, each (tile, stage) a 64 x 32 block in core-matrix order.
+static float tf32_round_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return x;   // inf / nan unchanged
+  u = (u + 0x1000u) & 0xFFFFE000u;                   // nearest, ties away from zero
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim) {
+  using namespace tc;
+  TcOperand op;
+  op.kdim = kdim;
+  op.ndim = ndim;
+  op.nks = (2 * kdim + BK - 1) / BK;
+  op.ntiles = (2 * ndim + BN - 1) / BN;
+  const size_t per = (size_t)BN * BK;
+  op.hi.assign(per * op.nks * op.ntiles, 0.0f);
+  op.lo.assign(per * op.nks * op.ntiles, 0.0f);
+  for (int nt = 0; nt < op.ntiles; ++nt)
+    for (int ks = 0; ks < op.nks; ++ks) {
+      const size_t blk = ((size_t)nt * op.nks + ks) * per;
+      for (int row = 0; row < BN; ++row)
+        for (int k = 0; k < BK; ++k) {
+          const int nr = nt * BN + row, kr = ks * BK + k;   // real column of C, real K index
+          double v = 0.0;
+          if (nr < 2 * ndim && kr < 2 * kdim) {
+            const std::complex<double> q = Q[(size_t)(kr >> 1) * ndim + (nr >> 1)];
+            const int a = kr & 1, b = nr & 1;                // B[2k+a][2n+b]
+            v = (a == 0) ? (b == 0 ? q.real() : q.imag()) : (b == 0 ? -q.imag() : q.real());
+          }
+          const float f = (float)v;
+          const float hi = tf32_round_host(f);
+          const float lo = tf32_round_host(f - hi);
+          op.hi[blk + core_off(row, k) / 4] = hi;
+          op.lo[blk + core_off(row, k) / 4] = lo;
+        }
+    }
+  return op;
+}
+
+static void tc_attributes() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+  });
+}
+
+cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
+                     int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
+                     int* err, cudaStream_t st) {
+  tc_attributes();
+  TcArgs a;
+  a.X = reinterpret_cast<const float*>(X);
+  a.ldx = 2 * ldx;
+  a.M = M;
+  a.K2 = 2 * B.kdim;
+  a.nks = B.nks;
+  a.Bhi = B.hi;
+  a.Blo = B.lo;
+  a.Nc = B.ndim;
+  a.C = C;
+  a.ldc = ldc;
+  a.mode = mode;
+  a.MB = MB;
+  a.E = E;
+  a.e_ld = e_ld;
+  a.e_mod = e_mod > 0 ? e_mod : 1;
+  a.escale = escale;
+  a.skip = skip;
+  a.err = err;
+  dim3 grid((M + tc::BM - 1) / tc::BM, B.ntiles);
+  k_tc_cgemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace sgi

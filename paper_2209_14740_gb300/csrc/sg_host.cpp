@@ -312,6 +312,8 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
   cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
   cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
+  for (auto& t : h->tcB) { cudaFree(t.hi); cudaFree(t.lo); }
+  cudaFree(h->d_err);
   sgi_free_gmres_work(h);
   delete h;
 }
@@ -339,6 +341,8 @@ constexpr int kFdMaxLine = 320;
 
 static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
   const int n = h->n;
+  SG_CUDA_TRY(cudaMalloc((void**)&h->d_err, sizeof(int)));
+  SG_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
   int* d_bad = nullptr;
   SG_CUDA_TRY(cudaMalloc((void**)&d_bad, sizeof(int)));
   SG_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
@@ -456,6 +460,29 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
           }
         if (upload(&h->d_Qy32, Qy32.data(), Qy32.size()) || upload(&h->d_Qyt32, Qyt32.data(), Qyt32.size()))
           return fail(SG_ENOMEM, "precond upload");
+        // tensor-core factors of the four transforms (complex FP64 on the host)
+        std::vector<cd> qx((size_t)mx * mx), qxt((size_t)mx * mx), qy((size_t)my * my), qyt((size_t)my * my);
+        for (int a = 0; a < mx; ++a)
+          for (int b = 0; b < mx; ++b) {
+            const cd v = Q[(size_t)a * mx + b] / std::sqrt(px.d[a]);
+            qx[(size_t)a * mx + b] = v;
+            qxt[(size_t)b * mx + a] = v;
+          }
+        for (int a = 0; a < my; ++a)
+          for (int b = 0; b < my; ++b) {
+            const cd v = Qy[(size_t)a * my + b] / std::sqrt(py.d[a]);
+            qy[(size_t)a * my + b] = v;
+            qyt[(size_t)b * my + a] = v;
+          }
+        const std::vector<cd>* facs[4] = {&qx, &qy, &qyt, &qxt};
+        const int dims[4] = {mx, my, my, mx};
+        for (int t = 0; t < 4; ++t) {
+          TcOperand op = tc_make_operand(*facs[t], dims[t], dims[t]);
+          TcDevOperand& d = h->tcB[t];
+          d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles;
+          if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()))
+            return fail(SG_ENOMEM, "precond upload");
+        }
         for (int which = 0; which < 2; ++which) {
           const cd shift = which == 0 ? cd(0, 0) : cd(0, -h->beta * kb * kb);
           for (int j = 0; j < my; ++j)

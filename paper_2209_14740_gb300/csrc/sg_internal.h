@@ -64,6 +64,26 @@ struct PrecBlock {
   TriFactors<float> f32;
 };
 
+// Constant right factor of a tensor-core complex GEMM (k_tc_gemm.cu): the
+// real embedding of a kdim x ndim complex matrix, split hi / lo in TF32,
+// in [column tile][K stage][64 x 32 core-matrix block] order.
+struct TcOperand {
+  int kdim = 0, ndim = 0, nks = 0, ntiles = 0;
+  std::vector<float> hi, lo;
+};
+struct TcDevOperand {
+  int kdim = 0, ndim = 0, nks = 0, ntiles = 0;
+  float* hi = nullptr;
+  float* lo = nullptr;
+};
+TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim);
+// C = X Q for M complex64 rows X (row stride ldx complex), placement mode 0
+// (row-major, ldc) or 1 (per-batch transpose, batches of MB rows), optional
+// elementwise factor E[n * e_ld + m % e_mod] * (*escale).
+cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
+                     int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
+                     int* err, cudaStream_t st);
+
 struct GmresWork {
   int restart = 0;         // basis capacity (columns restart+1)
   int prec_bytes = 0;      // 8 (c64) or 16 (c128) per element of V
@@ -122,6 +142,8 @@ struct sg_handle {
   float2* d_Qy32 = nullptr;          // Qhat_y = D_y^-1/2 Q_y, row-major my x my
   float2* d_Qyt32 = nullptr;         // Qhat_y^T
   float2* d_Linv32[2] = {nullptr, nullptr};   // [block] my x mx: 1 / (lambda_y,j + lambda_x,i + shift)
+  sgi::TcDevOperand tcB[4];          // tensor-core factors: Qhat_x, Qhat_y, Qhat_y^T, Qhat_x^T
+  int* d_err = nullptr;              // device flag: a bounded wait in a kernel timed out
 
   sgi::GmresWork gw;
 

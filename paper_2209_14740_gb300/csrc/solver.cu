@@ -864,7 +864,7 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     return SG_OK;
   }
   const int max_outer = mixed ? (opts->max_outer <= 0 ? 20 : opts->max_outer) : 1 << 30;
-  const double inner_tol = opts->inner_tol <= 0 ? 1e-4 : opts->inner_tol;
+  const double inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
   int iters = 0, cycles = 0, outer = 0;
   double relres = 1.0;
   int ctl[16];

@@ -43,6 +43,39 @@ WORKLOAD = {"workload": "helmholtz_2d_127x127_s3_deg3", "nodes": "127x127", "h":
             "unknowns": 322580, "kbar": 30.0, "sigma": 0.15, "restart": 50, "tol": 1e-8,
             "preconditioner": "mean-value I(x)S(xi_bar)", "source": "gaussian w=0.02 at (0.5,0.5)"}
 MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# generated complex64 operator kernel at 511 x 511, P = 84, from an ncu capture
+# (profiles/matvec_c64_511x511_s6_deg3.md).  Reported only while the generated
+# kernel source still has this SHA-256: a changed kernel reports null.
+MATVEC_TRAFFIC = {"sha256": "4be837e365e3ac14172caa1c496ecf55e26167d1d5d20286ec1358e8fb16a0c6",
+                  "bytes": 182964224 + 132611328}
+# Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
+# TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def nvtx(torch, name):
+    """Push an NVTX range (ncu --nvtx-include selects launches by it)."""
+    try:
+        torch.cuda.nvtx.range_push(name)
+        return True
+    except Exception:
+        return False
+
+
+def nvtx_pop(torch, pushed):
+    if pushed:
+        torch.cuda.nvtx.range_pop()
+
+
+def matvec_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2209_14740_gb300", "_build", "gen", "k_matvec_special.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return MATVEC_TRAFFIC["bytes"] if digest == MATVEC_TRAFFIC["sha256"] else None
 
 
 def load_peaks():
@@ -51,6 +84,14 @@ def load_peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def load_tensor_peak():
+    """TF32 dense TFLOP/s: measured BF16 burst peak x nominal TF32/BF16 ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]) * TF32_PER_BF16, "measured bf16 x nominal tf32/bf16"
+    return 1900.0 * TF32_PER_BF16, "fallback bf16 x nominal tf32/bf16"
 
 
 class ClockSampler:
@@ -290,6 +331,7 @@ def run_ours(args):
         clk.start()
     l0 = B.kernel_launches()
     times, infos = [], []
+    pushed = nvtx(torch, "timed")
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -301,6 +343,7 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1))
         infos.append(info)
     launches = B.kernel_launches() - l0
+    nvtx_pop(torch, pushed)
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop() if rank == 0 else None
@@ -322,6 +365,39 @@ def run_ours(args):
         e1.synchronize()
         t64.append(e0.elapsed_time(e1))
     fp64_ms = statistics.mean(t64)
+
+    # ---------------------------------------------------------------- dominant kernel of the step
+    # The FP32 preconditioner apply is four launches of the tensor-core
+    # transform kernel (k_tc_cgemm), each a complex GEMM of (P*m) x m by m x m.
+    # Timed on the solve's stream with CUDA events, 50 applies, L2 warm as in
+    # the solve (the vectors are L2-resident there too).
+    top = None
+    info_h = op.info
+    if info_h.get("fast_diag"):
+        Xp = torch.randn(N, dtype=torch.complex64, device=dev)
+        Zp = torch.empty_like(Xp)
+        for _ in range(3):
+            op.precond(Xp, Zp, B.PREC_MEAN, B.FP32)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 50
+        pushed = nvtx(torch, "precond")
+        e0.record(stream)
+        for _ in range(reps):
+            op.precond(Xp, Zp, B.PREC_MEAN, B.FP32)
+        e1.record(stream)
+        e1.synchronize()
+        nvtx_pop(torch, pushed)
+        t_launch = e0.elapsed_time(e1) / (4 * reps)            # ms per k_tc_cgemm launch
+        m = info_h["mx"]
+        flops = 8.0 * op.P * m * m * m                          # complex GEMM: 8 real flop per complex MAC
+        peak_t, peak_kind_t = load_tensor_peak()
+        ach = flops / (t_launch * 1e-3) / 1e12
+        top = {"kernel": "k_tc_cgemm (2D preconditioner transform, tcgen05 3xTF32)", "bound": "tensor",
+               "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t, "traffic": None,
+               "peak_kind": peak_kind_t, "us_per_launch": 1000.0 * t_launch,
+               "flops_per_launch": flops, "units": "8*P*m^3 real flop per launch (m = 127, P = 20)"}
+        del Xp, Zp
 
     # ---------------------------------------------------------------- end to end with host buffers
     bh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
@@ -446,11 +522,13 @@ def run_ours(args):
     if learned:
         line["learned"] = learned
     if mv:
+        tr = matvec_traffic()
+        mv["roofline"] = {"kernel": "k_mvt_s6r3 (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
+                          "achieved": mv["gbs"], "peak": mv["peak_gbs"], "unit": "GB/s",
+                          "frac": mv["gbs"] / mv["peak_gbs"], "traffic": tr, "peak_kind": mv["peak_kind"]}
         line["matvec"] = mv
-        line["roofline"] = {"kernel": "k_matvec (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
-                            "achieved": mv["gbs"], "peak": mv["peak_gbs"], "unit": "GB/s",
-                            "frac": mv["gbs"] / mv["peak_gbs"], "traffic": None,
-                            "peak_kind": mv["peak_kind"]}
+    if top:
+        line["roofline"] = top
     if world == 1 and not args.skip_cpu:
         times_c, its_c = oracle_solve_seconds(1)
         line["cpu_baseline"] = {"value": 1.0 / times_c[0], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",

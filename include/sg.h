@@ -110,6 +110,8 @@ typedef struct {
   int coupling_nnz;    /* nonzeros of the union P x P coupling pattern (incl. diagonal) */
   int separable;       /* 1 if k_0 is constant: 2D preconditioners available */
   int specialised;     /* 1 if a register-resident matvec kernel serves (s, r) */
+  int fast_diag;       /* 1 if FP32 2D preconditioner applies use the fast diagonalisation
+                          (both directions transformed, tensor-core GEMMs) */
 } sg_info;
 
 /* Builds the SG operator of Theorem 3.4 / Theorems A.1, A.2, A.5, A.6:

@@ -644,6 +644,7 @@ sg_status sg_get_info(const sg_handle* h, sg_info* info) {
   info->coupling_nnz = (int)h->col.size() + h->P;
   info->separable = h->separable ? 1 : 0;
   info->specialised = h->specialised;
+  info->fast_diag = h->fd ? 1 : 0;
   return SG_OK;
 }
 

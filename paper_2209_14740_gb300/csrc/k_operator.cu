@@ -19,6 +19,8 @@
 // and the coupling read shared memory; y-neighbours come through L1/L2.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "sg_internal.h"
 #include "k_operator_geom.cuh"
 
@@ -132,8 +134,14 @@ cudaError_t launch_matvec(const sg_handle* h, const C2<T>* X, C2<T>* Y, cudaStre
   if (per * blk > 220 * 1024) return cudaErrorInvalidConfiguration;
   const size_t smem = per * blk;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_matvec_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // one process-wide limit, set once: a per-call value would race between
+    // host threads (batched solves) and between capture and graph replay
+    static std::once_flag once;
+    static cudaError_t set_err = cudaSuccess;
+    std::call_once(once, [] {
+      set_err = cudaFuncSetAttribute(k_matvec_generic<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    });
+    if (set_err != cudaSuccess) return set_err;
   }
   OpParams<T> p;
   if constexpr (sizeof(T) == 8) p = h->op64(); else p = h->op32();

@@ -24,7 +24,13 @@ namespace sgi {
 static thread_local std::string g_err;
 static std::atomic<long long> g_launches{0};
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long thread_launches() { return t_launches; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 sg_status fail(sg_status st, const std::string& msg) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <complex>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -98,6 +99,17 @@ struct GmresWork {
   unsigned* counter = nullptr;
   int nblk = 0;            // blocks of the reduction kernels
   int cg_nblk = 0;         // blocks of the CGS2 passes
+  // Arnoldi step chunks captured as CUDA graphs, keyed by (inner precision,
+  // preconditioner, first step, steps): a key is captured on its second use
+  // and replayed from then on (one-shot solves never pay for instantiation).
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;   // kernel launches recorded in the graph
+  };
+  std::map<unsigned long long, Graph> graphs;
+  std::map<unsigned long long, int> graph_uses;
+  cudaStream_t stream = nullptr;   // private stream: capture needs a non-legacy stream
+  cudaEvent_t ev = nullptr;
 };
 
 }  // namespace sgi
@@ -172,6 +184,8 @@ cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R
 
 // launch bookkeeping (sg_kernel_launches)
 void note_launch();
+void note_launches(long long n);      // graph replays (n kernels) and capture corrections (-n)
+long long thread_launches();          // kernels noted by this host thread so far
 
 // true if a register-resident complex64 matvec kernel exists for (s, r)
 bool matvec_is_specialised(int s, int r);

@@ -596,6 +596,9 @@ using namespace sgi;
 
 void sgi_free_gmres_work(sg_handle* h) {
   GmresWork& w = h->gw;
+  for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (w.stream) cudaStreamDestroy(w.stream);
+  if (w.ev) cudaEventDestroy(w.ev);
   cudaFree(w.V); cudaFree(w.Z); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
   cudaFree(w.dscal); cudaFree(w.dctl); cudaFree(w.part); cudaFree(w.counter);
   w = GmresWork{};
@@ -638,6 +641,8 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   if (!e) e = cudaMalloc((void**)&w.part, part_doubles * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.counter, sizeof(unsigned));
   if (!e) e = cudaMemset(w.counter, 0, sizeof(unsigned));
+  if (!e) e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming);
   if (e) {
     sgi_free_gmres_work(h);
     return fail(SG_ENOMEM, std::string("GMRES workspace: ") + cudaGetErrorString(e));
@@ -703,6 +708,45 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   return cudaGetLastError();
 }
 
+// Arnoldi steps j0 .. j0+len-1: launched directly on the first use of the
+// chunk, captured into a CUDA graph on the second, replayed afterwards.  The
+// kernels read the done flag and skip their work once the cycle has ended, so
+// a replayed chunk is correct whichever step converges.
+template <typename T>
+cudaError_t arnoldi_steps(Ctx& c, sg_prec prec, int j0, int len) {
+  GmresWork& w = c.h->gw;
+  const unsigned long long key = ((unsigned long long)(sizeof(T) == 4) << 60) |
+                                 ((unsigned long long)prec << 56) | ((unsigned long long)j0 << 28) |
+                                 (unsigned long long)len;
+  auto it = w.graphs.find(key);
+  if (it == w.graphs.end()) {
+    if (++w.graph_uses[key] < 2) {
+      for (int j = j0; j < j0 + len; ++j) {
+        cudaError_t e = arnoldi_step<T>(c, prec, j);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    const long long t0 = thread_launches();
+    cudaError_t e = cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int j = j0; j < j0 + len && e == cudaSuccess; ++j) e = arnoldi_step<T>(c, prec, j);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c.st, &g);
+    const long long nk = thread_launches() - t0;
+    note_launches(-nk);   // recorded, not launched
+    if (e == cudaSuccess) e = e2;
+    GmresWork::Graph gr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gr.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    gr.kernels = nk;
+    it = w.graphs.emplace(key, gr).first;
+  }
+  note_launches(it->second.kernels);
+  return cudaGraphLaunch(it->second.exec, c.st);
+}
+
 // Runs one restart cycle whose starting residual is already in V[0] with its
 // squared norm in sc[RNORM2].  Leaves the correction u = M^-1 (V y) in Z.
 template <typename T>
@@ -714,13 +758,12 @@ sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int
   SG_CUDA_TRY(cudaStreamSynchronize(c.st));
   *any_step = false;
   if (done) return SG_OK;
-  for (int j = 0; j < m; ++j) {
-    SG_CUDA_TRY(arnoldi_step<T>(c, prec, j));
-    if ((j + 1) % check_every == 0 || j == m - 1) {
-      SG_CUDA_TRY(cudaMemcpyAsync(&done, w.dctl + CTL_DONE, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-      SG_CUDA_TRY(cudaStreamSynchronize(c.st));
-      if (done) break;
-    }
+  for (int j0 = 0; j0 < m; j0 += check_every) {
+    const int len = std::min(check_every, m - j0);
+    SG_CUDA_TRY(arnoldi_steps<T>(c, prec, j0, len));
+    SG_CUDA_TRY(cudaMemcpyAsync(&done, w.dctl + CTL_DONE, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    SG_CUDA_TRY(cudaStreamSynchronize(c.st));
+    if (done) break;
   }
   *any_step = true;
   C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
@@ -808,7 +851,20 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
   sg_status st0 = ensure_work(h, m, inner32 ? 8 : 16);
   if (st0 != SG_OK) return st0;
   GmresWork& w = h->gw;
-  cudaStream_t st = (cudaStream_t)stream;
+  // All work runs on the handle's private stream (stream capture needs a
+  // non-legacy stream), ordered after the caller's stream and joined back
+  // into it on every return.
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaStream_t st = w.stream;
+  SG_CUDA_TRY(cudaEventRecord(w.ev, caller));
+  SG_CUDA_TRY(cudaStreamWaitEvent(st, w.ev, 0));
+  struct Rejoin {
+    cudaEvent_t ev;
+    cudaStream_t from, to;
+    ~Rejoin() {
+      if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+    }
+  } rejoin{w.ev, st, caller};
   Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
   c.L = DevLayout(w.restart);
   // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
@@ -945,6 +1001,13 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
   }
   if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
   SG_CUDA_TRY(cudaStreamSynchronize(st));
+  int werr = 0;   // a bounded wait inside a kernel ran out (tensor-core transforms)
+  SG_CUDA_TRY(cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (werr) {
+    SG_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+    status = SG_ETIMEOUT;
+  }
   inf.iters = iters;
   inf.cycles = cycles;
   inf.outer = outer;
@@ -953,5 +1016,6 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
   if (info) *info = inf;
   if (status == SG_ENOTCONV) set_error("GMRES did not reach tol within maxit");
   if (status == SG_EBREAKDOWN) set_error("GMRES breakdown: non-finite values");
+  if (status == SG_ETIMEOUT) set_error("a device-side wait timed out in a preconditioner transform");
   return status;
 }

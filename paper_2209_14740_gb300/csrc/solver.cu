@@ -161,31 +161,62 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Warp sums of 16 values per lane with 16 shuffles (instead of 16 trees of
+// 5): each step halves the values a lane keeps and exchanges the other half
+// with the partner lane.  Afterwards lanes 2q and 2q+1 hold the warp sum of
+// value cg_value_of_lane(2q).
+template <typename T>
+__device__ __forceinline__ T warp_sum16(T (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, c = 16; o >= 2; o >>= 1, c >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < c / 2; ++k) {
+      const T send = up ? v[k] : v[k + c / 2];
+      const T keep = up ? v[k + c / 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ int cg_value_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
 // red[warp * nv + i] += warp sum of conj(V_i[e]) w_e over the thread's
-// elements of the chunk starting at `base`.
+// elements of the chunk starting at `base`, eight vectors at a time.
 template <typename T>
 __device__ __forceinline__ void chunk_dots(const C2<T>* __restrict__ V, long long N, int nv, long long base,
                                            const C2<T> (&wk)[CG_EPT], double2* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll 2
-  for (int i = 0; i < nv; ++i) {
-    const C2<T>* Vi = V + (size_t)i * N;
-    T ax = T(0), ay = T(0);
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    T acc[16];
 #pragma unroll
-    for (int k = 0; k < CG_EPT; ++k) {
-      const long long e = base + k * RED_THREADS;
-      if (e < N) {
-        const C2<T> v = __ldg(Vi + e);
-        ax += v.x * wk[k].x + v.y * wk[k].y;
-        ay += v.x * wk[k].y - v.y * wk[k].x;
+    for (int q = 0; q < 8; ++q) {
+      T ax = T(0), ay = T(0);
+      if (i0 + q < nv) {
+        const C2<T>* Vi = V + (size_t)(i0 + q) * N;
+#pragma unroll
+        for (int k = 0; k < CG_EPT; ++k) {
+          const long long e = base + k * RED_THREADS;
+          if (e < N) {
+            const C2<T> v = __ldg(Vi + e);
+            ax += v.x * wk[k].x + v.y * wk[k].y;
+            ay += v.x * wk[k].y - v.y * wk[k].x;
+          }
+        }
       }
+      acc[2 * q] = ax;
+      acc[2 * q + 1] = ay;
     }
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    if (lane == 0) {
-      double2& r = red[warp * nv + i];
-      r.x += (double)ax;
-      r.y += (double)ay;
+    const T sum = warp_sum16(acc);
+    if ((lane & 1) == 0) {
+      const int val = cg_value_of_lane(lane), i = i0 + (val >> 1);
+      if (i < nv) {
+        double2& r = red[warp * nv + i];
+        if (val & 1) r.y += (double)sum; else r.x += (double)sum;
+      }
     }
   }
 }

@@ -6,7 +6,11 @@ in csrc/k_operator.cu (Theorem 3.4 with Theorems A.1/A.2/A.5/A.6):
     (A X)_a(x) = (L X_a)(x) + sum_b M_ab(x) X_b(x),
     M(x) = -i w1 <k phi phi> - w2 <k^2 phi phi>,  k = k_0 + sum_l xi_l k_l,
 
-but with the chaos structure unrolled at compile time:
+but with the chaos structure unrolled at compile time.  The default kernels
+(gen_kernel_tk) factor the coupling through degree r + 1,
+<k phi phi> = T_k and <k^2 phi phi> = T_k^T T_k, which cuts the arithmetic
+of the per-term form (gen_kernel_tile, kept for comparison).  Common to
+both:
 
 * one thread per (grid unknown, real/imaginary component): it keeps its
   component of all P modes in registers, so X is read from HBM once and in
@@ -40,6 +44,15 @@ MINBLOCKS = 0        # __launch_bounds__ min blocks per SM (0 = none)
 STENCIL = "tile"     # "tile": 2D tile staged in shared memory; "split": coupling then stencil loop; "inline"
 SERIAL = True        # rows evaluated one after another (bounded register pressure)
 ROWS_PER_FENCE = 4   # tile mode: rows between register fences
+COUPLING = "tk"      # tile mode: "tk" = factorised through degree r + 1, "direct" = one product per term
+# Unknowns per CTA in x and y for 2D grids (two threads each).  Swept on GB300
+# over 16x4, 16x8, 32x4, 8x16, 32x8, 16x16, 64x4 and 32x16 for P = 10 ... 84:
+# 16x8 was fastest for every P (its halo is 37.5 % of the tile, 16x4's 62.5 %).
+TILE_2D = (16, 8)
+
+
+def tile_2d(P):
+    return TILE_2D
 
 
 def _multi_indices(s, r):
@@ -419,6 +432,164 @@ def gen_kernel_tile(s, r):
     return name, P, "\n".join(L)
 
 
+def gen_kernel_tk(s, r):
+    """Tiled variant with the coupling factorised through degree r + 1.
+
+    With K = sum_l k_l xi_l and k = k_0 + K, the Galerkin moments are
+    <k phi_a phi_b> = (T_k)_{ab} and <k^2 phi_a phi_b> = (T_k^T T_k)_{ab},
+    where T_k maps the degree <= r coefficients to degree <= r + 1:
+        (T_k X)_g = k_0 X_g + sum_l k_l (b_{g_l} X_{g - e_l} + b_{g_l + 1} X_{g + e_l})
+    (the three-term recurrence of the orthonormal Legendre polynomials; terms
+    outside degree <= r are absent).  This is exact: k phi_b lies in degree
+    <= r + 1, so the inner product over that space is the full expectation.
+    Each thread (one component of one unknown) forms W_g = (T_k X)_g for every
+    g of degree <= r + 1 and scatters -w2 T_k^T W into its P accumulators
+    straight away, so only X, the accumulators and one W value are live.  The
+    imaginary part, -i w1 (T_k X)_a, exists on absorbing boundary nodes only
+    and is exchanged with the partner lane there.  Then
+        Y_a = ldiag X_a - sum_nb w_nb X_a(nb) + Z_a.
+    The arithmetic per unknown is about 2 |T_k| + 6 P instead of one product
+    per coupling nonzero and term."""
+    al = _multi_indices(s, r)
+    ext = _multi_indices(s, r + 1)
+    P = len(al)
+    idx = {a: i for i, a in enumerate(al)}
+    name = "k_mvk_s%dr%d" % (s, r)
+    L = []
+    w = L.append
+
+    def xv(a):
+        return "x%d" % a
+
+    w("template <int TX, int TY>")
+    w("__global__ void __launch_bounds__(2 * TX * TY) %s(OpParams<float> p, const float* __restrict__ X, "
+      "float* __restrict__ Y) {" % name)
+    w("  constexpr int NT = 2 * TX * TY;            // threads = (unknown, component) pairs")
+    w("  constexpr int NH = 2 * (2 * TX + 2 * TY);  // halo entries per mode")
+    w("  constexpr int ST = NT + NH;                // shared-memory row stride per mode")
+    w("  extern __shared__ float xs[];              // [P][ST]: tile values, then halo values")
+    w("  if (p.skip && *p.skip) return;")
+    w("  const int t = threadIdx.x, c = t & 1, nid = t >> 1;")
+    w("  const int lx = nid % TX, ly = nid / TX;")
+    w("  const int iu0 = blockIdx.x * TX + lx, ju0 = blockIdx.y * TY + ly;")
+    w("  const bool valid = iu0 < p.mx && ju0 < p.my;")
+    w("  const int iu = min(iu0, p.mx - 1), ju = min(ju0, p.my - 1);")
+    w("  const int u = iu + p.mx * ju;")
+    w("  const long long n2 = 2ll * p.n;")
+    w("  const float* __restrict__ xp = X + 2ll * u + c;")
+    for a in range(P):
+        w("  float x%d = __ldg(xp + %d * n2);" % (a, a))
+    w("  {")
+    w("    constexpr int HALO_PER_THREAD = (%d * NH + NT - 1) / NT;" % P)
+    w("    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;")
+    w("    float hv[HALO_PER_THREAD];")
+    w("#pragma unroll")
+    w("    for (int i = 0; i < HALO_PER_THREAD; ++i) {")
+    w("      const int k = t + i * NT;")
+    w("      const int a = k / NH, e = k - a * NH, hc = e & 1, h = e >> 1;")
+    w("      int hx, hy;")
+    w("      if (h < TX) { hx = bx0 + h; hy = by0 - 1; }")
+    w("      else if (h < 2 * TX) { hx = bx0 + h - TX; hy = by0 + TY; }")
+    w("      else if (h < 2 * TX + TY) { hx = bx0 - 1; hy = by0 + h - 2 * TX; }")
+    w("      else { hx = bx0 + TX; hy = by0 + h - 2 * TX - TY; }")
+    w("      hv[i] = 0.0f;")
+    w("      if (k < %d * NH && hx >= 0 && hx < p.mx && hy >= 0 && hy < p.my)" % P)
+    w("        hv[i] = __ldg(X + (long long)a * n2 + 2ll * (hx + (long long)p.mx * hy) + hc);")
+    w("    }")
+    w("#pragma unroll")
+    w("    for (int i = 0; i < HALO_PER_THREAD; ++i) {")
+    w("      const int k = t + i * NT;")
+    w("      if (k < %d * NH) {" % P)
+    w("        const int a = k / NH, e = k - a * NH;")
+    w("        xs[a * ST + NT + e] = hv[i];")
+    w("      }")
+    w("    }")
+    w("  }")
+    for a in range(P):
+        w("  xs[%d * ST + t] = x%d;" % (a, a))
+    w("  const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
+    w("  const int oxm = lx > 0 ? t - 2 : NT + 2 * (2 * TX + ly) + c;")
+    w("  const int oxp = lx < TX - 1 ? t + 2 : NT + 2 * (2 * TX + TY + ly) + c;")
+    w("  const int oym = ly > 0 ? t - 2 * TX : NT + 2 * lx + c;")
+    w("  const int oyp = ly < TY - 1 ? t + 2 * TX : NT + 2 * (TX + lx) + c;")
+    w("  const float wxm = g.hxm ? g.wxm : 0.0f, wxp = g.hxp ? g.wxp : 0.0f;")
+    w("  const float wym = g.hym ? g.wym : 0.0f, wyp = g.hyp ? g.wyp : 0.0f;")
+    w("  const float k0 = __ldg(p.fields + u);")
+    for l in range(s):
+        w("  const float k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
+    w("  const float nw2 = -g.w2;")
+    # kb[l][n] = k_l * b_n, n = 1 .. r + 1
+    for l in range(s):
+        for n in range(1, r + 2):
+            w("  const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, _f(_b(n))))
+    w("  const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0f);")
+    w("  const float sw1 = c ? -g.w1 : g.w1;   // -i w1 W: re gets +w1 Im W, im gets -w1 Re W")
+    for a in range(P):
+        w("  float z%d = 0.0f;" % a)
+    w("  float* __restrict__ yp = Y + 2ll * u + c;")
+    w("  __syncthreads();")
+
+    def fence():
+        for i0 in range(0, P, 28):
+            ops = ", ".join('"+f"(x%d)' % i for i in range(i0, min(P, i0 + 28)))
+            w('  asm volatile("" : %s :: "memory");' % ops)
+
+    for gi, gm in enumerate(ext):
+        if gi % (2 * ROWS_PER_FENCE) == 0:
+            fence()
+        # W_g = k0 X_g + sum_l kb_l(g_l) X_{g-e_l} + kb_l(g_l+1) X_{g+e_l}
+        terms = []
+        if gm in idx:
+            terms.append(("k0", idx[gm]))
+        for l in range(s):
+            if gm[l] >= 1:
+                lo = list(gm)
+                lo[l] -= 1
+                terms.append(("kb%d_%d" % (l + 1, gm[l]), idx[tuple(lo)]))
+            hi = list(gm)
+            hi[l] += 1
+            if tuple(hi) in idx:
+                terms.append(("kb%d_%d" % (l + 1, gm[l] + 1), idx[tuple(hi)]))
+        if not terms:
+            continue
+        e = "%s * %s" % (terms[0][0], xv(terms[0][1]))
+        for cf, b in terms[1:]:
+            e = "fmaf(%s, %s, %s)" % (cf, xv(b), e)
+        w("  {  // g = %s" % (gm,))
+        w("    float wv = %s;" % e)
+        if gm in idx:
+            w("    if (bnd) z%d = fmaf(sw1, __shfl_xor_sync(0xffffffffu, wv, 1), z%d);" % (idx[gm], idx[gm]))
+        w("    wv *= nw2;")
+        # scatter T_k^T: Z_a += T_k[g][a] W_g for a = g, g - e_l, g + e_l in degree <= r
+        if gm in idx:
+            w("    z%d = fmaf(k0, wv, z%d);" % (idx[gm], idx[gm]))
+        for l in range(s):
+            if gm[l] >= 1:
+                lo = list(gm)
+                lo[l] -= 1
+                a = idx[tuple(lo)]
+                w("    z%d = fmaf(kb%d_%d, wv, z%d);" % (a, l + 1, gm[l], a))
+            hi = list(gm)
+            hi[l] += 1
+            if tuple(hi) in idx:
+                a = idx[tuple(hi)]
+                w("    z%d = fmaf(kb%d_%d, wv, z%d);" % (a, l + 1, gm[l] + 1, a))
+        w("  }")
+    fence()
+    for a in range(P):
+        w("  {")
+        w("    const float* q = xs + %d * ST;" % a)
+        w("    float y = fmaf(g.ldiag, %s, z%d);" % (xv(a), a))
+        w("    y = fmaf(-wxm, q[oxm], y);")
+        w("    y = fmaf(-wxp, q[oxp], y);")
+        w("    y = fmaf(-wym, q[oym], y);")
+        w("    y = fmaf(-wyp, q[oyp], y);")
+        w("    if (valid) yp[%d * n2] = y;" % a)
+        w("  }")
+    w("}")
+    return name, P, "\n".join(L)
+
+
 def gen_kernel_packed(s, r):
     """One thread per grid unknown holding both components (float2) of all P
     modes; the coupling uses packed FP32x2 FMAs (__ffma2_rn: the real
@@ -562,7 +733,10 @@ def generate(path: str) -> str:
              "}"]
     table = []
     for s, r in SPECIALISED:
-        name, P, src = gen_kernel_tile(s, r) if STENCIL == "tile" else gen_kernel(s, r)
+        if STENCIL == "tile":
+            name, P, src = gen_kernel_tk(s, r) if COUPLING == "tk" else gen_kernel_tile(s, r)
+        else:
+            name, P, src = gen_kernel(s, r)
         parts.append(src)
         table.append((s, r, name, P))
     if STENCIL == "tile":
@@ -597,7 +771,9 @@ def generate(path: str) -> str:
         parts.append("  if (h->s == %d && h->r == %d) {" % (s, r))
         parts.append("    *handled = true;")
         if STENCIL == "tile":
-            parts.append("    if (h->dim == 2) return launch_tile<16, 4>(%s<16, 4>, %d, h, p, X, Y, st);" % (name, P))
+            tx, ty = tile_2d(P)
+            parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"
+                         % (tx, ty, name, tx, ty, P))
             parts.append("    return launch_tile<64, 1>(%s<64, 1>, %d, h, p, X, Y, st);" % (name, P))
         else:
             parts.append("    %s<<<grid, %d, 0, st>>>(p, (const float*)X, (float*)Y); note_launch();" % (name, BLOCK))

@@ -45,9 +45,9 @@ WORKLOAD = {"workload": "helmholtz_2d_127x127_s3_deg3", "nodes": "127x127", "h":
 MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # generated complex64 operator kernel at 511 x 511, P = 84, from an ncu capture
-# (profiles/matvec_c64_511x511_s6_deg3.md).  Reported only while the generated
-# kernel source still has this SHA-256: a changed kernel reports null.
-MATVEC_TRAFFIC = {"sha256": "68d4ac7acfb5aa4f8f922ee6d282327e87101904863b79a350e4ddc6647f589b",
+# (profiles/matvec_c64_511x511_s6_deg3.md).  Reported only while the generator
+# still emits this kernel source (SHA-256 below): a changed kernel reports null.
+MATVEC_TRAFFIC = {"sha256": "9a4a75fd8a1d876a781efdfa70ee4861c1e9e9268ca02ff280f128e2d996fbd4",
                   "bytes": 182946816 + 132969472}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
@@ -70,11 +70,9 @@ def nvtx_pop(torch, pushed):
 
 def matvec_traffic():
     import hashlib
-    src = os.path.join(ROOT, "paper_2209_14740_gb300", "_build", "gen", "k_matvec_special.cu")
-    try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
+
+    from paper_2209_14740_gb300 import codegen_matvec
+    digest = hashlib.sha256(codegen_matvec.gen_kernel_tk(6, 3)[2].encode()).hexdigest()
     return MATVEC_TRAFFIC["bytes"] if digest == MATVEC_TRAFFIC["sha256"] else None
 
 
@@ -213,6 +211,76 @@ def run_reference(args):
             "gpu_launches": 0}
     print(json.dumps(line))
     return 0
+
+
+def cfg1_leg(B, torch, dev):
+    """1D workload (200 unknowns, Dirichlet / absorbing, k = 20 (1 + 0.1 xi),
+    degree 5, P = 6, N = 1200), mean-value preconditioner, GMRES(100) to
+    relres 1e-8 (latency bound: one solve is a few dozen tiny kernels).  Mixed
+    precision (FP32 Arnoldi, FP64 refinement) and plain FP64; single solves
+    replay CUDA graphs, the batch runs 256 copies concurrently (mixed)."""
+    from paper_2209_14740_gb300 import inputs
+    pr = inputs.helmholtz_1d_c1()
+    op = B.SG(pr)
+    b = torch.empty(op.N, dtype=torch.complex128, device=dev)
+    op.rhs(b, B.FP64)
+    x = torch.zeros_like(b)
+    out = {"workload": "1D: 200 unknowns, k = 20(1 + 0.1 xi), degree 5 (P = 6, N = 1200), mean-value, "
+                       "GMRES(100), tol 1e-8"}
+    for name, mode in (("mixed", B.MIXED), ("fp64", B.FP64)):
+        kw = dict(restart=100, tol=1e-8, prec=B.PREC_MEAN, mode=mode)
+        for _ in range(3):
+            info = op.gmres(b, x, **kw)
+        torch.cuda.synchronize()
+        reps = 50
+        t1 = time.perf_counter()
+        for _ in range(reps):
+            info = op.gmres(b, x, **kw)
+        torch.cuda.synchronize()
+        out[name] = {"solves_per_s": reps / (time.perf_counter() - t1), "iterations": info["iters"],
+                     "relres": info["relres"], "converged": bool(info["status"] == B.SG_OK)}
+    kw = dict(restart=100, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED)
+    ops = [B.SG(pr) for _ in range(256)]
+    bs = [b.clone() for _ in ops]
+    xs = [torch.zeros_like(b) for _ in ops]
+    B.gmres_batched(ops, bs, xs, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st, inf = B.gmres_batched(ops, bs, xs, **kw)
+    torch.cuda.synchronize()
+    out["mixed_batched_256_solves_per_s"] = len(ops) / (time.perf_counter() - t1)
+    out["batched_all_converged"] = bool(st == B.SG_OK)
+    for o in ops:
+        o.close()
+    op.close()
+    return out
+
+
+def cfg3_leg(B, torch, dev):
+    """511 x 511, s = 6, degree 3 (P = 84, N = 21,934,164): mixed-precision
+    GMRES(30) to relres 1e-8, mean-value preconditioner (tridiagonal path:
+    lines of 511 unknowns), one warm-up and two timed solves."""
+    from paper_2209_14740_gb300 import inputs
+    op = B.SG(inputs.config_2d_511())
+    b = torch.empty(op.N, dtype=torch.complex128, device=dev)
+    op.rhs(b, B.FP64)
+    x = torch.zeros_like(b)
+    kw = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, maxit=3000)
+    info = op.gmres(b, x, **kw)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for _ in range(2):
+        info = op.gmres(b, x, **kw)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    op.close()
+    return {"workload": "helmholtz_2d_511x511_s6_deg3 (P=84, N=21,934,164), mixed GMRES(30), mean-value, tol 1e-8",
+            "ms": ms, "solves_per_s": 1000.0 / ms, "iterations": info["iters"], "outer": info["outer"],
+            "relres": info["relres"], "converged": bool(info["status"] == B.SG_OK)}
 
 
 def learned_leg(args, B, torch, dev):
@@ -497,6 +565,12 @@ def run_ours(args):
             op.close()
         del bs, xs
 
+    # ---------------------------------------------------------------- the other two paper-shaped workloads
+    cfg1 = cfg3 = None
+    if rank == 0 and not args.skip_configs:
+        cfg1 = cfg1_leg(B, torch, dev)
+        cfg3 = cfg3_leg(B, torch, dev)
+
     # ---------------------------------------------------------------- learned initial guess + batched + mixed
     learned = None
     if rank == 0 and not args.skip_learned:
@@ -521,6 +595,10 @@ def run_ours(args):
         line["batched"] = batched
     if learned:
         line["learned"] = learned
+    if cfg1:
+        line["cfg1_1d"] = cfg1
+    if cfg3:
+        line["cfg3_511"] = cfg3
     if mv:
         tr = matvec_traffic()
         mv["roofline"] = {"kernel": "k_mvk_s6r3<16, 8> (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
@@ -548,6 +626,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-learned", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true", help="skip the 1D and 511x511 solve legs")
     ap.add_argument("--learned-train", type=int, default=4096, help="training solves of the warm-start network")
     ap.add_argument("--learned-test", type=int, default=256, help="held-out solves of the warm-start leg")
     args = ap.parse_args()

@@ -45,6 +45,10 @@ STENCIL = "tile"     # "tile": 2D tile staged in shared memory; "split": couplin
 SERIAL = True        # rows evaluated one after another (bounded register pressure)
 ROWS_PER_FENCE = 4   # tile mode: rows between register fences
 COUPLING = "tk"      # tile mode: "tk" = factorised through degree r + 1, "direct" = one product per term
+# FP64 kernels are generated for P up to this (two registers per value: the
+# mode values and accumulators of larger P do not fit)
+F64_MAX_P = 35
+
 # Unknowns per CTA in x and y for 2D grids (two threads each).  Swept on GB300
 # over 16x4, 16x8, 32x4, 8x16, 32x8, 16x16, 64x4 and 32x16 for P = 10 ... 84:
 # 16x8 was fastest for every P (its halo is 37.5 % of the tile, 16x4's 62.5 %).
@@ -432,7 +436,7 @@ def gen_kernel_tile(s, r):
     return name, P, "\n".join(L)
 
 
-def gen_kernel_tk(s, r):
+def gen_kernel_tk(s, r, prec="f32"):
     """Tiled variant with the coupling factorised through degree r + 1.
 
     With K = sum_l k_l xi_l and k = k_0 + K, the Galerkin moments are
@@ -454,7 +458,8 @@ def gen_kernel_tk(s, r):
     ext = _multi_indices(s, r + 1)
     P = len(al)
     idx = {a: i for i, a in enumerate(al)}
-    name = "k_mvk_s%dr%d" % (s, r)
+    name = ("k_mvk_s%dr%d" if prec == "f32" else "k_mvk64_s%dr%d") % (s, r)
+    lit = _f if prec == "f32" else (lambda v: "%.17e" % v)
     L = []
     w = L.append
 
@@ -521,7 +526,7 @@ def gen_kernel_tk(s, r):
     # kb[l][n] = k_l * b_n, n = 1 .. r + 1
     for l in range(s):
         for n in range(1, r + 2):
-            w("  const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, _f(_b(n))))
+            w("  const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, lit(_b(n))))
     w("  const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0f);")
     w("  const float sw1 = c ? -g.w1 : g.w1;   // -i w1 W: re gets +w1 Im W, im gets -w1 Re W")
     for a in range(P):
@@ -587,7 +592,17 @@ def gen_kernel_tk(s, r):
         w("    if (valid) yp[%d * n2] = y;" % a)
         w("  }")
     w("}")
-    return name, P, "\n".join(L)
+    src = "\n".join(L)
+    if prec == "f64":
+        # the same kernel on complex128 data: FP64 registers, shared memory
+        # and arithmetic (the Legendre constants are printed to 17 digits)
+        for a_, b_ in (("float", "double"), ("fmaf(", "fma("), ("0.0f", "0.0"), ('"+f"', '"+d"')):
+            src = src.replace(a_, b_)
+        # one extern shared array per element type in a translation unit
+        src = src.replace("  extern __shared__ double xs[];",
+                          "  extern __shared__ __align__(16) unsigned char xs64_raw[];\n"
+                          "  double* xs = reinterpret_cast<double*>(xs64_raw);")
+    return name, P, src
 
 
 def gen_kernel_packed(s, r):
@@ -732,6 +747,7 @@ def generate(path: str) -> str:
              "  return z;",
              "}"]
     table = []
+    table64 = []
     for s, r in SPECIALISED:
         if STENCIL == "tile":
             name, P, src = gen_kernel_tk(s, r) if COUPLING == "tk" else gen_kernel_tile(s, r)
@@ -739,23 +755,27 @@ def generate(path: str) -> str:
             name, P, src = gen_kernel(s, r)
         parts.append(src)
         table.append((s, r, name, P))
+        if STENCIL == "tile" and COUPLING == "tk" and P <= F64_MAX_P:
+            name64, _, src64 = gen_kernel_tk(s, r, "f64")
+            parts.append(src64)
+            table64.append((s, r, name64, P))
     if STENCIL == "tile":
         parts += [
             "// Launch of a tiled kernel: 2D problems use 16 x 4 unknowns per CTA,",
             "// 1D problems 64 x 1; dynamic shared memory holds P rows of",
             "// (tile + halo) values.",
-            "template <int TX, int TY>",
-            "static cudaError_t launch_tile(void (*kern)(OpParams<float>, const float*, float*), int P,",
-            "                               const sg_handle* h, const OpParams<float>& p, const float2* X, float2* Y,",
+            "template <int TX, int TY, typename T>",
+            "static cudaError_t launch_tile(void (*kern)(OpParams<T>, const T*, T*), int P,",
+            "                               const sg_handle* h, const OpParams<T>& p, const C2<T>* X, C2<T>* Y,",
             "                               cudaStream_t st) {",
             "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
-            "  const size_t smem = (size_t)P * (nt + nh) * sizeof(float);",
+            "  const size_t smem = (size_t)P * (nt + nh) * sizeof(T);",
             "  if (smem > 48 * 1024) {",
             "    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
             "    if (e != cudaSuccess) return e;",
             "  }",
             "  dim3 grid((h->mx + TX - 1) / TX, (h->my + TY - 1) / TY);",
-            "  kern<<<grid, nt, smem, st>>>(p, (const float*)X, (float*)Y);",
+            "  kern<<<grid, nt, smem, st>>>(p, (const T*)X, (T*)Y);",
             "  note_launch();",
             "  return cudaGetLastError();",
             "}",
@@ -778,6 +798,21 @@ def generate(path: str) -> str:
         else:
             parts.append("    %s<<<grid, %d, 0, st>>>(p, (const float*)X, (float*)Y); note_launch();" % (name, BLOCK))
             parts.append("    return cudaGetLastError();")
+        parts.append("  }")
+    parts.append("  return cudaSuccess;")
+    parts.append("}")
+    parts.append("cudaError_t matvec_special_f64(const sg_handle* h, const double2* X, double2* Y, cudaStream_t st,")
+    parts.append("                               const int* skip, bool* handled) {")
+    parts.append("  *handled = false;")
+    parts.append("  OpParams<double> p = h->op64();")
+    parts.append("  p.skip = skip;")
+    for s, r, name, P in table64:
+        tx, ty = tile_2d(P)
+        parts.append("  if (h->s == %d && h->r == %d) {" % (s, r))
+        parts.append("    *handled = true;")
+        parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"
+                     % (tx, ty, name, tx, ty, P))
+        parts.append("    return launch_tile<64, 1>(%s<64, 1>, %d, h, p, X, Y, st);" % (name, P))
         parts.append("  }")
     parts.append("  return cudaSuccess;")
     parts.append("}")

@@ -120,12 +120,16 @@ static size_t generic_smem_per_thread(const sg_handle* h) {
 
 cudaError_t matvec_special_f32(const sg_handle* h, const float2* X, float2* Y, cudaStream_t st, const int* skip,
                                bool* handled);
+cudaError_t matvec_special_f64(const sg_handle* h, const double2* X, double2* Y, cudaStream_t st, const int* skip,
+                               bool* handled);
 
 template <typename T>
 cudaError_t launch_matvec(const sg_handle* h, const C2<T>* X, C2<T>* Y, cudaStream_t st, const int* skip) {
-  if constexpr (sizeof(T) == 4) {
+  {
     bool handled = false;
-    cudaError_t e = matvec_special_f32(h, X, Y, st, skip, &handled);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) e = matvec_special_f32(h, X, Y, st, skip, &handled);
+    else e = matvec_special_f64(h, X, Y, st, skip, &handled);
     if (handled || e != cudaSuccess) return e;
   }
   const size_t per = generic_smem_per_thread<T>(h);

@@ -20,6 +20,8 @@
 //     parallel instead of mx * P sequential sweeps of length my.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "sg_internal.h"
 
 namespace sgi {
@@ -216,6 +218,78 @@ __global__ void k_tri_solve(int nsys, int nrhs, int len, long long sR, long long
   }
 }
 
+// 1D block solve for a few right-hand sides: the factors and this CTA's
+// right-hand sides are staged in shared memory (coalesced), one thread per
+// right-hand side sweeps forward and back in shared memory (a dependent step
+// costs a shared-memory latency instead of a global one), then the CTA writes
+// the solutions back.  Same gttrs steps as k_tri_solve; in place in shared
+// memory (step j writes row j after reading row j+1).  R and Z may coincide.
+template <typename T>
+__global__ void __launch_bounds__(256) k_tri_solve_1d(int n, int P, int rhs_per_cta, TriFactors<T> F,
+                                                      const C2<T>* R, C2<T>* Z,
+                                                      const int* skip, const double* in_scale) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C2<T>* sdl = reinterpret_cast<C2<T>*>(smraw);
+  C2<T>* sdu = sdl + n;
+  C2<T>* sdu2 = sdu + n;
+  C2<T>* sdinv = sdu2 + n;
+  C2<T>* sx = sdinv + n;                                   // [rhs][n + 1]
+  uint8_t* spiv = reinterpret_cast<uint8_t*>(sx + (size_t)rhs_per_cta * (n + 1));
+  const int p0 = blockIdx.x * rhs_per_cta, np = min(rhs_per_cta, P - p0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sdl[i] = F.dl[i];
+    sdu[i] = F.du[i];
+    sdu2[i] = F.du2[i];
+    sdinv[i] = F.dinv[i];
+    spiv[i] = F.piv[i];
+  }
+  const T s0 = in_scale ? (T)*in_scale : T(1);
+  for (int i = threadIdx.x; i < np * n; i += blockDim.x) {
+    const int q = i / n, j = i - q * n;
+    sx[q * (n + 1) + j] = cscale<T>(R[(size_t)p0 * n + i], s0);
+  }
+  __syncthreads();
+  if (threadIdx.x < np) {
+    C2<T>* x = sx + threadIdx.x * (n + 1);
+    C2<T> cur = x[0];
+    for (int j = 0; j + 1 < n; ++j) {
+      const C2<T> rn = x[j + 1], l = sdl[j];
+      if (!spiv[j]) {
+        x[j] = cur;
+        cur = csub<T>(rn, cmul<T>(l, cur));
+      } else {
+        x[j] = rn;
+        cur = csub<T>(cur, cmul<T>(l, rn));
+      }
+    }
+    C2<T> x1 = cmul<T>(cur, sdinv[n - 1]), x2;
+    x2.x = T(0);
+    x2.y = T(0);
+    x[n - 1] = x1;
+    for (int j = n - 2; j >= 0; --j) {
+      C2<T> b = csub<T>(x[j], cmul<T>(sdu[j], x1));
+      b = csub<T>(b, cmul<T>(sdu2[j], x2));
+      const C2<T> xj = cmul<T>(b, sdinv[j]);
+      x[j] = xj;
+      x2 = x1;
+      x1 = xj;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < np * n; i += blockDim.x) {
+    const int q = i / n, j = i - q * n;
+    Z[(size_t)p0 * n + i] = sx[q * (n + 1) + j];
+  }
+}
+
+// Shared memory of k_tri_solve_1d for rhs right-hand sides of length n.
+template <typename T>
+static size_t tri1d_smem(int n, int rhs) {
+  return (size_t)n * (4 * sizeof(C2<T>) + 1) + (size_t)rhs * (n + 1) * sizeof(C2<T>) + 16;
+}
+constexpr size_t kTri1dSmemMax = 200 * 1024;
+
 // ---------------------------------------------------------------- batched complex GEMM
 // C_b = A_b B_b for b = blockIdx.z, complex, row-major with row strides lda,
 // ldb, ldc and batch strides sA, sB, sC (0: operand shared by the batch).
@@ -361,7 +435,21 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
   TriFactors<T> F;
   if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;
   if (h->dim == 1) {
-    // one system of length n, P right-hand sides (the modes); out of place
+    // one system of length n, P right-hand sides (the modes)
+    const int n = h->n, P = h->P;
+    if (tri1d_smem<T>(n, 1) <= kTri1dSmemMax) {
+      static std::once_flag once;
+      std::call_once(once, [] {
+        cudaFuncSetAttribute(k_tri_solve_1d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTri1dSmemMax);
+      });
+      int rhs = 1;
+      while (rhs < P && rhs < 256 && tri1d_smem<T>(n, rhs + 1) <= kTri1dSmemMax) ++rhs;
+      const int grid = (P + rhs - 1) / rhs;
+      k_tri_solve_1d<T><<<grid, 256, tri1d_smem<T>(n, rhs), st>>>(n, P, rhs, F, R, Z, skip, in_scale);
+      note_launch();
+      return cudaGetLastError();
+    }
+    // longer lines: sweeps from global memory, out of place
     dim3 b(1, 64), g(1, (h->P + 63) / 64);
     C2<T>* out = (R == Z) ? tmp : Z;
     k_tri_solve<T><<<g, b, 0, st>>>(1, h->P, h->n, h->n, 1, 0, F, nullptr, R, out, skip, in_scale);
@@ -398,13 +486,27 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
   const T* dyinv;
   if constexpr (sizeof(T) == 8) { Q = h->d_Q; Qt = h->d_Qt; dyinv = h->d_dyinv; }
   else { Q = h->d_Q32; Qt = h->d_Qt32; dyinv = h->d_dyinv32; }
-  cudaError_t e = cgemm<T>(h, P * my, mx, mx, R, mx, 0, Q, mx, 0, tmp, mx, 0, 1, st, skip);   // (1)
+  // FP32: the x transforms on the tensor cores (factors built at set-up for
+  // lines longer than the fast-diagonalisation limit); FP64: CUDA cores
+  bool tcx = false;
+  if constexpr (sizeof(T) == 4) tcx = h->tcB[0].hi != nullptr && h->tcB[3].hi != nullptr;
+  cudaError_t e = cudaSuccess;
+  if (tcx) {
+    if constexpr (sizeof(T) == 4)
+      e = tc_cgemm(h->tcB[0], R, mx, P * my, tmp, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st);   // (1)
+  } else {
+    e = cgemm<T>(h, P * my, mx, mx, R, mx, 0, Q, mx, 0, tmp, mx, 0, 1, st, skip);   // (1)
+  }
   if (e != cudaSuccess) return e;
   dim3 b(32, 8), g((mx + 31) / 32, (P + 7) / 8);                     // (2) sys = i, rhs = mode, j = y line
   k_tri_solve<T><<<g, b, 0, st>>>(mx, P, my, plane, mx, 1, F, dyinv, tmp, tmp2, skip, in_scale);
   note_launch();
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (tcx) {
+    if constexpr (sizeof(T) == 4)
+      return tc_cgemm(h->tcB[3], tmp2, mx, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st);   // (3)
+  }
   return cgemm<T>(h, P * my, mx, mx, tmp2, mx, 0, Qt, mx, 0, Z, mx, 0, 1, st, skip);        // (3)
 }
 

@@ -446,6 +446,26 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
     // pencil (the same matrix as x on a square grid).  Four GEMMs replace
     // two GEMMs and mx * P sequential tridiagonal solves; worth it while
     // the lines are short (the GEMM work grows with mx^2).
+    if (mx > kFdMaxLine || my > kFdMaxLine) {
+      // longer lines keep the tridiagonal sweeps along y, but the two x
+      // transforms of the FP32 apply still run on the tensor cores
+      std::vector<cd> qx((size_t)mx * mx), qxt((size_t)mx * mx);
+      for (int a = 0; a < mx; ++a)
+        for (int b = 0; b < mx; ++b) {
+          const cd v = Q[(size_t)a * mx + b] / std::sqrt(px.d[a]);
+          qx[(size_t)a * mx + b] = v;
+          qxt[(size_t)b * mx + a] = v;
+        }
+      const std::vector<cd>* facs[2] = {&qx, &qxt};
+      const int slot[2] = {0, 3};
+      for (int t = 0; t < 2; ++t) {
+        TcOperand op = tc_make_operand(*facs[t], mx, mx);
+        TcDevOperand& d = h->tcB[slot[t]];
+        d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles;
+        if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()))
+          return fail(SG_ENOMEM, "precond upload");
+      }
+    }
     if (mx <= kFdMaxLine && my <= kFdMaxLine) {
       std::vector<cd> lamy, Qy;
       bool ok = true;

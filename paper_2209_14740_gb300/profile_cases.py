@@ -41,6 +41,7 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["matvec", "precond", "solve"])
+    ap.add_argument("--dim", type=int, default=2, choices=[1, 2], help="1: the 1D workload with --g unknowns")
     ap.add_argument("--g", type=int, default=127)
     ap.add_argument("--s", type=int, default=3)
     ap.add_argument("--r", type=int, default=3)
@@ -55,7 +56,10 @@ def main(argv=None):
 
     B.load()
     dev = torch.device("cuda", 0)
-    op = B.SG(inputs.helmholtz_2d(a.g, a.s, a.r, a.kbar, a.sigma))
+    if a.dim == 1:
+        op = B.SG(inputs.helmholtz_1d_c1(n_unknowns=a.g, r=a.r))
+    else:
+        op = B.SG(inputs.helmholtz_2d(a.g, a.s, a.r, a.kbar, a.sigma))
     prec = B.FP32 if a.prec == "fp32" else B.FP64
     cdt = torch.complex64 if prec == B.FP32 else torch.complex128
     gen = torch.Generator(device=dev).manual_seed(0)

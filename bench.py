@@ -140,33 +140,18 @@ class ClockSampler:
 
 
 def dist_setup(gpus: int):
-    import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    return world, rank, local
+    from paper_2209_14740_gb300 import replicas
+    return replicas.init()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2209_14740_gb300 import replicas
+    replicas.barrier(world)
 
 
 def max_over_ranks(v: float, world: int) -> float:
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2209_14740_gb300 import replicas
+    return replicas.max_over_ranks(v, world)
 
 
 def oracle_solve_seconds(repeats: int = 1):
@@ -416,7 +401,8 @@ def run_ours(args):
     barrier(world)
     clocks = clk.stop() if rank == 0 else None
     ms = max_over_ranks(statistics.mean(times), world)
-    value = world * 1000.0 / ms
+    from paper_2209_14740_gb300 import replicas
+    value = replicas.whole_job_rate(1.0, ms / 1000.0, world)   # one solve per step per rank
     ok = all(i["status"] == B.SG_OK and i["relres"] <= 1e-8 for i in infos)
 
     # ---------------------------------------------------------------- plain FP64 GPU GMRES, same workload

@@ -48,6 +48,9 @@ COUPLING = "tk"      # tile mode: "tk" = factorised through degree r + 1, "direc
 # FP64 kernels are generated for P up to this (two registers per value: the
 # mode values and accumulators of larger P do not fit)
 F64_MAX_P = 35
+# larger P: mode values in shared memory, accumulators in two parts; 16 x 4
+# unknowns per CTA keep P (tile + halo) FP64 values under the shared limit
+F64_HALVES_TILE = (16, 4)
 
 # Unknowns per CTA in x and y for 2D grids (two threads each).  Swept on GB300
 # over 16x4, 16x8, 32x4, 8x16, 32x8, 16x16, 64x4 and 32x16 for P = 10 ... 84:
@@ -605,6 +608,150 @@ def gen_kernel_tk(s, r, prec="f32"):
     return name, P, src
 
 
+def gen_kernel_tk64_halves(s, r, halves=3):
+    """FP64 factorised kernel for chaos sizes whose FP64 mode values and
+    accumulators do not fit in registers together.  The tile and its halo are
+    copied to shared memory by cp.async (no registers held in flight); the
+    accumulators are built for one part of the modes at a time, each part
+    recomputing the W_g it needs from shared memory.  Same arithmetic as
+    gen_kernel_tk otherwise (see there)."""
+    al = _multi_indices(s, r)
+    ext = _multi_indices(s, r + 1)
+    P = len(al)
+    idx = {a: i for i, a in enumerate(al)}
+    name = "k_mvk64h_s%dr%d" % (s, r)
+    lit = lambda v: "%.17e" % v
+    L = []
+    w = L.append
+    w("template <int TX, int TY>")
+    w("__global__ void __launch_bounds__(2 * TX * TY) %s(OpParams<double> p, const double* __restrict__ X, "
+      "double* __restrict__ Y) {" % name)
+    w("  constexpr int NT = 2 * TX * TY;")
+    w("  constexpr int NH = 2 * (2 * TX + 2 * TY);")
+    w("  constexpr int ST = NT + NH;")
+    w("  extern __shared__ __align__(16) unsigned char xs64h_raw[];")
+    w("  double* xs = reinterpret_cast<double*>(xs64h_raw);   // [P][ST]")
+    w("  if (p.skip && *p.skip) return;")
+    w("  const int t = threadIdx.x, c = t & 1, nid = t >> 1;")
+    w("  const int lx = nid % TX, ly = nid / TX;")
+    w("  const int iu0 = blockIdx.x * TX + lx, ju0 = blockIdx.y * TY + ly;")
+    w("  const bool valid = iu0 < p.mx && ju0 < p.my;")
+    w("  const int iu = min(iu0, p.mx - 1), ju = min(ju0, p.my - 1);")
+    w("  const int u = iu + p.mx * ju;")
+    w("  const long long n2 = 2ll * p.n;")
+    w("  const double* __restrict__ xp = X + 2ll * u + c;")
+    w("  {")
+    w("    const unsigned xs0 = (unsigned)__cvta_generic_to_shared(xs);")
+    w("    for (int a = 0; a < %d; ++a)" % P)
+    w('      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(xs0 + 8u * (a * ST + t)), '
+      '"l"(xp + a * n2) : "memory");')
+    w("    const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;")
+    w("    for (int k = t; k < %d * NH; k += NT) {" % P)
+    w("      const int a = k / NH, e = k - a * NH, hc = e & 1, h = e >> 1;")
+    w("      int hx, hy;")
+    w("      if (h < TX) { hx = bx0 + h; hy = by0 - 1; }")
+    w("      else if (h < 2 * TX) { hx = bx0 + h - TX; hy = by0 + TY; }")
+    w("      else if (h < 2 * TX + TY) { hx = bx0 - 1; hy = by0 + h - 2 * TX; }")
+    w("      else { hx = bx0 + TX; hy = by0 + h - 2 * TX - TY; }")
+    w("      const bool in = hx >= 0 && hx < p.mx && hy >= 0 && hy < p.my;")
+    w("      const double* src = in ? X + (long long)a * n2 + 2ll * (hx + (long long)p.mx * hy) + hc : X;")
+    w('      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(xs0 + 8u * (a * ST + NT + e)), '
+      '"l"(src), "r"(in ? 8 : 0) : "memory");')
+    w("    }")
+    w('    asm volatile("cp.async.wait_all;" ::: "memory");')
+    w("  }")
+    w("  const NodeGeom<double> g = node_geom<double>(p, iu, ju);")
+    w("  const int oxm = lx > 0 ? t - 2 : NT + 2 * (2 * TX + ly) + c;")
+    w("  const int oxp = lx < TX - 1 ? t + 2 : NT + 2 * (2 * TX + TY + ly) + c;")
+    w("  const int oym = ly > 0 ? t - 2 * TX : NT + 2 * lx + c;")
+    w("  const int oyp = ly < TY - 1 ? t + 2 * TX : NT + 2 * (TX + lx) + c;")
+    w("  const double wxm = g.hxm ? g.wxm : 0.0, wxp = g.hxp ? g.wxp : 0.0;")
+    w("  const double wym = g.hym ? g.wym : 0.0, wyp = g.hyp ? g.wyp : 0.0;")
+    w("  const double k0 = __ldg(p.fields + u);")
+    for l in range(s):
+        w("  const double k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
+    w("  const double nw2 = -g.w2;")
+    for l in range(s):
+        for n in range(1, r + 2):
+            w("  const double kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, lit(_b(n))))
+    w("  const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0);")
+    w("  const double sw1 = c ? -g.w1 : g.w1;")
+    w("  double* __restrict__ yp = Y + 2ll * u + c;")
+    w("  __syncthreads();")
+
+    def xv(a):
+        return "xs[%d * ST + t]" % a
+
+    bounds = [round(P * h / halves) for h in range(halves + 1)]
+    for hp in range(halves):
+        lo_a, hi_a = bounds[hp], bounds[hp + 1]
+        part = set(range(lo_a, hi_a))
+        w("  {  // modes %d .. %d" % (lo_a, hi_a - 1))
+        for a in range(lo_a, hi_a):
+            w("    double z%d = 0.0;" % a)
+        for gm in ext:
+            terms = []
+            if gm in idx:
+                terms.append(("k0", idx[gm]))
+            for l in range(s):
+                if gm[l] >= 1:
+                    lo = list(gm)
+                    lo[l] -= 1
+                    terms.append(("kb%d_%d" % (l + 1, gm[l]), idx[tuple(lo)]))
+                hi = list(gm)
+                hi[l] += 1
+                if tuple(hi) in idx:
+                    terms.append(("kb%d_%d" % (l + 1, gm[l] + 1), idx[tuple(hi)]))
+            # targets of the scatter inside this part
+            scat = []
+            if gm in idx and idx[gm] in part:
+                scat.append(("k0", idx[gm]))
+            for l in range(s):
+                if gm[l] >= 1:
+                    lo = list(gm)
+                    lo[l] -= 1
+                    if idx[tuple(lo)] in part:
+                        scat.append(("kb%d_%d" % (l + 1, gm[l]), idx[tuple(lo)]))
+                hi = list(gm)
+                hi[l] += 1
+                if tuple(hi) in idx and idx[tuple(hi)] in part:
+                    scat.append(("kb%d_%d" % (l + 1, gm[l] + 1), idx[tuple(hi)]))
+            own = gm in idx and idx[gm] in part
+            if not terms or (not scat and not own):
+                continue
+            e = "%s * %s" % (terms[0][0], xv(terms[0][1]))
+            for cf, b in terms[1:]:
+                e = "fma(%s, %s, %s)" % (cf, xv(b), e)
+            w('    asm volatile("" ::: "memory");')
+            w("    {")
+            w("      double wv = %s;" % e)
+            if own:
+                w("      if (bnd) z%d = fma(sw1, __shfl_xor_sync(0xffffffffu, wv, 1), z%d);" % (idx[gm], idx[gm]))
+            w("      wv *= nw2;")
+            for cf, a in scat:
+                w("      z%d = fma(%s, wv, z%d);" % (a, cf, a))
+            w("    }")
+        w('    asm volatile("" ::: "memory");')
+        # running store pointer, opaque to the compiler: the P store addresses
+        # are formed one at a time instead of all up front
+        w("    double* yq = yp + %d * n2;" % lo_a)
+        for a in range(lo_a, hi_a):
+            w("    {")
+            w("      const double* q = xs + %d * ST;" % a)
+            w("      double y = fma(g.ldiag, %s, z%d);" % (xv(a), a))
+            w("      y = fma(-wxm, q[oxm], y);")
+            w("      y = fma(-wxp, q[oxp], y);")
+            w("      y = fma(-wym, q[oym], y);")
+            w("      y = fma(-wyp, q[oyp], y);")
+            w("      if (valid) *yq = y;")
+            w("      yq += n2;")
+            w('      asm volatile("" : "+l"(yq));')
+            w("    }")
+        w("  }")
+    w("}")
+    return name, P, "\n".join(L)
+
+
 def gen_kernel_packed(s, r):
     """One thread per grid unknown holding both components (float2) of all P
     modes; the coupling uses packed FP32x2 FMAs (__ffma2_rn: the real
@@ -755,10 +902,14 @@ def generate(path: str) -> str:
             name, P, src = gen_kernel(s, r)
         parts.append(src)
         table.append((s, r, name, P))
-        if STENCIL == "tile" and COUPLING == "tk" and P <= F64_MAX_P:
-            name64, _, src64 = gen_kernel_tk(s, r, "f64")
+        if STENCIL == "tile" and COUPLING == "tk":
+            if P <= F64_MAX_P:
+                name64, _, src64 = gen_kernel_tk(s, r, "f64")
+                table64.append((s, r, name64, P, tile_2d(P)))
+            else:
+                name64, _, src64 = gen_kernel_tk64_halves(s, r)
+                table64.append((s, r, name64, P, F64_HALVES_TILE))
             parts.append(src64)
-            table64.append((s, r, name64, P))
     if STENCIL == "tile":
         parts += [
             "// Launch of a tiled kernel: 2D problems use 16 x 4 unknowns per CTA,",
@@ -806,8 +957,7 @@ def generate(path: str) -> str:
     parts.append("  *handled = false;")
     parts.append("  OpParams<double> p = h->op64();")
     parts.append("  p.skip = skip;")
-    for s, r, name, P in table64:
-        tx, ty = tile_2d(P)
+    for s, r, name, P, (tx, ty) in table64:
         parts.append("  if (h->s == %d && h->r == %d) {" % (s, r))
         parts.append("    *handled = true;")
         parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"

@@ -46,6 +46,7 @@ def problems():
         inputs.helmholtz_2d(19, 2, 4, 8.0, 0.2),
         _dirichlet_2d(),
         _rect_2d(),
+        inputs.helmholtz_2d(13, 6, 3, 10.0, 0.1),     # P = 84: the largest generated kernels (FP32 and FP64)
     ]
 
 

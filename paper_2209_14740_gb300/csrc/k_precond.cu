@@ -426,8 +426,9 @@ static cudaError_t cgemm(const sg_handle* h, int M, int Nn, int K, const C2<T>* 
   return cudaGetLastError();
 }
 
-// Z = M^-1 R for block `which`; tmp and tmp2 hold N complex values of type T
-// each (tmp2 only for 2D).  R and Z may be the same vector.
+// Z = M^-1 R for block `which`; tmp and tmp2 hold N complex128 values each
+// (tmp2 only for 2D; the FP32 2D transforms use up to 2N complex64 of each
+// for their even-length rows).  R and Z may be the same vector.
 template <typename T>
 static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                  const int* skip, const double* in_scale, C2<T>* tmp, C2<T>* tmp2) {
@@ -470,14 +471,20 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
       //   (2) T2'_p = L^-1 o (T1'_p Qhat_y)   [p][i][j], L^-1 indexed (j, i)
       //   (3) T3_p  = (T2'_p Qhat_y^T)^T      [p][y][i]
       //   (4) Z_p   = T3_p Qhat_x^T           [p][y][x]
-      cudaError_t e = tc_cgemm(h->tcB[0], R, mx, P * my, tmp, 0, 1, my, nullptr, 0, 1, nullptr, skip, h->d_err, st);
+      // The intermediates keep rows of even length (my or mx rounded up to
+      // even), so the next transform reads them with 16-byte copies; their
+      // P mx myp or P my mxp complex values fit in the scratch of N
+      // complex128 (= 2N complex64).
+      const int mxp = mx + (mx & 1), myp = my + (my & 1);
+      cudaError_t e =
+          tc_cgemm(h->tcB[0], R, mx, P * my, tmp, myp, 1, my, nullptr, 0, 1, nullptr, skip, h->d_err, st);
       if (e == cudaSuccess)
-        e = tc_cgemm(h->tcB[1], tmp, my, P * mx, tmp2, my, 0, 0, h->d_Linv32[which], mx, mx, in_scale, skip,
+        e = tc_cgemm(h->tcB[1], tmp, myp, P * mx, tmp2, myp, 0, 0, h->d_Linv32[which], mx, mx, in_scale, skip,
                      h->d_err, st);
       if (e == cudaSuccess)
-        e = tc_cgemm(h->tcB[2], tmp2, my, P * mx, tmp, 0, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st);
+        e = tc_cgemm(h->tcB[2], tmp2, myp, P * mx, tmp, mxp, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st);
       if (e == cudaSuccess)
-        e = tc_cgemm(h->tcB[3], tmp, mx, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st);
+        e = tc_cgemm(h->tcB[3], tmp, mxp, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st);
       return e;
     }
   }
@@ -517,8 +524,9 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
                           reinterpret_cast<C2<T>*>(h->d_tmp2));
 }
 
-// Same preconditioner apply with caller-provided scratch: tmp and tmp2 hold
-// at least N complex values of type T each (tmp2 is used by 2D problems only).
+// Same preconditioner apply with caller-provided scratch: tmp and tmp2 each
+// hold at least N complex128 values (2N complex64 when T is float; tmp2 is
+// used by 2D problems only).
 // Used by the allocation-free entry point.
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,

@@ -1,6 +1,6 @@
 // Complex GEMM with a constant right factor on the 5th-generation tensor
 // cores (tcgen05, TF32 inputs, FP32 accumulation in tensor memory), used by
-// the fast-diagonalisation transforms of the 2D preconditioner.
+// the transforms of the 2D preconditioner.
 //
 //   C = X Q,  X: M x K complex64 rows (the data), Q: K x N complex (constant)
 //
@@ -15,15 +15,19 @@
 // Xlo Bhi; the dropped Xlo Blo term is below FP32 rounding.  B's split is
 // precomputed on the host, X's is formed per tile in shared memory.
 //
-// One CTA owns 128 rows and 64 real output columns; the accumulator (128
-// lanes x 64 columns FP32) lives in tensor memory.  K is walked in stages
-// of 32 real values.  Eight loader warps copy raw X rows by cp.async (two
-// stages ahead), split them into hi/lo in the canonical K-major layout
-// (8-row x 16-byte core matrices, no swizzle) and copy the pre-laid-out B
-// tiles; one lane of a ninth warp issues the 12 MMAs of each stage (M=128,
-// N=64, K=8) and commits them to an mbarrier.  Every wait is bounded: on a
-// timeout the kernel records it, drains its copies, frees tensor memory and
-// returns.
+// One CTA owns 128 rows and BN (64 or 128) real output columns; the
+// accumulator (128 lanes x BN columns FP32) lives in tensor memory.  K is
+// walked in stages of 32 real values.  Warp roles:
+//   warps 0-7  copy raw X rows by cp.async (two stages ahead; 16-byte copies
+//              when the row pitch allows), split them into hi/lo in the
+//              canonical K-major layout (8-row x 16-byte core matrices, no
+//              swizzle), and run the epilogue;
+//   warp 8     one lane issues the 12 MMAs of each stage (M=128, N=BN, K=8)
+//              and commits them to an mbarrier;
+//   warp 9     one lane copies the pre-laid-out B tiles (hi and lo) of each
+//              stage with bulk asynchronous copies completing on an mbarrier.
+// Every wait is bounded: on a timeout the kernel records it, drains its
+// copies, frees tensor memory and returns.
 #include <cuda_runtime.h>
 
 #include <complex>
@@ -38,26 +42,41 @@ namespace sgi {
 namespace tc {
 
 constexpr int BM = 128;                 // rows per CTA = TMEM lanes
-constexpr int BN = 64;                  // real output columns per CTA = TMEM columns
 constexpr int BK = 32;                  // real K values per stage (128 bytes of FP32)
-constexpr int NLOAD = 256;              // loader / splitter threads (warps 0-7)
-constexpr int THREADS = NLOAD + 32;     // + one MMA warp
+constexpr int NLOAD = 256;              // loader / splitter / epilogue threads (warps 0-7)
+constexpr int MMA_WARP = NLOAD / 32;    // warp 8
+constexpr int THREADS = NLOAD + 64;     // + the MMA warp and the B-copy warp
 constexpr int NRAW = 3;                 // raw X slots: stages s, s+1, s+2 in flight
-constexpr int NBS = 4;                  // B slots: stage s-1 may still be read by its MMAs
 constexpr int NAS = 2;                  // split A (hi, lo) slots
+constexpr int NDONE = 4;                // MMA-completion barriers, indexed by stage % 4
 constexpr int RAW_PITCH = 144;          // bytes per raw X row (128 + 16: conflict-free split reads)
 constexpr int RAW_TILE = BM * RAW_PITCH;
 constexpr int A_TILE = BM * BK * 4;     // 16 KB, core-matrix layout
-constexpr int B_TILE = BN * BK * 4;     // 8 KB, core-matrix layout
 constexpr int OFF_RAW = 0;
-constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;              // [slot][hi, lo]
-constexpr int OFF_A = ((OFF_B + NBS * 2 * B_TILE + 1023) / 1024) * 1024;   // [slot][hi, lo]
-constexpr int OFF_BAR = OFF_A + NAS * 2 * A_TILE;             // full[NAS], done[NBS], TMEM address, abort flag
-constexpr int SMEM_BYTES = OFF_BAR + 128 + 1024;              // + slack for 1024-byte alignment
-constexpr int OUT_PITCH = BN / 2 + 1;                         // float2 per staged output row
-static_assert(BM * OUT_PITCH * 8 <= NRAW * RAW_TILE, "output staging must fit in the raw slots");
-static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
-constexpr uint32_t TMEM_COLS = 64;
+constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;   // [slot][hi, lo]
+
+// Layout that depends on the tile width.
+template <int BN>
+struct Cfg {
+  // B slots: a slot is refilled once the MMAs of the stage that used it
+  // have completed, so more slots let the copies run further ahead
+  static constexpr int NBS = BN == 64 ? 4 : 3;
+  static constexpr int B_TILE = BN * BK * 4;                     // 8 or 16 KB
+  static constexpr int OFF_A = ((OFF_B + NBS * 2 * B_TILE + 1023) / 1024) * 1024;   // [slot][hi, lo]
+  static constexpr int OFF_BAR = OFF_A + NAS * 2 * A_TILE;      // full[NAS], bfull[NBS], done[NDONE], TMEM addr, abort
+  static constexpr int SMEM_BYTES = OFF_BAR + 128 + 1024;        // + slack for 1024-byte alignment
+  static constexpr int OUT_PITCH = BN / 2 + 1;                   // float2 per staged output row
+  static constexpr uint32_t TMEM_COLS = BN;
+  // Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
+  // N = BN, M = BM.
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN == 64 || BN == 128, "tile width");
+  // the row-major output is staged over the raw and B slots (free by then)
+  static_assert(BM * OUT_PITCH * 8 <= OFF_A, "output staging must fit below the A slots");
+  static_assert(8 * (NAS + NBS + NDONE) + 16 <= 128, "barrier area");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+};
 
 // Byte offset of element (row, k) of a tile with 32 K values per row in the
 // no-swizzle K-major layout: core matrix (row / 8, k / 4) at 128-byte
@@ -76,16 +95,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
          (1ull << 46);
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
-// N = BN, M = BM.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -101,7 +115,8 @@ __device__ __forceinline__ uint64_t now_ns() {
 }
 
 // Waits for the phase with the given parity of an mbarrier; false after
-// about 0.5 s (the MMAs of one stage take well under a microsecond).
+// about 0.5 s (the copies and MMAs of one stage take well under a
+// microsecond).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   const uint64_t t0 = now_ns();
   for (uint32_t it = 0;; ++it) {
@@ -116,11 +131,31 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+// Arrive once and announce `bytes` of asynchronous copies on the barrier.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bulk global -> shared copy (16-byte aligned addresses, size a multiple of
+// 16) that completes its bytes on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+// 16-byte copy; bytes < 16 fills the rest of the destination with zeros
+__device__ __forceinline__ void cp_async16z(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -136,15 +171,17 @@ __device__ __forceinline__ float tf32_hi(float x) {
 
 // Output placement of C (complex, Nc columns):
 //   mode 0: C[m * ldc + n]
-//   mode 1: row m = p * MB + r goes to C[(p * Nc + n) * MB + r] (the
-//           per-batch transpose used to switch the transformed direction)
+//   mode 1: row m = p * MB + r goes to C[(p * Nc + n) * ldc + r] (the
+//           per-batch transpose used to switch the transformed direction;
+//           ldc >= MB is the pitch of the transposed rows)
 // With E: C *= E[n * e_ld + m % e_mod] * (*escale).
 struct TcArgs {
   const float* X;      // M rows of 2K floats, row stride ldx floats
   long long ldx;
   int M, K2;           // rows, real K (2K)
   int nks;             // K stages (ceil(K2 / 32)); B is laid out for nks stages
-  const float* Bhi;    // [n tile][stage][64 x 32 core-matrix tile]
+  int vec16;           // X 16-byte aligned and ldx a multiple of 4 floats
+  const float* Bhi;    // [n tile][stage][BN x 32 core-matrix tile]
   const float* Blo;
   int Nc;              // complex output columns
   float2* C;
@@ -157,7 +194,7 @@ struct TcArgs {
   int* err;            // set to 1 on a wait timeout
 };
 
-// Named barrier of the loader warps (the MMA warp does not take part).
+// Named barrier of the loader warps (the MMA and copy warps do not take part).
 __device__ __forceinline__ void loader_sync() { asm volatile("bar.sync 1, %0;" ::"n"(tc::NLOAD) : "memory"); }
 
 // Loader barrier that also ORs a flag over the loaders, so that every loader
@@ -172,31 +209,34 @@ __device__ __forceinline__ bool loader_sync_or(bool v) {
   return r != 0;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
-}
-
 // Pipeline (stage s = 32 real K values):
-//   loaders:  wait raw/B of s landed -> wait MMA(s-2) (frees A slot s%2)
-//             -> split raw -> A slot, arrive full[s%2] -> issue copies of s+2
-//   MMA lane: wait full[s%2] -> 12 MMAs (3xTF32 x 4 K steps) -> commit done[s%4]
+//   loaders:  wait raw X of s landed -> wait MMA(s-2) (frees A slot s%2)
+//             -> split raw -> A slot, arrive full[s%2] -> issue X copies of s+2
+//   B copier: wait MMA(s-NBS) (frees B slot s%NBS) -> bulk-copy B hi/lo of s
+//   MMA lane: wait full[s%2] and bfull[s%NBS] -> 12 MMAs (3xTF32 x 4 K steps)
+//             -> commit done[s%4]
 // so the split of stage s+1 and the copies of later stages overlap the MMAs
-// of stage s.
+// of stage s.  No waiter can fall two phases behind on a barrier: the MMA
+// lane runs at most two stages ahead of the loaders and cannot pass the copier.
+template <int BN>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   using namespace tc;
+  using L = Cfg<BN>;
+  constexpr int NBS = L::NBS, B_TILE = L::B_TILE;
   if (a.skip && *a.skip) return;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t s_base = smem_u32(sm);
-  const uint32_t full0 = s_base + OFF_BAR;              // NAS barriers, count NLOAD
-  const uint32_t done0 = full0 + 8 * NAS;               // NBS barriers, count 1 (MMA commit)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8 * (NAS + NBS));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_BAR + 8 * (NAS + NBS) + 8);
+  const uint32_t full0 = s_base + L::OFF_BAR;    // NAS barriers, count NLOAD
+  const uint32_t bfull0 = full0 + 8 * NAS;       // NBS barriers, count 1 + transaction bytes
+  const uint32_t done0 = bfull0 + 8 * NBS;       // NDONE barriers, count 1 (MMA commit)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::OFF_BAR + 8 * (NAS + NBS + NDONE));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::OFF_BAR + 8 * (NAS + NBS + NDONE) + 8);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(TMEM_COLS)
+                 "r"(L::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -204,6 +244,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     for (int i = 0; i < NAS; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * i), "n"(NLOAD) : "memory");
     for (int i = 0; i < NBS; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bfull0 + 8 * i) : "memory");
+    for (int i = 0; i < NDONE; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done0 + 8 * i) : "memory");
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -215,30 +257,32 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   const int m0 = blockIdx.x * BM;
   const int nks = a.nks;
 
-  if (warp < NLOAD / 32) {
+  if (warp < MMA_WARP) {
     // ---------------------------------------------------------------- loaders
-    const float* Bh = a.Bhi + (size_t)blockIdx.y * nks * (BN * BK);
-    const float* Bl = a.Blo + (size_t)blockIdx.y * nks * (BN * BK);
     auto issue = [&](int t) {
       const uint32_t raw = s_base + OFF_RAW + (t % NRAW) * RAW_TILE;
       const int k0 = t * BK;
+      if (a.vec16) {
 #pragma unroll
-      for (int q = 0; q < (BM * BK / 2) / NLOAD; ++q) {
-        const int idx = tid + q * NLOAD;
-        const int r = idx >> 4, kp = idx & 15;
-        const int m = m0 + r, k = k0 + 2 * kp;
-        const bool ok = m < a.M && k < a.K2;
-        const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
-        cp_async8(raw + r * RAW_PITCH + kp * 8, src, ok ? 8 : 0);
-      }
-      const uint32_t bh = s_base + OFF_B + (t % NBS) * 2 * B_TILE;
-      const float* gh = Bh + (size_t)t * (BN * BK);
-      const float* gl = Bl + (size_t)t * (BN * BK);
+        for (int q = 0; q < (BM * BK / 4) / NLOAD; ++q) {
+          const int idx = tid + q * NLOAD;
+          const int r = idx >> 3, c = idx & 7;
+          const int m = m0 + r, k = k0 + 4 * c;
+          const int rem = (a.K2 - k) * 4;
+          const int bytes = (m < a.M && rem > 0) ? (rem < 16 ? rem : 16) : 0;
+          const float* src = bytes ? a.X + (size_t)m * a.ldx + k : a.X;
+          cp_async16z(raw + r * RAW_PITCH + c * 16, src, bytes);
+        }
+      } else {
 #pragma unroll
-      for (int q = 0; q < (BN * BK / 4) / NLOAD; ++q) {
-        const int c = tid + q * NLOAD;
-        cp_async16(bh + c * 16, gh + 4 * c);
-        cp_async16(bh + B_TILE + c * 16, gl + 4 * c);
+        for (int q = 0; q < (BM * BK / 2) / NLOAD; ++q) {
+          const int idx = tid + q * NLOAD;
+          const int r = idx >> 4, kp = idx & 15;
+          const int m = m0 + r, k = k0 + 2 * kp;
+          const bool ok = m < a.M && k < a.K2;
+          const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
+          cp_async8(raw + r * RAW_PITCH + kp * 8, src, ok ? 8 : 0);
+        }
       }
     };
     for (int t = 0; t < 2; ++t) {
@@ -249,13 +293,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     for (int s = 0; s < nks; ++s) {
       cp_wait<1>();
       bool to = false;
-      if (s >= 2) to = !mbar_wait(done0 + 8 * ((s - 2) % NBS), ((s - 2) / NBS) & 1);
+      if (s >= 2) to = !mbar_wait(done0 + 8 * ((s - 2) % NDONE), ((s - 2) / NDONE) & 1);
       if (loader_sync_or(to || *abort_flag != 0)) { bad = true; break; }
       // split X into hi / lo: two threads per row, four 16-byte chunks each
       {
         const int row = tid & (BM - 1), half = tid >> 7;
         const unsigned char* raw = sm + OFF_RAW + (s % NRAW) * RAW_TILE + row * RAW_PITCH;
-        unsigned char* ahi = sm + OFF_A + (s % NAS) * 2 * A_TILE;
+        unsigned char* ahi = sm + L::OFF_A + (s % NAS) * 2 * A_TILE;
         unsigned char* alo = ahi + A_TILE;
 #pragma unroll
         for (int cc = 0; cc < BK / 8; ++cc) {
@@ -272,106 +316,139 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(full0 + 8 * (s % NAS));
-      // the raw slot of stage s+2 was split at s-1; its B slot was read by
-      // MMA(s-2), waited for above
+      // the raw slot of stage s+2 was split at s-1 by every loader (all of
+      // them passed the barrier above since)
       if (s + 2 < nks) issue(s + 2);
       cp_commit();
     }
     // all MMAs done before the accumulator is read
-    if (!bad && nks > 0 && !mbar_wait(done0 + 8 * ((nks - 1) % NBS), ((nks - 1) / NBS) & 1)) bad = true;
+    if (!bad && nks > 0 && !mbar_wait(done0 + 8 * ((nks - 1) % NDONE), ((nks - 1) / NDONE) & 1)) bad = true;
     cp_wait<0>();
     bad = loader_sync_or(bad || *abort_flag != 0);
     if (bad) {
       *abort_flag = 1;
-      if (tid == 0) atomicExch(a.err, 1);
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int n0 = blockIdx.y * (BN / 2);   // first complex column of the tile
+      // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the
+      // tile) and real columns [w / 4 * BN / 2, + BN / 2), 32 at a time.
+      constexpr int HALF = BN / 2;       // real columns per warp
+      const int lg = warp & 3, chalf = warp >> 2;
+      const int row = lg * 32 + lane, m = m0 + row;
+      const bool mok = m < a.M;
+      const int nq0 = blockIdx.y * (BN / 2) + chalf * (HALF / 2);   // first complex column of this warp
+      const int mr = (mok ? m : 0) % a.e_mod;
+      const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
       float2* stage = reinterpret_cast<float2*>(sm + OFF_RAW);
-      if (warp < 4) {
-        // warps 0-3 read TMEM lanes 32w..32w+31 (rows of the tile)
-        const int row = warp * 32 + lane, m = m0 + row;
-        float2 e[BN / 2];
-        if (a.E) {
-          const int mr = (m < a.M ? m : 0) % a.e_mod;
+      float2* cb = nullptr;   // mode 1: this row's element of column nq0
+      if (a.mode == 1 && mok) {
+        const int p = m / a.MB, r = m - p * a.MB;
+        cb = a.C + ((size_t)p * a.Nc + nq0) * a.ldc + r;
+      }
+      const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(chalf * HALF);
 #pragma unroll
-          for (int q = 0; q < BN / 2; ++q)
-            e[q] = (n0 + q < a.Nc) ? a.E[(size_t)(n0 + q) * a.e_ld + mr] : make_float2(0.f, 0.f);
-        }
-        const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
-        uint32_t v[BN];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-        for (int j0 = 0; j0 < BN; j0 += 16)
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-              "%13, %14, %15}, [%16];"
-              : "=r"(v[j0 + 0]), "=r"(v[j0 + 1]), "=r"(v[j0 + 2]), "=r"(v[j0 + 3]), "=r"(v[j0 + 4]),
-                "=r"(v[j0 + 5]), "=r"(v[j0 + 6]), "=r"(v[j0 + 7]), "=r"(v[j0 + 8]), "=r"(v[j0 + 9]),
-                "=r"(v[j0 + 10]), "=r"(v[j0 + 11]), "=r"(v[j0 + 12]), "=r"(v[j0 + 13]), "=r"(v[j0 + 14]),
-                "=r"(v[j0 + 15])
-              : "r"(taddr + (uint32_t)j0));
+      for (int j0 = 0; j0 < HALF; j0 += 32) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+            "[%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr + (uint32_t)j0));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float2 c[BN / 2];
 #pragma unroll
-        for (int q = 0; q < BN / 2; ++q) {
-          c[q] = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
-          if (a.E)
-            c[q] = make_float2(es * (c[q].x * e[q].x - c[q].y * e[q].y), es * (c[q].x * e[q].y + c[q].y * e[q].x));
-        }
-        if (a.mode == 1) {
-          // per-batch transpose: lanes hold consecutive rows r, so each
-          // store instruction writes consecutive addresses
-          if (m < a.M) {
-            const int p = m / a.MB, r = m - p * a.MB;
-#pragma unroll
-            for (int q = 0; q < BN / 2; ++q)
-              if (n0 + q < a.Nc) a.C[((size_t)p * a.Nc + n0 + q) * a.MB + r] = c[q];
+        for (int q = 0; q < 16; ++q) {
+          const int qq = j0 / 2 + q;        // complex column within this warp's half
+          const int n = nq0 + qq;
+          float2 c = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+          if (a.E) {
+            const float2 e = n < a.Nc ? a.E[(size_t)n * a.e_ld + mr] : make_float2(0.f, 0.f);
+            c = make_float2(es * (c.x * e.x - c.y * e.y), es * (c.x * e.y + c.y * e.x));
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < BN / 2; ++q) stage[row * OUT_PITCH + q] = c[q];
+          if (a.mode == 1) {
+            // lanes hold consecutive rows r: each store writes consecutive addresses
+            if (mok && n < a.Nc) cb[(size_t)qq * a.ldc] = c;
+          } else {
+            stage[row * L::OUT_PITCH + chalf * (HALF / 2) + qq] = c;
+          }
         }
       }
       if (a.mode == 0) {
         // row-major: all loader warps write the staged rows, consecutive
         // lanes on consecutive columns
         loader_sync();
+        const int n0 = blockIdx.y * (BN / 2);
         for (int idx = tid; idx < BM * (BN / 2); idx += NLOAD) {
           const int rr = idx / (BN / 2), q = idx % (BN / 2);
           const int mm = m0 + rr, n = n0 + q;
-          if (mm < a.M && n < a.Nc) a.C[(size_t)mm * a.ldc + n] = stage[rr * OUT_PITCH + q];
+          if (mm < a.M && n < a.Nc) a.C[(size_t)mm * a.ldc + n] = stage[rr * L::OUT_PITCH + q];
         }
       }
     }
-  } else if (lane == 0) {
+  } else if (warp == MMA_WARP) {
     // ---------------------------------------------------------------- MMA issue
-    for (int s = 0; s < nks; ++s) {
-      if (!mbar_wait(full0 + 8 * (s % NAS), (s / NAS) & 1)) { *abort_flag = 1; break; }
-      if (*abort_flag) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ahi = s_base + OFF_A + (s % NAS) * 2 * A_TILE, alo = ahi + A_TILE;
-      const uint32_t bhi = s_base + OFF_B + (s % NBS) * 2 * B_TILE, blo = bhi + B_TILE;
+    if (lane == 0) {
+      int last = -1;
+      for (int s = 0; s < nks; ++s) {
+        if (!mbar_wait(full0 + 8 * (s % NAS), (s / NAS) & 1)) { *abort_flag = 1; break; }
+        if (!mbar_wait(bfull0 + 8 * (s % NBS), (s / NBS) & 1)) { *abort_flag = 1; break; }
+        if (*abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ahi = s_base + L::OFF_A + (s % NAS) * 2 * A_TILE, alo = ahi + A_TILE;
+        const uint32_t bhi = s_base + OFF_B + (s % NBS) * 2 * B_TILE, blo = bhi + B_TILE;
 #pragma unroll
-      for (int ks = 0; ks < BK / 8; ++ks) {
-        const uint32_t o = 256u * ks;   // 8 TF32 = two core matrices along K
-        mma_tf32(tmem, sdesc(ahi + o), sdesc(bhi + o), (s > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), 1u);
-        mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), 1u);
+        for (int ks = 0; ks < BK / 8; ++ks) {
+          const uint32_t o = 256u * ks;   // 8 TF32 = two core matrices along K
+          mma_tf32(tmem, sdesc(ahi + o), sdesc(bhi + o), L::IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), L::IDESC, 1u);
+          mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), L::IDESC, 1u);
+        }
+        mma_commit(done0 + 8 * (s % NDONE));
+        last = s;
       }
-      mma_commit(done0 + 8 * (s % NBS));
+      // the accumulator must not be freed under running MMAs (matters only
+      // when a wait gave up: the loaders wait for this otherwise)
+      if (last >= 0 && !mbar_wait(done0 + 8 * (last % NDONE), (last / NDONE) & 1)) *abort_flag = 1;
     }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- B copies
+    const float* Bh = a.Bhi + (size_t)blockIdx.y * nks * (BN * BK);
+    const float* Bl = a.Blo + (size_t)blockIdx.y * nks * (BN * BK);
+    int issued = 0;
+    for (int t = 0; t < nks; ++t) {
+      if (t >= NBS && !mbar_wait(done0 + 8 * ((t - NBS) % NDONE), ((t - NBS) / NDONE) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const uint32_t bar = bfull0 + 8 * (t % NBS);
+      const uint32_t dst = s_base + OFF_B + (t % NBS) * 2 * B_TILE;
+      mbar_expect_tx(bar, 2u * B_TILE);
+      bulk_g2s(dst, Bh + (size_t)t * (BN * BK), B_TILE, bar);
+      bulk_g2s(dst + B_TILE, Bl + (size_t)t * (BN * BK), B_TILE, bar);
+      issued = t + 1;
+    }
+    // no copy may still be writing shared memory when the CTA exits: wait
+    // for the last copy into every slot
+    for (int t = issued > NBS ? issued - NBS : 0; t < issued; ++t)
+      if (!mbar_wait(bfull0 + 8 * (t % NBS), (t / NBS) & 1)) *abort_flag = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS)
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ host side
 // B layout for C = X Q with Q (kdim x ndim complex, row-major, FP64 on the
-// host): nt = ceil(2 ndim / 64) column tiles, nks = ceil(2 kdim / 32) K
-// stages, each (tile, stage) a 64 x 32 block in core-matrix order.
+// host) and tile width bn: nt = ceil(2 ndim / bn) column tiles, nks =
+// ceil(2 kdim / 32) K stages, each (tile, stage) a bn x 32 block in
+// core-matrix order.
 static float tf32_round_host(float x) {
   uint32_t u;
   std::memcpy(&u, &x, 4);
@@ -382,22 +459,23 @@ static float tf32_round_host(float x) {
   return r;
 }
 
-TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim) {
+TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim, int bn) {
   using namespace tc;
   TcOperand op;
   op.kdim = kdim;
   op.ndim = ndim;
+  op.bn = bn;
   op.nks = (2 * kdim + BK - 1) / BK;
-  op.ntiles = (2 * ndim + BN - 1) / BN;
-  const size_t per = (size_t)BN * BK;
+  op.ntiles = (2 * ndim + bn - 1) / bn;
+  const size_t per = (size_t)bn * BK;
   op.hi.assign(per * op.nks * op.ntiles, 0.0f);
   op.lo.assign(per * op.nks * op.ntiles, 0.0f);
   for (int nt = 0; nt < op.ntiles; ++nt)
     for (int ks = 0; ks < op.nks; ++ks) {
       const size_t blk = ((size_t)nt * op.nks + ks) * per;
-      for (int row = 0; row < BN; ++row)
+      for (int row = 0; row < bn; ++row)
         for (int k = 0; k < BK; ++k) {
-          const int nr = nt * BN + row, kr = ks * BK + k;   // real column of C, real K index
+          const int nr = nt * bn + row, kr = ks * BK + k;   // real column of C, real K index
           double v = 0.0;
           if (nr < 2 * ndim && kr < 2 * kdim) {
             const std::complex<double> q = Q[(size_t)(kr >> 1) * ndim + (nr >> 1)];
@@ -414,16 +492,26 @@ TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, 
   return op;
 }
 
+int tc_tile_width(long long rows, int ndim, int num_sms) {
+  // 128 columns halve the re-reads of X but give half as many CTAs: use
+  // them only while every SM still gets two tiles of the narrow form
+  const long long tiles64 = ((rows + tc::BM - 1) / tc::BM) * ((2LL * ndim + 63) / 64);
+  return tiles64 >= 2LL * num_sms ? 128 : 64;
+}
+
 static void tc_attributes() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_tc_cgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<64>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<128>::SMEM_BYTES);
   });
 }
 
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
                      int* err, cudaStream_t st) {
+  if (B.bn != 64 && B.bn != 128) return cudaErrorInvalidValue;
+  if (mode == 1 && (MB <= 0 || ldc < MB)) return cudaErrorInvalidValue;
   tc_attributes();
   TcArgs a;
   a.X = reinterpret_cast<const float*>(X);
@@ -431,6 +519,7 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   a.M = M;
   a.K2 = 2 * B.kdim;
   a.nks = B.nks;
+  a.vec16 = (ldx % 2 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) ? 1 : 0;
   a.Bhi = B.hi;
   a.Blo = B.lo;
   a.Nc = B.ndim;
@@ -445,7 +534,10 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   a.skip = skip;
   a.err = err;
   dim3 grid((M + tc::BM - 1) / tc::BM, B.ntiles);
-  k_tc_cgemm<<<grid, tc::THREADS, tc::SMEM_BYTES, st>>>(a);
+  if (B.bn == 128)
+    k_tc_cgemm<128><<<grid, tc::THREADS, tc::Cfg<128>::SMEM_BYTES, st>>>(a);
+  else
+    k_tc_cgemm<64><<<grid, tc::THREADS, tc::Cfg<64>::SMEM_BYTES, st>>>(a);
   note_launch();
   return cudaGetLastError();
 }

@@ -458,10 +458,11 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
         }
       const std::vector<cd>* facs[2] = {&qx, &qxt};
       const int slot[2] = {0, 3};
+      const int bn = tc_tile_width((long long)h->P * my, mx, h->num_sms);
       for (int t = 0; t < 2; ++t) {
-        TcOperand op = tc_make_operand(*facs[t], mx, mx);
+        TcOperand op = tc_make_operand(*facs[t], mx, mx, bn);
         TcDevOperand& d = h->tcB[slot[t]];
-        d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles;
+        d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
         if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()))
           return fail(SG_ENOMEM, "precond upload");
       }
@@ -502,10 +503,13 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
           }
         const std::vector<cd>* facs[4] = {&qx, &qy, &qyt, &qxt};
         const int dims[4] = {mx, my, my, mx};
+        // rows of the four GEMMs: P my, P mx, P mx, P my
+        const long long rows[4] = {(long long)h->P * my, (long long)h->P * mx, (long long)h->P * mx,
+                                   (long long)h->P * my};
         for (int t = 0; t < 4; ++t) {
-          TcOperand op = tc_make_operand(*facs[t], dims[t], dims[t]);
+          TcOperand op = tc_make_operand(*facs[t], dims[t], dims[t], tc_tile_width(rows[t], dims[t], h->num_sms));
           TcDevOperand& d = h->tcB[t];
-          d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles;
+          d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
           if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()))
             return fail(SG_ENOMEM, "precond upload");
         }

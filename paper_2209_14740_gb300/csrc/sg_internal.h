@@ -67,19 +67,24 @@ struct PrecBlock {
 
 // Constant right factor of a tensor-core complex GEMM (k_tc_gemm.cu): the
 // real embedding of a kdim x ndim complex matrix, split hi / lo in TF32,
-// in [column tile][K stage][64 x 32 core-matrix block] order.
+// in [column tile][K stage][bn x 32 core-matrix block] order, bn = 64 or 128
+// real output columns per CTA.
 struct TcOperand {
-  int kdim = 0, ndim = 0, nks = 0, ntiles = 0;
+  int kdim = 0, ndim = 0, nks = 0, ntiles = 0, bn = 64;
   std::vector<float> hi, lo;
 };
 struct TcDevOperand {
-  int kdim = 0, ndim = 0, nks = 0, ntiles = 0;
+  int kdim = 0, ndim = 0, nks = 0, ntiles = 0, bn = 64;
   float* hi = nullptr;
   float* lo = nullptr;
 };
-TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim);
+TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim, int bn);
+// Tile width (64 or 128 real columns) for a GEMM of `rows` rows and ndim
+// complex output columns on a GPU with num_sms SMs.
+int tc_tile_width(long long rows, int ndim, int num_sms);
 // C = X Q for M complex64 rows X (row stride ldx complex), placement mode 0
-// (row-major, ldc) or 1 (per-batch transpose, batches of MB rows), optional
+// (row-major, ldc) or 1 (per-batch transpose, batches of MB rows, transposed
+// rows ldc >= MB apart); 16-byte loads of X when ldx is even; optional
 // elementwise factor E[n * e_ld + m % e_mod] * (*escale).
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,

@@ -136,6 +136,39 @@ def test_511_precond_block_residual(B, cfg511):
         assert res32 < 1e-5, res32
 
 
+def test_255_precond_wide_tiles(B):
+    """255 x 255, s = 3, degree 3 (1.3 M unknowns): the FP32 apply takes the
+    fast-diagonalisation route with 128-column tensor-core tiles in all four
+    transforms (ragged in rows and columns) and odd lines, so the
+    intermediates have padded even-length rows.  Checked by the residual of
+    the n x n block on sampled modes and against the FP64 apply (sweeps on
+    the CUDA cores, a separate code path), on two calls in a row."""
+    pr = inputs.helmholtz_2d(255, 3, 3, 30.0, 0.15)
+    op = B.SG(pr)
+    assert op.info["fast_diag"]
+    N, n = op.N, op.n
+    grid = fd.make_grid(pr.dim, pr.nx, pr.ny, pr.h, pr.bc)
+    S0 = fd.deterministic_matrix(grid, pr.k0)
+    g = torch.Generator(device=DEV).manual_seed(21)
+    for call in range(2):
+        R = torch.randn(N, dtype=torch.complex128, device=DEV, generator=g)
+        R32 = R.to(torch.complex64)
+        for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+            Z = torch.empty_like(R)
+            op.precond(R32.to(torch.complex128), Z, kind, B.FP64)
+            Z32 = torch.empty_like(R32)
+            op.precond(R32, Z32, kind, B.FP32)
+            err = float(torch.linalg.vector_norm(Z32.to(torch.complex128) - Z) / torch.linalg.vector_norm(Z))
+            assert err < 2e-4, (call, kind, err)
+            if kind == B.PREC_MEAN:
+                for mode in (0, 7, 19):
+                    z32 = Z32[mode * n:(mode + 1) * n].cpu().numpy().astype(np.complex128)
+                    r32 = R32[mode * n:(mode + 1) * n].cpu().numpy().astype(np.complex128)
+                    res = np.linalg.norm(S0 @ z32 - r32) / (abs(S0) @ np.abs(z32) + np.abs(r32)).max() / np.sqrt(n)
+                    assert res < 1e-5, (call, mode, res)
+    op.close()
+
+
 def test_511_mixed_solve_residual(B, cfg511):
     """Mixed precision GMRES(30) with FP64 refinement reaches 1e-8 on the
     21.9 M-unknown system; the FP64 residual is re-computed here with the

@@ -18,8 +18,8 @@
 // One CTA owns 128 rows and BN (64 or 128) real output columns; the
 // accumulator (128 lanes x BN columns FP32) lives in tensor memory.  K is
 // walked in stages of 32 real values.  Warp roles:
-//   warps 0-7  copy raw X rows by cp.async (two stages ahead; 16-byte copies
-//              when the row pitch allows), split them into hi/lo in the
+//   warps 0-7  copy raw X rows by cp.async (two or three stages ahead;
+//              16-byte copies when the row pitch allows), split them into hi/lo in the
 //              canonical K-major layout (8-row x 16-byte core matrices, no
 //              swizzle), and run the epilogue;
 //   warp 8     one lane issues the 12 MMAs of each stage (M=128, N=BN, K=8)
@@ -28,6 +28,11 @@
 //              stage with bulk asynchronous copies completing on an mbarrier.
 // Every wait is bounded: on a timeout the kernel records it, drains its
 // copies, frees tensor memory and returns.
+//
+// Launched as a programmatic dependent of the previous kernel in the stream:
+// tensor-memory allocation, barrier set-up and the first B copies (B is
+// constant) overlap the previous kernel's tail; nothing it wrote is read,
+// and nothing in global memory is written, before griddepcontrol.wait.
 #include <cuda_runtime.h>
 
 #include <complex>
@@ -46,14 +51,12 @@ constexpr int BK = 32;                  // real K values per stage (128 bytes of
 constexpr int NLOAD = 256;              // loader / splitter / epilogue threads (warps 0-7)
 constexpr int MMA_WARP = NLOAD / 32;    // warp 8
 constexpr int THREADS = NLOAD + 64;     // + the MMA warp and the B-copy warp
-constexpr int NRAW = 3;                 // raw X slots: stages s, s+1, s+2 in flight
 constexpr int NAS = 2;                  // split A (hi, lo) slots
 constexpr int NDONE = 4;                // MMA-completion barriers, indexed by stage % 4
 constexpr int RAW_PITCH = 144;          // bytes per raw X row (128 + 16: conflict-free split reads)
 constexpr int RAW_TILE = BM * RAW_PITCH;
 constexpr int A_TILE = BM * BK * 4;     // 16 KB, core-matrix layout
 constexpr int OFF_RAW = 0;
-constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;   // [slot][hi, lo]
 
 // Layout that depends on the tile width.
 template <int BN>
@@ -61,7 +64,10 @@ struct Cfg {
   // B slots: a slot is refilled once the MMAs of the stage that used it
   // have completed, so more slots let the copies run further ahead
   static constexpr int NBS = BN == 64 ? 4 : 3;
+  // raw X slots: stages s .. s + NRAW - 1 in flight
+  static constexpr int NRAW = BN == 64 ? 4 : 3;
   static constexpr int B_TILE = BN * BK * 4;                     // 8 or 16 KB
+  static constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;        // [slot][hi, lo]
   static constexpr int OFF_A = ((OFF_B + NBS * 2 * B_TILE + 1023) / 1024) * 1024;   // [slot][hi, lo]
   static constexpr int OFF_BAR = OFF_A + NAS * 2 * A_TILE;      // full[NAS], bfull[NBS], done[NDONE], TMEM addr, abort
   static constexpr int SMEM_BYTES = OFF_BAR + 128 + 1024;        // + slack for 1024-byte alignment
@@ -209,9 +215,10 @@ __device__ __forceinline__ bool loader_sync_or(bool v) {
   return r != 0;
 }
 
-// Pipeline (stage s = 32 real K values):
+// Pipeline (stage s = 32 real K values, NRAW raw X slots):
 //   loaders:  wait raw X of s landed -> wait MMA(s-2) (frees A slot s%2)
-//             -> split raw -> A slot, arrive full[s%2] -> issue X copies of s+2
+//             -> split raw -> A slot, arrive full[s%2]
+//             -> issue X copies of s+NRAW-1
 //   B copier: wait MMA(s-NBS) (frees B slot s%NBS) -> bulk-copy B hi/lo of s
 //   MMA lane: wait full[s%2] and bfull[s%NBS] -> 12 MMAs (3xTF32 x 4 K steps)
 //             -> commit done[s%4]
@@ -222,8 +229,7 @@ template <int BN>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   using namespace tc;
   using L = Cfg<BN>;
-  constexpr int NBS = L::NBS, B_TILE = L::B_TILE;
-  if (a.skip && *a.skip) return;
+  constexpr int NBS = L::NBS, B_TILE = L::B_TILE, NRAW = L::NRAW, OFF_B = L::OFF_B;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -255,7 +261,25 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   const int m0 = blockIdx.x * BM;
-  const int nks = a.nks;
+  const float* Bh = a.Bhi + (size_t)blockIdx.y * a.nks * (BN * BK);
+  const float* Bl = a.Blo + (size_t)blockIdx.y * a.nks * (BN * BK);
+  auto copy_b = [&](int t) {
+    const uint32_t bar = bfull0 + 8 * (t % NBS);
+    const uint32_t dst = s_base + OFF_B + (t % NBS) * 2 * B_TILE;
+    mbar_expect_tx(bar, 2u * B_TILE);
+    bulk_g2s(dst, Bh + (size_t)t * (BN * BK), B_TILE, bar);
+    bulk_g2s(dst + B_TILE, Bl + (size_t)t * (BN * BK), B_TILE, bar);
+  };
+  // B is constant: its first stages are copied before the wait below
+  const int pre = a.nks < NBS ? a.nks : NBS;
+  if (warp == MMA_WARP + 1 && lane == 0)
+    for (int t = 0; t < pre; ++t) copy_b(t);
+  // everything the previous kernel wrote is visible after this; then the
+  // next kernel may start its own set-up
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const bool skipped = a.skip && *a.skip;
+  const int nks = skipped ? 0 : a.nks;
 
   if (warp < MMA_WARP) {
     // ---------------------------------------------------------------- loaders
@@ -285,13 +309,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
         }
       }
     };
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NRAW - 1; ++t) {
       if (t < nks) issue(t);
       cp_commit();
     }
     bool bad = false;
     for (int s = 0; s < nks; ++s) {
-      cp_wait<1>();
+      cp_wait<NRAW - 2>();
       bool to = false;
       if (s >= 2) to = !mbar_wait(done0 + 8 * ((s - 2) % NDONE), ((s - 2) / NDONE) & 1);
       if (loader_sync_or(to || *abort_flag != 0)) { bad = true; break; }
@@ -316,9 +340,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(full0 + 8 * (s % NAS));
-      // the raw slot of stage s+2 was split at s-1 by every loader (all of
-      // them passed the barrier above since)
-      if (s + 2 < nks) issue(s + 2);
+      // the raw slot of stage s+NRAW-1 was split at s-1 by every loader
+      // (all of them passed the barrier above since)
+      if (s + NRAW - 1 < nks) issue(s + NRAW - 1);
       cp_commit();
     }
     // all MMAs done before the accumulator is read
@@ -327,7 +351,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     bad = loader_sync_or(bad || *abort_flag != 0);
     if (bad) {
       *abort_flag = 1;
-    } else {
+    } else if (!skipped) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the
       // tile) and real columns [w / 4 * BN / 2, + BN / 2), 32 at a time.
@@ -415,20 +439,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     }
   } else if (lane == 0) {
     // ---------------------------------------------------------------- B copies
-    const float* Bh = a.Bhi + (size_t)blockIdx.y * nks * (BN * BK);
-    const float* Bl = a.Blo + (size_t)blockIdx.y * nks * (BN * BK);
-    int issued = 0;
-    for (int t = 0; t < nks; ++t) {
-      if (t >= NBS && !mbar_wait(done0 + 8 * ((t - NBS) % NDONE), ((t - NBS) / NDONE) & 1)) {
+    int issued = pre;   // stages copied before the wait (also when skipped)
+    for (int t = pre; t < nks; ++t) {
+      if (!mbar_wait(done0 + 8 * ((t - NBS) % NDONE), ((t - NBS) / NDONE) & 1)) {
         *abort_flag = 1;
         break;
       }
       if (*abort_flag) break;
-      const uint32_t bar = bfull0 + 8 * (t % NBS);
-      const uint32_t dst = s_base + OFF_B + (t % NBS) * 2 * B_TILE;
-      mbar_expect_tx(bar, 2u * B_TILE);
-      bulk_g2s(dst, Bh + (size_t)t * (BN * BK), B_TILE, bar);
-      bulk_g2s(dst + B_TILE, Bl + (size_t)t * (BN * BK), B_TILE, bar);
+      copy_b(t);
       issued = t + 1;
     }
     // no copy may still be writing shared memory when the CTA exits: wait
@@ -533,13 +551,27 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   a.escale = escale;
   a.skip = skip;
   a.err = err;
-  dim3 grid((M + tc::BM - 1) / tc::BM, B.ntiles);
-  if (B.bn == 128)
-    k_tc_cgemm<128><<<grid, tc::THREADS, tc::Cfg<128>::SMEM_BYTES, st>>>(a);
-  else
-    k_tc_cgemm<64><<<grid, tc::THREADS, tc::Cfg<64>::SMEM_BYTES, st>>>(a);
+  // programmatic dependent launch: may start while the previous kernel in
+  // the stream finishes (the kernel waits for it before touching its data)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((M + tc::BM - 1) / tc::BM, B.ntiles);
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  if (B.bn == 128) {
+    cfg.dynamicSmemBytes = tc::Cfg<128>::SMEM_BYTES;
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128>, a);
+  } else {
+    cfg.dynamicSmemBytes = tc::Cfg<64>::SMEM_BYTES;
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64>, a);
+  }
   note_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace sgi

@@ -45,6 +45,7 @@ STENCIL = "tile"     # "tile": 2D tile staged in shared memory; "split": couplin
 SERIAL = True        # rows evaluated one after another (bounded register pressure)
 ROWS_PER_FENCE = 4   # tile mode: rows between register fences
 COUPLING = "tk"      # tile mode: "tk" = factorised through degree r + 1, "direct" = one product per term
+PERSISTENT = True    # complex64 "tk" kernels: persistent CTAs, next tile copied during the coupling
 # FP64 kernels are generated for P up to this (two registers per value: the
 # mode values and accumulators of larger P do not fit)
 F64_MAX_P = 35
@@ -439,6 +440,95 @@ def gen_kernel_tile(s, r):
     return name, P, "\n".join(L)
 
 
+def _tk_rows(s, r):
+    """Rows of the factorised coupling in graded order: for every g of degree
+    <= r + 1 the entries T_k[g][b] (coefficient name, b) with b = g, g - e_l,
+    g + e_l in degree <= r.  The scatter of T_k^T touches the same entries:
+    Z_a += T_k[g][a] W_g."""
+    al = _multi_indices(s, r)
+    ext = _multi_indices(s, r + 1)
+    idx = {a: i for i, a in enumerate(al)}
+    rows = []
+    for gm in ext:
+        terms = []
+        if gm in idx:
+            terms.append(("k0", idx[gm]))
+        for l in range(s):
+            if gm[l] >= 1:
+                lo = list(gm)
+                lo[l] -= 1
+                terms.append(("kb%d_%d" % (l + 1, gm[l]), idx[tuple(lo)]))
+            hi = list(gm)
+            hi[l] += 1
+            if tuple(hi) in idx:
+                terms.append(("kb%d_%d" % (l + 1, gm[l] + 1), idx[tuple(hi)]))
+        if terms:
+            rows.append((gm, terms))
+    return idx, rows
+
+
+def _emit_tk_coupling(w, s, r, finish, hook=None, first_x=None, first_z=None):
+    """Z += -w2 T_k^T T_k X (and -i w1 (T_k X) on absorbing boundary nodes,
+    exchanged with the partner lane) in registers, one W_g at a time.  In
+    graded order X_b is dead after the last W_g that reads it and Z_a is
+    complete after the last W_g scattered into it; finish(a) is emitted right
+    then, so only the values of about two degrees are live at a time.
+    hook(), if given, is emitted before the first row of degree r + 1 (where
+    the fewest values are live); first_x(b) and first_z(a), if given, before
+    the first row that reads X_b or updates Z_a (all of degree <= r, so
+    before the hook).""" 
+    idx, rows = _tk_rows(s, r)
+    P = len(idx)
+    last_x = {}
+    last_z = {}
+    for ri, (gm, terms) in enumerate(rows):
+        for _, b in terms:
+            last_x[b] = ri
+            last_z[b] = ri
+    done_at = {}
+    for a in range(P):
+        done_at.setdefault(last_z[a], []).append(a)
+
+    seen = set()
+
+    def fence(ri):
+        # values declared so far (all of them when first_x is not used) that
+        # are still to be read
+        live = [b for b in range(P) if last_x.get(b, -1) >= ri and (first_x is None or b in seen)]
+        for i0 in range(0, len(live), 28):
+            ops = ", ".join('"+f"(x%d)' % i for i in live[i0:i0 + 28])
+            w('  asm volatile("" : %s :: "memory");' % ops)
+
+    first_top = min(ri for ri, (gm, _) in enumerate(rows) if sum(gm) == r + 1)
+    for ri, (gm, terms) in enumerate(rows):
+        if ri == first_top and hook:
+            fence(ri)
+            hook()
+        for _, b in terms:
+            if b not in seen:
+                assert ri < first_top
+                seen.add(b)
+                if first_x:
+                    first_x(b)
+                if first_z:
+                    first_z(b)
+        if ri % (2 * ROWS_PER_FENCE) == 0:
+            fence(ri)
+        e = "%s * x%d" % (terms[0][0], terms[0][1])
+        for cf, b in terms[1:]:
+            e = "fmaf(%s, x%d, %s)" % (cf, b, e)
+        w("  {  // g = %s" % (gm,))
+        w("    float wv = %s;" % e)
+        if gm in idx:
+            w("    if (bnd) z%d = fmaf(sw1, __shfl_xor_sync(0xffffffffu, wv, 1), z%d);" % (idx[gm], idx[gm]))
+        w("    wv *= nw2;")
+        for cf, a in terms:
+            w("    z%d = fmaf(%s, wv, z%d);" % (a, cf, a))
+        w("  }")
+        for a in done_at.get(ri, []):
+            finish(a)
+
+
 def gen_kernel_tk(s, r, prec="f32"):
     """Tiled variant with the coupling factorised through degree r + 1.
 
@@ -537,63 +627,18 @@ def gen_kernel_tk(s, r, prec="f32"):
     w("  float* __restrict__ yp = Y + 2ll * u + c;")
     w("  __syncthreads();")
 
-    def fence():
-        for i0 in range(0, P, 28):
-            ops = ", ".join('"+f"(x%d)' % i for i in range(i0, min(P, i0 + 28)))
-            w('  asm volatile("" : %s :: "memory");' % ops)
-
-    for gi, gm in enumerate(ext):
-        if gi % (2 * ROWS_PER_FENCE) == 0:
-            fence()
-        # W_g = k0 X_g + sum_l kb_l(g_l) X_{g-e_l} + kb_l(g_l+1) X_{g+e_l}
-        terms = []
-        if gm in idx:
-            terms.append(("k0", idx[gm]))
-        for l in range(s):
-            if gm[l] >= 1:
-                lo = list(gm)
-                lo[l] -= 1
-                terms.append(("kb%d_%d" % (l + 1, gm[l]), idx[tuple(lo)]))
-            hi = list(gm)
-            hi[l] += 1
-            if tuple(hi) in idx:
-                terms.append(("kb%d_%d" % (l + 1, gm[l] + 1), idx[tuple(hi)]))
-        if not terms:
-            continue
-        e = "%s * %s" % (terms[0][0], xv(terms[0][1]))
-        for cf, b in terms[1:]:
-            e = "fmaf(%s, %s, %s)" % (cf, xv(b), e)
-        w("  {  // g = %s" % (gm,))
-        w("    float wv = %s;" % e)
-        if gm in idx:
-            w("    if (bnd) z%d = fmaf(sw1, __shfl_xor_sync(0xffffffffu, wv, 1), z%d);" % (idx[gm], idx[gm]))
-        w("    wv *= nw2;")
-        # scatter T_k^T: Z_a += T_k[g][a] W_g for a = g, g - e_l, g + e_l in degree <= r
-        if gm in idx:
-            w("    z%d = fmaf(k0, wv, z%d);" % (idx[gm], idx[gm]))
-        for l in range(s):
-            if gm[l] >= 1:
-                lo = list(gm)
-                lo[l] -= 1
-                a = idx[tuple(lo)]
-                w("    z%d = fmaf(kb%d_%d, wv, z%d);" % (a, l + 1, gm[l], a))
-            hi = list(gm)
-            hi[l] += 1
-            if tuple(hi) in idx:
-                a = idx[tuple(hi)]
-                w("    z%d = fmaf(kb%d_%d, wv, z%d);" % (a, l + 1, gm[l] + 1, a))
-        w("  }")
-    fence()
-    for a in range(P):
+    def finish(a):
         w("  {")
         w("    const float* q = xs + %d * ST;" % a)
-        w("    float y = fmaf(g.ldiag, %s, z%d);" % (xv(a), a))
+        w("    float y = fmaf(g.ldiag, q[t], z%d);" % a)
         w("    y = fmaf(-wxm, q[oxm], y);")
         w("    y = fmaf(-wxp, q[oxp], y);")
         w("    y = fmaf(-wym, q[oym], y);")
         w("    y = fmaf(-wyp, q[oyp], y);")
         w("    if (valid) yp[%d * n2] = y;" % a)
         w("  }")
+
+    _emit_tk_coupling(w, s, r, finish)
     w("}")
     src = "\n".join(L)
     if prec == "f64":
@@ -606,6 +651,124 @@ def gen_kernel_tk(s, r, prec="f32"):
                           "  extern __shared__ __align__(16) unsigned char xs64_raw[];\n"
                           "  double* xs = reinterpret_cast<double*>(xs64_raw);")
     return name, P, src
+
+
+def gen_kernel_tkp(s, r):
+    """Persistent form of the factorised complex64 kernel (gen_kernel_tk):
+    each CTA walks tiles of TX x TY unknowns with a stride of the grid size,
+    and the copies of the next tile overlap the coupling of this one:
+
+      wait for this tile's copies -> Z_a = ldiag X_a - sum_nb w_nb X_a(nb)
+      straight from shared memory (X_a into registers) -> coupling rows of
+      degree <= r -> barrier -> issue the cp.async copies of the next tile's
+      values and halo into the same shared rows -> rows of degree r + 1
+      (the fewest live registers) -> Y_a = Z_a as each completes.
+
+    The stencil reads every shared value before the barrier, so one buffer
+    serves both tiles, and the CTA's single set of P accumulators (the
+    register file holds one CTA of 256 threads at P = 84) is no longer idle
+    while its next tile is in flight."""
+    idx, _ = _tk_rows(s, r)
+    P = len(idx)
+    name = "k_mvkp_s%dr%d" % (s, r)
+    L = []
+    w = L.append
+    w("template <int TX, int TY>")
+    w("__global__ void __launch_bounds__(2 * TX * TY) %s(OpParams<float> p, const float* __restrict__ X, "
+      "float* __restrict__ Y) {" % name)
+    w("  constexpr int NT = 2 * TX * TY;            // threads = (unknown, component) pairs")
+    w("  constexpr int NH = 2 * (2 * TX + 2 * TY);  // halo entries per mode")
+    w("  constexpr int ST = NT + NH;                // shared-memory row stride per mode")
+    w("  extern __shared__ float xs[];              // [P][ST]: tile values, then halo values")
+    w("  if (p.skip && *p.skip) return;")
+    w("  const int t = threadIdx.x, c = t & 1, nid = t >> 1;")
+    w("  const int lx = nid % TX, ly = nid / TX;")
+    w("  const int tiles_x = (p.mx + TX - 1) / TX;")
+    w("  const int tiles = tiles_x * ((p.my + TY - 1) / TY);")
+    w("  const long long n2 = 2ll * p.n;")
+    w("  const uint32_t xs0 = (uint32_t)__cvta_generic_to_shared(xs);")
+    w("  const int oxm = lx > 0 ? t - 2 : NT + 2 * (2 * TX + ly) + c;")
+    w("  const int oxp = lx < TX - 1 ? t + 2 : NT + 2 * (2 * TX + TY + ly) + c;")
+    w("  const int oym = ly > 0 ? t - 2 * TX : NT + 2 * lx + c;")
+    w("  const int oyp = ly < TY - 1 ? t + 2 * TX : NT + 2 * (TX + lx) + c;")
+    w("  // copies of one tile's values (this thread's unknown, every mode) and of")
+    w("  // its halo (with NT >= NH thread t < HG * NH owns halo slot t % NH of")
+    w("  // every HG-th mode); halo entries outside the grid are zero-filled")
+    w("  constexpr int HG = NT >= NH ? NT / NH : 1;")
+    w("  auto issue = [&](int tile) {")
+    w("    const int bx0 = (tile % tiles_x) * TX, by0 = (tile / tiles_x) * TY;")
+    w("    {")
+    w("      const int iu = min(bx0 + lx, p.mx - 1), ju = min(by0 + ly, p.my - 1);")
+    w("      const float* src = X + 2ll * (iu + (long long)p.mx * ju) + c;")
+    w("      uint32_t dst = xs0 + 4u * t;")
+    w("#pragma unroll 4")
+    w("      for (int a = 0; a < %d; ++a, src += n2, dst += 4u * ST) mv_cp_async4(dst, src, 4);" % P)
+    w("    }")
+    w("    // halo slot e of modes a0, a0 + hg, ...")
+    w("    auto halo = [&](int e, int a0, int hg) {")
+    w("      const int hc = e & 1, h = e >> 1;")
+    w("      int hx, hy;")
+    w("      if (h < TX) { hx = bx0 + h; hy = by0 - 1; }")
+    w("      else if (h < 2 * TX) { hx = bx0 + h - TX; hy = by0 + TY; }")
+    w("      else if (h < 2 * TX + TY) { hx = bx0 - 1; hy = by0 + h - 2 * TX; }")
+    w("      else { hx = bx0 + TX; hy = by0 + h - 2 * TX - TY; }")
+    w("      const bool ok = hx >= 0 && hx < p.mx && hy >= 0 && hy < p.my;")
+    w("      const float* src = ok ? X + (long long)a0 * n2 + 2ll * (hx + (long long)p.mx * hy) + hc : X;")
+    w("      const long long step = ok ? hg * n2 : 0;")
+    w("      uint32_t dst = xs0 + 4u * (a0 * ST + NT + e);")
+    w("#pragma unroll 4")
+    w("      for (int a = a0; a < %d; a += hg, src += step, dst += 4u * hg * ST) mv_cp_async4(dst, src, ok ? 4 : 0);" % P)
+    w("    };")
+    w("    if (NT >= NH) {")
+    w("      if (t < HG * NH) halo(t % NH, t / NH, HG);")
+    w("    } else {")
+    w("      for (int e = t; e < NH; e += NT) halo(e, 0, 1);")
+    w("    }")
+    w('    asm volatile("cp.async.commit_group;" ::: "memory");')
+    w("  };")
+    w("  int tile = blockIdx.x;")
+    w("  if (tile < tiles) issue(tile);")
+    w("  for (; tile < tiles; tile += gridDim.x) {")
+    w("    const int iu0 = (tile % tiles_x) * TX + lx, ju0 = (tile / tiles_x) * TY + ly;")
+    w("    const bool valid = iu0 < p.mx && ju0 < p.my;")
+    w("    const int iu = min(iu0, p.mx - 1), ju = min(ju0, p.my - 1);")
+    w("    const int u = iu + p.mx * ju;")
+    w("    const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
+    w("    const float wxm = g.hxm ? g.wxm : 0.0f, wxp = g.hxp ? g.wxp : 0.0f;")
+    w("    const float wym = g.hym ? g.wym : 0.0f, wyp = g.hyp ? g.wyp : 0.0f;")
+    w("    const float k0 = __ldg(p.fields + u);")
+    for l in range(s):
+        w("    const float k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
+    w("    const float nw2 = -g.w2;")
+    for l in range(s):
+        for n in range(1, r + 2):
+            w("    const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, _f(_b(n))))
+    w("    const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0f);")
+    w("    const float sw1 = c ? -g.w1 : g.w1;   // -i w1 W: re gets +w1 Im W, im gets -w1 Re W")
+    w("    float* __restrict__ yp = Y + 2ll * u + c;")
+    w('    asm volatile("cp.async.wait_all;" ::: "memory");')
+    w("    __syncthreads();")
+
+    # mode values into registers, and the stencil part of each output straight
+    # from shared memory, just before their first use in the coupling
+    def first_x(b):
+        w("    float x%d = xs[%d * ST + t];" % (b, b))
+
+    def first_z(a):
+        w("    float z%d = fmaf(g.ldiag, x%d, fmaf(-wxm, xs[%d * ST + oxm], fmaf(-wxp, xs[%d * ST + oxp], "
+          "fmaf(-wym, xs[%d * ST + oym], -wyp * xs[%d * ST + oyp]))));" % (a, a, a, a, a, a))
+
+    def next_tile():
+        w("    __syncthreads();   // every shared value of this tile has been read")
+        w("    if (tile + (int)gridDim.x < tiles) issue(tile + gridDim.x);")
+
+    def finish(a):
+        w("    if (valid) yp[%d * n2] = z%d;" % (a, a))
+
+    _emit_tk_coupling(w, s, r, finish, next_tile, first_x, first_z)
+    w("  }")
+    w("}")
+    return name, P, "\n".join(L)
 
 
 def gen_kernel_tk64_halves(s, r, halves=3):
@@ -883,6 +1046,7 @@ def gen_kernel_packed(s, r):
 def generate(path: str) -> str:
     parts = ["// GENERATED by paper_2209_14740_gb300/codegen_matvec.py -- do not edit.",
              "#include <cuda_runtime.h>",
+             "#include <algorithm>",
              '#include "sg_internal.h"',
              '#include "k_operator_geom.cuh"',
              "namespace sgi {",
@@ -892,12 +1056,19 @@ def generate(path: str) -> str:
              "  float z;",
              "  asm volatile(\"mov.b32 %0, 0;\" : \"=f\"(z));",
              "  return z;",
+             "}",
+             "// 4-byte asynchronous global -> shared copy; bytes = 0 writes a zero",
+             "__device__ __forceinline__ void mv_cp_async4(uint32_t dst, const float* src, int bytes) {",
+             "  asm volatile(\"cp.async.ca.shared.global [%0], [%1], 4, %2;\" :: \"r\"(dst), \"l\"(src), \"r\"(bytes) : \"memory\");",
              "}"]
     table = []
     table64 = []
     for s, r in SPECIALISED:
         if STENCIL == "tile":
-            name, P, src = gen_kernel_tk(s, r) if COUPLING == "tk" else gen_kernel_tile(s, r)
+            if COUPLING == "tk":
+                name, P, src = gen_kernel_tkp(s, r) if PERSISTENT else gen_kernel_tk(s, r)
+            else:
+                name, P, src = gen_kernel_tile(s, r)
         else:
             name, P, src = gen_kernel(s, r)
         parts.append(src)
@@ -930,6 +1101,30 @@ def generate(path: str) -> str:
             "  note_launch();",
             "  return cudaGetLastError();",
             "}",
+            "// Launch of a persistent kernel: as many CTAs as fit on the GPU at once",
+            "// (at most one per tile); *occ caches the CTAs per SM of this kernel.",
+            "template <int TX, int TY>",
+            "static cudaError_t launch_persist(void (*kern)(OpParams<float>, const float*, float*), int P, int* occ,",
+            "                                  const sg_handle* h, const OpParams<float>& p, const float2* X,",
+            "                                  float2* Y, cudaStream_t st) {",
+            "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
+            "  const size_t smem = (size_t)P * (nt + nh) * sizeof(float);",
+            "  if (smem > 48 * 1024) {",
+            "    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
+            "    if (e != cudaSuccess) return e;",
+            "  }",
+            "  if (*occ <= 0) {",
+            "    int o = 0;",
+            "    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, nt, smem);",
+            "    if (e != cudaSuccess) return e;",
+            "    *occ = o > 0 ? o : 1;",
+            "  }",
+            "  const long long tiles = (long long)((h->mx + TX - 1) / TX) * ((h->my + TY - 1) / TY);",
+            "  const int grid = (int)std::min<long long>(tiles, (long long)h->num_sms * *occ);",
+            "  kern<<<grid, nt, smem, st>>>(p, reinterpret_cast<const float*>(X), reinterpret_cast<float*>(Y));",
+            "  note_launch();",
+            "  return cudaGetLastError();",
+            "}",
         ]
     parts.append("cudaError_t matvec_special_f32(const sg_handle* h, const float2* X, float2* Y, cudaStream_t st,")
     parts.append("                               const int* skip, bool* handled) {")
@@ -941,7 +1136,13 @@ def generate(path: str) -> str:
     for s, r, name, P in table:
         parts.append("  if (h->s == %d && h->r == %d) {" % (s, r))
         parts.append("    *handled = true;")
-        if STENCIL == "tile":
+        if STENCIL == "tile" and COUPLING == "tk" and PERSISTENT:
+            tx, ty = tile_2d(P)
+            parts.append("    static int occ2 = 0, occ1 = 0;")
+            parts.append("    if (h->dim == 2) return launch_persist<%d, %d>(%s<%d, %d>, %d, &occ2, h, p, X, Y, st);"
+                         % (tx, ty, name, tx, ty, P))
+            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, &occ1, h, p, X, Y, st);" % (name, P))
+        elif STENCIL == "tile":
             tx, ty = tile_2d(P)
             parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"
                          % (tx, ty, name, tx, ty, P))

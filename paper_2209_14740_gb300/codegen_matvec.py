@@ -46,6 +46,10 @@ SERIAL = True        # rows evaluated one after another (bounded register pressu
 ROWS_PER_FENCE = 4   # tile mode: rows between register fences
 COUPLING = "tk"      # tile mode: "tk" = factorised through degree r + 1, "direct" = one product per term
 PERSISTENT = True    # complex64 "tk" kernels: persistent CTAs, next tile copied during the coupling
+# persistent kernels with at least this many modes emit the rows of degree
+# <= r twice (with and without the boundary exchange) so interior warps run
+# them without branches; smaller P keeps one copy (fewer registers, more CTAs)
+BND_SPLIT_MIN_P = 56
 # FP64 kernels are generated for P up to this (two registers per value: the
 # mode values and accumulators of larger P do not fit)
 F64_MAX_P = 35
@@ -653,6 +657,57 @@ def gen_kernel_tk(s, r, prec="f32"):
     return name, P, src
 
 
+def _emit_tk_rows(w, s, r, rows, lo, hi, finish, bnd, first_x=None, first_z=None, declared=()):
+    """Rows lo .. hi - 1 of the factorised coupling for the persistent kernel,
+    on mode values already scaled by -w2 (so W'_g = -w2 W_g and the scatter
+    needs no extra product).  bnd: emit the -i w1 W exchange with the partner
+    lane (warps holding an absorbing boundary node) unconditionally (True),
+    behind the warp-uniform flag ("branch") or not at all (False).  first_x(b) and
+    first_z(a) are emitted before the first row that reads X_b or updates
+    Z_a; `declared` lists the values that exist before row lo."""
+    idx, _ = _tk_rows(s, r)
+    P = len(idx)
+    last_x = {}
+    last_z = {}
+    for ri, (gm, terms) in enumerate(rows):
+        for _, b in terms:
+            last_x[b] = ri
+            last_z[b] = ri
+    seen = set(declared)
+
+    def fence(ri):
+        live = [b for b in range(P) if last_x.get(b, -1) >= ri and b in seen]
+        for i0 in range(0, len(live), 28):
+            ops = ", ".join('"+f"(x%d)' % i for i in live[i0:i0 + 28])
+            w('    asm volatile("" : %s :: "memory");' % ops)
+
+    for ri in range(lo, hi):
+        gm, terms = rows[ri]
+        if (ri - lo) % (2 * ROWS_PER_FENCE) == 0:
+            fence(ri)
+        for _, b in terms:
+            if b not in seen:
+                seen.add(b)
+                first_x(b)
+                first_z(b)
+        e = "%s * x%d" % (terms[0][0], terms[0][1])
+        for cf, b in terms[1:]:
+            e = "fmaf(%s, x%d, %s)" % (cf, b, e)
+        w("    {  // g = %s" % (gm,))
+        w("      const float wv = %s;" % e)
+        if bnd == "branch" and gm in idx:
+            w("      if (bnd) z%d = fmaf(sw1, __shfl_xor_sync(0xffffffffu, wv, 1), z%d);" % (idx[gm], idx[gm]))
+        elif bnd and gm in idx:
+            w("      z%d = fmaf(sw1, __shfl_xor_sync(0xffffffffu, wv, 1), z%d);" % (idx[gm], idx[gm]))
+        for cf, a in terms:
+            w("      z%d = fmaf(%s, wv, z%d);" % (a, cf, a))
+        w("    }")
+        for a in range(P):
+            if last_z[a] == ri:
+                finish(a)
+    return seen
+
+
 def gen_kernel_tkp(s, r):
     """Persistent form of the factorised complex64 kernel (gen_kernel_tk):
     each CTA walks tiles of TX x TY unknowns with a stride of the grid size,
@@ -679,7 +734,8 @@ def gen_kernel_tkp(s, r):
     w("  constexpr int NT = 2 * TX * TY;            // threads = (unknown, component) pairs")
     w("  constexpr int NH = 2 * (2 * TX + 2 * TY);  // halo entries per mode")
     w("  constexpr int ST = NT + NH;                // shared-memory row stride per mode")
-    w("  extern __shared__ float xs[];              // [P][ST]: tile values, then halo values")
+    w("  constexpr int FS = %d * ST;                // then the %d wavenumber fields of the tile's unknowns" % (P, s + 1))
+    w("  extern __shared__ float xs[];              // [P][ST]: tile values, then halo values; [s+1][NT/2] fields")
     w("  if (p.skip && *p.skip) return;")
     w("  const int t = threadIdx.x, c = t & 1, nid = t >> 1;")
     w("  const int lx = nid % TX, ly = nid / TX;")
@@ -703,6 +759,13 @@ def gen_kernel_tkp(s, r):
     w("      uint32_t dst = xs0 + 4u * t;")
     w("#pragma unroll 4")
     w("      for (int a = 0; a < %d; ++a, src += n2, dst += 4u * ST) mv_cp_async4(dst, src, 4);" % P)
+    w("      // the (s+1) wavenumber fields k_0 .. k_s of the unknown (one thread of the pair)")
+    w("      if (c == 0) {")
+    w("        const float* fsrc = p.fields + iu + (long long)p.mx * ju;")
+    w("        uint32_t fdst = xs0 + 4u * (FS + nid);")
+    w("#pragma unroll")
+    w("        for (int l = 0; l <= %d; ++l, fsrc += p.n, fdst += 4u * (NT / 2)) mv_cp_async4(fdst, fsrc, 4);" % s)
+    w("      }")
     w("    }")
     w("    // halo slot e of modes a0, a0 + hg, ...")
     w("    auto halo = [&](int e, int a0, int hg) {")
@@ -736,36 +799,53 @@ def gen_kernel_tkp(s, r):
     w("    const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
     w("    const float wxm = g.hxm ? g.wxm : 0.0f, wxp = g.hxp ? g.wxp : 0.0f;")
     w("    const float wym = g.hym ? g.wym : 0.0f, wyp = g.hyp ? g.wyp : 0.0f;")
-    w("    const float k0 = __ldg(p.fields + u);")
-    for l in range(s):
-        w("    const float k%d = __ldg(p.fields + (long long)%d * p.n + u);" % (l + 1, l + 1))
-    w("    const float nw2 = -g.w2;")
-    for l in range(s):
-        for n in range(1, r + 2):
-            w("    const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, _f(_b(n))))
+    w("    // mode values in registers are scaled by -w2 (a power of two: exact),")
+    w("    // so the diagonal and boundary weights applied to them take the")
+    w("    // inverse factor; the neighbours come unscaled from shared memory")
+    w("    const float nw2 = -g.w2, inw2 = -1.0f / g.w2;")
+    w("    const float ldg2 = g.ldiag * inw2;")
     w("    const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0f);")
-    w("    const float sw1 = c ? -g.w1 : g.w1;   // -i w1 W: re gets +w1 Im W, im gets -w1 Re W")
+    w("    const float sw1 = (c ? -g.w1 : g.w1) * inw2;   // -i w1 W: re gets +w1 Im W, im gets -w1 Re W")
     w("    float* __restrict__ yp = Y + 2ll * u + c;")
     w('    asm volatile("cp.async.wait_all;" ::: "memory");')
     w("    __syncthreads();")
+    w("    const float k0 = xs[FS + nid];")
+    for l in range(s):
+        w("    const float k%d = xs[FS + %d * (NT / 2) + nid];" % (l + 1, l + 1))
+    for l in range(s):
+        for n in range(1, r + 2):
+            w("    const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, _f(_b(n))))
+    w("    float %s;" % ", ".join("x%d" % a for a in range(P)))
+    w("    float %s;" % ", ".join("z%d" % a for a in range(P)))
 
-    # mode values into registers, and the stencil part of each output straight
-    # from shared memory, just before their first use in the coupling
+    # mode values into registers (scaled), and the stencil part of each output
+    # straight from shared memory, just before their first use
     def first_x(b):
-        w("    float x%d = xs[%d * ST + t];" % (b, b))
+        w("    x%d = nw2 * xs[%d * ST + t];" % (b, b))
 
     def first_z(a):
-        w("    float z%d = fmaf(g.ldiag, x%d, fmaf(-wxm, xs[%d * ST + oxm], fmaf(-wxp, xs[%d * ST + oxp], "
+        w("    z%d = fmaf(ldg2, x%d, fmaf(-wxm, xs[%d * ST + oxm], fmaf(-wxp, xs[%d * ST + oxp], "
           "fmaf(-wym, xs[%d * ST + oym], -wyp * xs[%d * ST + oyp]))));" % (a, a, a, a, a, a))
-
-    def next_tile():
-        w("    __syncthreads();   // every shared value of this tile has been read")
-        w("    if (tile + (int)gridDim.x < tiles) issue(tile + gridDim.x);")
 
     def finish(a):
         w("    if (valid) yp[%d * n2] = z%d;" % (a, a))
 
-    _emit_tk_coupling(w, s, r, finish, next_tile, first_x, first_z)
+    idx_, rows = _tk_rows(s, r)
+    top = min(ri for ri, (gm, _) in enumerate(rows) if sum(gm) == r + 1)
+    # rows of degree <= r: warps holding an absorbing boundary node exchange
+    # -i w1 W with the partner lane; the others run the same rows without
+    if P >= BND_SPLIT_MIN_P:
+        w("    if (bnd) {")
+        declared = _emit_tk_rows(w, s, r, rows, 0, top, finish, True, first_x, first_z)
+        w("    } else {")
+        _emit_tk_rows(w, s, r, rows, 0, top, finish, False, first_x, first_z)
+        w("    }")
+    else:
+        declared = _emit_tk_rows(w, s, r, rows, 0, top, finish, "branch", first_x, first_z)
+    w("    __syncthreads();   // every shared value of this tile has been read")
+    w("    if (tile + (int)gridDim.x < tiles) issue(tile + gridDim.x);")
+    # rows of degree r + 1 (no output of their own: no exchange)
+    _emit_tk_rows(w, s, r, rows, top, len(rows), finish, False, declared=declared)
     w("  }")
     w("}")
     return name, P, "\n".join(L)
@@ -1104,11 +1184,12 @@ def generate(path: str) -> str:
             "// Launch of a persistent kernel: as many CTAs as fit on the GPU at once",
             "// (at most one per tile); *occ caches the CTAs per SM of this kernel.",
             "template <int TX, int TY>",
-            "static cudaError_t launch_persist(void (*kern)(OpParams<float>, const float*, float*), int P, int* occ,",
+            "static cudaError_t launch_persist(void (*kern)(OpParams<float>, const float*, float*), int P, int nfields,",
+            "                                  int* occ,",
             "                                  const sg_handle* h, const OpParams<float>& p, const float2* X,",
             "                                  float2* Y, cudaStream_t st) {",
             "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
-            "  const size_t smem = (size_t)P * (nt + nh) * sizeof(float);",
+            "  const size_t smem = ((size_t)P * (nt + nh) + (size_t)nfields * (nt / 2)) * sizeof(float);",
             "  if (smem > 48 * 1024) {",
             "    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
             "    if (e != cudaSuccess) return e;",
@@ -1139,9 +1220,9 @@ def generate(path: str) -> str:
         if STENCIL == "tile" and COUPLING == "tk" and PERSISTENT:
             tx, ty = tile_2d(P)
             parts.append("    static int occ2 = 0, occ1 = 0;")
-            parts.append("    if (h->dim == 2) return launch_persist<%d, %d>(%s<%d, %d>, %d, &occ2, h, p, X, Y, st);"
-                         % (tx, ty, name, tx, ty, P))
-            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, &occ1, h, p, X, Y, st);" % (name, P))
+            parts.append("    if (h->dim == 2) return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, &occ2, h, p, X, Y, st);"
+                         % (tx, ty, name, tx, ty, P, s + 1))
+            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, &occ1, h, p, X, Y, st);" % (name, P, s + 1))
         elif STENCIL == "tile":
             tx, ty = tile_2d(P)
             parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"

@@ -46,9 +46,10 @@ MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # generated complex64 operator kernel at 511 x 511, P = 84, from an ncu capture
 # (profiles/matvec_c64_511x511_s6_deg3.md).  Reported only while the generator
-# still emits this kernel source (SHA-256 below): a changed kernel reports null.
-MATVEC_TRAFFIC = {"sha256": "9a4a75fd8a1d876a781efdfa70ee4861c1e9e9268ca02ff280f128e2d996fbd4",
-                  "bytes": 182946816 + 132969472}
+# still emits this kernel source and tile (SHA-256 below): a changed kernel
+# reports null.
+MATVEC_TRAFFIC = {"sha256": "a3d8c8025cd28b80947d9161bac4e96fbb2ff1d5c01e13b294d172f6d25d4338",
+                  "bytes": 183078144 + 126157312}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -72,7 +73,8 @@ def matvec_traffic():
     import hashlib
 
     from paper_2209_14740_gb300 import codegen_matvec
-    digest = hashlib.sha256(codegen_matvec.gen_kernel_tk(6, 3)[2].encode()).hexdigest()
+    src = codegen_matvec.gen_kernel_tkp(6, 3)[2] + repr(codegen_matvec.PTILE_2D)
+    digest = hashlib.sha256(src.encode()).hexdigest()
     return MATVEC_TRAFFIC["bytes"] if digest == MATVEC_TRAFFIC["sha256"] else None
 
 
@@ -587,7 +589,7 @@ def run_ours(args):
         line["cfg3_511"] = cfg3
     if mv:
         tr = matvec_traffic()
-        mv["roofline"] = {"kernel": "k_mvk_s6r3<16, 8> (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
+        mv["roofline"] = {"kernel": "k_mvkp_s6r3<32, 4> (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
                           "achieved": mv["gbs"], "peak": mv["peak_gbs"], "unit": "GB/s",
                           "frac": mv["gbs"] / mv["peak_gbs"], "traffic": tr, "peak_kind": mv["peak_kind"]}
         line["matvec"] = mv

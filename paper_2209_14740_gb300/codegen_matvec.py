@@ -63,6 +63,12 @@ F64_HALVES_TILE = (16, 4)
 TILE_2D = (16, 8)
 
 
+# Persistent complex64 kernels: swept on GB300 over 16x4, 32x4, 16x8 and 8x8
+# at P = 84 and P = 20; 32x4 was fastest or level (P = 84: 134 us against
+# 138 us for 16x8).
+PTILE_2D = (32, 4)
+
+
 def tile_2d(P):
     return TILE_2D
 
@@ -1218,7 +1224,7 @@ def generate(path: str) -> str:
         parts.append("  if (h->s == %d && h->r == %d) {" % (s, r))
         parts.append("    *handled = true;")
         if STENCIL == "tile" and COUPLING == "tk" and PERSISTENT:
-            tx, ty = tile_2d(P)
+            tx, ty = PTILE_2D
             parts.append("    static int occ2 = 0, occ1 = 0;")
             parts.append("    if (h->dim == 2) return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, &occ2, h, p, X, Y, st);"
                          % (tx, ty, name, tx, ty, P, s + 1))

@@ -68,8 +68,12 @@ typedef enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_CSL_MEAN = 2 } sg_pre
  * SG_FP32: complex64 operands and arithmetic (reductions accumulate in FP64
  *          across thread blocks).
  * SG_MIXED (sg_gmres only): complex64 inner GMRES inside an FP64 iterative
- *          refinement loop; b, x, x0 are complex128. */
-typedef enum { SG_FP64 = 0, SG_FP32 = 1, SG_MIXED = 2 } sg_precision;
+ *          refinement loop; b, x, x0 are complex128.
+ * SG_TF32 (sg_precond only): complex64 operands, the 2D fast-diagonalisation
+ *          transforms in plain TF32 on the tensor cores (relative error of
+ *          the apply ~2e-3); the preconditioner the complex64 inner cycles
+ *          of sg_gmres use (see there).  Not in the paper. */
+typedef enum { SG_FP64 = 0, SG_FP32 = 1, SG_MIXED = 2, SG_TF32 = 3 } sg_precision;
 
 /* Problem description (Sec. 2.2 wavenumber model; Appendix A grids).
  *   dim    1 or 2 (unit interval / unit square).
@@ -145,8 +149,10 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
 /* Z = (I_P (x) S_blk)^-1 R for the chosen block (see sg_prec), one
  * factorisation applied to all P modes at once (the reshape of Sec. 6.3).
  * SG_PREC_NONE copies R to Z.  R and Z: device, N complex; Z may equal R
- * (in place).  Returns SG_EUNSUPPORTED for 2D problems whose k_0 varies in
- * space (no separable factorisation). */
+ * (in place).  prec SG_FP64, SG_FP32 or SG_TF32 (complex64 data; 2D problems
+ * with lines of at most 320 nodes only, SG_EUNSUPPORTED otherwise).
+ * Returns SG_EUNSUPPORTED for 2D problems whose k_0 varies in space (no
+ * separable factorisation). */
 sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                      void* stream);
 
@@ -211,7 +217,12 @@ typedef struct {
 /* Solves A x = b with restarted, right-preconditioned GMRES: Arnoldi by
  * classical Gram-Schmidt applied twice, complex Givens rotations in FP64 on
  * the device, lazy normalisation of the basis (Sec. 6.3 names GMRES, this
- * library fixes the variant).  b and x: N complex (complex128 for FP64 and
+ * library fixes the variant).  Complex64 cycles (SG_FP32, and the inner
+ * cycles of SG_MIXED) on 2D problems whose preconditioner has the SG_TF32
+ * route run flexible GMRES with that preconditioner: z_j = M^-1 v_j is kept
+ * for every step and the correction is sum_j y_j z_j, so the inexact
+ * preconditioner changes the iteration count, not the attainable residual
+ * (the workspace then holds restart more complex64 vectors).  b and x: N complex (complex128 for FP64 and
  * MIXED, complex64 for FP32), device memory unless opts->host_io.  Blocks
  * the calling host thread until the solve ends.  Returns SG_OK when relres
  * <= tol, SG_ENOTCONV with the last iterate in x otherwise, SG_EBREAKDOWN on

@@ -20,7 +20,7 @@ STATUS_NAMES = ["SG_OK", "SG_EINVAL", "SG_ENOMEM", "SG_ECUDA", "SG_ENOTCONV", "S
                 "SG_ESINGULAR", "SG_ETIMEOUT", "SG_EUNSUPPORTED"]
 BC_DIRICHLET, BC_ABSORBING = 0, 1
 PREC_NONE, PREC_MEAN, PREC_CSL_MEAN = 0, 1, 2
-FP64, FP32, MIXED = 0, 1, 2
+FP64, FP32, MIXED, TF32 = 0, 1, 2, 3
 X0_AS_GIVEN, X0_FALLBACK, X0_SCALED = 0, 1, 2
 
 # every symbol include/sg.h declares

@@ -426,6 +426,40 @@ static cudaError_t cgemm(const sg_handle* h, int M, int Nn, int K, const C2<T>* 
   return cudaGetLastError();
 }
 
+// FP32 2D apply by fast diagonalisation: tensor-core transforms, each a GEMM
+// with a constant right factor; the per-batch transposes in (1) and (3) move
+// the direction being transformed into the rows' contiguous index:
+//   (1) T1'_p = (R_p Qhat_x)^T          [p][i][y]
+//   (2) T2'_p = L^-1 o (T1'_p Qhat_y)   [p][i][j], L^-1 indexed (j, i)
+//   (3) T3_p  = (T2'_p Qhat_y^T)^T      [p][y][i]
+//   (4) Z_p   = T3_p Qhat_x^T           [p][y][x]
+// The intermediates keep rows of even length (my or mx rounded up to even),
+// so the next transform reads them with 16-byte copies; their P mx myp or
+// P my mxp complex values fit in the scratch of N complex128 (= 2N
+// complex64).  split: FP32 accuracy (3xTF32), else plain TF32.
+static cudaError_t fd_apply(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                            const int* skip, const double* in_scale, float2* tmp, float2* tmp2, bool split) {
+  const int mx = h->mx, my = h->my, P = h->P;
+  const int mxp = mx + (mx & 1), myp = my + (my & 1);
+  cudaError_t e =
+      tc_cgemm(h->tcB[0], R, mx, P * my, tmp, myp, 1, my, nullptr, 0, 1, nullptr, skip, h->d_err, st, split);
+  if (e == cudaSuccess)
+    e = tc_cgemm(h->tcB[1], tmp, myp, P * mx, tmp2, myp, 0, 0, h->d_Linv32[which], mx, mx, in_scale, skip,
+                 h->d_err, st, split);
+  if (e == cudaSuccess)
+    e = tc_cgemm(h->tcB[2], tmp2, myp, P * mx, tmp, mxp, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st, split);
+  if (e == cudaSuccess)
+    e = tc_cgemm(h->tcB[3], tmp, mxp, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st, split);
+  return e;
+}
+
+cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                                const int* skip, const double* in_scale) {
+  if (h->dim != 2 || !h->fd || !h->blk[which].ready) return cudaErrorNotSupported;
+  return fd_apply(h, which, R, Z, st, skip, in_scale, reinterpret_cast<float2*>(h->d_tmp),
+                  reinterpret_cast<float2*>(h->d_tmp2), false);
+}
+
 // Z = M^-1 R for block `which`; tmp and tmp2 hold N complex128 values each
 // (tmp2 only for 2D; the FP32 2D transforms use up to 2N complex64 of each
 // for their even-length rows).  R and Z may be the same vector.
@@ -463,30 +497,7 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
   const int mx = h->mx, my = h->my, P = h->P;
   const long long plane = (long long)mx * my;
   if constexpr (sizeof(T) == 4) {
-    if (h->fd) {
-      // Tensor-core transforms, each a GEMM with a constant right factor; the
-      // per-batch transposes in (1) and (3) move the direction being
-      // transformed into the rows' contiguous index:
-      //   (1) T1'_p = (R_p Qhat_x)^T          [p][i][y]
-      //   (2) T2'_p = L^-1 o (T1'_p Qhat_y)   [p][i][j], L^-1 indexed (j, i)
-      //   (3) T3_p  = (T2'_p Qhat_y^T)^T      [p][y][i]
-      //   (4) Z_p   = T3_p Qhat_x^T           [p][y][x]
-      // The intermediates keep rows of even length (my or mx rounded up to
-      // even), so the next transform reads them with 16-byte copies; their
-      // P mx myp or P my mxp complex values fit in the scratch of N
-      // complex128 (= 2N complex64).
-      const int mxp = mx + (mx & 1), myp = my + (my & 1);
-      cudaError_t e =
-          tc_cgemm(h->tcB[0], R, mx, P * my, tmp, myp, 1, my, nullptr, 0, 1, nullptr, skip, h->d_err, st);
-      if (e == cudaSuccess)
-        e = tc_cgemm(h->tcB[1], tmp, myp, P * mx, tmp2, myp, 0, 0, h->d_Linv32[which], mx, mx, in_scale, skip,
-                     h->d_err, st);
-      if (e == cudaSuccess)
-        e = tc_cgemm(h->tcB[2], tmp2, myp, P * mx, tmp, mxp, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st);
-      if (e == cudaSuccess)
-        e = tc_cgemm(h->tcB[3], tmp, mxp, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st);
-      return e;
-    }
+    if (h->fd) return fd_apply(h, which, R, Z, st, skip, in_scale, tmp, tmp2, true);
   }
   const C2<T>* Q;
   const C2<T>* Qt;

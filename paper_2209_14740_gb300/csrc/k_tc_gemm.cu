@@ -14,6 +14,9 @@
 // x = hi + lo with hi = tf32(x), lo = x - hi, and C = Xhi Bhi + Xhi Blo +
 // Xlo Bhi; the dropped Xlo Blo term is below FP32 rounding.  B's split is
 // precomputed on the host, X's is formed per tile in shared memory.
+// Without the split (SPLIT = false) C = X Bhi in plain TF32 (X's low
+// mantissa bits are ignored by the tensor core): one MMA per K step, X
+// copied straight into the MMA layout, relative error ~1e-3.
 //
 // One CTA owns 128 rows and BN (64 or 128) real output columns; the
 // accumulator (128 lanes x BN columns FP32) lives in tensor memory.  K is
@@ -58,18 +61,23 @@ constexpr int RAW_TILE = BM * RAW_PITCH;
 constexpr int A_TILE = BM * BK * 4;     // 16 KB, core-matrix layout
 constexpr int OFF_RAW = 0;
 
-// Layout that depends on the tile width.
-template <int BN>
+// Layout that depends on the tile width and on the split.
+template <int BN, bool SPLIT>
 struct Cfg {
   // B slots: a slot is refilled once the MMAs of the stage that used it
   // have completed, so more slots let the copies run further ahead
-  static constexpr int NBS = BN == 64 ? 4 : 3;
-  // raw X slots: stages s .. s + NRAW - 1 in flight
-  static constexpr int NRAW = BN == 64 ? 4 : 3;
+  static constexpr int NBS = (BN == 64 || !SPLIT) ? 4 : 3;
+  // raw X slots (split only): stages s .. s + NRAW - 1 in flight
+  static constexpr int NRAW = !SPLIT ? 0 : BN == 64 ? 4 : 3;
+  // A slots: split (hi, lo) pairs, or X tiles copied straight into the MMA
+  // layout (stages s .. s + NA - 1 in flight)
+  static constexpr int NA = SPLIT ? NAS : 4;
+  static constexpr int A_SLOT = SPLIT ? 2 * A_TILE : A_TILE;
+  static constexpr int NBP = SPLIT ? 2 : 1;                      // B parts per slot (hi, lo)
   static constexpr int B_TILE = BN * BK * 4;                     // 8 or 16 KB
   static constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;        // [slot][hi, lo]
-  static constexpr int OFF_A = ((OFF_B + NBS * 2 * B_TILE + 1023) / 1024) * 1024;   // [slot][hi, lo]
-  static constexpr int OFF_BAR = OFF_A + NAS * 2 * A_TILE;      // full[NAS], bfull[NBS], done[NDONE], TMEM addr, abort
+  static constexpr int OFF_A = ((OFF_B + NBS * NBP * B_TILE + 1023) / 1024) * 1024;
+  static constexpr int OFF_BAR = OFF_A + NA * A_SLOT;           // full[NA], bfull[NBS], done[NDONE], TMEM addr, abort
   static constexpr int SMEM_BYTES = OFF_BAR + 128 + 1024;        // + slack for 1024-byte alignment
   static constexpr int OUT_PITCH = BN / 2 + 1;                   // float2 per staged output row
   static constexpr uint32_t TMEM_COLS = BN;
@@ -78,9 +86,9 @@ struct Cfg {
   static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                     ((uint32_t)(BM >> 4) << 24);
   static_assert(BN == 64 || BN == 128, "tile width");
-  // the row-major output is staged over the raw and B slots (free by then)
-  static_assert(BM * OUT_PITCH * 8 <= OFF_A, "output staging must fit below the A slots");
-  static_assert(8 * (NAS + NBS + NDONE) + 16 <= 128, "barrier area");
+  // the row-major output is staged over the data slots (free by then)
+  static_assert(BM * OUT_PITCH * 8 <= OFF_BAR, "output staging must fit below the barriers");
+  static_assert(8 * (NA + NBS + NDONE) + 16 <= 128, "barrier area");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
 
@@ -225,20 +233,20 @@ __device__ __forceinline__ bool loader_sync_or(bool v) {
 // so the split of stage s+1 and the copies of later stages overlap the MMAs
 // of stage s.  No waiter can fall two phases behind on a barrier: the MMA
 // lane runs at most two stages ahead of the loaders and cannot pass the copier.
-template <int BN>
+template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   using namespace tc;
-  using L = Cfg<BN>;
-  constexpr int NBS = L::NBS, B_TILE = L::B_TILE, NRAW = L::NRAW, OFF_B = L::OFF_B;
+  using L = Cfg<BN, SPLIT>;
+  constexpr int NBS = L::NBS, B_TILE = L::B_TILE, NRAW = L::NRAW, OFF_B = L::OFF_B, NA = L::NA;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t s_base = smem_u32(sm);
-  const uint32_t full0 = s_base + L::OFF_BAR;    // NAS barriers, count NLOAD
-  const uint32_t bfull0 = full0 + 8 * NAS;       // NBS barriers, count 1 + transaction bytes
+  const uint32_t full0 = s_base + L::OFF_BAR;    // NA barriers, count NLOAD
+  const uint32_t bfull0 = full0 + 8 * NA;        // NBS barriers, count 1 + transaction bytes
   const uint32_t done0 = bfull0 + 8 * NBS;       // NDONE barriers, count 1 (MMA commit)
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::OFF_BAR + 8 * (NAS + NBS + NDONE));
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::OFF_BAR + 8 * (NAS + NBS + NDONE) + 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::OFF_BAR + 8 * (NA + NBS + NDONE));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::OFF_BAR + 8 * (NA + NBS + NDONE) + 8);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < NAS; ++i)
+    for (int i = 0; i < NA; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * i), "n"(NLOAD) : "memory");
     for (int i = 0; i < NBS; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bfull0 + 8 * i) : "memory");
@@ -265,10 +273,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   const float* Bl = a.Blo + (size_t)blockIdx.y * a.nks * (BN * BK);
   auto copy_b = [&](int t) {
     const uint32_t bar = bfull0 + 8 * (t % NBS);
-    const uint32_t dst = s_base + OFF_B + (t % NBS) * 2 * B_TILE;
-    mbar_expect_tx(bar, 2u * B_TILE);
+    const uint32_t dst = s_base + OFF_B + (t % NBS) * L::NBP * B_TILE;
+    mbar_expect_tx(bar, (uint32_t)(L::NBP * B_TILE));
     bulk_g2s(dst, Bh + (size_t)t * (BN * BK), B_TILE, bar);
-    bulk_g2s(dst + B_TILE, Bl + (size_t)t * (BN * BK), B_TILE, bar);
+    if (SPLIT) bulk_g2s(dst + B_TILE, Bl + (size_t)t * (BN * BK), B_TILE, bar);
   };
   // B is constant: its first stages are copied before the wait below
   const int pre = a.nks < NBS ? a.nks : NBS;
@@ -282,68 +290,118 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   const int nks = skipped ? 0 : a.nks;
 
   if (warp < MMA_WARP) {
-    // ---------------------------------------------------------------- loaders
-    auto issue = [&](int t) {
-      const uint32_t raw = s_base + OFF_RAW + (t % NRAW) * RAW_TILE;
-      const int k0 = t * BK;
-      if (a.vec16) {
-#pragma unroll
-        for (int q = 0; q < (BM * BK / 4) / NLOAD; ++q) {
-          const int idx = tid + q * NLOAD;
-          const int r = idx >> 3, c = idx & 7;
-          const int m = m0 + r, k = k0 + 4 * c;
-          const int rem = (a.K2 - k) * 4;
-          const int bytes = (m < a.M && rem > 0) ? (rem < 16 ? rem : 16) : 0;
-          const float* src = bytes ? a.X + (size_t)m * a.ldx + k : a.X;
-          cp_async16z(raw + r * RAW_PITCH + c * 16, src, bytes);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < (BM * BK / 2) / NLOAD; ++q) {
-          const int idx = tid + q * NLOAD;
-          const int r = idx >> 4, kp = idx & 15;
-          const int m = m0 + r, k = k0 + 2 * kp;
-          const bool ok = m < a.M && k < a.K2;
-          const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
-          cp_async8(raw + r * RAW_PITCH + kp * 8, src, ok ? 8 : 0);
-        }
-      }
-    };
-    for (int t = 0; t < NRAW - 1; ++t) {
-      if (t < nks) issue(t);
-      cp_commit();
-    }
     bool bad = false;
-    for (int s = 0; s < nks; ++s) {
-      cp_wait<NRAW - 2>();
-      bool to = false;
-      if (s >= 2) to = !mbar_wait(done0 + 8 * ((s - 2) % NDONE), ((s - 2) / NDONE) & 1);
-      if (loader_sync_or(to || *abort_flag != 0)) { bad = true; break; }
-      // split X into hi / lo: two threads per row, four 16-byte chunks each
-      {
-        const int row = tid & (BM - 1), half = tid >> 7;
-        const unsigned char* raw = sm + OFF_RAW + (s % NRAW) * RAW_TILE + row * RAW_PITCH;
-        unsigned char* ahi = sm + L::OFF_A + (s % NAS) * 2 * A_TILE;
-        unsigned char* alo = ahi + A_TILE;
-#pragma unroll
-        for (int cc = 0; cc < BK / 8; ++cc) {
-          const int c = half * (BK / 8) + cc;
-          const float4 v = *reinterpret_cast<const float4*>(raw + 16 * c);
-          float4 h, l;
-          h.x = tf32_hi(v.x); l.x = v.x - h.x;
-          h.y = tf32_hi(v.y); l.y = v.y - h.y;
-          h.z = tf32_hi(v.z); l.z = v.z - h.z;
-          h.w = tf32_hi(v.w); l.w = v.w - h.w;
-          *reinterpret_cast<float4*>(ahi + core_off(row, 4 * c)) = h;
-          *reinterpret_cast<float4*>(alo + core_off(row, 4 * c)) = l;
+    if constexpr (!SPLIT) {
+      // ----------------------------------------- loaders (no split): X tiles
+      // go straight into the MMA layout; each loader arrives on full[s % NA]
+      // once its own copies of stage s have landed
+      auto issue = [&](int t) {
+        const uint32_t dst = s_base + L::OFF_A + (t % NA) * L::A_SLOT;
+        const int k0 = t * BK;
+        if (a.vec16) {
+  #pragma unroll
+          for (int q = 0; q < (BM * BK / 4) / NLOAD; ++q) {
+            const int idx = tid + q * NLOAD;
+            const int r = idx >> 3, c = idx & 7;
+            const int m = m0 + r, k = k0 + 4 * c;
+            const int rem = (a.K2 - k) * 4;
+            const int bytes = (m < a.M && rem > 0) ? (rem < 16 ? rem : 16) : 0;
+            const float* src = bytes ? a.X + (size_t)m * a.ldx + k : a.X;
+            cp_async16z(dst + core_off(r, 4 * c), src, bytes);
+          }
+        } else {
+  #pragma unroll
+          for (int q = 0; q < (BM * BK / 2) / NLOAD; ++q) {
+            const int idx = tid + q * NLOAD;
+            const int r = idx >> 4, kp = idx & 15;
+            const int m = m0 + r, k = k0 + 2 * kp;
+            const bool ok = m < a.M && k < a.K2;
+            const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
+            cp_async8(dst + core_off(r, 2 * kp), src, ok ? 8 : 0);
+          }
         }
+      };
+      for (int t = 0; t < NA - 1; ++t) {
+        if (t < nks) issue(t);
+        cp_commit();
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(full0 + 8 * (s % NAS));
-      // the raw slot of stage s+NRAW-1 was split at s-1 by every loader
-      // (all of them passed the barrier above since)
-      if (s + NRAW - 1 < nks) issue(s + NRAW - 1);
-      cp_commit();
+      for (int s = 0; s < nks; ++s) {
+        cp_wait<NA - 2>();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(full0 + 8 * (s % NA));
+        // stage s+NA-1 goes to the slot of stage s-1 once its MMAs are done
+        if (s + NA - 1 < nks) {
+          if (s >= 1 && !mbar_wait(done0 + 8 * ((s - 1) % NDONE), ((s - 1) / NDONE) & 1)) {
+            bad = true;
+            break;
+          }
+          issue(s + NA - 1);
+        }
+        cp_commit();
+      }
+    } else {
+      // ----------------------------------------- loaders (split)
+      auto issue = [&](int t) {
+        const uint32_t raw = s_base + OFF_RAW + (t % NRAW) * RAW_TILE;
+        const int k0 = t * BK;
+        if (a.vec16) {
+  #pragma unroll
+          for (int q = 0; q < (BM * BK / 4) / NLOAD; ++q) {
+            const int idx = tid + q * NLOAD;
+            const int r = idx >> 3, c = idx & 7;
+            const int m = m0 + r, k = k0 + 4 * c;
+            const int rem = (a.K2 - k) * 4;
+            const int bytes = (m < a.M && rem > 0) ? (rem < 16 ? rem : 16) : 0;
+            const float* src = bytes ? a.X + (size_t)m * a.ldx + k : a.X;
+            cp_async16z(raw + r * RAW_PITCH + c * 16, src, bytes);
+          }
+        } else {
+  #pragma unroll
+          for (int q = 0; q < (BM * BK / 2) / NLOAD; ++q) {
+            const int idx = tid + q * NLOAD;
+            const int r = idx >> 4, kp = idx & 15;
+            const int m = m0 + r, k = k0 + 2 * kp;
+            const bool ok = m < a.M && k < a.K2;
+            const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
+            cp_async8(raw + r * RAW_PITCH + kp * 8, src, ok ? 8 : 0);
+          }
+        }
+      };
+      for (int t = 0; t < NRAW - 1; ++t) {
+        if (t < nks) issue(t);
+        cp_commit();
+      }
+      for (int s = 0; s < nks; ++s) {
+        cp_wait<NRAW - 2>();
+        bool to = false;
+        if (s >= 2) to = !mbar_wait(done0 + 8 * ((s - 2) % NDONE), ((s - 2) / NDONE) & 1);
+        if (loader_sync_or(to || *abort_flag != 0)) { bad = true; break; }
+        // split X into hi / lo: two threads per row, four 16-byte chunks each
+        {
+          const int row = tid & (BM - 1), half = tid >> 7;
+          const unsigned char* raw = sm + OFF_RAW + (s % NRAW) * RAW_TILE + row * RAW_PITCH;
+          unsigned char* ahi = sm + L::OFF_A + (s % NAS) * 2 * A_TILE;
+          unsigned char* alo = ahi + A_TILE;
+  #pragma unroll
+          for (int cc = 0; cc < BK / 8; ++cc) {
+            const int c = half * (BK / 8) + cc;
+            const float4 v = *reinterpret_cast<const float4*>(raw + 16 * c);
+            float4 h, l;
+            h.x = tf32_hi(v.x); l.x = v.x - h.x;
+            h.y = tf32_hi(v.y); l.y = v.y - h.y;
+            h.z = tf32_hi(v.z); l.z = v.z - h.z;
+            h.w = tf32_hi(v.w); l.w = v.w - h.w;
+            *reinterpret_cast<float4*>(ahi + core_off(row, 4 * c)) = h;
+            *reinterpret_cast<float4*>(alo + core_off(row, 4 * c)) = l;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(full0 + 8 * (s % NAS));
+        // the raw slot of stage s+NRAW-1 was split at s-1 by every loader
+        // (all of them passed the barrier above since)
+        if (s + NRAW - 1 < nks) issue(s + NRAW - 1);
+        cp_commit();
+      }
     }
     // all MMAs done before the accumulator is read
     if (!bad && nks > 0 && !mbar_wait(done0 + 8 * ((nks - 1) % NDONE), ((nks - 1) / NDONE) & 1)) bad = true;
@@ -417,18 +475,20 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     if (lane == 0) {
       int last = -1;
       for (int s = 0; s < nks; ++s) {
-        if (!mbar_wait(full0 + 8 * (s % NAS), (s / NAS) & 1)) { *abort_flag = 1; break; }
+        if (!mbar_wait(full0 + 8 * (s % NA), (s / NA) & 1)) { *abort_flag = 1; break; }
         if (!mbar_wait(bfull0 + 8 * (s % NBS), (s / NBS) & 1)) { *abort_flag = 1; break; }
         if (*abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ahi = s_base + L::OFF_A + (s % NAS) * 2 * A_TILE, alo = ahi + A_TILE;
-        const uint32_t bhi = s_base + OFF_B + (s % NBS) * 2 * B_TILE, blo = bhi + B_TILE;
+        const uint32_t ahi = s_base + L::OFF_A + (s % NA) * L::A_SLOT, alo = ahi + A_TILE;
+        const uint32_t bhi = s_base + OFF_B + (s % NBS) * L::NBP * B_TILE, blo = bhi + B_TILE;
 #pragma unroll
         for (int ks = 0; ks < BK / 8; ++ks) {
           const uint32_t o = 256u * ks;   // 8 TF32 = two core matrices along K
           mma_tf32(tmem, sdesc(ahi + o), sdesc(bhi + o), L::IDESC, (s > 0 || ks > 0) ? 1u : 0u);
-          mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), L::IDESC, 1u);
-          mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), L::IDESC, 1u);
+          if (SPLIT) {
+            mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), L::IDESC, 1u);
+            mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), L::IDESC, 1u);
+          }
         }
         mma_commit(done0 + 8 * (s % NDONE));
         last = s;
@@ -520,14 +580,20 @@ int tc_tile_width(long long rows, int ndim, int num_sms) {
 static void tc_attributes() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_tc_cgemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<64>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_tc_cgemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<128>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc::Cfg<64, true>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc::Cfg<128, true>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc::Cfg<64, false>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc::Cfg<128, false>::SMEM_BYTES);
   });
 }
 
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
-                     int* err, cudaStream_t st) {
+                     int* err, cudaStream_t st, bool split) {
   if (B.bn != 64 && B.bn != 128) return cudaErrorInvalidValue;
   if (mode == 1 && (MB <= 0 || ldc < MB)) return cudaErrorInvalidValue;
   tc_attributes();
@@ -563,12 +629,18 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if (B.bn == 128) {
-    cfg.dynamicSmemBytes = tc::Cfg<128>::SMEM_BYTES;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128>, a);
+  if (B.bn == 128 && split) {
+    cfg.dynamicSmemBytes = tc::Cfg<128, true>::SMEM_BYTES;
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, true>, a);
+  } else if (split) {
+    cfg.dynamicSmemBytes = tc::Cfg<64, true>::SMEM_BYTES;
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, true>, a);
+  } else if (B.bn == 128) {
+    cfg.dynamicSmemBytes = tc::Cfg<128, false>::SMEM_BYTES;
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, false>, a);
   } else {
-    cfg.dynamicSmemBytes = tc::Cfg<64>::SMEM_BYTES;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64>, a);
+    cfg.dynamicSmemBytes = tc::Cfg<64, false>::SMEM_BYTES;
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, false>, a);
   }
   note_launch();
   return e != cudaSuccess ? e : cudaGetLastError();

@@ -699,7 +699,8 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
 
 sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z, void* stream) {
   if (!h || !R || !Z) return fail(SG_EINVAL, "NULL handle or vector");
-  if (prec != SG_FP64 && prec != SG_FP32) return fail(SG_EINVAL, "sg_precond precision must be SG_FP64 or SG_FP32");
+  if (prec != SG_FP64 && prec != SG_FP32 && prec != SG_TF32)
+    return fail(SG_EINVAL, "sg_precond precision must be SG_FP64, SG_FP32 or SG_TF32");
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = (size_t)h->N * (prec == SG_FP64 ? sizeof(double2) : sizeof(float2));
   if (kind == SG_PREC_NONE) {
@@ -710,8 +711,15 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
   int which = kind == SG_PREC_MEAN ? 0 : 1;
   if (!h->blk[which].ready)
     return fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
-  if (prec == SG_FP64) SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));
-  else SG_CUDA_TRY(launch_precond<float>(h, which, (const float2*)R, (float2*)Z, st));
+  if (prec == SG_TF32) {
+    if (h->dim != 2 || !h->fd)
+      return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with the fast-diagonalisation route (lines <= 320)");
+    SG_CUDA_TRY(launch_precond_tf32(h, which, (const float2*)R, (float2*)Z, st, nullptr, nullptr));
+  } else if (prec == SG_FP64) {
+    SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));
+  } else {
+    SG_CUDA_TRY(launch_precond<float>(h, which, (const float2*)R, (float2*)Z, st));
+  }
   return SG_OK;
 }
 

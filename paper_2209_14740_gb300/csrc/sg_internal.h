@@ -84,17 +84,20 @@ TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, 
 int tc_tile_width(long long rows, int ndim, int num_sms);
 // C = X Q for M complex64 rows X (row stride ldx complex), placement mode 0
 // (row-major, ldc) or 1 (per-batch transpose, batches of MB rows, transposed
-// rows ldc >= MB apart); 16-byte loads of X when ldx is even; optional
+// rows ldc >= MB apart); 16-byte loads of X when ldx is even; split: FP32
+// accuracy (3xTF32), else plain TF32 (one MMA per K step); optional
 // elementwise factor E[n * e_ld + m % e_mod] * (*escale).
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
-                     int* err, cudaStream_t st);
+                     int* err, cudaStream_t st, bool split = true);
 
 struct GmresWork {
   int restart = 0;         // basis capacity (columns restart+1)
   int prec_bytes = 0;      // 8 (c64) or 16 (c128) per element of V
   void* V = nullptr;       // (restart+1) * N inner precision
   void* Z = nullptr;       // N inner precision
+  void* Zb = nullptr;      // flexible GMRES (complex64 inner cycles with the TF32 preconditioner):
+                           // z_j = M^-1 v_j for every step j, restart * N complex64
   void* R64 = nullptr;     // N complex128 (mixed: outer residual; fp64: A x)
   void* X64 = nullptr;     // N complex128 staging for host_io / x0
   void* B64 = nullptr;     // N complex128 staging for host_io
@@ -182,6 +185,12 @@ cudaError_t launch_tri_factor(int nsys, int len, const double2* diag, const doub
 template <typename T>
 cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                            const int* skip = nullptr, const double* in_scale = nullptr);
+
+// FP32 apply of a 2D preconditioner with the fast-diagonalisation transforms
+// in plain TF32 (relative error ~1e-3: a fixed but inexact preconditioner,
+// used by flexible GMRES); cudaErrorNotSupported without that route.
+cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                                const int* skip, const double* in_scale);
 
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,

@@ -497,8 +497,9 @@ __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j) {
 }
 
 // y = R^-1 g (k x k upper triangle of the rotated Hessenberg matrix);
-// yc_i = y_i * vscale_i for the raw-basis linear combination.
-__global__ void k_lsq(double* D, const int* ctl, DevLayout L) {
+// yc_i = y_i * vscale_i for the raw-basis linear combination (raw != 0), or
+// y_i itself for the combination of the stored z_j (flexible GMRES).
+__global__ void k_lsq(double* D, const int* ctl, DevLayout L, int raw) {
   const int k = ctl[CTL_K];
   const int m = L.m;
   const double2* H = reinterpret_cast<const double2*>(D + L.H);
@@ -518,7 +519,8 @@ __global__ void k_lsq(double* D, const int* ctl, DevLayout L) {
     yc[i] = den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
                     : make_double2(0, 0);
   }
-  for (int i = 0; i < k; ++i) yc[i] = make_double2(yc[i].x * vs[i], yc[i].y * vs[i]);
+  if (raw)
+    for (int i = 0; i < k; ++i) yc[i] = make_double2(yc[i].x * vs[i], yc[i].y * vs[i]);
   for (int i = k; i <= m; ++i) yc[i] = make_double2(0, 0);
 }
 
@@ -630,7 +632,7 @@ void sgi_free_gmres_work(sg_handle* h) {
   for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
   if (w.stream) cudaStreamDestroy(w.stream);
   if (w.ev) cudaEventDestroy(w.ev);
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.Zb); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
   cudaFree(w.dscal); cudaFree(w.dctl); cudaFree(w.part); cudaFree(w.counter);
   w = GmresWork{};
 }
@@ -661,6 +663,9 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   cudaError_t e = cudaSuccess;
   if (!e) e = cudaMalloc(&w.V, (size_t)(m + 1) * N * elem_bytes);
   if (!e) e = cudaMalloc(&w.Z, N * elem_bytes);
+  // complex64 inner cycles on 2D problems with the fast-diagonalisation route
+  // run flexible GMRES with the TF32 preconditioner: keep every z_j
+  if (!e && elem_bytes == (int)sizeof(float2) && h->dim == 2 && h->fd) e = cudaMalloc(&w.Zb, (size_t)m * N * elem_bytes);
   if (!e) e = cudaMalloc(&w.R64, N * sizeof(double2));
   if (!e) e = cudaMalloc(&w.X64, N * sizeof(double2));
   if (!e) e = cudaMalloc(&w.B64, N * sizeof(double2));
@@ -710,20 +715,38 @@ cudaError_t precond_apply(Ctx& c, sg_prec prec, const C2<T>* R, C2<T>* Z, const 
   return launch_precond<T>(c.h, prec == SG_PREC_MEAN ? 0 : 1, R, Z, c.st, skip, in_scale);
 }
 
+// Flexible GMRES (complex64 inner cycles with a preconditioner that has a
+// plain-TF32 route): z_j = M^-1 v_j is kept for every step and the cycle's
+// correction is sum_j y_j z_j, so A Z = V H holds for the z_j actually
+// computed and the inexact (relative error ~1e-3) preconditioner changes
+// only the iteration count, not the attainable residual.
+template <typename T>
+static bool flexible(const Ctx& c, sg_prec prec) {
+  return sizeof(T) == sizeof(float) && prec != SG_PREC_NONE && c.h->gw.Zb != nullptr;
+}
+
 // One Arnoldi step j with CGS2 on the inner-precision basis.
 template <typename T>
 cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   GmresWork& w = c.h->gw;
   const long long N = c.h->N;
   C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
-  C2<T>* Z = reinterpret_cast<C2<T>*>(w.Z);
   C2<T>* vj = V + (size_t)j * N;
   C2<T>* wv = V + (size_t)(j + 1) * N;
   double* D = w.dscal;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   // z = M^-1 v_j with v_j = vscale_j V_j (normalised on the fly, so the raw
   // basis norms stay of the size of h_{j+1,j})
-  if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
+  C2<T>* Z;
+  if (flexible<T>(c, prec)) {
+    Z = reinterpret_cast<C2<T>*>(w.Zb) + (size_t)j * N;
+    if constexpr (sizeof(T) == sizeof(float))
+      e = launch_precond_tf32(c.h, prec == SG_PREC_MEAN ? 0 : 1, vj, Z, c.st, w.dctl, D + c.L.vscale + j);
+    if (e) return e;
+  } else {
+    Z = reinterpret_cast<C2<T>*>(w.Z);
+    if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
+  }
   if ((e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
   const int nv = j + 1;
   const size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
@@ -779,7 +802,8 @@ cudaError_t arnoldi_steps(Ctx& c, sg_prec prec, int j0, int len) {
 }
 
 // Runs one restart cycle whose starting residual is already in V[0] with its
-// squared norm in sc[RNORM2].  Leaves the correction u = M^-1 (V y) in Z.
+// squared norm in sc[RNORM2].  Leaves the correction u = M^-1 (V y) (or, for
+// flexible GMRES, sum_j y_j z_j) in Z.
 template <typename T>
 sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int check_every, bool* any_step) {
   GmresWork& w = c.h->gw;
@@ -799,10 +823,12 @@ sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int
   *any_step = true;
   C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
   C2<T>* Z = reinterpret_cast<C2<T>*>(w.Z);
-  k_lsq<<<1, 1, 0, c.st>>>(w.dscal, w.dctl, c.L); note_launch();
-  k_lincomb<T><<<c.grid, RED_THREADS, 0, c.st>>>(V, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
+  const bool flex = flexible<T>(c, prec);
+  k_lsq<<<1, 1, 0, c.st>>>(w.dscal, w.dctl, c.L, flex ? 0 : 1); note_launch();
+  const C2<T>* basis = flex ? reinterpret_cast<const C2<T>*>(w.Zb) : V;
+  k_lincomb<T><<<c.grid, RED_THREADS, 0, c.st>>>(basis, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
   SG_CUDA_TRY(cudaGetLastError());
-  SG_CUDA_TRY(precond_apply<T>(c, prec, Z, Z, nullptr));
+  if (!flex) SG_CUDA_TRY(precond_apply<T>(c, prec, Z, Z, nullptr));
   return SG_OK;
 }
 

@@ -142,7 +142,8 @@ def test_255_precond_wide_tiles(B):
     transforms (ragged in rows and columns) and odd lines, so the
     intermediates have padded even-length rows.  Checked by the residual of
     the n x n block on sampled modes and against the FP64 apply (sweeps on
-    the CUDA cores, a separate code path), on two calls in a row."""
+    the CUDA cores, a separate code path), on two calls in a row; the
+    plain-TF32 apply against the same, within its 5e-3 bound."""
     pr = inputs.helmholtz_2d(255, 3, 3, 30.0, 0.15)
     op = B.SG(pr)
     assert op.info["fast_diag"]
@@ -160,6 +161,10 @@ def test_255_precond_wide_tiles(B):
             op.precond(R32, Z32, kind, B.FP32)
             err = float(torch.linalg.vector_norm(Z32.to(torch.complex128) - Z) / torch.linalg.vector_norm(Z))
             assert err < 2e-4, (call, kind, err)
+            Zt = torch.empty_like(R32)
+            op.precond(R32, Zt, kind, B.TF32)
+            errt = float(torch.linalg.vector_norm(Zt.to(torch.complex128) - Z) / torch.linalg.vector_norm(Z))
+            assert errt < 5e-3, (call, kind, errt)
             if kind == B.PREC_MEAN:
                 for mode in (0, 7, 19):
                     z32 = Z32[mode * n:(mode + 1) * n].cpu().numpy().astype(np.complex128)

@@ -142,6 +142,42 @@ def test_precond(B, idx, kind):
     op.close()
 
 
+@pytest.mark.parametrize("idx", [7, 8, 9, 10])
+@pytest.mark.parametrize("kind", [1, 2])
+def test_precond_tf32(B, idx, kind):
+    """The plain-TF32 apply (the preconditioner of the complex64 GMRES
+    cycles): TF32 inputs carry a relative rounding of 2^-11 (the factors,
+    rounded) to 2^-10 (the data, truncated by the tensor core), through four
+    transforms whose eigenvector factors have condition numbers below 10, so
+    the apply is within ~2e-3 of the exact block solve; 5e-3 is the bound."""
+    pr = problems()[idx]
+    ref = sg.assemble_problem(pr)
+    blk = ref.S0 if kind == 1 else sg.csl_mean_block(ref, pr.beta)
+    M = krylov.BlockPrecond(blk, ref.P)
+    op = B.SG(pr)
+    x32 = rand_vec(op.N, 200 + idx).astype(np.complex64)
+    zr = M(x32.astype(np.complex128))
+    X = torch.from_numpy(x32).to(DEV)
+    Z = torch.empty_like(X)
+    op.precond(X, Z, kind, B.TF32)
+    e = np.linalg.norm(Z.cpu().numpy() - zr) / np.linalg.norm(zr)
+    assert e < 5e-3, e
+    # in place, and a second call gives the same result (a fixed operator)
+    Xi = X.clone()
+    op.precond(Xi, Xi, kind, B.TF32)
+    assert torch.equal(Xi, Z)
+    op.close()
+
+
+def test_precond_tf32_needs_the_2d_route(B):
+    op = B.SG(problems()[0])     # 1D
+    X = torch.zeros(op.N, dtype=torch.complex64, device=DEV)
+    with pytest.raises(B.SgError) as ei:
+        op.precond(X, X, B.PREC_MEAN, B.TF32)
+    assert ei.value.status == B.SG_EUNSUPPORTED
+    op.close()
+
+
 def test_precond_unsupported_for_varying_k0(B):
     pr = problems()[3]
     assert np.ptp(pr.k0) > 0

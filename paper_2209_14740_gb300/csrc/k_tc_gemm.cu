@@ -21,10 +21,12 @@
 // One CTA owns 128 rows and BN (64 or 128) real output columns; the
 // accumulator (128 lanes x BN columns FP32) lives in tensor memory.  K is
 // walked in stages of 32 real values.  Warp roles:
-//   warps 0-7  copy raw X rows by cp.async (two or three stages ahead;
-//              16-byte copies when the row pitch allows), split them into hi/lo in the
-//              canonical K-major layout (8-row x 16-byte core matrices, no
-//              swizzle), and run the epilogue;
+//   warps 0-7  copy raw X rows by cp.async (16-byte copies when the row
+//              pitch allows) two or three stages ahead and split them into
+//              hi/lo in the canonical K-major layout (8-row x 16-byte core
+//              matrices, no swizzle), or, without the split, copy X straight
+//              into that layout three stages ahead; then they run the
+//              epilogue;
 //   warp 8     one lane issues the 12 MMAs of each stage (M=128, N=BN, K=8)
 //              and commits them to an mbarrier;
 //   warp 9     one lane copies the pre-laid-out B tiles (hi and lo) of each
@@ -55,7 +57,6 @@ constexpr int NLOAD = 256;              // loader / splitter / epilogue threads 
 constexpr int MMA_WARP = NLOAD / 32;    // warp 8
 constexpr int THREADS = NLOAD + 64;     // + the MMA warp and the B-copy warp
 constexpr int NAS = 2;                  // split A (hi, lo) slots
-constexpr int NDONE = 4;                // MMA-completion barriers, indexed by stage % 4
 constexpr int RAW_PITCH = 144;          // bytes per raw X row (128 + 16: conflict-free split reads)
 constexpr int RAW_TILE = BM * RAW_PITCH;
 constexpr int A_TILE = BM * BK * 4;     // 16 KB, core-matrix layout
@@ -71,14 +72,20 @@ struct Cfg {
   static constexpr int NRAW = !SPLIT ? 0 : BN == 64 ? 4 : 3;
   // A slots: split (hi, lo) pairs, or X tiles copied straight into the MMA
   // layout (stages s .. s + NA - 1 in flight)
+  // (measured: eight slots make the first stage land later, so the last one
+  // lands no sooner; the kernel is bound by the L2 -> SM traffic of the
+  // re-read X and B tiles at small sizes)
   static constexpr int NA = SPLIT ? NAS : 4;
+  // MMA-completion barriers, indexed by stage % NDONE: at least NBS, so no
+  // wait on one of them can fall two phases behind
+  static constexpr int NDONE = 4;
   static constexpr int A_SLOT = SPLIT ? 2 * A_TILE : A_TILE;
   static constexpr int NBP = SPLIT ? 2 : 1;                      // B parts per slot (hi, lo)
   static constexpr int B_TILE = BN * BK * 4;                     // 8 or 16 KB
   static constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;        // [slot][hi, lo]
   static constexpr int OFF_A = ((OFF_B + NBS * NBP * B_TILE + 1023) / 1024) * 1024;
   static constexpr int OFF_BAR = OFF_A + NA * A_SLOT;           // full[NA], bfull[NBS], done[NDONE], TMEM addr, abort
-  static constexpr int SMEM_BYTES = OFF_BAR + 128 + 1024;        // + slack for 1024-byte alignment
+  static constexpr int SMEM_BYTES = OFF_BAR + 256 + 1024;        // + slack for 1024-byte alignment
   static constexpr int OUT_PITCH = BN / 2 + 1;                   // float2 per staged output row
   static constexpr uint32_t TMEM_COLS = BN;
   // Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
@@ -88,7 +95,8 @@ struct Cfg {
   static_assert(BN == 64 || BN == 128, "tile width");
   // the row-major output is staged over the data slots (free by then)
   static_assert(BM * OUT_PITCH * 8 <= OFF_BAR, "output staging must fit below the barriers");
-  static_assert(8 * (NA + NBS + NDONE) + 16 <= 128, "barrier area");
+  static_assert(8 * (NA + NBS + NDONE) + 16 <= 256, "barrier area");
+  static_assert(NDONE >= NBS && NDONE >= 2, "completion barriers");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
 
@@ -238,6 +246,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   using namespace tc;
   using L = Cfg<BN, SPLIT>;
   constexpr int NBS = L::NBS, B_TILE = L::B_TILE, NRAW = L::NRAW, OFF_B = L::OFF_B, NA = L::NA;
+  constexpr int NDONE = L::NDONE;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

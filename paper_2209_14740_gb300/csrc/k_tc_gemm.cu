@@ -300,6 +300,21 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
 
   if (warp < MMA_WARP) {
     bool bad = false;
+    // Epilogue geometry: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of
+    // the tile) and real columns [w / 4 * BN / 2, + BN / 2).  Its factors E
+    // (constant) are loaded now, so their latency overlaps the K loop.
+    constexpr int HALF = BN / 2;       // real columns per warp
+    const int lg = warp & 3, chalf = warp >> 2;
+    const int row = lg * 32 + lane, m = m0 + row;
+    const bool mok = m < a.M;
+    const int nq0 = blockIdx.y * (BN / 2) + chalf * (HALF / 2);   // first complex column of this warp
+    float2 ev[HALF / 2];
+    if (a.E) {
+      const int mr = (mok ? m : 0) % a.e_mod;
+#pragma unroll
+      for (int q = 0; q < HALF / 2; ++q)
+        ev[q] = nq0 + q < a.Nc ? a.E[(size_t)(nq0 + q) * a.e_ld + mr] : make_float2(0.f, 0.f);
+    }
     if constexpr (!SPLIT) {
       // ----------------------------------------- loaders (no split): X tiles
       // go straight into the MMA layout; each loader arrives on full[s % NA]
@@ -420,14 +435,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
       *abort_flag = 1;
     } else if (!skipped) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the
-      // tile) and real columns [w / 4 * BN / 2, + BN / 2), 32 at a time.
-      constexpr int HALF = BN / 2;       // real columns per warp
-      const int lg = warp & 3, chalf = warp >> 2;
-      const int row = lg * 32 + lane, m = m0 + row;
-      const bool mok = m < a.M;
-      const int nq0 = blockIdx.y * (BN / 2) + chalf * (HALF / 2);   // first complex column of this warp
-      const int mr = (mok ? m : 0) % a.e_mod;
+      // Epilogue, 32 real columns at a time
       const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
       float2* stage = reinterpret_cast<float2*>(sm + OFF_RAW);
       float2* cb = nullptr;   // mode 1: this row's element of column nq0
@@ -456,7 +464,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
           const int n = nq0 + qq;
           float2 c = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
           if (a.E) {
-            const float2 e = n < a.Nc ? a.E[(size_t)n * a.e_ld + mr] : make_float2(0.f, 0.f);
+            const float2 e = ev[qq];
             c = make_float2(es * (c.x * e.x - c.y * e.y), es * (c.x * e.y + c.y * e.x));
           }
           if (a.mode == 1) {

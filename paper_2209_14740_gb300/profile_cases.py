@@ -47,7 +47,8 @@ def main(argv=None):
     ap.add_argument("--r", type=int, default=3)
     ap.add_argument("--kbar", type=float, default=30.0)
     ap.add_argument("--sigma", type=float, default=0.15)
-    ap.add_argument("--prec", choices=["fp32", "fp64"], default="fp32", help="matvec/precond precision")
+    ap.add_argument("--prec", choices=["fp32", "fp64", "tf32"], default="fp32",
+                    help="matvec/precond precision (tf32: the plain-TF32 preconditioner, 2D only)")
     ap.add_argument("--mode", choices=["mixed", "fp64", "fp32"], default="mixed", help="solve precision")
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--reps", type=int, default=3)
@@ -60,8 +61,8 @@ def main(argv=None):
         op = B.SG(inputs.helmholtz_1d_c1(n_unknowns=a.g, r=a.r))
     else:
         op = B.SG(inputs.helmholtz_2d(a.g, a.s, a.r, a.kbar, a.sigma))
-    prec = B.FP32 if a.prec == "fp32" else B.FP64
-    cdt = torch.complex64 if prec == B.FP32 else torch.complex128
+    prec = {"fp32": B.FP32, "fp64": B.FP64, "tf32": B.TF32}[a.prec]
+    cdt = torch.complex128 if prec == B.FP64 else torch.complex64
     gen = torch.Generator(device=dev).manual_seed(0)
     if a.case == "solve":
         b = torch.empty(op.N, dtype=torch.complex128, device=dev)
@@ -80,7 +81,7 @@ def main(argv=None):
         Y = torch.empty_like(X)
         if a.case == "matvec":
             def call():
-                op.matvec(X, Y, prec)
+                op.matvec(X, Y, B.FP32 if prec == B.TF32 else prec)
         else:
             def call():
                 op.precond(X, Y, B.PREC_MEAN, prec)

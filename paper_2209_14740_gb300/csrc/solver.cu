@@ -184,11 +184,11 @@ __device__ __forceinline__ int cg_value_of_lane(int lane) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-// red[warp * nv + i] += warp sum of conj(V_i[e]) w_e over the thread's
-// elements of the chunk starting at `base`, eight vectors at a time.
+// red[warp * ld + i] += warp sum of conj(V_i[e]) w_e over the thread's
+// elements of the chunk starting at `base`, eight vectors at a time (i < nv).
 template <typename T>
 __device__ __forceinline__ void chunk_dots(const C2<T>* __restrict__ V, long long N, int nv, long long base,
-                                           const C2<T> (&wk)[CG_EPT], double2* red) {
+                                           const C2<T> (&wk)[CG_EPT], double2* red, int ld) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 < nv; i0 += 8) {
     T acc[16];
@@ -214,7 +214,7 @@ __device__ __forceinline__ void chunk_dots(const C2<T>* __restrict__ V, long lon
     if ((lane & 1) == 0) {
       const int val = cg_value_of_lane(lane), i = i0 + (val >> 1);
       if (i < nv) {
-        double2& r = red[warp * nv + i];
+        double2& r = red[warp * ld + i];
         if (val & 1) r.y += (double)sum; else r.x += (double)sum;
       }
     }
@@ -263,11 +263,15 @@ __device__ __forceinline__ bool finish_dots(int nv, const double2* red, double* 
 }
 
 // Pass 1: d = V^H w, c = vscale^2 d.  Dynamic shared memory: CG_WARPS * nv double2.
+// Two-pass form (c2prev != null): slot nv-1 still holds u, the previous
+// step's w after one projection, whose final form is u_hat = u - sum_{i<nv-1}
+// c2prev_i V_i; the last block turns u^H w into u_hat^H w = u^H w -
+// sum_i conj(c2prev_i) d_i before forming c.
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(const C2<T>* __restrict__ V, long long N, int nv,
                                                          const C2<T>* __restrict__ w, double* part,
                                                          unsigned* counter, const double* vscale, double* d_out,
-                                                         double* c_out, const int* ctl) {
+                                                         double* c_out, const int* ctl, const double* c2prev) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
@@ -280,9 +284,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(const C2<T>* __restric
       const long long e = base + k * RED_THREADS;
       wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
     }
-    chunk_dots<T>(V, N, nv, base, wk, red);
+    chunk_dots<T>(V, N, nv, base, wk, red, nv);
   }
-  finish_dots(nv, red, part, counter, vscale, d_out, c_out);
+  if (finish_dots(nv, red, part, counter, vscale, d_out, c_out) && c2prev) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int jn = nv - 1;
+      double sx = d_out[2 * jn], sy = d_out[2 * jn + 1];
+      for (int i = 0; i < jn; ++i) {
+        const double cx = c2prev[2 * i], cy = c2prev[2 * i + 1], dx = d_out[2 * i], dy = d_out[2 * i + 1];
+        sx -= cx * dx + cy * dy;   // conj(c) d
+        sy -= cx * dy - cy * dx;
+      }
+      d_out[2 * jn] = sx;
+      d_out[2 * jn + 1] = sy;
+      const double vs = vscale[jn];
+      c_out[2 * jn] = vs * vs * sx;
+      c_out[2 * jn + 1] = vs * vs * sy;
+    }
+  }
 }
 
 __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j);
@@ -335,7 +355,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restr
         nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
       }
     }
-    if (DOTS) chunk_dots<T>(V, N, nv, base, wk, red);
+    if (DOTS) chunk_dots<T>(V, N, nv, base, wk, red, nv);
   }
   if (DOTS) {
     finish_dots(nv, red, part, counter, vscale, d_out, c_out);
@@ -347,6 +367,146 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restr
   if (!last_block(counter)) return;
   sum_block_partials(part, 1, 1, [&](int, double s) { D[L.sc + SC_NORMSQ] = s; });
   if (threadIdx.x == 0) *counter = 0;
+  __syncthreads();
+  if (threadIdx.x < 32) givens_column(D, ctl, L, j);
+}
+
+// Two-pass form, pass 2 (flexible cycles): with j = nv - 1,
+//   u_hat = u - sum_{i<j} c2prev_i V_i           (finalises slot j)
+//   w    -= sum_{i<j} c1_i V_i + c1_j u_hat       (slot j+1)
+// then d2 = V^H w over slots 0..j, ||w||^2, and in the last block
+// c2 = vscale^2 d2, ||w - sum_i c2_i V_i||^2 = ||w||^2 - sum_i vscale_i^2 |d2_i|^2
+// (the basis is orthogonal, and the second-pass coefficients are tiny, so
+// the difference loses nothing) and the Givens update of column j.  The
+// vector w - sum c2_i V_i itself is formed by the next step's pass 2.
+// Dynamic shared memory: CG_WARPS * nv double2.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(C2<T>* __restrict__ V, long long N, int nv,
+                                                            const double* __restrict__ c1,
+                                                            const double* __restrict__ c2prev, double* part,
+                                                            unsigned* counter, const double* vscale,
+                                                            double* d_out, double* c_out, double* D, int* ctl,
+                                                            DevLayout L) {
+  if (ctl[CTL_DONE]) return;
+  extern __shared__ double2 red[];
+  __shared__ C2<T> cs1[MAXV];
+  __shared__ C2<T> cs2[MAXV];
+  __shared__ double sm[32];
+  const int j = nv - 1;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    cs1[i] = mkc<T>((T)c1[2 * i], (T)c1[2 * i + 1]);
+    cs2[i] = i < j ? mkc<T>((T)c2prev[2 * i], (T)c2prev[2 * i + 1]) : mkc<T>(T(0), T(0));
+  }
+  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  C2<T>* uj = V + (size_t)j * N;
+  C2<T>* w = V + (size_t)(j + 1) * N;
+  const long long chunk = (long long)RED_THREADS * CG_EPT;
+  T nacc = T(0);
+  for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
+    C2<T> wk[CG_EPT], uk[CG_EPT];
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
+      uk[k] = e < N ? uj[e] : mkc<T>(T(0), T(0));
+    }
+#pragma unroll 4
+    for (int i = 0; i < j; ++i) {
+      const C2<T>* Vi = V + (size_t)i * N;
+      const C2<T> a = cs1[i], b = cs2[i];
+#pragma unroll
+      for (int k = 0; k < CG_EPT; ++k) {
+        const long long e = base + k * RED_THREADS;
+        if (e < N) {
+          const C2<T> v = __ldg(Vi + e);
+          wk[k].x -= a.x * v.x - a.y * v.y;
+          wk[k].y -= a.x * v.y + a.y * v.x;
+          uk[k].x -= b.x * v.x - b.y * v.y;
+          uk[k].y -= b.x * v.y + b.y * v.x;
+        }
+      }
+    }
+    const C2<T> a = cs1[j];
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      if (e < N) {
+        wk[k].x -= a.x * uk[k].x - a.y * uk[k].y;
+        wk[k].y -= a.x * uk[k].y + a.y * uk[k].x;
+        uj[e] = uk[k];
+        w[e] = wk[k];
+        nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
+      }
+    }
+    // dots with the unchanged slots 0..j-1 (read-only path), and with the
+    // finalised slot j from registers (it was written by this kernel)
+    chunk_dots<T>(V, N, j, base, wk, red, nv);
+    T ax = T(0), ay = T(0);
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      ax += uk[k].x * wk[k].x + uk[k].y * wk[k].y;
+      ay += uk[k].x * wk[k].y - uk[k].y * wk[k].x;
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if ((threadIdx.x & 31) == 0) {
+      double2& r = red[(threadIdx.x >> 5) * nv + j];
+      r.x += (double)ax;
+      r.y += (double)ay;
+    }
+  }
+  // block sums of the dots (as finish_dots) and of ||w||^2 in one table
+  const int G = gridDim.x;
+  double dv[1] = {(double)nacc};
+  block_sum<1>(dv, sm);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < CG_WARPS; ++ww) {
+      sx += red[ww * nv + i].x;
+      sy += red[ww * nv + i].y;
+    }
+    part[(size_t)(2 * i) * G + blockIdx.x] = sx;
+    part[(size_t)(2 * i + 1) * G + blockIdx.x] = sy;
+  }
+  if (threadIdx.x == 0) part[(size_t)(2 * nv) * G + blockIdx.x] = dv[0];
+  if (!last_block(counter)) return;
+  __shared__ double wn2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k <= 2 * nv; k += CG_WARPS) {
+    const double* pk = part + (size_t)k * G;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < G; b += 64) {
+      s0 += __ldcg(pk + b);
+      s1 += __ldcg(pk + b + 32);
+    }
+    if (b < G) s0 += __ldcg(pk + b);
+    double ssum = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ssum += __shfl_down_sync(0xffffffffu, ssum, o);
+    if (lane == 0) {
+      if (k < 2 * nv) {
+        d_out[k] = ssum;
+        const double vs = vscale[k >> 1];
+        c_out[k] = vs * vs * ssum;
+      } else {
+        wn2 = ssum;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double corr = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      const double vs = vscale[i];
+      corr += vs * vs * (d_out[2 * i] * d_out[2 * i] + d_out[2 * i + 1] * d_out[2 * i + 1]);
+    }
+    const double r = wn2 - corr;
+    D[L.sc + SC_NORMSQ] = r > 0.0 ? r : 0.0;
+    *counter = 0;
+  }
   __syncthreads();
   if (threadIdx.x < 32) givens_column(D, ctl, L, j);
 }
@@ -647,6 +807,7 @@ static void cgs_attributes() {
     cudaFuncSetAttribute(k_cgs_dots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_cgs2_second<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   });
 }
 
@@ -672,8 +833,8 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   if (!e) e = cudaMalloc((void**)&w.dscal, L.total * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.dctl, 16 * sizeof(int));
   // block partials: the reduction kernels use nblk * 2 (MAXV + 2) doubles, the
-  // CGS2 passes 2 * MAXV * cg_nblk
-  const size_t part_doubles = std::max((size_t)w.nblk * 2 * (MAXV + 2), (size_t)2 * MAXV * w.cg_nblk);
+  // CGS2 passes up to (2 MAXV + 1) * cg_nblk
+  const size_t part_doubles = std::max((size_t)w.nblk * 2 * (MAXV + 2), (size_t)(2 * MAXV + 2) * w.cg_nblk);
   if (!e) e = cudaMalloc((void**)&w.part, part_doubles * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.counter, sizeof(unsigned));
   if (!e) e = cudaMemset(w.counter, 0, sizeof(unsigned));
@@ -751,8 +912,19 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   const int nv = j + 1;
   const size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
   const int G = c.cg_grid;
+  if (flexible<T>(c, prec)) {
+    // two passes: the reorthogonalisation of slot j is folded into this
+    // step's second pass (flexible GMRES lets the preconditioner take the
+    // once-projected vector)
+    k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
+                                                      D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.c2); note_launch();
+    k_cgs2_second<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, D + c.L.c1, D + c.L.c2, w.part, w.counter,
+                                                         D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl, c.L);
+    note_launch();
+    return cudaGetLastError();
+  }
   k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
-                                                    D + c.L.d1, D + c.L.c1, w.dctl); note_launch();
+                                                    D + c.L.d1, D + c.L.c1, w.dctl, nullptr); note_launch();
   k_cgs_update<T, true><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, w.counter,
                                                             D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl,
                                                             c.L, j); note_launch();

@@ -48,7 +48,10 @@ COUPLING = "tk"      # tile mode: "tk" = factorised through degree r + 1, "direc
 PERSISTENT = True    # complex64 "tk" kernels: persistent CTAs, next tile copied during the coupling
 # persistent kernels with at least this many modes emit the rows of degree
 # <= r twice (with and without the boundary exchange) so interior warps run
-# them without branches; smaller P keeps one copy (fewer registers, more CTAs)
+# them without branches, and issue the next tile's copies right after the
+# last row that reads shared memory; smaller P keeps one copy of the rows and
+# issues the copies at the first row of degree r + 1 (fewer registers, more
+# CTAs; measured faster at P = 20)
 BND_SPLIT_MIN_P = 56
 # FP64 kernels are generated for P up to this (two registers per value: the
 # mode values and accumulators of larger P do not fit)
@@ -720,10 +723,11 @@ def gen_kernel_tkp(s, r):
     and the copies of the next tile overlap the coupling of this one:
 
       wait for this tile's copies -> Z_a = ldiag X_a - sum_nb w_nb X_a(nb)
-      straight from shared memory (X_a into registers) -> coupling rows of
-      degree <= r -> barrier -> issue the cp.async copies of the next tile's
-      values and halo into the same shared rows -> rows of degree r + 1
-      (the fewest live registers) -> Y_a = Z_a as each completes.
+      straight from shared memory (X_a into registers, each just before its
+      first use) -> coupling rows up to the last one that reads shared memory
+      -> barrier -> issue the cp.async copies of the next tile's values and
+      halo into the same shared rows -> the remaining rows -> Y_a = Z_a as
+      each completes.
 
     The stencil reads every shared value before the barrier, so one buffer
     serves both tiles, and the CTA's single set of P accumulators (the
@@ -838,18 +842,38 @@ def gen_kernel_tkp(s, r):
 
     idx_, rows = _tk_rows(s, r)
     top = min(ri for ri, (gm, _) in enumerate(rows) if sum(gm) == r + 1)
+    # the next tile's copies go out right after the last row that reads
+    # shared memory (the first use of a mode value or of an output's stencil)
+    seen = set()
+    hook = 0
+    for ri, (gm, terms) in enumerate(rows):
+        for _, b in terms:
+            if b not in seen:
+                seen.add(b)
+                hook = ri + 1
+    assert hook <= top
+    if P < BND_SPLIT_MIN_P:
+        # measured: small P is faster with the copies issued at the first row
+        # of degree r + 1 (fewer registers while they are issued)
+        hook = top
     # rows of degree <= r: warps holding an absorbing boundary node exchange
     # -i w1 W with the partner lane; the others run the same rows without
-    if P >= BND_SPLIT_MIN_P:
-        w("    if (bnd) {")
-        declared = _emit_tk_rows(w, s, r, rows, 0, top, finish, True, first_x, first_z)
-        w("    } else {")
-        _emit_tk_rows(w, s, r, rows, 0, top, finish, False, first_x, first_z)
-        w("    }")
-    else:
-        declared = _emit_tk_rows(w, s, r, rows, 0, top, finish, "branch", first_x, first_z)
+    # (two regions, so the barrier before the copies stays outside branches)
+    def region(lo, hi, declared=()):
+        if hi <= lo:
+            return set(declared)
+        if P >= BND_SPLIT_MIN_P:
+            w("    if (bnd) {")
+            d = _emit_tk_rows(w, s, r, rows, lo, hi, finish, True, first_x, first_z, declared)
+            w("    } else {")
+            _emit_tk_rows(w, s, r, rows, lo, hi, finish, False, first_x, first_z, declared)
+            w("    }")
+            return d
+        return _emit_tk_rows(w, s, r, rows, lo, hi, finish, "branch", first_x, first_z, declared)
+    declared = region(0, hook)
     w("    __syncthreads();   // every shared value of this tile has been read")
     w("    if (tile + (int)gridDim.x < tiles) issue(tile + gridDim.x);")
+    declared = region(hook, top, declared)
     # rows of degree r + 1 (no output of their own: no exchange)
     _emit_tk_rows(w, s, r, rows, top, len(rows), finish, False, declared=declared)
     w("  }")

@@ -27,10 +27,11 @@
 //              matrices, no swizzle), or, without the split, copy X straight
 //              into that layout three stages ahead; then they run the
 //              epilogue;
-//   warp 8     one lane issues the 12 MMAs of each stage (M=128, N=BN, K=8)
-//              and commits them to an mbarrier;
-//   warp 9     one lane copies the pre-laid-out B tiles (hi and lo) of each
-//              stage with bulk asynchronous copies completing on an mbarrier.
+//   warp 8     one lane issues the MMAs of each stage (M=128, N=BN, K=8; 12
+//              with the split, 4 without) and commits them to an mbarrier;
+//   warp 9     one lane copies the pre-laid-out B tiles (hi and lo, or hi
+//              only) of each stage with bulk asynchronous copies completing
+//              on an mbarrier.
 // Every wait is bounded: on a timeout the kernel records it, drains its
 // copies, frees tensor memory and returns.
 //
@@ -231,16 +232,19 @@ __device__ __forceinline__ bool loader_sync_or(bool v) {
   return r != 0;
 }
 
-// Pipeline (stage s = 32 real K values, NRAW raw X slots):
-//   loaders:  wait raw X of s landed -> wait MMA(s-2) (frees A slot s%2)
-//             -> split raw -> A slot, arrive full[s%2]
+// Pipeline (stage s = 32 real K values):
+//   loaders (split):  wait raw X of s landed -> wait MMA(s-2) (frees A slot
+//             s%2) -> split raw -> A slot, arrive full[s%2]
 //             -> issue X copies of s+NRAW-1
-//   B copier: wait MMA(s-NBS) (frees B slot s%NBS) -> bulk-copy B hi/lo of s
-//   MMA lane: wait full[s%2] and bfull[s%NBS] -> 12 MMAs (3xTF32 x 4 K steps)
-//             -> commit done[s%4]
-// so the split of stage s+1 and the copies of later stages overlap the MMAs
-// of stage s.  No waiter can fall two phases behind on a barrier: the MMA
-// lane runs at most two stages ahead of the loaders and cannot pass the copier.
+//   loaders (no split): wait own X copies of s landed, arrive full[s%NA]
+//             -> wait MMA(s-1) (frees slot (s-1)%NA) -> issue X copies of
+//             s+NA-1 into it
+//   B copier: wait MMA(s-NBS) (frees B slot s%NBS) -> bulk-copy B of s
+//   MMA lane: wait full and bfull of s -> 12 (3xTF32) or 4 MMAs over the 4
+//             K steps -> commit done[s%NDONE]
+// so the loads of later stages overlap the MMAs of stage s.  No waiter can
+// fall two phases behind on a barrier: the MMA lane runs at most one or two
+// stages ahead of the loaders, cannot pass the copier, and NDONE >= NBS.
 template <int BN, bool SPLIT>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   using namespace tc;

@@ -1,0 +1,180 @@
+"""CPU checks of the algebra behind the complex64 GMRES cycles (no GPU).
+
+1. The two-pass CGS2 of the flexible cycles, restated in numpy with the same
+   quantities the kernels keep (raw basis slots, their inverse norms, the
+   coefficients c1 = vscale^2 d1 and c2 = vscale^2 d2 of the previous step):
+   the newest slot holds the once-projected vector u; the next step's first
+   pass corrects u^H w to u_hat^H w with u_hat = u - sum_i c2_i V_i, its
+   second pass finalises u_hat, and the new norm comes from
+   ||w1||^2 - sum_i vscale_i^2 |d2_i|^2.  Checked: the flexible Arnoldi
+   relation A Z = V H to rounding, an orthonormal basis, and the Hessenberg
+   columns equal to those of a plain CGS2 projection of the same A z_j.
+2. The accuracy bound of the plain-TF32 preconditioner the GPU tests use
+   (5e-3): the four fast-diagonalisation transforms emulated with TF32
+   inputs (data truncated to 10 mantissa bits, factors rounded) and FP32
+   sums, against the same transforms in FP64.
+"""
+import numpy as np
+import pytest
+
+
+def two_pass_flexible_arnoldi(A, minv, r0, m, leak=0.0, seed=0):
+    """m steps; returns (V (n x m+1, finalised, orthonormal), Z, H).  leak > 0
+    perturbs the first-pass coefficients by that relative amount (used for
+    both the projection and H, so A Z = V H stays exact): the once-projected
+    vector then keeps a component along the basis, as the rounding of the
+    complex64 first pass leaves one on the GPU, and only the second pass, the
+    correction of the newest coefficient and the Pythagorean norm remove it."""
+    rng = np.random.default_rng(seed)
+    n = r0.size
+    slots = np.zeros((m + 1, n), dtype=complex)   # raw slot vectors
+    vs = np.zeros(m + 1)
+    slots[0] = r0
+    vs[0] = 1.0 / np.linalg.norm(r0)
+    c2prev = np.zeros(0, dtype=complex)
+    Z = np.zeros((m, n), dtype=complex)
+    H = np.zeros((m + 1, m), dtype=complex)
+    for j in range(m):
+        u = slots[j].copy()
+        Z[j] = minv(vs[j] * u)
+        w = A @ Z[j]
+        # first pass: dots with slots 0..j (slot j still u), correction of the last
+        d1 = slots[: j + 1].conj() @ w
+        d1[j] -= np.dot(c2prev.conj(), d1[:j])
+        if leak:
+            e = rng.standard_normal(j + 1) + 1j * rng.standard_normal(j + 1)
+            d1 = d1 + leak * np.linalg.norm(d1) * e / np.sqrt(2 * (j + 1))
+        c1 = vs[: j + 1] ** 2 * d1
+        # second pass: finalise slot j, project w once, dots, norm
+        u_hat = u - c2prev @ slots[:j]
+        slots[j] = u_hat
+        w1 = w - c1[:j] @ slots[:j] - c1[j] * u_hat
+        d2 = slots[: j + 1].conj() @ w1
+        c2 = vs[: j + 1] ** 2 * d2
+        nsq = np.vdot(w1, w1).real - np.sum(vs[: j + 1] ** 2 * np.abs(d2) ** 2)
+        H[: j + 1, j] = vs[: j + 1] * (d1 + d2)
+        H[j + 1, j] = np.sqrt(nsq)
+        vs[j + 1] = 1.0 / np.sqrt(nsq)
+        slots[j + 1] = w1
+        c2prev = c2
+    # the last slot is finalised by what would be the next step's second pass
+    slots[m] = slots[m] - c2prev @ slots[:m]
+    V = (slots * vs[:, None]).T
+    return V, Z.T, H
+
+
+def test_two_pass_flexible_arnoldi_relation():
+    rng = np.random.default_rng(3)
+    n, m = 120, 25
+    A = np.eye(n) * 4 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    # an inexact, slightly non-linear preconditioner (rounded to ~3 digits)
+    D = np.diag(A).copy()
+
+    def minv(v):
+        z = v / D
+        return np.round(z.real, 3) + 1j * np.round(z.imag, 3)
+
+    r0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    V, Z, H = two_pass_flexible_arnoldi(A, minv, r0, m, leak=1e-3)
+    scale = np.linalg.norm(A, 2) * np.linalg.norm(Z, 2)
+    assert np.linalg.norm(A @ Z - V @ H) <= 1e-12 * scale
+    # the components left by the inexact first pass are removed
+    assert np.abs(V.conj().T @ V - np.eye(m + 1)).max() <= 1e-12
+    assert np.allclose(V[:, 0], r0 / np.linalg.norm(r0), atol=1e-14)
+    # column j equals a plain CGS2 projection of A z_j onto the finalised basis
+    # (exact first pass)
+    V, Z, H = two_pass_flexible_arnoldi(A, minv, r0, m)
+    for j in (0, 5, m - 1):
+        w = A @ Z[:, j]
+        Vj = V[:, : j + 1]
+        h1 = Vj.conj().T @ w
+        w1 = w - Vj @ h1
+        h2 = Vj.conj().T @ w1
+        w2 = w1 - Vj @ h2
+        ref = np.concatenate([h1 + h2, [np.linalg.norm(w2)]])
+        assert np.allclose(H[: j + 2, j], ref, rtol=0, atol=1e-12 * np.linalg.norm(w))
+
+
+def test_two_pass_flexible_gmres_reaches_tolerance():
+    """The least-squares correction over the stored z_j gives the residual
+    the Hessenberg predicts, even with the inexact preconditioner."""
+    rng = np.random.default_rng(8)
+    n, m = 80, 40
+    A = np.eye(n) * 3 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    D = np.diag(A).copy()
+
+    def minv(v):
+        z = v / D
+        return np.round(z.real, 2) + 1j * np.round(z.imag, 2)
+
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    V, Z, H = two_pass_flexible_arnoldi(A, minv, b, m)
+    g = np.zeros(m + 1, dtype=complex)
+    g[0] = np.linalg.norm(b)
+    y, *_ = np.linalg.lstsq(H, g, rcond=None)
+    x = Z @ y
+    pred = np.linalg.norm(g - H @ y)
+    true = np.linalg.norm(b - A @ x)
+    assert true <= 1e-8 * np.linalg.norm(b)
+    assert abs(true - pred) <= 1e-10 * np.linalg.norm(b)
+
+
+def _pencil_g(m, kb):
+    """G = D^-1/2 (T - i (kb/h) E - (kb^2/2) D) D^-1/2 of the 1D absorbing
+    pencil (the matrix the fast diagonalisation decomposes)."""
+    h = 1.0 / (m - 1)
+    tdiag = np.full(m, 2 / h ** 2)
+    toff = np.full(m - 1, -1 / h ** 2)
+    d = np.ones(m)
+    e = np.zeros(m)
+    tdiag[[0, -1]] = 1 / h ** 2
+    d[[0, -1]] = 0.5
+    e[[0, -1]] = 1.0
+    gd = (tdiag - 0.5 * kb * kb * d - 1j * (kb / h) * e) / d
+    go = toff / np.sqrt(d[:-1] * d[1:])
+    return np.diag(gd) + np.diag(go, 1) + np.diag(go, -1), d
+
+
+def _tf32_trunc(a):
+    a = np.asarray(a, np.complex64)
+    re = (a.real.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    im = (a.imag.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+    return re + 1j * im
+
+
+def _tf32_round(a):
+    a = np.asarray(a, np.complex64)
+
+    def rn(x):
+        u = x.copy().view(np.uint32).astype(np.uint64)
+        return ((u + 0x1000) & 0xFFFFE000).astype(np.uint32).view(np.float32)
+
+    return rn(a.real) + 1j * rn(a.imag)
+
+
+@pytest.mark.parametrize("m,kb", [(13, 10.0), (21, 12.0), (127, 30.0)])
+def test_tf32_transform_bound(m, kb):
+    G, d = _pencil_g(m, kb)
+    lam, Q = np.linalg.eig(G)
+    Q = Q / np.sqrt(np.sum(Q * Q, axis=0))          # complex-symmetric normalisation Q^T Q = I
+    Qh = Q / np.sqrt(d)[:, None]
+    Linv = 1.0 / (lam[None, :] + lam[:, None])
+
+    def gemm(X, B, tf32):
+        if not tf32:
+            return X @ B
+        return (_tf32_trunc(X).astype(np.complex128) @ _tf32_round(B).astype(np.complex128)).astype(np.complex64)
+
+    def apply(R, tf32):
+        T1 = gemm(R, Qh, tf32)
+        T2 = gemm(T1.T, Qh, tf32) * Linv.T
+        T3 = gemm(T2, Qh.T, tf32)
+        return gemm(T3.T, Qh.T, tf32)
+
+    rng = np.random.default_rng(m)
+    R = (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))).astype(np.complex64)
+    Z = apply(R.astype(np.complex128), False)
+    Zt = apply(R, True)
+    err = np.linalg.norm(Zt - Z) / np.linalg.norm(Z)
+    assert err < 5e-3, err
+    assert err > 1e-5          # really the TF32 arithmetic, not FP32

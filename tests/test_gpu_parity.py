@@ -169,6 +169,29 @@ def test_precond_tf32(B, idx, kind):
     op.close()
 
 
+@pytest.mark.parametrize("g", [63, 127])
+def test_precond_tf32_larger_grids(B, g):
+    """The plain-TF32 apply on grids with 4 and 8 K stages per transform
+    (ragged last stage at 63) against the FP64 apply (a separate code path,
+    checked against the oracle above), within the 5e-3 bound; a second call
+    gives the same bits."""
+    pr = inputs.helmholtz_2d(g, 3, 3, 30.0, 0.15)
+    op = B.SG(pr)
+    gen = torch.Generator(device=DEV).manual_seed(g)
+    X = torch.randn(op.N, dtype=torch.complex64, device=DEV, generator=gen)
+    for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+        Zr = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.precond(X.to(torch.complex128), Zr, kind, B.FP64)
+        Zt = torch.empty_like(X)
+        op.precond(X, Zt, kind, B.TF32)
+        err = float(torch.linalg.vector_norm(Zt.to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+        assert err < 5e-3, (kind, err)
+        Zt2 = torch.empty_like(X)
+        op.precond(X, Zt2, kind, B.TF32)
+        assert torch.equal(Zt, Zt2)
+    op.close()
+
+
 def test_precond_tf32_needs_the_2d_route(B):
     op = B.SG(problems()[0])     # 1D
     X = torch.zeros(op.N, dtype=torch.complex64, device=DEV)

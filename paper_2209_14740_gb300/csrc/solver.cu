@@ -659,29 +659,61 @@ __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j) {
 // y = R^-1 g (k x k upper triangle of the rotated Hessenberg matrix);
 // yc_i = y_i * vscale_i for the raw-basis linear combination (raw != 0), or
 // y_i itself for the combination of the stored z_j (flexible GMRES).
-__global__ void k_lsq(double* D, const int* ctl, DevLayout L, int raw) {
+constexpr int LSQ_SMEM_K = 64;      // triangles up to this size are solved from shared memory
+constexpr int LSQ_THREADS = 128;
+
+__global__ void __launch_bounds__(LSQ_THREADS) k_lsq(double* D, const int* ctl, DevLayout L, int raw) {
+  extern __shared__ double2 Hs[];   // k x k upper triangle, column-major (k <= LSQ_SMEM_K)
+  __shared__ double2 y[LSQ_SMEM_K];
   const int k = ctl[CTL_K];
   const int m = L.m;
+  const int tid = threadIdx.x;
   const double2* H = reinterpret_cast<const double2*>(D + L.H);
   const double2* g = reinterpret_cast<const double2*>(D + L.g);
   double2* yc = reinterpret_cast<double2*>(D + L.yc);
   const double* vs = D + L.vscale;
-  for (int i = k - 1; i >= 0; --i) {
-    double2 s = g[i];
-    for (int l = i + 1; l < k; ++l) {
-      const double2 h = H[(size_t)l * (m + 1) + i];
-      const double2 y = yc[l];   // still unscaled y_l here
-      s.x -= h.x * y.x - h.y * y.y;
-      s.y -= h.x * y.y + h.y * y.x;
-    }
-    const double2 d = H[(size_t)i * (m + 1) + i];
+  auto cdiv = [](double2 s, double2 d) {
     const double den = d.x * d.x + d.y * d.y;
-    yc[i] = den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
-                    : make_double2(0, 0);
+    return den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
+                   : make_double2(0, 0);
+  };
+  if (k <= LSQ_SMEM_K) {
+    // the triangle and g into shared memory by all threads, then column by
+    // column: y_i = y_i / R_ii, y_l -= R_li y_i for l < i (in parallel)
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+      const int i = idx / k, l = idx - i * k;
+      if (l <= i) Hs[idx] = H[(size_t)i * (m + 1) + l];
+    }
+    for (int i = tid; i < k; i += blockDim.x) y[i] = g[i];
+    __syncthreads();
+    for (int i = k - 1; i >= 0; --i) {
+      if (tid == 0) y[i] = cdiv(y[i], Hs[i * k + i]);
+      __syncthreads();
+      const double2 yi = y[i];
+      for (int l = tid; l < i; l += blockDim.x) {
+        const double2 h = Hs[i * k + l];
+        y[l].x -= h.x * yi.x - h.y * yi.y;
+        y[l].y -= h.x * yi.y + h.y * yi.x;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < k; i += blockDim.x)
+      yc[i] = raw ? make_double2(y[i].x * vs[i], y[i].y * vs[i]) : y[i];
+  } else if (tid == 0) {
+    for (int i = k - 1; i >= 0; --i) {
+      double2 sum = g[i];
+      for (int l = i + 1; l < k; ++l) {
+        const double2 h = H[(size_t)l * (m + 1) + i];
+        const double2 yl = yc[l];   // still unscaled y_l here
+        sum.x -= h.x * yl.x - h.y * yl.y;
+        sum.y -= h.x * yl.y + h.y * yl.x;
+      }
+      yc[i] = cdiv(sum, H[(size_t)i * (m + 1) + i]);
+    }
+    if (raw)
+      for (int i = 0; i < k; ++i) yc[i] = make_double2(yc[i].x * vs[i], yc[i].y * vs[i]);
   }
-  if (raw)
-    for (int i = 0; i < k; ++i) yc[i] = make_double2(yc[i].x * vs[i], yc[i].y * vs[i]);
-  for (int i = k; i <= m; ++i) yc[i] = make_double2(0, 0);
+  for (int i = k + tid; i <= m; i += blockDim.x) yc[i] = make_double2(0, 0);
 }
 
 // u = sum_{i<k} yc_i V_i  (k read on the device).
@@ -808,6 +840,8 @@ static void cgs_attributes() {
     cudaFuncSetAttribute(k_cgs_update<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs2_second<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         LSQ_SMEM_K * LSQ_SMEM_K * (int)sizeof(double2));
   });
 }
 
@@ -996,7 +1030,11 @@ sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int
   C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
   C2<T>* Z = reinterpret_cast<C2<T>*>(w.Z);
   const bool flex = flexible<T>(c, prec);
-  k_lsq<<<1, 1, 0, c.st>>>(w.dscal, w.dctl, c.L, flex ? 0 : 1); note_launch();
+  {
+    const int kmax = std::min(m, LSQ_SMEM_K);
+    k_lsq<<<1, LSQ_THREADS, (size_t)kmax * kmax * sizeof(double2), c.st>>>(w.dscal, w.dctl, c.L, flex ? 0 : 1);
+    note_launch();
+  }
   const C2<T>* basis = flex ? reinterpret_cast<const C2<T>*>(w.Zb) : V;
   k_lincomb<T><<<c.grid, RED_THREADS, 0, c.st>>>(basis, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
   SG_CUDA_TRY(cudaGetLastError());

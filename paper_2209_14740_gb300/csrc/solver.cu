@@ -145,6 +145,9 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 //   k_cgs_update<DOTS>     w -= V c1, then d2 = V^H w      (c2 = vscale^2 d2)
 //   k_cgs_update<GIVENS>   w -= V c2, ||w||^2, then the Givens update of
 //                          column j in the last block to finish.
+// Flexible complex64 cycles take two passes instead (k_cgs_dots with the
+// correction of the newest slot, then k_cgs2_second): the third pass's update
+// is folded into the next step's second pass.
 // Each block walks chunks of RED_THREADS * CG_EPT consecutive elements (grid
 // stride), a thread keeps its CG_EPT elements of w in registers, and every
 // pass reads each V_i element once (the DOTS re-read of the chunk it just

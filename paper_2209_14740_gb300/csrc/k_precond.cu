@@ -441,15 +441,21 @@ static cudaError_t fd_apply(const sg_handle* h, int which, const float2* R, floa
                             const int* skip, const double* in_scale, float2* tmp, float2* tmp2, bool split) {
   const int mx = h->mx, my = h->my, P = h->P;
   const int mxp = mx + (mx & 1), myp = my + (my & 1);
+  // plain TF32 on the handle's own intermediates: transforms 2-4 read them by
+  // tensor copies (maps encoded at set-up)
+  const bool maps = !split && h->tc_xmap_ok && tmp == reinterpret_cast<const float2*>(h->d_tmp) &&
+                    tmp2 == reinterpret_cast<const float2*>(h->d_tmp2);
   cudaError_t e =
       tc_cgemm(h->tcB[0], R, mx, P * my, tmp, myp, 1, my, nullptr, 0, 1, nullptr, skip, h->d_err, st, split);
   if (e == cudaSuccess)
     e = tc_cgemm(h->tcB[1], tmp, myp, P * mx, tmp2, myp, 0, 0, h->d_Linv32[which], mx, mx, in_scale, skip,
-                 h->d_err, st, split);
+                 h->d_err, st, split, maps ? &h->tc_xmap[0] : nullptr);
   if (e == cudaSuccess)
-    e = tc_cgemm(h->tcB[2], tmp2, myp, P * mx, tmp, mxp, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st, split);
+    e = tc_cgemm(h->tcB[2], tmp2, myp, P * mx, tmp, mxp, 1, mx, nullptr, 0, 1, nullptr, skip, h->d_err, st, split,
+                 maps ? &h->tc_xmap[1] : nullptr);
   if (e == cudaSuccess)
-    e = tc_cgemm(h->tcB[3], tmp, mxp, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st, split);
+    e = tc_cgemm(h->tcB[3], tmp, mxp, P * my, Z, mx, 0, 0, nullptr, 0, 1, nullptr, skip, h->d_err, st, split,
+                 maps ? &h->tc_xmap[2] : nullptr);
   return e;
 }
 

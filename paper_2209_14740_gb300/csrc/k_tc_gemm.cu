@@ -35,10 +35,17 @@
 // Every wait is bounded: on a timeout the kernel records it, drains its
 // copies, frees tensor memory and returns.
 //
+// With a tensor map of X (plain TF32, X rows of even length), the copy warp
+// also loads X: one 4D tensor copy per stage (4 values x 8 rows x 8 chunks x
+// 16 row groups) lands directly in the core-matrix layout, and the loader
+// warps only run the epilogue.
+//
 // Launched as a programmatic dependent of the previous kernel in the stream:
 // tensor-memory allocation, barrier set-up and the first B copies (B is
 // constant) overlap the previous kernel's tail; nothing it wrote is read,
 // and nothing in global memory is written, before griddepcontrol.wait.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <complex>
@@ -173,6 +180,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+// 4D tensor copy global -> shared completing its bytes on an mbarrier
+__device__ __forceinline__ void tensor_g2s_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
@@ -245,10 +262,12 @@ __device__ __forceinline__ bool loader_sync_or(bool v) {
 // so the loads of later stages overlap the MMAs of stage s.  No waiter can
 // fall two phases behind on a barrier: the MMA lane runs at most one or two
 // stages ahead of the loaders, cannot pass the copier, and NDONE >= NBS.
-template <int BN, bool SPLIT>
-__global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
+template <int BN, bool SPLIT, bool TMAX>
+__global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __grid_constant__ CUtensorMap xmap) {
   using namespace tc;
   using L = Cfg<BN, SPLIT>;
+  static_assert(!(SPLIT && TMAX), "X by tensor copy only in the plain-TF32 form");
+  static_assert(!TMAX || L::NA == L::NBS, "X and B stages share their slot index");
   constexpr int NBS = L::NBS, B_TILE = L::B_TILE, NRAW = L::NRAW, OFF_B = L::OFF_B, NA = L::NA;
   constexpr int NDONE = L::NDONE;
   extern __shared__ unsigned char smem_dyn[];
@@ -269,7 +288,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   }
   if (tid == 0) {
     for (int i = 0; i < NA; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * i), "n"(NLOAD) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * i), "n"(TMAX ? 1 : NLOAD)
+                   : "memory");
     for (int i = 0; i < NBS; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bfull0 + 8 * i) : "memory");
     for (int i = 0; i < NDONE; ++i)
@@ -290,6 +310,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
     mbar_expect_tx(bar, (uint32_t)(L::NBP * B_TILE));
     bulk_g2s(dst, Bh + (size_t)t * (BN * BK), B_TILE, bar);
     if (SPLIT) bulk_g2s(dst + B_TILE, Bl + (size_t)t * (BN * BK), B_TILE, bar);
+  };
+  // X of stage t by one tensor copy into A slot t % NA (TMAX)
+  auto copy_x = [&](int t) {
+    const uint32_t bar = full0 + 8 * (t % NA);
+    mbar_expect_tx(bar, (uint32_t)A_TILE);
+    tensor_g2s_4d(s_base + L::OFF_A + (t % NA) * L::A_SLOT, &xmap, 0, 0, t * (BK / 4), m0 / 8, bar);
   };
   // B is constant: its first stages are copied before the wait below
   const int pre = a.nks < NBS ? a.nks : NBS;
@@ -319,7 +345,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
       for (int q = 0; q < HALF / 2; ++q)
         ev[q] = nq0 + q < a.Nc ? a.E[(size_t)(nq0 + q) * a.e_ld + mr] : make_float2(0.f, 0.f);
     }
-    if constexpr (!SPLIT) {
+    if constexpr (TMAX) {
+      // X arrives by tensor copies.  The loaders follow the MMA completions
+      // stage by stage, so that no wait on a completion barrier is ever two
+      // phases behind (a parity wait on a barrier that has not reached the
+      // previous phase would succeed at once)
+      for (int s = 0; s < nks; ++s)
+        if (!mbar_wait(done0 + 8 * (s % NDONE), (s / NDONE) & 1)) {
+          bad = true;
+          break;
+        }
+    } else if constexpr (!SPLIT) {
       // ----------------------------------------- loaders (no split): X tiles
       // go straight into the MMA layout; each loader arrives on full[s % NA]
       // once its own copies of stage s have landed
@@ -443,9 +479,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
       const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
       float2* stage = reinterpret_cast<float2*>(sm + OFF_RAW);
       float2* cb = nullptr;   // mode 1: this row's element of column nq0
+      bool pad1 = false;      // mode 1: also zero the pad entry after the last row r
       if (a.mode == 1 && mok) {
         const int p = m / a.MB, r = m - p * a.MB;
         cb = a.C + ((size_t)p * a.Nc + nq0) * a.ldc + r;
+        pad1 = r == a.MB - 1 && a.ldc > a.MB;
       }
       const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(chalf * HALF);
 #pragma unroll
@@ -473,7 +511,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
           }
           if (a.mode == 1) {
             // lanes hold consecutive rows r: each store writes consecutive addresses
-            if (mok && n < a.Nc) cb[(size_t)qq * a.ldc] = c;
+            if (mok && n < a.Nc) {
+              cb[(size_t)qq * a.ldc] = c;
+              // rows padded to even length are read whole by the next
+              // transform's tensor copies: keep the pad at zero
+              if (pad1) cb[(size_t)qq * a.ldc + 1] = make_float2(0.f, 0.f);
+            }
           } else {
             stage[row * L::OUT_PITCH + chalf * (HALF / 2) + qq] = c;
           }
@@ -487,7 +530,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
         for (int idx = tid; idx < BM * (BN / 2); idx += NLOAD) {
           const int rr = idx / (BN / 2), q = idx % (BN / 2);
           const int mm = m0 + rr, n = n0 + q;
-          if (mm < a.M && n < a.Nc) a.C[(size_t)mm * a.ldc + n] = stage[rr * L::OUT_PITCH + q];
+          if (mm < a.M && n < a.Nc) {
+            a.C[(size_t)mm * a.ldc + n] = stage[rr * L::OUT_PITCH + q];
+            if (n == a.Nc - 1 && a.ldc > a.Nc) a.C[(size_t)mm * a.ldc + a.Nc] = make_float2(0.f, 0.f);
+          }
         }
       }
     }
@@ -521,6 +567,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
   } else if (lane == 0) {
     // ---------------------------------------------------------------- B copies
     int issued = pre;   // stages copied before the wait (also when skipped)
+    int xissued = 0;    // X stages copied (TMAX), after the wait
+    if (TMAX)
+      for (; xissued < pre && xissued < nks; ++xissued) copy_x(xissued);
     for (int t = pre; t < nks; ++t) {
       if (!mbar_wait(done0 + 8 * ((t - NBS) % NDONE), ((t - NBS) / NDONE) & 1)) {
         *abort_flag = 1;
@@ -529,7 +578,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a) {
       if (*abort_flag) break;
       copy_b(t);
       issued = t + 1;
+      if (TMAX) {
+        copy_x(t);
+        xissued = t + 1;
+      }
     }
+    // no tensor copy may still be writing shared memory when the CTA exits
+    if (TMAX)
+      for (int t = xissued > NA ? xissued - NA : 0; t < xissued; ++t)
+        if (!mbar_wait(full0 + 8 * (t % NA), (t / NA) & 1)) *abort_flag = 1;
     // no copy may still be writing shared memory when the CTA exits: wait
     // for the last copy into every slot
     for (int t = issued > NBS ? issued - NBS : 0; t < issued; ++t)
@@ -598,23 +655,52 @@ int tc_tile_width(long long rows, int ndim, int num_sms) {
   return tiles64 >= 2LL * num_sms ? 128 : 64;
 }
 
+bool tc_make_xmap(CUtensorMap* map, const float2* X, long long ldx, int M, int kdim) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!enc || ldx % 2 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || M <= 0 || kdim <= 0) return false;
+  const cuuint64_t pitch = (cuuint64_t)ldx * 8;    // bytes per row (complex64)
+  // view: (4 values, 8 rows, K2/4 chunks, M/8 row groups); every stride a
+  // multiple of 16 bytes; the last row group may reach 7 rows past M, inside
+  // the caller's buffer (rows there only produce discarded output rows)
+  cuuint64_t dims[4] = {4, 8, (cuuint64_t)((2 * kdim + 3) / 4), (cuuint64_t)((M + 7) / 8)};
+  cuuint64_t strides[3] = {pitch, 16, 8 * pitch};
+  cuuint32_t box[4] = {4, 8, (cuuint32_t)(tc::BK / 4), (cuuint32_t)(tc::BM / 8)};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(X), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static void tc_attributes() {
   static std::once_flag once;
   std::call_once(once, [] {
-    cudaFuncSetAttribute(k_tc_cgemm<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_cgemm<64, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tc::Cfg<64, true>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_tc_cgemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_cgemm<128, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tc::Cfg<128, true>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_tc_cgemm<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_cgemm<64, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tc::Cfg<64, false>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_tc_cgemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tc_cgemm<128, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc::Cfg<128, false>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<64, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         tc::Cfg<64, false>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm<128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tc::Cfg<128, false>::SMEM_BYTES);
   });
 }
 
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
-                     int* err, cudaStream_t st, bool split) {
+                     int* err, cudaStream_t st, bool split, const CUtensorMap* xmap) {
   if (B.bn != 64 && B.bn != 128) return cudaErrorInvalidValue;
   if (mode == 1 && (MB <= 0 || ldc < MB)) return cudaErrorInvalidValue;
   tc_attributes();
@@ -649,19 +735,36 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  // X by tensor copies when the transform has at least one tile per SM
+  // (measured: 255^2 and 319^2 applies 3-5 % faster; at 127^2, 80 tiles, the
+  // loader warps' own copies are faster)
+  static int num_sms = 0;
+  if (num_sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      num_sms = v;
+  }
+  const bool tmax = !split && xmap != nullptr && num_sms > 0 &&
+                    (long long)cfg.gridDim.x * cfg.gridDim.y >= num_sms;
+  const CUtensorMap& m = tmax ? *xmap : none;
   cudaError_t e;
   if (B.bn == 128 && split) {
     cfg.dynamicSmemBytes = tc::Cfg<128, true>::SMEM_BYTES;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, true>, a);
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, true, false>, a, m);
   } else if (split) {
     cfg.dynamicSmemBytes = tc::Cfg<64, true>::SMEM_BYTES;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, true>, a);
+    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, true, false>, a, m);
   } else if (B.bn == 128) {
     cfg.dynamicSmemBytes = tc::Cfg<128, false>::SMEM_BYTES;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, false>, a);
+    e = tmax ? cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, false, true>, a, m)
+             : cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, false, false>, a, m);
   } else {
     cfg.dynamicSmemBytes = tc::Cfg<64, false>::SMEM_BYTES;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, false>, a);
+    e = tmax ? cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, false, true>, a, m)
+             : cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, false, false>, a, m);
   }
   note_launch();
   return e != cudaSuccess ? e : cudaGetLastError();

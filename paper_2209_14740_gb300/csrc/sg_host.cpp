@@ -527,6 +527,16 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
     }
   }
   SG_CUDA_TRY(cudaMalloc(&h->d_tmp, (size_t)h->N * sizeof(double2)));
+  if (h->dim == 2 && h->fd) {
+    // inputs of transforms 2-4 of the plain-TF32 apply (rows of even length)
+    const int mx = h->mx, my = h->my, P = h->P;
+    const int mxp = mx + (mx & 1), myp = my + (my & 1);
+    const float2* t1 = reinterpret_cast<const float2*>(h->d_tmp);
+    const float2* t2 = reinterpret_cast<const float2*>(h->d_tmp2);
+    h->tc_xmap_ok = tc_make_xmap(&h->tc_xmap[0], t1, myp, P * mx, my) &&
+                    tc_make_xmap(&h->tc_xmap[1], t2, myp, P * mx, my) &&
+                    tc_make_xmap(&h->tc_xmap[2], t1, mxp, P * my, mx);
+  }
   int bad = 0;
   SG_CUDA_TRY(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
   cudaFree(d_bad);

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 SG Helmholtz library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,7 +90,13 @@ int tc_tile_width(long long rows, int ndim, int num_sms);
 // elementwise factor E[n * e_ld + m % e_mod] * (*escale).
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
-                     int* err, cudaStream_t st, bool split = true);
+                     int* err, cudaStream_t st, bool split = true, const CUtensorMap* xmap = nullptr);
+// Tensor map of X (M rows, K2 real values per row, row pitch ldx floats, 16-byte
+// aligned, ldx a multiple of 4) for the plain-TF32 transform: a 4D view
+// (4 values, 8 rows, K2/4 chunks, M/8 row groups) whose 4 x 8 x 8 x 16 box is one
+// K stage in the tensor cores' no-swizzle K-major layout.  False if the driver
+// entry point or the encoding is unavailable (the kernel then copies X itself).
+bool tc_make_xmap(CUtensorMap* map, const float2* X, long long ldx, int M, int kdim);
 
 struct GmresWork {
   int restart = 0;         // basis capacity (columns restart+1)
@@ -125,6 +132,10 @@ struct GmresWork {
 struct sg_handle {
   int dim = 1, nx = 0, ny = 1, mx = 0, my = 1, offx = 0, offy = 0, n = 0, P = 0, s = 0, r = 0;
   int T_terms = 0;
+  // tensor maps of the plain-TF32 transforms' inputs (fast diagonalisation,
+  // transforms 2-4: d_tmp, d_tmp2, d_tmp with their even row pitches)
+  CUtensorMap tc_xmap[3];
+  bool tc_xmap_ok = false;
   long long N = 0;
   double h = 0, beta = 0.5, kbar = 0;
   int bc[4] = {0, 0, 0, 0};

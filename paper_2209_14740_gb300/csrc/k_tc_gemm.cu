@@ -740,13 +740,12 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   // X by tensor copies when the transform has at least one tile per SM
   // (measured: 255^2 and 319^2 applies 3-5 % faster; at 127^2, 80 tiles, the
   // loader warps' own copies are faster)
-  static int num_sms = 0;
-  if (num_sms == 0) {
+  static const int num_sms = [] {   // thread-safe once (batched solves call from many threads)
     int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-      num_sms = v;
-  }
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 0;
+    return v;
+  }();
   const bool tmax = !split && xmap != nullptr && num_sms > 0 &&
                     (long long)cfg.gridDim.x * cfg.gridDim.y >= num_sms;
   const CUtensorMap& m = tmax ? *xmap : none;

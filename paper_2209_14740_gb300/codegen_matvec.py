@@ -1211,27 +1211,38 @@ def generate(path: str) -> str:
             "  note_launch();",
             "  return cudaGetLastError();",
             "}",
+            "// Shared memory of a persistent kernel's CTA: P rows of (tile + halo)",
+            "// values and the tile's wavenumber fields.",
+            "template <int TX, int TY>",
+            "static size_t persist_smem(int P, int nfields) {",
+            "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
+            "  return ((size_t)P * (nt + nh) + (size_t)nfields * (nt / 2)) * sizeof(float);",
+            "}",
+            "// CTAs per SM of a persistent kernel (its shared-memory limit raised first);",
+            "// each call site keeps the value in a static initialised once (thread-safe).",
+            "template <int TX, int TY>",
+            "static int persist_occupancy(void (*kern)(OpParams<float>, const float*, float*), int P, int nfields) {",
+            "  const size_t smem = persist_smem<TX, TY>(P, nfields);",
+            "  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
+            "  int o = 0;",
+            "  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 2 * TX * TY, smem) != cudaSuccess) o = 0;",
+            "  return o > 0 ? o : 1;",
+            "}",
             "// Launch of a persistent kernel: as many CTAs as fit on the GPU at once",
-            "// (at most one per tile); *occ caches the CTAs per SM of this kernel.",
+            "// (at most one per tile); occ = CTAs per SM of this kernel.",
             "template <int TX, int TY>",
             "static cudaError_t launch_persist(void (*kern)(OpParams<float>, const float*, float*), int P, int nfields,",
-            "                                  int* occ,",
+            "                                  int occ,",
             "                                  const sg_handle* h, const OpParams<float>& p, const float2* X,",
             "                                  float2* Y, cudaStream_t st) {",
-            "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
-            "  const size_t smem = ((size_t)P * (nt + nh) + (size_t)nfields * (nt / 2)) * sizeof(float);",
+            "  const int nt = 2 * TX * TY;",
+            "  const size_t smem = persist_smem<TX, TY>(P, nfields);",
             "  if (smem > 48 * 1024) {",
             "    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
             "    if (e != cudaSuccess) return e;",
             "  }",
-            "  if (*occ <= 0) {",
-            "    int o = 0;",
-            "    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, nt, smem);",
-            "    if (e != cudaSuccess) return e;",
-            "    *occ = o > 0 ? o : 1;",
-            "  }",
             "  const long long tiles = (long long)((h->mx + TX - 1) / TX) * ((h->my + TY - 1) / TY);",
-            "  const int grid = (int)std::min<long long>(tiles, (long long)h->num_sms * *occ);",
+            "  const int grid = (int)std::min<long long>(tiles, (long long)h->num_sms * occ);",
             "  kern<<<grid, nt, smem, st>>>(p, reinterpret_cast<const float*>(X), reinterpret_cast<float*>(Y));",
             "  note_launch();",
             "  return cudaGetLastError();",
@@ -1249,10 +1260,14 @@ def generate(path: str) -> str:
         parts.append("    *handled = true;")
         if STENCIL == "tile" and COUPLING == "tk" and PERSISTENT:
             tx, ty = PTILE_2D
-            parts.append("    static int occ2 = 0, occ1 = 0;")
-            parts.append("    if (h->dim == 2) return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, &occ2, h, p, X, Y, st);"
+            parts.append("    if (h->dim == 2) {")
+            parts.append("      static const int occ2 = persist_occupancy<%d, %d>(%s<%d, %d>, %d, %d);"
                          % (tx, ty, name, tx, ty, P, s + 1))
-            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, &occ1, h, p, X, Y, st);" % (name, P, s + 1))
+            parts.append("      return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, occ2, h, p, X, Y, st);"
+                         % (tx, ty, name, tx, ty, P, s + 1))
+            parts.append("    }")
+            parts.append("    static const int occ1 = persist_occupancy<64, 1>(%s<64, 1>, %d, %d);" % (name, P, s + 1))
+            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, occ1, h, p, X, Y, st);" % (name, P, s + 1))
         elif STENCIL == "tile":
             tx, ty = tile_2d(P)
             parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"

@@ -53,6 +53,17 @@ PERSISTENT = True    # complex64 "tk" kernels: persistent CTAs, next tile copied
 # issues the copies at the first row of degree r + 1 (fewer registers, more
 # CTAs; measured faster at P = 20)
 BND_SPLIT_MIN_P = 56
+# persistent kernels with at least BND_SPLIT_MIN_P modes copy whole unknowns
+# (8 bytes) and keep the wavenumber fields, and up to DBUF_MAX_K of the modes
+# read last (the highest, in graded order), in two shared buffers, so that
+# those copies of the next tile go out at the start of this one; the other
+# modes are copied once the rows that read them are done.  Measured at
+# P = 84: 56 double-buffered modes made the kernel slower (0.150 against
+# 0.129 ms; the 231 KB carve-out leaves ~28 KB of L1 to the cp.async.ca
+# copies), so none are.
+DBUF = True
+DBUF_MAX_K = 0
+SMEM_LIMIT = 227 * 1024   # dynamic shared memory per CTA (opt-in maximum)
 # FP64 kernels are generated for P up to this (two registers per value: the
 # mode values and accumulators of larger P do not fit)
 F64_MAX_P = 35
@@ -717,6 +728,23 @@ def _emit_tk_rows(w, s, r, rows, lo, hi, finish, bnd, first_x=None, first_z=None
     return seen
 
 
+def dbuf_modes(s, r):
+    """Number of double-buffered modes of the persistent kernel for (s, r):
+    None for the single-buffer form (gen_kernel_tkp), else K >= 0 for
+    _gen_kernel_tkp_dbuf, at most DBUF_MAX_K and as many as the shared-memory
+    limit allows for both tile shapes (with two buffers of the s+1
+    wavenumber fields)."""
+    P = len(_multi_indices(s, r))
+    if not (PERSISTENT and DBUF) or P < BND_SPLIT_MIN_P:
+        return None
+    k = min(P, DBUF_MAX_K)
+    for tx, ty in (PTILE_2D, (64, 1)):
+        nt = 2 * tx * ty
+        st = nt + 2 * (2 * tx + 2 * ty)
+        k = min(k, (SMEM_LIMIT // 4 - 2 * (s + 1) * (nt // 2)) // st - P)
+    return max(k, 0)
+
+
 def gen_kernel_tkp(s, r):
     """Persistent form of the factorised complex64 kernel (gen_kernel_tk):
     each CTA walks tiles of TX x TY unknowns with a stride of the grid size,
@@ -735,6 +763,9 @@ def gen_kernel_tkp(s, r):
     while its next tile is in flight."""
     idx, _ = _tk_rows(s, r)
     P = len(idx)
+    K = dbuf_modes(s, r)
+    if K is not None:
+        return _gen_kernel_tkp_dbuf(s, r, K)
     name = "k_mvkp_s%dr%d" % (s, r)
     L = []
     w = L.append
@@ -875,6 +906,209 @@ def gen_kernel_tkp(s, r):
     w("    if (tile + (int)gridDim.x < tiles) issue(tile + gridDim.x);")
     declared = region(hook, top, declared)
     # rows of degree r + 1 (no output of their own: no exchange)
+    _emit_tk_rows(w, s, r, rows, top, len(rows), finish, False, declared=declared)
+    w("  }")
+    w("}")
+    return name, P, "\n".join(L)
+
+
+def _gen_kernel_tkp_dbuf(s, r, K):
+    """gen_kernel_tkp with the modes P0 = P - K .. P - 1 and the wavenumber
+    fields in two shared buffers (tile parity q):
+
+      wait for this tile's copies -> copy the next tile's modes P0.. and
+      fields into the other buffer -> rows up to the last one that reads a
+      mode < P0 from shared memory -> barrier -> copy the next tile's modes
+      < P0 -> the remaining rows.
+
+    In graded order the modes < P0 are the low degrees, which the first rows
+    already read in full, so the single-buffered copies go out after a few
+    rows and the double-buffered ones a whole tile ahead.  Same arithmetic,
+    in the same order, as the single-buffer form."""
+    idx, rows = _tk_rows(s, r)
+    P = len(idx)
+    P0 = P - K
+    name = "k_mvkp_s%dr%d" % (s, r)
+    L = []
+    w = L.append
+    w("template <int TX, int TY>")
+    w("__global__ void __launch_bounds__(2 * TX * TY) %s(OpParams<float> p, const float* __restrict__ X, "
+      "float* __restrict__ Y) {" % name)
+    w("  constexpr int NT = 2 * TX * TY;            // threads = (unknown, component) pairs")
+    w("  constexpr int NN = NT / 2;                 // unknowns of a tile")
+    w("  constexpr int NH = 2 * (2 * TX + 2 * TY);  // halo entries per mode")
+    w("  constexpr int NHN = NH / 2;                // halo unknowns")
+    w("  constexpr int ST = NT + NH;                // shared-memory row stride per mode")
+    w("  constexpr int P0 = %d;                     // modes 0 .. P0-1: one buffer" % P0)
+    if K:
+        w("  constexpr int K = %d;                      // modes P0 .. %d: two buffers of K rows" % (K, P - 1))
+    else:
+        w("  constexpr int K = 0;                       // (no double-buffered modes)")
+    w("  constexpr int NF = %d;                     // wavenumber fields k_0 .. k_s" % (s + 1))
+    if K:
+        w("  constexpr int FS = (P0 + 2 * K) * ST;      // then two buffers of [NF][NN] fields")
+        w("  // [P0][ST] | [2][K][ST] | [2][NF][NN]; a mode row holds the tile's values")
+    else:
+        w("  constexpr int FS = P0 * ST;                // then the [NF][NN] fields")
+        w("  // [P][ST] | [NF][NN]; a mode row holds the tile's values")
+    w("  // (unknown-major, re/im adjacent), then the halo's")
+    w("  extern __shared__ __align__(16) float xs[];")
+    w("  if (p.skip && *p.skip) return;")
+    w("  const int t = threadIdx.x, c = t & 1, nid = t >> 1;")
+    w("  const int lx = nid % TX, ly = nid / TX;")
+    w("  const int tiles_x = (p.mx + TX - 1) / TX;")
+    w("  const int tiles = tiles_x * ((p.my + TY - 1) / TY);")
+    w("  const long long n2 = 2ll * p.n;")
+    w("  const uint32_t xs0 = (uint32_t)__cvta_generic_to_shared(xs);")
+    w("  const int oxm = lx > 0 ? t - 2 : NT + 2 * (2 * TX + ly) + c;")
+    w("  const int oxp = lx < TX - 1 ? t + 2 : NT + 2 * (2 * TX + TY + ly) + c;")
+    w("  const int oym = ly > 0 ? t - 2 * TX : NT + 2 * lx + c;")
+    w("  const int oyp = ly < TY - 1 ? t + 2 * TX : NT + 2 * (TX + lx) + c;")
+    w("  // 8-byte copies of modes a_lo .. a_hi - 1 of one tile into the rows")
+    w("  // starting at shared byte address base (row a_lo first): thread t copies")
+    w("  // unknown t % NN of every other mode, and (NT >= NHN) halo unknown")
+    w("  // t % NHN of every HG-th mode; halo unknowns outside the grid are")
+    w("  // zero-filled, tile unknowns outside it repeat the last row or column")
+    w("  auto copy_modes = [&](int tile, int a_lo, int a_hi, uint32_t base) {")
+    w("    const int bx0 = (tile % tiles_x) * TX, by0 = (tile / tiles_x) * TY;")
+    w("    {")
+    w("      const int nd = t % NN, a0 = t / NN;")
+    w("      const int iu = min(bx0 + nd % TX, p.mx - 1), ju = min(by0 + nd / TX, p.my - 1);")
+    w("      const float* src = X + (long long)(a_lo + a0) * n2 + 2ll * (iu + (long long)p.mx * ju);")
+    w("      uint32_t dst = base + 4u * (a0 * ST + 2 * nd);")
+    w("#pragma unroll 4")
+    w("      for (int a = a_lo + a0; a < a_hi; a += 2, src += 2 * n2, dst += 8u * ST) mv_cp_async8(dst, src, 8);")
+    w("    }")
+    w("    auto halo = [&](int hn, int a0, int hg) {")
+    w("      int hx, hy;")
+    w("      if (hn < TX) { hx = bx0 + hn; hy = by0 - 1; }")
+    w("      else if (hn < 2 * TX) { hx = bx0 + hn - TX; hy = by0 + TY; }")
+    w("      else if (hn < 2 * TX + TY) { hx = bx0 - 1; hy = by0 + hn - 2 * TX; }")
+    w("      else { hx = bx0 + TX; hy = by0 + hn - 2 * TX - TY; }")
+    w("      const bool ok = hx >= 0 && hx < p.mx && hy >= 0 && hy < p.my;")
+    w("      const float* src = ok ? X + (long long)a0 * n2 + 2ll * (hx + (long long)p.mx * hy) : X;")
+    w("      const long long step = ok ? hg * n2 : 0;")
+    w("      uint32_t dst = base + 4u * ((a0 - a_lo) * ST + NT + 2 * hn);")
+    w("#pragma unroll 4")
+    w("      for (int a = a0; a < a_hi; a += hg, src += step, dst += 4u * hg * ST) mv_cp_async8(dst, src, ok ? 8 : 0);")
+    w("    };")
+    w("    constexpr int HG = NT >= NHN ? NT / NHN : 0;")
+    w("    if (HG > 0) {")
+    w("      if (t < HG * NHN) halo(t % NHN, a_lo + t / NHN, HG);")
+    w("    } else {")
+    w("      for (int hn = t; hn < NHN; hn += NT) halo(hn, a_lo, 1);")
+    w("    }")
+    w("  };")
+    # the s+1 wavenumber fields of the tile's unknowns (one thread of each pair)
+    def emit_fields(dst_expr):
+        w("    if (c == 0) {")
+        w("      const int bx0 = (tile % tiles_x) * TX, by0 = (tile / tiles_x) * TY;")
+        w("      const int iu = min(bx0 + lx, p.mx - 1), ju = min(by0 + ly, p.my - 1);")
+        w("      const float* fsrc = p.fields + iu + (long long)p.mx * ju;")
+        w("      uint32_t fdst = xs0 + 4u * (%s + nid);" % dst_expr)
+        w("#pragma unroll")
+        w("      for (int l = 0; l < NF; ++l, fsrc += p.n, fdst += 4u * NN) mv_cp_async4(fdst, fsrc, 4);")
+        w("    }")
+    if K:
+        w("  // modes P0.. and the fields of a tile into buffer q")
+        w("  auto issue_early = [&](int tile, int q) {")
+        w("    copy_modes(tile, P0, P0 + K, xs0 + 4u * ((P0 + q * K) * ST));")
+        emit_fields("FS + q * NF * NN")
+        w('    asm volatile("cp.async.commit_group;" ::: "memory");')
+        w("  };")
+        w("  // modes 0 .. P0-1 of a tile (single buffer)")
+    else:
+        w("  // all modes and the fields of a tile")
+    w("  auto issue_late = [&](int tile) {")
+    w("    copy_modes(tile, 0, P0, xs0);")
+    if not K:
+        emit_fields("FS")
+    w('    asm volatile("cp.async.commit_group;" ::: "memory");')
+    w("  };")
+    if K:
+        w("  int tile = blockIdx.x, q = 0;")
+        w("  if (tile < tiles) {")
+        w("    issue_early(tile, 0);")
+        w("    issue_late(tile);")
+        w("  }")
+        w("  for (; tile < tiles; tile += gridDim.x, q ^= 1) {")
+    else:
+        w("  int tile = blockIdx.x;")
+        w("  if (tile < tiles) issue_late(tile);")
+        w("  for (; tile < tiles; tile += gridDim.x) {")
+    w("    const int iu0 = (tile % tiles_x) * TX + lx, ju0 = (tile / tiles_x) * TY + ly;")
+    w("    const bool valid = iu0 < p.mx && ju0 < p.my;")
+    w("    const int iu = min(iu0, p.mx - 1), ju = min(ju0, p.my - 1);")
+    w("    const int u = iu + p.mx * ju;")
+    w("    const NodeGeom<float> g = node_geom<float>(p, iu, ju);")
+    w("    const float wxm = g.hxm ? g.wxm : 0.0f, wxp = g.hxp ? g.wxp : 0.0f;")
+    w("    const float wym = g.hym ? g.wym : 0.0f, wyp = g.hyp ? g.wyp : 0.0f;")
+    w("    // mode values in registers are scaled by -w2 (a power of two: exact),")
+    w("    // so the diagonal and boundary weights applied to them take the")
+    w("    // inverse factor; the neighbours come unscaled from shared memory")
+    w("    const float nw2 = -g.w2, inw2 = -1.0f / g.w2;")
+    w("    const float ldg2 = g.ldiag * inw2;")
+    w("    const bool bnd = __any_sync(0xffffffffu, g.w1 != 0.0f);")
+    w("    const float sw1 = (c ? -g.w1 : g.w1) * inw2;   // -i w1 W: re gets +w1 Im W, im gets -w1 Re W")
+    w("    float* __restrict__ yp = Y + 2ll * u + c;")
+    w('    asm volatile("cp.async.wait_all;" ::: "memory");')
+    w("    __syncthreads();")
+    if K:
+        w("    // every read of the other buffer (the previous tile's) is done")
+        w("    if (tile + (int)gridDim.x < tiles) issue_early(tile + gridDim.x, q ^ 1);")
+        w("    const float* __restrict__ xq = xs + q * (K * ST);   // xq[a * ST + ..]: mode a >= P0")
+        w("    const float* __restrict__ fq = xs + FS + q * (NF * NN);")
+    else:
+        w("    const float* __restrict__ fq = xs + FS;")
+    w("    const float k0 = fq[nid];")
+    for l in range(s):
+        w("    const float k%d = fq[%d * NN + nid];" % (l + 1, l + 1))
+    for l in range(s):
+        for n in range(1, r + 2):
+            w("    const float kb%d_%d = k%d * %s;" % (l + 1, n, l + 1, _f(_b(n))))
+    w("    float %s;" % ", ".join("x%d" % a for a in range(P)))
+    w("    float %s;" % ", ".join("z%d" % a for a in range(P)))
+
+    def arr(b):
+        return "xs" if b < P0 else "xq"
+
+    def first_x(b):
+        w("    x%d = nw2 * %s[%d * ST + t];" % (b, arr(b), b))
+
+    def first_z(a):
+        m = arr(a)
+        w("    z%d = fmaf(ldg2, x%d, fmaf(-wxm, %s[%d * ST + oxm], fmaf(-wxp, %s[%d * ST + oxp], "
+          "fmaf(-wym, %s[%d * ST + oym], -wyp * %s[%d * ST + oyp]))));" % (a, a, m, a, m, a, m, a, m, a))
+
+    def finish(a):
+        w("    if (valid) yp[%d * n2] = z%d;" % (a, a))
+
+    top = min(ri for ri, (gm, _) in enumerate(rows) if sum(gm) == r + 1)
+    # the single-buffered copies go out right after the last row that reads a
+    # mode < P0 from shared memory (its first use or its output's stencil)
+    seen = set()
+    hook = 0
+    for ri, (gm, terms) in enumerate(rows):
+        for _, b in terms:
+            if b not in seen:
+                seen.add(b)
+                if b < P0:
+                    hook = ri + 1
+    assert hook <= top
+
+    def region(lo, hi, declared=()):
+        if hi <= lo:
+            return set(declared)
+        w("    if (bnd) {")
+        d = _emit_tk_rows(w, s, r, rows, lo, hi, finish, True, first_x, first_z, declared)
+        w("    } else {")
+        _emit_tk_rows(w, s, r, rows, lo, hi, finish, False, first_x, first_z, declared)
+        w("    }")
+        return d
+    declared = region(0, hook)
+    w("    __syncthreads();   // every shared value of modes < P0 has been read")
+    w("    if (tile + (int)gridDim.x < tiles) issue_late(tile + gridDim.x);")
+    declared = region(hook, top, declared)
     _emit_tk_rows(w, s, r, rows, top, len(rows), finish, False, declared=declared)
     w("  }")
     w("}")
@@ -1170,6 +1404,9 @@ def generate(path: str) -> str:
              "// 4-byte asynchronous global -> shared copy; bytes = 0 writes a zero",
              "__device__ __forceinline__ void mv_cp_async4(uint32_t dst, const float* src, int bytes) {",
              "  asm volatile(\"cp.async.ca.shared.global [%0], [%1], 4, %2;\" :: \"r\"(dst), \"l\"(src), \"r\"(bytes) : \"memory\");",
+             "}",
+             "__device__ __forceinline__ void mv_cp_async8(uint32_t dst, const float* src, int bytes) {",
+             "  asm volatile(\"cp.async.ca.shared.global [%0], [%1], 8, %2;\" :: \"r\"(dst), \"l\"(src), \"r\"(bytes) : \"memory\");",
              "}"]
     table = []
     table64 = []
@@ -1212,17 +1449,20 @@ def generate(path: str) -> str:
             "  return cudaGetLastError();",
             "}",
             "// Shared memory of a persistent kernel's CTA: P rows of (tile + halo)",
-            "// values and the tile's wavenumber fields.",
+            "// values and the tile's wavenumber fields; K > 0: the last K rows and",
+            "// the fields twice (double-buffered).",
             "template <int TX, int TY>",
-            "static size_t persist_smem(int P, int nfields) {",
+            "static size_t persist_smem(int P, int nfields, int K) {",
             "  const int nt = 2 * TX * TY, nh = 2 * (2 * TX + 2 * TY);",
-            "  return ((size_t)P * (nt + nh) + (size_t)nfields * (nt / 2)) * sizeof(float);",
+            "  const int rows = K > 0 ? P + K : P, fbufs = K > 0 ? 2 : 1;",
+            "  return ((size_t)rows * (nt + nh) + (size_t)fbufs * nfields * (nt / 2)) * sizeof(float);",
             "}",
             "// CTAs per SM of a persistent kernel (its shared-memory limit raised first);",
             "// each call site keeps the value in a static initialised once (thread-safe).",
             "template <int TX, int TY>",
-            "static int persist_occupancy(void (*kern)(OpParams<float>, const float*, float*), int P, int nfields) {",
-            "  const size_t smem = persist_smem<TX, TY>(P, nfields);",
+            "static int persist_occupancy(void (*kern)(OpParams<float>, const float*, float*), int P, int nfields,",
+            "                             int K) {",
+            "  const size_t smem = persist_smem<TX, TY>(P, nfields, K);",
             "  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
             "  int o = 0;",
             "  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 2 * TX * TY, smem) != cudaSuccess) o = 0;",
@@ -1232,11 +1472,11 @@ def generate(path: str) -> str:
             "// (at most one per tile); occ = CTAs per SM of this kernel.",
             "template <int TX, int TY>",
             "static cudaError_t launch_persist(void (*kern)(OpParams<float>, const float*, float*), int P, int nfields,",
-            "                                  int occ,",
+            "                                  int K, int occ,",
             "                                  const sg_handle* h, const OpParams<float>& p, const float2* X,",
             "                                  float2* Y, cudaStream_t st) {",
             "  const int nt = 2 * TX * TY;",
-            "  const size_t smem = persist_smem<TX, TY>(P, nfields);",
+            "  const size_t smem = persist_smem<TX, TY>(P, nfields, K);",
             "  if (smem > 48 * 1024) {",
             "    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);",
             "    if (e != cudaSuccess) return e;",
@@ -1260,14 +1500,18 @@ def generate(path: str) -> str:
         parts.append("    *handled = true;")
         if STENCIL == "tile" and COUPLING == "tk" and PERSISTENT:
             tx, ty = PTILE_2D
+            K = dbuf_modes(s, r)
+            K = -1 if K is None else K
             parts.append("    if (h->dim == 2) {")
-            parts.append("      static const int occ2 = persist_occupancy<%d, %d>(%s<%d, %d>, %d, %d);"
-                         % (tx, ty, name, tx, ty, P, s + 1))
-            parts.append("      return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, occ2, h, p, X, Y, st);"
-                         % (tx, ty, name, tx, ty, P, s + 1))
+            parts.append("      static const int occ2 = persist_occupancy<%d, %d>(%s<%d, %d>, %d, %d, %d);"
+                         % (tx, ty, name, tx, ty, P, s + 1, K))
+            parts.append("      return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, %d, occ2, h, p, X, Y, st);"
+                         % (tx, ty, name, tx, ty, P, s + 1, K))
             parts.append("    }")
-            parts.append("    static const int occ1 = persist_occupancy<64, 1>(%s<64, 1>, %d, %d);" % (name, P, s + 1))
-            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, occ1, h, p, X, Y, st);" % (name, P, s + 1))
+            parts.append("    static const int occ1 = persist_occupancy<64, 1>(%s<64, 1>, %d, %d, %d);"
+                         % (name, P, s + 1, K))
+            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, %d, occ1, h, p, X, Y, st);"
+                         % (name, P, s + 1, K))
         elif STENCIL == "tile":
             tx, ty = tile_2d(P)
             parts.append("    if (h->dim == 2) return launch_tile<%d, %d>(%s<%d, %d>, %d, h, p, X, Y, st);"

@@ -151,11 +151,36 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 // Each block walks chunks of RED_THREADS * CG_EPT consecutive elements (grid
 // stride), a thread keeps its CG_EPT elements of w in registers, and every
 // pass reads each V_i element once (the DOTS re-read of the chunk it just
-// updated comes from L1).  Per-warp sums go to a [warp][value] table in
+// updated comes from L1 or L2).  Complex64 passes read the basis four
+// vectors at a time, all loads of a group issued (predicated, not behind a
+// branch per vector) before any is used, so that a thread keeps 16 in
+// flight; they are limited to 85 registers so that three blocks fit an SM
+// and the grid runs in one wave.  Per-warp sums go to a [warp][value] table in
 // shared memory, block sums to part[value * gridDim.x + block], and the last
 // block adds the blocks in a fixed order (bitwise reproducible).
 constexpr int CG_EPT = 4;
 constexpr int CG_WARPS = RED_THREADS / 32;
+constexpr int CG_QB = 4;   // complex64: basis vectors per group of loads in flight
+// Resident blocks per SM the complex64 passes are compiled for (at most 85
+// registers a thread); their complex128 forms keep the compiler's choice.
+constexpr int CG_MIN_BLOCKS_C64 = 3;
+
+// v[q][k] = V_{i0+q}[base + k RED_THREADS] for i0 + q < nv and elements below
+// N, else zero; every load is issued before the caller uses any.
+template <typename T>
+__device__ __forceinline__ void load_group(const C2<T>* __restrict__ V, long long N, int nv, int i0,
+                                           long long base, C2<T> (&v)[CG_QB][CG_EPT]) {
+#pragma unroll
+  for (int q = 0; q < CG_QB; ++q) {
+    const bool live = i0 + q < nv;
+    const C2<T>* Vi = V + (size_t)(live ? i0 + q : 0) * N;
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      v[q][k] = live && e < N ? __ldg(Vi + e) : mkc<T>(T(0), T(0));
+    }
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -195,23 +220,47 @@ __device__ __forceinline__ void chunk_dots(const C2<T>* __restrict__ V, long lon
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 < nv; i0 += 8) {
     T acc[16];
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      T ax = T(0), ay = T(0);
-      if (i0 + q < nv) {
-        const C2<T>* Vi = V + (size_t)(i0 + q) * N;
+      for (int qb = 0; qb < 8; qb += CG_QB) {
+        if (i0 + qb >= nv) {   // warp-uniform: a group with no vector left
 #pragma unroll
-        for (int k = 0; k < CG_EPT; ++k) {
-          const long long e = base + k * RED_THREADS;
-          if (e < N) {
-            const C2<T> v = __ldg(Vi + e);
-            ax += v.x * wk[k].x + v.y * wk[k].y;
-            ay += v.x * wk[k].y - v.y * wk[k].x;
+          for (int q = 0; q < 2 * CG_QB; ++q) acc[2 * qb + q] = T(0);
+          continue;
+        }
+        C2<T> v[CG_QB][CG_EPT];
+        load_group<T>(V, N, nv, i0 + qb, base, v);
+#pragma unroll
+        for (int q = 0; q < CG_QB; ++q) {
+          T ax = T(0), ay = T(0);
+#pragma unroll
+          for (int k = 0; k < CG_EPT; ++k) {
+            ax += v[q][k].x * wk[k].x + v[q][k].y * wk[k].y;
+            ay += v[q][k].x * wk[k].y - v[q][k].y * wk[k].x;
           }
+          acc[2 * (qb + q)] = ax;
+          acc[2 * (qb + q) + 1] = ay;
         }
       }
-      acc[2 * q] = ax;
-      acc[2 * q + 1] = ay;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        T ax = T(0), ay = T(0);
+        if (i0 + q < nv) {
+          const C2<T>* Vi = V + (size_t)(i0 + q) * N;
+#pragma unroll
+          for (int k = 0; k < CG_EPT; ++k) {
+            const long long e = base + k * RED_THREADS;
+            if (e < N) {
+              const C2<T> v = __ldg(Vi + e);
+              ax += v.x * wk[k].x + v.y * wk[k].y;
+              ay += v.x * wk[k].y - v.y * wk[k].x;
+            }
+          }
+        }
+        acc[2 * q] = ax;
+        acc[2 * q + 1] = ay;
+      }
     }
     const T sum = warp_sum16(acc);
     if ((lane & 1) == 0) {
@@ -271,10 +320,9 @@ __device__ __forceinline__ bool finish_dots(int nv, const double2* red, double* 
 // c2prev_i V_i; the last block turns u^H w into u_hat^H w = u^H w -
 // sum_i conj(c2prev_i) d_i before forming c.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(const C2<T>* __restrict__ V, long long N, int nv,
-                                                         const C2<T>* __restrict__ w, double* part,
-                                                         unsigned* counter, const double* vscale, double* d_out,
-                                                         double* c_out, const int* ctl, const double* c2prev) {
+__device__ __forceinline__ void cgs_dots_body(
+    const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
@@ -307,6 +355,18 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(const C2<T>* __restric
     }
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(
+    const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev) {
+  cgs_dots_body<T>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev);
+}
+template <>
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_dots<float>(
+    const C2<float>* __restrict__ V, long long N, int nv, const C2<float>* __restrict__ w, double* part,
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev) {
+  cgs_dots_body<float>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev);
+}
 
 __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j);
 
@@ -314,11 +374,10 @@ __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j);
 // ||w||^2 and the Givens update of column j (GIVENS).
 // Dynamic shared memory (DOTS): CG_WARPS * nv double2.
 template <typename T, bool DOTS>
-__global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restrict__ V, long long N, int nv,
-                                                           C2<T>* __restrict__ w, const double* __restrict__ c,
-                                                           double* part, unsigned* counter, const double* vscale,
-                                                           double* d_out, double* c_out, double* D, int* ctl,
-                                                           DevLayout L, int j) {
+__device__ __forceinline__ void cgs_update_body(
+    const C2<T>* __restrict__ V, long long N, int nv, C2<T>* __restrict__ w,
+    const double* __restrict__ c, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L, int j) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   __shared__ C2<T> cs[MAXV];
@@ -336,17 +395,34 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restr
       const long long e = base + k * RED_THREADS;
       wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
     }
-#pragma unroll 4
-    for (int i = 0; i < nv; ++i) {
-      const C2<T>* Vi = V + (size_t)i * N;
-      const C2<T> ci = cs[i];
+    if constexpr (sizeof(T) == 4) {
+      for (int i0 = 0; i0 < nv; i0 += CG_QB) {
+        C2<T> v[CG_QB][CG_EPT];
+        load_group<T>(V, N, nv, i0, base, v);
 #pragma unroll
-      for (int k = 0; k < CG_EPT; ++k) {
-        const long long e = base + k * RED_THREADS;
-        if (e < N) {
-          const C2<T> v = __ldg(Vi + e);
-          wk[k].x -= ci.x * v.x - ci.y * v.y;
-          wk[k].y -= ci.x * v.y + ci.y * v.x;
+        for (int q = 0; q < CG_QB; ++q) {
+          if (i0 + q >= nv) break;
+          const C2<T> ci = cs[i0 + q];
+#pragma unroll
+          for (int k = 0; k < CG_EPT; ++k) {
+            wk[k].x -= ci.x * v[q][k].x - ci.y * v[q][k].y;
+            wk[k].y -= ci.x * v[q][k].y + ci.y * v[q][k].x;
+          }
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int i = 0; i < nv; ++i) {
+        const C2<T>* Vi = V + (size_t)i * N;
+        const C2<T> ci = cs[i];
+#pragma unroll
+        for (int k = 0; k < CG_EPT; ++k) {
+          const long long e = base + k * RED_THREADS;
+          if (e < N) {
+            const C2<T> v = __ldg(Vi + e);
+            wk[k].x -= ci.x * v.x - ci.y * v.y;
+            wk[k].y -= ci.x * v.y + ci.y * v.x;
+          }
         }
       }
     }
@@ -373,6 +449,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restr
   __syncthreads();
   if (threadIdx.x < 32) givens_column(D, ctl, L, j);
 }
+template <typename T, bool DOTS>
+__global__ void __launch_bounds__(RED_THREADS) k_cgs_update(
+    const C2<T>* __restrict__ V, long long N, int nv, C2<T>* __restrict__ w,
+    const double* __restrict__ c, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L, int j) {
+  cgs_update_body<T, DOTS>(V, N, nv, w, c, part, counter, vscale, d_out, c_out, D, ctl, L, j);
+}
+template <>
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_update<float, true>(
+    const C2<float>* __restrict__ V, long long N, int nv, C2<float>* __restrict__ w,
+    const double* __restrict__ c, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L, int j) {
+  cgs_update_body<float, true>(V, N, nv, w, c, part, counter, vscale, d_out, c_out, D, ctl, L, j);
+}
+template <>
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_update<float, false>(
+    const C2<float>* __restrict__ V, long long N, int nv, C2<float>* __restrict__ w,
+    const double* __restrict__ c, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L, int j) {
+  cgs_update_body<float, false>(V, N, nv, w, c, part, counter, vscale, d_out, c_out, D, ctl, L, j);
+}
 
 // Two-pass form, pass 2 (flexible cycles): with j = nv - 1,
 //   u_hat = u - sum_{i<j} c2prev_i V_i           (finalises slot j)
@@ -384,12 +481,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs_update(const C2<T>* __restr
 // vector w - sum c2_i V_i itself is formed by the next step's pass 2.
 // Dynamic shared memory: CG_WARPS * nv double2.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(C2<T>* __restrict__ V, long long N, int nv,
-                                                            const double* __restrict__ c1,
-                                                            const double* __restrict__ c2prev, double* part,
-                                                            unsigned* counter, const double* vscale,
-                                                            double* d_out, double* c_out, double* D, int* ctl,
-                                                            DevLayout L) {
+__device__ __forceinline__ void cgs2_second_body(
+    C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
+    const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   __shared__ C2<T> cs1[MAXV];
@@ -414,19 +509,38 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(C2<T>* __restrict__
       wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
       uk[k] = e < N ? uj[e] : mkc<T>(T(0), T(0));
     }
-#pragma unroll 4
-    for (int i = 0; i < j; ++i) {
-      const C2<T>* Vi = V + (size_t)i * N;
-      const C2<T> a = cs1[i], b = cs2[i];
+    if constexpr (sizeof(T) == 4) {
+      for (int i0 = 0; i0 < j; i0 += CG_QB) {
+        C2<T> v[CG_QB][CG_EPT];
+        load_group<T>(V, N, j, i0, base, v);
 #pragma unroll
-      for (int k = 0; k < CG_EPT; ++k) {
-        const long long e = base + k * RED_THREADS;
-        if (e < N) {
-          const C2<T> v = __ldg(Vi + e);
-          wk[k].x -= a.x * v.x - a.y * v.y;
-          wk[k].y -= a.x * v.y + a.y * v.x;
-          uk[k].x -= b.x * v.x - b.y * v.y;
-          uk[k].y -= b.x * v.y + b.y * v.x;
+        for (int q = 0; q < CG_QB; ++q) {
+          if (i0 + q >= j) break;
+          const C2<T> a = cs1[i0 + q], b = cs2[i0 + q];
+#pragma unroll
+          for (int k = 0; k < CG_EPT; ++k) {
+            wk[k].x -= a.x * v[q][k].x - a.y * v[q][k].y;
+            wk[k].y -= a.x * v[q][k].y + a.y * v[q][k].x;
+            uk[k].x -= b.x * v[q][k].x - b.y * v[q][k].y;
+            uk[k].y -= b.x * v[q][k].y + b.y * v[q][k].x;
+          }
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int i = 0; i < j; ++i) {
+        const C2<T>* Vi = V + (size_t)i * N;
+        const C2<T> a = cs1[i], b = cs2[i];
+#pragma unroll
+        for (int k = 0; k < CG_EPT; ++k) {
+          const long long e = base + k * RED_THREADS;
+          if (e < N) {
+            const C2<T> v = __ldg(Vi + e);
+            wk[k].x -= a.x * v.x - a.y * v.y;
+            wk[k].y -= a.x * v.y + a.y * v.x;
+            uk[k].x -= b.x * v.x - b.y * v.y;
+            uk[k].y -= b.x * v.y + b.y * v.x;
+          }
         }
       }
     }
@@ -512,6 +626,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(C2<T>* __restrict__
   }
   __syncthreads();
   if (threadIdx.x < 32) givens_column(D, ctl, L, j);
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(
+    C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
+    const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L) {
+  cgs2_second_body<T>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L);
+}
+template <>
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs2_second<float>(
+    C2<float>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
+    const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* c_out, double* D, int* ctl, DevLayout L) {
+  cgs2_second_body<float>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L);
 }
 
 // r = b - Ax (or r = b when Ax == nullptr) written in the inner precision;

@@ -450,7 +450,7 @@ def run_ours(args):
         flops = 8.0 * op.P * m * m * m                          # complex GEMM: 8 real flop per complex MAC
         peak_t, peak_kind_t = load_tensor_peak()
         ach = flops / (t_launch * 1e-3) / 1e12
-        top = {"kernel": "k_tc_cgemm<64, false> (2D preconditioner transform, tcgen05 TF32)", "bound": "tensor",
+        top = {"kernel": "k_tc_cgemm<64, false, false> (2D preconditioner transform, tcgen05 TF32)", "bound": "tensor",
                "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t, "traffic": None,
                "peak_kind": peak_kind_t, "us_per_launch": 1000.0 * t_launch,
                "flops_per_launch": flops, "units": "8*P*m^3 real flop per launch (m = 127, P = 20)"}

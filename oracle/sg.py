@@ -29,7 +29,10 @@ Pins: tests/test_oracle_sg.py (size and nnz of Table 2 for r = 0..8,
 complex symmetry A^T = A and the semidefiniteness statements of Theorem 3.4,
 the theta = 0 collapse of Remark 6.1, the spectrum inclusion of Theorem 4.1,
 the condition numbers printed in Sec. 6.2 and 6.3, the inf-norm ordering of
-Sec. 6.3, SG mean against quadrature of deterministic solves).
+Sec. 6.3, SG mean against quadrature of deterministic solves);
+tests/test_oracle_galerkin_quadrature.py (every Galerkin block against the
+Gauss-Legendre mean of phi_i phi_j S(xi) built one realisation at a time,
+the Frobenius bound of Theorem 5.1 and the O(theta) rate of Theorem 5.2).
 """
 from __future__ import annotations
 

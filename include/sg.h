@@ -300,6 +300,22 @@ long long sg_kernel_launches(void);
 /* ABI version: 100 * major + minor. */
 int sg_version(void);
 
+/* Check of the device-side failure detection (not in the paper).  Launches
+ * one warp that waits, through the bounded mbarrier wait of the
+ * preconditioner's tensor-core transform kernel, for a barrier phase that
+ * nothing completes (count 1, no arrival, no copy in flight).  The wait gives
+ * up after its limit (0.5 s of %globaltimer), the kernel records that in a
+ * device flag, as the transform kernel does, and returns; the CUDA context
+ * stays usable.
+ *   stream     CUDA stream (NULL: legacy default stream); the call synchronises it.
+ *   timed_out  host int, out: 1 if the wait gave up, 0 if it completed.
+ *   seconds    host double, out (may be NULL): kernel time by CUDA events.
+ * Returns SG_ETIMEOUT when the wait gave up (the designed outcome), SG_OK if
+ * the barrier completed (a defect of the wait), SG_EINVAL for NULL timed_out,
+ * SG_ECUDA on a CUDA error or if the kernel did not reach its end.  Allocates
+ * and frees 8 bytes of device memory. */
+sg_status sg_selftest_wait_timeout(void* stream, int* timed_out, double* seconds);
+
 #ifdef __cplusplus
 }
 #endif

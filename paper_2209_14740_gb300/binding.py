@@ -27,7 +27,8 @@ X0_AS_GIVEN, X0_FALLBACK, X0_SCALED = 0, 1, 2
 EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "sg_precond", "sg_gmres",
             "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched",
             "sg_mlp_create", "sg_mlp_destroy", "sg_mlp_num_params", "sg_mlp_set_params", "sg_mlp_get_params",
-            "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn"]
+            "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
+            "sg_selftest_wait_timeout"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -120,6 +121,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_cgemm_hn.restype = i
     lib.sg_cgemm_nn.argtypes = [vp, vp, i, i, i, vp, i, vp]
     lib.sg_cgemm_nn.restype = i
+    lib.sg_selftest_wait_timeout.argtypes = [vp, C.POINTER(i), dp]
+    lib.sg_selftest_wait_timeout.restype = i
     del fp
     _lib = lib
     return lib
@@ -127,6 +130,15 @@ def load(path: str = LIB_PATH) -> C.CDLL:
 
 def kernel_launches() -> int:
     return int(load().sg_kernel_launches())
+
+
+def selftest_wait_timeout(stream=None):
+    """sg_selftest_wait_timeout: (status, timed_out, seconds)."""
+    lib = load()
+    t = C.c_int(0)
+    sec = C.c_double(0.0)
+    st = lib.sg_selftest_wait_timeout(_stream(stream), C.byref(t), C.byref(sec))
+    return st, t.value, sec.value
 
 
 class MLP:

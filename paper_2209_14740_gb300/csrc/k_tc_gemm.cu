@@ -600,6 +600,25 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
                  : "memory");
 }
 
+// Check of the bounded wait: one warp waits for phase 0 of a barrier that
+// nothing arrives on (count 1, no arrival, no copy), through the same
+// mbar_wait as the transform kernel.  The wait must give up after its limit
+// and the kernel must then report it in the device flag, as the transform
+// does, and return; *done = 1 records that the kernel ran to its end.
+__global__ void __launch_bounds__(32) k_wait_selftest(int* err, int* done) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1) : "memory");
+  __syncwarp();
+  const bool ok = tc::mbar_wait(b, 0);
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    if (!ok) atomicExch(err, 1);
+    atomicExch(done, 1);
+  }
+}
+
 // ------------------------------------------------------------------ host side
 // B layout for C = X Q with Q (kdim x ndim complex, row-major, FP64 on the
 // host) and tile width bn: nt = ceil(2 ndim / bn) column tiles, nks =
@@ -768,5 +787,12 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   note_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+cudaError_t tc_wait_selftest(int* err, int* done, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(err, done);
+  note_launch();
+  return cudaGetLastError();
+}
+
 
 }  // namespace sgi

@@ -733,4 +733,34 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
   return SG_OK;
 }
 
+sg_status sg_selftest_wait_timeout(void* stream, int* timed_out, double* seconds) {
+  g_err.clear();
+  if (!timed_out) return fail(SG_EINVAL, "NULL timed_out");
+  *timed_out = 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* d = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int hflags[2] = {0, 0};
+  float ms = 0.f;
+  cudaError_t e = cudaMalloc((void**)&d, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = tc_wait_selftest(d, d + 1, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(SG_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  if (!hflags[1]) return fail(SG_ECUDA, "wait self-test: the kernel did not reach its end");
+  *timed_out = hflags[0];
+  if (seconds) *seconds = ms * 1e-3;
+  if (hflags[0]) return fail(SG_ETIMEOUT, "a device-side wait timed out (self-test: the expected outcome)");
+  return SG_OK;
+}
+
 }  // extern "C"

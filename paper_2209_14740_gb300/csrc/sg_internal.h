@@ -91,6 +91,10 @@ int tc_tile_width(long long rows, int ndim, int num_sms);
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
                      int* err, cudaStream_t st, bool split = true, const CUtensorMap* xmap = nullptr);
+// One warp waits on an mbarrier nothing arrives on, with the transform
+// kernel's bounded wait; sets *err = 1 when the wait gives up, *done = 1 at
+// the end (device ints).
+cudaError_t tc_wait_selftest(int* err, int* done, cudaStream_t st);
 // Tensor map of X (M rows, K2 real values per row, row pitch ldx floats, 16-byte
 // aligned, ldx a multiple of 4) for the plain-TF32 transform: a 4D view
 // (4 values, 8 rows, K2/4 chunks, M/8 row groups) whose 4 x 8 x 8 x 16 box is one

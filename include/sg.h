@@ -50,7 +50,7 @@ typedef enum {
   SG_ENOTCONV = 4,      /* GMRES stopped at maxit above tol (x = best iterate) */
   SG_EBREAKDOWN = 5,    /* Arnoldi breakdown or non-finite value in the solve */
   SG_ESINGULAR = 6,     /* zero pivot in a preconditioner factorisation */
-  SG_ETIMEOUT = 7,      /* device iteration watchdog fired */
+  SG_ETIMEOUT = 7,      /* a bounded device-side wait gave up (kernel returned, context usable) */
   SG_EUNSUPPORTED = 8   /* valid input the library does not implement */
 } sg_status;
 
@@ -152,7 +152,9 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
  * (in place).  prec SG_FP64, SG_FP32 or SG_TF32 (complex64 data; 2D problems
  * with lines of at most 320 nodes only, SG_EUNSUPPORTED otherwise).
  * Returns SG_EUNSUPPORTED for 2D problems whose k_0 varies in space (no
- * separable factorisation). */
+ * separable factorisation).  Asynchronous: a bounded wait that gives up
+ * inside a tensor-core transform sets the handle's device flag, which the
+ * next sg_gmres call on the handle reports as SG_ETIMEOUT. */
 sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                      void* stream);
 
@@ -226,7 +228,9 @@ typedef struct {
  * MIXED, complex64 for FP32), device memory unless opts->host_io.  Blocks
  * the calling host thread until the solve ends.  Returns SG_OK when relres
  * <= tol, SG_ENOTCONV with the last iterate in x otherwise, SG_EBREAKDOWN on
- * non-finite values.  info may be NULL. */
+ * non-finite values, SG_ETIMEOUT if a bounded device-side wait gave up
+ * during the solve (or in an earlier sg_precond on the handle; the flag is
+ * cleared).  info may be NULL. */
 sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void* x,
                    sg_gmres_info* info, void* stream);
 

@@ -21,7 +21,8 @@
 Pins: tests/test_oracle_krylov.py (GMRES iteration counts of Sec. 6.3 for
 none / M / M_0 / A_0 at kbar = 50, agreement with the direct solution to the
 1.7e-14 printed there, convergence at theta = 0.1 and divergence at
-theta = 0.2 of the stationary iteration, Sec. 7).
+theta = 0.2 of the stationary iteration, and its slower convergence for a
+larger degree, Sec. 7).
 """
 from __future__ import annotations
 

@@ -89,3 +89,19 @@ def test_stationary_iteration_converges_and_diverges():
         out[theta] = errs
     assert out[0.1][-1] < 1e-3 * out[0.1][0]
     assert out[0.2][-1] > out[0.2][0]
+
+
+def test_stationary_iteration_slower_for_larger_degree():
+    """Sec. 7: at theta = 0.1 the stationary iteration with B = A_0 converges,
+    more slowly for a larger degree r (the SG matrix grows with r).  Wedge
+    with q = 63 (the paper uses 127; at q = 31 the iteration already diverges
+    for r >= 4): contraction rate over iterations 10..30 at r = 2 and r = 4."""
+    rates = {}
+    for r in (2, 4):
+        S = sg.assemble_problem(inputs.wedge(63, 0.1, r))
+        xd = krylov.direct(S.A, S.b)
+        pre = krylov.BlockPrecond(S.S0, S.P)
+        _, errs = krylov.stationary(S.A, pre, S.b, 30, x_ref=xd)
+        assert errs[-1] < 1e-3 * errs[0]
+        rates[r] = (errs[-1] / errs[10]) ** (1.0 / 20)
+    assert rates[2] < rates[4] < 1.0, rates

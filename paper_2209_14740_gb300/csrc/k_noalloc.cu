@@ -55,29 +55,31 @@ sg_status scratch_address(void** out) {
 
 extern "C" sg_status sg_precond_noalloc(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                                         void* stream) {
-  if (!h || !R || !Z) return sgi::fail(SG_EINVAL, "NULL handle or vector");
-  if (prec != SG_FP64 && prec != SG_FP32) return sgi::fail(SG_EINVAL, "precision must be SG_FP64 or SG_FP32");
-  if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN)
-    return sgi::fail(SG_EINVAL, "sg_precond_noalloc: kind must be SG_PREC_MEAN or SG_PREC_CSL_MEAN");
-  if (h->N > (long long)SG_NOALLOC_MAX_N)
-    return sgi::fail(SG_EINVAL, "sg_precond_noalloc: N = " + std::to_string(h->N) +
-                                    " exceeds the static scratch limit SG_NOALLOC_MAX_N = " +
-                                    std::to_string((long long)SG_NOALLOC_MAX_N));
-  const int which = kind == SG_PREC_MEAN ? 0 : 1;
-  if (!h->blk[which].ready)
-    return sgi::fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
-  void* base = nullptr;
-  sg_status s = scratch_address(&base);
-  if (s != SG_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  double2* s0 = reinterpret_cast<double2*>(base);
-  double2* s1 = s0 + (size_t)SG_NOALLOC_MAX_N;
-  cudaError_t e;
-  if (prec == SG_FP64)
-    e = sgi::launch_precond_scratch<double>(h, which, (const double2*)R, (double2*)Z, st, s0, s1);
-  else
-    e = sgi::launch_precond_scratch<float>(h, which, (const float2*)R, (float2*)Z, st,
-                                           reinterpret_cast<float2*>(s0), reinterpret_cast<float2*>(s1));
-  if (e != cudaSuccess) return sgi::fail(SG_ECUDA, std::string("sg_precond_noalloc: ") + cudaGetErrorString(e));
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !R || !Z) return sgi::fail(SG_EINVAL, "NULL handle or vector");
+    if (prec != SG_FP64 && prec != SG_FP32) return sgi::fail(SG_EINVAL, "precision must be SG_FP64 or SG_FP32");
+    if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN)
+      return sgi::fail(SG_EINVAL, "sg_precond_noalloc: kind must be SG_PREC_MEAN or SG_PREC_CSL_MEAN");
+    if (h->N > (long long)SG_NOALLOC_MAX_N)
+      return sgi::fail(SG_EINVAL, "sg_precond_noalloc: N = " + std::to_string(h->N) +
+                                      " exceeds the static scratch limit SG_NOALLOC_MAX_N = " +
+                                      std::to_string((long long)SG_NOALLOC_MAX_N));
+    const int which = kind == SG_PREC_MEAN ? 0 : 1;
+    if (!h->blk[which].ready)
+      return sgi::fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
+    void* base = nullptr;
+    sg_status s = scratch_address(&base);
+    if (s != SG_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double2* s0 = reinterpret_cast<double2*>(base);
+    double2* s1 = s0 + (size_t)SG_NOALLOC_MAX_N;
+    cudaError_t e;
+    if (prec == SG_FP64)
+      e = sgi::launch_precond_scratch<double>(h, which, (const double2*)R, (double2*)Z, st, s0, s1);
+    else
+      e = sgi::launch_precond_scratch<float>(h, which, (const float2*)R, (float2*)Z, st,
+                                             reinterpret_cast<float2*>(s0), reinterpret_cast<float2*>(s1));
+    if (e != cudaSuccess) return sgi::fail(SG_ECUDA, std::string("sg_precond_noalloc: ") + cudaGetErrorString(e));
+    return SG_OK;
+  });
 }

@@ -135,39 +135,43 @@ extern "C" {
 
 sg_status sg_cgemm_hn(const void* A, long long lda, const void* B, long long ldb, int m, int n, long long k, void* C,
                       void* workspace, void* stream) {
-  if (!A || !B || !C || !workspace || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < k)
-    return fail(SG_EINVAL, "bad sg_cgemm_hn arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  double2* acc = reinterpret_cast<double2*>(workspace);
-  SG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)m * n * sizeof(double2), st));
-  const long long tiles = (long long)((m + 31) / 32) * ((n + 31) / 32);
-  // slices of at most 1024 terms keep the FP32 partial sums short; more
-  // slices than that only when the tiles alone would leave SMs idle
-  const long long by_len = (k + 1023) / 1024;
-  const long long by_occ = std::min((k + 15) / 16, (4LL * 152 + tiles - 1) / tiles);
-  const int slices = (int)std::min(65535LL, std::max(by_len, by_occ));
-  dim3 grid((n + 31) / 32, (m + 31) / 32, slices);
-  k_cgemm_hn<<<grid, 256, 0, st>>>(m, n, k, (const float2*)A, lda, (const float2*)B, ldb, acc);
-  note_launch();
-  SG_CUDA_TRY(cudaGetLastError());
-  const long long cnt = (long long)m * n;
-  k_c128_to_c64<<<(int)std::min((cnt + 255) / 256, 4096LL), 256, 0, st>>>(acc, (float2*)C, cnt);
-  note_launch();
-  SG_CUDA_TRY(cudaGetLastError());
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!A || !B || !C || !workspace || m <= 0 || n <= 0 || k <= 0 || lda < k || ldb < k)
+      return fail(SG_EINVAL, "bad sg_cgemm_hn arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    double2* acc = reinterpret_cast<double2*>(workspace);
+    SG_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)m * n * sizeof(double2), st));
+    const long long tiles = (long long)((m + 31) / 32) * ((n + 31) / 32);
+    // slices of at most 1024 terms keep the FP32 partial sums short; more
+    // slices than that only when the tiles alone would leave SMs idle
+    const long long by_len = (k + 1023) / 1024;
+    const long long by_occ = std::min((k + 15) / 16, (4LL * 152 + tiles - 1) / tiles);
+    const int slices = (int)std::min(65535LL, std::max(by_len, by_occ));
+    dim3 grid((n + 31) / 32, (m + 31) / 32, slices);
+    k_cgemm_hn<<<grid, 256, 0, st>>>(m, n, k, (const float2*)A, lda, (const float2*)B, ldb, acc);
+    note_launch();
+    SG_CUDA_TRY(cudaGetLastError());
+    const long long cnt = (long long)m * n;
+    k_c128_to_c64<<<(int)std::min((cnt + 255) / 256, 4096LL), 256, 0, st>>>(acc, (float2*)C, cnt);
+    note_launch();
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+  });
 }
 
 sg_status sg_cgemm_nn(const void* A, const void* B, int m, int n, int k, void* C, int out_c128, void* stream) {
-  if (!A || !B || !C || m <= 0 || n <= 0 || k <= 0) return fail(SG_EINVAL, "bad sg_cgemm_nn arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  dim3 grid((n + 63) / 64, (m + 31) / 32);
-  if (out_c128)
-    k_cgemm_nn<double2><<<grid, 256, 0, st>>>(m, n, k, (const float2*)A, (const float2*)B, (double2*)C);
-  else
-    k_cgemm_nn<float2><<<grid, 256, 0, st>>>(m, n, k, (const float2*)A, (const float2*)B, (float2*)C);
-  note_launch();
-  SG_CUDA_TRY(cudaGetLastError());
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!A || !B || !C || m <= 0 || n <= 0 || k <= 0) return fail(SG_EINVAL, "bad sg_cgemm_nn arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((n + 63) / 64, (m + 31) / 32);
+    if (out_c128)
+      k_cgemm_nn<double2><<<grid, 256, 0, st>>>(m, n, k, (const float2*)A, (const float2*)B, (double2*)C);
+    else
+      k_cgemm_nn<float2><<<grid, 256, 0, st>>>(m, n, k, (const float2*)A, (const float2*)B, (float2*)C);
+    note_launch();
+    SG_CUDA_TRY(cudaGetLastError());
+    return SG_OK;
+  });
 }
 
 }  // extern "C"

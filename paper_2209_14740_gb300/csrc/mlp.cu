@@ -238,42 +238,44 @@ using namespace sgi;
 extern "C" {
 
 sg_status sg_mlp_create(int in_dim, int width, int hidden, int out_dim, sg_mlp** out) {
-  if (!out || in_dim <= 0 || width <= 0 || hidden < 0 || out_dim <= 0 || width > 1 << 14)
-    return fail(SG_EINVAL, "bad MLP shape");
-  auto* m = new sg_mlp();
-  m->in = in_dim;
-  m->width = width;
-  m->hidden = hidden;
-  m->out = out_dim;
-  m->layers = hidden + 1;
-  m->dims.push_back(in_dim);
-  for (int l = 0; l < hidden; ++l) m->dims.push_back(width);
-  m->dims.push_back(out_dim);
-  long long off = 0;
-  for (int l = 0; l < m->layers; ++l) {
-    m->woff.push_back(off);
-    off += (long long)m->dims[l + 1] * m->dims[l];
-    m->boff.push_back(off);
-    off += m->dims[l + 1];
-  }
-  m->nparams = off;
-  cudaError_t e = cudaSuccess;
-  if (!e) e = cudaMalloc((void**)&m->p, off * sizeof(float));
-  if (!e) e = cudaMalloc((void**)&m->g, off * sizeof(float));
-  if (!e) e = cudaMalloc((void**)&m->m1, off * sizeof(float));
-  if (!e) e = cudaMalloc((void**)&m->m2, off * sizeof(float));
-  if (!e) e = cudaMalloc((void**)&m->wb, off * sizeof(__nv_bfloat16));
-  if (!e) e = cudaMalloc((void**)&m->loss, sizeof(double));
-  if (!e) e = cudaMemset(m->p, 0, off * sizeof(float));
-  if (!e) e = cudaMemset(m->m1, 0, off * sizeof(float));
-  if (!e) e = cudaMemset(m->m2, 0, off * sizeof(float));
-  if (!e) e = cudaMemset(m->wb, 0, off * sizeof(__nv_bfloat16));
-  if (e) {
-    sg_mlp_destroy(m);
-    return fail(SG_ENOMEM, std::string("MLP allocation: ") + cudaGetErrorString(e));
-  }
-  *out = m;
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!out || in_dim <= 0 || width <= 0 || hidden < 0 || out_dim <= 0 || width > 1 << 14)
+      return fail(SG_EINVAL, "bad MLP shape");
+    auto* m = new sg_mlp();
+    m->in = in_dim;
+    m->width = width;
+    m->hidden = hidden;
+    m->out = out_dim;
+    m->layers = hidden + 1;
+    m->dims.push_back(in_dim);
+    for (int l = 0; l < hidden; ++l) m->dims.push_back(width);
+    m->dims.push_back(out_dim);
+    long long off = 0;
+    for (int l = 0; l < m->layers; ++l) {
+      m->woff.push_back(off);
+      off += (long long)m->dims[l + 1] * m->dims[l];
+      m->boff.push_back(off);
+      off += m->dims[l + 1];
+    }
+    m->nparams = off;
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMalloc((void**)&m->p, off * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&m->g, off * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&m->m1, off * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&m->m2, off * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&m->wb, off * sizeof(__nv_bfloat16));
+    if (!e) e = cudaMalloc((void**)&m->loss, sizeof(double));
+    if (!e) e = cudaMemset(m->p, 0, off * sizeof(float));
+    if (!e) e = cudaMemset(m->m1, 0, off * sizeof(float));
+    if (!e) e = cudaMemset(m->m2, 0, off * sizeof(float));
+    if (!e) e = cudaMemset(m->wb, 0, off * sizeof(__nv_bfloat16));
+    if (e) {
+      sg_mlp_destroy(m);
+      return fail(SG_ENOMEM, std::string("MLP allocation: ") + cudaGetErrorString(e));
+    }
+    *out = m;
+    return SG_OK;
+  });
 }
 
 void sg_mlp_destroy(sg_mlp* m) {
@@ -288,77 +290,87 @@ void sg_mlp_destroy(sg_mlp* m) {
 long long sg_mlp_num_params(const sg_mlp* m) { return m ? m->nparams : -1; }
 
 sg_status sg_mlp_set_params(sg_mlp* m, const float* src, void* stream) {
-  if (!m || !src) return fail(SG_EINVAL, "NULL argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  SG_CUDA_TRY(cudaMemcpyAsync(m->p, src, m->nparams * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  SG_CUDA_TRY(cudaMemsetAsync(m->m1, 0, m->nparams * sizeof(float), st));
-  SG_CUDA_TRY(cudaMemsetAsync(m->m2, 0, m->nparams * sizeof(float), st));
-  k_to_bf16<<<grid_for(m->nparams), 256, 0, st>>>(m->p, m->wb, m->nparams);
-  note_launch();
-  SG_CUDA_TRY(cudaGetLastError());
-  m->step = 0;
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!m || !src) return fail(SG_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    SG_CUDA_TRY(cudaMemcpyAsync(m->p, src, m->nparams * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    SG_CUDA_TRY(cudaMemsetAsync(m->m1, 0, m->nparams * sizeof(float), st));
+    SG_CUDA_TRY(cudaMemsetAsync(m->m2, 0, m->nparams * sizeof(float), st));
+    k_to_bf16<<<grid_for(m->nparams), 256, 0, st>>>(m->p, m->wb, m->nparams);
+    note_launch();
+    SG_CUDA_TRY(cudaGetLastError());
+    m->step = 0;
+    return SG_OK;
+  });
 }
 
 sg_status sg_mlp_get_params(const sg_mlp* m, float* dst, void* stream) {
-  if (!m || !dst) return fail(SG_EINVAL, "NULL argument");
-  SG_CUDA_TRY(cudaMemcpyAsync(dst, m->p, m->nparams * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!m || !dst) return fail(SG_EINVAL, "NULL argument");
+    SG_CUDA_TRY(cudaMemcpyAsync(dst, m->p, m->nparams * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SG_OK;
+  });
 }
 
 sg_status sg_mlp_forward(sg_mlp* m, const float* X, int batch, float* Y, void* stream) {
-  if (!m || !X || !Y || batch <= 0) return fail(SG_EINVAL, "bad sg_mlp_forward arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  SG_CUDA_TRY(ensure_batch(m, batch));
-  SG_CUDA_TRY(forward(m, X, batch, st));
-  SG_CUDA_TRY(cudaMemcpyAsync(Y, m->act[m->layers], (size_t)batch * m->out * sizeof(float), cudaMemcpyDeviceToDevice,
-                              st));
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!m || !X || !Y || batch <= 0) return fail(SG_EINVAL, "bad sg_mlp_forward arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    SG_CUDA_TRY(ensure_batch(m, batch));
+    SG_CUDA_TRY(forward(m, X, batch, st));
+    SG_CUDA_TRY(cudaMemcpyAsync(Y, m->act[m->layers], (size_t)batch * m->out * sizeof(float), cudaMemcpyDeviceToDevice,
+                                st));
+    return SG_OK;
+  });
 }
 
 sg_status sg_mlp_loss_grad(sg_mlp* m, const float* X, const float* T, int batch, double* loss, float* grad,
                            void* stream) {
-  if (!m || !X || !T || batch <= 0) return fail(SG_EINVAL, "bad sg_mlp_loss_grad arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  SG_CUDA_TRY(ensure_batch(m, batch));
-  SG_CUDA_TRY(loss_and_grad(m, X, T, batch, st));
-  if (grad) SG_CUDA_TRY(cudaMemcpyAsync(grad, m->g, m->nparams * sizeof(float), cudaMemcpyDeviceToDevice, st));
-  if (loss) {
-    SG_CUDA_TRY(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(cudaStreamSynchronize(st));
-  }
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!m || !X || !T || batch <= 0) return fail(SG_EINVAL, "bad sg_mlp_loss_grad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    SG_CUDA_TRY(ensure_batch(m, batch));
+    SG_CUDA_TRY(loss_and_grad(m, X, T, batch, st));
+    if (grad) SG_CUDA_TRY(cudaMemcpyAsync(grad, m->g, m->nparams * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (loss) {
+      SG_CUDA_TRY(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return SG_OK;
+  });
 }
 
 sg_status sg_mlp_train(sg_mlp* m, const float* X, const float* T, int nsamples, int batch, int epochs, float lr,
                        double* loss_history, void* stream) {
-  if (!m || !X || !T || nsamples <= 0 || batch <= 0 || epochs < 0 || !(lr > 0))
-    return fail(SG_EINVAL, "bad sg_mlp_train arguments");
-  cudaStream_t st = (cudaStream_t)stream;
-  batch = std::min(batch, nsamples);
-  SG_CUDA_TRY(ensure_batch(m, batch));
-  for (int ep = 0; ep < epochs; ++ep) {
-    // the epoch's mini-batch losses accumulate on the device: one read per epoch
-    SG_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
-    int nb = 0;
-    for (int s0 = 0; s0 + batch <= nsamples; s0 += batch, ++nb) {
-      SG_CUDA_TRY(loss_and_grad(m, X + (size_t)s0 * m->in, T + (size_t)s0 * m->out, batch, st, false));
-      ++m->step;
-      const float c1 = 1.0f / (1.0f - powf(0.9f, (float)m->step));
-      const float c2 = 1.0f / (1.0f - powf(0.999f, (float)m->step));
-      k_adam<<<grid_for(m->nparams), 256, 0, st>>>(m->p, m->g, m->m1, m->m2, m->wb, m->nparams, lr, c1, c2);
-      note_launch();
-      SG_CUDA_TRY(cudaGetLastError());
+  return sgi::guarded([&]() -> sg_status {
+    if (!m || !X || !T || nsamples <= 0 || batch <= 0 || epochs < 0 || !(lr > 0))
+      return fail(SG_EINVAL, "bad sg_mlp_train arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    batch = std::min(batch, nsamples);
+    SG_CUDA_TRY(ensure_batch(m, batch));
+    for (int ep = 0; ep < epochs; ++ep) {
+      // the epoch's mini-batch losses accumulate on the device: one read per epoch
+      SG_CUDA_TRY(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
+      int nb = 0;
+      for (int s0 = 0; s0 + batch <= nsamples; s0 += batch, ++nb) {
+        SG_CUDA_TRY(loss_and_grad(m, X + (size_t)s0 * m->in, T + (size_t)s0 * m->out, batch, st, false));
+        ++m->step;
+        const float c1 = 1.0f / (1.0f - powf(0.9f, (float)m->step));
+        const float c2 = 1.0f / (1.0f - powf(0.999f, (float)m->step));
+        k_adam<<<grid_for(m->nparams), 256, 0, st>>>(m->p, m->g, m->m1, m->m2, m->wb, m->nparams, lr, c1, c2);
+        note_launch();
+        SG_CUDA_TRY(cudaGetLastError());
+      }
+      if (loss_history) {
+        double l = 0;
+        SG_CUDA_TRY(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+        loss_history[ep] = nb ? l / nb : 0.0;
+      }
     }
-    if (loss_history) {
-      double l = 0;
-      SG_CUDA_TRY(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
-      SG_CUDA_TRY(cudaStreamSynchronize(st));
-      loss_history[ep] = nb ? l / nb : 0.0;
-    }
-  }
-  SG_CUDA_TRY(cudaStreamSynchronize(st));
-  return SG_OK;
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SG_OK;
+  });
 }
 
 }  // extern "C"

@@ -554,213 +554,225 @@ int sg_version(void) { return 100; }
 long long sg_kernel_launches(void) { return sgi::g_launches.load(); }
 
 sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
-  g_err.clear();
-  if (!desc || !out) return fail(SG_EINVAL, "NULL desc or out");
-  const sg_desc& D = *desc;
-  if (D.dim != 1 && D.dim != 2) return fail(SG_EINVAL, "dim must be 1 or 2");
-  if (D.nx < 3 || (D.dim == 2 && D.ny < 3) || (D.dim == 1 && D.ny != 1))
-    return fail(SG_EINVAL, "grid too small (nx, ny >= 3; ny = 1 in 1D)");
-  if (!(D.h > 0) || !std::isfinite(D.h)) return fail(SG_EINVAL, "h must be positive");
-  if (D.s < 0 || D.s > 16 || D.r < 0 || D.r > 12) return fail(SG_EINVAL, "s in [0,16], r in [0,12]");
-  for (int i = 0; i < (D.dim == 2 ? 4 : 2); ++i)
-    if (D.bc[i] != SG_BC_DIRICHLET && D.bc[i] != SG_BC_ABSORBING) return fail(SG_EINVAL, "bad bc");
-  if (D.dim == 2 && !(D.bc[0] == D.bc[1] && D.bc[1] == D.bc[2] && D.bc[2] == D.bc[3]))
-    return fail(SG_EINVAL, "2D needs all-Dirichlet or all-absorbing boundaries (Theorems A.5/A.6)");
-  if (!D.k0 || (D.s > 0 && !D.kl)) return fail(SG_EINVAL, "NULL wavenumber field");
-  if (!std::isfinite(D.beta)) return fail(SG_EINVAL, "beta not finite");
+  return sgi::guarded([&]() -> sg_status {
+    g_err.clear();
+    if (!desc || !out) return fail(SG_EINVAL, "NULL desc or out");
+    const sg_desc& D = *desc;
+    if (D.dim != 1 && D.dim != 2) return fail(SG_EINVAL, "dim must be 1 or 2");
+    if (D.nx < 3 || (D.dim == 2 && D.ny < 3) || (D.dim == 1 && D.ny != 1))
+      return fail(SG_EINVAL, "grid too small (nx, ny >= 3; ny = 1 in 1D)");
+    if (!(D.h > 0) || !std::isfinite(D.h)) return fail(SG_EINVAL, "h must be positive");
+    if (D.s < 0 || D.s > 16 || D.r < 0 || D.r > 12) return fail(SG_EINVAL, "s in [0,16], r in [0,12]");
+    for (int i = 0; i < (D.dim == 2 ? 4 : 2); ++i)
+      if (D.bc[i] != SG_BC_DIRICHLET && D.bc[i] != SG_BC_ABSORBING) return fail(SG_EINVAL, "bad bc");
+    if (D.dim == 2 && !(D.bc[0] == D.bc[1] && D.bc[1] == D.bc[2] && D.bc[2] == D.bc[3]))
+      return fail(SG_EINVAL, "2D needs all-Dirichlet or all-absorbing boundaries (Theorems A.5/A.6)");
+    if (!D.k0 || (D.s > 0 && !D.kl)) return fail(SG_EINVAL, "NULL wavenumber field");
+    if (!std::isfinite(D.beta)) return fail(SG_EINVAL, "beta not finite");
 
-  auto* h = new sg_handle();
-  h->dim = D.dim; h->nx = D.nx; h->ny = D.dim == 2 ? D.ny : 1; h->h = D.h; h->beta = D.beta;
-  for (int i = 0; i < 4; ++i) h->bc[i] = (D.dim == 1 && i >= 2) ? SG_BC_DIRICHLET : D.bc[i];
-  h->s = D.s; h->r = D.r;
-  h->offx = h->bc[0] == SG_BC_DIRICHLET ? 1 : 0;
-  h->mx = D.nx - h->offx - (h->bc[1] == SG_BC_DIRICHLET ? 1 : 0);
-  if (D.dim == 2) {
-    h->offy = h->bc[2] == SG_BC_DIRICHLET ? 1 : 0;
-    h->my = D.ny - h->offy - (h->bc[3] == SG_BC_DIRICHLET ? 1 : 0);
-  }
-  h->n = h->mx * h->my;
-  h->P = D.s == 0 ? 1 : binom(D.s + D.r, D.s);
-  h->N = (long long)h->n * h->P;
-  h->T_terms = 2 * D.s + D.s * (D.s - 1) / 2;
-  if (h->P > 4096) { delete h; return fail(SG_EINVAL, "too many chaos modes"); }
-
-  // node fields restricted to the unknowns, validation k > 0 (Sec. 3.2)
-  const int n = h->n, s = h->s, P = h->P;
-  const size_t nodes = (size_t)D.nx * h->ny;
-  std::vector<double> fields((size_t)(s + 1) * n);
-  h->b0.assign(n, 0.0);
-  double kmin = 1e300, kmax = -1e300, k0min = 1e300, k0max = -1e300;
-  for (int ju = 0; ju < h->my; ++ju)
-    for (int iu = 0; iu < h->mx; ++iu) {
-      size_t node = (size_t)(iu + h->offx) + (size_t)D.nx * (ju + h->offy);
-      int u = iu + h->mx * ju;
-      double k0 = D.k0[node], spread = 0;
-      fields[u] = k0;
-      for (int l = 0; l < s; ++l) {
-        double kl = D.kl[(size_t)l * nodes + node];
-        fields[(size_t)(l + 1) * n + u] = kl;
-        spread += std::fabs(kl);
-        if (!std::isfinite(kl)) { delete h; return fail(SG_EINVAL, "non-finite k_l"); }
-      }
-      if (!std::isfinite(k0)) { delete h; return fail(SG_EINVAL, "non-finite k_0"); }
-      kmin = std::min(kmin, k0 - spread);
-      kmax = std::max(kmax, k0 + spread);
-      k0min = std::min(k0min, k0);
-      k0max = std::max(k0max, k0);
-      double f = D.f ? D.f[node] : 0.0;
-      if (!std::isfinite(f)) { delete h; return fail(SG_EINVAL, "non-finite f"); }
-      bool xabs = (iu == 0 && h->bc[0] == SG_BC_ABSORBING) || (iu == h->mx - 1 && h->bc[1] == SG_BC_ABSORBING);
-      bool yabs = D.dim == 2 && ((ju == 0 && h->bc[2] == SG_BC_ABSORBING) ||
-                                 (ju == h->my - 1 && h->bc[3] == SG_BC_ABSORBING));
-      h->b0[u] = (xabs ? 0.5 : 1.0) * (yabs ? 0.5 : 1.0) * f;
+    auto* h = new sg_handle();
+    h->dim = D.dim; h->nx = D.nx; h->ny = D.dim == 2 ? D.ny : 1; h->h = D.h; h->beta = D.beta;
+    for (int i = 0; i < 4; ++i) h->bc[i] = (D.dim == 1 && i >= 2) ? SG_BC_DIRICHLET : D.bc[i];
+    h->s = D.s; h->r = D.r;
+    h->offx = h->bc[0] == SG_BC_DIRICHLET ? 1 : 0;
+    h->mx = D.nx - h->offx - (h->bc[1] == SG_BC_DIRICHLET ? 1 : 0);
+    if (D.dim == 2) {
+      h->offy = h->bc[2] == SG_BC_DIRICHLET ? 1 : 0;
+      h->my = D.ny - h->offy - (h->bc[3] == SG_BC_DIRICHLET ? 1 : 0);
     }
-  if (!(kmin > 0)) { delete h; return fail(SG_EINVAL, "k(x, xi) must be positive for all xi (k_0 - sum|k_l| <= 0)"); }
-  h->kbar = 0.5 * (k0min + k0max);
-  h->specialised = matvec_is_specialised(h->s, h->r) ? 1 : 0;
-  h->separable = (k0max - k0min) <= 1e-13 * k0max;
-  h->k0u.assign(fields.begin(), fields.begin() + n);
+    h->n = h->mx * h->my;
+    h->P = D.s == 0 ? 1 : binom(D.s + D.r, D.s);
+    h->N = (long long)h->n * h->P;
+    h->T_terms = 2 * D.s + D.s * (D.s - 1) / 2;
+    if (h->P > 4096) { delete h; return fail(SG_EINVAL, "too many chaos modes"); }
 
-  // chaos tables
-  h->alpha = multi_indices(s, h->r);
-  if (s == 0) h->alpha.clear();
-  h->rowptr.assign(P + 1, 0);
-  for (int a = 0; a < P; ++a) {
-    for (int b = 0; b < P; ++b) {
-      if (a == b) continue;
-      int t;
-      double g;
-      if (coupling(s, &h->alpha[(size_t)a * s], &h->alpha[(size_t)b * s], &t, &g)) {
-        h->col.push_back(b);
-        h->term.push_back(t);
-        h->gval.push_back(g);
+    // node fields restricted to the unknowns, validation k > 0 (Sec. 3.2)
+    const int n = h->n, s = h->s, P = h->P;
+    const size_t nodes = (size_t)D.nx * h->ny;
+    std::vector<double> fields((size_t)(s + 1) * n);
+    h->b0.assign(n, 0.0);
+    double kmin = 1e300, kmax = -1e300, k0min = 1e300, k0max = -1e300;
+    for (int ju = 0; ju < h->my; ++ju)
+      for (int iu = 0; iu < h->mx; ++iu) {
+        size_t node = (size_t)(iu + h->offx) + (size_t)D.nx * (ju + h->offy);
+        int u = iu + h->mx * ju;
+        double k0 = D.k0[node], spread = 0;
+        fields[u] = k0;
+        for (int l = 0; l < s; ++l) {
+          double kl = D.kl[(size_t)l * nodes + node];
+          fields[(size_t)(l + 1) * n + u] = kl;
+          spread += std::fabs(kl);
+          if (!std::isfinite(kl)) { delete h; return fail(SG_EINVAL, "non-finite k_l"); }
+        }
+        if (!std::isfinite(k0)) { delete h; return fail(SG_EINVAL, "non-finite k_0"); }
+        kmin = std::min(kmin, k0 - spread);
+        kmax = std::max(kmax, k0 + spread);
+        k0min = std::min(k0min, k0);
+        k0max = std::max(k0max, k0);
+        double f = D.f ? D.f[node] : 0.0;
+        if (!std::isfinite(f)) { delete h; return fail(SG_EINVAL, "non-finite f"); }
+        bool xabs = (iu == 0 && h->bc[0] == SG_BC_ABSORBING) || (iu == h->mx - 1 && h->bc[1] == SG_BC_ABSORBING);
+        bool yabs = D.dim == 2 && ((ju == 0 && h->bc[2] == SG_BC_ABSORBING) ||
+                                   (ju == h->my - 1 && h->bc[3] == SG_BC_ABSORBING));
+        h->b0[u] = (xabs ? 0.5 : 1.0) * (yabs ? 0.5 : 1.0) * f;
       }
-    }
-    h->rowptr[a + 1] = (int)h->col.size();
-  }
-  h->gdiag.assign((size_t)std::max(s, 1) * P, 0.0);
-  for (int l = 0; l < s; ++l)
+    if (!(kmin > 0)) { delete h; return fail(SG_EINVAL, "k(x, xi) must be positive for all xi (k_0 - sum|k_l| <= 0)"); }
+    h->kbar = 0.5 * (k0min + k0max);
+    h->specialised = matvec_is_specialised(h->s, h->r) ? 1 : 0;
+    h->separable = (k0max - k0min) <= 1e-13 * k0max;
+    h->k0u.assign(fields.begin(), fields.begin() + n);
+
+    // chaos tables
+    h->alpha = multi_indices(s, h->r);
+    if (s == 0) h->alpha.clear();
+    h->rowptr.assign(P + 1, 0);
     for (int a = 0; a < P; ++a) {
-      int al = h->alpha[(size_t)a * s + l];
-      h->gdiag[(size_t)l * P + a] = leg_b(al) * leg_b(al) + leg_b(al + 1) * leg_b(al + 1);
+      for (int b = 0; b < P; ++b) {
+        if (a == b) continue;
+        int t;
+        double g;
+        if (coupling(s, &h->alpha[(size_t)a * s], &h->alpha[(size_t)b * s], &t, &g)) {
+          h->col.push_back(b);
+          h->term.push_back(t);
+          h->gval.push_back(g);
+        }
+      }
+      h->rowptr[a + 1] = (int)h->col.size();
     }
+    h->gdiag.assign((size_t)std::max(s, 1) * P, 0.0);
+    for (int l = 0; l < s; ++l)
+      for (int a = 0; a < P; ++a) {
+        int al = h->alpha[(size_t)a * s + l];
+        h->gdiag[(size_t)l * P + a] = leg_b(al) * leg_b(al) + leg_b(al + 1) * leg_b(al + 1);
+      }
 
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaGetDevice(&h->device);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  if (e != cudaSuccess) { delete h; return fail(SG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)); }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { delete h; return fail(SG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)); }
 
-  std::vector<float> gval32(h->gval.begin(), h->gval.end()), gdiag32(h->gdiag.begin(), h->gdiag.end()),
-      fields32(fields.begin(), fields.end());
-  if (upload(&h->d_rowptr, h->rowptr.data(), h->rowptr.size()) ||
-      upload(&h->d_col, h->col.data(), h->col.size()) || upload(&h->d_term, h->term.data(), h->term.size()) ||
-      upload(&h->d_gval, h->gval.data(), h->gval.size()) || upload(&h->d_gdiag, h->gdiag.data(), h->gdiag.size()) ||
-      upload(&h->d_fields, fields.data(), fields.size()) || upload(&h->d_b0, h->b0.data(), h->b0.size()) ||
-      upload(&h->d_gval32, gval32.data(), gval32.size()) ||
-      upload(&h->d_gdiag32, gdiag32.data(), gdiag32.size()) ||
-      upload(&h->d_fields32, fields32.data(), fields32.size())) {
-    destroy_impl(h);
-    return fail(SG_ENOMEM, "device allocation for fields/tables failed");
-  }
-  sg_status ps = setup_preconditioners(h, st);
-  if (ps != SG_OK && ps != SG_ESINGULAR) {
-    destroy_impl(h);
-    return ps;
-  }
-  if (ps == SG_ESINGULAR) {
-    destroy_impl(h);
-    return ps;
-  }
-  *out = h;
-  return SG_OK;
+    std::vector<float> gval32(h->gval.begin(), h->gval.end()), gdiag32(h->gdiag.begin(), h->gdiag.end()),
+        fields32(fields.begin(), fields.end());
+    if (upload(&h->d_rowptr, h->rowptr.data(), h->rowptr.size()) ||
+        upload(&h->d_col, h->col.data(), h->col.size()) || upload(&h->d_term, h->term.data(), h->term.size()) ||
+        upload(&h->d_gval, h->gval.data(), h->gval.size()) || upload(&h->d_gdiag, h->gdiag.data(), h->gdiag.size()) ||
+        upload(&h->d_fields, fields.data(), fields.size()) || upload(&h->d_b0, h->b0.data(), h->b0.size()) ||
+        upload(&h->d_gval32, gval32.data(), gval32.size()) ||
+        upload(&h->d_gdiag32, gdiag32.data(), gdiag32.size()) ||
+        upload(&h->d_fields32, fields32.data(), fields32.size())) {
+      destroy_impl(h);
+      return fail(SG_ENOMEM, "device allocation for fields/tables failed");
+    }
+    sg_status ps = setup_preconditioners(h, st);
+    if (ps != SG_OK && ps != SG_ESINGULAR) {
+      destroy_impl(h);
+      return ps;
+    }
+    if (ps == SG_ESINGULAR) {
+      destroy_impl(h);
+      return ps;
+    }
+    *out = h;
+    return SG_OK;
+  });
 }
 
 void sg_destroy(sg_handle* h) { destroy_impl(h); }
 
 sg_status sg_get_info(const sg_handle* h, sg_info* info) {
-  if (!h || !info) return fail(SG_EINVAL, "NULL handle or info");
-  info->dim = h->dim; info->mx = h->mx; info->my = h->my; info->n = h->n; info->P = h->P;
-  info->N = h->N; info->s = h->s; info->r = h->r; info->terms = h->T_terms;
-  info->coupling_nnz = (int)h->col.size() + h->P;
-  info->separable = h->separable ? 1 : 0;
-  info->specialised = h->specialised;
-  info->fast_diag = h->fd ? 1 : 0;
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !info) return fail(SG_EINVAL, "NULL handle or info");
+    info->dim = h->dim; info->mx = h->mx; info->my = h->my; info->n = h->n; info->P = h->P;
+    info->N = h->N; info->s = h->s; info->r = h->r; info->terms = h->T_terms;
+    info->coupling_nnz = (int)h->col.size() + h->P;
+    info->separable = h->separable ? 1 : 0;
+    info->specialised = h->specialised;
+    info->fast_diag = h->fd ? 1 : 0;
+    return SG_OK;
+  });
 }
 
 sg_status sg_rhs(sg_handle* h, sg_precision prec, void* b, void* stream) {
-  if (!h || !b) return fail(SG_EINVAL, "NULL handle or b");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (prec == SG_FP64) SG_CUDA_TRY(launch_rhs<double>(h, (double2*)b, st));
-  else if (prec == SG_FP32) SG_CUDA_TRY(launch_rhs<float>(h, (float2*)b, st));
-  else return fail(SG_EINVAL, "sg_rhs precision must be SG_FP64 or SG_FP32");
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !b) return fail(SG_EINVAL, "NULL handle or b");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == SG_FP64) SG_CUDA_TRY(launch_rhs<double>(h, (double2*)b, st));
+    else if (prec == SG_FP32) SG_CUDA_TRY(launch_rhs<float>(h, (float2*)b, st));
+    else return fail(SG_EINVAL, "sg_rhs precision must be SG_FP64 or SG_FP32");
+    return SG_OK;
+  });
 }
 
 sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, void* stream) {
-  if (!h || !X || !Y) return fail(SG_EINVAL, "NULL handle or vector");
-  if (X == Y) return fail(SG_EINVAL, "sg_matvec: X and Y must not overlap");
-  cudaStream_t st = (cudaStream_t)stream;
-  if (prec == SG_FP64) SG_CUDA_TRY(launch_matvec<double>(h, (const double2*)X, (double2*)Y, st));
-  else if (prec == SG_FP32) SG_CUDA_TRY(launch_matvec<float>(h, (const float2*)X, (float2*)Y, st));
-  else return fail(SG_EINVAL, "sg_matvec precision must be SG_FP64 or SG_FP32");
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !X || !Y) return fail(SG_EINVAL, "NULL handle or vector");
+    if (X == Y) return fail(SG_EINVAL, "sg_matvec: X and Y must not overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == SG_FP64) SG_CUDA_TRY(launch_matvec<double>(h, (const double2*)X, (double2*)Y, st));
+    else if (prec == SG_FP32) SG_CUDA_TRY(launch_matvec<float>(h, (const float2*)X, (float2*)Y, st));
+    else return fail(SG_EINVAL, "sg_matvec precision must be SG_FP64 or SG_FP32");
+    return SG_OK;
+  });
 }
 
 sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z, void* stream) {
-  if (!h || !R || !Z) return fail(SG_EINVAL, "NULL handle or vector");
-  if (prec != SG_FP64 && prec != SG_FP32 && prec != SG_TF32)
-    return fail(SG_EINVAL, "sg_precond precision must be SG_FP64, SG_FP32 or SG_TF32");
-  cudaStream_t st = (cudaStream_t)stream;
-  size_t bytes = (size_t)h->N * (prec == SG_FP64 ? sizeof(double2) : sizeof(float2));
-  if (kind == SG_PREC_NONE) {
-    if (R != Z) SG_CUDA_TRY(cudaMemcpyAsync(Z, R, bytes, cudaMemcpyDeviceToDevice, st));
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !R || !Z) return fail(SG_EINVAL, "NULL handle or vector");
+    if (prec != SG_FP64 && prec != SG_FP32 && prec != SG_TF32)
+      return fail(SG_EINVAL, "sg_precond precision must be SG_FP64, SG_FP32 or SG_TF32");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)h->N * (prec == SG_FP64 ? sizeof(double2) : sizeof(float2));
+    if (kind == SG_PREC_NONE) {
+      if (R != Z) SG_CUDA_TRY(cudaMemcpyAsync(Z, R, bytes, cudaMemcpyDeviceToDevice, st));
+      return SG_OK;
+    }
+    if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN) return fail(SG_EINVAL, "unknown preconditioner");
+    int which = kind == SG_PREC_MEAN ? 0 : 1;
+    if (!h->blk[which].ready)
+      return fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
+    if (prec == SG_TF32) {
+      if (h->dim != 2 || !h->fd)
+        return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with the fast-diagonalisation route (lines <= 320)");
+      SG_CUDA_TRY(launch_precond_tf32(h, which, (const float2*)R, (float2*)Z, st, nullptr, nullptr));
+    } else if (prec == SG_FP64) {
+      SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));
+    } else {
+      SG_CUDA_TRY(launch_precond<float>(h, which, (const float2*)R, (float2*)Z, st));
+    }
     return SG_OK;
-  }
-  if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN) return fail(SG_EINVAL, "unknown preconditioner");
-  int which = kind == SG_PREC_MEAN ? 0 : 1;
-  if (!h->blk[which].ready)
-    return fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
-  if (prec == SG_TF32) {
-    if (h->dim != 2 || !h->fd)
-      return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with the fast-diagonalisation route (lines <= 320)");
-    SG_CUDA_TRY(launch_precond_tf32(h, which, (const float2*)R, (float2*)Z, st, nullptr, nullptr));
-  } else if (prec == SG_FP64) {
-    SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));
-  } else {
-    SG_CUDA_TRY(launch_precond<float>(h, which, (const float2*)R, (float2*)Z, st));
-  }
-  return SG_OK;
+  });
 }
 
 sg_status sg_selftest_wait_timeout(void* stream, int* timed_out, double* seconds) {
-  g_err.clear();
-  if (!timed_out) return fail(SG_EINVAL, "NULL timed_out");
-  *timed_out = 0;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  int* d = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  int hflags[2] = {0, 0};
-  float ms = 0.f;
-  cudaError_t e = cudaMalloc((void**)&d, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
-  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-  if (e == cudaSuccess) e = tc_wait_selftest(d, d + 1, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-  for (cudaEvent_t x : ev)
-    if (x) cudaEventDestroy(x);
-  if (d) cudaFree(d);
-  if (e != cudaSuccess) return fail(SG_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
-  if (!hflags[1]) return fail(SG_ECUDA, "wait self-test: the kernel did not reach its end");
-  *timed_out = hflags[0];
-  if (seconds) *seconds = ms * 1e-3;
-  if (hflags[0]) return fail(SG_ETIMEOUT, "a device-side wait timed out (self-test: the expected outcome)");
-  return SG_OK;
+  return sgi::guarded([&]() -> sg_status {
+    g_err.clear();
+    if (!timed_out) return fail(SG_EINVAL, "NULL timed_out");
+    *timed_out = 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int* d = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int hflags[2] = {0, 0};
+    float ms = 0.f;
+    cudaError_t e = cudaMalloc((void**)&d, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = tc_wait_selftest(d, d + 1, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hflags, d, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return fail(SG_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+    if (!hflags[1]) return fail(SG_ECUDA, "wait self-test: the kernel did not reach its end");
+    *timed_out = hflags[0];
+    if (seconds) *seconds = ms * 1e-3;
+    if (hflags[0]) return fail(SG_ETIMEOUT, "a device-side wait timed out (self-test: the expected outcome)");
+    return SG_OK;
+  });
 }
 
 }  // extern "C"

@@ -6,7 +6,9 @@
 #include <stdint.h>
 
 #include <complex>
+#include <exception>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -19,6 +21,21 @@ using cd = std::complex<double>;
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 sg_status fail(sg_status st, const std::string& msg);
+// Runs the body of an ABI entry point: no C++ exception (a failed host
+// allocation, a container error) may cross the C ABI, so each becomes a
+// status and a message.
+template <typename F>
+sg_status guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(SG_ENOMEM, "host memory allocation failed");
+  } catch (const std::exception& e) {
+    return fail(SG_EINVAL, std::string("host exception: ") + e.what());
+  } catch (...) {
+    return fail(SG_EINVAL, "unknown host exception");
+  }
+}
 #define SG_CUDA_TRY(expr)                                                       \
   do {                                                                          \
     cudaError_t e_ = (expr);                                                    \

@@ -1228,192 +1228,194 @@ sg_status sgi_prepare_workspace(sg_handle* h, const sg_gmres_opts* opts) {
 
 extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void* x,
                               sg_gmres_info* info, void* stream) {
-  if (!h || !opts || !b || !x) return fail(SG_EINVAL, "NULL argument to sg_gmres");
-  if (opts->mode != SG_FP64 && opts->mode != SG_FP32 && opts->mode != SG_MIXED)
-    return fail(SG_EINVAL, "bad mode");
-  if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN)
-    return fail(SG_EINVAL, "bad preconditioner");
-  if (!(opts->tol > 0) || !std::isfinite(opts->tol)) return fail(SG_EINVAL, "tol must be positive");
-  if (opts->x0_policy < SG_X0_AS_GIVEN || opts->x0_policy > SG_X0_SCALED) return fail(SG_EINVAL, "bad x0_policy");
-  if (opts->prec != SG_PREC_NONE && !h->blk[opts->prec == SG_PREC_MEAN ? 0 : 1].ready)
-    return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (2D needs a constant k_0)");
-  const long long N = h->N;
-  int m = opts->restart <= 0 ? (int)std::min<long long>(N, MAXV - 1) : opts->restart;
-  if (m > MAXV - 1) return fail(SG_EINVAL, "restart must be <= 511");
-  m = (int)std::min<long long>(m, N);
-  const int maxit = opts->maxit <= 0 ? (int)std::min<long long>(N, 1 << 30) : opts->maxit;
-  const int check_every = opts->check_every <= 0 ? 8 : opts->check_every;
-  const bool mixed = opts->mode == SG_MIXED;
-  const bool f32 = opts->mode == SG_FP32;
-  const bool inner32 = mixed || f32;
-  sg_status st0 = ensure_work(h, m, inner32 ? 8 : 16);
-  if (st0 != SG_OK) return st0;
-  GmresWork& w = h->gw;
-  // All work runs on the handle's private stream (stream capture needs a
-  // non-legacy stream), ordered after the caller's stream and joined back
-  // into it on every return.
-  cudaStream_t caller = (cudaStream_t)stream;
-  cudaStream_t st = w.stream;
-  SG_CUDA_TRY(cudaEventRecord(w.ev, caller));
-  SG_CUDA_TRY(cudaStreamWaitEvent(st, w.ev, 0));
-  struct Rejoin {
-    cudaEvent_t ev;
-    cudaStream_t from, to;
-    ~Rejoin() {
-      if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !opts || !b || !x) return fail(SG_EINVAL, "NULL argument to sg_gmres");
+    if (opts->mode != SG_FP64 && opts->mode != SG_FP32 && opts->mode != SG_MIXED)
+      return fail(SG_EINVAL, "bad mode");
+    if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN)
+      return fail(SG_EINVAL, "bad preconditioner");
+    if (!(opts->tol > 0) || !std::isfinite(opts->tol)) return fail(SG_EINVAL, "tol must be positive");
+    if (opts->x0_policy < SG_X0_AS_GIVEN || opts->x0_policy > SG_X0_SCALED) return fail(SG_EINVAL, "bad x0_policy");
+    if (opts->prec != SG_PREC_NONE && !h->blk[opts->prec == SG_PREC_MEAN ? 0 : 1].ready)
+      return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (2D needs a constant k_0)");
+    const long long N = h->N;
+    int m = opts->restart <= 0 ? (int)std::min<long long>(N, MAXV - 1) : opts->restart;
+    if (m > MAXV - 1) return fail(SG_EINVAL, "restart must be <= 511");
+    m = (int)std::min<long long>(m, N);
+    const int maxit = opts->maxit <= 0 ? (int)std::min<long long>(N, 1 << 30) : opts->maxit;
+    const int check_every = opts->check_every <= 0 ? 8 : opts->check_every;
+    const bool mixed = opts->mode == SG_MIXED;
+    const bool f32 = opts->mode == SG_FP32;
+    const bool inner32 = mixed || f32;
+    sg_status st0 = ensure_work(h, m, inner32 ? 8 : 16);
+    if (st0 != SG_OK) return st0;
+    GmresWork& w = h->gw;
+    // All work runs on the handle's private stream (stream capture needs a
+    // non-legacy stream), ordered after the caller's stream and joined back
+    // into it on every return.
+    cudaStream_t caller = (cudaStream_t)stream;
+    cudaStream_t st = w.stream;
+    SG_CUDA_TRY(cudaEventRecord(w.ev, caller));
+    SG_CUDA_TRY(cudaStreamWaitEvent(st, w.ev, 0));
+    struct Rejoin {
+      cudaEvent_t ev;
+      cudaStream_t from, to;
+      ~Rejoin() {
+        if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+      }
+    } rejoin{w.ev, st, caller};
+    Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+    c.L = DevLayout(w.restart);
+    // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
+    const size_t obytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
+
+    // outer vectors (x, b) in the outer precision
+    void* xd = x;
+    const void* bd = b;
+    if (opts->host_io) {
+      SG_CUDA_TRY(cudaMemcpyAsync(w.B64, b, obytes, cudaMemcpyHostToDevice, st));
+      bd = w.B64;
+      xd = w.X64;
     }
-  } rejoin{w.ev, st, caller};
-  Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
-  c.L = DevLayout(w.restart);
-  // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
-  const size_t obytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
-
-  // outer vectors (x, b) in the outer precision
-  void* xd = x;
-  const void* bd = b;
-  if (opts->host_io) {
-    SG_CUDA_TRY(cudaMemcpyAsync(w.B64, b, obytes, cudaMemcpyHostToDevice, st));
-    bd = w.B64;
-    xd = w.X64;
-  }
-  bool x_zero = opts->x0 == nullptr;
-  if (opts->x0 && opts->x0 != xd) {
-    SG_CUDA_TRY(cudaMemcpyAsync(xd, opts->x0, obytes, opts->host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
-  } else if (!opts->x0) {
-    SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
-  }
-  int ctl0[16] = {0};
-  ctl0[CTL_MAXIT] = maxit;
-  SG_CUDA_TRY(cudaMemcpyAsync(w.dctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, st));
-
-  // ||b||
-  double bn2 = 0;
-  {
-    double* out = w.dscal + c.L.sc + SC_BNORM;
-    if (f32)
-      k_residual<float, float><<<c.grid, RED_THREADS, 0, st>>>((const float2*)bd, nullptr, nullptr, N, w.part,
-                                                               c.pstride, w.counter, out);
-    else
-      k_residual<double, double><<<c.grid, RED_THREADS, 0, st>>>((const double2*)bd, nullptr, nullptr, N, w.part,
-                                                                 c.pstride, w.counter, out);
-    note_launch();
-    SG_CUDA_TRY(cudaGetLastError());
-    SG_CUDA_TRY(cudaMemcpyAsync(&bn2, out, sizeof(double), cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(cudaStreamSynchronize(st));
-  }
-  const double bnorm = std::sqrt(bn2);
-  sg_gmres_info inf{};
-  sg_status status = SG_ENOTCONV;
-  if (!std::isfinite(bnorm)) {
-    status = fail(SG_EINVAL, "right-hand side is not finite");
-    if (info) { inf.status = status; *info = inf; }
-    return status;
-  }
-  if (bnorm == 0.0) {
-    SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
-    if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(cudaStreamSynchronize(st));
-    inf.status = SG_OK;
-    if (info) *info = inf;
-    return SG_OK;
-  }
-  const int max_outer = mixed ? (opts->max_outer <= 0 ? 20 : opts->max_outer) : 1 << 30;
-  const double inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
-  int iters = 0, cycles = 0, outer = 0;
-  double relres = 1.0;
-  int ctl[16];
-  bool ax_ready = false;   // A x already in the residual scratch (scaled guess)
-  if (!x_zero && opts->x0_policy == SG_X0_SCALED) {
-    sg_status s = f32 ? scale_guess<float>(c, (const float2*)bd, (float2*)xd, (float2*)w.Z)
-                      : scale_guess<double>(c, (const double2*)bd, (double2*)xd, (double2*)w.R64);
-    if (s != SG_OK) return s;
-    ax_ready = true;
-  }
-  for (;;) {
-    double rn2 = 0;
-    sg_status s;
-    if (f32)
-      s = residual_norm<float>(c, (const float2*)bd, (const float2*)xd, x_zero, (float2*)w.Z, w.V, true, &rn2,
-                               ax_ready);
-    else
-      s = residual_norm<double>(c, (const double2*)bd, (const double2*)xd, x_zero, (double2*)w.R64, w.V, inner32,
-                                &rn2, ax_ready);
-    ax_ready = false;
-    if (s != SG_OK) return s;
-    relres = std::sqrt(rn2) / bnorm;
-    if (cycles == 0 && !x_zero && opts->x0_policy != SG_X0_AS_GIVEN && !(relres <= 1.0)) {
-      // the supplied guess is worse than zero: start from zero instead
+    bool x_zero = opts->x0 == nullptr;
+    if (opts->x0 && opts->x0 != xd) {
+      SG_CUDA_TRY(cudaMemcpyAsync(xd, opts->x0, obytes, opts->host_io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    } else if (!opts->x0) {
       SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
-      x_zero = true;
-      continue;
     }
-    if (!std::isfinite(relres)) { status = SG_EBREAKDOWN; break; }
-    if (relres <= opts->tol) { status = SG_OK; break; }
-    if (iters >= maxit) { status = SG_ENOTCONV; break; }
-    if (mixed && outer >= max_outer) { status = SG_ENOTCONV; break; }
-    // inner tolerance on |g| relative to ref
-    double tol_est, ref;
-    if (mixed) {
-      // reduce by inner_tol per refinement step, but finish in this step when
-      // the remaining reduction is within 20x of it (saves a refinement step
-      // that would only cover the last factor)
-      ref = std::sqrt(rn2);
-      const double need = 0.5 * opts->tol * bnorm / ref;
-      tol_est = need >= 0.05 * inner_tol ? need : inner_tol;
-      tol_est = std::min(tol_est, 0.5);
-    } else {
-      ref = bnorm;
-      tol_est = opts->tol;
-    }
-    bool any = false;
-    s = inner32 ? run_cycle<float>(c, opts->prec, m, tol_est, ref, check_every, &any)
-                : run_cycle<double>(c, opts->prec, m, tol_est, ref, check_every, &any);
-    if (s != SG_OK) return s;
-    SG_CUDA_TRY(cudaMemcpyAsync(ctl, w.dctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(cudaStreamSynchronize(st));
-    if (ctl[CTL_FLAGS] & FL_NAN) { status = SG_EBREAKDOWN; break; }
-    if (any) {
+    int ctl0[16] = {0};
+    ctl0[CTL_MAXIT] = maxit;
+    SG_CUDA_TRY(cudaMemcpyAsync(w.dctl, ctl0, sizeof(ctl0), cudaMemcpyHostToDevice, st));
+
+    // ||b||
+    double bn2 = 0;
+    {
+      double* out = w.dscal + c.L.sc + SC_BNORM;
       if (f32)
-        k_axpy<float, float><<<c.grid, RED_THREADS, 0, st>>>((float2*)xd, (const float2*)w.Z, N, w.dctl);
-      else if (mixed)
-        k_axpy<double, float><<<c.grid, RED_THREADS, 0, st>>>((double2*)xd, (const float2*)w.Z, N, w.dctl);
+        k_residual<float, float><<<c.grid, RED_THREADS, 0, st>>>((const float2*)bd, nullptr, nullptr, N, w.part,
+                                                                 c.pstride, w.counter, out);
       else
-        k_axpy<double, double><<<c.grid, RED_THREADS, 0, st>>>((double2*)xd, (const double2*)w.Z, N, w.dctl);
+        k_residual<double, double><<<c.grid, RED_THREADS, 0, st>>>((const double2*)bd, nullptr, nullptr, N, w.part,
+                                                                   c.pstride, w.counter, out);
       note_launch();
       SG_CUDA_TRY(cudaGetLastError());
-      x_zero = false;
+      SG_CUDA_TRY(cudaMemcpyAsync(&bn2, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    iters = ctl[CTL_ITERS];
-    ++cycles;
-    if (mixed) ++outer;
-    if (!any && !(ctl[CTL_FLAGS] & FL_CONV)) { status = SG_ENOTCONV; break; }
-    if (!any && (ctl[CTL_FLAGS] & FL_CONV)) {
-      // estimate says converged at zero steps but the true residual disagrees
-      status = SG_ENOTCONV;
-      break;
+    const double bnorm = std::sqrt(bn2);
+    sg_gmres_info inf{};
+    sg_status status = SG_ENOTCONV;
+    if (!std::isfinite(bnorm)) {
+      status = fail(SG_EINVAL, "right-hand side is not finite");
+      if (info) { inf.status = status; *info = inf; }
+      return status;
     }
-    if ((ctl[CTL_FLAGS] & FL_BREAK) && !(ctl[CTL_FLAGS] & FL_CONV)) {
-      // invariant subspace: the update solved the system up to rounding; one more residual check
-      ctl[CTL_FLAGS] &= ~FL_BREAK;
+    if (bnorm == 0.0) {
+      SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
+      if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+      inf.status = SG_OK;
+      if (info) *info = inf;
+      return SG_OK;
     }
-  }
-  if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
-  SG_CUDA_TRY(cudaStreamSynchronize(st));
-  int werr = 0;   // a bounded wait inside a kernel ran out (tensor-core transforms)
-  SG_CUDA_TRY(cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  SG_CUDA_TRY(cudaStreamSynchronize(st));
-  if (werr) {
-    SG_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
-    status = SG_ETIMEOUT;
-  }
-  inf.iters = iters;
-  inf.cycles = cycles;
-  inf.outer = outer;
-  inf.relres = relres;
-  inf.status = status;
-  if (info) *info = inf;
-  if (status == SG_ENOTCONV) set_error("GMRES did not reach tol within maxit");
-  if (status == SG_EBREAKDOWN) set_error("GMRES breakdown: non-finite values");
-  if (status == SG_ETIMEOUT) set_error("a device-side wait timed out in a preconditioner transform");
-  return status;
+    const int max_outer = mixed ? (opts->max_outer <= 0 ? 20 : opts->max_outer) : 1 << 30;
+    const double inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
+    int iters = 0, cycles = 0, outer = 0;
+    double relres = 1.0;
+    int ctl[16];
+    bool ax_ready = false;   // A x already in the residual scratch (scaled guess)
+    if (!x_zero && opts->x0_policy == SG_X0_SCALED) {
+      sg_status s = f32 ? scale_guess<float>(c, (const float2*)bd, (float2*)xd, (float2*)w.Z)
+                        : scale_guess<double>(c, (const double2*)bd, (double2*)xd, (double2*)w.R64);
+      if (s != SG_OK) return s;
+      ax_ready = true;
+    }
+    for (;;) {
+      double rn2 = 0;
+      sg_status s;
+      if (f32)
+        s = residual_norm<float>(c, (const float2*)bd, (const float2*)xd, x_zero, (float2*)w.Z, w.V, true, &rn2,
+                                 ax_ready);
+      else
+        s = residual_norm<double>(c, (const double2*)bd, (const double2*)xd, x_zero, (double2*)w.R64, w.V, inner32,
+                                  &rn2, ax_ready);
+      ax_ready = false;
+      if (s != SG_OK) return s;
+      relres = std::sqrt(rn2) / bnorm;
+      if (cycles == 0 && !x_zero && opts->x0_policy != SG_X0_AS_GIVEN && !(relres <= 1.0)) {
+        // the supplied guess is worse than zero: start from zero instead
+        SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
+        x_zero = true;
+        continue;
+      }
+      if (!std::isfinite(relres)) { status = SG_EBREAKDOWN; break; }
+      if (relres <= opts->tol) { status = SG_OK; break; }
+      if (iters >= maxit) { status = SG_ENOTCONV; break; }
+      if (mixed && outer >= max_outer) { status = SG_ENOTCONV; break; }
+      // inner tolerance on |g| relative to ref
+      double tol_est, ref;
+      if (mixed) {
+        // reduce by inner_tol per refinement step, but finish in this step when
+        // the remaining reduction is within 20x of it (saves a refinement step
+        // that would only cover the last factor)
+        ref = std::sqrt(rn2);
+        const double need = 0.5 * opts->tol * bnorm / ref;
+        tol_est = need >= 0.05 * inner_tol ? need : inner_tol;
+        tol_est = std::min(tol_est, 0.5);
+      } else {
+        ref = bnorm;
+        tol_est = opts->tol;
+      }
+      bool any = false;
+      s = inner32 ? run_cycle<float>(c, opts->prec, m, tol_est, ref, check_every, &any)
+                  : run_cycle<double>(c, opts->prec, m, tol_est, ref, check_every, &any);
+      if (s != SG_OK) return s;
+      SG_CUDA_TRY(cudaMemcpyAsync(ctl, w.dctl, sizeof(ctl), cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+      if (ctl[CTL_FLAGS] & FL_NAN) { status = SG_EBREAKDOWN; break; }
+      if (any) {
+        if (f32)
+          k_axpy<float, float><<<c.grid, RED_THREADS, 0, st>>>((float2*)xd, (const float2*)w.Z, N, w.dctl);
+        else if (mixed)
+          k_axpy<double, float><<<c.grid, RED_THREADS, 0, st>>>((double2*)xd, (const float2*)w.Z, N, w.dctl);
+        else
+          k_axpy<double, double><<<c.grid, RED_THREADS, 0, st>>>((double2*)xd, (const double2*)w.Z, N, w.dctl);
+        note_launch();
+        SG_CUDA_TRY(cudaGetLastError());
+        x_zero = false;
+      }
+      iters = ctl[CTL_ITERS];
+      ++cycles;
+      if (mixed) ++outer;
+      if (!any && !(ctl[CTL_FLAGS] & FL_CONV)) { status = SG_ENOTCONV; break; }
+      if (!any && (ctl[CTL_FLAGS] & FL_CONV)) {
+        // estimate says converged at zero steps but the true residual disagrees
+        status = SG_ENOTCONV;
+        break;
+      }
+      if ((ctl[CTL_FLAGS] & FL_BREAK) && !(ctl[CTL_FLAGS] & FL_CONV)) {
+        // invariant subspace: the update solved the system up to rounding; one more residual check
+        ctl[CTL_FLAGS] &= ~FL_BREAK;
+      }
+    }
+    if (opts->host_io) SG_CUDA_TRY(cudaMemcpyAsync(x, xd, obytes, cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    int werr = 0;   // a bounded wait inside a kernel ran out (tensor-core transforms)
+    SG_CUDA_TRY(cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (werr) {
+      SG_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+      status = SG_ETIMEOUT;
+    }
+    inf.iters = iters;
+    inf.cycles = cycles;
+    inf.outer = outer;
+    inf.relres = relres;
+    inf.status = status;
+    if (info) *info = inf;
+    if (status == SG_ENOTCONV) set_error("GMRES did not reach tol within maxit");
+    if (status == SG_EBREAKDOWN) set_error("GMRES breakdown: non-finite values");
+    if (status == SG_ETIMEOUT) set_error("a device-side wait timed out in a preconditioner transform");
+    return status;
+  });
 }

@@ -16,8 +16,8 @@ moments.
 
 Pins: tests/test_oracle_mlp.py (central finite differences of the loss, a
 one-layer closed form, the first Adam step's closed form lr * sign(g)).
-Parity of the learned guess itself is unpinned: the paper has no
-counterpart; what the guess is measured against is the zero initial guess.
+The quality of the learned guess itself: parity unpinned (the paper has no
+counterpart; the guess is measured against the zero initial guess).
 """
 from __future__ import annotations
 

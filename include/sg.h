@@ -123,7 +123,7 @@ typedef struct {
  * mean-value and CSL blocks (1D: tridiagonal LU with partial pivoting;
  * 2D with constant k_0: eigenvectors of the 1D pencil in x plus tridiagonal
  * LU with partial pivoting along y, all pivots in FP64).
- * Returns SG_EINVAL on inconsistent sizes, NaN/Inf fields or k <= 0,
+ * Returns SG_EINVAL on inconsistent sizes (or more than 2^30 nodes), NaN/Inf fields or k <= 0,
  * SG_ESINGULAR if a factorisation meets a zero pivot.  *out is set only on
  * success. */
 sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out);

@@ -567,6 +567,9 @@ sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
       if (D.bc[i] != SG_BC_DIRICHLET && D.bc[i] != SG_BC_ABSORBING) return fail(SG_EINVAL, "bad bc");
     if (D.dim == 2 && !(D.bc[0] == D.bc[1] && D.bc[1] == D.bc[2] && D.bc[2] == D.bc[3]))
       return fail(SG_EINVAL, "2D needs all-Dirichlet or all-absorbing boundaries (Theorems A.5/A.6)");
+    // unknowns are indexed with 32-bit integers on the device (2 n + 1 < 2^31)
+    if ((long long)D.nx * (D.dim == 2 ? D.ny : 1) > (1LL << 30))
+      return fail(SG_EINVAL, "grid too large (at most 2^30 nodes)");
     if (!D.k0 || (D.s > 0 && !D.kl)) return fail(SG_EINVAL, "NULL wavenumber field");
     if (!std::isfinite(D.beta)) return fail(SG_EINVAL, "beta not finite");
 

@@ -54,5 +54,10 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     d.dim = 3
     assert lib.sg_assemble(C.byref(d), None, C.byref(h)) == binding.SG_EINVAL
     assert b"dim" in lib.sg_last_error()
+    # a grid whose node count overflows the device's 32-bit unknown index
+    d = binding.SgDesc()
+    d.dim, d.nx, d.ny, d.h, d.s, d.r = 2, 50000, 50000, 1e-5, 0, 0
+    assert lib.sg_assemble(C.byref(d), None, C.byref(h)) == binding.SG_EINVAL
+    assert b"too large" in lib.sg_last_error()
     assert lib.sg_matvec(None, 0, None, None, None) == binding.SG_EINVAL
     assert lib.sg_gmres(None, None, None, None, None, None) == binding.SG_EINVAL

@@ -116,6 +116,9 @@ typedef struct {
   int specialised;     /* 1 if a register-resident matvec kernel serves (s, r) */
   int fast_diag;       /* 1 if FP32 2D preconditioner applies use the fast diagonalisation
                           (both directions transformed, tensor-core GEMMs) */
+  double eig_orth_err; /* separable 2D: max |Q^T Q - I| of the 1D pencils' eigenvector
+                          factors (set-up rejects > 1e-10); 0 otherwise */
+  double eig_kappa;    /* separable 2D: cond(Q) of those factors (set-up rejects > 100) */
 } sg_info;
 
 /* Builds the SG operator of Theorem 3.4 / Theorems A.1, A.2, A.5, A.6:

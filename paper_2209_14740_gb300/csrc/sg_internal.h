@@ -187,7 +187,8 @@ struct sg_handle {
   float* d_dyinv32 = nullptr;
   void* d_tmp = nullptr;             // N complex128 scratch (preconditioner intermediate)
   void* d_tmp2 = nullptr;            // N complex128 scratch (2D: second intermediate)
-  double eig_orth_err = 0.0;         // max |Q^T Q - I| of the host eigenvectors
+  double eig_orth_err = 0.0;         // max |Q^T Q - I| of the host eigenvectors (<= 1e-10 accepted)
+  double eig_kappa = 0.0;            // cond(Q) of the eigenvector factors (<= 100 accepted)
   // 2D fast diagonalisation (FP32 applies): both directions transformed,
   // S^-1 = (Qhat_y (x) Qhat_x) diag(1 / (lambda_y,j + lambda_x,i + shift)) (Qhat_y (x) Qhat_x)^T
   bool fd = false;
@@ -236,7 +237,4 @@ long long thread_launches();          // kernels noted by this host thread so fa
 // true if a register-resident complex64 matvec kernel exists for (s, r)
 bool matvec_is_specialised(int s, int r);
 
-// host helpers
-bool csym_tridiag_eig(int n, const std::vector<cd>& diag, const std::vector<cd>& off,
-                      std::vector<cd>& lam, std::vector<cd>& Q, double* orth_err);
 }  // namespace sgi

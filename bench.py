@@ -44,10 +44,10 @@ WORKLOAD = {"workload": "helmholtz_2d_127x127_s3_deg3", "nodes": "127x127", "h":
             "preconditioner": "mean-value I(x)S(xi_bar)", "source": "gaussian w=0.02 at (0.5,0.5)"}
 MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
-# generated complex64 operator kernel at 511 x 511, P = 84, from an ncu capture
-# (profiles/matvec_c64_511x511_s6_deg3.md).  Reported only while the generator
-# still emits this kernel source and tile (SHA-256 below): a changed kernel
-# reports null.
+# generated complex64 operator kernel at 511 x 511, P = 84, from an earlier ncu
+# capture (the matvec summary under profiles/), not measured live by this
+# script.  Reported only while the generator still emits this kernel source and
+# tile (SHA-256 below): a changed kernel reports null.
 MATVEC_TRAFFIC = {"sha256": "0e5a4679d2e0f084f9f73ce6af95304f6010fe7044be5c825df92d9d73acfd2d",
                   "bytes": 183150592 + 123807488}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on

@@ -30,6 +30,9 @@
  *   - The library owns the handle, its device fields, factors and
  *     workspace (allocated by sg_assemble / the first sg_gmres call, freed by
  *     sg_destroy).  Handles are not thread-safe; use one per host thread.
+ *   - One CUDA device per process: kernel attributes and SM counts are set
+ *     up on the device of the first sg_assemble, and sg_assemble on another
+ *     device returns SG_EUNSUPPORTED (run one process per GPU).
  */
 #ifndef SG_GB300_H
 #define SG_GB300_H
@@ -173,13 +176,17 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
  * forbidden or too slow in their context, or device memory owned by another
  * allocator's pool); the handle itself must still come from sg_assemble.
  *   - N must be <= SG_NOALLOC_MAX_N, else SG_EINVAL with a message.
- *   - The array holds 2 * SG_NOALLOC_MAX_N complex128 values (16 MiB) on every
- *     device that loads the library, until the process exits.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - The array holds 2 * SG_NOALLOC_MAX_N complex128 values (16 MiB) on the
+ *     device, until the process exits.  sg_assemble looks up its device
+ *     address (cudaGetSymbolAddress), which is also what loads it under lazy
+ *     module loading, so no call of this entry point loads code or commits
+ *     memory.
  *   - All calls share the array: calls that overlap on the GPU (several
  *     streams or host threads) race.  Each call overwrites what it reads, so
  *     no clearing is needed between calls.
+ *   - SG_FP32 on a 2D handle with the tensor-core transforms shares the
+ *     handle's device timeout flag with sg_precond: a bounded wait that gives
+ *     up there is reported by the next sg_gmres on the handle (SG_ETIMEOUT).
  * R, Z: device, N complex of precision prec (FP64 or FP32); Z may equal R. */
 sg_status sg_precond_noalloc(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                              void* stream);

@@ -10,14 +10,19 @@
 // lives in the library image, so it works with handles whose scratch must
 // not be touched (for example while another stream uses it).
 //
-// The scratch is a file-scope __device__ array: every GPU that loads the
+// The scratch is a file-scope __device__ array: the GPU that loads the
 // library holds SG_NOALLOC_MAX_N * 2 complex128 values (16 MiB) until the
 // process exits.  All calls share it, so calls that overlap on the GPU (two
 // streams, two host threads) race.  Every call fully writes the parts of the
 // array it later reads, so nothing has to start at zero.
+//
+// Host code may not use the array's name as a device address; its address is
+// looked up by sg_assemble (sgi::noalloc_scratch_address below), where
+// allocation is allowed anyway: that lookup is what loads this file's module
+// and commits the array under lazy module loading, so sg_precond_noalloc
+// itself never does.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "sg_internal.h"
@@ -28,30 +33,22 @@ namespace {
 // storage; the complex64 path uses the first half of each).
 static __device__ __align__(256) double2 g_noalloc_scratch[2 * (size_t)SG_NOALLOC_MAX_N];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
+}  // namespace
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code may not use the array's name as a device address).
-sg_status scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return sgi::fail(SG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return sgi::fail(SG_EUNSUPPORTED, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return sgi::fail(SG_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return SG_OK;
+namespace sgi {
+
+// Device address of the scratch array on the current device (called by
+// sg_assemble with the handle's device current).
+cudaError_t noalloc_scratch_address(void** out) {
+  *out = nullptr;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e == cudaSuccess && !p) e = cudaErrorInvalidSymbol;
+  if (e == cudaSuccess) *out = p;
+  return e;
 }
 
-}  // namespace
+}  // namespace sgi
 
 extern "C" sg_status sg_precond_noalloc(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z,
                                         void* stream) {
@@ -67,9 +64,8 @@ extern "C" sg_status sg_precond_noalloc(sg_handle* h, sg_prec kind, sg_precision
     const int which = kind == SG_PREC_MEAN ? 0 : 1;
     if (!h->blk[which].ready)
       return sgi::fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
-    void* base = nullptr;
-    sg_status s = scratch_address(&base);
-    if (s != SG_OK) return s;
+    void* base = h->noalloc_scratch;
+    if (!base) return sgi::fail(SG_ECUDA, "sg_precond_noalloc: the static scratch has no device address");
     cudaStream_t st = (cudaStream_t)stream;
     double2* s0 = reinterpret_cast<double2*>(base);
     double2* s1 = s0 + (size_t)SG_NOALLOC_MAX_N;

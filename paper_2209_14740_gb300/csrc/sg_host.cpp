@@ -24,6 +24,7 @@ namespace sgi {
 
 static thread_local std::string g_err;
 static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_device{-1};   // the one CUDA device this process's handles use
 
 static thread_local long long t_launches = 0;
 void note_launch() {
@@ -535,6 +536,23 @@ sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) { delete h; return fail(SG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)); }
+    // one device per process: kernel attributes (dynamic shared memory
+    // limits) and SM counts are set up once, on the first device used
+    {
+      int expected = -1;
+      if (!g_device.compare_exchange_strong(expected, h->device) && expected != h->device) {
+        const int first = expected;
+        delete h;
+        return fail(SG_EUNSUPPORTED, "the library serves one CUDA device per process (first used: device " +
+                                         std::to_string(first) + "); run one process per GPU");
+      }
+    }
+    // the allocation-free entry point's static scratch: its address is looked
+    // up here, where allocation is allowed (the lookup loads its module)
+    if ((e = noalloc_scratch_address(&h->noalloc_scratch)) != cudaSuccess) {
+      delete h;
+      return fail(SG_ECUDA, std::string("static scratch address: ") + cudaGetErrorString(e));
+    }
 
     std::vector<float> gval32(h->gval.begin(), h->gval.end()), gdiag32(h->gdiag.begin(), h->gdiag.end()),
         fields32(fields.begin(), fields.end());

@@ -197,6 +197,7 @@ struct sg_handle {
   float2* d_Linv32[2] = {nullptr, nullptr};   // [block] my x mx: 1 / (lambda_y,j + lambda_x,i + shift)
   sgi::TcDevOperand tcB[4];          // tensor-core factors: Qhat_x, Qhat_y, Qhat_y^T, Qhat_x^T
   int* d_err = nullptr;              // device flag: a bounded wait in a kernel timed out
+  void* noalloc_scratch = nullptr;   // device address of the static scratch of sg_precond_noalloc
 
   sgi::GmresWork gw;
 
@@ -228,6 +229,10 @@ cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, 
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                    C2<T>* tmp, C2<T>* tmp2);
+
+// Device address of the allocation-free entry point's static scratch on the
+// current device (loads its module; called once per handle by sg_assemble).
+cudaError_t noalloc_scratch_address(void** out);
 
 // launch bookkeeping (sg_kernel_launches)
 void note_launch();

@@ -5,7 +5,7 @@ once untimed (first-use costs), then `--reps` times inside an NVTX range
 named "profiled", so a profiler can restrict itself to those launches:
 
     python -m paper_2209_14740_gb300.profile_cases matvec --g 511 --s 6 --r 3
-    ncu --nvtx --nvtx-include "profiled/" --metrics gpu__time_duration.sum ...
+    ncu --clock-control none --nvtx --nvtx-include "profiled/" --metrics gpu__time_duration.sum ...
         python -m paper_2209_14740_gb300.profile_cases solve --mode mixed
 
 Cases: matvec (the SG operator), precond (the mean-value preconditioner),

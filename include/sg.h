@@ -93,6 +93,14 @@ typedef enum { SG_FP64 = 0, SG_FP32 = 1, SG_MIXED = 2, SG_TF32 = 3 } sg_precisio
  *   f      host, nx*ny doubles: source values at the nodes (before FD
  *          weights).  May be NULL (zero source).
  *   beta   CSL shift for SG_PREC_CSL_MEAN (Sec. 4; the paper uses 1/2).
+ *   point_source, point_x, point_y
+ *          if point_source != 0, a unit point source delta(x - a) at
+ *          a = point_x (1D) or (point_x, point_y) (2D) is added to f, with
+ *          the discretisation of App. A.3: 1/h^dim at the grid node closest
+ *          to a (of two equally close nodes, the one with the smaller index;
+ *          for a = 1/2 the node t = ceil(q/2)), zero elsewhere.  a must lie
+ *          in [0, 1] per coordinate (else SG_EINVAL); a source on an
+ *          eliminated Dirichlet node contributes nothing.
  * The host arrays are read during sg_assemble only. */
 typedef struct {
   int dim;
@@ -104,6 +112,8 @@ typedef struct {
   const double* kl;
   const double* f;
   double beta;
+  int point_source;
+  double point_x, point_y;
 } sg_desc;
 
 typedef struct {

@@ -48,6 +48,26 @@ def point_source_index(q: int) -> int:
     return (q + 1) // 2
 
 
+def nearest_node(a: float, h: float, nnodes: int) -> int:
+    """Index j of the grid point x_j = j h closest to a; of two equally close
+    points the smaller one (App. A.3: for a = 1/2 on x_0..x_{q+1} this is
+    t = ceil(q/2)).  The 1e-9 guard keeps exact ties from being split by the
+    rounding of a / h."""
+    j = ceil(a / h - 0.5 - 1e-9)
+    return min(max(j, 0), nnodes - 1)
+
+
+def point_source(dim: int, nx: int, ny: int, h: float, point) -> np.ndarray:
+    """Node values of a unit point source f = delta(x - a) (App. A.3): 1/h in
+    1D, 1/h^2 in 2D at the grid point closest to a, zero elsewhere; nodes
+    x fastest, boundary nodes included."""
+    f = np.zeros(nx * ny)
+    tx = nearest_node(point[0], h, nx)
+    ty = nearest_node(point[1], h, ny) if dim == 2 else 0
+    f[tx + nx * ty] = 1.0 / h ** dim
+    return f
+
+
 @dataclass
 class Axis:
     """One grid direction: nodes x_0..x_{q+1}, the unknown nodes among them,

@@ -97,7 +97,16 @@ def assemble_problem(prob) -> SGSystem:
     """Assemble from an input record with the fields dim, nx, ny, h, bc, s,
     r, k0, kl, f (the seeded workload generators produce such records)."""
     return assemble(prob.dim, prob.nx, prob.ny, prob.h, prob.bc, prob.s, prob.r,
-                    prob.k0, prob.kl, prob.f)
+                    prob.k0, prob.kl, source_nodes(prob))
+
+
+def source_nodes(prob) -> np.ndarray:
+    """The record's source f at the nodes, plus its unit point source
+    (``prob.point``, if any) discretised as App. A.3 states."""
+    f = np.asarray(prob.f, dtype=float).reshape(-1).copy()
+    if getattr(prob, "point", None) is not None:
+        f = f + fd.point_source(prob.dim, prob.nx, prob.ny, prob.h, prob.point)
+    return f
 
 
 def csl_matrix(sys: SGSystem, beta: float) -> sp.csr_matrix:

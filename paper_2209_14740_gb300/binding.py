@@ -36,7 +36,7 @@ class SgDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("h", C.c_double),
                 ("bc", C.c_int * 4), ("s", C.c_int), ("r", C.c_int),
                 ("k0", C.POINTER(C.c_double)), ("kl", C.POINTER(C.c_double)), ("f", C.POINTER(C.c_double)),
-                ("beta", C.c_double)]
+                ("beta", C.c_double), ("point_source", C.c_int), ("point_x", C.c_double), ("point_y", C.c_double)]
 
 
 class SgInfo(C.Structure):
@@ -231,6 +231,11 @@ class SG:
         d.kl = kl.ctypes.data_as(dp) if kl.size else None
         d.f = f.ctypes.data_as(dp)
         d.beta = float(getattr(prob, "beta", 0.5))
+        pt = getattr(prob, "point", None)
+        if pt is not None:
+            d.point_source = 1
+            d.point_x = float(pt[0])
+            d.point_y = float(pt[1]) if len(pt) > 1 else 0.0
         h = C.c_void_p()
         _check(lib.sg_assemble(C.byref(d), _stream(stream), C.byref(h)))
         self.h = h

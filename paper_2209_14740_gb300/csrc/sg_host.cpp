@@ -455,6 +455,9 @@ sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
       return fail(SG_EINVAL, "grid too large (at most 2^30 nodes)");
     if (!D.k0 || (D.s > 0 && !D.kl)) return fail(SG_EINVAL, "NULL wavenumber field");
     if (!std::isfinite(D.beta)) return fail(SG_EINVAL, "beta not finite");
+    if (D.point_source && (!(D.point_x >= 0.0 && D.point_x <= 1.0) ||
+                           (D.dim == 2 && !(D.point_y >= 0.0 && D.point_y <= 1.0))))
+      return fail(SG_EINVAL, "point source outside the unit interval / square");
 
     auto* h = new sg_handle();
     h->dim = D.dim; h->nx = D.nx; h->ny = D.dim == 2 ? D.ny : 1; h->h = D.h; h->beta = D.beta;
@@ -503,6 +506,24 @@ sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
         h->b0[u] = (xabs ? 0.5 : 1.0) * (yabs ? 0.5 : 1.0) * f;
       }
     if (!(kmin > 0)) { delete h; return fail(SG_EINVAL, "k(x, xi) must be positive for all xi (k_0 - sum|k_l| <= 0)"); }
+    if (D.point_source) {
+      // App. A.3: delta(x - a) becomes 1/h^dim at the node closest to a (the
+      // smaller index on a tie; the small guard keeps an exact tie from being
+      // split by the rounding of a / h), weighted like f by the D_2 weights
+      auto nearest = [&](double a, int nodes_dir) {
+        const int j = (int)std::ceil(a / D.h - 0.5 - 1e-9);
+        return std::min(std::max(j, 0), nodes_dir - 1);
+      };
+      const int iu = nearest(D.point_x, D.nx) - h->offx;
+      const int ju = D.dim == 2 ? nearest(D.point_y, h->ny) - h->offy : 0;
+      if (iu >= 0 && iu < h->mx && ju >= 0 && ju < h->my) {
+        const bool xabs = (iu == 0 && h->bc[0] == SG_BC_ABSORBING) || (iu == h->mx - 1 && h->bc[1] == SG_BC_ABSORBING);
+        const bool yabs = D.dim == 2 && ((ju == 0 && h->bc[2] == SG_BC_ABSORBING) ||
+                                         (ju == h->my - 1 && h->bc[3] == SG_BC_ABSORBING));
+        const double val = D.dim == 2 ? 1.0 / (D.h * D.h) : 1.0 / D.h;
+        h->b0[(size_t)iu + (size_t)h->mx * ju] += (xabs ? 0.5 : 1.0) * (yabs ? 0.5 : 1.0) * val;
+      }
+    }
     h->kbar = 0.5 * (k0min + k0max);
     h->specialised = matvec_is_specialised(h->s, h->r) ? 1 : 0;
     h->separable = (k0max - k0min) <= 1e-13 * k0max;

@@ -26,10 +26,15 @@ numpy.random.default_rng(seed)):
     unknowns.
 * ``batch_64``: 64 problems with g ~ U{63..255}, kbar ~ U[10, 40],
   sigma ~ U[0.05, 0.2], s ~ U{2, 3, 4}, degree ~ U{2, 3}.
-* ``paper_1d``: the 1D experiment of Sec. 6 (absorbing at both ends, point
-  source at x = 1/2, k = (1 + theta xi) kbar, mesh rule with maxk = kbar).
+* ``paper_1d``: the 1D experiment of Sec. 6 (absorbing at both ends, unit
+  point source at x = 1/2, k = (1 + theta xi) kbar) on q interior nodes; the
+  caller picks q (Sec. 6 takes it from its mesh rule with maxk = kbar, e.g.
+  q = 127 for kbar = 50).
 * ``wedge``: the 2D experiment of Sec. 7 (three layers with k_1 = 30,
-  k_2 = 15, k_3 = 20, theta = 0.1, point source at the centre).
+  k_2 = 15, k_3 = 20, theta = 0.1, unit point source at the centre).
+
+Point sources are described by their location only (``Problem.point``); each
+consumer discretises the Dirac distribution itself (App. A.3).
 * ``random_problem``: small random positive fields for parity tests.
 
 The paper measures on analytic workloads only (no dataset); these recipes
@@ -38,7 +43,7 @@ stand in for them.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from math import ceil, log2, pi
+from math import pi
 
 import numpy as np
 
@@ -61,6 +66,7 @@ class Problem:
     f: np.ndarray        # (nx*ny,) float64
     beta: float = 0.5
     meta: dict = field(default_factory=dict)
+    point: tuple | None = None   # location of a unit point source delta(x - a), added to f
 
     @property
     def nodes(self) -> int:
@@ -139,23 +145,14 @@ def warmstart_problem(p, g: int = 127, s: int = 3, r: int = 3) -> Problem:
     return helmholtz_2d(g, s, r, kbar, sigma, lc=lc, xs=xs, ys=ys)
 
 
-def mesh_q(maxk: float) -> int:
-    lev = max(ceil(log2((15.0 * maxk) / (2.0 * pi))), 1)
-    return 2 ** lev - 1
-
-
-def paper_1d(kbar: float = 50.0, theta: float = 0.1, m: int = 3, q: int | None = None,
-             beta: float = 0.5) -> Problem:
-    q = mesh_q(kbar) if q is None else q
+def paper_1d(kbar: float, theta: float, m: int, q: int, beta: float = 0.5) -> Problem:
     nx = q + 2
     h = 1.0 / (q + 1)
     k0 = np.full(nx, kbar)
     kl = np.full((1, nx), theta * kbar)
-    f = np.zeros(nx)
-    f[(q + 1) // 2] = 1.0 / h
-    return Problem("paper_1d_k%g_t%g_m%d" % (kbar, theta, m), 1, nx, 1, h,
-                   (ABSORBING, ABSORBING, DIRICHLET, DIRICHLET), 1, m, k0, kl, f, beta=beta,
-                   meta=dict(kbar=kbar, theta=theta, q=q))
+    return Problem("paper_1d_k%g_t%g_m%d_q%d" % (kbar, theta, m, q), 1, nx, 1, h,
+                   (ABSORBING, ABSORBING, DIRICHLET, DIRICHLET), 1, m, k0, kl, np.zeros(nx), beta=beta,
+                   meta=dict(kbar=kbar, theta=theta, q=q), point=(0.5,))
 
 
 def wedge(q: int = 127, theta: float = 0.1, r: int = 3, k=(30.0, 15.0, 20.0), beta: float = 0.5) -> Problem:
@@ -170,11 +167,9 @@ def wedge(q: int = 127, theta: float = 0.1, r: int = 3, k=(30.0, 15.0, 20.0), be
     for l in range(3):
         k0[regs[l]] = k[l]
         kl[l, regs[l]] = theta * k[l]
-    f = np.zeros(g * g)
-    t = (q + 1) // 2
-    f[t + g * t] = 1.0 / (1.0 / (q + 1)) ** 2
     return Problem("wedge_q%d_t%g_r%d" % (q, theta, r), 2, g, g, 1.0 / (q + 1),
-                   (ABSORBING,) * 4, 3, r, k0, kl, f, beta=beta, meta=dict(theta=theta))
+                   (ABSORBING,) * 4, 3, r, k0, kl, np.zeros(g * g), beta=beta, meta=dict(theta=theta),
+                   point=(0.5, 0.5))
 
 
 def random_problem(seed: int, dim: int = 2, g: int = 12, s: int = 2, r: int = 2,

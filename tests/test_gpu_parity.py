@@ -43,7 +43,7 @@ def problems():
     D, A = inputs.DIRICHLET, inputs.ABSORBING
     return [
         inputs.helmholtz_1d_c1(n_unknowns=37, r=5),
-        inputs.paper_1d(10.0, 0.1, 3),
+        inputs.paper_1d(10.0, 0.1, 3, q=31),          # q from the Sec. 6 mesh rule at kbar = 10
         inputs.random_problem(31, dim=1, g=150, s=1, r=8, bc=(A, A, D, D)),
         inputs.random_problem(32, dim=2, g=13, s=2, r=2),
         inputs.random_problem(33, dim=2, g=11, s=3, r=3, bc=(D, D, D, D)),
@@ -116,6 +116,33 @@ def test_rhs(B):
     np.testing.assert_array_equal(b32.cpu().numpy(), ref.b.astype(np.complex64))
 
 
+def test_rhs_point_source(B):
+    """Point sources (App. A.3) are discretised by the library (sg_desc's
+    point fields) and by the oracle (oracle.fd.point_source) independently;
+    the two right-hand sides must agree bit for bit: odd and even q (the
+    midpoint and the tie broken towards the smaller node), 1D and 2D, a
+    general location, a source on an absorbing edge (weight 1/2), a
+    distributed f added to it, and a source on an eliminated Dirichlet node."""
+    cases = [inputs.paper_1d(50.0, 0.1, 3, q=127), inputs.paper_1d(20.0, 0.1, 2, q=30),
+             inputs.wedge(63, 0.1, 2), inputs.wedge(62, 0.1, 2)]
+    p = inputs.random_problem(50, dim=2, g=14, s=2, r=2)
+    p.point = (0.31, 0.77)
+    cases.append(p)
+    p = inputs.random_problem(51, dim=2, g=14, s=2, r=2)
+    p.point = (0.0, 0.42)                 # on the absorbing edge x = 0
+    cases.append(p)
+    p = inputs.random_problem(52, dim=2, g=12, s=1, r=2, bc=(inputs.DIRICHLET,) * 4)
+    p.point = (1.0, 0.5)                  # on an eliminated Dirichlet node: no contribution
+    cases.append(p)
+    for pr in cases:
+        ref = sg.assemble_problem(pr)
+        op = B.SG(pr)
+        b = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.rhs(b, B.FP64)
+        np.testing.assert_array_equal(b.cpu().numpy(), ref.b, err_msg=pr.name)
+        op.close()
+
+
 PREC_CASES = [0, 1, 2, 3, 7, 8, 9, 10, 12]   # 1D, or 2D with constant k_0 (index 3 is skipped)
 
 
@@ -157,13 +184,24 @@ def test_precond_1d_long_lines(B, n_unknowns):
     """1D lines too long for the shared-memory sweep (FP64 above ~2,500
     unknowns, FP32 above ~5,000): the pivoted tridiagonal solve runs from
     global memory, out of place through the scratch vector when R = Z.
-    Against SuperLU's block solve, both blocks, in and out of place."""
+    Against SuperLU's block solve, both blocks, in and out of place.  The
+    blocks grow ill-conditioned with n (kappa_1 = 1.7e6 and 7e6 for the mean
+    block at 3,000 and 6,000 unknowns), so the FP32 forward error is held to
+    kappa_1 u32 (measured 1.8e-3 and 5.7e-3 against bounds 0.10 and 0.42) and
+    its normwise backward error ||S z - r|| / (|| |S| |z| || + ||r||) to 1e-6."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
     pr = inputs.helmholtz_1d_c1(n_unknowns=n_unknowns, kbar=20.0, sigma=0.1, r=3)
     ref = sg.assemble_problem(pr)
     op = B.SG(pr)
     for kind in (1, 2):
         blk = ref.S0 if kind == 1 else sg.csl_mean_block(ref, pr.beta)
         M = krylov.BlockPrecond(blk, ref.P)
+        lu = spl.splu(sp.csc_matrix(blk))
+        n = blk.shape[0]
+        inv = spl.LinearOperator((n, n), matvec=lambda v: lu.solve(np.asarray(v, complex).ravel()),
+                                 rmatvec=lambda v: lu.solve(np.asarray(v, complex).ravel(), trans="H"), dtype=complex)
+        kappa1 = spl.norm(blk, 1) * spl.onenormest(inv)
         x = rand_vec(op.N, 300 + kind)
         zr = M(x)
         X = torch.from_numpy(x).to(DEV)
@@ -179,9 +217,16 @@ def test_precond_1d_long_lines(B, n_unknowns):
         Z32 = torch.empty_like(X32)
         op.precond(X32, Z32, kind, B.FP32)
         e32 = np.linalg.norm(Z32.cpu().numpy() - zr32) / np.linalg.norm(zr32)
+        z32 = Z32.cpu().numpy().astype(np.complex128)
         op.precond(X32, X32, kind, B.FP32)
         e32i = np.linalg.norm(X32.cpu().numpy() - zr32) / np.linalg.norm(zr32)
-        assert e32 < 2e-4 and e32i < 2e-4, (e32, e32i)
+        bound = kappa1 * 2.0 ** -24
+        print("1D n=%d kind %d: FP64 %.2e, FP32 %.2e (kappa_1 u32 = %.2e)" % (n_unknowns, kind, e64, e32, bound))
+        assert e32 <= bound and e32i <= bound, (e32, e32i, bound)
+        Zm = z32.reshape(ref.P, n).T
+        Rm = x32.astype(np.complex128).reshape(ref.P, n).T
+        back = np.linalg.norm(blk @ Zm - Rm) / (np.linalg.norm(abs(blk) @ np.abs(Zm)) + np.linalg.norm(Rm))
+        assert back <= 1e-6, back
     op.close()
 
 

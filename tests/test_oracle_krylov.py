@@ -4,7 +4,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import krylov, sg
+from oracle import fd, krylov, sg
 from paper_2209_14740_gb300 import inputs
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -21,7 +21,7 @@ def load_counts():
 
 @pytest.fixture(scope="module")
 def kbar50():
-    S = sg.assemble_problem(inputs.paper_1d(50.0, 0.1, 3))
+    S = sg.assemble_problem(inputs.paper_1d(50.0, 0.1, 3, q=fd.mesh_rule(50.0)))
     return S, krylov.direct(S.A, S.b)
 
 

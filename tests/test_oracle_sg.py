@@ -8,7 +8,7 @@ import scipy.linalg as sl
 import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
-from oracle import krylov, pc, sg
+from oracle import fd, krylov, pc, sg
 from paper_2209_14740_gb300 import inputs
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -59,7 +59,7 @@ def test_theta_zero_collapse():
     """Remark 6.1 / Corollary 3.3: with theta = 0, A = I_P (x) S(0) is block
     diagonal, the modes i >= 1 of the solution vanish and V_0 is the
     deterministic solution."""
-    pr = inputs.paper_1d(30.0, 0.0, 4)
+    pr = inputs.paper_1d(30.0, 0.0, 4, q=fd.mesh_rule(30.0))
     S = sg.assemble_problem(pr)
     A0 = sg.mean_value_matrix(S)
     assert abs(S.A - A0).max() == 0.0
@@ -80,7 +80,7 @@ def _spectrum(pr, beta=0.5):
 def test_spectrum_in_disk_absorbing():
     """Theorem 4.1(1) and Remark 4.2: eig(A M^-1) lies in |z - 1/2| <= 1/2 and
     outside |z - (1 - i beta/2)| < beta/2."""
-    ev = _spectrum(inputs.paper_1d(50.0, 0.1, 3))
+    ev = _spectrum(inputs.paper_1d(50.0, 0.1, 3, q=fd.mesh_rule(50.0)))
     assert np.max(np.abs(ev - 0.5)) <= 0.5 + 1e-9
     assert np.min(np.abs(ev - (1 - 0.25j))) >= 0.25 - 1e-9
 
@@ -108,7 +108,7 @@ def _cond(M):
 
 
 def _conds_for(kbar):
-    S = sg.assemble_problem(inputs.paper_1d(kbar, 0.1, 3))
+    S = sg.assemble_problem(inputs.paper_1d(kbar, 0.1, 3, q=fd.mesh_rule(kbar)))
     A = S.A.toarray()
     M = sg.csl_matrix(S, 0.5).toarray()
     A0 = sg.mean_value_matrix(S).toarray()
@@ -136,7 +136,7 @@ def test_cond_M_bound():
 
 def test_infnorm_ordering():
     """Sec. 6.3: ||A - A_0||_inf < ||A - M||_inf < ||A - M_0||_inf at kbar = 50."""
-    S = sg.assemble_problem(inputs.paper_1d(50.0, 0.1, 3))
+    S = sg.assemble_problem(inputs.paper_1d(50.0, 0.1, 3, q=fd.mesh_rule(50.0)))
     A0 = sg.mean_value_matrix(S)
     M = sg.csl_matrix(S, 0.5)
     M0 = sp.kron(sp.identity(S.P), sg.csl_mean_block(S, 0.5))

@@ -128,10 +128,12 @@ typedef struct {
   int separable;       /* 1 if k_0 is constant: 2D preconditioners available */
   int specialised;     /* 1 if a register-resident matvec kernel serves (s, r) */
   int fast_diag;       /* 1 if FP32 2D preconditioner applies use the fast diagonalisation
-                          (both directions transformed, tensor-core GEMMs) */
+                          (both directions transformed, tensor-core GEMMs; lines <= 320) */
   double eig_orth_err; /* separable 2D: max |Q^T Q - I| of the 1D pencils' eigenvector
                           factors (set-up rejects > 1e-10); 0 otherwise */
   double eig_kappa;    /* separable 2D: cond(Q) of those factors (set-up rejects > 100) */
+  int tf32_route;      /* 1 if SG_TF32 applies are available (separable 2D, any line length);
+                          the complex64 GMRES cycles then run flexible GMRES with them */
 } sg_info;
 
 /* Builds the SG operator of Theorem 3.4 / Theorems A.1, A.2, A.5, A.6:
@@ -165,8 +167,8 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
 /* Z = (I_P (x) S_blk)^-1 R for the chosen block (see sg_prec), one
  * factorisation applied to all P modes at once (the reshape of Sec. 6.3).
  * SG_PREC_NONE copies R to Z.  R and Z: device, N complex; Z may equal R
- * (in place).  prec SG_FP64, SG_FP32 or SG_TF32 (complex64 data; 2D problems
- * with lines of at most 320 nodes only, SG_EUNSUPPORTED otherwise).
+ * (in place).  prec SG_FP64, SG_FP32 or SG_TF32 (complex64 data; separable
+ * 2D problems only, SG_EUNSUPPORTED otherwise).
  * Returns SG_EUNSUPPORTED for 2D problems whose k_0 varies in space (no
  * separable factorisation).  Asynchronous: a bounded wait that gives up
  * inside a tensor-core transform sets the handle's device flag, which the

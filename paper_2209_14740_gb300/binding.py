@@ -43,7 +43,8 @@ class SgInfo(C.Structure):
     _fields_ = [("dim", C.c_int), ("mx", C.c_int), ("my", C.c_int), ("n", C.c_int), ("P", C.c_int),
                 ("N", C.c_longlong), ("s", C.c_int), ("r", C.c_int), ("terms", C.c_int),
                 ("coupling_nnz", C.c_int), ("separable", C.c_int), ("specialised", C.c_int),
-                ("fast_diag", C.c_int), ("eig_orth_err", C.c_double), ("eig_kappa", C.c_double)]
+                ("fast_diag", C.c_int), ("eig_orth_err", C.c_double), ("eig_kappa", C.c_double),
+                ("tf32_route", C.c_int)]
 
 
 class SgGmresOpts(C.Structure):

@@ -503,7 +503,7 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
   const int mx = h->mx, my = h->my, P = h->P;
   const long long plane = (long long)mx * my;
   if constexpr (sizeof(T) == 4) {
-    if (h->fd) return fd_apply(h, which, R, Z, st, skip, in_scale, tmp, tmp2, true);
+    if (h->fd && h->fd_fp32) return fd_apply(h, which, R, Z, st, skip, in_scale, tmp, tmp2, true);
   }
   const C2<T>* Q;
   const C2<T>* Qt;

@@ -224,6 +224,7 @@ struct TcArgs {
   const float* Bhi;    // [n tile][stage][BN x 32 core-matrix tile]
   const float* Blo;
   int Nc;              // complex output columns
+  int ntiles;          // column tiles; CTA b owns column tile b % ntiles of row tile b / ntiles
   float2* C;
   long long ldc;
   int mode, MB;
@@ -301,9 +302,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const int m0 = blockIdx.x * BM;
-  const float* Bh = a.Bhi + (size_t)blockIdx.y * a.nks * (BN * BK);
-  const float* Bl = a.Blo + (size_t)blockIdx.y * a.nks * (BN * BK);
+  // the column tiles of one row tile are consecutive CTAs, so they run close
+  // together and read that row tile of X from L2 rather than from HBM
+  const int ctile = (int)(blockIdx.x % (unsigned)a.ntiles);
+  const int m0 = (int)(blockIdx.x / (unsigned)a.ntiles) * BM;
+  const float* Bh = a.Bhi + (size_t)ctile * a.nks * (BN * BK);
+  const float* Bl = a.Blo + (size_t)ctile * a.nks * (BN * BK);
   auto copy_b = [&](int t) {
     const uint32_t bar = bfull0 + 8 * (t % NBS);
     const uint32_t dst = s_base + OFF_B + (t % NBS) * L::NBP * B_TILE;
@@ -337,7 +341,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
     const int lg = warp & 3, chalf = warp >> 2;
     const int row = lg * 32 + lane, m = m0 + row;
     const bool mok = m < a.M;
-    const int nq0 = blockIdx.y * (BN / 2) + chalf * (HALF / 2);   // first complex column of this warp
+    const int nq0 = ctile * (BN / 2) + chalf * (HALF / 2);   // first complex column of this warp
     float2 ev[HALF / 2];
     if (a.E) {
       const int mr = (mok ? m : 0) % a.e_mod;
@@ -526,7 +530,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
         // row-major: all loader warps write the staged rows, consecutive
         // lanes on consecutive columns
         loader_sync();
-        const int n0 = blockIdx.y * (BN / 2);
+        const int n0 = ctile * (BN / 2);
         for (int idx = tid; idx < BM * (BN / 2); idx += NLOAD) {
           const int rr = idx / (BN / 2), q = idx % (BN / 2);
           const int mm = m0 + rr, n = n0 + q;
@@ -733,6 +737,7 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   a.Bhi = B.hi;
   a.Blo = B.lo;
   a.Nc = B.ndim;
+  a.ntiles = B.ntiles;
   a.C = C;
   a.ldc = ldc;
   a.mode = mode;
@@ -746,7 +751,9 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   // programmatic dependent launch: may start while the previous kernel in
   // the stream finishes (the kernel waits for it before touching its data)
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((M + tc::BM - 1) / tc::BM, B.ntiles);
+  const long long ctas = (long long)((M + tc::BM - 1) / tc::BM) * B.ntiles;
+  if (ctas <= 0 || ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3(tc::THREADS);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -766,7 +773,7 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
     return v;
   }();
   const bool tmax = !split && xmap != nullptr && num_sms > 0 &&
-                    (long long)cfg.gridDim.x * cfg.gridDim.y >= num_sms;
+                    (long long)cfg.gridDim.x >= num_sms;
   const CUtensorMap& m = tmax ? *xmap : none;
   cudaError_t e;
   if (B.bn == 128 && split) {

@@ -323,32 +323,16 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
     }
     cudaFree(d_gd); cudaFree(d_ls); cudaFree(d_go);
     SG_CUDA_TRY(cudaMalloc(&h->d_tmp2, (size_t)h->N * sizeof(double2)));
-    // Fast diagonalisation for the FP32 applies: also diagonalise the y
-    // pencil (the same matrix as x on a square grid).  Four GEMMs replace
-    // two GEMMs and mx * P sequential tridiagonal solves; worth it while
-    // the lines are short (the GEMM work grows with mx^2).
-    if (mx > kFdMaxLine || my > kFdMaxLine) {
-      // longer lines keep the tridiagonal sweeps along y, but the two x
-      // transforms of the FP32 apply still run on the tensor cores
-      std::vector<cd> qx((size_t)mx * mx), qxt((size_t)mx * mx);
-      for (int a = 0; a < mx; ++a)
-        for (int b = 0; b < mx; ++b) {
-          const cd v = Q[(size_t)a * mx + b] / std::sqrt(px.d[a]);
-          qx[(size_t)a * mx + b] = v;
-          qxt[(size_t)b * mx + a] = v;
-        }
-      const std::vector<cd>* facs[2] = {&qx, &qxt};
-      const int slot[2] = {0, 3};
-      const int bn = tc_tile_width((long long)h->P * my, mx, h->num_sms);
-      for (int t = 0; t < 2; ++t) {
-        TcOperand op = tc_make_operand(*facs[t], mx, mx, bn);
-        TcDevOperand& d = h->tcB[slot[t]];
-        d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
-        if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()))
-          return fail(SG_ENOMEM, "precond upload");
-      }
-    }
-    if (mx <= kFdMaxLine && my <= kFdMaxLine) {
+    // Fast diagonalisation: also diagonalise the y pencil (the same matrix as
+    // x on a square grid), so the block inverse is four dense transforms on
+    // the tensor cores.  The plain-TF32 form (SG_TF32, the preconditioner of
+    // the complex64 GMRES cycles) always takes it.  The FP32-accurate form
+    // (3xTF32, three MMAs per product) takes it only while the lines are
+    // short: four such GEMMs replace two GEMMs and mx * P sequential
+    // tridiagonal solves, and the GEMM work grows with mx^2; longer lines
+    // keep the y sweeps and use the x factors (slots 0 and 3) alone.
+    h->fd_fp32 = mx <= kFdMaxLine && my <= kFdMaxLine;
+    {
       std::vector<cd> lamy, Qy;
       bool ok = true;
       if (my == mx) {
@@ -611,7 +595,8 @@ sg_status sg_get_info(const sg_handle* h, sg_info* info) {
     info->coupling_nnz = (int)h->col.size() + h->P;
     info->separable = h->separable ? 1 : 0;
     info->specialised = h->specialised;
-    info->fast_diag = h->fd ? 1 : 0;
+    info->fast_diag = h->fd && h->fd_fp32 ? 1 : 0;
+    info->tf32_route = h->fd ? 1 : 0;
     info->eig_orth_err = h->eig_orth_err;
     info->eig_kappa = h->eig_kappa;
     return SG_OK;
@@ -658,7 +643,7 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
       return fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
     if (prec == SG_TF32) {
       if (h->dim != 2 || !h->fd)
-        return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with the fast-diagonalisation route (lines <= 320)");
+        return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with constant k_0 (the fast-diagonalisation route)");
       SG_CUDA_TRY(launch_precond_tf32(h, which, (const float2*)R, (float2*)Z, st, nullptr, nullptr));
     } else if (prec == SG_FP64) {
       SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));

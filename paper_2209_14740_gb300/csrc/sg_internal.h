@@ -191,7 +191,8 @@ struct sg_handle {
   double eig_kappa = 0.0;            // cond(Q) of the eigenvector factors (<= 100 accepted)
   // 2D fast diagonalisation (FP32 applies): both directions transformed,
   // S^-1 = (Qhat_y (x) Qhat_x) diag(1 / (lambda_y,j + lambda_x,i + shift)) (Qhat_y (x) Qhat_x)^T
-  bool fd = false;
+  bool fd = false;                   // fast-diagonalisation factors built (SG_TF32 route)
+  bool fd_fp32 = false;              // FP32 (3xTF32) applies use them too (lines <= 320)
   float2* d_Qy32 = nullptr;          // Qhat_y = D_y^-1/2 Q_y, row-major my x my
   float2* d_Qyt32 = nullptr;         // Qhat_y^T
   float2* d_Linv32[2] = {nullptr, nullptr};   // [block] my x mx: 1 / (lambda_y,j + lambda_x,i + shift)

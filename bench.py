@@ -2,23 +2,29 @@
 """Benchmark of the SG Helmholtz GMRES hot path on GB300.
 
 Headline (`value`): SG-GMRES solves per second to relative residual 1e-8
-(||b - A x|| / ||b|| computed in FP64) on the 2D workload: 127 x 127 nodes
-(h = 1/126), absorbing boundary, k = 30 (1 + 0.15 sum_{l<=3} l^-1 cos(l pi x)
-cos(l pi y) xi_l), Legendre chaos of total degree 3 (P = 20), Gaussian source
-at the centre: 322,580 complex unknowns; restarted GMRES(50), mean-value
-preconditioner, zero initial guess.  The timed step is one full solve of the
-mixed-precision path (complex64 Arnoldi inside FP64 iterative refinement)
-with b resident in HBM.  The preconditioner factorisation (done once per
-system in sg_assemble) is reported separately as setup_ms.
+(||b - A x|| / ||b|| computed in FP64) on the largest single-GPU workload:
+511 x 511 nodes (h = 1/510), absorbing boundary,
+k = 60 (1 + 0.1 sum_{l<=6} l^-1 cos(l pi x) cos(l pi y) xi_l), Legendre chaos
+of total degree 3 in 6 variables (P = 84), Gaussian source at the centre:
+21,934,164 complex unknowns.  The timed step is one full solve of the
+mixed-precision path (complex64 GMRES(30) cycles inside FP64 iterative
+refinement, mean-value preconditioner, zero initial guess) with b resident
+in HBM.  The preconditioner set-up (once per system, in sg_assemble) is
+reported separately as setup_ms.
 
-Beside it the line reports: the plain FP64 GPU GMRES on the same workload,
-the end-to-end number through the C ABI with host buffers (host_io), the SG
-matvec bandwidth on the 511 x 511, s = 6, degree 3 workload (21.9 M unknowns,
-complex64), the roofline of the dominant kernel, clocks sampled during the
-timed region, and the CPU oracle timed on the host (cpu_baseline).
+Beside it the line reports: the plain FP64 GPU GMRES(30) on the same system
+(`fp64`, with the FP64 kernels against the measured FP64 FMA rate), the error
+of every mixed result against an FP64 GPU solve to 1e-12 (`error`), the
+end-to-end number through the C ABI with host buffers (`e2e`), the roofline
+of the dominant kernel (`roofline`), the SG matvec bandwidth (`matvec`), the
+127 x 127 workload (`cfg2_127`), the 1D workload, the batched and learned
+warm-start legs, clocks sampled during the timed region, and the CPU oracle
+(`cpu_baseline`) on a bounded sample.
 
---impl reference times the CPU oracle (oracle/, plain FP64 NumPy/SciPy) on the
-same workload, one solve per step.
+--impl reference times the CPU oracle (oracle/, plain FP64 NumPy/SciPy) on
+the same metric: each step a bounded sample (Arnoldi steps of its GMRES(30)
+on the 127 x 127 member of the workload family), extrapolated as stated in
+the line.
 
 Multi-GPU: the solves are independent (replicas only): each rank solves its
 own copy, value = total solves / max rank time, scaling "weak".
@@ -37,10 +43,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "SG-GMRES solves/s to rel.res 1e-8 (mixed precision, GMRES(50), mean-value preconditioner)"
+METRIC = ("SG-GMRES solves/s to rel.res 1e-8 (mixed precision: complex64 GMRES(30) in FP64 refinement, "
+          "mean-value preconditioner)")
 UNIT = "solves/s"
-WORKLOAD = {"workload": "helmholtz_2d_127x127_s3_deg3", "nodes": "127x127", "h": "1/126", "P": 20,
-            "unknowns": 322580, "kbar": 30.0, "sigma": 0.15, "restart": 50, "tol": 1e-8,
+WORKLOAD = {"workload": "helmholtz_2d_511x511_s6_deg3", "nodes": "511x511", "h": "1/510", "s": 6, "degree": 3,
+            "P": 84, "unknowns": 21934164, "kbar": 60.0, "sigma": 0.1, "restart": 30, "tol": 1e-8,
             "preconditioner": "mean-value I(x)S(xi_bar)", "source": "gaussian w=0.02 at (0.5,0.5)"}
 MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
@@ -53,6 +60,13 @@ MATVEC_TRAFFIC = {"sha256": "0e5a4679d2e0f084f9f73ce6af95304f6010fe7044be5c825df
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
+# The oracle's sample: the 127 x 127 member of the workload family (same s,
+# degree, kbar, sigma; N = 1,354,836), Arnoldi steps of its GMRES(30).
+ORACLE_SAMPLE_G = 127
+ORACLE_SAMPLE_STEPS = 10
+# Arnoldi steps of the plain FP64 GPU GMRES(30) on the 511 x 511 system
+# (measured: used by the reference arm, which runs without a GPU)
+FP64_STEPS_511 = 40
 
 
 def nvtx(torch, name):
@@ -156,23 +170,42 @@ def max_over_ranks(v: float, world: int) -> float:
     return replicas.max_over_ranks(v, world)
 
 
-def oracle_solve_seconds(repeats: int = 1):
-    """The CPU oracle on the same workload: GMRES(50) with the mean-value
-    block preconditioner (SuperLU of S(xi_bar) factored once, as the GPU
-    path's sg_assemble does), zero initial guess, tol 1e-8."""
+def oracle_sample_setup():
+    """Assemble the oracle's explicit SG system of the sample (the 127 x 127
+    member of the workload family) and factor its mean-value block once (as
+    sg_assemble does on the GPU side)."""
     from oracle import krylov, sg
     from paper_2209_14740_gb300 import inputs
-    pr = inputs.config_2d_127()
+    pr = inputs.helmholtz_2d(ORACLE_SAMPLE_G, 6, 3, 60.0, 0.1)
     S = sg.assemble_problem(pr)
-    M = krylov.BlockPrecond(S.S0, S.P)
-    times, its = [], []
-    for _ in range(repeats):
-        t0 = time.perf_counter()
-        res = krylov.gmres(S.A, S.b, M, restart=50, tol=1e-8, maxit=2000)
-        times.append(time.perf_counter() - t0)
-        its.append(res.iters)
-        assert res.converged
-    return times, its
+    return S, krylov.BlockPrecond(S.S0, S.P)
+
+
+def oracle_sample_step_seconds(S, M, steps=ORACLE_SAMPLE_STEPS):
+    """Mean seconds per Arnoldi step of the oracle's GMRES(30) (mean-value
+    block preconditioner, CGS2, Givens) over the first `steps` steps of a
+    cycle, plus its closing true-residual evaluation."""
+    from oracle import krylov
+    t0 = time.perf_counter()
+    krylov.gmres(S.A, S.b, M, restart=30, tol=1e-300, maxit=steps)
+    return (time.perf_counter() - t0) / steps
+
+
+def oracle_extrapolate(step_s, n_sample, steps_511):
+    """Oracle seconds per solve of the 511 x 511 system: step time x ratio of
+    unknowns x Arnoldi steps of the solve.  The oracle's costs per step grow at
+    least linearly in the unknowns (measured 63^2 -> 127^2 -> 255^2: 0.23,
+    0.61, 2.69 s), and its CGS2 share grows with the step index, so this is an
+    optimistic estimate of the oracle."""
+    return step_s * (WORKLOAD["unknowns"] / n_sample) * steps_511
+
+
+def oracle_sample_text(n_sample, steps_511, samples):
+    return ("%d x %d Arnoldi steps of the oracle's GMRES(30) on the %dx%d member of the workload family "
+            "(s=6, degree 3, kbar=60, sigma=0.1; N=%d), mean step time x %.2f (unknowns 511^2 / %d^2) x %d "
+            "(Arnoldi steps of the FP64 solve of the 511^2 system); SuperLU single threaded, NumPy BLAS on all "
+            "cores" % (samples, ORACLE_SAMPLE_STEPS, ORACLE_SAMPLE_G, ORACLE_SAMPLE_G, n_sample,
+                       WORKLOAD["unknowns"] / n_sample, ORACLE_SAMPLE_G, steps_511))
 
 
 def run_reference(args):
@@ -180,20 +213,22 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    S, M = oracle_sample_setup()
+    n_sample = S.A.shape[0]
     for _ in range(args.warmup):
-        oracle_solve_seconds(1)
-    times, its = oracle_solve_seconds(args.steps)
-    ms = 1000.0 * statistics.mean(times)
+        oracle_sample_step_seconds(S, M)
+    per_solve = [oracle_extrapolate(oracle_sample_step_seconds(S, M), n_sample, FP64_STEPS_511)
+                 for _ in range(args.steps)]
+    ms = 1000.0 * statistics.mean(per_solve)
     value = 1000.0 / ms
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": dict(WORKLOAD, oracle="NumPy/SciPy FP64 GMRES(50) + SuperLU block preconditioner",
+            "config": dict(WORKLOAD, oracle="NumPy/SciPy FP64 GMRES(30) + SuperLU block preconditioner",
                            world_size=world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d full oracle solves of the workload (%s iterations each)"
-                                       % (args.steps, its[0])},
+                             "sample": oracle_sample_text(n_sample, FP64_STEPS_511, args.steps)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line))
@@ -241,33 +276,6 @@ def cfg1_leg(B, torch, dev):
         o.close()
     op.close()
     return out
-
-
-def cfg3_leg(B, torch, dev):
-    """511 x 511, s = 6, degree 3 (P = 84, N = 21,934,164): mixed-precision
-    GMRES(30) to relres 1e-8, mean-value preconditioner (tridiagonal path:
-    lines of 511 unknowns), one warm-up and two timed solves."""
-    from paper_2209_14740_gb300 import inputs
-    op = B.SG(inputs.config_2d_511())
-    b = torch.empty(op.N, dtype=torch.complex128, device=dev)
-    op.rhs(b, B.FP64)
-    x = torch.zeros_like(b)
-    kw = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, maxit=3000)
-    info = op.gmres(b, x, **kw)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    stream = torch.cuda.current_stream()
-    e0.record(stream)
-    for _ in range(2):
-        info = op.gmres(b, x, **kw)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / 2
-    op.close()
-    return {"workload": "helmholtz_2d_511x511_s6_deg3 (P=84, N=21,934,164), mixed GMRES(30), mean-value, tol 1e-8",
-            "ms": ms, "solves_per_s": 1000.0 / ms, "iterations": info["iters"], "outer": info["outer"],
-            "relres": info["relres"], "converged": bool(info["status"] == B.SG_OK)}
 
 
 def learned_leg(args, B, torch, dev):
@@ -349,11 +357,109 @@ def learned_leg(args, B, torch, dev):
                                   and all(i["relres"] <= 1e-8 for i in inf_l))}
 
 
+def timed_solves(op, b, x, steps, flush, stream, torch, **kw):
+    """`steps` solves, each timed with CUDA events on `stream`, L2 flushed
+    before each."""
+    times, infos = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = op.gmres(b, x, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+    return times, infos
+
+
+def event_ms(torch, stream, fn, reps):
+    """Mean milliseconds of fn() over reps calls, CUDA events on `stream`."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def rel_err(torch, a, ref):
+    return float(torch.linalg.vector_norm(a - ref) / torch.linalg.vector_norm(ref))
+
+
+def cfg2_leg(B, torch, dev, flush, stream):
+    """127 x 127, s = 3, degree 3 (P = 20, N = 322,580): mixed GMRES(50) and
+    plain FP64 GMRES(50), mean-value preconditioner, tol 1e-8."""
+    from paper_2209_14740_gb300 import inputs
+    op = B.SG(inputs.config_2d_127())
+    b = torch.empty(op.N, dtype=torch.complex128, device=dev)
+    op.rhs(b, B.FP64)
+    x = torch.zeros_like(b)
+    out = {"workload": "helmholtz_2d_127x127_s3_deg3 (P=20, N=322,580), GMRES(50), mean-value, tol 1e-8"}
+    for name, mode, reps in (("mixed", B.MIXED, 10), ("fp64", B.FP64, 3)):
+        kw = dict(restart=50, tol=1e-8, prec=B.PREC_MEAN, mode=mode)
+        for _ in range(3):
+            op.gmres(b, x, **kw)
+        t, inf = timed_solves(op, b, x, reps, flush, stream, torch, **kw)
+        ms = statistics.mean(t)
+        out[name] = {"ms": ms, "solves_per_s": 1000.0 / ms, "iterations": inf[-1]["iters"],
+                     "outer": inf[-1]["outer"], "relres": inf[-1]["relres"],
+                     "converged": all(i["status"] == B.SG_OK for i in inf)}
+    out["mixed_speedup_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    op.close()
+    return out
+
+
+def batched_leg(B, torch, dev):
+    """64 heterogeneous systems (g ~ U{63..255}, kbar ~ U[10,40], sigma ~
+    U[0.05,0.2], s ~ U{2,3,4}, degree ~ U{2,3}): mixed batched solve against
+    plain FP64 one at a time."""
+    from paper_2209_14740_gb300 import inputs
+    probs = inputs.batch_64()
+    ops = [B.SG(p) for p in probs]
+    bs = []
+    for op in ops:
+        bb = torch.empty(op.N, dtype=torch.complex128, device=dev)
+        op.rhs(bb, B.FP64)
+        bs.append(bb)
+    xs = [torch.zeros_like(bb) for bb in bs]
+    kw = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, maxit=20000)
+    B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)          # warm-up (allocates workspaces)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st_b, inf_b = B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t1
+    ok_b = st_b == B.SG_OK and all(i["relres"] <= 1e-8 for i in inf_b)
+    for op, bb, xx in zip(ops, bs, xs):                        # warm-up of the FP64 workspaces
+        op.gmres(bb, xx, mode=B.FP64, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    inf_s = [op.gmres(bb, xx, mode=B.FP64, **kw) for op, bb, xx in zip(ops, bs, xs)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t1
+    ok_s = all(i["status"] == B.SG_OK for i in inf_s)
+    out = {"systems": len(ops), "workload": "64 systems: g ~ U{63..255}, kbar ~ U[10,40], "
+           "sigma ~ U[0.05,0.2], s ~ U{2,3,4}, degree ~ U{2,3} (P 6-35), GMRES(30), mean-value",
+           "unknowns_total": int(sum(op.N for op in ops)),
+           "mixed_batched_solves_per_s": len(ops) / t_batched,
+           "fp64_sequential_solves_per_s": len(ops) / t_seq,
+           "speedup_vs_fp64_sequential": t_seq / t_batched,
+           "all_converged": bool(ok_b and ok_s),
+           "iterations_mixed_total": int(sum(i["iters"] for i in inf_b)),
+           "iterations_fp64_total": int(sum(i["iters"] for i in inf_s))}
+    for op in ops:
+        op.close()
+    return out
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
-    from paper_2209_14740_gb300 import binding, inputs
+    from paper_2209_14740_gb300 import binding, inputs, replicas
 
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
@@ -362,17 +468,18 @@ def run_ours(args):
     B.load()
 
     # ---------------------------------------------------------------- set-up
-    pr = inputs.config_2d_127()
+    pr = inputs.config_2d_511()
     t0 = time.perf_counter()
     op = B.SG(pr)
     torch.cuda.synchronize()
     setup_ms = 1000 * (time.perf_counter() - t0)
-    N = op.N
+    N, n, P = op.N, op.n, op.P
+    info_h = op.info
     b = torch.empty(N, dtype=torch.complex128, device=dev)
     op.rhs(b, B.FP64)
     x = torch.zeros_like(b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2 (129 MB)
-    solve = dict(restart=50, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED)
+    solve = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, maxit=3000)
 
     for _ in range(args.warmup):
         op.gmres(b, x, **solve)
@@ -385,88 +492,55 @@ def run_ours(args):
     if rank == 0:
         clk.start()
     l0 = B.kernel_launches()
-    times, infos = [], []
     pushed = nvtx(torch, "timed")
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        info = op.gmres(b, x, **solve)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        infos.append(info)
+    times, infos = timed_solves(op, b, x, args.steps, flush, stream, torch, **solve)
     launches = B.kernel_launches() - l0
     nvtx_pop(torch, pushed)
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop() if rank == 0 else None
     ms = max_over_ranks(statistics.mean(times), world)
-    from paper_2209_14740_gb300 import replicas
     value = replicas.whole_job_rate(1.0, ms / 1000.0, world)   # one solve per step per rank
     ok = all(i["status"] == B.SG_OK and i["relres"] <= 1e-8 for i in infos)
-
-    # ---------------------------------------------------------------- plain FP64 GPU GMRES, same workload
-    fp64 = dict(solve, mode=B.FP64)
-    op.gmres(b, x, **fp64)
-    t64, i64 = [], None
-    for _ in range(max(2, min(args.steps, 5))):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        i64 = op.gmres(b, x, **fp64)
-        e1.record(stream)
-        e1.synchronize()
-        t64.append(e0.elapsed_time(e1))
-    fp64_ms = statistics.mean(t64)
+    x_mixed = x.clone()
 
     # ---------------------------------------------------------------- dominant kernel of the step
     # The preconditioner apply of the solve's complex64 cycles (SG_TF32) is
     # four launches of the tensor-core transform kernel (k_tc_cgemm, plain
-    # TF32 form), each a complex GEMM of (P*m) x m by m x m.  Timed on the
-    # solve's stream with CUDA events, 50 applies, L2 warm as in the solve
-    # (the vectors are L2-resident there too).
+    # TF32 form), complex GEMMs of (P my) x mx by mx x mx (x direction) and
+    # (P mx) x my by my x my (y direction).  Timed on the solve's stream with
+    # CUDA events, 20 applies.
     top = None
-    info_h = op.info
-    if info_h.get("fast_diag"):
+    if info_h.get("tf32_route"):
         Xp = torch.randn(N, dtype=torch.complex64, device=dev)
         Zp = torch.empty_like(Xp)
         for _ in range(3):
             op.precond(Xp, Zp, B.PREC_MEAN, B.TF32)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        reps = 50
+        reps = 20
         pushed = nvtx(torch, "precond")
-        e0.record(stream)
-        for _ in range(reps):
-            op.precond(Xp, Zp, B.PREC_MEAN, B.TF32)
-        e1.record(stream)
-        e1.synchronize()
+        t_apply = event_ms(torch, stream, lambda: op.precond(Xp, Zp, B.PREC_MEAN, B.TF32), reps)
         nvtx_pop(torch, pushed)
-        t_launch = e0.elapsed_time(e1) / (4 * reps)            # ms per k_tc_cgemm launch
-        m = info_h["mx"]
-        flops = 8.0 * op.P * m * m * m                          # complex GEMM: 8 real flop per complex MAC
+        mx, my = info_h["mx"], info_h["my"]
+        flops = 8.0 * P * (mx * my * mx * 2 + mx * my * my * 2) / 4      # mean over the four launches
+        t_launch = t_apply / 4
         peak_t, peak_kind_t = load_tensor_peak()
         ach = flops / (t_launch * 1e-3) / 1e12
-        top = {"kernel": "k_tc_cgemm<64, false, false> (2D preconditioner transform, tcgen05 TF32)", "bound": "tensor",
+        top = {"kernel": "k_tc_cgemm<128, false, *> (2D preconditioner transform, tcgen05 TF32)", "bound": "tensor",
                "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t, "traffic": None,
-               "peak_kind": peak_kind_t, "us_per_launch": 1000.0 * t_launch,
-               "flops_per_launch": flops, "units": "8*P*m^3 real flop per launch (m = 127, P = 20)"}
+               "peak_kind": peak_kind_t, "us_per_launch": 1000.0 * t_launch, "apply_ms": t_apply,
+               "flops_per_launch": flops,
+               "units": "8 P m^3 real flop per launch (complex GEMM of (P m) x m by m x m; m = 511, P = 84)"}
         del Xp, Zp
 
     # ---------------------------------------------------------------- end to end with host buffers
     bh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
     bh.copy_(b)
     xh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
-    # untimed warm-up of the host-buffer path (its first call pays one-time
-    # costs the device-resident solves above paid in their own warm-up)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, min(args.warmup, 2))):
         op.gmres(bh.numpy(), xh.numpy(), host_io=True, **solve)
     torch.cuda.synchronize()
     te = []
-    for _ in range(max(2, min(args.steps, 5))):
+    for _ in range(max(2, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -474,98 +548,89 @@ def run_ours(args):
         te.append(time.perf_counter() - t1)
         assert ie["status"] == B.SG_OK
     e2e_ms = 1000 * statistics.mean(te)
-    op.close()
+    x_e2e = torch.from_numpy(xh.numpy()).to(dev)
+    del bh, xh
+
+    # ---------------------------------------------------------------- plain FP64 GPU GMRES, same system
+    fp64_kw = dict(solve, mode=B.FP64)
+    op.gmres(b, torch.zeros_like(b), **dict(fp64_kw, maxit=1))       # FP64 workspace
+    x64 = torch.zeros_like(b)
+    t64, i64 = timed_solves(op, b, x64, 2 if not args.quick else 1, flush, stream, torch, **fp64_kw)
+    fp64_ms = statistics.mean(t64)
+    # reference solution for the error of every result: FP64 GPU GMRES(30) to 1e-12
+    x_ref = torch.zeros_like(b)
+    i_ref = op.gmres(b, x_ref, **dict(fp64_kw, tol=1e-12))
+    error = {"reference": "FP64 GPU GMRES(30) to relres 1e-12 (relres %.2e, %d Arnoldi steps)"
+                          % (i_ref["relres"], i_ref["iters"]),
+             "mixed": rel_err(torch, x_mixed, x_ref), "mixed_e2e": rel_err(torch, x_e2e, x_ref),
+             "fp64_tol_1e-8": rel_err(torch, x64, x_ref)}
+    del x_e2e
+
+    # FP64 kernels against the measured FP64 FMA rate of this GPU
+    fp64_peak = B.alu_peak(True)
+    fp32_peak = B.alu_peak(False)
+    X64 = torch.randn(N, dtype=torch.complex128, device=dev)
+    Z64 = torch.empty_like(X64)
+    op.precond(X64, Z64, B.PREC_MEAN, B.FP64)
+    t_ap64 = event_ms(torch, stream, lambda: op.precond(X64, Z64, B.PREC_MEAN, B.FP64), 3)
+    mx, my = info_h["mx"], info_h["my"]
+    fl_ap64 = 2 * 8.0 * P * my * mx * mx                     # the two x eigen-transforms (complex GEMMs)
+    op.matvec(X64, Z64, B.FP64)
+    t_mv64 = event_ms(torch, stream, lambda: op.matvec(X64, Z64, B.FP64), 3)
+    fl_mv64 = 4.0 * (info_h["coupling_nnz"] + 5 * P) * n    # real x complex products of a row, interior nodes
+    del X64, Z64
+    fp64 = {"solves_per_s": 1000.0 / fp64_ms, "ms": fp64_ms, "iterations": i64[-1]["iters"],
+            "relres": i64[-1]["relres"], "mixed_speedup": fp64_ms / ms * world,
+            "fp64_fma_peak_tflops": fp64_peak, "fp32_fma_peak_tflops": fp32_peak,
+            "precond_apply": {"ms": t_ap64, "flops": fl_ap64,
+                              "tflops": fl_ap64 / (t_ap64 * 1e-3) / 1e12,
+                              "frac_of_fp64_peak": fl_ap64 / (t_ap64 * 1e-3) / 1e12 / fp64_peak,
+                              "note": "two complex FP64 eigen-transforms (k_cgemm<double>, 8 P m^3 flop each) plus "
+                                      "the pivoted y sweeps, whose time is included (a lower bound on the GEMMs' rate)"},
+            "operator": {"ms": t_mv64, "flops": fl_mv64, "tflops": fl_mv64 / (t_mv64 * 1e-3) / 1e12,
+                         "frac_of_fp64_peak": fl_mv64 / (t_mv64 * 1e-3) / 1e12 / fp64_peak,
+                         "gbs": (N * 16 * 2 + (pr.s + 1) * n * 8) / (t_mv64 * 1e-3) / 1e9,
+                         "note": "4 (nnz of the P x P coupling + 5 P) flop per grid point"}}
 
     # ---------------------------------------------------------------- matvec bandwidth (dominant HBM kernel)
     mv = None
     if rank == 0 and not args.skip_matvec:
-        pr3 = inputs.config_2d_511()
-        op3 = B.SG(pr3)
-        N3, n3, s3 = op3.N, op3.n, pr3.s
         g = torch.Generator(device=dev).manual_seed(0)
-        X = torch.randn(N3, dtype=torch.complex64, device=dev, generator=g)
+        X = torch.randn(N, dtype=torch.complex64, device=dev, generator=g)
         Y = torch.empty_like(X)
         for _ in range(3):
-            op3.matvec(X, Y, B.FP32)
+            op.matvec(X, Y, B.FP32)
         torch.cuda.synchronize()
         reps = 20
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
         for k in range(reps):
             flush.zero_()
             ev[2 * k].record(stream)
-            op3.matvec(X, Y, B.FP32)
+            op.matvec(X, Y, B.FP32)
             ev[2 * k + 1].record(stream)
         torch.cuda.synchronize()
         t_mv = statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
-        bytes_mv = N3 * 8 * 2 + (s3 + 1) * n3 * 4
+        bytes_mv = N * 8 * 2 + (pr.s + 1) * n * 4
         peak, peak_kind = load_peaks()
         mv = {"workload": MATVEC_WORKLOAD, "dtype": "c64", "ms": t_mv, "bytes": bytes_mv,
               "gbs": bytes_mv / (t_mv * 1e-3) / 1e9, "peak_gbs": peak, "peak_kind": peak_kind}
-        # FP64 operator on the same grid
-        X64 = X.to(torch.complex128)
-        Y64 = torch.empty_like(X64)
-        op3.matvec(X64, Y64, B.FP64)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        e0.record(stream)
-        op3.matvec(X64, Y64, B.FP64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mv["fp64_ms"] = e0.elapsed_time(e1)
-        mv["fp64_gbs"] = (N3 * 16 * 2 + (s3 + 1) * n3 * 8) / (mv["fp64_ms"] * 1e-3) / 1e9
-        del X, Y, X64, Y64
-        op3.close()
+        tr = matvec_traffic()
+        mv["roofline"] = {"kernel": "k_mvkp_s6r3<32, 4> (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
+                          "achieved": mv["gbs"], "peak": peak, "unit": "GB/s", "frac": mv["gbs"] / peak,
+                          "traffic": tr, "traffic_source": "earlier ncu capture of this kernel source" if tr else None,
+                          "peak_kind": peak_kind}
+        del X, Y
+    op.close()
+    del b, x, x64, x_ref, x_mixed
+    torch.cuda.empty_cache()
 
-    # ---------------------------------------------------------------- 64 heterogeneous systems
-    batched = None
-    if rank == 0 and not args.skip_batch:
-        probs = inputs.batch_64()
-        ops = [B.SG(p) for p in probs]
-        bs = []
-        for op in ops:
-            bb = torch.empty(op.N, dtype=torch.complex128, device=dev)
-            op.rhs(bb, B.FP64)
-            bs.append(bb)
-        xs = [torch.zeros_like(bb) for bb in bs]
-        kw = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, maxit=20000)
-        B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)          # warm-up (allocates workspaces)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        st_b, inf_b = B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)
-        torch.cuda.synchronize()
-        t_batched = time.perf_counter() - t1
-        ok_b = st_b == B.SG_OK and all(i["relres"] <= 1e-8 for i in inf_b)
-        for op, bb, xx in zip(ops, bs, xs):                        # warm-up of the FP64 workspaces
-            op.gmres(bb, xx, mode=B.FP64, **kw)
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        inf_s = [op.gmres(bb, xx, mode=B.FP64, **kw) for op, bb, xx in zip(ops, bs, xs)]
-        torch.cuda.synchronize()
-        t_seq = time.perf_counter() - t1
-        ok_s = all(i["status"] == B.SG_OK for i in inf_s)
-        batched = {"systems": len(ops), "workload": "64 systems: g ~ U{63..255}, kbar ~ U[10,40], "
-                   "sigma ~ U[0.05,0.2], s ~ U{2,3,4}, degree ~ U{2,3} (P 6-35), GMRES(30), mean-value",
-                   "unknowns_total": int(sum(op.N for op in ops)),
-                   "mixed_batched_solves_per_s": len(ops) / t_batched,
-                   "fp64_sequential_solves_per_s": len(ops) / t_seq,
-                   "speedup_vs_fp64_sequential": t_seq / t_batched,
-                   "all_converged": bool(ok_b and ok_s),
-                   "iterations_mixed_total": int(sum(i["iters"] for i in inf_b)),
-                   "iterations_fp64_total": int(sum(i["iters"] for i in inf_s))}
-        for op in ops:
-            op.close()
-        del bs, xs
-
-    # ---------------------------------------------------------------- the other two paper-shaped workloads
-    cfg1 = cfg3 = None
+    # ---------------------------------------------------------------- the other workloads
+    cfg2 = batched = cfg1 = learned = None
     if rank == 0 and not args.skip_configs:
+        cfg2 = cfg2_leg(B, torch, dev, flush, stream)
         cfg1 = cfg1_leg(B, torch, dev)
-        cfg3 = cfg3_leg(B, torch, dev)
-
-    # ---------------------------------------------------------------- learned initial guess + batched + mixed
-    learned = None
+    if rank == 0 and not args.skip_batch:
+        batched = batched_leg(B, torch, dev)
     if rank == 0 and not args.skip_learned:
         learned = learned_leg(args, B, torch, dev)
 
@@ -575,36 +640,37 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single", l2="flushed (256 MB write) "
-                       "before every timed solve", iterations=infos[-1]["iters"], outer=infos[-1]["outer"],
-                       relres=infos[-1]["relres"], all_converged=ok, setup_ms=setup_ms),
-        "fp64": {"solves_per_s": 1000.0 / fp64_ms, "ms": fp64_ms, "iterations": i64["iters"],
-                 "relres": i64["relres"], "mixed_speedup": fp64_ms / ms * world},
-        "e2e": {"value": 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16},
+        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single",
+                       l2="flushed (256 MB write) before every timed solve; the 5.4 GB Krylov basis exceeds L2",
+                       iterations=infos[-1]["iters"], outer=infos[-1]["outer"], relres=infos[-1]["relres"],
+                       all_converged=ok, setup_ms=setup_ms),
+        "error": error,
+        "fp64": fp64,
+        "e2e": {"value": 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16,
+                "path": "sg_gmres with host_io=1 (pinned host b and x copied inside the call)"},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if top:
+        line["roofline"] = top
+    if mv:
+        line["matvec"] = mv
+    if cfg2:
+        line["cfg2_127"] = cfg2
+    if cfg1:
+        line["cfg1_1d"] = cfg1
     if batched:
         line["batched"] = batched
     if learned:
         line["learned"] = learned
-    if cfg1:
-        line["cfg1_1d"] = cfg1
-    if cfg3:
-        line["cfg3_511"] = cfg3
-    if mv:
-        tr = matvec_traffic()
-        mv["roofline"] = {"kernel": "k_mvkp_s6r3<32, 4> (SG operator, complex64, 511x511 P=84)", "bound": "hbm",
-                          "achieved": mv["gbs"], "peak": mv["peak_gbs"], "unit": "GB/s",
-                          "frac": mv["gbs"] / mv["peak_gbs"], "traffic": tr, "peak_kind": mv["peak_kind"]}
-        line["matvec"] = mv
-    if top:
-        line["roofline"] = top
     if world == 1 and not args.skip_cpu:
-        times_c, its_c = oracle_solve_seconds(1)
-        line["cpu_baseline"] = {"value": 1.0 / times_c[0], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": "1 full oracle solve of the workload (%d iterations), SuperLU single "
-                                          "threaded, NumPy BLAS on all cores" % its_c[0]}
+        S, M = oracle_sample_setup()
+        n_sample = S.A.shape[0]
+        steps511 = fp64["iterations"]
+        per = [oracle_extrapolate(oracle_sample_step_seconds(S, M), n_sample, steps511) for _ in range(2)]
+        line["cpu_baseline"] = {"value": 1.0 / statistics.mean(per), "unit": UNIT, "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": oracle_sample_text(n_sample, steps511, 2)}
+        del S, M
     print(json.dumps(line))
     return 0
 
@@ -619,7 +685,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-learned", action="store_true")
-    ap.add_argument("--skip-configs", action="store_true", help="skip the 1D and 511x511 solve legs")
+    ap.add_argument("--skip-configs", action="store_true", help="skip the 127x127 and 1D legs")
+    ap.add_argument("--quick", action="store_true", help="one FP64 solve instead of two")
     ap.add_argument("--learned-train", type=int, default=4096, help="training solves of the warm-start network")
     ap.add_argument("--learned-test", type=int, default=256, help="held-out solves of the warm-start leg")
     args = ap.parse_args()

@@ -326,6 +326,13 @@ long long sg_kernel_launches(void);
 /* ABI version: 100 * major + minor. */
 int sg_version(void);
 
+/* Measured arithmetic peak of the GPU's CUDA cores (not in the paper: a
+ * diagnostic for roofline figures).  Runs a kernel of independent fused
+ * multiply-add chains (FP64 if fp64 != 0, else FP32) over the whole GPU,
+ * timed with CUDA events, and writes the rate in TFLOP/s (2 flop per FMA) to
+ * *tflops.  Synchronises `stream`; allocates and frees a small buffer. */
+sg_status sg_alu_peak(int fp64, double* tflops, void* stream);
+
 /* Check of the device-side failure detection (not in the paper).  Launches
  * one warp that waits, through the bounded mbarrier wait of the
  * preconditioner's tensor-core transform kernel, for a barrier phase that

@@ -28,7 +28,7 @@ EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "
             "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched",
             "sg_mlp_create", "sg_mlp_destroy", "sg_mlp_num_params", "sg_mlp_set_params", "sg_mlp_get_params",
             "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
-            "sg_selftest_wait_timeout"]
+            "sg_selftest_wait_timeout", "sg_alu_peak"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -124,9 +124,18 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_cgemm_nn.restype = i
     lib.sg_selftest_wait_timeout.argtypes = [vp, C.POINTER(i), dp]
     lib.sg_selftest_wait_timeout.restype = i
+    lib.sg_alu_peak.argtypes = [i, dp, vp]
+    lib.sg_alu_peak.restype = i
     del fp
     _lib = lib
     return lib
+
+
+def alu_peak(fp64: bool, stream=None) -> float:
+    """sg_alu_peak: measured FMA rate of the CUDA cores in TFLOP/s."""
+    v = C.c_double(0.0)
+    _check(load().sg_alu_peak(1 if fp64 else 0, C.byref(v), _stream(stream)))
+    return v.value
 
 
 def kernel_launches() -> int:

@@ -35,10 +35,15 @@
 // Every wait is bounded: on a timeout the kernel records it, drains its
 // copies, frees tensor memory and returns.
 //
-// With a tensor map of X (plain TF32, X rows of even length), the copy warp
-// also loads X: one 4D tensor copy per stage (4 values x 8 rows x 8 chunks x
-// 16 row groups) lands directly in the core-matrix layout, and the loader
-// warps only run the epilogue.
+// In the plain-TF32 form the A operand (X) is kept in the 128-byte swizzle
+// layout: each K stage of a row is one 128-byte row of the tile.  With a
+// tensor map of X (X rows of even length), the copy warp also loads X: one 2D
+// tensor copy of 32 values x 128 rows per stage, 128-byte requests, lands in
+// that layout directly, and the loader warps only run the epilogue.  (A
+// layout of 16-byte core matrices filled by 16-byte requests kept the
+// L1-to-L2 request path ~80 % busy at a quarter of its bandwidth.)  The B
+// operand and the 3xTF32 form's split X tiles use the no-swizzle
+// core-matrix layout.
 //
 // Launched as a programmatic dependent of the previous kernel in the stream:
 // tensor-memory allocation, barrier set-up and the first B copies (B is
@@ -125,6 +130,24 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
          (1ull << 46);
 }
 
+// Shared memory matrix descriptor of a K-major tile in the 128-byte swizzle
+// layout: rows of 128 bytes (32 TF32 values, one K stage), 16-byte chunk c of
+// row r stored at chunk c ^ (r % 8); 8-row groups 1024 bytes apart (stride
+// byte offset); the leading byte offset is unused (one MMA's 8 K values, 32
+// bytes, lie inside a row); swizzle mode 2 (128 B) in bits 61-63.  The tile
+// starts on a 1024-byte boundary; the k-th MMA of a stage starts 32 k bytes
+// into it (the swizzle is a function of the address bits, so the offset
+// start selects the k-th 32-byte column of every row).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
+}
+
+// Byte offset of element (row, k), k < 32, in the 128-byte swizzle layout.
+__host__ __device__ constexpr int sw128_off(int row, int k) {
+  return row * 128 + ((((k >> 2) ^ (row & 7)) & 7) << 4) + (k & 3) * 4;
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -180,13 +203,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// 4D tensor copy global -> shared completing its bytes on an mbarrier
-__device__ __forceinline__ void tensor_g2s_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                              uint32_t bar) {
+// 2D tensor copy global -> shared completing its bytes on an mbarrier
+__device__ __forceinline__ void tensor_g2s_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
       : "memory");
 }
 
@@ -319,7 +341,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
   auto copy_x = [&](int t) {
     const uint32_t bar = full0 + 8 * (t % NA);
     mbar_expect_tx(bar, (uint32_t)A_TILE);
-    tensor_g2s_4d(s_base + L::OFF_A + (t % NA) * L::A_SLOT, &xmap, 0, 0, t * (BK / 4), m0 / 8, bar);
+    tensor_g2s_2d(s_base + L::OFF_A + (t % NA) * L::A_SLOT, &xmap, t * BK, m0, bar);
   };
   // B is constant: its first stages are copied before the wait below
   const int pre = a.nks < NBS ? a.nks : NBS;
@@ -375,7 +397,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
             const int rem = (a.K2 - k) * 4;
             const int bytes = (m < a.M && rem > 0) ? (rem < 16 ? rem : 16) : 0;
             const float* src = bytes ? a.X + (size_t)m * a.ldx + k : a.X;
-            cp_async16z(dst + core_off(r, 4 * c), src, bytes);
+            cp_async16z(dst + sw128_off(r, 4 * c), src, bytes);
           }
         } else {
   #pragma unroll
@@ -385,7 +407,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
             const int m = m0 + r, k = k0 + 2 * kp;
             const bool ok = m < a.M && k < a.K2;
             const float* src = ok ? a.X + (size_t)m * a.ldx + k : a.X;
-            cp_async8(dst + core_off(r, 2 * kp), src, ok ? 8 : 0);
+            cp_async8(dst + sw128_off(r, 2 * kp), src, ok ? 8 : 0);
           }
         }
       };
@@ -554,8 +576,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
         const uint32_t bhi = s_base + OFF_B + (s % NBS) * L::NBP * B_TILE, blo = bhi + B_TILE;
 #pragma unroll
         for (int ks = 0; ks < BK / 8; ++ks) {
-          const uint32_t o = 256u * ks;   // 8 TF32 = two core matrices along K
-          mma_tf32(tmem, sdesc(ahi + o), sdesc(bhi + o), L::IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+          const uint32_t o = 256u * ks;   // 8 TF32 = two core matrices along K (no-swizzle tiles)
+          // A: the 128-byte swizzle layout in the plain form (8 TF32 = 32 bytes of each row)
+          const uint64_t ad = SPLIT ? sdesc(ahi + o) : sdesc_sw128(ahi + 32u * ks);
+          mma_tf32(tmem, ad, sdesc(bhi + o), L::IDESC, (s > 0 || ks > 0) ? 1u : 0u);
           if (SPLIT) {
             mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), L::IDESC, 1u);
             mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), L::IDESC, 1u);
@@ -689,16 +713,16 @@ bool tc_make_xmap(CUtensorMap* map, const float2* X, long long ldx, int M, int k
     return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }();
   if (!enc || ldx % 2 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || M <= 0 || kdim <= 0) return false;
-  const cuuint64_t pitch = (cuuint64_t)ldx * 8;    // bytes per row (complex64)
-  // view: (4 values, 8 rows, K2/4 chunks, M/8 row groups); every stride a
-  // multiple of 16 bytes; the last row group may reach 7 rows past M, inside
-  // the caller's buffer (rows there only produce discarded output rows)
-  cuuint64_t dims[4] = {4, 8, (cuuint64_t)((2 * kdim + 3) / 4), (cuuint64_t)((M + 7) / 8)};
-  cuuint64_t strides[3] = {pitch, 16, 8 * pitch};
-  cuuint32_t box[4] = {4, 8, (cuuint32_t)(tc::BK / 4), (cuuint32_t)(tc::BM / 8)};
-  cuuint32_t es[4] = {1, 1, 1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(X), dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+  // view: (2 kdim real values, M rows), row pitch a multiple of 16 bytes; a
+  // box of 32 values x 128 rows (one K stage of one row tile, 128-byte rows)
+  // lands in the 128-byte swizzle layout the MMA descriptor expects; values
+  // past 2 kdim and rows past M are read as zeros
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * kdim), (cuuint64_t)M};
+  cuuint64_t strides[1] = {(cuuint64_t)ldx * 8};
+  cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(X), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }

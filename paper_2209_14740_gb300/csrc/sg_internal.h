@@ -112,11 +112,11 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
 // kernel's bounded wait; sets *err = 1 when the wait gives up, *done = 1 at
 // the end (device ints).
 cudaError_t tc_wait_selftest(int* err, int* done, cudaStream_t st);
-// Tensor map of X (M rows, K2 real values per row, row pitch ldx floats, 16-byte
-// aligned, ldx a multiple of 4) for the plain-TF32 transform: a 4D view
-// (4 values, 8 rows, K2/4 chunks, M/8 row groups) whose 4 x 8 x 8 x 16 box is one
-// K stage in the tensor cores' no-swizzle K-major layout.  False if the driver
-// entry point or the encoding is unavailable (the kernel then copies X itself).
+// Tensor map of X (M complex64 rows of kdim values, row pitch ldx complex, 16-byte
+// aligned, ldx even) for the plain-TF32 transform: a 2D view (2 kdim real values,
+// M rows) whose 32 x 128 box is one K stage of one row tile, landing in the
+// 128-byte swizzle layout of the MMA's A operand.  False if the driver entry
+// point or the encoding is unavailable (the kernel then copies X itself).
 bool tc_make_xmap(CUtensorMap* map, const float2* X, long long ldx, int M, int kdim);
 
 struct GmresWork {

@@ -217,3 +217,27 @@ def test_511_mixed_solve_residual(B, cfg511):
     relres = float(torch.linalg.vector_norm(b - Ax) / torch.linalg.vector_norm(b))
     print("511x511 mixed: iters %d outer %d relres %.3e" % (info["iters"], info["outer"], relres))
     assert info["status"] == B.SG_OK and relres <= 1e-8
+
+
+def test_511_tf32_apply(B, cfg511):
+    """The plain-TF32 apply at 511 x 511, P = 84 (the complex64 GMRES
+    cycles' preconditioner there): four transforms of 42,924 x 1,022 x 1,022
+    real, 2,688 output tiles walked by one persistent CTA per SM (about 18
+    tiles each, accumulators alternating between two tensor-memory buffers),
+    against the FP64 apply within the TF32 bound 5e-3, both blocks, two calls
+    giving the same bits."""
+    pr, op = cfg511
+    g = torch.Generator(device=DEV).manual_seed(13)
+    X = torch.randn(op.N, dtype=torch.complex64, device=DEV, generator=g)
+    for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+        Zr = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.precond(X.to(torch.complex128), Zr, kind, B.FP64)
+        Zt = torch.empty_like(X)
+        op.precond(X, Zt, kind, B.TF32)
+        err = float(torch.linalg.vector_norm(Zt.to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+        print("511x511 TF32 apply kind %d: error vs FP64 apply %.2e" % (kind, err))
+        assert err < 5e-3, (kind, err)
+        Zt2 = torch.empty_like(X)
+        op.precond(X, Zt2, kind, B.TF32)
+        assert torch.equal(Zt, Zt2)
+        del Zr

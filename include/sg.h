@@ -273,6 +273,53 @@ sg_status sg_gmres_batched(sg_handle* const* h, int count, const sg_gmres_opts* 
                            void* const* x, const void* const* x0, sg_gmres_info* infos, int concurrency,
                            void* stream);
 
+/* Stationary iteration with the mean-value splitting (Sec. 5; Sec. 7 runs it
+ * with A_0): B x^(i+1) = b - (A - B) x^(i), i.e.
+ * x^(i+1) = x^(i) + B^-1 (b - A x^(i)), with B = I_P (x) S_blk the block of
+ * opts->prec (SG_PREC_MEAN: A_0; SG_PREC_CSL_MEAN: M_0).  It converges when
+ * the spectral radius of I - B^-1 A is below one (small theta) and diverges
+ * otherwise (the paper's wedge: theta = 0.1 converges, theta = 0.2 does not).
+ *   x0_given  1: x holds the initial iterate on entry; 0: x^(0) = 0 (then
+ *             x^(1) = B^-1 b, the paper's starting vector).
+ *   maxit     steps at most; tol: stop when ||b - A x|| / ||b|| <= tol.
+ *   mode      SG_FP64 (complex128 b, x) or SG_FP32 (complex64).
+ * history (host, may be NULL): maxit + 1 doubles, relres of x^(0), x^(1), ...
+ * up to the last iterate.  info (may be NULL): steps taken, final relres,
+ * status, and diverged = 1 if the residual ended above 1e6 times the first
+ * one (or became non-finite).  Returns SG_OK at tol, SG_ENOTCONV at maxit,
+ * SG_EBREAKDOWN on a non-finite residual.  Device buffers; blocks the host
+ * thread until done. */
+typedef struct {
+  sg_prec prec;
+  sg_precision mode;
+  int maxit;
+  double tol;
+  int x0_given;
+} sg_stationary_opts;
+
+typedef struct {
+  int iters;
+  double relres;
+  int diverged;
+  sg_status status;
+} sg_stationary_info;
+
+sg_status sg_stationary(sg_handle* h, const sg_stationary_opts* opts, const void* b, void* x,
+                        sg_stationary_info* info, double* history, void* stream);
+
+/* Post-processing of an SG solution V (N complex of precision prec, device;
+ * Sec. 7): with the orthonormal chaos basis the expected value of
+ * u~(x, xi) = sum_i V_i(x) phi_i(xi) is V_0(x), and the variances of its real
+ * and imaginary parts are sum_{i>=1} (Re V_i(x))^2 and sum_{i>=1} (Im V_i(x))^2.
+ *   mean     device, n complex (prec) or NULL
+ *   var_re, var_im  device, n reals (prec) or NULL
+ *   gamma    host, r + 1 doubles or NULL: gamma_j = max { ||V_i||_inf :
+ *            total degree of phi_i = j }, j = 0..r (the magnitudes the paper
+ *            plots against the degree); the call then synchronises `stream`.
+ * The first call with gamma allocates a P-entry device buffer in the handle. */
+sg_status sg_statistics(sg_handle* h, sg_precision prec, const void* V, void* mean, void* var_re, void* var_im,
+                        double* gamma, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned initial guess (not in the paper: a throughput aid whose result is
  * always finished by sg_gmres to the same tolerance; the zero guess remains

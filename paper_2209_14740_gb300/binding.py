@@ -28,7 +28,7 @@ EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "
             "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched",
             "sg_mlp_create", "sg_mlp_destroy", "sg_mlp_num_params", "sg_mlp_set_params", "sg_mlp_get_params",
             "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
-            "sg_selftest_wait_timeout", "sg_alu_peak"]
+            "sg_selftest_wait_timeout", "sg_alu_peak", "sg_stationary", "sg_statistics"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -56,6 +56,15 @@ class SgGmresOpts(C.Structure):
 class SgGmresInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("cycles", C.c_int), ("relres", C.c_double),
                 ("status", C.c_int)]
+
+
+class SgStationaryOpts(C.Structure):
+    _fields_ = [("prec", C.c_int), ("mode", C.c_int), ("maxit", C.c_int), ("tol", C.c_double),
+                ("x0_given", C.c_int)]
+
+
+class SgStationaryInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("relres", C.c_double), ("diverged", C.c_int), ("status", C.c_int)]
 
 
 class SgError(RuntimeError):
@@ -126,6 +135,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_selftest_wait_timeout.restype = i
     lib.sg_alu_peak.argtypes = [i, dp, vp]
     lib.sg_alu_peak.restype = i
+    lib.sg_stationary.argtypes = [vp, C.POINTER(SgStationaryOpts), vp, vp, C.POINTER(SgStationaryInfo), dp, vp]
+    lib.sg_stationary.restype = i
+    lib.sg_statistics.argtypes = [vp, i, vp, vp, vp, vp, dp, vp]
+    lib.sg_statistics.restype = i
     del fp
     _lib = lib
     return lib
@@ -278,6 +291,26 @@ class SG:
         """sg_precond_noalloc: the same apply with the library's static scratch
         (no device memory is allocated by the call)."""
         _check(load().sg_precond_noalloc(self.h, kind, prec, _ptr(R), _ptr(Z), _stream(stream)))
+
+    def stationary(self, b, x, *, prec=PREC_MEAN, mode=FP64, maxit=50, tol=1e-8, x0_given=False, stream=None):
+        """sg_stationary: returns (info dict, relres history list)."""
+        o = SgStationaryOpts()
+        o.prec, o.mode, o.maxit, o.tol, o.x0_given = prec, mode, maxit, tol, 1 if x0_given else 0
+        inf = SgStationaryInfo()
+        hist = (C.c_double * (maxit + 1))()
+        st = load().sg_stationary(self.h, C.byref(o), _ptr(b), _ptr(x), C.byref(inf), hist, _stream(stream))
+        if st not in (SG_OK, SG_ENOTCONV, SG_EBREAKDOWN):
+            _check(st)
+        return (dict(iters=inf.iters, relres=inf.relres, diverged=inf.diverged, status=st),
+                list(hist)[: inf.iters + 1])
+
+    def statistics(self, V, mean=None, var_re=None, var_im=None, gamma=True, prec=FP64, stream=None):
+        """sg_statistics: fills the given device outputs; returns gamma_0..r (or None)."""
+        g = (C.c_double * (self.info["r"] + 1))() if gamma else None
+        _check(load().sg_statistics(self.h, prec, _ptr(V), _ptr(mean) if mean is not None else None,
+                                    _ptr(var_re) if var_re is not None else None,
+                                    _ptr(var_im) if var_im is not None else None, g, _stream(stream)))
+        return list(g) if gamma else None
 
     def gmres(self, b, x, *, restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, x0=None, max_outer=0,
               inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False,

@@ -200,6 +200,7 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
   for (auto& t : h->tcB) { cudaFree(t.hi); cudaFree(t.lo); }
   cudaFree(h->d_err);
+  cudaFree(h->d_modemax);
   sgi_free_gmres_work(h);
   delete h;
 }

@@ -199,6 +199,7 @@ struct sg_handle {
   sgi::TcDevOperand tcB[4];          // tensor-core factors: Qhat_x, Qhat_y, Qhat_y^T, Qhat_x^T
   int* d_err = nullptr;              // device flag: a bounded wait in a kernel timed out
   void* noalloc_scratch = nullptr;   // device address of the static scratch of sg_precond_noalloc
+  unsigned long long* d_modemax = nullptr;   // P per-mode maxima of sg_statistics (allocated on first use)
 
   sgi::GmresWork gw;
 

@@ -1419,3 +1419,114 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     return status;
   });
 }
+
+// ------------------------------------------------------------------ stationary iteration
+// The stationary iteration of Sec. 5 with the mean-value (or CSL mean-value)
+// block as the splitting matrix B: B x^(i+1) = b - (A - B) x^(i), i.e.
+// x^(i+1) = x^(i) + B^-1 (b - A x^(i)).  Each step is one operator
+// application with the residual and its norm (FP64 reduction), one block
+// solve for all P modes and one update, on the handle's private stream.
+extern "C" sg_status sg_stationary(sg_handle* h, const sg_stationary_opts* opts, const void* b, void* x,
+                                   sg_stationary_info* info, double* history, void* stream) {
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !opts || !b || !x) return fail(SG_EINVAL, "NULL argument to sg_stationary");
+    if (opts->mode != SG_FP64 && opts->mode != SG_FP32) return fail(SG_EINVAL, "mode must be SG_FP64 or SG_FP32");
+    if (opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN)
+      return fail(SG_EINVAL, "the splitting matrix must be SG_PREC_MEAN or SG_PREC_CSL_MEAN");
+    if (opts->maxit < 0) return fail(SG_EINVAL, "maxit must be >= 0");
+    if (!(opts->tol >= 0) || !std::isfinite(opts->tol)) return fail(SG_EINVAL, "tol must be finite and >= 0");
+    if (!h->blk[opts->prec == SG_PREC_MEAN ? 0 : 1].ready)
+      return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (2D needs a constant k_0)");
+    const bool f32 = opts->mode == SG_FP32;
+    sg_status st0 = ensure_work(h, 1, f32 ? 8 : 16);
+    if (st0 != SG_OK) return st0;
+    GmresWork& w = h->gw;
+    cudaStream_t caller = (cudaStream_t)stream;
+    cudaStream_t st = w.stream;
+    SG_CUDA_TRY(cudaEventRecord(w.ev, caller));
+    SG_CUDA_TRY(cudaStreamWaitEvent(st, w.ev, 0));
+    struct Rejoin {
+      cudaEvent_t ev;
+      cudaStream_t from, to;
+      ~Rejoin() {
+        if (cudaEventRecord(ev, from) == cudaSuccess) cudaStreamWaitEvent(to, ev, 0);
+      }
+    } rejoin{w.ev, st, caller};
+    Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+    const long long N = h->N;
+    const size_t bytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
+    bool x_zero = !opts->x0_given;
+    if (x_zero) SG_CUDA_TRY(cudaMemsetAsync(x, 0, bytes, st));
+    // ||b||
+    double bn2 = 0;
+    {
+      double* out = w.dscal + c.L.sc + SC_BNORM;
+      if (f32)
+        k_residual<float, float><<<c.grid, RED_THREADS, 0, st>>>((const float2*)b, nullptr, nullptr, N, w.part,
+                                                                 c.pstride, w.counter, out);
+      else
+        k_residual<double, double><<<c.grid, RED_THREADS, 0, st>>>((const double2*)b, nullptr, nullptr, N, w.part,
+                                                                   c.pstride, w.counter, out);
+      note_launch();
+      SG_CUDA_TRY(cudaGetLastError());
+      SG_CUDA_TRY(cudaMemcpyAsync(&bn2, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    const double bnorm = std::sqrt(bn2);
+    if (!std::isfinite(bnorm)) return fail(SG_EINVAL, "right-hand side is not finite");
+    sg_stationary_info inf{};
+    inf.status = SG_ENOTCONV;
+    double relres0 = -1.0;
+    for (int it = 0;; ++it) {
+      // r = b - A x (into the basis slot V_0), ||r||^2
+      double rn2 = 0;
+      sg_status s = f32 ? residual_norm<float>(c, (const float2*)b, (const float2*)x, x_zero, (float2*)w.Z, w.V, true,
+                                               &rn2)
+                        : residual_norm<double>(c, (const double2*)b, (const double2*)x, x_zero, (double2*)w.R64, w.V,
+                                                false, &rn2);
+      if (s != SG_OK) return s;
+      const double relres = bnorm > 0 ? std::sqrt(rn2) / bnorm : 0.0;
+      if (history) history[it] = relres;
+      inf.iters = it;
+      inf.relres = relres;
+      if (relres0 < 0) relres0 = relres;
+      if (!std::isfinite(relres)) {
+        inf.status = SG_EBREAKDOWN;
+        inf.diverged = 1;
+        break;
+      }
+      if (relres <= opts->tol) {
+        inf.status = SG_OK;
+        break;
+      }
+      if (it >= opts->maxit) {
+        // a residual that grew by 1e6 over the first one: the splitting does not converge
+        inf.diverged = relres > 1e6 * relres0 ? 1 : 0;
+        break;
+      }
+      // x += B^-1 r
+      if (f32) {
+        SG_CUDA_TRY(precond_apply<float>(c, opts->prec, (const float2*)w.V, (float2*)w.Z, nullptr));
+        k_axpy<float, float><<<c.grid, RED_THREADS, 0, st>>>((float2*)x, (const float2*)w.Z, N, nullptr);
+      } else {
+        SG_CUDA_TRY(precond_apply<double>(c, opts->prec, (const double2*)w.V, (double2*)w.R64, nullptr));
+        k_axpy<double, double><<<c.grid, RED_THREADS, 0, st>>>((double2*)x, (const double2*)w.R64, N, nullptr);
+      }
+      note_launch();
+      SG_CUDA_TRY(cudaGetLastError());
+      x_zero = false;
+    }
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    int werr = 0;
+    SG_CUDA_TRY(cudaMemcpyAsync(&werr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(cudaStreamSynchronize(st));
+    if (werr) {
+      SG_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), st));
+      inf.status = SG_ETIMEOUT;
+    }
+    if (info) *info = inf;
+    if (inf.status == SG_ENOTCONV) set_error("stationary iteration did not reach tol within maxit");
+    if (inf.status == SG_EBREAKDOWN) set_error("stationary iteration: non-finite residual (diverged)");
+    return inf.status;
+  });
+}

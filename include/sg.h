@@ -363,6 +363,26 @@ sg_status sg_cgemm_hn(const void* A, long long lda, const void* B, long long ldb
  * complex128 if out_c128 else complex64.  Expansion x = c U of a basis. */
 sg_status sg_cgemm_nn(const void* A, const void* B, int m, int n, int k, void* C, int out_c128, void* stream);
 
+/* A trained warm-start model: the network (not owned: it must outlive the
+ * model), a copy of the decoder D = scale * U (rank rows of N complex64
+ * values, device, row-major: the scaled rank-R basis of training
+ * solutions) and the box [lo, hi] (host, in_dim doubles each, lo < hi) that
+ * the network's inputs are normalised from.  The network's output width must
+ * be 2 * rank (rank complex coefficients as interleaved pairs). */
+typedef struct sg_warmstart sg_warmstart;
+sg_status sg_warmstart_create(sg_mlp* net, const void* D, int rank, long long N, const double* lo, const double* hi,
+                              sg_warmstart** out);
+void sg_warmstart_destroy(sg_warmstart* w);
+/* Initial guesses x0 for `count` parameter rows (params: host, count x
+ * in_dim doubles, e.g. (kbar, sigma, correlation length, x_s, y_s)):
+ * x0 (device, count x N complex128, row k for row k of params) =
+ * net(2 (p - lo) / (hi - lo) - 1) viewed as rank complex values, times D.
+ * Every step runs on the device in the library's kernels; the first call
+ * with a larger count allocates the model's small input/output buffers.
+ * Pass a row of x0 to sg_gmres as opts.x0 (with SG_X0_SCALED or
+ * SG_X0_FALLBACK, so that a poor guess never starts above the zero guess). */
+sg_status sg_warmstart_predict(sg_warmstart* w, const double* params, int count, void* x0, void* stream);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* sg_last_error(void);
 

@@ -28,7 +28,8 @@ EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "
             "sg_last_error", "sg_version", "sg_kernel_launches", "sg_precond_noalloc", "sg_gmres_batched",
             "sg_mlp_create", "sg_mlp_destroy", "sg_mlp_num_params", "sg_mlp_set_params", "sg_mlp_get_params",
             "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
-            "sg_selftest_wait_timeout", "sg_alu_peak", "sg_stationary", "sg_statistics"]
+            "sg_selftest_wait_timeout", "sg_alu_peak", "sg_stationary", "sg_statistics",
+            "sg_warmstart_create", "sg_warmstart_destroy", "sg_warmstart_predict"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -139,6 +140,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_stationary.restype = i
     lib.sg_statistics.argtypes = [vp, i, vp, vp, vp, vp, dp, vp]
     lib.sg_statistics.restype = i
+    lib.sg_warmstart_create.argtypes = [vp, vp, i, C.c_longlong, dp, dp, C.POINTER(vp)]
+    lib.sg_warmstart_create.restype = i
+    lib.sg_warmstart_destroy.argtypes = [vp]
+    lib.sg_warmstart_destroy.restype = None
+    lib.sg_warmstart_predict.argtypes = [vp, dp, i, vp, vp]
+    lib.sg_warmstart_predict.restype = i
     del fp
     _lib = lib
     return lib
@@ -205,6 +212,39 @@ class MLP:
         _check(load().sg_mlp_train(self.h, _ptr(X), _ptr(T), X.shape[0], batch, epochs, C.c_float(lr), hist,
                                    _stream(stream)))
         return list(hist)[:epochs]
+
+
+class WarmStartModel:
+    """sg_warmstart: a trained network plus its decoder, predicting initial
+    guesses on the device."""
+
+    def __init__(self, mlp, D, rank, lo, hi):
+        self._lo = np.ascontiguousarray(lo, dtype=np.float64)
+        self._hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self.mlp = mlp                       # the model borrows the network
+        self.rank, self.N = rank, int(D.shape[-1])
+        h = C.c_void_p()
+        dp = C.POINTER(C.c_double)
+        _check(load().sg_warmstart_create(mlp.h, _ptr(D), rank, self.N, self._lo.ctypes.data_as(dp),
+                                          self._hi.ctypes.data_as(dp), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().sg_warmstart_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, params, x0, stream=None):
+        """x0 (device, count x N complex128) for the parameter rows (host)."""
+        p = np.ascontiguousarray(np.atleast_2d(params), dtype=np.float64)
+        _check(load().sg_warmstart_predict(self.h, p.ctypes.data_as(C.POINTER(C.c_double)), p.shape[0], _ptr(x0),
+                                           _stream(stream)))
 
 
 def cgemm_hn(A, lda, B, ldb, m, n, k, Cout, work, stream=None):

@@ -374,3 +374,11 @@ sg_status sg_mlp_train(sg_mlp* m, const float* X, const float* T, int nsamples, 
 }
 
 }  // extern "C"
+
+namespace sgi {
+// Input and output widths of a network (for the warm-start model's checks).
+void mlp_dims(const sg_mlp* m, int* in_dim, int* out_dim) {
+  *in_dim = m->in;
+  *out_dim = m->out;
+}
+}  // namespace sgi

@@ -232,6 +232,9 @@ template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                    C2<T>* tmp, C2<T>* tmp2);
 
+// Input and output widths of a warm-start network (mlp.cu).
+void mlp_dims(const sg_mlp* m, int* in_dim, int* out_dim);
+
 // Device address of the allocation-free entry point's static scratch on the
 // current device (loads its module; called once per handle by sg_assemble).
 cudaError_t noalloc_scratch_address(void** out);

@@ -16,8 +16,9 @@ arguments around):
    scaled to unit RMS;
 4. network: 5 -> 512 -> 512 -> 512 -> 2R, tanh, bf16 weights with FP32
    accumulation, trained with Adam by `sg_mlp_train`;
-5. inference: x0 = (net(params) as R complex) * scale @ U (`sg_mlp_forward`,
-   `sg_cgemm_nn`), then `sg_gmres` from x0 with the zero-guess fallback on.
+5. inference: x0 = (net(params) as R complex) * scale @ U (`sg_warmstart_predict`:
+   normalisation, network and expansion on the device), then `sg_gmres` from x0
+   with the zero-guess fallback on.
 """
 from __future__ import annotations
 
@@ -91,16 +92,14 @@ class WarmStart:
     lo: np.ndarray
     hi: np.ndarray
     timings: dict
+    model: B.WarmStartModel = None   # sg_warmstart: normalisation, network, expansion on the device
 
     def predict(self, params, torch, dev):
-        """x0 (k x N complex128, device) for k parameter rows."""
-        X = torch.from_numpy(normalise(params, self.lo, self.hi)).to(dev)
-        Y = torch.empty((X.shape[0], 2 * self.rank), dtype=torch.float32, device=dev)
-        self.mlp.forward(X, Y)
-        c = torch.view_as_complex(Y.view(X.shape[0], self.rank, 2)).contiguous()
-        N = self.U.shape[1]
-        x0 = torch.empty((X.shape[0], N), dtype=torch.complex128, device=dev)
-        B.cgemm_nn(c, self.Udec, X.shape[0], N, self.rank, x0, out_c128=True)
+        """x0 (k x N complex128, device) for k parameter rows, by
+        sg_warmstart_predict."""
+        p = np.atleast_2d(np.asarray(params, dtype=np.float64))
+        x0 = torch.empty((p.shape[0], self.U.shape[1]), dtype=torch.complex128, device=dev)
+        self.model.predict(p, x0)
         return x0
 
 
@@ -151,5 +150,6 @@ def build(params, S, torch, dev, rank=64, n_snapshots=512, width=512, hidden=3, 
     hist = mlp.train(X, T, batch, epochs, lr)
     timings["train_s"] = time.perf_counter() - t0
     Udec = (U * scale).contiguous()
+    model = B.WarmStartModel(mlp, Udec, rank, lo, hi)
     return WarmStart(U, Udec, mlp, scale, rank, hist, energy, np.asarray(lo, float), np.asarray(hi, float),
-                     timings)
+                     timings, model)

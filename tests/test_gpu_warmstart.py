@@ -184,6 +184,47 @@ def test_pod_basis_is_orthonormal(B, trained):
     assert ws.energy_captured > 0.9
 
 
+def test_predict_matches_the_composition(B, trained):
+    """sg_warmstart_predict (normalisation kernel, network, complex view,
+    expansion, all in the library) against the same steps composed from the
+    separate entry points: normalisation in numpy, sg_mlp_forward, the
+    complex view of its output, sg_cgemm_nn.  Bit for bit: the normalisation
+    formula is the same in FP64, and the products are the same kernels."""
+    from paper_2209_14740_gb300 import warmstart
+    ws, _ = trained
+    ptest = box_params(300, 7)
+    X = torch.from_numpy(warmstart.normalise(ptest, ws.lo, ws.hi)).to(DEV)
+    Y = torch.empty((X.shape[0], 2 * ws.rank), dtype=torch.float32, device=DEV)
+    ws.mlp.forward(X, Y)
+    c = torch.view_as_complex(Y.view(X.shape[0], ws.rank, 2)).contiguous()
+    N = ws.U.shape[1]
+    xc = torch.empty((X.shape[0], N), dtype=torch.complex128, device=DEV)
+    B.cgemm_nn(c, ws.Udec, X.shape[0], N, ws.rank, xc, out_c128=True)
+    xp = ws.predict(ptest, torch, DEV)
+    assert torch.equal(xp, xc)
+
+
+def test_predict_one_parameter_set_through_ctypes(B, trained):
+    """The C ABI called directly with one parameter set (5 doubles) and a
+    device buffer, as a C caller would: the same row as a batched call."""
+    import ctypes as C
+    ws, _ = trained
+    ptest = box_params(301, 3)
+    xb = ws.predict(ptest, torch, DEV)
+    lib = B.load()
+    N = ws.U.shape[1]
+    for k in range(3):
+        p = (C.c_double * 5)(*ptest[k])
+        x0 = torch.empty(N, dtype=torch.complex128, device=DEV)
+        st = lib.sg_warmstart_predict(ws.model.h, p, 1, C.c_void_p(x0.data_ptr()),
+                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == B.SG_OK
+        assert torch.equal(x0, xb[k])
+    # a bad count is rejected
+    p = (C.c_double * 5)(*ptest[0])
+    assert lib.sg_warmstart_predict(ws.model.h, p, 0, C.c_void_p(xb.data_ptr()), None) == B.SG_EINVAL
+
+
 def test_warm_start_beats_zero_guess(B, trained):
     ws, _ = trained
     ptest = box_params(200, 12)

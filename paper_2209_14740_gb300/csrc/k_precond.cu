@@ -502,6 +502,8 @@ static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, 
   }
   const int mx = h->mx, my = h->my, P = h->P;
   const long long plane = (long long)mx * my;
+  if (blk.band.ab)   // k_0 varies in space: banded LU of the n x n block, the P modes as right-hand sides
+    return band_solve<T>(blk.band, P, R, tmp, Z, h->n, st, skip, in_scale);
   if constexpr (sizeof(T) == 4) {
     if (h->fd && h->fd_fp32) return fd_apply(h, which, R, Z, st, skip, in_scale, tmp, tmp2, true);
   }

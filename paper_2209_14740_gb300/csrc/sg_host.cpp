@@ -168,6 +168,7 @@ static cudaError_t upload(T** dst, const T* src, size_t count) {
 static void free_factors(PrecBlock& b) {
   cudaFree(b.f64.dl); cudaFree(b.f64.dinv); cudaFree(b.f64.du); cudaFree(b.f64.du2); cudaFree(b.f64.piv);
   cudaFree(b.f32.dl); cudaFree(b.f32.dinv); cudaFree(b.f32.du); cudaFree(b.f32.du2);
+  cudaFree(b.band.ab); cudaFree(b.band.ab32); cudaFree(b.band.piv);
   b = PrecBlock{};
 }
 
@@ -194,7 +195,7 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_rowptr); cudaFree(h->d_col); cudaFree(h->d_term);
   cudaFree(h->d_gval); cudaFree(h->d_gdiag); cudaFree(h->d_fields); cudaFree(h->d_b0);
   cudaFree(h->d_gval32); cudaFree(h->d_gdiag32); cudaFree(h->d_fields32);
-  for (auto& b : h->blk) if (b.f64.dl) free_factors(b);
+  for (auto& b : h->blk) if (b.f64.dl || b.band.ab) free_factors(b);
   cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
   cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
   cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
@@ -391,6 +392,46 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
           if (upload(&h->d_Linv32[which], Linv.data(), Linv.size())) return fail(SG_ENOMEM, "precond upload");
         }
         h->fd = true;
+      }
+    }
+  } else {
+    // 2D with k_0 varying in space (the paper's wedge): S_blk has no
+    // separable inverse.  Band LU of the n x n block, unknowns x fastest, so
+    // kl = ku = mx; pivots in FP64 (Sec. 6.3 factors the block once for all
+    // P modes).  Entries from Theorem A.5 / A.6: L = D_y (x) T_x + T_y (x) D_x
+    // (D = I for Dirichlet sides), D_1 = k/h on every absorbing boundary node
+    // (corners once), D_2 = d_x d_y k^2.
+    const int mx = h->mx, my = h->my, kl = mx, ku = mx, kv = kl + ku, ldab = 2 * kl + ku + 1;
+    const double bytes = 2.0 * (double)ldab * n * (sizeof(double2) + sizeof(float2));
+    if (band_fits(kl, ku) && bytes <= 16e9) {
+      Pencil1D px = pencil(mx, h->h, h->bc[0] == SG_BC_ABSORBING, h->bc[1] == SG_BC_ABSORBING);
+      Pencil1D py = pencil(my, h->h, h->bc[2] == SG_BC_ABSORBING, h->bc[3] == SG_BC_ABSORBING);
+      for (int which = 0; which < 2; ++which) {
+        const double bc_ = which == 0 ? 0.0 : h->beta;
+        std::vector<double2> ab((size_t)ldab * n, make_double2(0.0, 0.0));
+        auto set = [&](int i, int c, double re, double im) {
+          ab[(size_t)kv + i - c + (size_t)c * ldab] = make_double2(re, im);
+        };
+        for (int jy = 0; jy < my; ++jy)
+          for (int ix = 0; ix < mx; ++ix) {
+            const int u = ix + mx * jy;
+            const double w2 = px.d[ix] * py.d[jy];
+            const double w1 = (px.e[ix] > 0.0 || py.e[jy] > 0.0) ? 1.0 / h->h : 0.0;
+            const double k = h->k0u[u];
+            set(u, u, py.d[jy] * px.tdiag[ix] + py.tdiag[jy] * px.d[ix] - w2 * k * k, -w1 * k - bc_ * w2 * k * k);
+            if (ix > 0) set(u, u - 1, py.d[jy] * px.toff[ix - 1], 0.0);
+            if (ix + 1 < mx) set(u, u + 1, py.d[jy] * px.toff[ix], 0.0);
+            if (jy > 0) set(u, u - mx, py.toff[jy - 1] * px.d[ix], 0.0);
+            if (jy + 1 < my) set(u, u + mx, py.toff[jy] * px.d[ix], 0.0);
+          }
+        BandFactor& f = h->blk[which].band;
+        f.n = n; f.kl = kl; f.ku = ku; f.ldab = ldab;
+        if (upload(&f.ab, ab.data(), ab.size())) return fail(SG_ENOMEM, "band factor upload");
+        SG_CUDA_TRY(cudaMalloc((void**)&f.ab32, ab.size() * sizeof(float2)));
+        SG_CUDA_TRY(cudaMalloc((void**)&f.piv, (size_t)n * sizeof(int)));
+        SG_CUDA_TRY(band_factor(f, d_bad, st));
+        SG_CUDA_TRY(cudaStreamSynchronize(st));
+        h->blk[which].ready = true;
       }
     }
   }

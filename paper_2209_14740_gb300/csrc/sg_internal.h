@@ -77,10 +77,31 @@ struct TriFactors {
   uint8_t* piv = nullptr; // 1 if rows j, j+1 were swapped
 };
 
+// Banded LU with partial pivoting (k_band.cu; LAPACK gbtrf layout: column j
+// at ab + j * ldab, entry (i, j) at row kl + ku + i - j, ldab = 2 kl + ku + 1),
+// factored in FP64 with an FP32 copy for complex64 solves.
+struct BandFactor {
+  int n = 0, kl = 0, ku = 0, ldab = 0;
+  double2* ab = nullptr;
+  float2* ab32 = nullptr;
+  int* piv = nullptr;
+};
+// Factors f.ab in place (FP64 pivots), fills f.piv and f.ab32; *d_bad = 1 on
+// a zero pivot.
+cudaError_t band_factor(BandFactor& f, int* d_bad, cudaStream_t st);
+// Z = A^-1 (s R) for nrhs right-hand sides (column q at q * ld, s = *in_scale
+// or 1), through the intermediate Y; R, Y, Z may be the same vector.
+template <typename T>
+cudaError_t band_solve(const BandFactor& f, int nrhs, const C2<T>* R, C2<T>* Y, C2<T>* Z, long long ld,
+                       cudaStream_t st, const int* skip, const double* in_scale);
+// Whether the solve kernel's shared memory holds a window of this band.
+bool band_fits(int kl, int ku);
+
 struct PrecBlock {
   bool ready = false;
   TriFactors<double> f64;
   TriFactors<float> f32;
+  BandFactor band;          // 2D blocks without a separable inverse (k_0 varies in space)
 };
 
 // Constant right factor of a tensor-core complex GEMM (k_tc_gemm.cu): the

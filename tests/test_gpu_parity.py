@@ -143,15 +143,13 @@ def test_rhs_point_source(B):
         op.close()
 
 
-PREC_CASES = [0, 1, 2, 3, 7, 8, 9, 10, 12]   # 1D, or 2D with constant k_0 (index 3 is skipped)
+PREC_CASES = [0, 1, 2, 3, 7, 8, 9, 10, 12]   # 1D, 2D with constant k_0, and index 3 (k_0 varies: band LU)
 
 
 @pytest.mark.parametrize("idx", PREC_CASES)
 @pytest.mark.parametrize("kind", [1, 2])
 def test_precond(B, idx, kind):
     pr = problems()[idx]
-    if pr.dim == 2 and np.ptp(pr.k0) > 0:
-        pytest.skip("2D preconditioner needs constant k_0")
     ref = sg.assemble_problem(pr)
     blk = ref.S0 if kind == 1 else sg.csl_mean_block(ref, pr.beta)
     M = krylov.BlockPrecond(blk, ref.P)
@@ -289,18 +287,22 @@ def test_precond_tf32_needs_the_2d_route(B):
     op.close()
 
 
-def test_precond_unsupported_for_varying_k0(B):
+def test_tf32_unsupported_for_varying_k0(B):
+    """A 2D problem whose k_0 varies has the banded block solve (FP64, FP32),
+    not the fast-diagonalisation route: SG_TF32 is refused."""
     pr = problems()[3]
     assert np.ptp(pr.k0) > 0
     op = B.SG(pr)
-    X = torch.zeros(op.N, dtype=torch.complex128, device=DEV)
+    assert not op.info["separable"] and not op.info["tf32_route"]
+    X = torch.zeros(op.N, dtype=torch.complex64, device=DEV)
     with pytest.raises(B.SgError) as ei:
-        op.precond(X, X, B.PREC_MEAN, B.FP64)
+        op.precond(X, X, B.PREC_MEAN, B.TF32)
     assert ei.value.status == B.SG_EUNSUPPORTED
     op.close()
 
 
 GMRES_CASES = [(0, 0, 1), (0, 0, 2), (0, 0, 0), (1, 0, 1), (7, 20, 1), (7, 20, 2), (8, 10, 1), (4, 15, 0),
+               (3, 15, 1), (3, 15, 2),
                (12, 0, 1), (12, 0, 2)]
 
 

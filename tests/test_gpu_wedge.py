@@ -1,0 +1,139 @@
+"""The paper's 2D wedge workload (Sec. 7) on the GPU: k_0 varies in space,
+so the mean-value block S(xi_bar) has no separable inverse and the library
+factors it as a band (LU with FP64 partial pivoting, kl = ku = q + 2), one
+factorisation for all P modes (Sec. 6.3).
+
+* the banded block solve against SuperLU's (oracle.krylov.BlockPrecond),
+  FP64 within 1e-10, FP32 within kappa_1 u32 plus a backward-error bound;
+* FP64 GMRES on the wedge at degree 3 against the oracle's GMRES with the
+  same restart and preconditioner: iteration counts within +-2 at tol 1e-8,
+  and the solutions within 1e-10 at tol 1e-13;
+* the paper's own experiment at degree 8 (2,745,765 unknowns): iteration
+  counts inside the bands around the printed "about 20" (theta = 0.1) and
+  "about 60" (theta = 0.2) (tests/golden/sec7_wedge_gmres.txt), the FP64
+  residual recomputed with the FP64 operator, and the mixed-precision path
+  reaching 1e-8 as well.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import krylov, sg
+from paper_2209_14740_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sec7_wedge_gmres.txt")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2209_14740_gb300 import binding
+    binding.load()
+    return binding
+
+
+def golden_counts():
+    out = {}
+    for line in open(GOLDEN):
+        if line.strip() and not line.startswith("#"):
+            th, c, lo, hi = line.split()
+            out[float(th)] = (int(c), int(lo), int(hi))
+    return out
+
+
+@pytest.mark.parametrize("q,r,bc", [(31, 2, "abs"), (20, 2, "abs"), (23, 1, "dir")])
+def test_band_block_solve(B, q, r, bc):
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    pr = inputs.wedge(q, 0.1, r)
+    if bc == "dir":
+        pr.bc = (inputs.DIRICHLET,) * 4
+    ref = sg.assemble_problem(pr)
+    op = B.SG(pr)
+    assert not op.info["separable"]
+    rng = np.random.default_rng(q + r)
+    for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+        blk = ref.S0 if kind == B.PREC_MEAN else sg.csl_mean_block(ref, pr.beta)
+        M = krylov.BlockPrecond(blk, ref.P)
+        x = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+        zr = M(x)
+        X = torch.from_numpy(x).to(DEV)
+        Z = torch.empty_like(X)
+        op.precond(X, Z, kind, B.FP64)
+        e64 = np.linalg.norm(Z.cpu().numpy() - zr) / np.linalg.norm(zr)
+        op.precond(X, X, kind, B.FP64)
+        e64i = np.linalg.norm(X.cpu().numpy() - zr) / np.linalg.norm(zr)
+        assert e64 <= 1e-10 and e64i <= 1e-10, (e64, e64i)
+        lu = spl.splu(sp.csc_matrix(blk))
+        n = blk.shape[0]
+        inv = spl.LinearOperator((n, n), matvec=lambda v: lu.solve(np.asarray(v, complex).ravel()),
+                                 rmatvec=lambda v: lu.solve(np.asarray(v, complex).ravel(), trans="H"), dtype=complex)
+        kappa1 = spl.norm(blk, 1) * spl.onenormest(inv)
+        x32 = x.astype(np.complex64)
+        zr32 = M(x32.astype(np.complex128))
+        X32 = torch.from_numpy(x32).to(DEV)
+        Z32 = torch.empty_like(X32)
+        op.precond(X32, Z32, kind, B.FP32)
+        z32 = Z32.cpu().numpy().astype(np.complex128)
+        e32 = np.linalg.norm(z32 - zr32) / np.linalg.norm(zr32)
+        assert e32 <= kappa1 * 2.0 ** -24, (e32, kappa1)
+        Zm, Rm = z32.reshape(ref.P, n).T, x32.astype(np.complex128).reshape(ref.P, n).T
+        back = np.linalg.norm(blk @ Zm - Rm) / (np.linalg.norm(abs(blk) @ np.abs(Zm)) + np.linalg.norm(Rm))
+        assert back <= 1e-6, back
+    op.close()
+
+
+@pytest.mark.parametrize("theta", [0.1, 0.2])
+def test_wedge_gmres_against_oracle(B, theta):
+    pr = inputs.wedge(127, theta, 3)
+    ref = sg.assemble_problem(pr)
+    M = krylov.BlockPrecond(ref.S0, ref.P)
+    ro = krylov.gmres(ref.A, ref.b, M, restart=200, tol=1e-8, maxit=400)
+    op = B.SG(pr)
+    b = torch.from_numpy(ref.b).to(DEV)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=200, tol=1e-8, prec=B.PREC_MEAN, mode=B.FP64, maxit=400)
+    relres = np.linalg.norm(ref.b - ref.A @ x.cpu().numpy()) / np.linalg.norm(ref.b)
+    print("wedge q=127 r=3 theta=%g: iters %d (oracle %d), relres %.2e" % (theta, info["iters"], ro.iters, relres))
+    assert info["status"] == B.SG_OK and relres <= 1e-8
+    assert abs(info["iters"] - ro.iters) <= 2, (info["iters"], ro.iters)
+    if theta == 0.1:
+        ro2 = krylov.gmres(ref.A, ref.b, M, restart=200, tol=1e-13, maxit=400)
+        x2 = torch.zeros_like(b)
+        op.gmres(b, x2, restart=200, tol=1e-13, prec=B.PREC_MEAN, mode=B.FP64, maxit=400)
+        xg = x2.cpu().numpy()
+        err = np.linalg.norm(xg - ro2.x) / np.linalg.norm(ro2.x)
+        emax = np.abs(xg - ro2.x).max() / np.abs(ro2.x).max()
+        print("  tol 1e-13: err vs oracle %.2e (max-norm %.2e)" % (err, emax))
+        assert err <= 1e-10 and emax <= 1e-10
+    op.close()
+
+
+@pytest.mark.parametrize("theta", [0.1, 0.2])
+def test_wedge_degree8_paper_counts(B, theta):
+    """Sec. 7: degree 8 (P = 165), full GMRES, tol 1e-8, A_0 from the right."""
+    c, lo, hi = golden_counts()[theta]
+    pr = inputs.wedge(127, theta, 8)
+    op = B.SG(pr)
+    assert op.P == 165 and op.N == 2745765
+    b = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+    op.rhs(b, B.FP64)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=0, tol=1e-8, prec=B.PREC_MEAN, mode=B.FP64, maxit=400)
+    Ax = torch.empty_like(x)
+    op.matvec(x, Ax, B.FP64)
+    relres = float(torch.linalg.vector_norm(b - Ax) / torch.linalg.vector_norm(b))
+    xm = torch.zeros_like(b)
+    im = op.gmres(b, xm, restart=0, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, maxit=400)
+    op.matvec(xm, Ax, B.FP64)
+    relres_m = float(torch.linalg.vector_norm(b - Ax) / torch.linalg.vector_norm(b))
+    err_m = float(torch.linalg.vector_norm(xm - x) / torch.linalg.vector_norm(x))
+    print("wedge r=8 theta=%g: FP64 %d iterations (paper about %d), relres %.2e; mixed %d steps, %d refinements, "
+          "relres %.2e, vs FP64 %.2e" % (theta, info["iters"], c, relres, im["iters"], im["outer"], relres_m, err_m))
+    assert info["status"] == B.SG_OK and relres <= 1e-8
+    assert lo <= info["iters"] <= hi, (info["iters"], lo, hi)
+    assert im["status"] == B.SG_OK and relres_m <= 1e-8
+    op.close()

@@ -137,3 +137,27 @@ def test_wedge_degree8_paper_counts(B, theta):
     assert lo <= info["iters"] <= hi, (info["iters"], lo, hi)
     assert im["status"] == B.SG_OK and relres_m <= 1e-8
     op.close()
+
+
+def test_wedge_stationary_iteration(B):
+    """Sec. 7: the stationary iteration with B = A_0 converges for theta =
+    0.1 and diverges for theta = 0.2 (wedge, degree 2, q = 63 as in the
+    oracle's test); the device iterates match the oracle's."""
+    for theta, converges in ((0.1, True), (0.2, False)):
+        pr = inputs.wedge(63, theta, 2)
+        S = sg.assemble_problem(pr)
+        M = krylov.BlockPrecond(S.S0, S.P)
+        xo, _ = krylov.stationary(S.A, M, S.b, 10)
+        op = B.SG(pr)
+        b = torch.from_numpy(S.b).to(DEV)
+        x = torch.zeros_like(b)
+        info, hist = op.stationary(b, x, prec=B.PREC_MEAN, mode=B.FP64, maxit=11, tol=0.0)
+        err = np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo)
+        assert err <= 1e-10, (theta, err)
+        x.zero_()
+        info, hist = op.stationary(b, x, prec=B.PREC_MEAN, mode=B.FP64, maxit=60, tol=1e-8)
+        if converges:
+            assert info["status"] == B.SG_OK, info
+        else:
+            assert info["status"] != B.SG_OK and hist[-1] > hist[1], (info, hist[:3], hist[-1])
+        op.close()

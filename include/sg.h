@@ -64,8 +64,14 @@ typedef enum { SG_BC_DIRICHLET = 0, SG_BC_ABSORBING = 1 } sg_bc;
  *                     uniform variables, so S(xi_bar) is the FD matrix of the
  *                     wavenumber k_0 (Sec. 5, Remark 6.1);
  *   SG_PREC_CSL_MEAN  mean-value complex shifted Laplace
- *                     M_0 = I_P (x) (S(xi_bar) - i beta D_2(k_0^2)) (Sec. 6.3). */
-typedef enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_CSL_MEAN = 2 } sg_prec;
+ *                     M_0 = I_P (x) (S(xi_bar) - i beta D_2(k_0^2)) (Sec. 6.3);
+ *   SG_PREC_CSL       the coupled complex shifted Laplace matrix
+ *                     M(beta) = A - i beta K, K = [C_ij] the k^2 part of A
+ *                     (Sec. 4; the paper uses it in 1D), factored as a band
+ *                     with the unknowns numbered point by point (kl = ku = P in
+ *                     1D, mx P in 2D) on first use; SG_EUNSUPPORTED when that
+ *                     band is too wide (most 2D problems). */
+typedef enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_CSL_MEAN = 2, SG_PREC_CSL = 3 } sg_prec;
 
 /* SG_FP64: complex128 operands and arithmetic.
  * SG_FP32: complex64 operands and arithmetic (reductions accumulate in FP64
@@ -228,6 +234,10 @@ typedef struct {
   int host_io;          /* 1: b, x0, x are HOST buffers (copied in and out inside the call) */
   int check_every;      /* steps between host reads of the convergence flag; <= 0 means 8 */
   int x0_policy;        /* sg_x0_policy: how a supplied x0 is used (0 = as given) */
+  int side;             /* 0: right preconditioning A M^-1 y = b, x = M^-1 y, stopping on
+                           ||b - A x|| / ||b||; 1: left, M^-1 A x = M^-1 b, stopping on
+                           ||M^-1 (b - A x)|| / ||M^-1 b|| (Sec. 6.3 compares both; SG_FP64 and
+                           SG_FP32 only) */
 } sg_gmres_opts;
 
 typedef struct {
@@ -236,6 +246,8 @@ typedef struct {
   int cycles;           /* restart cycles */
   double relres;        /* final ||b - A x|| / ||b|| computed in FP64 (FP32 for SG_FP32) */
   sg_status status;
+  double relres_prec;   /* the stopping quantity: ||M^-1 (b - A x)|| / ||M^-1 b|| for side = 1,
+                           relres otherwise */
 } sg_gmres_info;
 
 /* Solves A x = b with restarted, right-preconditioned GMRES: Arnoldi by

@@ -19,7 +19,7 @@ SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ENOTCONV, SG_EBREAKDOWN, SG_ESINGULAR,
 STATUS_NAMES = ["SG_OK", "SG_EINVAL", "SG_ENOMEM", "SG_ECUDA", "SG_ENOTCONV", "SG_EBREAKDOWN",
                 "SG_ESINGULAR", "SG_ETIMEOUT", "SG_EUNSUPPORTED"]
 BC_DIRICHLET, BC_ABSORBING = 0, 1
-PREC_NONE, PREC_MEAN, PREC_CSL_MEAN = 0, 1, 2
+PREC_NONE, PREC_MEAN, PREC_CSL_MEAN, PREC_CSL = 0, 1, 2, 3
 FP64, FP32, MIXED, TF32 = 0, 1, 2, 3
 X0_AS_GIVEN, X0_FALLBACK, X0_SCALED = 0, 1, 2
 
@@ -51,12 +51,12 @@ class SgInfo(C.Structure):
 class SgGmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("max_outer", C.c_int), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("prec", C.c_int), ("mode", C.c_int), ("x0", C.c_void_p),
-                ("host_io", C.c_int), ("check_every", C.c_int), ("x0_policy", C.c_int)]
+                ("host_io", C.c_int), ("check_every", C.c_int), ("x0_policy", C.c_int), ("side", C.c_int)]
 
 
 class SgGmresInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("cycles", C.c_int), ("relres", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("relres_prec", C.c_double)]
 
 
 class SgStationaryOpts(C.Structure):
@@ -354,9 +354,10 @@ class SG:
 
     def gmres(self, b, x, *, restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, x0=None, max_outer=0,
               inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False,
-              x0_policy=0):
+              x0_policy=0, side=0):
         o = SgGmresOpts()
         o.x0_policy = x0_policy
+        o.side = side
         o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
         o.prec, o.mode = prec, mode
         o.x0 = _ptr(x0) if x0 is not None else None
@@ -367,12 +368,14 @@ class SG:
                              None if host_io and stream is None else _stream(stream))
         if st not in (SG_OK, SG_ENOTCONV) or (raise_on_notconv and st == SG_ENOTCONV):
             _check(st)
-        return dict(iters=inf.iters, outer=inf.outer, cycles=inf.cycles, relres=inf.relres, status=st)
+        return dict(iters=inf.iters, outer=inf.outer, cycles=inf.cycles, relres=inf.relres, status=st,
+                    relres_prec=inf.relres_prec)
 
 
 def _opts(restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, max_outer=0, inner_tol=0.0, host_io=False,
-          check_every=0, x0_policy=0):
+          check_every=0, x0_policy=0, side=0):
     o = SgGmresOpts()
+    o.side = side
     o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
     o.prec, o.mode = prec, mode
     o.x0 = None

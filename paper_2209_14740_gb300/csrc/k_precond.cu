@@ -469,9 +469,50 @@ cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, 
 // Z = M^-1 R for block `which`; tmp and tmp2 hold N complex128 values each
 // (tmp2 only for 2D; the FP32 2D transforms use up to 2N complex64 of each
 // for their even-length rows).  R and Z may be the same vector.
+// Mode-major (V_a over the grid, the ABI's layout) <-> point-by-point order
+// (row u P + a, the coupled CSL band's numbering), with the input scale.
+template <typename T>
+__global__ void k_to_points(const C2<T>* __restrict__ R, int n, int P, C2<T>* __restrict__ out,
+                            const double* __restrict__ in_scale, const int* skip) {
+  if (skip && *skip) return;
+  const T s = in_scale ? (T)*in_scale : (T)1;
+  const long long N = (long long)n * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    const long long u = e / P, a = e - u * P;
+    C2<T> v = R[a * n + u];
+    v.x *= s;
+    v.y *= s;
+    out[e] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_from_points(const C2<T>* __restrict__ in, int n, int P, C2<T>* __restrict__ Z, const int* skip) {
+  if (skip && *skip) return;
+  const long long N = (long long)n * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+    const long long a = e / n, u = e - a * n;
+    Z[e] = in[u * P + a];
+  }
+}
+
 template <typename T>
 static cudaError_t precond_apply(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                  const int* skip, const double* in_scale, C2<T>* tmp, C2<T>* tmp2) {
+  if (which == 2) {
+    // the coupled CSL matrix: its band is numbered point by point, one right-hand side
+    if (!h->csl_full.ab) return cudaErrorNotReady;
+    const long long N = h->N;
+    const int grid = (int)std::min<long long>((N + 255) / 256, 4096);
+    k_to_points<T><<<grid, 256, 0, st>>>(R, h->n, h->P, tmp, in_scale, skip);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = band_solve<T>(h->csl_full, 1, tmp, tmp, tmp, N, st, skip, nullptr);
+    if (e != cudaSuccess) return e;
+    k_from_points<T><<<grid, 256, 0, st>>>(tmp, h->n, h->P, Z, skip);
+    note_launch();
+    return cudaGetLastError();
+  }
   const PrecBlock& blk = h->blk[which];
   TriFactors<T> F;
   if constexpr (sizeof(T) == 8) F = blk.f64; else F = blk.f32;

@@ -196,6 +196,7 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_gval); cudaFree(h->d_gdiag); cudaFree(h->d_fields); cudaFree(h->d_b0);
   cudaFree(h->d_gval32); cudaFree(h->d_gdiag32); cudaFree(h->d_fields32);
   for (auto& b : h->blk) if (b.f64.dl || b.band.ab) free_factors(b);
+  cudaFree(h->csl_full.ab); cudaFree(h->csl_full.ab32); cudaFree(h->csl_full.piv);
   cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
   cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
   cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
@@ -456,6 +457,126 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
   return status;
 }
 
+namespace sgi {
+
+// The coupled CSL matrix M(beta) = L - iB - (1 + i beta) C = A - i beta K of
+// Sec. 4 (K = [C_ij], the k^2 part of A; Theorem 3.4), numbered point by
+// point: row u P + a for grid unknown u and chaos mode a.  Within a grid
+// unknown the P x P coupling of Sec. 3.2 (<k phi_a phi_b> with D_1, <k^2
+// phi_a phi_b> with D_2); between neighbouring unknowns the FD stencil of
+// L on each mode.  So the band has kl = ku = P in 1D and mx P in 2D.
+// Assembled on the host from the chaos tables and factored (FP64 pivots) on
+// first use; too wide a band returns SG_EUNSUPPORTED.
+sg_status ensure_csl_full(sg_handle* h, cudaStream_t st) {
+  if (h->csl_full.ab) return SG_OK;
+  const int n = h->n, P = h->P, s = h->s, mx = h->mx, my = h->my;
+  const long long N = h->N;
+  const int kl = (h->dim == 1 ? 1 : mx) * P, ku = kl, kv = kl + ku, ldab = 2 * kl + ku + 1;
+  if (!band_fits(kl, ku) || (double)N * kl * (double)(kl + ku) > 2e9)
+    return fail(SG_EUNSUPPORTED, "the coupled CSL matrix's band (" + std::to_string(kl) +
+                                     " sub-diagonals) is too wide for the banded factorisation");
+  // term t -> (l, l') of its coefficient field(s)
+  std::vector<int> tl(h->T_terms, 0), tl2(h->T_terms, 0);
+  for (int l = 0; l < s; ++l) {
+    tl[l] = l;
+    tl[s + l] = l;
+    for (int lp = l + 1; lp < s; ++lp) {
+      const int t = 2 * s + pair_index(s, l, lp);
+      tl[t] = l;
+      tl2[t] = lp;
+    }
+  }
+  Pencil1D px = pencil(mx, h->h, h->bc[0] == SG_BC_ABSORBING, h->bc[1] == SG_BC_ABSORBING);
+  Pencil1D py = h->dim == 2 ? pencil(my, h->h, h->bc[2] == SG_BC_ABSORBING, h->bc[3] == SG_BC_ABSORBING) : Pencil1D{};
+  const double beta = h->beta;
+  std::vector<double2> ab((size_t)ldab * N, make_double2(0.0, 0.0));
+  auto set = [&](long long i, long long c, double re, double im) {
+    ab[(size_t)(kv + i - c) + (size_t)c * ldab] = make_double2(re, im);
+  };
+  const double* F = h->fields_host.data();
+  for (int jy = 0; jy < my; ++jy)
+    for (int ix = 0; ix < mx; ++ix) {
+      const int u = ix + mx * jy;
+      double lu, w1, w2;
+      if (h->dim == 1) {
+        lu = px.tdiag[ix];
+        w1 = px.e[ix] / h->h;
+        w2 = px.d[ix];
+      } else {
+        lu = py.d[jy] * px.tdiag[ix] + py.tdiag[jy] * px.d[ix];
+        w1 = (px.e[ix] > 0.0 || py.e[jy] > 0.0) ? 1.0 / h->h : 0.0;
+        w2 = px.d[ix] * py.d[jy];
+      }
+      const double k0 = F[u];
+      for (int a = 0; a < P; ++a) {
+        const long long row = (long long)u * P + a;
+        // <k^2 phi_a phi_a> and <k phi_a phi_a> = k_0
+        double d2 = k0 * k0;
+        for (int l = 0; l < s; ++l) {
+          const double kl_ = F[(size_t)(l + 1) * n + u];
+          d2 += kl_ * kl_ * h->gdiag[(size_t)l * P + a];
+        }
+        set(row, row, lu - w2 * d2, -w1 * k0 - beta * w2 * d2);
+        for (int e = h->rowptr[a]; e < h->rowptr[a + 1]; ++e) {
+          const int b = h->col[e], t = h->term[e];
+          const double g = h->gval[e];
+          const double kA = F[(size_t)(tl[t] + 1) * n + u];
+          double c1 = 0.0, c2;
+          if (t < s) {
+            c1 = kA;
+            c2 = 2.0 * k0 * kA;
+          } else if (t < 2 * s) {
+            c2 = kA * kA;
+          } else {
+            c2 = 2.0 * kA * F[(size_t)(tl2[t] + 1) * n + u];
+          }
+          set(row, (long long)u * P + b, -w2 * c2 * g, -w1 * c1 * g - beta * w2 * c2 * g);
+        }
+        // the FD stencil between neighbouring unknowns, mode by mode
+        if (h->dim == 1) {
+          if (ix > 0) set(row, row - P, px.toff[ix - 1], 0.0);
+          if (ix + 1 < mx) set(row, row + P, px.toff[ix], 0.0);
+        } else {
+          if (ix > 0) set(row, row - P, py.d[jy] * px.toff[ix - 1], 0.0);
+          if (ix + 1 < mx) set(row, row + P, py.d[jy] * px.toff[ix], 0.0);
+          if (jy > 0) set(row, row - (long long)mx * P, py.toff[jy - 1] * px.d[ix], 0.0);
+          if (jy + 1 < my) set(row, row + (long long)mx * P, py.toff[jy] * px.d[ix], 0.0);
+        }
+      }
+    }
+  BandFactor f;
+  f.n = (int)N; f.kl = kl; f.ku = ku; f.ldab = ldab;
+  int* d_bad = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (upload(&f.ab, ab.data(), ab.size())) e = cudaErrorMemoryAllocation;
+  if (!e) e = cudaMalloc((void**)&f.ab32, ab.size() * sizeof(float2));
+  if (!e) e = cudaMalloc((void**)&f.piv, (size_t)N * sizeof(int));
+  if (!e) e = cudaMalloc((void**)&d_bad, sizeof(int));
+  if (!e) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  if (!e) e = band_factor(f, d_bad, st);
+  int bad = 0;
+  if (!e) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  cudaFree(d_bad);
+  if (e || bad) {
+    cudaFree(f.ab); cudaFree(f.ab32); cudaFree(f.piv);
+    if (e) return fail(SG_ECUDA, std::string("coupled CSL factorisation: ") + cudaGetErrorString(e));
+    return fail(SG_ESINGULAR, "zero pivot in the coupled CSL factorisation");
+  }
+  h->csl_full = f;
+  return SG_OK;
+}
+
+// Block index of a preconditioner kind (0 mean value, 1 CSL mean value, 2
+// coupled CSL) and whether it is available for the handle.
+bool prec_available(const sg_handle* h, sg_prec kind) {
+  if (kind == SG_PREC_MEAN) return h->blk[0].ready;
+  if (kind == SG_PREC_CSL_MEAN) return h->blk[1].ready;
+  return kind == SG_PREC_CSL;
+}
+
+}  // namespace sgi
+
 extern "C" {
 
 const char* sg_last_error(void) { return sgi::g_err.c_str(); }
@@ -554,6 +675,7 @@ sg_status sg_assemble(const sg_desc* desc, void* stream, sg_handle** out) {
     h->specialised = matvec_is_specialised(h->s, h->r) ? 1 : 0;
     h->separable = (k0max - k0min) <= 1e-13 * k0max;
     h->k0u.assign(fields.begin(), fields.begin() + n);
+    h->fields_host = fields;
 
     // chaos tables
     h->alpha = multi_indices(s, h->r);
@@ -679,10 +801,16 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
       if (R != Z) SG_CUDA_TRY(cudaMemcpyAsync(Z, R, bytes, cudaMemcpyDeviceToDevice, st));
       return SG_OK;
     }
-    if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN) return fail(SG_EINVAL, "unknown preconditioner");
-    int which = kind == SG_PREC_MEAN ? 0 : 1;
-    if (!h->blk[which].ready)
-      return fail(SG_EUNSUPPORTED, "no factorisation for this block (2D needs a constant k_0)");
+    if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN && kind != SG_PREC_CSL)
+      return fail(SG_EINVAL, "unknown preconditioner");
+    const int which = kind == SG_PREC_MEAN ? 0 : kind == SG_PREC_CSL_MEAN ? 1 : 2;
+    if (which == 2) {
+      if (prec == SG_TF32) return fail(SG_EUNSUPPORTED, "SG_TF32 has no coupled CSL route");
+      sg_status s = ensure_csl_full(h, st);
+      if (s != SG_OK) return s;
+    } else if (!h->blk[which].ready) {
+      return fail(SG_EUNSUPPORTED, "no factorisation for this block (its band is too wide for the device solve)");
+    }
     if (prec == SG_TF32) {
       if (h->dim != 2 || !h->fd)
         return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with constant k_0 (the fast-diagonalisation route)");

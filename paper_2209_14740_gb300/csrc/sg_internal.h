@@ -192,6 +192,7 @@ struct sg_handle {
   std::vector<double> gval, gdiag;   // off-diagonal values, diagonal moments [l][a]
   std::vector<double> b0;            // n, FD-weighted source on the unknowns
   std::vector<double> k0u;           // n, k_0 on the unknowns
+  std::vector<double> fields_host;   // (s+1) n: k_0, k_1..k_s on the unknowns
 
   // device tables
   int *d_rowptr = nullptr, *d_col = nullptr, *d_term = nullptr;
@@ -200,6 +201,9 @@ struct sg_handle {
 
   // preconditioner data
   sgi::PrecBlock blk[2];             // [0] mean value S(xi_bar), [1] CSL M_0 block
+  // the coupled CSL matrix M(beta) = A - i beta K (Sec. 4), numbered point by
+  // point (row u P + a), banded; factored on first use
+  sgi::BandFactor csl_full;
   double2* d_Q = nullptr;            // 2D: Qhat = D_x^-1/2 Q, row-major mx x mx
   double2* d_Qt = nullptr;           // 2D: Qhat^T
   float2* d_Q32 = nullptr;
@@ -252,6 +256,13 @@ cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, 
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                    C2<T>* tmp, C2<T>* tmp2);
+
+// The coupled CSL matrix of Sec. 4 as a band, factored on first use
+// (sg_host.cpp); SG_EUNSUPPORTED when its band is too wide.
+sg_status ensure_csl_full(sg_handle* h, cudaStream_t st);
+// Whether a preconditioner kind can be applied for this handle (the coupled
+// CSL one is decided by ensure_csl_full).
+bool prec_available(const sg_handle* h, sg_prec kind);
 
 // Input and output widths of a warm-start network (mlp.cu).
 void mlp_dims(const sg_mlp* m, int* in_dim, int* out_dim);

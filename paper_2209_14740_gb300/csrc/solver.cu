@@ -1023,6 +1023,7 @@ struct Ctx {
   int grid;
   int pstride;
   int cg_grid;   // blocks of the CGS2 passes
+  bool left = false;   // left preconditioning: Arnoldi on M^-1 A
 };
 
 // Z = M^-1 (s R) with s = *in_scale (1 if null).
@@ -1038,7 +1039,8 @@ cudaError_t precond_apply(Ctx& c, sg_prec prec, const C2<T>* R, C2<T>* Z, const 
     if (R != Z) return cudaMemcpyAsync(Z, R, (size_t)c.h->N * sizeof(C2<T>), cudaMemcpyDeviceToDevice, c.st);
     return cudaSuccess;
   }
-  return launch_precond<T>(c.h, prec == SG_PREC_MEAN ? 0 : 1, R, Z, c.st, skip, in_scale);
+  return launch_precond<T>(c.h, prec == SG_PREC_MEAN ? 0 : prec == SG_PREC_CSL_MEAN ? 1 : 2, R, Z, c.st, skip,
+                           in_scale);
 }
 
 // Flexible GMRES (complex64 inner cycles with a preconditioner that has a
@@ -1048,7 +1050,8 @@ cudaError_t precond_apply(Ctx& c, sg_prec prec, const C2<T>* R, C2<T>* Z, const 
 // only the iteration count, not the attainable residual.
 template <typename T>
 static bool flexible(const Ctx& c, sg_prec prec) {
-  return sizeof(T) == sizeof(float) && prec != SG_PREC_NONE && c.h->gw.Zb != nullptr;
+  return sizeof(T) == sizeof(float) && !c.left && (prec == SG_PREC_MEAN || prec == SG_PREC_CSL_MEAN) &&
+         c.h->gw.Zb != nullptr;
 }
 
 // One Arnoldi step j with CGS2 on the inner-precision basis.
@@ -1069,11 +1072,16 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
     if constexpr (sizeof(T) == sizeof(float))
       e = launch_precond_tf32(c.h, prec == SG_PREC_MEAN ? 0 : 1, vj, Z, c.st, w.dctl, D + c.L.vscale + j);
     if (e) return e;
+  } else if (c.left) {
+    // left: w = M^-1 (vscale_j A V_j) = M^-1 A v_j
+    Z = reinterpret_cast<C2<T>*>(w.Z);
+    if ((e = launch_matvec<T>(c.h, vj, Z, c.st, w.dctl))) return e;
+    if ((e = precond_apply<T>(c, prec, Z, wv, w.dctl, D + c.L.vscale + j))) return e;
   } else {
     Z = reinterpret_cast<C2<T>*>(w.Z);
     if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
   }
-  if ((e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
+  if (!c.left && (e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
   const int nv = j + 1;
   const size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
   const int G = c.cg_grid;
@@ -1107,8 +1115,8 @@ template <typename T>
 cudaError_t arnoldi_steps(Ctx& c, sg_prec prec, int j0, int len) {
   GmresWork& w = c.h->gw;
   const unsigned long long key = ((unsigned long long)(sizeof(T) == 4) << 60) |
-                                 ((unsigned long long)prec << 56) | ((unsigned long long)j0 << 28) |
-                                 (unsigned long long)len;
+                                 ((unsigned long long)(c.left ? 1 : 0) << 59) | ((unsigned long long)prec << 56) |
+                                 ((unsigned long long)j0 << 28) | (unsigned long long)len;
   auto it = w.graphs.find(key);
   if (it == w.graphs.end()) {
     if (++w.graph_uses[key] < 2) {
@@ -1169,7 +1177,7 @@ sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int
   const C2<T>* basis = flex ? reinterpret_cast<const C2<T>*>(w.Zb) : V;
   k_lincomb<T><<<c.grid, RED_THREADS, 0, c.st>>>(basis, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
   SG_CUDA_TRY(cudaGetLastError());
-  if (!flex) SG_CUDA_TRY(precond_apply<T>(c, prec, Z, Z, nullptr));
+  if (!flex && !c.left) SG_CUDA_TRY(precond_apply<T>(c, prec, Z, Z, nullptr));
   return SG_OK;
 }
 
@@ -1232,12 +1240,21 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     if (!h || !opts || !b || !x) return fail(SG_EINVAL, "NULL argument to sg_gmres");
     if (opts->mode != SG_FP64 && opts->mode != SG_FP32 && opts->mode != SG_MIXED)
       return fail(SG_EINVAL, "bad mode");
-    if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN)
+    if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN &&
+        opts->prec != SG_PREC_CSL)
       return fail(SG_EINVAL, "bad preconditioner");
     if (!(opts->tol > 0) || !std::isfinite(opts->tol)) return fail(SG_EINVAL, "tol must be positive");
     if (opts->x0_policy < SG_X0_AS_GIVEN || opts->x0_policy > SG_X0_SCALED) return fail(SG_EINVAL, "bad x0_policy");
-    if (opts->prec != SG_PREC_NONE && !h->blk[opts->prec == SG_PREC_MEAN ? 0 : 1].ready)
-      return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (2D needs a constant k_0)");
+    if (opts->side != 0 && opts->side != 1) return fail(SG_EINVAL, "side must be 0 (right) or 1 (left)");
+    const bool left = opts->side == 1 && opts->prec != SG_PREC_NONE;
+    if (left && opts->mode == SG_MIXED)
+      return fail(SG_EUNSUPPORTED, "left preconditioning is available for SG_FP64 and SG_FP32, not SG_MIXED");
+    if (opts->prec == SG_PREC_CSL) {
+      sg_status s = ensure_csl_full(h, (cudaStream_t)stream);
+      if (s != SG_OK) return s;
+    } else if (opts->prec != SG_PREC_NONE && !prec_available(h, opts->prec)) {
+      return fail(SG_EUNSUPPORTED, "preconditioner not available for this problem (its band is too wide)");
+    }
     const long long N = h->N;
     int m = opts->restart <= 0 ? (int)std::min<long long>(N, MAXV - 1) : opts->restart;
     if (m > MAXV - 1) return fail(SG_EINVAL, "restart must be <= 511");
@@ -1266,6 +1283,7 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     } rejoin{w.ev, st, caller};
     Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
     c.L = DevLayout(w.restart);
+    c.left = left;
     // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
     const size_t obytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
 
@@ -1318,10 +1336,36 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
       if (info) *info = inf;
       return SG_OK;
     }
+    // left preconditioning measures residuals after M^-1: ||M^-1 b|| is the reference
+    // (M^-1 (b - A x) against it is the stopping test, MATLAB's convention)
+    auto prec_norm2 = [&](const void* v, double* out_host) -> sg_status {
+      double* out = w.dscal + c.L.sc + SC_WORK;
+      if (f32)
+        k_residual<float, float><<<c.grid, RED_THREADS, 0, st>>>((const float2*)v, nullptr, nullptr, N, w.part,
+                                                                 c.pstride, w.counter, out);
+      else
+        k_residual<double, double><<<c.grid, RED_THREADS, 0, st>>>((const double2*)v, nullptr, nullptr, N, w.part,
+                                                                   c.pstride, w.counter, out);
+      note_launch();
+      SG_CUDA_TRY(cudaGetLastError());
+      SG_CUDA_TRY(cudaMemcpyAsync(out_host, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(cudaStreamSynchronize(st));
+      return SG_OK;
+    };
+    double bnorm_ref = bnorm;
+    if (left) {
+      double bl2 = 0;
+      if (f32) SG_CUDA_TRY(precond_apply<float>(c, opts->prec, (const float2*)bd, (float2*)w.Z, nullptr));
+      else SG_CUDA_TRY(precond_apply<double>(c, opts->prec, (const double2*)bd, (double2*)w.R64, nullptr));
+      sg_status s = prec_norm2(f32 ? (const void*)w.Z : (const void*)w.R64, &bl2);
+      if (s != SG_OK) return s;
+      bnorm_ref = std::sqrt(bl2);
+      if (!(bnorm_ref > 0.0) || !std::isfinite(bnorm_ref)) return fail(SG_EBREAKDOWN, "||M^-1 b|| is zero or not finite");
+    }
     const int max_outer = mixed ? (opts->max_outer <= 0 ? 20 : opts->max_outer) : 1 << 30;
     const double inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
     int iters = 0, cycles = 0, outer = 0;
-    double relres = 1.0;
+    double relres = 1.0, relres_p = 1.0;
     int ctl[16];
     bool ax_ready = false;   // A x already in the residual scratch (scaled guess)
     if (!x_zero && opts->x0_policy == SG_X0_SCALED) {
@@ -1342,14 +1386,26 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
       ax_ready = false;
       if (s != SG_OK) return s;
       relres = std::sqrt(rn2) / bnorm;
+      relres_p = relres;
       if (cycles == 0 && !x_zero && opts->x0_policy != SG_X0_AS_GIVEN && !(relres <= 1.0)) {
         // the supplied guess is worse than zero: start from zero instead
         SG_CUDA_TRY(cudaMemsetAsync(xd, 0, obytes, st));
         x_zero = true;
         continue;
       }
-      if (!std::isfinite(relres)) { status = SG_EBREAKDOWN; break; }
-      if (relres <= opts->tol) { status = SG_OK; break; }
+      if (left) {
+        // the cycle starts from M^-1 r (in place in V_0) and its norm
+        double rp2 = 0;
+        if (f32) SG_CUDA_TRY(precond_apply<float>(c, opts->prec, (const float2*)w.V, (float2*)w.V, nullptr));
+        else SG_CUDA_TRY(precond_apply<double>(c, opts->prec, (const double2*)w.V, (double2*)w.V, nullptr));
+        s = prec_norm2(w.V, &rp2);
+        if (s != SG_OK) return s;
+        SG_CUDA_TRY(cudaMemcpyAsync(w.dscal + c.L.sc + SC_RNORM2, w.dscal + c.L.sc + SC_WORK, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+        relres_p = std::sqrt(rp2) / bnorm_ref;
+      }
+      if (!std::isfinite(relres) || !std::isfinite(relres_p)) { status = SG_EBREAKDOWN; break; }
+      if (relres_p <= opts->tol) { status = SG_OK; break; }
       if (iters >= maxit) { status = SG_ENOTCONV; break; }
       if (mixed && outer >= max_outer) { status = SG_ENOTCONV; break; }
       // inner tolerance on |g| relative to ref
@@ -1363,7 +1419,7 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
         tol_est = need >= 0.05 * inner_tol ? need : inner_tol;
         tol_est = std::min(tol_est, 0.5);
       } else {
-        ref = bnorm;
+        ref = bnorm_ref;
         tol_est = opts->tol;
       }
       bool any = false;
@@ -1411,6 +1467,7 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     inf.cycles = cycles;
     inf.outer = outer;
     inf.relres = relres;
+    inf.relres_prec = relres_p;
     inf.status = status;
     if (info) *info = inf;
     if (status == SG_ENOTCONV) set_error("GMRES did not reach tol within maxit");

@@ -248,6 +248,8 @@ typedef struct {
   sg_status status;
   double relres_prec;   /* the stopping quantity: ||M^-1 (b - A x)|| / ||M^-1 b|| for side = 1,
                            relres otherwise */
+  int graph_outer;      /* sg_gmres_batched: refinement steps run inside the one-graph launch
+                           (0 on the per-system route and for sg_gmres) */
 } sg_gmres_info;
 
 /* Solves A x = b with restarted, right-preconditioned GMRES: Arnoldi by
@@ -269,11 +271,24 @@ sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void*
                    sg_gmres_info* info, void* stream);
 
 /* Solves `count` independent SG systems (different grids, chaos sizes and
- * wavenumbers allowed) with the same options, concurrently: each system runs
- * the sg_gmres algorithm on its own internal CUDA stream, and up to
- * `concurrency` systems (<= 0 means min(count, 16)) are in flight at once,
- * driven by a pool of host threads.  Workspaces are allocated for all handles
- * before any solve starts.  The solves wait for work already queued on
+ * wavenumbers allowed) with the same options.
+ *   - One-graph route (SG_MIXED, device buffers, zero initial guesses, right
+ *     or no preconditioning; taken unless concurrency < 0): the whole batch
+ *     is ONE CUDA graph launch.  Each system is a chain of conditional nodes
+ *     (refinement steps, chunks of 8 Arnoldi steps) whose conditions its own
+ *     kernels set on the device, so restarts, refinements and convergence
+ *     are decided without the host; per-system records are read back once.
+ *     The graph is built and instantiated on the first call with a given
+ *     set of handles, vectors and options and reused afterwards.  It unrolls
+ *     4 refinement steps; a system still above tol after them continues on
+ *     the per-system route from its current iterate (its info sums both).
+ *     Arithmetic per system is sg_gmres's, so the result equals a solve of
+ *     that system alone.
+ *   - Per-system route (otherwise): each system runs sg_gmres on its own
+ *     internal CUDA stream, and up to `concurrency` systems (<= 0 means
+ *     min(count, 16)) are in flight at once, driven by a pool of host
+ *     threads.
+ * Workspaces are allocated for all handles before any solve starts.  The solves wait for work already queued on
  * `stream` and are complete when the call returns.  h[k], b[k], x[k] as in
  * sg_gmres (opts->host_io is honoured per system); x0 (may be NULL): per
  * system initial guesses overriding opts->x0 (entries may be NULL = zero).

@@ -56,7 +56,7 @@ class SgGmresOpts(C.Structure):
 
 class SgGmresInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("cycles", C.c_int), ("relres", C.c_double),
-                ("status", C.c_int), ("relres_prec", C.c_double)]
+                ("status", C.c_int), ("relres_prec", C.c_double), ("graph_outer", C.c_int)]
 
 
 class SgStationaryOpts(C.Structure):
@@ -400,5 +400,5 @@ def gmres_batched(ops, bs, xs, *, x0s=None, concurrency=0, stream=None, **kw):
                                  None if kw.get("host_io") and stream is None else _stream(stream))
     if st not in (SG_OK, SG_ENOTCONV):
         _check(st)
-    return st, [dict(iters=f.iters, outer=f.outer, cycles=f.cycles, relres=f.relres, status=f.status)
-                for f in infos]
+    return st, [dict(iters=f.iters, outer=f.outer, cycles=f.cycles, relres=f.relres, status=f.status,
+                     graph_outer=f.graph_outer) for f in infos]

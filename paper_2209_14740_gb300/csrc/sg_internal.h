@@ -167,6 +167,7 @@ struct GmresWork {
   std::map<unsigned long long, int> graph_uses;
   cudaStream_t stream = nullptr;   // private stream: capture needs a non-legacy stream
   cudaEvent_t ev = nullptr;
+  unsigned long long uid = 0;      // unique per allocation: keys the batched-solve graphs
 };
 
 }  // namespace sgi

@@ -22,7 +22,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -950,8 +952,11 @@ __global__ void k_convert(const C2<TA>* __restrict__ a, C2<TB>* __restrict__ b, 
 
 using namespace sgi;
 
+void sgi_forget_batched_graphs(unsigned long long uid);   // below
+
 void sgi_free_gmres_work(sg_handle* h) {
   GmresWork& w = h->gw;
+  if (w.uid) sgi_forget_batched_graphs(w.uid);
   for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
   if (w.stream) cudaStreamDestroy(w.stream);
   if (w.ev) cudaEventDestroy(w.ev);
@@ -1009,8 +1014,10 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
     sgi_free_gmres_work(h);
     return fail(SG_ENOMEM, std::string("GMRES workspace: ") + cudaGetErrorString(e));
   }
+  static std::atomic<unsigned long long> next_uid{1};
   w.restart = m;
   w.prec_bytes = elem_bytes;
+  w.uid = next_uid.fetch_add(1);
   return SG_OK;
 }
 
@@ -1586,4 +1593,399 @@ extern "C" sg_status sg_stationary(sg_handle* h, const sg_stationary_opts* opts,
     if (inf.status == SG_EBREAKDOWN) set_error("stationary iteration: non-finite residual (diverged)");
     return inf.status;
   });
+}
+
+// ------------------------------------------------------------------ batched solve as one graph
+// Independent SG systems solved by ONE cudaGraphLaunch: the graph holds one
+// chain per system, and the device decides the control flow the host takes
+// in sg_gmres.  Per system (mixed precision, zero initial guess):
+//   init: x = 0, r = b (complex64, V_0), ||b||^2;
+//   R times: [decide: relres = ||r|| / ||b||; at tol, maxit or a non-finite
+//            value the system stops, else a cycle starts (same inner
+//            tolerance rule as sg_gmres)] -> IF(cycle) {
+//              C times: [decide: not done] -> IF { Arnoldi steps 8c .. 8c+7 }
+//              least squares, correction, x += correction (FP64),
+//              r = b - A x (FP64 operator, FP64 norm) }
+//   finish: the system's record (steps, refinements, relres, status).
+// The plain kernel sequences are captured with the same launch code as
+// sg_gmres (so a system's arithmetic is the one-at-a-time solve's, bit for
+// bit); the IF nodes are conditional graph nodes whose values the decide
+// kernels set (cudaGraphSetConditional).  Systems still above tol after R
+// refinement steps are finished by the caller from where the graph left them.
+namespace {
+
+constexpr int BG_CHUNK = 8;        // Arnoldi steps per conditional chunk
+constexpr int BG_MAX_OUTER = 4;    // refinement steps unrolled in the graph
+
+struct BgRecord {                  // per system, device
+  int status;                      // 0 running, 1 converged, 2 breakdown, 3 step or refinement cap,
+                                   // 4 right-hand side not finite
+  int outer;                       // refinement steps started
+  int taken;                       // chunk bodies taken but the last of a cycle (for the launch count)
+  int taken_last;                  // last-chunk bodies taken
+  int iters;
+  double relres;
+};
+
+__global__ void k_bg_init(int* ctl, int maxit, BgRecord* rec) {
+  for (int i = 0; i < 16; ++i) ctl[i] = 0;
+  ctl[CTL_MAXIT] = maxit;
+  rec->status = 0;
+  rec->outer = 0;
+  rec->taken = 0;
+  rec->taken_last = 0;
+  rec->iters = 0;
+  rec->relres = 1.0;
+}
+
+// Start of refinement step: stop or start a cycle (k_cycle_init's work with
+// sg_gmres's mixed inner tolerance: reduce by inner_tol, or aim at tol
+// directly when that is within 20x of it).
+__global__ void k_bg_decide_outer(double* D, int* ctl, DevLayout L, double tol, double inner_tol, int max_outer,
+                                  cudaGraphConditionalHandle hdl, BgRecord* rec) {
+  const double bnorm = sqrt(D[L.sc + SC_BNORM]);
+  const double rn = sqrt(D[L.sc + SC_RNORM2]);
+  const double relres = bnorm == 0.0 ? 0.0 : rn / bnorm;   // b = 0: x = 0 is the solution
+  rec->relres = relres;
+  rec->iters = ctl[CTL_ITERS];
+  unsigned go = 0;
+  if (rec->status == 0) {
+    if (!(bnorm <= 1.7976931348623157e308)) {
+      rec->status = 4;
+    } else if (!(relres == relres) || relres > 1e300 || (ctl[CTL_FLAGS] & FL_NAN)) {
+      rec->status = 2;
+    } else if (relres <= tol) {
+      rec->status = 1;
+    } else if (ctl[CTL_ITERS] >= ctl[CTL_MAXIT] || rec->outer >= max_outer) {
+      rec->status = 3;
+    } else {
+      const double need = 0.5 * tol * bnorm / rn;
+      double tol_est = need >= 0.05 * inner_tol ? need : inner_tol;
+      tol_est = fmin(tol_est, 0.5);
+      for (int i = 0; i < 2 * (L.m + 1); ++i) D[L.g + i] = 0.0;
+      D[L.g] = rn;
+      D[L.vscale] = rn > 0 ? 1.0 / rn : 0.0;
+      D[L.sc + SC_TOL] = tol_est;
+      D[L.sc + SC_REF] = rn;
+      D[L.sc + SC_EST] = 1.0;
+      ctl[CTL_K] = 0;
+      ctl[CTL_DONE] = 0;
+      ctl[CTL_FLAGS] = 0;
+      rec->outer += 1;
+      go = 1;
+    }
+  }
+  cudaGraphSetConditional(hdl, go);
+}
+
+__global__ void k_bg_decide_chunk(const int* ctl, int last, cudaGraphConditionalHandle hdl, BgRecord* rec) {
+  const unsigned go = ctl[CTL_DONE] ? 0u : 1u;
+  if (last) rec->taken_last += (int)go;
+  else rec->taken += (int)go;
+  cudaGraphSetConditional(hdl, go);
+}
+
+// After the unrolled steps: the last residual decides (as the next
+// refinement step's test would).
+__global__ void k_bg_finish(const double* D, const int* ctl, DevLayout L, double tol, BgRecord* rec) {
+  const double bnorm = sqrt(D[L.sc + SC_BNORM]);
+  const double relres = bnorm == 0.0 ? 0.0 : sqrt(D[L.sc + SC_RNORM2]) / bnorm;
+  rec->iters = ctl[CTL_ITERS];
+  if (rec->status == 0) {
+    rec->relres = relres;
+    if (!(relres == relres) || relres > 1e300 || (ctl[CTL_FLAGS] & FL_NAN)) rec->status = 2;
+    else if (relres <= tol) rec->status = 1;
+  }
+}
+
+struct BgGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  BgRecord* rec = nullptr;           // count records, device
+  long long k_fixed = 0;             // kernels that run on every launch
+  std::vector<long long> k_outer;    // per system: kernels of one taken refinement step (without its chunks)
+  std::vector<long long> k_chunk;    // per system: kernels of a taken chunk (all but the last of a cycle)
+  std::vector<long long> k_last;     // per system: kernels of a taken last chunk
+  int count = 0;
+};
+
+// Graphs keyed by (restart, maxit, max_outer, preconditioner, tol, inner_tol,
+// then per system: workspace id, b, x).  Workspace ids are never reused, so a
+// graph can never name a freed or reallocated workspace; freeing a workspace
+// also drops the graphs that name it.
+constexpr int BG_KEY_HEAD = 6;
+std::mutex g_bg_mu;
+std::map<std::vector<uintptr_t>, BgGraph> g_bg_cache;
+
+void bg_free(BgGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  cudaFree(g.rec);
+  g = BgGraph{};
+}
+
+// Captures fn()'s launches on stream st into a new graph; the kernels it
+// records are counted in *nk and removed from the launch counter (they run
+// when the graph does).
+template <typename F>
+cudaError_t bg_capture(cudaStream_t st, F&& fn, cudaGraph_t* out, long long* nk) {
+  const long long t0 = thread_launches();
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t e1 = fn();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  *nk = thread_launches() - t0;
+  note_launches(-*nk);
+  if (e1 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e1;
+  }
+  if (e2 != cudaSuccess) return e2;
+  *out = g;
+  return cudaSuccess;
+}
+
+cudaError_t bg_add_child(cudaGraph_t parent, cudaGraphNode_t* prev, cudaGraph_t child) {
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, *prev ? prev : nullptr, *prev ? 1 : 0, child);
+  cudaGraphDestroy(child);
+  if (e == cudaSuccess) *prev = node;
+  return e;
+}
+
+cudaError_t bg_add_if(cudaGraph_t parent, cudaGraphNode_t* prev, cudaGraphConditionalHandle hdl, cudaGraph_t* body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hdl;
+  p.conditional.type = cudaGraphCondTypeIf;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddNode(&node, parent, *prev ? prev : nullptr, nullptr, *prev ? 1 : 0, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  *prev = node;
+  return cudaSuccess;
+}
+
+cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b, void* const* x,
+                     int m, int maxit, int max_outer, BgGraph* out) {
+  BgGraph G;
+  G.count = count;
+  G.k_outer.assign(count, 0);
+  G.k_chunk.assign(count, 0);
+  G.k_last.assign(count, 0);
+  cudaError_t e = cudaGraphCreate(&G.graph, 0);
+  if (!e) e = cudaMalloc((void**)&G.rec, (size_t)count * sizeof(BgRecord));
+  const double tol = opts->tol, inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
+  const int nch = (m + BG_CHUNK - 1) / BG_CHUNK;
+  for (int s = 0; s < count && !e; ++s) {
+    sg_handle* hs = h[s];
+    GmresWork& w = hs->gw;
+    Ctx c{hs, w.stream, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+    const long long N = hs->N;
+    const sg_prec prec = opts->prec;
+    BgRecord* rec = G.rec + s;
+    const double2* bs = static_cast<const double2*>(b[s]);
+    double2* xs = static_cast<double2*>(x[s]);
+    double* D = w.dscal;
+    // sg_gmres's step cap: opts->maxit, else min(N, 2^30)
+    const int maxit_s = maxit > 0 ? maxit : (int)std::min<long long>(N, 1 << 30);
+    cudaGraphNode_t prev = nullptr;
+    cudaGraph_t g = nullptr;
+    long long nk = 0;
+    // init
+    e = bg_capture(c.st, [&]() -> cudaError_t {
+      cudaError_t e3 = cudaMemsetAsync(xs, 0, (size_t)N * sizeof(double2), c.st);
+      if (e3) return e3;
+      k_bg_init<<<1, 1, 0, c.st>>>(w.dctl, maxit_s, rec); note_launch();
+      k_residual<double, double><<<c.grid, RED_THREADS, 0, c.st>>>(bs, nullptr, nullptr, N, w.part, c.pstride,
+                                                                   w.counter, D + c.L.sc + SC_BNORM); note_launch();
+      k_residual<double, float><<<c.grid, RED_THREADS, 0, c.st>>>(bs, nullptr, (float2*)w.V, N, w.part, c.pstride,
+                                                                  w.counter, D + c.L.sc + SC_RNORM2); note_launch();
+      return cudaGetLastError();
+    }, &g, &nk);
+    if (!e) e = bg_add_child(G.graph, &prev, g);
+    G.k_fixed += nk;
+    for (int o = 0; o < BG_MAX_OUTER && !e; ++o) {
+      cudaGraphConditionalHandle ho;
+      e = cudaGraphConditionalHandleCreate(&ho, G.graph, 0, cudaGraphCondAssignDefault);
+      if (!e) e = bg_capture(c.st, [&]() -> cudaError_t {
+        k_bg_decide_outer<<<1, 1, 0, c.st>>>(D, w.dctl, c.L, tol, inner_tol, max_outer, ho, rec); note_launch();
+        return cudaGetLastError();
+      }, &g, &nk);
+      if (!e) e = bg_add_child(G.graph, &prev, g);
+      G.k_fixed += nk;
+      cudaGraph_t body = nullptr;
+      if (!e) e = bg_add_if(G.graph, &prev, ho, &body);
+      cudaGraphNode_t bprev = nullptr;
+      for (int ch = 0; ch < nch && !e; ++ch) {
+        cudaGraphConditionalHandle hc;
+        e = cudaGraphConditionalHandleCreate(&hc, G.graph, 0, cudaGraphCondAssignDefault);
+        if (!e) e = bg_capture(c.st, [&]() -> cudaError_t {
+          k_bg_decide_chunk<<<1, 1, 0, c.st>>>(w.dctl, ch == nch - 1 ? 1 : 0, hc, rec); note_launch();
+          return cudaGetLastError();
+        }, &g, &nk);
+        if (!e) e = bg_add_child(body, &bprev, g);
+        if (o == 0) G.k_outer[s] += nk;
+        cudaGraph_t cbody = nullptr;
+        if (!e) e = bg_add_if(body, &bprev, hc, &cbody);
+        const int j0 = ch * BG_CHUNK, j1 = std::min(m, j0 + BG_CHUNK);
+        if (!e) e = bg_capture(c.st, [&]() -> cudaError_t {
+          for (int j = j0; j < j1; ++j) {
+            cudaError_t e3 = arnoldi_step<float>(c, prec, j);
+            if (e3) return e3;
+          }
+          return cudaSuccess;
+        }, &g, &nk);
+        cudaGraphNode_t cprev = nullptr;
+        if (!e) e = bg_add_child(cbody, &cprev, g);
+        if (o == 0) {
+          long long& slot = ch == nch - 1 ? G.k_last[s] : G.k_chunk[s];
+          slot = std::max(slot, nk);
+        }
+      }
+      // end of the cycle: correction, x += correction, new FP64 residual
+      if (!e) e = bg_capture(c.st, [&]() -> cudaError_t {
+        const bool flex = flexible<float>(c, prec);
+        const int kmax = std::min(m, LSQ_SMEM_K);
+        k_lsq<<<1, LSQ_THREADS, (size_t)kmax * kmax * sizeof(double2), c.st>>>(D, w.dctl, c.L, flex ? 0 : 1);
+        note_launch();
+        const float2* basis = flex ? reinterpret_cast<const float2*>(w.Zb) : reinterpret_cast<const float2*>(w.V);
+        float2* Z = reinterpret_cast<float2*>(w.Z);
+        k_lincomb<float><<<c.grid, RED_THREADS, 0, c.st>>>(basis, N, D + c.L.yc, w.dctl, Z); note_launch();
+        cudaError_t e3 = cudaGetLastError();
+        if (!e3 && !flex) e3 = precond_apply<float>(c, prec, Z, Z, nullptr);
+        if (e3) return e3;
+        k_axpy<double, float><<<c.grid, RED_THREADS, 0, c.st>>>(xs, Z, N, w.dctl); note_launch();
+        e3 = launch_matvec<double>(hs, xs, (double2*)w.R64, c.st);
+        if (e3) return e3;
+        k_residual<double, float><<<c.grid, RED_THREADS, 0, c.st>>>(bs, (const double2*)w.R64, (float2*)w.V, N,
+                                                                    w.part, c.pstride, w.counter,
+                                                                    D + c.L.sc + SC_RNORM2); note_launch();
+        return cudaGetLastError();
+      }, &g, &nk);
+      if (!e) e = bg_add_child(body, &bprev, g);
+      if (o == 0) G.k_outer[s] += nk;
+    }
+    if (!e) e = bg_capture(c.st, [&]() -> cudaError_t {
+      k_bg_finish<<<1, 1, 0, c.st>>>(D, w.dctl, c.L, tol, rec); note_launch();
+      return cudaGetLastError();
+    }, &g, &nk);
+    if (!e) e = bg_add_child(G.graph, &prev, g);
+    G.k_fixed += nk;
+  }
+  if (!e) e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+  if (e) {
+    bg_free(G);
+    return e;
+  }
+  *out = G;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// Whether sg_gmres_batched can take the one-graph route for these options.
+bool sgi_batched_graph_eligible(const sg_gmres_opts* opts, const void* const* x0, int count) {
+  if (opts->mode != SG_MIXED || opts->host_io || opts->x0 || opts->side != 0) return false;
+  if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN) return false;
+  if (x0)
+    for (int k = 0; k < count; ++k)
+      if (x0[k]) return false;
+  return true;
+}
+
+// Drops the cached batch graphs that name workspace `uid` (it is being freed).
+void sgi_forget_batched_graphs(unsigned long long uid) {
+  std::lock_guard<std::mutex> lock(g_bg_mu);
+  for (auto it = g_bg_cache.begin(); it != g_bg_cache.end();) {
+    bool hit = false;
+    for (size_t i = BG_KEY_HEAD; i < it->first.size(); i += 3) hit = hit || it->first[i] == (uintptr_t)uid;
+    if (hit) {
+      bg_free(it->second);
+      it = g_bg_cache.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// One-graph batched solve (see above).  infos[k] gets the graph's share of
+// system k's solve; *pending lists the systems still running after the
+// unrolled refinement steps (the caller continues them from x[k]; their
+// infos then hold the steps taken so far and status SG_ENOTCONV).
+sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b,
+                            void* const* x, sg_gmres_info* infos, void* stream, std::vector<int>* pending) {
+  pending->clear();
+  int m = 0;
+  for (int k = 0; k < count; ++k) {
+    int mk = opts->restart <= 0 ? (int)std::min<long long>(h[k]->N, MAXV - 1) : opts->restart;
+    mk = (int)std::min<long long>(mk, h[k]->N);
+    if (k == 0) m = mk;
+    if (mk != m || h[k]->gw.restart < m || h[k]->gw.prec_bytes != (int)sizeof(float2) || !h[k]->gw.uid)
+      return fail(SG_EUNSUPPORTED, "batch graph: the systems need the same restart length and complex64 workspaces");
+  }
+  // sg_gmres's defaults: maxit min(N, 2^30) per system (bg_build), max_outer 20
+  const int maxit = opts->maxit <= 0 ? 0 : opts->maxit;
+  const int max_outer = opts->max_outer <= 0 ? 20 : opts->max_outer;
+  std::vector<uintptr_t> key;
+  key.push_back((uintptr_t)m);
+  key.push_back((uintptr_t)maxit);
+  key.push_back((uintptr_t)max_outer);
+  key.push_back((uintptr_t)opts->prec);
+  uint64_t tb, ib;
+  std::memcpy(&tb, &opts->tol, 8);
+  const double itol = opts->inner_tol;
+  std::memcpy(&ib, &itol, 8);
+  key.push_back((uintptr_t)tb);
+  key.push_back((uintptr_t)ib);
+  for (int k = 0; k < count; ++k) {
+    key.push_back((uintptr_t)h[k]->gw.uid);
+    key.push_back((uintptr_t)b[k]);
+    key.push_back((uintptr_t)x[k]);
+  }
+  std::lock_guard<std::mutex> lock(g_bg_mu);
+  auto it = g_bg_cache.find(key);
+  if (it == g_bg_cache.end()) {
+    if (g_bg_cache.size() >= 4) {
+      for (auto& kv : g_bg_cache) bg_free(kv.second);
+      g_bg_cache.clear();
+    }
+    BgGraph G;
+    SG_CUDA_TRY(bg_build(h, count, opts, b, x, m, maxit, max_outer, &G));
+    it = g_bg_cache.emplace(key, G).first;
+  }
+  BgGraph& G = it->second;
+  cudaStream_t st = (cudaStream_t)stream;
+  SG_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+  std::vector<BgRecord> rec(count);
+  SG_CUDA_TRY(cudaMemcpyAsync(rec.data(), G.rec, (size_t)count * sizeof(BgRecord), cudaMemcpyDeviceToHost, st));
+  std::vector<int> werr(count, 0);   // bounded waits that ran out (tensor-core transforms)
+  for (int k = 0; k < count; ++k)
+    SG_CUDA_TRY(cudaMemcpyAsync(&werr[k], h[k]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(cudaStreamSynchronize(st));
+  long long kernels = G.k_fixed;
+  for (int k = 0; k < count; ++k) {
+    kernels += (long long)rec[k].outer * G.k_outer[k] + (long long)rec[k].taken * G.k_chunk[k] +
+               (long long)rec[k].taken_last * G.k_last[k];
+    sg_gmres_info inf{};
+    inf.iters = rec[k].iters;
+    inf.outer = rec[k].outer;
+    inf.cycles = rec[k].outer;
+    inf.graph_outer = rec[k].outer;
+    inf.relres = rec[k].relres;
+    inf.relres_prec = rec[k].relres;
+    const int r = rec[k].status;
+    inf.status = r == 1 ? SG_OK : r == 2 ? SG_EBREAKDOWN : r == 4 ? SG_EINVAL : SG_ENOTCONV;
+    if (werr[k]) {
+      SG_CUDA_TRY(cudaMemsetAsync(h[k]->d_err, 0, sizeof(int), st));
+      inf.status = SG_ETIMEOUT;
+    } else if (r == 0) {
+      pending->push_back(k);
+    }
+    if (infos) infos[k] = inf;
+  }
+  note_launches(kernels);
+  return SG_OK;
 }

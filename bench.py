@@ -427,13 +427,21 @@ def batched_leg(B, torch, dev):
         bs.append(bb)
     xs = [torch.zeros_like(bb) for bb in bs]
     kw = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, maxit=20000)
-    B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)          # warm-up (allocates workspaces)
+    B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)          # warm-up (workspaces, graph instantiation)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     st_b, inf_b = B.gmres_batched(ops, bs, xs, mode=B.MIXED, **kw)
     torch.cuda.synchronize()
     t_batched = time.perf_counter() - t1
     ok_b = st_b == B.SG_OK and all(i["relres"] <= 1e-8 for i in inf_b)
+    # the per-system route (host thread pool, one stream per system)
+    B.gmres_batched(ops, bs, xs, mode=B.MIXED, concurrency=-1, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st_p, inf_p = B.gmres_batched(ops, bs, xs, mode=B.MIXED, concurrency=-1, **kw)
+    torch.cuda.synchronize()
+    t_pool = time.perf_counter() - t1
+    ok_b = ok_b and st_p == B.SG_OK and [i["iters"] for i in inf_p] == [i["iters"] for i in inf_b]
     for op, bb, xx in zip(ops, bs, xs):                        # warm-up of the FP64 workspaces
         op.gmres(bb, xx, mode=B.FP64, **kw)
     torch.cuda.synchronize()
@@ -446,6 +454,9 @@ def batched_leg(B, torch, dev):
            "sigma ~ U[0.05,0.2], s ~ U{2,3,4}, degree ~ U{2,3} (P 6-35), GMRES(30), mean-value",
            "unknowns_total": int(sum(op.N for op in ops)),
            "mixed_batched_solves_per_s": len(ops) / t_batched,
+           "mixed_batched_route": "one graph launch, %d of %d refinement steps inside it" % (
+               sum(i["graph_outer"] for i in inf_b), sum(i["outer"] for i in inf_b)),
+           "mixed_per_system_route_solves_per_s": len(ops) / t_pool,
            "fp64_sequential_solves_per_s": len(ops) / t_seq,
            "speedup_vs_fp64_sequential": t_seq / t_batched,
            "all_converged": bool(ok_b and ok_s),

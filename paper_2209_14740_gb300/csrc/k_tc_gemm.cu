@@ -76,11 +76,14 @@ constexpr int A_TILE = BM * BK * 4;     // 16 KB, core-matrix layout
 constexpr int OFF_RAW = 0;
 
 // Layout that depends on the tile width and on the split.
+#ifndef SG_TC_PLAIN_STAGES
+#define SG_TC_PLAIN_STAGES 4
+#endif
 template <int BN, bool SPLIT>
 struct Cfg {
   // B slots: a slot is refilled once the MMAs of the stage that used it
   // have completed, so more slots let the copies run further ahead
-  static constexpr int NBS = (BN == 64 || !SPLIT) ? 4 : 3;
+  static constexpr int NBS = !SPLIT ? SG_TC_PLAIN_STAGES : BN == 64 ? 4 : 3;
   // raw X slots (split only): stages s .. s + NRAW - 1 in flight
   static constexpr int NRAW = !SPLIT ? 0 : BN == 64 ? 4 : 3;
   // A slots: split (hi, lo) pairs, or X tiles copied straight into the MMA
@@ -88,16 +91,16 @@ struct Cfg {
   // (measured: eight slots make the first stage land later, so the last one
   // lands no sooner; the kernel is bound by the L2 -> SM traffic of the
   // re-read X and B tiles at small sizes)
-  static constexpr int NA = SPLIT ? NAS : 4;
+  static constexpr int NA = SPLIT ? NAS : SG_TC_PLAIN_STAGES;
   // MMA-completion barriers, indexed by stage % NDONE: at least NBS, so no
   // wait on one of them can fall two phases behind
-  static constexpr int NDONE = 4;
+  static constexpr int NDONE = NBS > 4 ? NBS : 4;
   static constexpr int A_SLOT = SPLIT ? 2 * A_TILE : A_TILE;
   static constexpr int NBP = SPLIT ? 2 : 1;                      // B parts per slot (hi, lo)
   static constexpr int B_TILE = BN * BK * 4;                     // 8 or 16 KB
   static constexpr int OFF_B = OFF_RAW + NRAW * RAW_TILE;        // [slot][hi, lo]
   static constexpr int OFF_A = ((OFF_B + NBS * NBP * B_TILE + 1023) / 1024) * 1024;
-  static constexpr int OFF_BAR = OFF_A + NA * A_SLOT;           // full[NA], bfull[NBS], done[NDONE], TMEM addr, abort
+  static constexpr int OFF_BAR = OFF_A + NA * A_SLOT;           // full[NA], bfull[NBS], done[NDONE], TMEM addr, abort, accf
   static constexpr int SMEM_BYTES = OFF_BAR + 256 + 1024;        // + slack for 1024-byte alignment
   static constexpr int OUT_PITCH = BN / 2 + 1;                   // float2 per staged output row
   static constexpr uint32_t TMEM_COLS = BN;
@@ -108,7 +111,7 @@ struct Cfg {
   static_assert(BN == 64 || BN == 128, "tile width");
   // the row-major output is staged over the data slots (free by then)
   static_assert(BM * OUT_PITCH * 8 <= OFF_BAR, "output staging must fit below the barriers");
-  static_assert(8 * (NA + NBS + NDONE) + 16 <= 256, "barrier area");
+  static_assert(8 * (NA + NBS + NDONE) + 24 <= 256, "barrier area");
   static_assert(NDONE >= NBS && NDONE >= 2, "completion barriers");
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
@@ -281,10 +284,15 @@ __device__ __forceinline__ bool loader_sync_or(bool v) {
 //             s+NA-1 into it
 //   B copier: wait MMA(s-NBS) (frees B slot s%NBS) -> bulk-copy B of s
 //   MMA lane: wait full and bfull of s -> 12 (3xTF32) or 4 MMAs over the 4
-//             K steps -> commit done[s%NDONE]
+//             K steps -> commit done[s%NDONE]; after the last stage one
+//             more commit to the single-phase accumulator barrier, which
+//             the loaders wait on before the epilogue
 // so the loads of later stages overlap the MMAs of stage s.  No waiter can
-// fall two phases behind on a barrier: the MMA lane runs at most one or two
-// stages ahead of the loaders, cannot pass the copier, and NDONE >= NBS.
+// fall two phases behind on a barrier: where the loaders copy X, the MMA
+// lane runs at most one or two stages ahead of them; the copier waits only
+// for stages the MMA lane has issued, and NDONE >= NBS.  With X by tensor
+// copies nothing holds the MMA lane back for the loaders, so they wait only
+// on the accumulator barrier.
 template <int BN, bool SPLIT, bool TMAX>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __grid_constant__ CUtensorMap xmap) {
   using namespace tc;
@@ -302,6 +310,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
   const uint32_t done0 = bfull0 + 8 * NBS;       // NDONE barriers, count 1 (MMA commit)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::OFF_BAR + 8 * (NA + NBS + NDONE));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::OFF_BAR + 8 * (NA + NBS + NDONE) + 8);
+  // accumulator complete: one phase per launch (the MMA warp's final commit,
+  // or a plain arrival if it issued no MMA), so a wait on it cannot alias
+  const uint32_t accf = done0 + 8 * NDONE + 16;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -317,6 +328,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bfull0 + 8 * i) : "memory");
     for (int i = 0; i < NDONE; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done0 + 8 * i) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accf) : "memory");
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -372,15 +384,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
         ev[q] = nq0 + q < a.Nc ? a.E[(size_t)(nq0 + q) * a.e_ld + mr] : make_float2(0.f, 0.f);
     }
     if constexpr (TMAX) {
-      // X arrives by tensor copies.  The loaders follow the MMA completions
-      // stage by stage, so that no wait on a completion barrier is ever two
-      // phases behind (a parity wait on a barrier that has not reached the
-      // previous phase would succeed at once)
-      for (int s = 0; s < nks; ++s)
-        if (!mbar_wait(done0 + 8 * (s % NDONE), (s / NDONE) & 1)) {
-          bad = true;
-          break;
-        }
+      // X arrives by tensor copies: the loaders have nothing to do until the
+      // accumulator is complete (below).  They must not follow the per-stage
+      // completion barriers: nothing holds the MMA warp back for them, and a
+      // parity wait on a barrier two or more phases ahead never ends.
     } else if constexpr (!SPLIT) {
       // ----------------------------------------- loaders (no split): X tiles
       // go straight into the MMA layout; each loader arrives on full[s % NA]
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
       }
     }
     // all MMAs done before the accumulator is read
-    if (!bad && nks > 0 && !mbar_wait(done0 + 8 * ((nks - 1) % NDONE), ((nks - 1) / NDONE) & 1)) bad = true;
+    if (!bad && !mbar_wait(accf, 0)) bad = true;
     cp_wait<0>();
     bad = loader_sync_or(bad || *abort_flag != 0);
     if (bad) {
@@ -588,9 +595,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
         mma_commit(done0 + 8 * (s % NDONE));
         last = s;
       }
-      // the accumulator must not be freed under running MMAs (matters only
-      // when a wait gave up: the loaders wait for this otherwise)
-      if (last >= 0 && !mbar_wait(done0 + 8 * (last % NDONE), (last / NDONE) & 1)) *abort_flag = 1;
+      // one arrival on the accumulator barrier when every MMA issued has
+      // completed (also after an abort: the accumulator must not be freed
+      // under running MMAs); a plain arrival if none was issued
+      if (last >= 0) mma_commit(accf);
+      else mbar_arrive(accf);
+      if (!mbar_wait(accf, 0)) *abort_flag = 1;
     }
   } else if (lane == 0) {
     // ---------------------------------------------------------------- B copies
@@ -619,6 +629,246 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
     // for the last copy into every slot
     for (int t = issued > NBS ? issued - NBS : 0; t < issued; ++t)
       if (!mbar_wait(bfull0 + 8 * (t % NBS), (t / NBS) & 1)) *abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ persistent plain-TF32 form
+// The plain-TF32 transform with X by tensor copies, as a persistent kernel:
+// one CTA per SM walks the tiles b, b + G, b + 2G, ... (column tiles of a
+// row tile consecutive, as above) with two accumulators in tensor memory
+// (2 BN columns), so that the epilogue of tile i (TMEM -> registers ->
+// global) runs while the MMAs of tile i + 1 accumulate into the other
+// buffer, and the copies of tile i + 1 start while tile i's last stages
+// are still in the MMA pipe.  Barriers:
+//   full[s % NS], bfull[s % NS]  X and B of stage s landed (transaction bytes)
+//   done[s % NS]                 MMAs of stage s complete (slot free)
+//   accf[i % 2]                  accumulator of tile i complete
+//   acce[i % 2]                  accumulator of tile i read by all 8 epilogue warps
+//   fin                          every MMA issued has completed (teardown)
+// Stages are counted across tiles.  No waiter can fall two phases behind:
+// the copier waits only for stages the MMA lane has issued; the MMA lane
+// starts tile i + 2 in buffer i % 2 only after the epilogue released tile i,
+// and the epilogue waits for tile i's accumulator before releasing it.
+#ifndef SG_TC_PERSIST
+#define SG_TC_PERSIST 1
+#endif
+#ifndef SG_TC_PS_STAGES
+#define SG_TC_PS_STAGES 4
+#endif
+template <int BN>
+struct CfgP {
+  static constexpr int NS = SG_TC_PS_STAGES;
+  static constexpr int B_TILE = BN * tc::BK * 4;
+  static constexpr int OUT_PITCH = BN / 2 + 1;
+  static constexpr int STAGE_BYTES = ((tc::BM * OUT_PITCH * 8 + 1023) / 1024) * 1024;   // mode-0 output staging
+  static constexpr int OFF_B = STAGE_BYTES;
+  static constexpr int OFF_A = OFF_B + NS * B_TILE;
+  static constexpr int OFF_BAR = OFF_A + NS * tc::A_TILE;
+  static constexpr int NBAR = 3 * NS + 5;
+  static constexpr int SMEM_BYTES = OFF_BAR + 8 * NBAR + 16 + 1024;   // + TMEM address, abort flag, alignment slack
+  static constexpr uint32_t TMEM_COLS = 2 * BN;
+  static_assert(OFF_B % 1024 == 0 && OFF_A % 1024 == 0 && OFF_BAR % 8 == 0, "alignment");
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+};
+
+template <int BN>
+__global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const __grid_constant__ CUtensorMap xmap) {
+  using namespace tc;
+  using L = CfgP<BN>;
+  constexpr int NS = L::NS, B_TILE = L::B_TILE;
+  constexpr uint32_t IDESC = Cfg<BN, false>::IDESC;
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t s_base = smem_u32(sm);
+  const uint32_t full0 = s_base + L::OFF_BAR, bfull0 = full0 + 8 * NS, done0 = bfull0 + 8 * NS;
+  const uint32_t accf0 = done0 + 8 * NS, acce0 = accf0 + 16, fin = acce0 + 16;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::OFF_BAR + 8 * L::NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + L::OFF_BAR + 8 * L::NBAR + 8);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(L::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 3 * NS + 2; ++i)   // full, bfull, done, accf: one arrival (+ bytes / commit)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * i) : "memory");
+    for (int i = 0; i < 2; ++i)            // acce: one arrival per epilogue warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acce0 + 8 * i), "n"(NLOAD / 32) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fin) : "memory");
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const bool skipped = a.skip && *a.skip;
+  const int nks = a.nks;
+  const int total = skipped ? 0 : ((a.M + BM - 1) / BM) * a.ntiles;
+
+  if (warp < MMA_WARP) {
+    // ---------------------------------------------------------------- epilogue
+    constexpr int HALF = BN / 2;   // real columns per warp
+    const int lg = warp & 3, chalf = warp >> 2;
+    const int row = lg * 32 + lane;
+    float2* stage = reinterpret_cast<float2*>(sm);
+    const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
+    int it = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+      const int b = it & 1;
+      const int ctile = t % a.ntiles, m0 = (t / a.ntiles) * BM;
+      const int m = m0 + row;
+      const bool mok = m < a.M;
+      const int nq0 = ctile * (BN / 2) + chalf * (HALF / 2);
+      float2 ev[HALF / 2];
+      if (a.E) {   // loaded before the wait: the latency overlaps the MMAs
+        const int mr = (mok ? m : 0) % a.e_mod;
+#pragma unroll
+        for (int q = 0; q < HALF / 2; ++q)
+          ev[q] = nq0 + q < a.Nc ? a.E[(size_t)(nq0 + q) * a.e_ld + mr] : make_float2(0.f, 0.f);
+      }
+      const bool to = !mbar_wait(accf0 + 8 * b, (uint32_t)(it >> 1) & 1u);
+      if (loader_sync_or(to || *abort_flag != 0)) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float2* cb = nullptr;
+      bool pad1 = false;
+      if (a.mode == 1 && mok) {
+        const int p = m / a.MB, r = m - p * a.MB;
+        cb = a.C + ((size_t)p * a.Nc + nq0) * a.ldc + r;
+        pad1 = r == a.MB - 1 && a.ldc > a.MB;
+      }
+      const uint32_t taddr = tmem + (uint32_t)(b * BN) + ((uint32_t)(lg * 32) << 16) + (uint32_t)(chalf * HALF);
+#pragma unroll
+      for (int j0 = 0; j0 < HALF; j0 += 32) {
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+            "[%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr + (uint32_t)j0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (j0 + 32 >= HALF) {
+          // this warp's last read of the accumulator: release it to the MMA lane
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int qq = j0 / 2 + q;
+          const int n = nq0 + qq;
+          float2 c = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+          if (a.E) {
+            const float2 e = ev[qq];
+            c = make_float2(es * (c.x * e.x - c.y * e.y), es * (c.x * e.y + c.y * e.x));
+          }
+          if (a.mode == 1) {
+            if (mok && n < a.Nc) {
+              cb[(size_t)qq * a.ldc] = c;
+              if (pad1) cb[(size_t)qq * a.ldc + 1] = make_float2(0.f, 0.f);
+            }
+          } else {
+            stage[row * L::OUT_PITCH + chalf * (HALF / 2) + qq] = c;
+          }
+        }
+      }
+      if (a.mode == 0) {
+        loader_sync();
+        const int n0 = ctile * (BN / 2);
+        for (int idx = tid; idx < BM * (BN / 2); idx += NLOAD) {
+          const int rr = idx / (BN / 2), q = idx % (BN / 2);
+          const int mm = m0 + rr, n = n0 + q;
+          if (mm < a.M && n < a.Nc) {
+            a.C[(size_t)mm * a.ldc + n] = stage[rr * L::OUT_PITCH + q];
+            if (n == a.Nc - 1 && a.ldc > a.Nc) a.C[(size_t)mm * a.ldc + a.Nc] = make_float2(0.f, 0.f);
+          }
+        }
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      bool any = false, stop = false;
+      int g = 0, it = 0;
+      for (int t = blockIdx.x; t < total && !stop; t += gridDim.x, ++it) {
+        const int b = it & 1;
+        if (it >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)((it >> 1) - 1) & 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int s = 0; s < nks; ++s, ++g) {
+          const int slot = g % NS;
+          const uint32_t par = (uint32_t)(g / NS) & 1u;
+          if (!mbar_wait(full0 + 8 * slot, par) || !mbar_wait(bfull0 + 8 * slot, par) || *abort_flag) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t aa = s_base + L::OFF_A + slot * A_TILE, bb = s_base + L::OFF_B + slot * B_TILE;
+#pragma unroll
+          for (int ks = 0; ks < BK / 8; ++ks)
+            mma_tf32(acc, sdesc_sw128(aa + 32u * ks), sdesc(bb + 256u * ks), IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+          mma_commit(done0 + 8 * slot);
+          any = true;
+        }
+        if (!stop) mma_commit(accf0 + 8 * b);
+      }
+      // tensor memory is freed only after every MMA issued has completed
+      if (any) mma_commit(fin);
+      else mbar_arrive(fin);
+      if (!mbar_wait(fin, 0)) *abort_flag = 1;
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- X and B copies
+    int g = 0;
+    bool stop = false;
+    for (int t = blockIdx.x; t < total && !stop; t += gridDim.x) {
+      const int ctile = t % a.ntiles, m0 = (t / a.ntiles) * BM;
+      const float* Bh = a.Bhi + (size_t)ctile * nks * (BN * BK);
+      for (int s = 0; s < nks; ++s, ++g) {
+        if (g >= NS && !mbar_wait(done0 + 8 * ((g - NS) % NS), (uint32_t)((g - NS) / NS) & 1u)) {
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        if (*abort_flag) {
+          stop = true;
+          break;
+        }
+        const int slot = g % NS;
+        mbar_expect_tx(bfull0 + 8 * slot, (uint32_t)B_TILE);
+        bulk_g2s(s_base + L::OFF_B + slot * B_TILE, Bh + (size_t)s * (BN * BK), B_TILE, bfull0 + 8 * slot);
+        mbar_expect_tx(full0 + 8 * slot, (uint32_t)A_TILE);
+        tensor_g2s_2d(s_base + L::OFF_A + slot * A_TILE, &xmap, s * BK, m0, full0 + 8 * slot);
+      }
+    }
+    // no copy may still be writing shared memory when the CTA exits
+    for (int q = g > NS ? g - NS : 0; q < g; ++q) {
+      const uint32_t par = (uint32_t)(q / NS) & 1u;
+      if (!mbar_wait(full0 + 8 * (q % NS), par) || !mbar_wait(bfull0 + 8 * (q % NS), par)) *abort_flag = 1;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -742,6 +992,8 @@ static void tc_attributes() {
                          tc::Cfg<64, false>::SMEM_BYTES);
     cudaFuncSetAttribute(k_tc_cgemm<128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tc::Cfg<128, false>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm_ps<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<64>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm_ps<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<128>::SMEM_BYTES);
   });
 }
 
@@ -800,7 +1052,12 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
                     (long long)cfg.gridDim.x >= num_sms;
   const CUtensorMap& m = tmax ? *xmap : none;
   cudaError_t e;
-  if (B.bn == 128 && split) {
+  if (tmax && SG_TC_PERSIST) {
+    // persistent: one CTA per SM walks the tiles
+    cfg.gridDim = dim3((unsigned)std::min<long long>(ctas, num_sms));
+    cfg.dynamicSmemBytes = B.bn == 128 ? CfgP<128>::SMEM_BYTES : CfgP<64>::SMEM_BYTES;
+    e = B.bn == 128 ? cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<128>, a, m) : cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<64>, a, m);
+  } else if (B.bn == 128 && split) {
     cfg.dynamicSmemBytes = tc::Cfg<128, true>::SMEM_BYTES;
     e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, true, false>, a, m);
   } else if (split) {

@@ -172,3 +172,33 @@ def test_graph_relaunch_and_caps(B):
             assert torch.equal(xs2[k], x1), k
     for op in ops:
         op.close()
+
+
+def test_graph_route_64_heterogeneous_systems(B):
+    """The 64-system workload (g 63 ... 255, P 6 ... 35): many chains in
+    flight at once, transforms large enough for X by tensor copies.  Both
+    routes converge every system with equal bits and counts; the FP64
+    residual, formed on the device, meets tol."""
+    probs = inputs.batch_64()
+    ops = [B.SG(p) for p in probs]
+    bs = []
+    for op in ops:
+        b = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.rhs(b, B.FP64)
+        bs.append(b)
+    kw = dict(restart=30, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, maxit=20000)
+    xg = [torch.zeros_like(b) for b in bs]
+    stg, infg = B.gmres_batched(ops, bs, xg, **kw)
+    xp = [torch.zeros_like(b) for b in bs]
+    stp, infp = B.gmres_batched(ops, bs, xp, concurrency=-1, **kw)
+    assert stg == stp == B.SG_OK
+    for k, op in enumerate(ops):
+        assert infg[k]["status"] == B.SG_OK and infg[k]["graph_outer"] >= 1, (k, infg[k])
+        assert infg[k]["iters"] == infp[k]["iters"] and infg[k]["outer"] == infp[k]["outer"], (k, infg[k], infp[k])
+        assert torch.equal(xg[k], xp[k]), k
+        ax = torch.empty_like(xg[k])
+        op.matvec(xg[k], ax, B.FP64)
+        relres = (torch.linalg.vector_norm(bs[k] - ax) / torch.linalg.vector_norm(bs[k])).item()
+        assert relres <= 1e-8, (k, relres)
+    for op in ops:
+        op.close()

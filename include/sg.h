@@ -413,6 +413,53 @@ sg_status sg_warmstart_predict(sg_warmstart* w, const double* params, int count,
 /* Message of the last failing call on this host thread ("" if none). */
 const char* sg_last_error(void);
 
+/* ---------------------------------------------------------------- launch-shape tuning
+ * Three launch shapes of the hot path depend on the problem (grid, P) and
+ * are not fixed by the method (the paper times whole solves only):
+ *   cgs_blocks_per_sm  grid of the CGS2 passes of every Arnoldi step, in
+ *                      blocks per SM (1 .. 8); 0: the built-in rule (4);
+ *   op_ctas_per_sm     CTAs per SM of the persistent complex64 SG operator
+ *                      (1 .. 16, clamped to what fits); 0: as many as fit;
+ *                      ignored by problems without that kernel;
+ *   tc_tile_n          output tile width of the plain-TF32 transforms of 2D
+ *                      separable preconditioners (64 or 128 real columns);
+ *                      0: the built-in rule per transform.
+ * None changes the operator, the preconditioner or the method: the operator
+ * and the transforms give the same bits for every choice; the CGS2 grid
+ * changes the order of the block sums of the inner products (rounding only,
+ * still reproducible for a fixed choice).
+ * The *_us fields are filled by sg_autotune: measured times of one step's
+ * CGS2 passes at step restart / 2, one complex64 operator application and
+ * one plain-TF32 preconditioner apply (0 where not timed). */
+typedef struct {
+  int cgs_blocks_per_sm;
+  int op_ctas_per_sm;
+  int tc_tile_n;
+  int reserved;
+  double cgs_us;
+  double op_us;
+  double apply_us;
+} sg_tune;
+
+/* Times the candidate shapes on this handle's problem (CUDA events on
+ * `stream`, after warm-up; CGS2 with the complex64 basis of GMRES(restart),
+ * restart <= 0 meaning 30, allocated like sg_gmres would) and applies the
+ * fastest of each; *out (may be NULL) receives the choices and their times.
+ * Overwrites the handle's GMRES workspace; must not run concurrently with
+ * another call on the same handle.  Blocks until done. */
+sg_status sg_autotune(sg_handle* h, int restart, sg_tune* out, void* stream);
+
+/* The shapes in effect for this handle (0 = built-in rule), with the times
+ * of the last sg_autotune (zeros if it never ran). */
+sg_status sg_tune_get(const sg_handle* h, sg_tune* out);
+
+/* Applies stored shapes (e.g. a table of sg_autotune results for this
+ * problem size); the *_us fields are ignored.  SG_EINVAL for values out of
+ * range.  Releases the GMRES workspace if the CGS2 grid changes (the next
+ * solve allocates it again).  Must not run concurrently with another call
+ * on the same handle. */
+sg_status sg_tune_set(sg_handle* h, const sg_tune* t);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles, all threads; a diagnostic for benchmarks). */
 long long sg_kernel_launches(void);

@@ -29,7 +29,8 @@ EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "
             "sg_mlp_create", "sg_mlp_destroy", "sg_mlp_num_params", "sg_mlp_set_params", "sg_mlp_get_params",
             "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
             "sg_selftest_wait_timeout", "sg_alu_peak", "sg_stationary", "sg_statistics",
-            "sg_warmstart_create", "sg_warmstart_destroy", "sg_warmstart_predict"]
+            "sg_warmstart_create", "sg_warmstart_destroy", "sg_warmstart_predict", "sg_autotune", "sg_tune_get",
+            "sg_tune_set"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -57,6 +58,14 @@ class SgGmresOpts(C.Structure):
 class SgGmresInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("cycles", C.c_int), ("relres", C.c_double),
                 ("status", C.c_int), ("relres_prec", C.c_double), ("graph_outer", C.c_int)]
+
+
+class SgTune(C.Structure):
+    _fields_ = [("cgs_blocks_per_sm", C.c_int), ("op_ctas_per_sm", C.c_int), ("tc_tile_n", C.c_int),
+                ("reserved", C.c_int), ("cgs_us", C.c_double), ("op_us", C.c_double), ("apply_us", C.c_double)]
+
+
+TUNE_KEYS = ("cgs_blocks_per_sm", "op_ctas_per_sm", "tc_tile_n")
 
 
 class SgStationaryOpts(C.Structure):
@@ -136,6 +145,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_selftest_wait_timeout.restype = i
     lib.sg_alu_peak.argtypes = [i, dp, vp]
     lib.sg_alu_peak.restype = i
+    lib.sg_autotune.argtypes = [vp, i, C.POINTER(SgTune), vp]
+    lib.sg_autotune.restype = i
+    lib.sg_tune_get.argtypes = [vp, C.POINTER(SgTune)]
+    lib.sg_tune_get.restype = i
+    lib.sg_tune_set.argtypes = [vp, C.POINTER(SgTune)]
+    lib.sg_tune_set.restype = i
     lib.sg_stationary.argtypes = [vp, C.POINTER(SgStationaryOpts), vp, vp, C.POINTER(SgStationaryInfo), dp, vp]
     lib.sg_stationary.restype = i
     lib.sg_statistics.argtypes = [vp, i, vp, vp, vp, vp, dp, vp]
@@ -277,7 +292,9 @@ def _stream(stream) -> int | None:
 class SG:
     """One assembled SG Helmholtz system (owns an sg_handle)."""
 
-    def __init__(self, prob, stream=None):
+    def __init__(self, prob, stream=None, tuned=True):
+        """tuned: apply the launch shapes of the committed tuning table
+        (tune_table.json) when it has this problem size."""
         lib = load()
         self._keep = []
         k0 = np.ascontiguousarray(prob.k0, dtype=np.float64)
@@ -306,6 +323,30 @@ class SG:
         _check(lib.sg_get_info(h, C.byref(inf)))
         self.info = {k: getattr(inf, k) for k, _ in SgInfo._fields_}
         self.n, self.P, self.N = inf.n, inf.P, inf.N
+        if tuned:
+            from . import tune_table
+            entry = tune_table.lookup(prob.dim, inf.mx, inf.my, prob.s, prob.r)
+            if entry is not None:
+                self.tune_set(entry)
+
+    def autotune(self, restart=30, stream=None) -> dict:
+        """sg_autotune: time the candidate launch shapes on this problem and
+        keep the fastest; returns the choices and their times."""
+        t = SgTune()
+        _check(load().sg_autotune(self.h, restart, C.byref(t), _stream(stream)))
+        return {k: getattr(t, k) for k, _ in SgTune._fields_ if k != "reserved"}
+
+    def tune_get(self) -> dict:
+        t = SgTune()
+        _check(load().sg_tune_get(self.h, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in SgTune._fields_ if k != "reserved"}
+
+    def tune_set(self, shapes: dict):
+        """sg_tune_set with the keys of TUNE_KEYS (missing keys: 0 = rule)."""
+        t = SgTune()
+        for k in TUNE_KEYS:
+            setattr(t, k, int(shapes.get(k, 0)))
+        _check(load().sg_tune_set(self.h, C.byref(t)))
 
     def close(self):
         if getattr(self, "h", None):

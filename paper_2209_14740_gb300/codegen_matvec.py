@@ -1488,6 +1488,26 @@ def generate(path: str) -> str:
             "  return cudaGetLastError();",
             "}",
         ]
+    if STENCIL == "tile" and COUPLING == "tk" and PERSISTENT:
+        # CTAs per SM of the persistent kernels: the tuner's choice (at most
+        # the occupancy), else the occupancy
+        parts.append("static int tuned_occ(const sg_handle* h, int occ) {")
+        parts.append("  return h->tune_op_occ > 0 ? std::min(h->tune_op_occ, occ) : occ;")
+        parts.append("}")
+        parts.append("int matvec_special_occupancy(const sg_handle* h) {")
+        for s, r, name, P in table:
+            tx, ty = PTILE_2D
+            K = dbuf_modes(s, r)
+            K = -1 if K is None else K
+            parts.append("  if (h->s == %d && h->r == %d)" % (s, r))
+            parts.append("    return h->dim == 2 ? persist_occupancy<%d, %d>(%s<%d, %d>, %d, %d, %d)"
+                         % (tx, ty, name, tx, ty, P, s + 1, K))
+            parts.append("                       : persist_occupancy<64, 1>(%s<64, 1>, %d, %d, %d);"
+                         % (name, P, s + 1, K))
+        parts.append("  return 0;")
+        parts.append("}")
+    else:
+        parts.append("int matvec_special_occupancy(const sg_handle*) { return 0; }")
     parts.append("cudaError_t matvec_special_f32(const sg_handle* h, const float2* X, float2* Y, cudaStream_t st,")
     parts.append("                               const int* skip, bool* handled) {")
     parts.append("  *handled = false;")
@@ -1505,12 +1525,12 @@ def generate(path: str) -> str:
             parts.append("    if (h->dim == 2) {")
             parts.append("      static const int occ2 = persist_occupancy<%d, %d>(%s<%d, %d>, %d, %d, %d);"
                          % (tx, ty, name, tx, ty, P, s + 1, K))
-            parts.append("      return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, %d, occ2, h, p, X, Y, st);"
+            parts.append("      return launch_persist<%d, %d>(%s<%d, %d>, %d, %d, %d, tuned_occ(h, occ2), h, p, X, Y, st);"
                          % (tx, ty, name, tx, ty, P, s + 1, K))
             parts.append("    }")
             parts.append("    static const int occ1 = persist_occupancy<64, 1>(%s<64, 1>, %d, %d, %d);"
                          % (name, P, s + 1, K))
-            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, %d, occ1, h, p, X, Y, st);"
+            parts.append("    return launch_persist<64, 1>(%s<64, 1>, %d, %d, %d, tuned_occ(h, occ1), h, p, X, Y, st);"
                          % (name, P, s + 1, K))
         elif STENCIL == "tile":
             tx, ty = tile_2d(P)

@@ -189,6 +189,34 @@ static cudaError_t alloc_factors(PrecBlock& b, size_t cnt) {
 
 void sgi_free_gmres_work(sg_handle* h);  // solver.cu
 
+namespace sgi {
+// Device operands of the four tensor-core transforms from the host factors
+// (hi / lo TF32 parts in the MMA's core-matrix order, tile width bn or the
+// rule).  The old operands are freed only once the new ones are in place.
+sg_status tc_build_operands(sg_handle* h, int bn) {
+  if (bn != 0 && bn != 64 && bn != 128) return fail(SG_EINVAL, "transform tile width must be 64 or 128");
+  TcDevOperand fresh[4];
+  for (int t = 0; t < 4; ++t) {
+    if (h->tc_fac[t].empty()) return fail(SG_EUNSUPPORTED, "this problem has no tensor-core transforms");
+    const int w = bn ? bn : tc_tile_width(h->tc_rows[t], h->tc_dim[t], h->num_sms);
+    TcOperand op = tc_make_operand(h->tc_fac[t], h->tc_dim[t], h->tc_dim[t], w);
+    TcDevOperand& d = fresh[t];
+    d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
+    if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size())) {
+      for (int u = 0; u <= t; ++u) { cudaFree(fresh[u].hi); cudaFree(fresh[u].lo); }
+      return fail(SG_ENOMEM, "transform operand upload");
+    }
+  }
+  SG_CUDA_TRY(cudaDeviceSynchronize());   // no transform of the old operands still running
+  for (int t = 0; t < 4; ++t) {
+    cudaFree(h->tcB[t].hi);
+    cudaFree(h->tcB[t].lo);
+    h->tcB[t] = fresh[t];
+  }
+  return SG_OK;
+}
+}  // namespace sgi
+
 static void destroy_impl(sg_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
@@ -371,18 +399,18 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
             qy[(size_t)a * my + b] = v;
             qyt[(size_t)b * my + a] = v;
           }
-        const std::vector<cd>* facs[4] = {&qx, &qy, &qyt, &qxt};
+        std::vector<cd>* facs[4] = {&qx, &qy, &qyt, &qxt};
         const int dims[4] = {mx, my, my, mx};
         // rows of the four GEMMs: P my, P mx, P mx, P my
         const long long rows[4] = {(long long)h->P * my, (long long)h->P * mx, (long long)h->P * mx,
                                    (long long)h->P * my};
         for (int t = 0; t < 4; ++t) {
-          TcOperand op = tc_make_operand(*facs[t], dims[t], dims[t], tc_tile_width(rows[t], dims[t], h->num_sms));
-          TcDevOperand& d = h->tcB[t];
-          d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
-          if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()))
-            return fail(SG_ENOMEM, "precond upload");
+          h->tc_fac[t] = std::move(*facs[t]);
+          h->tc_dim[t] = dims[t];
+          h->tc_rows[t] = rows[t];
         }
+        sg_status bst = tc_build_operands(h, 0);
+        if (bst != SG_OK) return bst;
         for (int which = 0; which < 2; ++which) {
           const cd shift = which == 0 ? cd(0, 0) : cd(0, -h->beta * kb * kb);
           for (int j = 0; j < my; ++j)

@@ -226,6 +226,16 @@ struct sg_handle {
   int* d_err = nullptr;              // device flag: a bounded wait in a kernel timed out
   void* noalloc_scratch = nullptr;   // device address of the static scratch of sg_precond_noalloc
   unsigned long long* d_modemax = nullptr;   // P per-mode maxima of sg_statistics (allocated on first use)
+  // launch shapes chosen by sg_autotune / sg_tune_set (0: built-in rule)
+  int tune_cgs_bpsm = 0;             // CGS2 passes: grid of this many blocks per SM
+  int tune_op_occ = 0;               // persistent complex64 operator: CTAs per SM (at most its occupancy)
+  int tune_tc_bn = 0;                // plain-TF32 transforms: output tile width (64 or 128)
+  double tune_us[3] = {0.0, 0.0, 0.0};   // measured: CGS2 step, operator, TF32 apply (microseconds)
+  // host factors of the four tensor-core transforms (kept to rebuild them
+  // for another tile width), their sizes and GEMM row counts
+  std::vector<sgi::cd> tc_fac[4];
+  int tc_dim[4] = {0, 0, 0, 0};
+  long long tc_rows[4] = {0, 0, 0, 0};
 
   sgi::GmresWork gw;
 
@@ -279,5 +289,18 @@ long long thread_launches();          // kernels noted by this host thread so fa
 
 // true if a register-resident complex64 matvec kernel exists for (s, r)
 bool matvec_is_specialised(int s, int r);
+// CTAs per SM that fit of the persistent complex64 operator kernel of this
+// handle (0: it has none)
+int matvec_special_occupancy(const sg_handle* h);
+
+// (Re)builds the device operands of the four tensor-core transforms from
+// the host factors, with tile width bn (0: the built-in rule per transform).
+sg_status tc_build_operands(sg_handle* h, int bn);
+// Times the CGS2 passes of Arnoldi step j (complex64) on the handle's
+// workspace, whose contents it overwrites: mean microseconds over reps.
+sg_status time_cgs_passes(sg_handle* h, sg_prec prec, int j, int reps, cudaStream_t st, double* us);
+// Applies a CGS2 grid choice (blocks per SM, 0 = rule) to the handle and
+// its workspace, dropping graphs captured with the old grid.
+void set_cgs_blocks(sg_handle* h, int bpsm);
 
 }  // namespace sgi

@@ -981,6 +981,15 @@ static void cgs_attributes() {
   });
 }
 
+// Grid of the CGS2 passes: blocks per SM (the tuner's choice, else 4), at
+// most one block per chunk of RED_THREADS * CG_EPT elements.
+constexpr int CG_DEFAULT_BPSM = 4;
+constexpr int CG_MAX_BPSM = 8;
+static int cgs_blocks(const sg_handle* h, int bpsm) {
+  const long long chunks = ((long long)h->N + RED_THREADS * CG_EPT - 1) / (RED_THREADS * CG_EPT);
+  return (int)std::max<long long>(1, std::min<long long>((long long)bpsm * h->num_sms, chunks));
+}
+
 static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   GmresWork& w = h->gw;
   if (w.V && w.restart >= m && w.prec_bytes == elem_bytes) return SG_OK;
@@ -988,8 +997,7 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   const size_t N = (size_t)h->N;
   DevLayout L(m);
   w.nblk = std::max(1, std::min(h->num_sms * 2, (int)((N + 2 * RED_THREADS - 1) / (2 * RED_THREADS))));
-  w.cg_nblk = (int)std::max<long long>(
-      1, std::min<long long>(4LL * h->num_sms, ((long long)N + RED_THREADS * CG_EPT - 1) / (RED_THREADS * CG_EPT)));
+  w.cg_nblk = cgs_blocks(h, h->tune_cgs_bpsm > 0 ? h->tune_cgs_bpsm : CG_DEFAULT_BPSM);
   cgs_attributes();
   cudaError_t e = cudaSuccess;
   if (!e) e = cudaMalloc(&w.V, (size_t)(m + 1) * N * elem_bytes);
@@ -1004,7 +1012,10 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   if (!e) e = cudaMalloc((void**)&w.dctl, 16 * sizeof(int));
   // block partials: the reduction kernels use nblk * 2 (MAXV + 2) doubles, the
   // CGS2 passes up to (2 MAXV + 1) * cg_nblk
-  const size_t part_doubles = std::max((size_t)w.nblk * 2 * (MAXV + 2), (size_t)(2 * MAXV + 2) * w.cg_nblk);
+  // (sized for the largest grid the tuner may choose, so that a new choice
+  // needs no new allocation)
+  const size_t part_doubles =
+      std::max((size_t)w.nblk * 2 * (MAXV + 2), (size_t)(2 * MAXV + 2) * cgs_blocks(h, CG_MAX_BPSM));
   if (!e) e = cudaMalloc((void**)&w.part, part_doubles * sizeof(double));
   if (!e) e = cudaMalloc((void**)&w.counter, sizeof(unsigned));
   if (!e) e = cudaMemset(w.counter, 0, sizeof(unsigned));
@@ -1061,6 +1072,9 @@ static bool flexible(const Ctx& c, sg_prec prec) {
          c.h->gw.Zb != nullptr;
 }
 
+template <typename T>
+cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j);
+
 // One Arnoldi step j with CGS2 on the inner-precision basis.
 template <typename T>
 cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
@@ -1089,6 +1103,17 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
     if ((e = precond_apply<T>(c, prec, vj, Z, w.dctl, D + c.L.vscale + j))) return e;
   }
   if (!c.left && (e = launch_matvec<T>(c.h, Z, wv, c.st, w.dctl))) return e;
+  return cgs_passes<T>(c, prec, j);
+}
+
+// The CGS2 passes of Arnoldi step j (w = V_{j+1} against V_0 .. V_j).
+template <typename T>
+cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j) {
+  GmresWork& w = c.h->gw;
+  const long long N = c.h->N;
+  C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
+  C2<T>* wv = V + (size_t)(j + 1) * N;
+  double* D = w.dscal;
   const int nv = j + 1;
   const size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
   const int G = c.cg_grid;
@@ -1483,6 +1508,63 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     return status;
   });
 }
+
+// ------------------------------------------------------------------ launch-shape tuning support
+namespace sgi {
+
+// A new CGS2 grid for the handle: the existing workspace takes it at once
+// (its partial-sum buffer is sized for the largest grid); captured graphs
+// hold the old grid and are dropped.
+void set_cgs_blocks(sg_handle* h, int bpsm) {
+  h->tune_cgs_bpsm = bpsm;
+  GmresWork& w = h->gw;
+  if (!w.V) return;
+  const int nb = cgs_blocks(h, bpsm > 0 ? bpsm : CG_DEFAULT_BPSM);
+  if (nb == w.cg_nblk) return;
+  cudaDeviceSynchronize();   // no replay of the old graphs still running
+  for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
+  w.graphs.clear();
+  w.graph_uses.clear();
+  if (w.uid) sgi_forget_batched_graphs(w.uid);
+  w.cg_nblk = nb;
+}
+
+sg_status time_cgs_passes(sg_handle* h, sg_prec prec, int j, int reps, cudaStream_t st, double* us) {
+  GmresWork& w = h->gw;
+  if (!w.V || w.prec_bytes != (int)sizeof(float2) || j < 0 || j + 1 > w.restart || reps < 1)
+    return fail(SG_EINVAL, "CGS2 timing needs a complex64 workspace with room for step j");
+  Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+  // zero basis and scalars: the passes read and write the same amount
+  // whatever the values; the done flag is cleared before every step so that
+  // no pass skips its work
+  SG_CUDA_TRY(cudaMemsetAsync(w.V, 0, (size_t)(j + 2) * h->N * sizeof(float2), st));
+  SG_CUDA_TRY(cudaMemsetAsync(w.dscal, 0, (size_t)c.L.total * sizeof(double), st));
+  auto step = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(w.dctl, 0, 16 * sizeof(int), st);
+    return e ? e : cgs_passes<float>(c, prec, j);
+  };
+  for (int r = 0; r < 2; ++r) SG_CUDA_TRY(step());
+  cudaEvent_t e0, e1;
+  SG_CUDA_TRY(cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e) {
+    cudaEventDestroy(e0);
+    return fail(SG_ECUDA, std::string("cudaEventCreate: ") + cudaGetErrorString(e));
+  }
+  e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && !e; ++r) e = step();
+  if (!e) e = cudaEventRecord(e1, st);
+  if (!e) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e) return fail(SG_ECUDA, std::string("CGS2 timing: ") + cudaGetErrorString(e));
+  *us = 1000.0 * ms / reps;
+  return SG_OK;
+}
+
+}  // namespace sgi
 
 // ------------------------------------------------------------------ stationary iteration
 // The stationary iteration of Sec. 5 with the mean-value (or CSL mean-value)

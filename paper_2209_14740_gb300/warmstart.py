@@ -103,6 +103,46 @@ class WarmStart:
         return x0
 
 
+def pod_basis(S, rank, n_snapshots, torch, dev):
+    """Rank-`rank` POD basis of the first n_snapshots rows of S (n x N
+    complex64, device): rows u_i = lambda_i^-1/2 sum_k V_ki s_k from the
+    eigenpairs (lambda_i, V_i) of the snapshot Gram matrix, in decreasing
+    lambda, orthonormal.  Returns U (rank x N complex64, device) and all
+    eigenvalues in decreasing order (host)."""
+    n, N = S.shape
+    ns = min(n_snapshots, n)
+    G = torch.empty((ns, ns), dtype=torch.complex64, device=dev)
+    work = torch.empty(ns * ns, dtype=torch.complex128, device=dev)
+    B.cgemm_hn(S, N, S, N, ns, ns, N, G, work)
+    Gh = G.cpu().numpy().astype(np.complex128)
+    Gh = 0.5 * (Gh + Gh.conj().T)
+    lam, V = np.linalg.eigh(Gh)
+    order = np.argsort(lam)[::-1]
+    rank = min(rank, ns)
+    lam_top = np.maximum(lam[order[:rank]], 1e-30)
+    W = (V[:, order[:rank]] / np.sqrt(lam_top)).T.astype(np.complex64)
+    U = torch.empty((rank, N), dtype=torch.complex64, device=dev)
+    B.cgemm_nn(torch.from_numpy(np.ascontiguousarray(W)).to(dev), S[:ns].contiguous(), rank, N, ns, U)
+    return U, lam[order]
+
+
+def pod_errors(U, X, ranks, torch, dev):
+    """Best-approximation errors of the rows x_j of X (m x N complex64,
+    device) in the spans of the first R rows of U (orthonormal), for each R
+    in ranks: ||x - P_R x|| / ||x|| = sqrt(1 - sum_{i<R} |<u_i, x>|^2 /
+    ||x||^2).  Returns {R: per-row errors (host)} -- the floor that any
+    decoder x0 = U_R c reaches with the best coefficients c."""
+    r, N = U.shape
+    m = X.shape[0]
+    Cm = torch.empty((r, m), dtype=torch.complex64, device=dev)
+    work = torch.empty(r * m, dtype=torch.complex128, device=dev)
+    B.cgemm_hn(U, N, X, N, r, m, N, Cm, work)
+    c2 = (Cm.abs().double() ** 2).cpu().numpy()               # r x m
+    x2 = (X.abs().double() ** 2).sum(dim=1).cpu().numpy()     # m
+    csum = np.cumsum(c2, axis=0)
+    return {R: np.sqrt(np.clip(1.0 - csum[min(R, r) - 1] / x2, 0.0, None)) for R in ranks}
+
+
 def build(params, S, torch, dev, rank=64, n_snapshots=512, width=512, hidden=3, epochs=300, batch=128, lr=1e-3,
           seed=7, lo=PARAM_LO, hi=PARAM_HI):
     """POD decoder + trained network from training parameters (n x 5, host)

@@ -316,3 +316,33 @@ def test_scaled_guess_never_starts_above_zero_guess(B):
     zeta = np.vdot(Ag, ref.b) / np.vdot(Ag, Ag).real
     assert np.linalg.norm(ref.b - zeta * Ag) <= np.linalg.norm(ref.b)
     op.close()
+
+
+def test_pod_ceiling_against_numpy(B):
+    """pod_basis / pod_errors (the decoder's best-approximation floor) on
+    random low-rank-plus-noise snapshots: the basis rows are orthonormal, span
+    the leading left singular space of the snapshots (numpy SVD), and the
+    reported errors equal numpy's projection errors."""
+    from paper_2209_14740_gb300 import warmstart
+    rng = np.random.default_rng(11)
+    n, N, r = 96, 2000, 12
+    A = (rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r))) @ \
+        (rng.standard_normal((r, N)) + 1j * rng.standard_normal((r, N)))
+    A += 0.3 * (rng.standard_normal((n, N)) + 1j * rng.standard_normal((n, N)))
+    S = torch.from_numpy(A.astype(np.complex64)).to(DEV)
+    U, lam = warmstart.pod_basis(S, 16, 80, torch, DEV)
+    Uh = U.cpu().numpy().astype(np.complex128)
+    assert np.abs(Uh.conj() @ Uh.T - np.eye(16)).max() < 2e-4
+    sv = np.linalg.svd(A[:80].astype(np.complex64).astype(np.complex128), compute_uv=False)
+    np.testing.assert_allclose(lam[:16], sv[:16] ** 2, rtol=1e-3)
+    X = rng.standard_normal((5, N)) + 0j
+    X[:3] = (rng.standard_normal((3, n)) @ A) / n          # inside the snapshot span (mostly)
+    Xd = torch.from_numpy(X.astype(np.complex64)).to(DEV)
+    errs = warmstart.pod_errors(U, Xd, (4, 12, 16), torch, DEV)
+    Xc = X.astype(np.complex64).astype(np.complex128)
+    for R, e in errs.items():
+        Q = Uh[:R].conj()                                   # coefficients c = conj(U) x
+        proj = (Q @ Xc.T).T @ Uh[:R]
+        ref = np.linalg.norm(Xc - proj, axis=1) / np.linalg.norm(Xc, axis=1)
+        np.testing.assert_allclose(e, ref, rtol=5e-3, atol=2e-3)
+    assert errs[12][:3].max() < 0.2 and np.all(errs[4][:3] > errs[12][:3]) and errs[16][3:].min() > 0.9

@@ -655,6 +655,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
 // the copier waits only for stages the MMA lane has issued; the MMA lane
 // starts tile i + 2 in buffer i % 2 only after the epilogue released tile i,
 // and the epilogue waits for tile i's accumulator before releasing it.
+#ifndef SG_TC_PDL
+#define SG_TC_PDL 1
+#endif
 #ifndef SG_TC_PERSIST
 #define SG_TC_PERSIST 1
 #endif
@@ -1034,7 +1037,7 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = SG_TC_PDL;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   CUtensorMap none;

@@ -160,7 +160,10 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 // and the grid runs in one wave.  Per-warp sums go to a [warp][value] table in
 // shared memory, block sums to part[value * gridDim.x + block], and the last
 // block adds the blocks in a fixed order (bitwise reproducible).
-constexpr int CG_EPT = 4;
+#ifndef SG_CG_EPT
+#define SG_CG_EPT 4
+#endif
+constexpr int CG_EPT = SG_CG_EPT;
 constexpr int CG_WARPS = RED_THREADS / 32;
 constexpr int CG_QB = 4;   // complex64: basis vectors per group of loads in flight
 // Resident blocks per SM the complex64 passes are compiled for (at most 85
@@ -849,26 +852,55 @@ __global__ void __launch_bounds__(LSQ_THREADS) k_lsq(double* D, const int* ctl, 
   for (int i = k + tid; i <= m; i += blockDim.x) yc[i] = make_double2(0, 0);
 }
 
-// u = sum_{i<k} yc_i V_i  (k read on the device).
+// u = sum_{i<k} yc_i V_i  (k read on the device).  Chunks of RED_THREADS *
+// CG_EPT elements per block as in the CGS2 passes: a thread keeps CG_EPT
+// accumulators and issues the loads of CG_QB basis vectors (CG_QB * CG_EPT
+// values) before using any; each element adds the terms in the order
+// i = 0 .. k-1.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_lincomb(const C2<T>* __restrict__ V, long long N,
-                                                        const double* __restrict__ yc, const int* ctl,
-                                                        C2<T>* __restrict__ u) {
+__device__ __forceinline__ void lincomb_body(const C2<T>* __restrict__ V, long long N,
+                                             const double* __restrict__ yc, const int* ctl, C2<T>* __restrict__ u) {
   __shared__ C2<T> cs[MAXV];
   const int k = ctl[CTL_K];
   for (int i = threadIdx.x; i < k; i += blockDim.x) cs[i] = mkc<T>((T)yc[2 * i], (T)yc[2 * i + 1]);
   __syncthreads();
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
-    C2<T> acc = mkc<T>(T(0), T(0));
-    for (int i = 0; i < k; ++i) {
-      const C2<T> v = V[(size_t)i * N + e];
-      const C2<T> c = cs[i];
-      acc.x += c.x * v.x - c.y * v.y;
-      acc.y += c.x * v.y + c.y * v.x;
+  const long long chunk = (long long)RED_THREADS * CG_EPT;
+  for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
+    C2<T> acc[CG_EPT];
+#pragma unroll
+    for (int kk = 0; kk < CG_EPT; ++kk) acc[kk] = mkc<T>(T(0), T(0));
+    for (int i0 = 0; i0 < k; i0 += CG_QB) {
+      C2<T> v[CG_QB][CG_EPT];
+      load_group<T>(V, N, k, i0, base, v);
+#pragma unroll
+      for (int q = 0; q < CG_QB; ++q) {
+        if (i0 + q >= k) break;
+        const C2<T> c = cs[i0 + q];
+#pragma unroll
+        for (int kk = 0; kk < CG_EPT; ++kk) {
+          acc[kk].x += c.x * v[q][kk].x - c.y * v[q][kk].y;
+          acc[kk].y += c.x * v[q][kk].y + c.y * v[q][kk].x;
+        }
+      }
     }
-    u[e] = acc;
+#pragma unroll
+    for (int kk = 0; kk < CG_EPT; ++kk) {
+      const long long e = base + kk * RED_THREADS;
+      if (e < N) u[e] = acc[kk];
+    }
   }
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_lincomb(const C2<T>* __restrict__ V, long long N,
+                                                        const double* __restrict__ yc, const int* ctl,
+                                                        C2<T>* __restrict__ u) {
+  lincomb_body<T>(V, N, yc, ctl, u);
+}
+template <>
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_lincomb<float>(
+    const C2<float>* __restrict__ V, long long N, const double* __restrict__ yc, const int* ctl,
+    C2<float>* __restrict__ u) {
+  lincomb_body<float>(V, N, yc, ctl, u);
 }
 
 // x += z (z may be lower precision); skipped if k == 0.
@@ -1207,7 +1239,7 @@ sg_status run_cycle(Ctx& c, sg_prec prec, int m, double tol_est, double ref, int
     note_launch();
   }
   const C2<T>* basis = flex ? reinterpret_cast<const C2<T>*>(w.Zb) : V;
-  k_lincomb<T><<<c.grid, RED_THREADS, 0, c.st>>>(basis, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
+  k_lincomb<T><<<c.cg_grid, RED_THREADS, 0, c.st>>>(basis, c.h->N, w.dscal + c.L.yc, w.dctl, Z); note_launch();
   SG_CUDA_TRY(cudaGetLastError());
   if (!flex && !c.left) SG_CUDA_TRY(precond_apply<T>(c, prec, Z, Z, nullptr));
   return SG_OK;
@@ -1935,7 +1967,7 @@ cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, 
         note_launch();
         const float2* basis = flex ? reinterpret_cast<const float2*>(w.Zb) : reinterpret_cast<const float2*>(w.V);
         float2* Z = reinterpret_cast<float2*>(w.Z);
-        k_lincomb<float><<<c.grid, RED_THREADS, 0, c.st>>>(basis, N, D + c.L.yc, w.dctl, Z); note_launch();
+        k_lincomb<float><<<c.cg_grid, RED_THREADS, 0, c.st>>>(basis, N, D + c.L.yc, w.dctl, Z); note_launch();
         cudaError_t e3 = cudaGetLastError();
         if (!e3 && !flex) e3 = precond_apply<float>(c, prec, Z, Z, nullptr);
         if (e3) return e3;

@@ -272,8 +272,10 @@ sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void*
 
 /* Solves `count` independent SG systems (different grids, chaos sizes and
  * wavenumbers allowed) with the same options.
- *   - One-graph route (SG_MIXED, device buffers, zero initial guesses, right
- *     or no preconditioning; taken unless concurrency < 0): the whole batch
+ *   - One-graph route (SG_MIXED, device buffers, right or no
+ *     preconditioning, zero initial guesses or per-system guesses x0[k]
+ *     under any x0_policy, opts->x0 NULL; taken unless concurrency < 0):
+ *     the whole batch
  *     is ONE CUDA graph launch.  Each system is a chain of conditional nodes
  *     (refinement steps, chunks of 8 Arnoldi steps) whose conditions its own
  *     kernels set on the device, so restarts, refinements and convergence
@@ -281,9 +283,11 @@ sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const void* b, void*
  *     The graph is built and instantiated on the first call with a given
  *     set of handles, vectors and options and reused afterwards.  It unrolls
  *     4 refinement steps; a system still above tol after them continues on
- *     the per-system route from its current iterate (its info sums both).
- *     Arithmetic per system is sg_gmres's, so the result equals a solve of
- *     that system alone.
+ *     the per-system route from its current iterate (its info sums both);
+ *     a system whose guess is worse than zero, or whose b is zero while a
+ *     guess is given, is solved again on that route from the start (as
+ *     sg_gmres restarts it).  Arithmetic per system is sg_gmres's, so the
+ *     result equals a solve of that system alone.
  *   - Per-system route (otherwise): each system runs sg_gmres on its own
  *     internal CUDA stream, and up to `concurrency` systems (<= 0 means
  *     min(count, 16)) are in flight at once, driven by a pool of host

@@ -2,12 +2,14 @@
 //
 // Every system keeps its own device-resident GMRES state (the handle's
 // workspace).  Two routes:
-//  * one graph (mixed precision, zero initial guesses, right or no
-//    preconditioning): the whole batch is one cudaGraphLaunch whose
-//    conditional nodes let the device take the restart, refinement and
-//    convergence decisions (solver.cu, sgi_batched_graph); the few systems
-//    still above tol after the graph's unrolled refinement steps continue on
-//    the per-system route from their current iterate;
+//  * one graph (mixed precision, device buffers, right or no
+//    preconditioning, zero or per-system initial guesses): the whole batch is
+//    one cudaGraphLaunch whose conditional nodes let the device take the
+//    restart, refinement and convergence decisions (solver.cu,
+//    sgi_batched_graph); the few systems still above tol after the graph's
+//    unrolled refinement steps continue on the per-system route from their
+//    current iterate, and a system whose guess is worse than zero (or whose
+//    b is zero) is solved again there from the start;
 //  * per system: each system runs sg_gmres on its own non-blocking CUDA
 //    stream, driven by a small pool of host threads (each thread owns one
 //    stream and takes the next unsolved system from a shared counter).
@@ -24,7 +26,8 @@
 sg_status sgi_prepare_workspace(sg_handle* h, const sg_gmres_opts* opts);   // solver.cu
 bool sgi_batched_graph_eligible(const sg_gmres_opts* opts, const void* const* x0, int count);
 sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b,
-                            void* const* x, sg_gmres_info* infos, void* stream, std::vector<int>* pending);
+                            void* const* x, const void* const* x0, sg_gmres_info* infos, void* stream,
+                            std::vector<int>* pending, std::vector<int>* redo);
 
 namespace {
 
@@ -143,11 +146,13 @@ extern "C" sg_status sg_gmres_batched(sg_handle* const* h, int count, const sg_g
     for (int k = 0; k < count; ++k) all[k] = k;
     bool done = false;
     if (concurrency >= 0 && sgi_batched_graph_eligible(opts, x0, count)) {
-      std::vector<int> pending;
-      if (sgi_batched_graph(h, count, opts, b, x, inf.data(), stream, &pending) == SG_OK) {
+      std::vector<int> pending, redo;
+      if (sgi_batched_graph(h, count, opts, b, x, x0, inf.data(), stream, &pending, &redo) == SG_OK) {
         for (int k = 0; k < count; ++k) status[k] = inf[k].status;
         for (int k : pending) status[k] = SG_OK;
+        for (int k : redo) status[k] = SG_OK;
         sg_status s = run_pool(h, pending, opts, b, x, x0, inf, status, errs, concurrency, stream, true);
+        if (s == SG_OK) s = run_pool(h, redo, opts, b, x, x0, inf, status, errs, concurrency, stream, false);
         if (s != SG_OK) return s;
         done = true;
       }

@@ -1712,8 +1712,9 @@ extern "C" sg_status sg_stationary(sg_handle* h, const sg_stationary_opts* opts,
 // ------------------------------------------------------------------ batched solve as one graph
 // Independent SG systems solved by ONE cudaGraphLaunch: the graph holds one
 // chain per system, and the device decides the control flow the host takes
-// in sg_gmres.  Per system (mixed precision, zero initial guess):
-//   init: x = 0, r = b (complex64, V_0), ||b||^2;
+// in sg_gmres.  Per system (mixed precision):
+//   init: x = 0 or the system's guess (scaled by its minimal-residual
+//         multiple under SG_X0_SCALED), ||b||^2, r = b - A x (complex64, V_0);
 //   R times: [decide: relres = ||r|| / ||b||; at tol, maxit or a non-finite
 //            value the system stops, else a cycle starts (same inner
 //            tolerance rule as sg_gmres)] -> IF(cycle) {
@@ -1725,7 +1726,9 @@ extern "C" sg_status sg_stationary(sg_handle* h, const sg_stationary_opts* opts,
 // sg_gmres (so a system's arithmetic is the one-at-a-time solve's, bit for
 // bit); the IF nodes are conditional graph nodes whose values the decide
 // kernels set (cudaGraphSetConditional).  Systems still above tol after R
-// refinement steps are finished by the caller from where the graph left them.
+// refinement steps are finished by the caller from where the graph left them;
+// a system whose guess is worse than zero (sg_gmres would restart it from
+// zero) or whose b is zero is solved again by the caller with sg_gmres.
 namespace {
 
 constexpr int BG_CHUNK = 8;        // Arnoldi steps per conditional chunk
@@ -1733,7 +1736,8 @@ constexpr int BG_MAX_OUTER = 4;    // refinement steps unrolled in the graph
 
 struct BgRecord {                  // per system, device
   int status;                      // 0 running, 1 converged, 2 breakdown, 3 step or refinement cap,
-                                   // 4 right-hand side not finite
+                                   // 4 right-hand side not finite, 5 start over on the per-system
+                                   // route (a guess worse than zero, or b = 0 with a guess)
   int outer;                       // refinement steps started
   int taken;                       // chunk bodies taken but the last of a cycle (for the launch count)
   int taken_last;                  // last-chunk bodies taken
@@ -1756,7 +1760,7 @@ __global__ void k_bg_init(int* ctl, int maxit, BgRecord* rec) {
 // sg_gmres's mixed inner tolerance: reduce by inner_tol, or aim at tol
 // directly when that is within 20x of it).
 __global__ void k_bg_decide_outer(double* D, int* ctl, DevLayout L, double tol, double inner_tol, int max_outer,
-                                  cudaGraphConditionalHandle hdl, BgRecord* rec) {
+                                  int guess, cudaGraphConditionalHandle hdl, BgRecord* rec) {
   const double bnorm = sqrt(D[L.sc + SC_BNORM]);
   const double rn = sqrt(D[L.sc + SC_RNORM2]);
   const double relres = bnorm == 0.0 ? 0.0 : rn / bnorm;   // b = 0: x = 0 is the solution
@@ -1766,6 +1770,10 @@ __global__ void k_bg_decide_outer(double* D, int* ctl, DevLayout L, double tol, 
   if (rec->status == 0) {
     if (!(bnorm <= 1.7976931348623157e308)) {
       rec->status = 4;
+    } else if (rec->outer == 0 && (((guess & 1) && bnorm == 0.0) || ((guess & 2) && !(rn / bnorm <= 1.0)))) {
+      // an initial guess that is worse than zero (sg_gmres restarts from
+      // zero), or b = 0 with a guess (sg_gmres returns x = 0)
+      rec->status = 5;
     } else if (!(relres == relres) || relres > 1e300 || (ctl[CTL_FLAGS] & FL_NAN)) {
       rec->status = 2;
     } else if (relres <= tol) {
@@ -1824,10 +1832,11 @@ struct BgGraph {
 };
 
 // Graphs keyed by (restart, maxit, max_outer, preconditioner, tol, inner_tol,
-// then per system: workspace id, b, x).  Workspace ids are never reused, so a
+// guess policy, then per system: workspace id, b, x, x0).  Workspace ids are never reused, so a
 // graph can never name a freed or reallocated workspace; freeing a workspace
 // also drops the graphs that name it.
-constexpr int BG_KEY_HEAD = 6;
+constexpr int BG_KEY_HEAD = 7;
+constexpr int BG_KEY_PER_SYSTEM = 4;
 std::mutex g_bg_mu;
 std::map<std::vector<uintptr_t>, BgGraph> g_bg_cache;
 
@@ -1883,7 +1892,7 @@ cudaError_t bg_add_if(cudaGraph_t parent, cudaGraphNode_t* prev, cudaGraphCondit
 }
 
 cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b, void* const* x,
-                     int m, int maxit, int max_outer, BgGraph* out) {
+                     const void* const* x0, int m, int maxit, int max_outer, BgGraph* out) {
   BgGraph G;
   G.count = count;
   G.k_outer.assign(count, 0);
@@ -1908,14 +1917,33 @@ cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, 
     cudaGraphNode_t prev = nullptr;
     cudaGraph_t g = nullptr;
     long long nk = 0;
-    // init
+    // init (sg_gmres's sequence: x0 or zero, ||b||, the scaled guess, r)
+    const double2* x0s = x0 ? static_cast<const double2*>(x0[s]) : nullptr;
+    const int policy = opts->x0_policy;
+    // bit 0: a guess is given; bit 1: it must not be worse than zero
+    const int guess = x0s ? (policy != SG_X0_AS_GIVEN ? 3 : 1) : 0;
     e = bg_capture(c.st, [&]() -> cudaError_t {
-      cudaError_t e3 = cudaMemsetAsync(xs, 0, (size_t)N * sizeof(double2), c.st);
+      cudaError_t e3 = cudaSuccess;
+      if (!x0s) e3 = cudaMemsetAsync(xs, 0, (size_t)N * sizeof(double2), c.st);
+      else if (x0s != xs) e3 = cudaMemcpyAsync(xs, x0s, (size_t)N * sizeof(double2), cudaMemcpyDeviceToDevice, c.st);
       if (e3) return e3;
       k_bg_init<<<1, 1, 0, c.st>>>(w.dctl, maxit_s, rec); note_launch();
       k_residual<double, double><<<c.grid, RED_THREADS, 0, c.st>>>(bs, nullptr, nullptr, N, w.part, c.pstride,
                                                                    w.counter, D + c.L.sc + SC_BNORM); note_launch();
-      k_residual<double, float><<<c.grid, RED_THREADS, 0, c.st>>>(bs, nullptr, (float2*)w.V, N, w.part, c.pstride,
+      if (!x0s) {
+        k_residual<double, float><<<c.grid, RED_THREADS, 0, c.st>>>(bs, nullptr, (float2*)w.V, N, w.part, c.pstride,
+                                                                    w.counter, D + c.L.sc + SC_RNORM2); note_launch();
+        return cudaGetLastError();
+      }
+      double2* ax = (double2*)w.R64;
+      if ((e3 = launch_matvec<double>(hs, xs, ax, c.st))) return e3;
+      if (policy == SG_X0_SCALED) {
+        double* zeta = D + c.L.sc + SC_ZETA;
+        k_x0_zeta<double><<<c.grid, RED_THREADS, 0, c.st>>>(bs, ax, N, w.part, c.pstride, w.counter, zeta);
+        note_launch();
+        k_cscale2<double><<<c.grid, RED_THREADS, 0, c.st>>>(xs, ax, N, zeta); note_launch();
+      }
+      k_residual<double, float><<<c.grid, RED_THREADS, 0, c.st>>>(bs, ax, (float2*)w.V, N, w.part, c.pstride,
                                                                   w.counter, D + c.L.sc + SC_RNORM2); note_launch();
       return cudaGetLastError();
     }, &g, &nk);
@@ -1925,7 +1953,8 @@ cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, 
       cudaGraphConditionalHandle ho;
       e = cudaGraphConditionalHandleCreate(&ho, G.graph, 0, cudaGraphCondAssignDefault);
       if (!e) e = bg_capture(c.st, [&]() -> cudaError_t {
-        k_bg_decide_outer<<<1, 1, 0, c.st>>>(D, w.dctl, c.L, tol, inner_tol, max_outer, ho, rec); note_launch();
+        k_bg_decide_outer<<<1, 1, 0, c.st>>>(D, w.dctl, c.L, tol, inner_tol, max_outer, guess, ho, rec);
+        note_launch();
         return cudaGetLastError();
       }, &g, &nk);
       if (!e) e = bg_add_child(G.graph, &prev, g);
@@ -2002,12 +2031,12 @@ cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, 
 
 // Whether sg_gmres_batched can take the one-graph route for these options.
 bool sgi_batched_graph_eligible(const sg_gmres_opts* opts, const void* const* x0, int count) {
+  (void)x0;
+  (void)count;
   if (opts->mode != SG_MIXED || opts->host_io || opts->x0 || opts->side != 0) return false;
-  if (opts->prec != SG_PREC_NONE && opts->prec != SG_PREC_MEAN && opts->prec != SG_PREC_CSL_MEAN) return false;
-  if (x0)
-    for (int k = 0; k < count; ++k)
-      if (x0[k]) return false;
-  return true;
+  if (opts->x0_policy != SG_X0_AS_GIVEN && opts->x0_policy != SG_X0_FALLBACK && opts->x0_policy != SG_X0_SCALED)
+    return false;
+  return opts->prec == SG_PREC_NONE || opts->prec == SG_PREC_MEAN || opts->prec == SG_PREC_CSL_MEAN;
 }
 
 // Drops the cached batch graphs that name workspace `uid` (it is being freed).
@@ -2015,7 +2044,7 @@ void sgi_forget_batched_graphs(unsigned long long uid) {
   std::lock_guard<std::mutex> lock(g_bg_mu);
   for (auto it = g_bg_cache.begin(); it != g_bg_cache.end();) {
     bool hit = false;
-    for (size_t i = BG_KEY_HEAD; i < it->first.size(); i += 3) hit = hit || it->first[i] == (uintptr_t)uid;
+    for (size_t i = BG_KEY_HEAD; i < it->first.size(); i += BG_KEY_PER_SYSTEM) hit = hit || it->first[i] == (uintptr_t)uid;
     if (hit) {
       bg_free(it->second);
       it = g_bg_cache.erase(it);
@@ -2030,8 +2059,10 @@ void sgi_forget_batched_graphs(unsigned long long uid) {
 // unrolled refinement steps (the caller continues them from x[k]; their
 // infos then hold the steps taken so far and status SG_ENOTCONV).
 sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts* opts, const void* const* b,
-                            void* const* x, sg_gmres_info* infos, void* stream, std::vector<int>* pending) {
+                            void* const* x, const void* const* x0, sg_gmres_info* infos, void* stream,
+                            std::vector<int>* pending, std::vector<int>* redo) {
   pending->clear();
+  redo->clear();
   int m = 0;
   for (int k = 0; k < count; ++k) {
     int mk = opts->restart <= 0 ? (int)std::min<long long>(h[k]->N, MAXV - 1) : opts->restart;
@@ -2054,10 +2085,12 @@ sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts*
   std::memcpy(&ib, &itol, 8);
   key.push_back((uintptr_t)tb);
   key.push_back((uintptr_t)ib);
+  key.push_back((uintptr_t)opts->x0_policy);
   for (int k = 0; k < count; ++k) {
     key.push_back((uintptr_t)h[k]->gw.uid);
     key.push_back((uintptr_t)b[k]);
     key.push_back((uintptr_t)x[k]);
+    key.push_back((uintptr_t)(x0 ? x0[k] : nullptr));
   }
   std::lock_guard<std::mutex> lock(g_bg_mu);
   auto it = g_bg_cache.find(key);
@@ -2067,7 +2100,7 @@ sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts*
       g_bg_cache.clear();
     }
     BgGraph G;
-    SG_CUDA_TRY(bg_build(h, count, opts, b, x, m, maxit, max_outer, &G));
+    SG_CUDA_TRY(bg_build(h, count, opts, b, x, x0, m, maxit, max_outer, &G));
     it = g_bg_cache.emplace(key, G).first;
   }
   BgGraph& G = it->second;
@@ -2097,6 +2130,8 @@ sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts*
       inf.status = SG_ETIMEOUT;
     } else if (r == 0) {
       pending->push_back(k);
+    } else if (r == 5) {
+      redo->push_back(k);
     }
     if (infos) infos[k] = inf;
   }

@@ -202,3 +202,52 @@ def test_graph_route_64_heterogeneous_systems(B):
         assert relres <= 1e-8, (k, relres)
     for op in ops:
         op.close()
+
+
+@pytest.mark.parametrize("policy", ["scaled", "fallback", "as_given"])
+def test_graph_route_with_initial_guesses(B, policy):
+    """Per-system guesses on the graph route: good guesses (the solution
+    perturbed), one guess worse than zero (restarted from zero by sg_gmres:
+    the graph hands that system back under SG_X0_FALLBACK; scaled, it is
+    never worse than zero; as given, it is kept), one
+    system without a guess and one with b = 0; every system equals the
+    one-at-a-time sg_gmres with the same guess, bit for bit."""
+    pol = {"scaled": B.X0_SCALED, "fallback": B.X0_FALLBACK, "as_given": B.X0_AS_GIVEN}[policy]
+    probs = batch_problems()[:5]
+    ops = [B.SG(p) for p in probs]
+    refs = [sg.assemble_problem(p) for p in probs]
+    bs = [torch.from_numpy(r.b).to(DEV) for r in refs]
+    bs[4].zero_()
+    rng = np.random.default_rng(9)
+    x0s = []
+    for k, r in enumerate(refs):
+        xd = np.linalg.solve(r.A.toarray(), r.b) if r.A.shape[0] <= 4000 else None
+        if k == 2:
+            x0s.append(None)
+            continue
+        if k == 1 or xd is None:
+            g = 1e3 * (rng.standard_normal(r.A.shape[0]) + 1j * rng.standard_normal(r.A.shape[0]))
+        else:
+            g = xd * (1 + 0.05 * rng.standard_normal(xd.shape))
+        x0s.append(torch.from_numpy(g).to(DEV))
+    kw = dict(restart=20, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=5000, x0_policy=pol)
+    seq = []
+    for op, b, g in zip(ops, bs, x0s):
+        x = torch.zeros_like(b)
+        inf = op.gmres(b, x, x0=g, **kw)
+        seq.append((x, inf))
+    xs = [torch.full_like(b, float("nan")) for b in bs]
+    st, infos = B.gmres_batched(ops, bs, xs, x0s=x0s, **kw)
+    statuses = [i0["status"] for _, i0 in seq]
+    assert st == (B.SG_OK if all(s == B.SG_OK for s in statuses) else B.SG_ENOTCONV)
+    for k in range(len(ops)):
+        x1, i0 = seq[k]
+        assert infos[k]["status"] == i0["status"], (k, infos[k], i0)
+        assert infos[k]["iters"] == i0["iters"] and infos[k]["outer"] == i0["outer"], (k, infos[k], i0)
+        assert torch.equal(xs[k], x1), k
+    assert not xs[4].any() and infos[4]["relres"] == 0.0
+    if pol == B.X0_FALLBACK:
+        assert infos[1]["graph_outer"] == 0          # handed back: its guess is worse than zero
+    assert infos[0]["graph_outer"] >= 1 and infos[2]["graph_outer"] >= 1
+    for op in ops:
+        op.close()

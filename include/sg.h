@@ -417,6 +417,22 @@ sg_status sg_warmstart_predict(sg_warmstart* w, const double* params, int count,
 /* Message of the last failing call on this host thread ("" if none). */
 const char* sg_last_error(void);
 
+/* One of the four plain-TF32 transforms of the 2D fast-diagonalisation
+ * preconditioner (the SG_TF32 apply of sg_precond is t = 0, 1, 2, 3 in turn;
+ * the block solve for all P modes at once of Sec. 6.3, with S_blk^-1 =
+ * (Qhat_y (x) Qhat_x) diag(1 / (lambda_y,j + lambda_x,i + shift))
+ * (Qhat_y (x) Qhat_x)^T).  complex64, device buffers, per mode p (mxp, myp =
+ * mx, my rounded up to even; pad entries of Y are written as zero):
+ *   t = 0: Y_p = (X_p Qhat_x)^T        X [P][my][mx],  Y [P][mx][myp]
+ *   t = 1: Y_p = L^-1 o (X_p Qhat_y)   X, Y [P][mx][myp]  (L^-1 of `kind`)
+ *   t = 2: Y_p = (X_p Qhat_y^T)^T      X [P][mx][myp], Y [P][my][mxp]
+ *   t = 3: Y_p = X_p Qhat_x^T          X [P][my][mxp], Y [P][my][mx]
+ * kind: SG_PREC_MEAN or SG_PREC_CSL_MEAN.  X and Y must not overlap.  The
+ * same kernels as the apply (a primitive for timing one transform and for
+ * callers that fuse their own steps between them); SG_EUNSUPPORTED without the
+ * fast-diagonalisation route.  Asynchronous on `stream`. */
+sg_status sg_fd_transform(sg_handle* h, sg_prec kind, int t, const void* X, void* Y, void* stream);
+
 /* ---------------------------------------------------------------- launch-shape tuning
  * Three launch shapes of the hot path depend on the problem (grid, P) and
  * are not fixed by the method (the paper times whole solves only):

@@ -30,7 +30,7 @@ EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "
             "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
             "sg_selftest_wait_timeout", "sg_alu_peak", "sg_stationary", "sg_statistics",
             "sg_warmstart_create", "sg_warmstart_destroy", "sg_warmstart_predict", "sg_autotune", "sg_tune_get",
-            "sg_tune_set"]
+            "sg_tune_set", "sg_fd_transform"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -145,6 +145,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_selftest_wait_timeout.restype = i
     lib.sg_alu_peak.argtypes = [i, dp, vp]
     lib.sg_alu_peak.restype = i
+    lib.sg_fd_transform.argtypes = [vp, i, i, vp, vp, vp]
+    lib.sg_fd_transform.restype = i
     lib.sg_autotune.argtypes = [vp, i, C.POINTER(SgTune), vp]
     lib.sg_autotune.restype = i
     lib.sg_tune_get.argtypes = [vp, C.POINTER(SgTune)]
@@ -328,6 +330,11 @@ class SG:
             entry = tune_table.lookup(prob.dim, inf.mx, inf.my, prob.s, prob.r)
             if entry is not None:
                 self.tune_set(entry)
+
+    def fd_transform(self, t, X, Y, kind=PREC_MEAN, stream=None):
+        """sg_fd_transform: transform t (0 .. 3) of the plain-TF32 fast
+        diagonalisation, X -> Y (complex64 device tensors, layouts in sg.h)."""
+        _check(load().sg_fd_transform(self.h, kind, t, _ptr(X), _ptr(Y), _stream(stream)))
 
     def autotune(self, restart=30, stream=None) -> dict:
         """sg_autotune: time the candidate launch shapes on this problem and

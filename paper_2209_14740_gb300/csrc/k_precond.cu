@@ -459,6 +459,23 @@ static cudaError_t fd_apply(const sg_handle* h, int which, const float2* R, floa
   return e;
 }
 
+// One plain-TF32 transform t of fd_apply (0 .. 3) on caller buffers, in the
+// layouts listed there; X by tensor copies where its row pitch allows (a map
+// encoded for X on each call), as the apply does on the handle's own buffers.
+cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, float2* Y, cudaStream_t st) {
+  if (h->dim != 2 || !h->fd || !h->blk[which].ready || t < 0 || t > 3) return cudaErrorNotSupported;
+  const int mx = h->mx, my = h->my, P = h->P;
+  const int mxp = mx + (mx & 1), myp = my + (my & 1);
+  // (input pitch, rows, K, output pitch, mode, batch rows) of the four transforms
+  const long long ldx[4] = {mx, myp, myp, mxp}, ldc[4] = {myp, myp, mxp, mx};
+  const int rows[4] = {P * my, P * mx, P * mx, P * my}, kdim[4] = {mx, my, my, mx};
+  const int mode[4] = {1, 0, 1, 0}, mb[4] = {my, 0, mx, 0};
+  CUtensorMap map;
+  const bool okm = tc_make_xmap(&map, X, ldx[t], rows[t], kdim[t]);
+  return tc_cgemm(h->tcB[t], X, ldx[t], rows[t], Y, ldc[t], mode[t], mb[t], t == 1 ? h->d_Linv32[which] : nullptr,
+                  t == 1 ? mx : 0, t == 1 ? mx : 1, nullptr, nullptr, h->d_err, st, false, okm ? &map : nullptr);
+}
+
 cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
                                 const int* skip, const double* in_scale) {
   if (h->dim != 2 || !h->fd || !h->blk[which].ready) return cudaErrorNotSupported;

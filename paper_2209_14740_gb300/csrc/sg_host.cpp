@@ -852,6 +852,19 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
   });
 }
 
+sg_status sg_fd_transform(sg_handle* h, sg_prec kind, int t, const void* X, void* Y, void* stream) {
+  return sgi::guarded([&]() -> sg_status {
+    if (!h || !X || !Y) return fail(SG_EINVAL, "NULL handle or vector");
+    if (t < 0 || t > 3) return fail(SG_EINVAL, "transform index must be 0 .. 3");
+    if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN) return fail(SG_EINVAL, "kind must be SG_PREC_MEAN or SG_PREC_CSL_MEAN");
+    const int which = kind == SG_PREC_MEAN ? 0 : 1;
+    if (h->dim != 2 || !h->fd || !h->blk[which].ready)
+      return fail(SG_EUNSUPPORTED, "the fast-diagonalisation transforms need a 2D problem with constant k_0");
+    SG_CUDA_TRY(fd_transform(h, which, t, (const float2*)X, (float2*)Y, (cudaStream_t)stream));
+    return SG_OK;
+  });
+}
+
 sg_status sg_selftest_wait_timeout(void* stream, int* timed_out, double* seconds) {
   return sgi::guarded([&]() -> sg_status {
     g_err.clear();

@@ -264,6 +264,9 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
 cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
                                 const int* skip, const double* in_scale);
 
+// One of the four plain-TF32 transforms of that apply on caller buffers.
+cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, float2* Y, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
                                    C2<T>* tmp, C2<T>* tmp2);

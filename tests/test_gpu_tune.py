@@ -94,3 +94,33 @@ def test_table_entries_are_applied(B):
         want = entry[k] if k != "tc_tile_n" or op.info["fast_diag"] else 0
         assert t[k] == want, (k, t, entry)
     op.close()
+
+
+@pytest.mark.parametrize("g,kind", [(63, "mean"), (64, "csl_mean"), (127, "mean")])
+def test_fd_transforms_compose_to_the_tf32_apply(B, g, kind):
+    """sg_fd_transform t = 0 .. 3 in turn gives the SG_TF32 preconditioner
+    apply bit for bit (odd and even grid widths: padded intermediates)."""
+    pr = inputs.helmholtz_2d(g, 3, 2, 20.0, 0.1)
+    op = B.SG(pr)
+    pk = B.PREC_MEAN if kind == "mean" else B.PREC_CSL_MEAN
+    mx, my, P = op.info["mx"], op.info["my"], op.P
+    mxp, myp = mx + (mx & 1), my + (my & 1)
+    rng = np.random.default_rng(g)
+    x = (rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)).astype(np.complex64)
+    X = torch.from_numpy(x).to(DEV)
+    Z = torch.empty_like(X)
+    op.precond(X, Z, pk, B.TF32)
+    size = P * max(mx, my) * max(mxp, myp)
+    T1 = torch.full((size,), float("nan"), dtype=torch.complex64, device=DEV)
+    T2 = torch.full((size,), float("nan"), dtype=torch.complex64, device=DEV)
+    Y = torch.full_like(X, float("nan"))
+    op.fd_transform(0, X, T1, pk)
+    op.fd_transform(1, T1, T2, pk)
+    op.fd_transform(2, T2, T1, pk)
+    op.fd_transform(3, T1, Y, pk)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, Z)
+    with pytest.raises(B.SgError) as ei:
+        op.fd_transform(4, X, T1, pk)
+    assert ei.value.status == B.SG_EINVAL
+    op.close()

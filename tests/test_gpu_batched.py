@@ -200,6 +200,17 @@ def test_graph_route_64_heterogeneous_systems(B):
         op.matvec(xg[k], ax, B.FP64)
         relres = (torch.linalg.vector_norm(bs[k] - ax) / torch.linalg.vector_norm(bs[k])).item()
         assert relres <= 1e-8, (k, relres)
+    # the oracle's residual and direct solution for the three smallest systems
+    small = sorted(range(len(ops)), key=lambda k: ops[k].N)[:3]
+    for k in small:
+        ref = sg.assemble_problem(probs[k])
+        assert np.array_equal(bs[k].cpu().numpy(), ref.b)
+        xk = xg[k].cpu().numpy()
+        rr = np.linalg.norm(ref.b - ref.A @ xk) / np.linalg.norm(ref.b)
+        assert rr <= 1e-8, (k, rr)
+        from oracle import krylov
+        xd = krylov.direct(ref.A, ref.b)
+        assert np.linalg.norm(xk - xd) / np.linalg.norm(xd) <= 1e-5, k
     for op in ops:
         op.close()
 

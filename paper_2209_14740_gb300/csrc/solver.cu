@@ -175,6 +175,16 @@ constexpr int CG_MIN_BLOCKS_C64 = 3;
 template <typename T>
 __device__ __forceinline__ void load_group(const C2<T>* __restrict__ V, long long N, int nv, int i0,
                                            long long base, C2<T> (&v)[CG_QB][CG_EPT]) {
+  // the whole group in range (all but the last chunk, all but the last group
+  // of vectors; a block-uniform test): plain loads at constant offsets
+  if (i0 + CG_QB <= nv && base - (long long)threadIdx.x + (long long)RED_THREADS * CG_EPT <= N) {
+    const C2<T>* __restrict__ p = V + (size_t)i0 * N + base;
+#pragma unroll
+    for (int q = 0; q < CG_QB; ++q)
+#pragma unroll
+      for (int k = 0; k < CG_EPT; ++k) v[q][k] = __ldg(p + (size_t)q * N + k * RED_THREADS);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < CG_QB; ++q) {
     const bool live = i0 + q < nv;

@@ -61,3 +61,19 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert b"too large" in lib.sg_last_error()
     assert lib.sg_matvec(None, 0, None, None, None) == binding.SG_EINVAL
     assert lib.sg_gmres(None, None, None, None, None, None) == binding.SG_EINVAL
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    """include/sg.h is a C header: a C99 translation unit that uses its
+    structs compiles with gcc -Wall -Werror."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use.c"
+    src.write_text('#include "sg.h"\n'
+                   'int main(void) { sg_desc d; sg_gmres_opts o; sg_gmres_info i; sg_tune t;\n'
+                   '  (void)d; (void)o; (void)i; (void)t; return (int)sizeof(sg_tune); }\n')
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
+                    str(tmp_path / "use.o")], check=True)

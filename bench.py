@@ -118,12 +118,15 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_tensor_peak():
-    """TF32 dense TFLOP/s: measured BF16 burst peak x nominal TF32/BF16 ratio."""
+def load_tensor_peak(fp16=False):
+    """Dense tensor TFLOP/s for TF32 (measured BF16 burst peak x nominal
+    TF32/BF16 ratio) or binary16 (the BF16 peak itself: the same nominal rate)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    ratio = 1.0 if fp16 else TF32_PER_BF16
+    how = "measured bf16 (binary16 runs at the bf16 rate)" if fp16 else "measured bf16 x nominal tf32/bf16"
     if os.path.exists(p):
-        return float(json.load(open(p))["bf16_tflops"]) * TF32_PER_BF16, "measured bf16 x nominal tf32/bf16"
-    return 1900.0 * TF32_PER_BF16, "fallback bf16 x nominal tf32/bf16"
+        return float(json.load(open(p))["bf16_tflops"]) * ratio, how
+    return 1900.0 * ratio, how.replace("measured", "fallback")
 
 
 class ClockSampler:
@@ -561,52 +564,61 @@ def run_ours(args):
     x_mixed = x.clone()
 
     # ---------------------------------------------------------------- dominant kernel of the step
-    # The preconditioner apply of the solve's complex64 cycles (SG_TF32) is
-    # four launches of the tensor-core transform kernel (plain TF32 form),
-    # complex GEMMs of (P my) x mx by mx x mx (x direction) and (P mx) x my
-    # by my x my (y direction): the first reads the odd-pitch input with the
-    # loader warps (k_tc_cgemm), the other three take X by tensor copies in
-    # the persistent form (k_tc_cgemm_ps, the step's dominant kernel).  The
-    # persistent kernel alone is timed through sg_fd_transform (transform 2,
-    # the same launch as inside the apply), 20 launches with CUDA events on
-    # the solve's stream; the whole apply and transform 1 beside it.
+    # The preconditioner apply of the solve's complex64 cycles is four
+    # launches of the tensor-core transform kernel, complex GEMMs of (P my) x
+    # mx by mx x mx (x direction) and (P mx) x my by my x my (y direction):
+    # the first reads the odd-pitch complex64 input with the loader warps
+    # (k_tc_cgemm, TF32), the other three take X by tensor copies in the
+    # persistent form (k_tc_cgemm_ps: binary16 operands where the binary16
+    # route exists and the tuning keeps it, else TF32) -- the step's dominant
+    # kernel.  It is timed alone through sg_fd_transform (transform 2, the
+    # same launch as inside the apply), 20 launches with CUDA events on the
+    # solve's stream; the whole apply and transform 1 beside it.
     top = None
     if info_h.get("tf32_route"):
         mx, my = info_h["mx"], info_h["my"]
-        mxp, myp = mx + (mx & 1), my + (my & 1)
+        f16 = bool(info_h.get("fp16_route")) and not op.tune_get().get("tf32_transforms")
+        if f16:
+            mxp, myp = (mx + 3) // 4 * 4, (my + 3) // 4 * 4
+        else:
+            mxp, myp = mx + (mx & 1), my + (my & 1)
+        form = B.FP16 if f16 else B.TF32
         reps = 20
         Xp = torch.randn(N, dtype=torch.complex64, device=dev)
         Zp = torch.empty_like(Xp)
         for _ in range(3):
-            op.precond(Xp, Zp, B.PREC_MEAN, B.TF32)
+            op.precond(Xp, Zp, B.PREC_MEAN, form)
         pushed = nvtx(torch, "precond")
-        t_apply = event_ms(torch, stream, lambda: op.precond(Xp, Zp, B.PREC_MEAN, B.TF32), reps)
+        t_apply = event_ms(torch, stream, lambda: op.precond(Xp, Zp, B.PREC_MEAN, form), reps)
         nvtx_pop(torch, pushed)
         del Xp, Zp
         size = P * max(mx, my) * max(mxp, myp)
         T1 = torch.randn(size, dtype=torch.complex64, device=dev)
+        if f16:
+            T1.zero_()
         T2 = torch.empty_like(T1)
         for _ in range(3):
-            op.fd_transform(1, T1, T2)
-            op.fd_transform(0, T1, T2)
-        t_ps = event_ms(torch, stream, lambda: op.fd_transform(1, T1, T2), reps)
-        t_t1 = event_ms(torch, stream, lambda: op.fd_transform(0, T1, T2), reps)
+            op.fd_transform(1, T1, T2, B.PREC_MEAN, form)
+            op.fd_transform(0, T1, T2, B.PREC_MEAN, form)
+        t_ps = event_ms(torch, stream, lambda: op.fd_transform(1, T1, T2, B.PREC_MEAN, form), reps)
+        t_t1 = event_ms(torch, stream, lambda: op.fd_transform(0, T1, T2, B.PREC_MEAN, form), reps)
         del T1, T2
         flops = 8.0 * P * mx * my * my           # transform 2: (P mx) x my by my x my, complex
-        peak_t, peak_kind_t = load_tensor_peak()
+        peak_t, peak_kind_t = load_tensor_peak(fp16=f16)
+        peak_tf32, _ = load_tensor_peak(fp16=False)
         ach = flops / (t_ps * 1e-3) / 1e12
-        tr = transform_traffic()
-        top = {"kernel": "k_tc_cgemm_ps<128> (persistent plain-TF32 transform of the 2D preconditioner, "
-                         "3 of the 4 launches per apply)", "bound": "tensor",
+        tr = None if f16 else transform_traffic()
+        top = {"kernel": ("k_tc_cgemm_ps<128, true> (persistent binary16 transform, kind::f16" if f16 else
+                          "k_tc_cgemm_ps<128, false> (persistent plain-TF32 transform") +
+                         " of the 2D preconditioner, 3 of the 4 launches per apply)", "bound": "tensor",
                "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t, "traffic": tr,
                "traffic_source": "ncu capture of this kernel source (profiles/tc_cgemm_ps_511x511_s6_deg3.md)"
                if tr else None,
                "peak_kind": peak_kind_t, "us_per_launch": 1000.0 * t_ps, "flops_per_launch": flops,
                "units": "8 P m^3 real flop per launch (complex GEMM of (P m) x m by m x m; m = 511, P = 84)",
                "transform1_us": 1000.0 * t_t1,
-               "transform1_frac": flops / (t_t1 * 1e-3) / 1e12 / peak_t,
-               "apply_ms": t_apply,
-               "apply_mean_frac": flops / (t_apply / 4 * 1e-3) / 1e12 / peak_t}
+               "transform1_frac_tf32": flops / (t_t1 * 1e-3) / 1e12 / peak_tf32,
+               "apply_ms": t_apply}
 
     # ---------------------------------------------------------------- end to end with host buffers
     bh = torch.empty(N, dtype=torch.complex128, pin_memory=True)

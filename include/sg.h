@@ -80,9 +80,14 @@ typedef enum { SG_PREC_NONE = 0, SG_PREC_MEAN = 1, SG_PREC_CSL_MEAN = 2, SG_PREC
  *          refinement loop; b, x, x0 are complex128.
  * SG_TF32 (sg_precond only): complex64 operands, the 2D fast-diagonalisation
  *          transforms in plain TF32 on the tensor cores (relative error of
- *          the apply ~2e-3); the preconditioner the complex64 inner cycles
- *          of sg_gmres use (see there).  Not in the paper. */
-typedef enum { SG_FP64 = 0, SG_FP32 = 1, SG_MIXED = 2, SG_TF32 = 3 } sg_precision;
+ *          the apply ~2e-3).  Not in the paper.
+ * SG_FP16 (sg_precond only): complex64 operands, transforms 2-4 of the same
+ *          apply on binary16 operands (tensor-core kind::f16, FP32
+ *          accumulation) with binary16 intermediates, scaled to stay near 1
+ *          (the input by 1 / ||R||); the same 11-bit significands as TF32.
+ *          Where it exists (sg_info.fp16_route) the complex64 inner cycles
+ *          of sg_gmres use it (see there), else SG_TF32.  Not in the paper. */
+typedef enum { SG_FP64 = 0, SG_FP32 = 1, SG_MIXED = 2, SG_TF32 = 3, SG_FP16 = 4 } sg_precision;
 
 /* Problem description (Sec. 2.2 wavenumber model; Appendix A grids).
  *   dim    1 or 2 (unit interval / unit square).
@@ -140,6 +145,8 @@ typedef struct {
   double eig_kappa;    /* separable 2D: cond(Q) of those factors (set-up rejects > 100) */
   int tf32_route;      /* 1 if SG_TF32 applies are available (separable 2D, any line length);
                           the complex64 GMRES cycles then run flexible GMRES with them */
+  int fp16_route;      /* 1 if SG_FP16 applies are available (and the complex64 GMRES
+                          cycles use them unless sg_tune.tf32_transforms is set) */
 } sg_info;
 
 /* Builds the SG operator of Theorem 3.4 / Theorems A.1, A.2, A.5, A.6:
@@ -173,8 +180,9 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
 /* Z = (I_P (x) S_blk)^-1 R for the chosen block (see sg_prec), one
  * factorisation applied to all P modes at once (the reshape of Sec. 6.3).
  * SG_PREC_NONE copies R to Z.  R and Z: device, N complex; Z may equal R
- * (in place).  prec SG_FP64, SG_FP32 or SG_TF32 (complex64 data; separable
- * 2D problems only, SG_EUNSUPPORTED otherwise).
+ * (in place).  prec SG_FP64, SG_FP32, SG_TF32 or SG_FP16 (complex64 data;
+ * separable 2D problems only, SG_EUNSUPPORTED otherwise; SG_FP16 where
+ * sg_info.fp16_route).
  * Returns SG_EUNSUPPORTED for 2D problems whose k_0 varies in space (no
  * separable factorisation).  Asynchronous: a bounded wait that gives up
  * inside a tensor-core transform sets the handle's device flag, which the
@@ -257,7 +265,8 @@ typedef struct {
  * the device, lazy normalisation of the basis (Sec. 6.3 names GMRES, this
  * library fixes the variant).  Complex64 cycles (SG_FP32, and the inner
  * cycles of SG_MIXED) on 2D problems whose preconditioner has the SG_TF32
- * route run flexible GMRES with that preconditioner: z_j = M^-1 v_j is kept
+ * route run flexible GMRES with that preconditioner (its SG_FP16 form where
+ * it exists): z_j = M^-1 v_j is kept
  * for every step and the correction is sum_j y_j z_j, so the inexact
  * preconditioner changes the iteration count, not the attainable residual
  * (the workspace then holds restart more complex64 vectors).  b and x: N complex (complex128 for FP64 and
@@ -430,8 +439,15 @@ const char* sg_last_error(void);
  * kind: SG_PREC_MEAN or SG_PREC_CSL_MEAN.  X and Y must not overlap.  The
  * same kernels as the apply (a primitive for timing one transform and for
  * callers that fuse their own steps between them); SG_EUNSUPPORTED without the
- * fast-diagonalisation route.  Asynchronous on `stream`. */
-sg_status sg_fd_transform(sg_handle* h, sg_prec kind, int t, const void* X, void* Y, void* stream);
+ * fast-diagonalisation route.  Asynchronous on `stream`.
+ * prec SG_TF32: the layouts above in complex64.  prec SG_FP16 (where
+ * sg_info.fp16_route): the binary16 route of the solver's cycles: X of t = 0
+ * and Y of t = 3 complex64, the others binary16 pairs with rows padded to a
+ * multiple of 4 pairs (mx4, my4 in place of mxp, myp); t = 0 scales by
+ * sqrt(N) (the input taken as unit norm), t = 1 by 1 / max |L^-1|, t = 3
+ * divides both out. */
+sg_status sg_fd_transform(sg_handle* h, sg_prec kind, sg_precision prec, int t, const void* X, void* Y,
+                          void* stream);
 
 /* ---------------------------------------------------------------- launch-shape tuning
  * Three launch shapes of the hot path depend on the problem (grid, P) and
@@ -443,19 +459,23 @@ sg_status sg_fd_transform(sg_handle* h, sg_prec kind, int t, const void* X, void
  *                      ignored by problems without that kernel;
  *   tc_tile_n          output tile width of the plain-TF32 transforms of 2D
  *                      separable preconditioners (64 or 128 real columns);
- *                      0: the built-in rule per transform.
+ *                      0: the built-in rule per transform;
+ *   tf32_transforms    1: the complex64 GMRES cycles apply the SG_TF32 form
+ *                      of the preconditioner even where the SG_FP16 form
+ *                      exists; 0: SG_FP16 where it exists.
  * None changes the operator, the preconditioner or the method: the operator
  * and the transforms give the same bits for every choice; the CGS2 grid
  * changes the order of the block sums of the inner products (rounding only,
- * still reproducible for a fixed choice).
+ * still reproducible for a fixed choice); the transform precision changes the
+ * preconditioner within its ~2e-3 accuracy (the flexible cycles absorb it).
  * The *_us fields are filled by sg_autotune: measured times of one step's
  * CGS2 passes at step restart / 2, one complex64 operator application and
- * one plain-TF32 preconditioner apply (0 where not timed). */
+ * one preconditioner apply of the cycles' form (0 where not timed). */
 typedef struct {
   int cgs_blocks_per_sm;
   int op_ctas_per_sm;
   int tc_tile_n;
-  int reserved;
+  int tf32_transforms;
   double cgs_us;
   double op_us;
   double apply_us;

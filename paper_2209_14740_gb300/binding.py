@@ -20,7 +20,7 @@ STATUS_NAMES = ["SG_OK", "SG_EINVAL", "SG_ENOMEM", "SG_ECUDA", "SG_ENOTCONV", "S
                 "SG_ESINGULAR", "SG_ETIMEOUT", "SG_EUNSUPPORTED"]
 BC_DIRICHLET, BC_ABSORBING = 0, 1
 PREC_NONE, PREC_MEAN, PREC_CSL_MEAN, PREC_CSL = 0, 1, 2, 3
-FP64, FP32, MIXED, TF32 = 0, 1, 2, 3
+FP64, FP32, MIXED, TF32, FP16 = 0, 1, 2, 3, 4
 X0_AS_GIVEN, X0_FALLBACK, X0_SCALED = 0, 1, 2
 
 # every symbol include/sg.h declares
@@ -46,7 +46,7 @@ class SgInfo(C.Structure):
                 ("N", C.c_longlong), ("s", C.c_int), ("r", C.c_int), ("terms", C.c_int),
                 ("coupling_nnz", C.c_int), ("separable", C.c_int), ("specialised", C.c_int),
                 ("fast_diag", C.c_int), ("eig_orth_err", C.c_double), ("eig_kappa", C.c_double),
-                ("tf32_route", C.c_int)]
+                ("tf32_route", C.c_int), ("fp16_route", C.c_int)]
 
 
 class SgGmresOpts(C.Structure):
@@ -62,10 +62,10 @@ class SgGmresInfo(C.Structure):
 
 class SgTune(C.Structure):
     _fields_ = [("cgs_blocks_per_sm", C.c_int), ("op_ctas_per_sm", C.c_int), ("tc_tile_n", C.c_int),
-                ("reserved", C.c_int), ("cgs_us", C.c_double), ("op_us", C.c_double), ("apply_us", C.c_double)]
+                ("tf32_transforms", C.c_int), ("cgs_us", C.c_double), ("op_us", C.c_double), ("apply_us", C.c_double)]
 
 
-TUNE_KEYS = ("cgs_blocks_per_sm", "op_ctas_per_sm", "tc_tile_n")
+TUNE_KEYS = ("cgs_blocks_per_sm", "op_ctas_per_sm", "tc_tile_n", "tf32_transforms")
 
 
 class SgStationaryOpts(C.Structure):
@@ -145,7 +145,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_selftest_wait_timeout.restype = i
     lib.sg_alu_peak.argtypes = [i, dp, vp]
     lib.sg_alu_peak.restype = i
-    lib.sg_fd_transform.argtypes = [vp, i, i, vp, vp, vp]
+    lib.sg_fd_transform.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.sg_fd_transform.restype = i
     lib.sg_autotune.argtypes = [vp, i, C.POINTER(SgTune), vp]
     lib.sg_autotune.restype = i
@@ -331,22 +331,22 @@ class SG:
             if entry is not None:
                 self.tune_set(entry)
 
-    def fd_transform(self, t, X, Y, kind=PREC_MEAN, stream=None):
-        """sg_fd_transform: transform t (0 .. 3) of the plain-TF32 fast
-        diagonalisation, X -> Y (complex64 device tensors, layouts in sg.h)."""
-        _check(load().sg_fd_transform(self.h, kind, t, _ptr(X), _ptr(Y), _stream(stream)))
+    def fd_transform(self, t, X, Y, kind=PREC_MEAN, prec=TF32, stream=None):
+        """sg_fd_transform: transform t (0 .. 3) of the fast diagonalisation
+        (SG_TF32 or SG_FP16 form), X -> Y (device tensors, layouts in sg.h)."""
+        _check(load().sg_fd_transform(self.h, kind, prec, t, _ptr(X), _ptr(Y), _stream(stream)))
 
     def autotune(self, restart=30, stream=None) -> dict:
         """sg_autotune: time the candidate launch shapes on this problem and
         keep the fastest; returns the choices and their times."""
         t = SgTune()
         _check(load().sg_autotune(self.h, restart, C.byref(t), _stream(stream)))
-        return {k: getattr(t, k) for k, _ in SgTune._fields_ if k != "reserved"}
+        return {k: getattr(t, k) for k, _ in SgTune._fields_}
 
     def tune_get(self) -> dict:
         t = SgTune()
         _check(load().sg_tune_get(self.h, C.byref(t)))
-        return {k: getattr(t, k) for k, _ in SgTune._fields_ if k != "reserved"}
+        return {k: getattr(t, k) for k, _ in SgTune._fields_}
 
     def tune_set(self, shapes: dict):
         """sg_tune_set with the keys of TUNE_KEYS (missing keys: 0 = rule)."""

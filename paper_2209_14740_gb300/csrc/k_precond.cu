@@ -20,6 +20,8 @@
 //     parallel instead of mx * P sequential sweeps of length my.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <mutex>
 
 #include "sg_internal.h"
@@ -462,8 +464,33 @@ static cudaError_t fd_apply(const sg_handle* h, int which, const float2* R, floa
 // One plain-TF32 transform t of fd_apply (0 .. 3) on caller buffers, in the
 // layouts listed there; X by tensor copies where its row pitch allows (a map
 // encoded for X on each call), as the apply does on the handle's own buffers.
-cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, float2* Y, cudaStream_t st) {
+cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, float2* Y, cudaStream_t st,
+                         bool f16) {
   if (h->dim != 2 || !h->fd || !h->blk[which].ready || t < 0 || t > 3) return cudaErrorNotSupported;
+  if (f16) {
+    // the binary16 route's transform t with the apply's fixed scales (the
+    // input taken as unit norm): complex64 in for t = 0, out for t = 3,
+    // binary16 pairs with rows padded to a multiple of 4 in between
+    if (!h->fd16) return cudaErrorNotSupported;
+    const int mx = h->mx, my = h->my, P = h->P;
+    const int mx4 = (mx + 3) & ~3, my4 = (my + 3) & ~3;
+    const float c1 = (float)std::sqrt((double)h->N), c2 = h->fd16_scale[which];
+    if (t == 0)
+      return tc_cgemm(h->tcB[0], X, mx, P * my, Y, my4, 1, my, nullptr, 0, 1, nullptr, nullptr, h->d_err, st, false,
+                      nullptr, true, c1);
+    const long long ldx[4] = {0, my4, my4, mx4}, ldc[4] = {0, my4, mx4, mx};
+    const int rows[4] = {0, P * mx, P * mx, P * my}, kdim[4] = {0, my, my, mx};
+    CUtensorMap map;
+    if (!tc_make_xmap16(&map, X, ldx[t], rows[t], kdim[t])) return cudaErrorInvalidValue;
+    if (t == 1)
+      return tc_hgemm(h->tcB[1], X, rows[1], Y, ldc[1], 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true, nullptr,
+                      h->d_err, st, &map);
+    if (t == 2)
+      return tc_hgemm(h->tcB[2], X, rows[2], Y, ldc[2], 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, nullptr, h->d_err,
+                      st, &map);
+    return tc_hgemm(h->tcB[3], X, rows[3], Y, ldc[3], 0, 0, nullptr, 0, 1, nullptr, 1.0f / (c1 * c2), false, nullptr,
+                    h->d_err, st, &map);
+  }
   const int mx = h->mx, my = h->my, P = h->P;
   const int mxp = mx + (mx & 1), myp = my + (my & 1);
   // (input pitch, rows, K, output pitch, mode, batch rows) of the four transforms
@@ -474,6 +501,101 @@ cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, 
   const bool okm = tc_make_xmap(&map, X, ldx[t], rows[t], kdim[t]);
   return tc_cgemm(h->tcB[t], X, ldx[t], rows[t], Y, ldc[t], mode[t], mb[t], t == 1 ? h->d_Linv32[which] : nullptr,
                   t == 1 ? mx : 0, t == 1 ? mx : 1, nullptr, nullptr, h->d_err, st, false, okm ? &map : nullptr);
+}
+
+// ||R||^2 of N complex64 values in a fixed order: kFd16Blocks block sums,
+// then one block adds them in order and stores 1 / ||R|| and ||R||.
+__global__ void __launch_bounds__(256) k_fd16_norm_part(const float2* __restrict__ R, long long N,
+                                                        double* __restrict__ part) {
+  __shared__ double sm[256];
+  // a thread's sum in FP32 (a scale factor needs no more), four loads in
+  // flight; block and final sums in FP64
+  float acc = 0.0f;
+  const long long stride = (long long)gridDim.x * 256;
+  long long e = blockIdx.x * 256LL + threadIdx.x;
+  for (; e + 3 * stride < N; e += 4 * stride) {
+    const float2 v0 = R[e], v1 = R[e + stride], v2 = R[e + 2 * stride], v3 = R[e + 3 * stride];
+    acc += v0.x * v0.x + v0.y * v0.y + v1.x * v1.x + v1.y * v1.y + v2.x * v2.x + v2.y * v2.y + v3.x * v3.x +
+           v3.y * v3.y;
+  }
+  for (; e < N; e += stride) {
+    const float2 v = R[e];
+    acc += v.x * v.x + v.y * v.y;
+  }
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void __launch_bounds__(256) k_fd16_norm_final(const double* __restrict__ part, int nb,
+                                                         double* __restrict__ out) {
+  __shared__ double sm[256];
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 256) acc += part[b];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(sm[0]);
+    out[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    out[1] = nrm;
+  }
+}
+
+// fd_apply with transforms 2-4 in binary16 (kind::f16): transform 1 (the
+// odd-pitch complex64 input) stays TF32 and writes binary16 pairs.  Scaling
+// keeps the binary16 values near 1: the input normalised (in_scale, else 1 /
+// ||R|| computed here) times sqrt(N) (unit-norm vectors have entries near
+// 1 / sqrt(N)); transform 2's L^-1 times 1 / max |L^-1|; transform 4 undoes
+// both (and the norm when it was computed here).
+static cudaError_t fd_apply_h(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                              const int* skip, const double* in_scale) {
+  const int mx = h->mx, my = h->my, P = h->P;
+  const int mx4 = (mx + 3) & ~3, my4 = (my + 3) & ~3;
+  const float c1 = (float)std::sqrt((double)h->N), c2 = h->fd16_scale[which];
+  const double* s_in = in_scale;
+  const double* s_out = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!s_in) {
+    k_fd16_norm_part<<<kFd16Blocks, 256, 0, st>>>(R, h->N, h->d_fd16part); note_launch();
+    k_fd16_norm_final<<<1, 256, 0, st>>>(h->d_fd16part, kFd16Blocks, h->d_fd16s); note_launch();
+    if ((e = cudaGetLastError())) return e;
+    s_in = h->d_fd16s;
+    s_out = h->d_fd16s + 1;
+  }
+  void* t1 = h->d_tmp;
+  void* t2 = h->d_tmp2;
+  e = tc_cgemm(h->tcB[0], R, mx, P * my, reinterpret_cast<float2*>(t1), my4, 1, my, nullptr, 0, 1, s_in, skip,
+               h->d_err, st, false, nullptr, true, c1);
+  if (!e)
+    e = tc_hgemm(h->tcB[1], t1, P * mx, t2, my4, 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true, skip,
+                 h->d_err, st, &h->tc_xmap16[0]);
+  if (!e)
+    e = tc_hgemm(h->tcB[2], t2, P * mx, t1, mx4, 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, skip, h->d_err, st,
+                 &h->tc_xmap16[1]);
+  if (!e)
+    e = tc_hgemm(h->tcB[3], t1, P * my, Z, mx, 0, 0, nullptr, 0, 1, s_out, 1.0f / (c1 * c2), false, skip,
+                 h->d_err, st, &h->tc_xmap16[2]);
+  return e;
+}
+
+cudaError_t launch_precond_f16(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                               const int* skip, const double* in_scale) {
+  if (h->dim != 2 || !h->fd || !h->fd16 || !h->blk[which].ready) return cudaErrorNotSupported;
+  if (!in_scale && (!h->d_fd16s || !h->d_fd16part)) return cudaErrorNotSupported;
+  return fd_apply_h(h, which, R, Z, st, skip, in_scale);
+}
+
+cudaError_t launch_precond_fast(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                                const int* skip, const double* in_scale) {
+  if (h->fd16 && !h->tune_tf32 && in_scale) return fd_apply_h(h, which, R, Z, st, skip, in_scale);
+  return launch_precond_tf32(h, which, R, Z, st, skip, in_scale);
 }
 
 cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,

@@ -51,6 +51,7 @@
 // and nothing in global memory is written, before griddepcontrol.wait.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <complex>
@@ -159,6 +160,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t ad, uint64_t b
       : "memory");
 }
 
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -239,7 +248,7 @@ __device__ __forceinline__ float tf32_hi(float x) {
 //   mode 1: row m = p * MB + r goes to C[(p * Nc + n) * ldc + r] (the
 //           per-batch transpose used to switch the transformed direction;
 //           ldc >= MB is the pitch of the transposed rows)
-// With E: C *= E[n * e_ld + m % e_mod] * (*escale).
+// With E: C *= E[n * e_ld + m % e_mod]; then C *= (*escale if given) * oscale.
 struct TcArgs {
   const float* X;      // M rows of 2K floats, row stride ldx floats
   long long ldx;
@@ -258,7 +267,15 @@ struct TcArgs {
   const double* escale;
   const int* skip;
   int* err;            // set to 1 on a wait timeout
+  int out_half;        // C holds binary16 pairs (round to nearest even) instead of complex64
+  float oscale;        // every output value is multiplied by oscale (and by *escale if given)
 };
+
+// Element idx of C (one complex value), as complex64 or as a binary16 pair.
+__device__ __forceinline__ void put_c(const TcArgs& a, size_t idx, float2 c) {
+  if (a.out_half) reinterpret_cast<__half2*>(a.C)[idx] = __floats2half2_rn(c.x, c.y);
+  else a.C[idx] = c;
+}
 
 // Named barrier of the loader warps (the MMA and copy warps do not take part).
 __device__ __forceinline__ void loader_sync() { asm volatile("bar.sync 1, %0;" ::"n"(tc::NLOAD) : "memory"); }
@@ -509,13 +526,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
     } else if (!skipped) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // Epilogue, 32 real columns at a time
-      const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
+      const float es = (a.escale ? (float)*a.escale : 1.0f) * a.oscale;
       float2* stage = reinterpret_cast<float2*>(sm + OFF_RAW);
-      float2* cb = nullptr;   // mode 1: this row's element of column nq0
+      size_t cb = 0;          // mode 1: index in C of this row's element of column nq0
       bool pad1 = false;      // mode 1: also zero the pad entry after the last row r
       if (a.mode == 1 && mok) {
         const int p = m / a.MB, r = m - p * a.MB;
-        cb = a.C + ((size_t)p * a.Nc + nq0) * a.ldc + r;
+        cb = ((size_t)p * a.Nc + nq0) * a.ldc + r;
         pad1 = r == a.MB - 1 && a.ldc > a.MB;
       }
       const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(chalf * HALF);
@@ -541,14 +558,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
           if (a.E) {
             const float2 e = ev[qq];
             c = make_float2(es * (c.x * e.x - c.y * e.y), es * (c.x * e.y + c.y * e.x));
+          } else {
+            c = make_float2(es * c.x, es * c.y);
           }
           if (a.mode == 1) {
             // lanes hold consecutive rows r: each store writes consecutive addresses
             if (mok && n < a.Nc) {
-              cb[(size_t)qq * a.ldc] = c;
+              put_c(a, cb + (size_t)qq * a.ldc, c);
               // rows padded to even length are read whole by the next
               // transform's tensor copies: keep the pad at zero
-              if (pad1) cb[(size_t)qq * a.ldc + 1] = make_float2(0.f, 0.f);
+              if (pad1) put_c(a, cb + (size_t)qq * a.ldc + 1, make_float2(0.f, 0.f));
             }
           } else {
             stage[row * L::OUT_PITCH + chalf * (HALF / 2) + qq] = c;
@@ -564,8 +583,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm(TcArgs a, const __g
           const int rr = idx / (BN / 2), q = idx % (BN / 2);
           const int mm = m0 + rr, n = n0 + q;
           if (mm < a.M && n < a.Nc) {
-            a.C[(size_t)mm * a.ldc + n] = stage[rr * L::OUT_PITCH + q];
-            if (n == a.Nc - 1 && a.ldc > a.Nc) a.C[(size_t)mm * a.ldc + a.Nc] = make_float2(0.f, 0.f);
+            put_c(a, (size_t)mm * a.ldc + n, stage[rr * L::OUT_PITCH + q]);
+            if (n == a.Nc - 1 && a.ldc > a.Nc) put_c(a, (size_t)mm * a.ldc + a.Nc, make_float2(0.f, 0.f));
           }
         }
       }
@@ -680,12 +699,16 @@ struct CfgP {
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
 
-template <int BN>
+template <int BN, bool H>
 __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const __grid_constant__ CUtensorMap xmap) {
   using namespace tc;
   using L = CfgP<BN>;
   constexpr int NS = L::NS, B_TILE = L::B_TILE;
-  constexpr uint32_t IDESC = Cfg<BN, false>::IDESC;
+  // H: binary16 operands (kind::f16, K = 16 per MMA, 64 per 128-byte stage
+  // row; the byte layout of the stages is that of the TF32 form)
+  constexpr uint32_t IDESC = H ? ((1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24))
+                               : Cfg<BN, false>::IDESC;
+  constexpr int KE = H ? 2 * BK : BK;   // K values per stage
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -726,7 +749,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
     const int lg = warp & 3, chalf = warp >> 2;
     const int row = lg * 32 + lane;
     float2* stage = reinterpret_cast<float2*>(sm);
-    const float es = (a.E && a.escale) ? (float)*a.escale : 1.0f;
+    const float es = (a.escale ? (float)*a.escale : 1.0f) * a.oscale;
     int it = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
       const int b = it & 1;
@@ -747,11 +770,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float2* cb = nullptr;
+      size_t cb = 0;
       bool pad1 = false;
       if (a.mode == 1 && mok) {
         const int p = m / a.MB, r = m - p * a.MB;
-        cb = a.C + ((size_t)p * a.Nc + nq0) * a.ldc + r;
+        cb = ((size_t)p * a.Nc + nq0) * a.ldc + r;
         pad1 = r == a.MB - 1 && a.ldc > a.MB;
       }
       const uint32_t taddr = tmem + (uint32_t)(b * BN) + ((uint32_t)(lg * 32) << 16) + (uint32_t)(chalf * HALF);
@@ -783,11 +806,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
           if (a.E) {
             const float2 e = ev[qq];
             c = make_float2(es * (c.x * e.x - c.y * e.y), es * (c.x * e.y + c.y * e.x));
+          } else {
+            c = make_float2(es * c.x, es * c.y);
           }
           if (a.mode == 1) {
             if (mok && n < a.Nc) {
-              cb[(size_t)qq * a.ldc] = c;
-              if (pad1) cb[(size_t)qq * a.ldc + 1] = make_float2(0.f, 0.f);
+              put_c(a, cb + (size_t)qq * a.ldc, c);
+              if (pad1) put_c(a, cb + (size_t)qq * a.ldc + 1, make_float2(0.f, 0.f));
             }
           } else {
             stage[row * L::OUT_PITCH + chalf * (HALF / 2) + qq] = c;
@@ -801,8 +826,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
           const int rr = idx / (BN / 2), q = idx % (BN / 2);
           const int mm = m0 + rr, n = n0 + q;
           if (mm < a.M && n < a.Nc) {
-            a.C[(size_t)mm * a.ldc + n] = stage[rr * L::OUT_PITCH + q];
-            if (n == a.Nc - 1 && a.ldc > a.Nc) a.C[(size_t)mm * a.ldc + a.Nc] = make_float2(0.f, 0.f);
+            put_c(a, (size_t)mm * a.ldc + n, stage[rr * L::OUT_PITCH + q]);
+            if (n == a.Nc - 1 && a.ldc > a.Nc) put_c(a, (size_t)mm * a.ldc + a.Nc, make_float2(0.f, 0.f));
           }
         }
       }
@@ -831,8 +856,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t aa = s_base + L::OFF_A + slot * A_TILE, bb = s_base + L::OFF_B + slot * B_TILE;
 #pragma unroll
-          for (int ks = 0; ks < BK / 8; ++ks)
-            mma_tf32(acc, sdesc_sw128(aa + 32u * ks), sdesc(bb + 256u * ks), IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            if constexpr (H)
+              mma_f16(acc, sdesc_sw128(aa + 32u * ks), sdesc(bb + 256u * ks), IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+            else
+              mma_tf32(acc, sdesc_sw128(aa + 32u * ks), sdesc(bb + 256u * ks), IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+          }
           mma_commit(done0 + 8 * slot);
           any = true;
         }
@@ -864,7 +893,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
         mbar_expect_tx(bfull0 + 8 * slot, (uint32_t)B_TILE);
         bulk_g2s(s_base + L::OFF_B + slot * B_TILE, Bh + (size_t)s * (BN * BK), B_TILE, bfull0 + 8 * slot);
         mbar_expect_tx(full0 + 8 * slot, (uint32_t)A_TILE);
-        tensor_g2s_2d(s_base + L::OFF_A + slot * A_TILE, &xmap, s * BK, m0, full0 + 8 * slot);
+        tensor_g2s_2d(s_base + L::OFF_A + slot * A_TILE, &xmap, s * KE, m0, full0 + 8 * slot);
       }
     }
     // no copy may still be writing shared memory when the CTA exits
@@ -945,7 +974,53 @@ TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, 
           op.lo[blk + core_off(row, k) / 4] = lo;
         }
     }
+  // binary16 tiles (round to nearest even): K stages of 64 values, the same
+  // 128-byte rows, core matrices of 8 rows x 8 values
+  op.nks16 = (2 * kdim + 2 * BK - 1) / (2 * BK);
+  const size_t per16 = (size_t)bn * 2 * BK;
+  op.h16.assign(per16 * op.nks16 * op.ntiles, 0);
+  for (int nt = 0; nt < op.ntiles; ++nt)
+    for (int ks = 0; ks < op.nks16; ++ks) {
+      const size_t blk = ((size_t)nt * op.nks16 + ks) * per16;
+      for (int row = 0; row < bn; ++row)
+        for (int k = 0; k < 2 * BK; ++k) {
+          const int nr = nt * bn + row, kr = ks * 2 * BK + k;
+          double v = 0.0;
+          if (nr < 2 * ndim && kr < 2 * kdim) {
+            const std::complex<double> q = Q[(size_t)(kr >> 1) * ndim + (nr >> 1)];
+            const int a = kr & 1, b = nr & 1;
+            v = (a == 0) ? (b == 0 ? q.real() : q.imag()) : (b == 0 ? -q.imag() : q.real());
+          }
+          const __half hv = __float2half_rn((float)v);
+          uint16_t bits;
+          std::memcpy(&bits, &hv, 2);
+          const int off = ((row >> 3) * 8 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2;   // bytes
+          op.h16[blk + off / 2] = bits;
+        }
+    }
   return op;
+}
+
+bool tc_make_xmap16(CUtensorMap* map, const void* X, long long ldx, int M, int kdim) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  // rows of ldx binary16 pairs: the pitch (4 ldx bytes) must be a multiple of 16
+  if (!enc || ldx % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || M <= 0 || kdim <= 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)(2 * kdim), (cuuint64_t)M};
+  cuuint64_t strides[1] = {(cuuint64_t)ldx * 4};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * tc::BK), (cuuint32_t)tc::BM};
+  cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(X), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 int tc_tile_width(long long rows, int ndim, int num_sms) {
@@ -995,14 +1070,16 @@ static void tc_attributes() {
                          tc::Cfg<64, false>::SMEM_BYTES);
     cudaFuncSetAttribute(k_tc_cgemm<128, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tc::Cfg<128, false>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_tc_cgemm_ps<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<64>::SMEM_BYTES);
-    cudaFuncSetAttribute(k_tc_cgemm_ps<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<128>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm_ps<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<64>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm_ps<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<128>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm_ps<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<64>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_cgemm_ps<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<128>::SMEM_BYTES);
   });
 }
 
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
-                     int* err, cudaStream_t st, bool split, const CUtensorMap* xmap) {
+                     int* err, cudaStream_t st, bool split, const CUtensorMap* xmap, bool out_half, float oscale) {
   if (B.bn != 64 && B.bn != 128) return cudaErrorInvalidValue;
   if (mode == 1 && (MB <= 0 || ldc < MB)) return cudaErrorInvalidValue;
   tc_attributes();
@@ -1027,6 +1104,8 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
   a.escale = escale;
   a.skip = skip;
   a.err = err;
+  a.out_half = out_half ? 1 : 0;
+  a.oscale = oscale;
   // programmatic dependent launch: may start while the previous kernel in
   // the stream finishes (the kernel waits for it before touching its data)
   cudaLaunchConfig_t cfg = {};
@@ -1059,7 +1138,8 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
     // persistent: one CTA per SM walks the tiles
     cfg.gridDim = dim3((unsigned)std::min<long long>(ctas, num_sms));
     cfg.dynamicSmemBytes = B.bn == 128 ? CfgP<128>::SMEM_BYTES : CfgP<64>::SMEM_BYTES;
-    e = B.bn == 128 ? cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<128>, a, m) : cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<64>, a, m);
+    e = B.bn == 128 ? cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<128, false>, a, m)
+                    : cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<64, false>, a, m);
   } else if (B.bn == 128 && split) {
     cfg.dynamicSmemBytes = tc::Cfg<128, true>::SMEM_BYTES;
     e = cudaLaunchKernelEx(&cfg, k_tc_cgemm<128, true, false>, a, m);
@@ -1075,6 +1155,57 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
     e = tmax ? cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, false, true>, a, m)
              : cudaLaunchKernelEx(&cfg, k_tc_cgemm<64, false, false>, a, m);
   }
+  note_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t tc_hgemm(const TcDevOperand& B, const void* X, int M, void* C, long long ldc, int mode, int MB,
+                     const float2* E, int e_ld, int e_mod, const double* escale, float oscale, bool out_half,
+                     const int* skip, int* err, cudaStream_t st, const CUtensorMap* xmap) {
+  if ((B.bn != 64 && B.bn != 128) || !B.h16 || !xmap) return cudaErrorInvalidValue;
+  if (mode == 1 && (MB <= 0 || ldc < MB)) return cudaErrorInvalidValue;
+  tc_attributes();
+  TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.X = reinterpret_cast<const float*>(X);
+  a.M = M;
+  a.K2 = 2 * B.kdim;
+  a.nks = B.nks16;
+  a.Bhi = reinterpret_cast<const float*>(B.h16);
+  a.Nc = B.ndim;
+  a.ntiles = B.ntiles;
+  a.C = reinterpret_cast<float2*>(C);
+  a.ldc = ldc;
+  a.mode = mode;
+  a.MB = MB;
+  a.E = E;
+  a.e_ld = e_ld;
+  a.e_mod = e_mod > 0 ? e_mod : 1;
+  a.escale = escale;
+  a.skip = skip;
+  a.err = err;
+  a.out_half = out_half ? 1 : 0;
+  a.oscale = oscale;
+  static const int num_sms = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 0;
+    return v;
+  }();
+  const long long ctas = (long long)((M + tc::BM - 1) / tc::BM) * B.ntiles;
+  if (ctas <= 0 || ctas > 0x7fffffffLL || num_sms <= 0) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)std::min<long long>(ctas, num_sms));
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = SG_TC_PDL;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.dynamicSmemBytes = B.bn == 128 ? CfgP<128>::SMEM_BYTES : CfgP<64>::SMEM_BYTES;
+  const cudaError_t e = B.bn == 128 ? cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<128, true>, a, *xmap)
+                                    : cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<64, true>, a, *xmap);
   note_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -202,15 +202,20 @@ sg_status tc_build_operands(sg_handle* h, int bn) {
     TcOperand op = tc_make_operand(h->tc_fac[t], h->tc_dim[t], h->tc_dim[t], w);
     TcDevOperand& d = fresh[t];
     d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
-    if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size())) {
-      for (int u = 0; u <= t; ++u) { cudaFree(fresh[u].hi); cudaFree(fresh[u].lo); }
+    d.nks16 = op.nks16;
+    if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()) ||
+        upload(&d.h16, op.h16.data(), op.h16.size())) {
+      for (int u = 0; u <= t; ++u) { cudaFree(fresh[u].hi); cudaFree(fresh[u].lo); cudaFree(fresh[u].h16); }
       return fail(SG_ENOMEM, "transform operand upload");
     }
   }
-  SG_CUDA_TRY(cudaDeviceSynchronize());   // no transform of the old operands still running
+  // no transform of the old operands still running, and no captured graph
+  // left that names them
+  drop_graphs(h);
   for (int t = 0; t < 4; ++t) {
     cudaFree(h->tcB[t].hi);
     cudaFree(h->tcB[t].lo);
+    cudaFree(h->tcB[t].h16);
     h->tcB[t] = fresh[t];
   }
   return SG_OK;
@@ -228,7 +233,8 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_Q); cudaFree(h->d_Qt); cudaFree(h->d_Q32); cudaFree(h->d_Qt32);
   cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
   cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
-  for (auto& t : h->tcB) { cudaFree(t.hi); cudaFree(t.lo); }
+  for (auto& t : h->tcB) { cudaFree(t.hi); cudaFree(t.lo); cudaFree(t.h16); }
+  cudaFree(h->d_fd16s); cudaFree(h->d_fd16part);
   cudaFree(h->d_err);
   cudaFree(h->d_modemax);
   sgi_free_gmres_work(h);
@@ -413,11 +419,14 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
         if (bst != SG_OK) return bst;
         for (int which = 0; which < 2; ++which) {
           const cd shift = which == 0 ? cd(0, 0) : cd(0, -h->beta * kb * kb);
+          double lmax = 0.0;
           for (int j = 0; j < my; ++j)
             for (int i = 0; i < mx; ++i) {
               const cd v = 1.0 / (lamy[j] + lam[i] + shift);
               Linv[(size_t)j * mx + i] = make_float2((float)v.real(), (float)v.imag());
+              lmax = std::max(lmax, std::abs(v));
             }
+          h->fd16_scale[which] = lmax > 0.0 && std::isfinite(lmax) ? (float)(1.0 / lmax) : 1.0f;
           if (upload(&h->d_Linv32[which], Linv.data(), Linv.size())) return fail(SG_ENOMEM, "precond upload");
         }
         h->fd = true;
@@ -474,6 +483,18 @@ static sg_status setup_preconditioners(sg_handle* h, cudaStream_t st) {
     h->tc_xmap_ok = tc_make_xmap(&h->tc_xmap[0], t1, myp, P * mx, my) &&
                     tc_make_xmap(&h->tc_xmap[1], t2, myp, P * mx, my) &&
                     tc_make_xmap(&h->tc_xmap[2], t1, mxp, P * my, mx);
+    // the binary16 route: rows of mx or my pairs padded to a multiple of 4
+    const int mx4 = (mx + 3) & ~3, my4 = (my + 3) & ~3;
+    // (boxes of 64 values x 128 rows inside the tensors: lines of at least 32
+    // unknowns, at least 128 rows)
+    h->fd16 = h->tcB[1].h16 && mx >= 32 && my >= 32 && (long long)P * mx >= 128 && (long long)P * my >= 128 &&
+              tc_make_xmap16(&h->tc_xmap16[0], h->d_tmp, my4, P * mx, my) &&
+              tc_make_xmap16(&h->tc_xmap16[1], h->d_tmp2, my4, P * mx, my) &&
+              tc_make_xmap16(&h->tc_xmap16[2], h->d_tmp, mx4, P * my, mx);
+    if (h->fd16) {
+      SG_CUDA_TRY(cudaMalloc((void**)&h->d_fd16s, 2 * sizeof(double)));
+      SG_CUDA_TRY(cudaMalloc((void**)&h->d_fd16part, (size_t)kFd16Blocks * sizeof(double)));
+    }
   }
   int bad = 0;
   SG_CUDA_TRY(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
@@ -789,6 +810,7 @@ sg_status sg_get_info(const sg_handle* h, sg_info* info) {
     info->specialised = h->specialised;
     info->fast_diag = h->fd && h->fd_fp32 ? 1 : 0;
     info->tf32_route = h->fd ? 1 : 0;
+    info->fp16_route = h->fd16 ? 1 : 0;
     info->eig_orth_err = h->eig_orth_err;
     info->eig_kappa = h->eig_kappa;
     return SG_OK;
@@ -821,8 +843,8 @@ sg_status sg_matvec(sg_handle* h, sg_precision prec, const void* X, void* Y, voi
 sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* R, void* Z, void* stream) {
   return sgi::guarded([&]() -> sg_status {
     if (!h || !R || !Z) return fail(SG_EINVAL, "NULL handle or vector");
-    if (prec != SG_FP64 && prec != SG_FP32 && prec != SG_TF32)
-      return fail(SG_EINVAL, "sg_precond precision must be SG_FP64, SG_FP32 or SG_TF32");
+    if (prec != SG_FP64 && prec != SG_FP32 && prec != SG_TF32 && prec != SG_FP16)
+      return fail(SG_EINVAL, "sg_precond precision must be SG_FP64, SG_FP32, SG_TF32 or SG_FP16");
     cudaStream_t st = (cudaStream_t)stream;
     size_t bytes = (size_t)h->N * (prec == SG_FP64 ? sizeof(double2) : sizeof(float2));
     if (kind == SG_PREC_NONE) {
@@ -833,7 +855,7 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
       return fail(SG_EINVAL, "unknown preconditioner");
     const int which = kind == SG_PREC_MEAN ? 0 : kind == SG_PREC_CSL_MEAN ? 1 : 2;
     if (which == 2) {
-      if (prec == SG_TF32) return fail(SG_EUNSUPPORTED, "SG_TF32 has no coupled CSL route");
+      if (prec == SG_TF32 || prec == SG_FP16) return fail(SG_EUNSUPPORTED, "SG_TF32 / SG_FP16 have no coupled CSL route");
       sg_status s = ensure_csl_full(h, st);
       if (s != SG_OK) return s;
     } else if (!h->blk[which].ready) {
@@ -843,6 +865,9 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
       if (h->dim != 2 || !h->fd)
         return fail(SG_EUNSUPPORTED, "SG_TF32 needs a 2D problem with constant k_0 (the fast-diagonalisation route)");
       SG_CUDA_TRY(launch_precond_tf32(h, which, (const float2*)R, (float2*)Z, st, nullptr, nullptr));
+    } else if (prec == SG_FP16) {
+      if (!h->fd16) return fail(SG_EUNSUPPORTED, "no SG_FP16 route for this problem");
+      SG_CUDA_TRY(launch_precond_f16(h, which, (const float2*)R, (float2*)Z, st, nullptr, nullptr));
     } else if (prec == SG_FP64) {
       SG_CUDA_TRY(launch_precond<double>(h, which, (const double2*)R, (double2*)Z, st));
     } else {
@@ -852,15 +877,18 @@ sg_status sg_precond(sg_handle* h, sg_prec kind, sg_precision prec, const void* 
   });
 }
 
-sg_status sg_fd_transform(sg_handle* h, sg_prec kind, int t, const void* X, void* Y, void* stream) {
+sg_status sg_fd_transform(sg_handle* h, sg_prec kind, sg_precision prec, int t, const void* X, void* Y,
+                          void* stream) {
   return sgi::guarded([&]() -> sg_status {
     if (!h || !X || !Y) return fail(SG_EINVAL, "NULL handle or vector");
+    if (prec != SG_TF32 && prec != SG_FP16) return fail(SG_EINVAL, "precision must be SG_TF32 or SG_FP16");
+    if (prec == SG_FP16 && !h->fd16) return fail(SG_EUNSUPPORTED, "no SG_FP16 route for this problem");
     if (t < 0 || t > 3) return fail(SG_EINVAL, "transform index must be 0 .. 3");
     if (kind != SG_PREC_MEAN && kind != SG_PREC_CSL_MEAN) return fail(SG_EINVAL, "kind must be SG_PREC_MEAN or SG_PREC_CSL_MEAN");
     const int which = kind == SG_PREC_MEAN ? 0 : 1;
     if (h->dim != 2 || !h->fd || !h->blk[which].ready)
       return fail(SG_EUNSUPPORTED, "the fast-diagonalisation transforms need a 2D problem with constant k_0");
-    SG_CUDA_TRY(fd_transform(h, which, t, (const float2*)X, (float2*)Y, (cudaStream_t)stream));
+    SG_CUDA_TRY(fd_transform(h, which, t, (const float2*)X, (float2*)Y, (cudaStream_t)stream, prec == SG_FP16));
     return SG_OK;
   });
 }

@@ -108,14 +108,18 @@ struct PrecBlock {
 // real embedding of a kdim x ndim complex matrix, split hi / lo in TF32,
 // in [column tile][K stage][bn x 32 core-matrix block] order, bn = 64 or 128
 // real output columns per CTA.
+// The same factor in binary16 (h16): K stages of 64 values in 128-byte rows,
+// core matrices of 8 rows x 8 values, for the FP16 transforms.
 struct TcOperand {
-  int kdim = 0, ndim = 0, nks = 0, ntiles = 0, bn = 64;
+  int kdim = 0, ndim = 0, nks = 0, ntiles = 0, bn = 64, nks16 = 0;
   std::vector<float> hi, lo;
+  std::vector<uint16_t> h16;
 };
 struct TcDevOperand {
-  int kdim = 0, ndim = 0, nks = 0, ntiles = 0, bn = 64;
+  int kdim = 0, ndim = 0, nks = 0, ntiles = 0, bn = 64, nks16 = 0;
   float* hi = nullptr;
   float* lo = nullptr;
+  uint16_t* h16 = nullptr;
 };
 TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim, int bn);
 // Tile width (64 or 128 real columns) for a GEMM of `rows` rows and ndim
@@ -126,9 +130,22 @@ int tc_tile_width(long long rows, int ndim, int num_sms);
 // rows ldc >= MB apart); 16-byte loads of X when ldx is even; split: FP32
 // accuracy (3xTF32), else plain TF32 (one MMA per K step); optional
 // elementwise factor E[n * e_ld + m % e_mod] * (*escale).
+// out_half: C gets binary16 pairs; every output value is scaled by oscale
+// (and by *escale if given).
 cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int M, float2* C, long long ldc,
                      int mode, int MB, const float2* E, int e_ld, int e_mod, const double* escale, const int* skip,
-                     int* err, cudaStream_t st, bool split = true, const CUtensorMap* xmap = nullptr);
+                     int* err, cudaStream_t st, bool split = true, const CUtensorMap* xmap = nullptr,
+                     bool out_half = false, float oscale = 1.0f);
+// The FP16 form (persistent, kind::f16 MMAs): X binary16 pairs by tensor
+// copies through xmap (tc_make_xmap16), B's binary16 tiles, output binary16
+// pairs (out_half) or complex64, scaled by (*escale) * oscale.
+cudaError_t tc_hgemm(const TcDevOperand& B, const void* X, int M, void* C, long long ldc, int mode, int MB,
+                     const float2* E, int e_ld, int e_mod, const double* escale, float oscale, bool out_half,
+                     const int* skip, int* err, cudaStream_t st, const CUtensorMap* xmap);
+// Tensor map of M rows of kdim binary16 pairs, row pitch ldx pairs (ldx a
+// multiple of 4, X 16-byte aligned): boxes of 64 values x 128 rows in the
+// 128-byte swizzle.
+bool tc_make_xmap16(CUtensorMap* map, const void* X, long long ldx, int M, int kdim);
 // One warp waits on an mbarrier nothing arrives on, with the transform
 // kernel's bounded wait; sets *err = 1 when the wait gives up, *done = 1 at
 // the end (device ints).
@@ -179,6 +196,15 @@ struct sg_handle {
   // transforms 2-4: d_tmp, d_tmp2, d_tmp with their even row pitches)
   CUtensorMap tc_xmap[3];
   bool tc_xmap_ok = false;
+  // binary16 route of the same transforms (the solver's flexible cycles):
+  // inputs of transforms 2-4 as binary16 pairs in d_tmp / d_tmp2 with rows
+  // padded to a multiple of 4 pairs, and transform 2's output scale per block
+  // (1 / max |L^-1|, so that the scaled values stay near 1)
+  CUtensorMap tc_xmap16[3];
+  bool fd16 = false;
+  float fd16_scale[2] = {1.0f, 1.0f};
+  double* d_fd16s = nullptr;          // sg_precond(SG_FP16): 1 / ||R|| and ||R|| (device)
+  double* d_fd16part = nullptr;       // its block partial sums
   long long N = 0;
   double h = 0, beta = 0.5, kbar = 0;
   int bc[4] = {0, 0, 0, 0};
@@ -230,6 +256,7 @@ struct sg_handle {
   int tune_cgs_bpsm = 0;             // CGS2 passes: grid of this many blocks per SM
   int tune_op_occ = 0;               // persistent complex64 operator: CTAs per SM (at most its occupancy)
   int tune_tc_bn = 0;                // plain-TF32 transforms: output tile width (64 or 128)
+  int tune_tf32 = 0;                 // 1: the solver's transforms in TF32 even where the binary16 route exists
   double tune_us[3] = {0.0, 0.0, 0.0};   // measured: CGS2 step, operator, TF32 apply (microseconds)
   // host factors of the four tensor-core transforms (kept to rebuild them
   // for another tile width), their sizes and GEMM row counts
@@ -263,9 +290,22 @@ cudaError_t launch_precond(const sg_handle* h, int which, const C2<T>* R, C2<T>*
 // used by flexible GMRES); cudaErrorNotSupported without that route.
 cudaError_t launch_precond_tf32(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
                                 const int* skip, const double* in_scale);
+// The same apply with transforms 2-4 on binary16 operands (kind::f16 MMAs)
+// and binary16 intermediates: the same 11-bit significands as TF32, twice
+// the K per copied stage.  The input is taken as normalised by in_scale (the
+// solver's v_j = vscale_j V_j); without in_scale its norm is computed first.
+cudaError_t launch_precond_f16(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                               const int* skip, const double* in_scale);
+// Block partial sums of the input norm of the binary16 apply without in_scale.
+constexpr int kFd16Blocks = 1024;
+// The solver's fast apply: binary16 where available (and not switched off by
+// the tuner), else TF32.
+cudaError_t launch_precond_fast(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
+                                const int* skip, const double* in_scale);
 
 // One of the four plain-TF32 transforms of that apply on caller buffers.
-cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, float2* Y, cudaStream_t st);
+cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, float2* Y, cudaStream_t st,
+                         bool f16 = false);
 
 template <typename T>
 cudaError_t launch_precond_scratch(const sg_handle* h, int which, const C2<T>* R, C2<T>* Z, cudaStream_t st,
@@ -305,5 +345,8 @@ sg_status time_cgs_passes(sg_handle* h, sg_prec prec, int j, int reps, cudaStrea
 // Applies a CGS2 grid choice (blocks per SM, 0 = rule) to the handle and
 // its workspace, dropping graphs captured with the old grid.
 void set_cgs_blocks(sg_handle* h, int bpsm);
+// Drops every graph captured from the handle's launches (after any change of
+// its launch shapes, operands or preconditioner route).
+void drop_graphs(sg_handle* h);
 
 }  // namespace sgi

@@ -1133,7 +1133,7 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   if (flexible<T>(c, prec)) {
     Z = reinterpret_cast<C2<T>*>(w.Zb) + (size_t)j * N;
     if constexpr (sizeof(T) == sizeof(float))
-      e = launch_precond_tf32(c.h, prec == SG_PREC_MEAN ? 0 : 1, vj, Z, c.st, w.dctl, D + c.L.vscale + j);
+      e = launch_precond_fast(c.h, prec == SG_PREC_MEAN ? 0 : 1, vj, Z, c.st, w.dctl, D + c.L.vscale + j);
     if (e) return e;
   } else if (c.left) {
     // left: w = M^-1 (vscale_j A V_j) = M^-1 A v_j
@@ -1554,6 +1554,18 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
 // ------------------------------------------------------------------ launch-shape tuning support
 namespace sgi {
 
+// Drops the graphs captured from this handle's launches (the Arnoldi-step
+// chunks and the batched solves that name its workspace): they hold the
+// launch shapes and the operand addresses of the time of capture.
+void drop_graphs(sg_handle* h) {
+  GmresWork& w = h->gw;
+  cudaDeviceSynchronize();   // no replay of the old graphs still running
+  for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
+  w.graphs.clear();
+  w.graph_uses.clear();
+  if (w.uid) sgi_forget_batched_graphs(w.uid);
+}
+
 // A new CGS2 grid for the handle: the existing workspace takes it at once
 // (its partial-sum buffer is sized for the largest grid); captured graphs
 // hold the old grid and are dropped.
@@ -1563,11 +1575,7 @@ void set_cgs_blocks(sg_handle* h, int bpsm) {
   if (!w.V) return;
   const int nb = cgs_blocks(h, bpsm > 0 ? bpsm : CG_DEFAULT_BPSM);
   if (nb == w.cg_nblk) return;
-  cudaDeviceSynchronize();   // no replay of the old graphs still running
-  for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
-  w.graphs.clear();
-  w.graph_uses.clear();
-  if (w.uid) sgi_forget_batched_graphs(w.uid);
+  drop_graphs(h);
   w.cg_nblk = nb;
 }
 

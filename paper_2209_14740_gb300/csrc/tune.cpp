@@ -49,7 +49,7 @@ void fill(const sg_handle* h, sg_tune* t) {
   t->cgs_blocks_per_sm = h->tune_cgs_bpsm;
   t->op_ctas_per_sm = h->tune_op_occ;
   t->tc_tile_n = h->tune_tc_bn;
-  t->reserved = 0;
+  t->tf32_transforms = h->tune_tf32;
   t->cgs_us = h->tune_us[0];
   t->op_us = h->tune_us[1];
   t->apply_us = h->tune_us[2];
@@ -72,11 +72,15 @@ extern "C" sg_status sg_tune_set(sg_handle* h, const sg_tune* t) {
     if (t->op_ctas_per_sm < 0 || t->op_ctas_per_sm > 16) return fail(SG_EINVAL, "op_ctas_per_sm must be 0 .. 16");
     if (t->tc_tile_n != 0 && t->tc_tile_n != 64 && t->tc_tile_n != 128)
       return fail(SG_EINVAL, "tc_tile_n must be 0, 64 or 128");
+    if (t->tf32_transforms != 0 && t->tf32_transforms != 1) return fail(SG_EINVAL, "tf32_transforms must be 0 or 1");
     if (t->tc_tile_n != h->tune_tc_bn && h->fd) {
       sg_status s = tc_build_operands(h, t->tc_tile_n);
       if (s != SG_OK) return s;
     }
+    const int tf32 = h->fd16 ? t->tf32_transforms : 0;
+    if (tf32 != h->tune_tf32 || t->op_ctas_per_sm != h->tune_op_occ) drop_graphs(h);   // captured shapes
     h->tune_tc_bn = h->fd ? t->tc_tile_n : 0;
+    h->tune_tf32 = tf32;
     h->tune_op_occ = t->op_ctas_per_sm;
     set_cgs_blocks(h, t->cgs_blocks_per_sm);
     return SG_OK;
@@ -93,6 +97,7 @@ extern "C" sg_status sg_autotune(sg_handle* h, int restart, sg_tune* out, void* 
     o.prec = SG_PREC_MEAN;
     sg_status s = sgi_prepare_workspace(h, &o);
     if (s != SG_OK) return s;
+    drop_graphs(h);   // the shapes change while they are timed
     GmresWork& w = h->gw;
     const long long N = h->N;
     float2* V0 = reinterpret_cast<float2*>(w.V);
@@ -136,20 +141,35 @@ extern "C" sg_status sg_autotune(sg_handle* h, int restart, sg_tune* out, void* 
       h->tune_op_occ = choice;
       h->tune_us[1] = best;
     }
-    // 3. tile width of the plain-TF32 transforms (2D separable problems)
+    // 3. tile width and precision (binary16 where it exists, TF32) of the
+    // transforms of the cycles' preconditioner (2D separable problems); the
+    // input is scaled to unit norm as in the cycles
     h->tune_us[2] = 0.0;
     if (h->fd) {
+      double* unit = nullptr;   // a unit input scale on the device
+      const double one = 1.0;
+      SG_CUDA_TRY(cudaMalloc((void**)&unit, sizeof(double)));
+      struct Free {
+        double* p;
+        ~Free() { cudaFree(p); }
+      } free_unit{unit};
+      SG_CUDA_TRY(cudaMemcpy(unit, &one, sizeof(double), cudaMemcpyHostToDevice));
       double best = 0.0;
-      int choice = 0;
+      int choice = 0, tf32 = 0;
       for (int bn : {64, 128}) {
         s = tc_build_operands(h, bn);
         if (s != SG_OK) return s;
-        double us = 0.0;
-        s = time_us(st, TUNE_REPS, [&]() { return launch_precond_tf32(h, 0, V0, V1, st, nullptr, nullptr); }, &us);
-        if (s != SG_OK) return s;
-        if (choice == 0 || us < best) {
-          best = us;
-          choice = bn;
+        for (int use_tf32 : {0, 1}) {
+          if (!use_tf32 && !h->fd16) continue;
+          h->tune_tf32 = use_tf32;
+          double us = 0.0;
+          s = time_us(st, TUNE_REPS, [&]() { return launch_precond_fast(h, 0, V0, V1, st, nullptr, unit); }, &us);
+          if (s != SG_OK) return s;
+          if (choice == 0 || us < best) {
+            best = us;
+            choice = bn;
+            tf32 = use_tf32;
+          }
         }
       }
       if (choice != 128) {
@@ -157,6 +177,7 @@ extern "C" sg_status sg_autotune(sg_handle* h, int restart, sg_tune* out, void* 
         if (s != SG_OK) return s;
       }
       h->tune_tc_bn = choice;
+      h->tune_tf32 = tf32;
       h->tune_us[2] = best;
     }
     SG_CUDA_TRY(cudaStreamSynchronize(st));

@@ -19,7 +19,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE_PATH = os.path.join(HERE, "tune_table.json")
 KEY = ("dim", "mx", "my", "s", "r")
-CHOICES = {"cgs_blocks_per_sm": range(0, 9), "op_ctas_per_sm": range(0, 17), "tc_tile_n": (0, 64, 128)}
+CHOICES = {"cgs_blocks_per_sm": range(0, 9), "op_ctas_per_sm": range(0, 17), "tc_tile_n": (0, 64, 128),
+           "tf32_transforms": (0, 1)}
 
 _cache = None
 
@@ -36,9 +37,9 @@ def load_table(path: str = TABLE_PATH) -> dict:
         if k in out:
             raise ValueError("duplicate tuning entry %r" % (k,))
         for name, allowed in CHOICES.items():
-            if int(e[name]) not in allowed:
+            if int(e.get(name, 0)) not in allowed:
                 raise ValueError("tuning entry %r: %s = %r out of range" % (k, name, e[name]))
-        out[k] = {name: int(e[name]) for name in CHOICES}
+        out[k] = {name: int(e.get(name, 0)) for name in CHOICES}
     return out
 
 

@@ -178,3 +178,41 @@ def test_tf32_transform_bound(m, kb):
     err = np.linalg.norm(Zt - Z) / np.linalg.norm(Z)
     assert err < 5e-3, err
     assert err > 1e-5          # really the TF32 arithmetic, not FP32
+
+
+@pytest.mark.parametrize("m,kb", [(33, 10.0), (127, 30.0), (255, 40.0)])
+def test_fp16_transform_bound(m, kb):
+    """The binary16 route (transform 1 in TF32 writing binary16, transforms
+    2-4 with binary16 operands and intermediates, FP32 accumulation), with
+    its scalings (unit-norm input times sqrt(n), L^-1 times 1 / max |L^-1|,
+    both divided out at the end), emulated in numpy: within the same 5e-3 of
+    the exact apply as the TF32 form, and no binary16 value overflows."""
+    G, d = _pencil_g(m, kb)
+    lam, Q = np.linalg.eig(G)
+    Q = Q / np.sqrt(np.sum(Q * Q, axis=0))
+    Qh = Q / np.sqrt(d)[:, None]
+    Linv = 1.0 / (lam[None, :] + lam[:, None])
+    c2 = 1.0 / np.abs(Linv).max()
+
+    def h16(a):
+        a = np.asarray(a)
+        re, im = a.real.astype(np.float16), a.imag.astype(np.float16)
+        assert np.all(np.isfinite(re)) and np.all(np.isfinite(im))       # no overflow
+        return re.astype(np.float64) + 1j * im.astype(np.float64)
+
+    def gemm16(X, B):
+        return (h16(X) @ h16(B)).astype(np.complex64).astype(np.complex128)
+
+    rng = np.random.default_rng(m + 1)
+    R = (rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))).astype(np.complex64)
+    Rn = R / np.linalg.norm(R)                       # the cycles' normalised input
+    c1 = float(np.sqrt(R.size))
+    T1 = h16((_tf32_trunc(Rn).astype(np.complex128) @ _tf32_round(Qh).astype(np.complex128)) * c1)
+    T2 = h16(gemm16(T1.T, Qh) * Linv.T * c2)
+    T3 = h16(gemm16(T2, Qh.T))
+    Zh = gemm16(T3.T, Qh.T) / (c1 * c2) * np.linalg.norm(R)
+    Rd = R.astype(np.complex128)
+    Z = ((((Rd @ Qh).T @ Qh) * Linv.T) @ Qh.T).T @ Qh.T
+    err = np.linalg.norm(Zh - Z) / np.linalg.norm(Z)
+    assert err < 5e-3, err
+    assert err > 1e-5

@@ -1,0 +1,100 @@
+"""The binary16 route of the 2D fast-diagonalisation preconditioner (SG_FP16;
+transforms 2-4 with kind::f16 tensor-core MMAs and binary16 intermediates,
+transform 1 in TF32 writing binary16), on the GPU: the apply against the
+FP64 apply within the same 5e-3 as the TF32 form, the four transforms
+through sg_fd_transform, and mixed-precision GMRES with the binary16
+preconditioner in its flexible cycles against the TF32 one (same tolerance
+reached, steps within +-2, the oracle's residual)."""
+import numpy as np
+import pytest
+
+from oracle import sg
+from paper_2209_14740_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2209_14740_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.mark.parametrize("g,s,r", [(63, 3, 2), (64, 2, 3), (127, 3, 3)])
+def test_fp16_apply_against_fp64(B, g, s, r):
+    op = B.SG(inputs.helmholtz_2d(g, s, r, 20.0, 0.1), tuned=False)
+    assert op.info["fp16_route"] == 1 and op.info["tf32_route"] == 1
+    rng = np.random.default_rng(g + s)
+    x = (rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)).astype(np.complex64)
+    X = torch.from_numpy(x).to(DEV)
+    for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+        Zr = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.precond(X.to(torch.complex128), Zr, kind, B.FP64)
+        Zh = torch.empty_like(X)
+        op.precond(X, Zh, kind, B.FP16)
+        Zt = torch.empty_like(X)
+        op.precond(X, Zt, kind, B.TF32)
+        eh = float(torch.linalg.vector_norm(Zh.to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+        et = float(torch.linalg.vector_norm(Zt.to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+        assert 1e-6 < eh < 5e-3 and et < 5e-3, (kind, eh, et)
+        Xi = X.clone()
+        op.precond(Xi, Xi, kind, B.FP16)         # in place
+        assert torch.equal(Xi, Zh)
+    op.close()
+
+
+def test_fp16_transforms_compose(B):
+    """sg_fd_transform in its SG_FP16 form, t = 0 .. 3 on a unit-norm input,
+    gives the FP64 apply within 5e-3."""
+    op = B.SG(inputs.helmholtz_2d(127, 3, 2, 25.0, 0.1), tuned=False)
+    mx, my, P = op.info["mx"], op.info["my"], op.P
+    mx4, my4 = (mx + 3) // 4 * 4, (my + 3) // 4 * 4
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)
+    x /= np.linalg.norm(x)
+    X = torch.from_numpy(x.astype(np.complex64)).to(DEV)
+    # binary16 pairs are 4 bytes: float32 storage of the same size
+    T1 = torch.zeros(P * max(mx, my) * max(mx4, my4), dtype=torch.float32, device=DEV)
+    T2 = torch.zeros_like(T1)
+    Y = torch.empty_like(X)
+    op.fd_transform(0, X, T1, B.PREC_MEAN, B.FP16)
+    op.fd_transform(1, T1, T2, B.PREC_MEAN, B.FP16)
+    op.fd_transform(2, T2, T1, B.PREC_MEAN, B.FP16)
+    op.fd_transform(3, T1, Y, B.PREC_MEAN, B.FP16)
+    Zr = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+    op.precond(torch.from_numpy(x).to(DEV), Zr, B.PREC_MEAN, B.FP64)
+    err = float(torch.linalg.vector_norm(Y.to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+    assert err < 5e-3, err
+    op.close()
+
+
+@pytest.mark.parametrize("g", [96, 127])
+def test_fp16_route_in_mixed_gmres(B, g):
+    pr = inputs.helmholtz_2d(g, 3, 3, 30.0, 0.15)
+    S = sg.assemble_problem(pr)
+    b = torch.from_numpy(S.b).to(DEV)
+    its = {}
+    for tf32 in (0, 1):
+        op = B.SG(pr, tuned=False)
+        op.tune_set({"tf32_transforms": tf32})
+        x = torch.zeros_like(b)
+        info = op.gmres(b, x, restart=50, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000)
+        assert info["status"] == B.SG_OK
+        relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
+        assert relres <= 1e-9, (tf32, relres)
+        its[tf32] = info["iters"]
+        op.close()
+    assert abs(its[0] - its[1]) <= 2, its
+
+
+def test_fp16_route_absent_on_small_grids(B):
+    op = B.SG(inputs.helmholtz_2d(15, 2, 2, 9.0, 0.1), tuned=False)
+    assert op.info["fp16_route"] == 0
+    X = torch.zeros(op.N, dtype=torch.complex64, device=DEV)
+    with pytest.raises(B.SgError) as ei:
+        op.precond(X, torch.empty_like(X), B.PREC_MEAN, B.FP16)
+    assert ei.value.status == B.SG_EUNSUPPORTED
+    op.close()

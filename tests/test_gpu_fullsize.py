@@ -241,3 +241,32 @@ def test_511_tf32_apply(B, cfg511):
         op.precond(X, Zt2, kind, B.TF32)
         assert torch.equal(Zt, Zt2)
         del Zr
+
+
+def test_511_fp16_apply(B, cfg511):
+    """The binary16 route at 511 x 511, P = 84 (the complex64 cycles'
+    preconditioner where it exists): transform 1 in TF32 writing binary16,
+    transforms 2-4 with kind::f16 MMAs on binary16 operands and
+    intermediates; within the same 5e-3 of the FP64 apply, both blocks,
+    repeatable, and the input scaled to unit norm internally (a scaled input
+    gives the scaled output)."""
+    pr, op = cfg511
+    assert op.info["fp16_route"] == 1
+    g = torch.Generator(device=DEV).manual_seed(14)
+    X = torch.randn(op.N, dtype=torch.complex64, device=DEV, generator=g)
+    for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+        Zr = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.precond(X.to(torch.complex128), Zr, kind, B.FP64)
+        Zh = torch.empty_like(X)
+        op.precond(X, Zh, kind, B.FP16)
+        err = float(torch.linalg.vector_norm(Zh.to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+        print("511x511 FP16 apply kind %d: error vs FP64 apply %.2e" % (kind, err))
+        assert 1e-6 < err < 5e-3, (kind, err)
+        Zh2 = torch.empty_like(X)
+        op.precond(X, Zh2, kind, B.FP16)
+        assert torch.equal(Zh, Zh2)
+        Zs = torch.empty_like(X)
+        op.precond(X * 1e-6, Zs, kind, B.FP16)
+        errs = float(torch.linalg.vector_norm(Zs.to(torch.complex128) * 1e6 - Zr) / torch.linalg.vector_norm(Zr))
+        assert errs < 5e-3, (kind, errs)
+        del Zr

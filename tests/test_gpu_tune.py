@@ -124,3 +124,38 @@ def test_fd_transforms_compose_to_the_tf32_apply(B, g, kind):
         op.fd_transform(4, X, T1, pk)
     assert ei.value.status == B.SG_EINVAL
     op.close()
+
+
+def test_retuning_after_solves_drops_captured_graphs(B):
+    """Solves capture their Arnoldi-step chunks as graphs (on the second
+    use).  Changing the transform precision or tile width afterwards must
+    reach the next solve: the route change shows in the result's bits, and a
+    rebuilt operand (tile width) is never read through a stale graph; every
+    solve meets the oracle's residual."""
+    pr = inputs.helmholtz_2d(127, 3, 2, 25.0, 0.1)
+    S = sg.assemble_problem(pr)
+    op = B.SG(pr, tuned=False)
+    assert op.info["fp16_route"] == 1
+    b = torch.from_numpy(S.b).to(DEV)
+    kw = dict(restart=30, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000)
+
+    def solve():
+        x = torch.zeros_like(b)
+        for _ in range(3):                      # captured on the second use, replayed on the third
+            x.zero_()
+            info = op.gmres(b, x, **kw)
+        assert info["status"] == B.SG_OK
+        rr = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
+        assert rr <= 1e-9, rr
+        return x
+
+    x16 = solve()
+    op.tune_set({"tf32_transforms": 1})
+    x32 = solve()
+    assert not torch.equal(x16, x32)            # the TF32 transforms really ran
+    for width in (64, 128, 64):
+        op.tune_set({"tf32_transforms": 1, "tc_tile_n": width})
+        solve()
+    op.tune_set({"tf32_transforms": 0})
+    assert torch.equal(solve(), x16)            # back to the binary16 route, same bits
+    op.close()

@@ -57,12 +57,12 @@ MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
 # tile (SHA-256 below): a changed kernel reports null.
 MATVEC_TRAFFIC = {"sha256": "0e5a4679d2e0f084f9f73ce6af95304f6010fe7044be5c825df92d9d73acfd2d",
                   "bytes": 183150592 + 123807488}
-# DRAM bytes of one launch of the persistent plain-TF32 transform
-# (k_tc_cgemm_ps<128>, transform 2 of an apply at 511 x 511, P = 84) from the
-# ncu capture summarised under profiles/; reported while the kernel source
+# DRAM bytes of one launch of the persistent binary16 transform
+# (k_tc_cgemm_ps<128, true>, transform 2 of an apply at 511 x 511, P = 84) from
+# the ncu capture summarised under profiles/; reported while the kernel source
 # (the persistent section of k_tc_gemm.cu, SHA-256 below) is unchanged.
-TRANSFORM_TRAFFIC = {"sha256": "ab82fbc4b4b2b73105f75d5fadcbe016218966807109b71a0582de5dcf59c749",
-                     "bytes": 182176768 + 134826752}
+TRANSFORM_TRAFFIC = {"sha256": "17314e41f33bc6264a05f8d99e050307a6d6ddc102cc9323a472040d7ea71198",
+                     "bytes": 92218112 + 47893248}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -607,7 +607,7 @@ def run_ours(args):
         peak_t, peak_kind_t = load_tensor_peak(fp16=f16)
         peak_tf32, _ = load_tensor_peak(fp16=False)
         ach = flops / (t_ps * 1e-3) / 1e12
-        tr = None if f16 else transform_traffic()
+        tr = transform_traffic() if f16 else None
         top = {"kernel": ("k_tc_cgemm_ps<128, true> (persistent binary16 transform, kind::f16" if f16 else
                           "k_tc_cgemm_ps<128, false> (persistent plain-TF32 transform") +
                          " of the 2D preconditioner, 3 of the 4 launches per apply)", "bound": "tensor",

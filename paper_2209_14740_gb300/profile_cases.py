@@ -47,8 +47,9 @@ def main(argv=None):
     ap.add_argument("--r", type=int, default=3)
     ap.add_argument("--kbar", type=float, default=30.0)
     ap.add_argument("--sigma", type=float, default=0.15)
-    ap.add_argument("--prec", choices=["fp32", "fp64", "tf32"], default="fp32",
-                    help="matvec/precond precision (tf32: the plain-TF32 preconditioner, 2D only)")
+    ap.add_argument("--prec", choices=["fp32", "fp64", "tf32", "fp16"], default="fp32",
+                    help="matvec/precond precision (tf32 / fp16: the TF32 or binary16 fast-diagonalisation "
+                         "preconditioner, 2D only)")
     ap.add_argument("--mode", choices=["mixed", "fp64", "fp32"], default="mixed", help="solve precision")
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--reps", type=int, default=3)
@@ -61,7 +62,7 @@ def main(argv=None):
         op = B.SG(inputs.helmholtz_1d_c1(n_unknowns=a.g, r=a.r))
     else:
         op = B.SG(inputs.helmholtz_2d(a.g, a.s, a.r, a.kbar, a.sigma))
-    prec = {"fp32": B.FP32, "fp64": B.FP64, "tf32": B.TF32}[a.prec]
+    prec = {"fp32": B.FP32, "fp64": B.FP64, "tf32": B.TF32, "fp16": B.FP16}[a.prec]
     cdt = torch.complex128 if prec == B.FP64 else torch.complex64
     gen = torch.Generator(device=dev).manual_seed(0)
     if a.case == "solve":
@@ -81,7 +82,7 @@ def main(argv=None):
         Y = torch.empty_like(X)
         if a.case == "matvec":
             def call():
-                op.matvec(X, Y, B.FP32 if prec == B.TF32 else prec)
+                op.matvec(X, Y, B.FP32 if prec in (B.TF32, B.FP16) else prec)
         else:
             def call():
                 op.precond(X, Y, B.PREC_MEAN, prec)

@@ -554,11 +554,13 @@ __global__ void __launch_bounds__(256) k_fd16_norm_final(const double* __restric
 // ||R|| computed here) times sqrt(N) (unit-norm vectors have entries near
 // 1 / sqrt(N)); transform 2's L^-1 times 1 / max |L^-1|; transform 4 undoes
 // both (and the norm when it was computed here).
+static cudaError_t fd16_tail(const sg_handle* h, int which, float2* Z, cudaStream_t st, const int* skip,
+                             const double* s_out);
 static cudaError_t fd_apply_h(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
                               const int* skip, const double* in_scale) {
   const int mx = h->mx, my = h->my, P = h->P;
-  const int mx4 = (mx + 3) & ~3, my4 = (my + 3) & ~3;
-  const float c1 = (float)std::sqrt((double)h->N), c2 = h->fd16_scale[which];
+  const int my4 = (my + 3) & ~3;
+  const float c1 = (float)std::sqrt((double)h->N);
   const double* s_in = in_scale;
   const double* s_out = nullptr;
   cudaError_t e = cudaSuccess;
@@ -569,13 +571,22 @@ static cudaError_t fd_apply_h(const sg_handle* h, int which, const float2* R, fl
     s_in = h->d_fd16s;
     s_out = h->d_fd16s + 1;
   }
+  e = tc_cgemm(h->tcB[0], R, mx, P * my, reinterpret_cast<float2*>(h->d_tmp), my4, 1, my, nullptr, 0, 1, s_in,
+               skip, h->d_err, st, false, nullptr, true, c1);
+  return e ? e : fd16_tail(h, which, Z, st, skip, s_out);
+}
+
+// Transforms 2-4 of the binary16 apply: d_tmp (transform 1's output, scaled
+// to sqrt(N) times a unit vector) -> Z, times *s_out if given.
+static cudaError_t fd16_tail(const sg_handle* h, int which, float2* Z, cudaStream_t st, const int* skip,
+                             const double* s_out) {
+  const int mx = h->mx, my = h->my, P = h->P;
+  const int mx4 = (mx + 3) & ~3, my4 = (my + 3) & ~3;
+  const float c1 = (float)std::sqrt((double)h->N), c2 = h->fd16_scale[which];
   void* t1 = h->d_tmp;
   void* t2 = h->d_tmp2;
-  e = tc_cgemm(h->tcB[0], R, mx, P * my, reinterpret_cast<float2*>(t1), my4, 1, my, nullptr, 0, 1, s_in, skip,
-               h->d_err, st, false, nullptr, true, c1);
-  if (!e)
-    e = tc_hgemm(h->tcB[1], t1, P * mx, t2, my4, 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true, skip,
-                 h->d_err, st, &h->tc_xmap16[0]);
+  cudaError_t e = tc_hgemm(h->tcB[1], t1, P * mx, t2, my4, 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true,
+                           skip, h->d_err, st, &h->tc_xmap16[0]);
   if (!e)
     e = tc_hgemm(h->tcB[2], t2, P * mx, t1, mx4, 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, skip, h->d_err, st,
                  &h->tc_xmap16[1]);
@@ -583,6 +594,17 @@ static cudaError_t fd_apply_h(const sg_handle* h, int which, const float2* R, fl
     e = tc_hgemm(h->tcB[3], t1, P * my, Z, mx, 0, 0, nullptr, 0, 1, s_out, 1.0f / (c1 * c2), false, skip,
                  h->d_err, st, &h->tc_xmap16[2]);
   return e;
+}
+
+cudaError_t launch_precond_f16_copy(const sg_handle* h, int which, const void* X16, const CUtensorMap* xmap,
+                                    float2* Z, cudaStream_t st, const int* skip, const double* in_scale) {
+  if (h->dim != 2 || !h->fd || !h->fd16 || !h->blk[which].ready || !h->tcB[0].h16 || !X16 || !xmap || !in_scale)
+    return cudaErrorNotSupported;
+  // transform 1 as a binary16 GEMM: the copy's rows (K = mx) against Qhat_x,
+  // per-batch transposed into d_tmp as fd_apply_h's transform 1 writes it
+  const cudaError_t e = tc_hgemm(h->tcB[0], X16, h->P * h->my, h->d_tmp, (h->my + 3) & ~3, 1, h->my, nullptr, 0, 1,
+                                 in_scale, 1.0f, true, skip, h->d_err, st, xmap);
+  return e ? e : fd16_tail(h, which, Z, st, skip, nullptr);
 }
 
 cudaError_t launch_precond_f16(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,

@@ -19,6 +19,7 @@
 // Reductions: per thread in the vector precision, across warps and blocks in
 // FP64, blocks combined by the last block to finish (fixed order, so results
 // are bitwise reproducible).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,7 +65,11 @@ struct DevLayout {
   }
 };
 // sc[] slots
-enum { SC_NORMSQ = 0, SC_BNORM = 1, SC_RNORM2 = 2, SC_EST = 3, SC_TOL = 4, SC_REF = 5, SC_WORK = 6, SC_ZETA = 8 };
+enum {
+  SC_NORMSQ = 0, SC_BNORM = 1, SC_RNORM2 = 2, SC_EST = 3, SC_TOL = 4, SC_REF = 5, SC_WORK = 6, SC_ZETA = 8,
+  SC_H16 = 10,     // scale of the binary16 copy of the newest basis vector (flexible pass 1)
+  SC_H16IN = 11    // its input scale for the next binary16 transform 1 (flexible pass 2)
+};
 // ctl[] slots
 enum { CTL_DONE = 0, CTL_ITERS = 1, CTL_K = 2, CTL_FLAGS = 3, CTL_MAXIT = 4 };
 enum { FL_CONV = 1, FL_BREAK = 2, FL_NAN = 4, FL_MAXIT = 8 };
@@ -334,15 +339,24 @@ __device__ __forceinline__ bool finish_dots(int nv, const double2* red, double* 
 // step's w after one projection, whose final form is u_hat = u - sum_{i<nv-1}
 // c2prev_i V_i; the last block turns u^H w into u_hat^H w = u^H w -
 // sum_i conj(c2prev_i) d_i before forming c.
+// With sc (the binary16 route) it also sums ||w||^2 and stores in
+// sc[SC_H16] the scale of pass 2's binary16 copy of w - sum_i c_i V_i:
+// sqrt(N) / 4 over that vector's norm, which Pythagoras gives from the dots
+// (||w||^2 - sum_i vscale_i^2 |d_i|^2; taken as at least 1e-8 ||w||^2, as the
+// difference cancels when w is nearly in the span).  The copy's entries then
+// have a root mean square near 1/4, far inside the binary16 range.
 template <typename T>
 __device__ __forceinline__ void cgs_dots_body(
     const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev) {
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev,
+    double* sc) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
+  __shared__ double sm[32];
   for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
   __syncthreads();
   const long long chunk = (long long)RED_THREADS * CG_EPT;
+  T nacc = T(0);
   for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
     C2<T> wk[CG_EPT];
 #pragma unroll
@@ -350,9 +364,21 @@ __device__ __forceinline__ void cgs_dots_body(
       const long long e = base + k * RED_THREADS;
       wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
     }
+    if (sc) {
+#pragma unroll
+      for (int k = 0; k < CG_EPT; ++k) nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
+    }
     chunk_dots<T>(V, N, nv, base, wk, red, nv);
   }
-  if (finish_dots(nv, red, part, counter, vscale, d_out, c_out) && c2prev) {
+  const int G = gridDim.x;
+  if (sc) {
+    // this block's ||w||^2 in the row after the dots' 2 nv rows
+    double dv[1] = {(double)nacc};
+    block_sum<1>(dv, sm);
+    if (threadIdx.x == 0) part[(size_t)(2 * nv) * G + blockIdx.x] = dv[0];
+  }
+  if (!finish_dots(nv, red, part, counter, vscale, d_out, c_out)) return;
+  if (c2prev) {
     __syncthreads();
     if (threadIdx.x == 0) {
       const int jn = nv - 1;
@@ -369,18 +395,41 @@ __device__ __forceinline__ void cgs_dots_body(
       c_out[2 * jn + 1] = vs * vs * sy;
     }
   }
+  if (sc) {
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const double* pk = part + (size_t)(2 * nv) * G;
+      double s0 = 0.0;
+      for (int b = lane; b < G; b += 32) s0 += __ldcg(pk + b);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s0 += __shfl_down_sync(0xffffffffu, s0, o);
+      if (lane == 0) {
+        double corr = 0.0;
+        for (int i = 0; i < nv; ++i) {
+          const double vs = vscale[i];
+          corr += vs * vs * (d_out[2 * i] * d_out[2 * i] + d_out[2 * i + 1] * d_out[2 * i + 1]);
+        }
+        const double est2 = fmax(s0 - corr, 1e-8 * s0);
+        const double q = 0.25 * sqrt((double)N);
+        sc[SC_H16] = est2 > 0.0 && est2 < 1e300 ? q / sqrt(est2) : 1.0;
+      }
+    }
+  }
 }
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(
     const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev) {
-  cgs_dots_body<T>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev);
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev,
+    double* sc) {
+  cgs_dots_body<T>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev, sc);
 }
 template <>
 __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_dots<float>(
     const C2<float>* __restrict__ V, long long N, int nv, const C2<float>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev) {
-  cgs_dots_body<float>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev);
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev,
+    double* sc) {
+  cgs_dots_body<float>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev, sc);
 }
 
 __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j);
@@ -494,12 +543,25 @@ __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_update<f
 // (the basis is orthogonal, and the second-pass coefficients are tiny, so
 // the difference loses nothing) and the Givens update of column j.  The
 // vector w - sum c2_i V_i itself is formed by the next step's pass 2.
+// With a half copy (hc.p), w is also written, times pass 1's scale
+// D[sc + SC_H16], as binary16 pairs in rows of mx4 pairs (the input of the
+// next step's binary16 transform 1): element e = row mx + col goes to row
+// mx4 + col, row = e / mx by a multiply-shift (hc.mul = ceil(2^(32+s) / mx),
+// hc.shift = 32 + s, s = ceil(log2 mx): exact for e < 2^31); the last block
+// stores in D[sc + SC_H16IN] the factor that turns the copy into
+// sqrt(N) v_{j+1} (vscale_{j+1} sqrt(N) / scale), transform 1's input scale.
 // Dynamic shared memory: CG_WARPS * nv double2.
+struct HalfCopy {
+  __half2* p;
+  unsigned long long mul;
+  int shift;
+  int mx, mx4;
+};
 template <typename T>
 __device__ __forceinline__ void cgs2_second_body(
     C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
     const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* c_out, double* D, int* ctl, DevLayout L) {
+    double* c_out, double* D, int* ctl, DevLayout L, HalfCopy hc) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   __shared__ C2<T> cs1[MAXV];
@@ -514,6 +576,7 @@ __device__ __forceinline__ void cgs2_second_body(
   __syncthreads();
   C2<T>* uj = V + (size_t)j * N;
   C2<T>* w = V + (size_t)(j + 1) * N;
+  const float hs = hc.p ? (float)D[L.sc + SC_H16] : 0.0f;
   const long long chunk = (long long)RED_THREADS * CG_EPT;
   T nacc = T(0);
   for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
@@ -569,6 +632,12 @@ __device__ __forceinline__ void cgs2_second_body(
         uj[e] = uk[k];
         w[e] = wk[k];
         nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
+        if (hc.p) {
+          const unsigned long long row = ((unsigned long long)e * hc.mul) >> hc.shift;
+          const long long col = e - (long long)row * hc.mx;
+          hc.p[(size_t)row * hc.mx4 + col] =
+              __floats2half2_rn(hs * (float)wk[k].x, hs * (float)wk[k].y);
+        }
       }
     }
     // dots with the unchanged slots 0..j-1 (read-only path), and with the
@@ -640,21 +709,24 @@ __device__ __forceinline__ void cgs2_second_body(
     *counter = 0;
   }
   __syncthreads();
-  if (threadIdx.x < 32) givens_column(D, ctl, L, j);
+  if (threadIdx.x < 32) {
+    givens_column(D, ctl, L, j);
+    if (hc.p && threadIdx.x == 0) D[L.sc + SC_H16IN] = D[L.vscale + j + 1] * sqrt((double)N) / (double)hs;
+  }
 }
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(
     C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
     const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* c_out, double* D, int* ctl, DevLayout L) {
-  cgs2_second_body<T>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L);
+    double* c_out, double* D, int* ctl, DevLayout L, HalfCopy hc) {
+  cgs2_second_body<T>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L, hc);
 }
 template <>
 __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs2_second<float>(
     C2<float>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
     const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* c_out, double* D, int* ctl, DevLayout L) {
-  cgs2_second_body<float>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L);
+    double* c_out, double* D, int* ctl, DevLayout L, HalfCopy hc) {
+  cgs2_second_body<float>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L, hc);
 }
 
 // r = b - Ax (or r = b when Ax == nullptr) written in the inner precision;
@@ -1002,7 +1074,7 @@ void sgi_free_gmres_work(sg_handle* h) {
   for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
   if (w.stream) cudaStreamDestroy(w.stream);
   if (w.ev) cudaEventDestroy(w.ev);
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.Zb); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.Zb); cudaFree(w.V16); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
   cudaFree(w.dscal); cudaFree(w.dctl); cudaFree(w.part); cudaFree(w.counter);
   w = GmresWork{};
 }
@@ -1047,6 +1119,20 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
   // complex64 inner cycles on 2D problems with the fast-diagonalisation route
   // run flexible GMRES with the TF32 preconditioner: keep every z_j
   if (!e && elem_bytes == (int)sizeof(float2) && h->dim == 2 && h->fd) e = cudaMalloc(&w.Zb, (size_t)m * N * elem_bytes);
+  // and with the binary16 transforms, the newest basis vector's binary16 copy
+  // (its padding columns stay zero); the copy's row index is formed by a
+  // multiply-shift that is exact for indices below 2^31
+  const bool v16 = elem_bytes == (int)sizeof(float2) && h->dim == 2 && h->fd && h->fd16 && h->tcB[0].h16 &&
+                   N < (1ULL << 31);
+  if (!e && v16) {
+    const size_t rows = (size_t)h->P * h->my, mx4 = (size_t)((h->mx + 3) & ~3);
+    e = cudaMalloc(&w.V16, rows * mx4 * sizeof(__half2));
+    if (!e) e = cudaMemset(w.V16, 0, rows * mx4 * sizeof(__half2));
+    if (!e && !tc_make_xmap16(&w.v16map, w.V16, (long long)mx4, (int)rows, h->mx)) {
+      cudaFree(w.V16);   // no tensor map: the step keeps the complex64 transform 1
+      w.V16 = nullptr;
+    }
+  }
   if (!e) e = cudaMalloc(&w.R64, N * sizeof(double2));
   if (!e) e = cudaMalloc(&w.X64, N * sizeof(double2));
   if (!e) e = cudaMalloc(&w.B64, N * sizeof(double2));
@@ -1114,6 +1200,25 @@ static bool flexible(const Ctx& c, sg_prec prec) {
          c.h->gw.Zb != nullptr;
 }
 
+// The binary16 route's half copy of the newest basis vector (pass 2 writes
+// it, the next step's transform 1 reads it): on 2D problems with that route
+// and a complex64 workspace that holds the copy.
+bool use_half_copy(const Ctx& c) {
+  return c.h->fd16 && !c.h->tune_tf32 && c.h->gw.V16 && !c.left;
+}
+HalfCopy half_copy(const sg_handle* h) {
+  HalfCopy hc{};
+  const int mx = h->mx;
+  int sft = 0;
+  while ((1 << sft) < mx) ++sft;
+  hc.p = reinterpret_cast<__half2*>(h->gw.V16);
+  hc.mul = ((1ULL << (32 + sft)) + (unsigned long long)mx - 1) / (unsigned long long)mx;
+  hc.shift = 32 + sft;
+  hc.mx = mx;
+  hc.mx4 = (mx + 3) & ~3;
+  return hc;
+}
+
 template <typename T>
 cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j);
 
@@ -1132,8 +1237,13 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   C2<T>* Z;
   if (flexible<T>(c, prec)) {
     Z = reinterpret_cast<C2<T>*>(w.Zb) + (size_t)j * N;
-    if constexpr (sizeof(T) == sizeof(float))
-      e = launch_precond_fast(c.h, prec == SG_PREC_MEAN ? 0 : 1, vj, Z, c.st, w.dctl, D + c.L.vscale + j);
+    if constexpr (sizeof(T) == sizeof(float)) {
+      const int which = prec == SG_PREC_MEAN ? 0 : 1;
+      if (j >= 1 && use_half_copy(c))   // V_j's binary16 copy, written by step j-1's pass 2
+        e = launch_precond_f16_copy(c.h, which, w.V16, &w.v16map, Z, c.st, w.dctl, D + c.L.sc + SC_H16IN);
+      else
+        e = launch_precond_fast(c.h, which, vj, Z, c.st, w.dctl, D + c.L.vscale + j);
+    }
     if (e) return e;
   } else if (c.left) {
     // left: w = M^-1 (vscale_j A V_j) = M^-1 A v_j
@@ -1163,15 +1273,21 @@ cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j) {
     // two passes: the reorthogonalisation of slot j is folded into this
     // step's second pass (flexible GMRES lets the preconditioner take the
     // once-projected vector)
+    // the binary16 route: pass 2 also writes w as the next step's binary16
+    // input, at a scale pass 1 derives from ||w||
+    HalfCopy hc{};
+    if (sizeof(T) == sizeof(float) && use_half_copy(c)) hc = half_copy(c.h);
     k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
-                                                      D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.c2); note_launch();
+                                                      D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.c2,
+                                                      hc.p ? D + c.L.sc : nullptr); note_launch();
     k_cgs2_second<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, D + c.L.c1, D + c.L.c2, w.part, w.counter,
-                                                         D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl, c.L);
+                                                         D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl, c.L,
+                                                         hc);
     note_launch();
     return cudaGetLastError();
   }
   k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
-                                                    D + c.L.d1, D + c.L.c1, w.dctl, nullptr); note_launch();
+                                                    D + c.L.d1, D + c.L.c1, w.dctl, nullptr, nullptr); note_launch();
   k_cgs_update<T, true><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, w.counter,
                                                             D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl,
                                                             c.L, j); note_launch();

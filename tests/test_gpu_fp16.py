@@ -98,3 +98,30 @@ def test_fp16_route_absent_on_small_grids(B):
         op.precond(X, torch.empty_like(X), B.PREC_MEAN, B.FP16)
     assert ei.value.status == B.SG_EUNSUPPORTED
     op.close()
+
+
+@pytest.mark.parametrize("g,kind", [(96, "csl"), (129, "mean")])
+def test_fp16_copy_route_scale_invariant(B, g, kind):
+    """The flexible cycles' binary16 copy of each new basis vector (written by
+    the second CGS2 pass, read by the next step's binary16 transform 1) takes
+    its scale from that vector's norm: a right-hand side scaled by 2^-40 or
+    2^40 converges in the same number of steps (within 1) to the same
+    tolerance, and the result is the scaled solution."""
+    pr = inputs.helmholtz_2d(g, 3, 2, 25.0, 0.1)
+    S = sg.assemble_problem(pr)
+    prec = B.PREC_CSL_MEAN if kind == "csl" else B.PREC_MEAN
+    op = B.SG(pr, tuned=False)
+    assert op.info["fp16_route"] == 1
+    its = {}
+    for e in (0, -40, 40):
+        f = 2.0 ** e
+        b = torch.from_numpy(S.b * f).to(DEV)
+        x = torch.zeros_like(b)
+        info = op.gmres(b, x, restart=40, tol=1e-9, prec=prec, mode=B.MIXED, maxit=4000)
+        assert info["status"] == B.SG_OK, (e, info)
+        xs = x.cpu().numpy() / f
+        relres = np.linalg.norm(S.b - S.A @ xs) / np.linalg.norm(S.b)
+        assert relres <= 1e-9, (e, relres)
+        its[e] = info["iters"]
+    assert max(its.values()) - min(its.values()) <= 1, its
+    op.close()

@@ -457,8 +457,13 @@ sg_status sg_fd_transform(sg_handle* h, sg_prec kind, sg_precision prec, int t, 
  *   op_ctas_per_sm     CTAs per SM of the persistent complex64 SG operator
  *                      (1 .. 16, clamped to what fits); 0: as many as fit;
  *                      ignored by problems without that kernel;
- *   tc_tile_n          output tile width of the plain-TF32 transforms of 2D
+ *   tc_tile_n          output tile width of the tensor-core transforms of 2D
  *                      separable preconditioners (64 or 128 real columns);
+ *                      256: the binary16 transforms (SG_FP16) in the paired
+ *                      form, two CTAs of a cluster on adjacent row tiles
+ *                      sharing each B stage by multicast copies, the TF32
+ *                      ones at 128 (SG_EUNSUPPORTED without the binary16
+ *                      route or on a GPU that cannot hold such clusters);
  *                      0: the built-in rule per transform;
  *   tf32_transforms    1: the complex64 GMRES cycles apply the SG_TF32 form
  *                      of the preconditioner even where the SG_FP16 form

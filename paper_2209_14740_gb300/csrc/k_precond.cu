@@ -461,6 +461,17 @@ static cudaError_t fd_apply(const sg_handle* h, int which, const float2* R, floa
   return e;
 }
 
+// Binary16 transform t: the paired 256-column form where the handle is tuned
+// to it, else the persistent 64/128-column form.
+static cudaError_t hgemm(const sg_handle* h, int t, const void* X, int M, void* C, long long ldc, int mode, int MB,
+                         const float2* E, int e_ld, int e_mod, const double* escale, float oscale, bool out_half,
+                         const int* skip, int* err, cudaStream_t st, const CUtensorMap* xmap) {
+  if (h->tc_wide && h->tcW[t].h16)
+    return tc_hgemm_w(h->tcW[t], X, M, C, ldc, mode, MB, E, e_ld, e_mod, escale, oscale, out_half, skip, err, st,
+                      xmap);
+  return tc_hgemm(h->tcB[t], X, M, C, ldc, mode, MB, E, e_ld, e_mod, escale, oscale, out_half, skip, err, st, xmap);
+}
+
 // One plain-TF32 transform t of fd_apply (0 .. 3) on caller buffers, in the
 // layouts listed there; X by tensor copies where its row pitch allows (a map
 // encoded for X on each call), as the apply does on the handle's own buffers.
@@ -483,12 +494,12 @@ cudaError_t fd_transform(const sg_handle* h, int which, int t, const float2* X, 
     CUtensorMap map;
     if (!tc_make_xmap16(&map, X, ldx[t], rows[t], kdim[t])) return cudaErrorInvalidValue;
     if (t == 1)
-      return tc_hgemm(h->tcB[1], X, rows[1], Y, ldc[1], 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true, nullptr,
+      return hgemm(h, 1, X, rows[1], Y, ldc[1], 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true, nullptr,
                       h->d_err, st, &map);
     if (t == 2)
-      return tc_hgemm(h->tcB[2], X, rows[2], Y, ldc[2], 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, nullptr, h->d_err,
+      return hgemm(h, 2, X, rows[2], Y, ldc[2], 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, nullptr, h->d_err,
                       st, &map);
-    return tc_hgemm(h->tcB[3], X, rows[3], Y, ldc[3], 0, 0, nullptr, 0, 1, nullptr, 1.0f / (c1 * c2), false, nullptr,
+    return hgemm(h, 3, X, rows[3], Y, ldc[3], 0, 0, nullptr, 0, 1, nullptr, 1.0f / (c1 * c2), false, nullptr,
                     h->d_err, st, &map);
   }
   const int mx = h->mx, my = h->my, P = h->P;
@@ -585,13 +596,13 @@ static cudaError_t fd16_tail(const sg_handle* h, int which, float2* Z, cudaStrea
   const float c1 = (float)std::sqrt((double)h->N), c2 = h->fd16_scale[which];
   void* t1 = h->d_tmp;
   void* t2 = h->d_tmp2;
-  cudaError_t e = tc_hgemm(h->tcB[1], t1, P * mx, t2, my4, 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true,
+  cudaError_t e = hgemm(h, 1, t1, P * mx, t2, my4, 0, 0, h->d_Linv32[which], mx, mx, nullptr, c2, true,
                            skip, h->d_err, st, &h->tc_xmap16[0]);
   if (!e)
-    e = tc_hgemm(h->tcB[2], t2, P * mx, t1, mx4, 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, skip, h->d_err, st,
+    e = hgemm(h, 2, t2, P * mx, t1, mx4, 1, mx, nullptr, 0, 1, nullptr, 1.0f, true, skip, h->d_err, st,
                  &h->tc_xmap16[1]);
   if (!e)
-    e = tc_hgemm(h->tcB[3], t1, P * my, Z, mx, 0, 0, nullptr, 0, 1, s_out, 1.0f / (c1 * c2), false, skip,
+    e = hgemm(h, 3, t1, P * my, Z, mx, 0, 0, nullptr, 0, 1, s_out, 1.0f / (c1 * c2), false, skip,
                  h->d_err, st, &h->tc_xmap16[2]);
   return e;
 }
@@ -602,7 +613,7 @@ cudaError_t launch_precond_f16_copy(const sg_handle* h, int which, const void* X
     return cudaErrorNotSupported;
   // transform 1 as a binary16 GEMM: the copy's rows (K = mx) against Qhat_x,
   // per-batch transposed into d_tmp as fd_apply_h's transform 1 writes it
-  const cudaError_t e = tc_hgemm(h->tcB[0], X16, h->P * h->my, h->d_tmp, (h->my + 3) & ~3, 1, h->my, nullptr, 0, 1,
+  const cudaError_t e = hgemm(h, 0, X16, h->P * h->my, h->d_tmp, (h->my + 3) & ~3, 1, h->my, nullptr, 0, 1,
                                  in_scale, 1.0f, true, skip, h->d_err, st, xmap);
   return e ? e : fd16_tail(h, which, Z, st, skip, nullptr);
 }

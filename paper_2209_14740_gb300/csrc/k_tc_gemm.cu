@@ -910,6 +910,312 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
                  : "memory");
 }
 
+// ------------------------------------------------------------------ paired 256-column binary16 form
+// The binary16 transform of large GEMMs as a persistent kernel on clusters
+// of two CTAs.  A CTA owns 128 rows and 256 real output columns (MMAs of
+// M = 128, N = 256, K = 16); the two CTAs of a cluster take vertically
+// adjacent row tiles of the same column tile, so they need the same B stage,
+// and each copies one half of it (rows 0-127 or 128-255 of the 256 x 64
+// tile, 16 KB) into the shared memory of both with one multicast bulk copy.
+// Per CTA and stage, L2 then delivers 16 KB of X and 16 KB of B for a
+// 128 x 256 x 64 product: half the bytes per MMA of the 128-column form,
+// whose large transforms run at a fixed ~32 KB per stage and SM whatever the
+// MMA cost of the stage (TF32 or binary16), i.e. bound by the L2 -> SM
+// traffic of the re-read X and B tiles.
+// Barriers, per CTA:
+//   full[s % NS]  X (16 KB) and both B halves (2 x 16 KB) of stage s landed
+//   done[s % NS]  the MMAs of stage s completed in both CTAs (count 2: each
+//                 MMA lane commits to the barrier at this offset in both)
+//   accf[i % 2], acce[i % 2], fin  as in the 128-column persistent form
+// A producer refills slot s % NS for stage s only after done(s - NS), that is
+// after both MMA lanes consumed stage s - NS: no copy lands in a slot still
+// being read, and no barrier gets arrivals for a phase beyond the one its
+// waiter is on (the peer's copies of stage s need this CTA's commit of
+// stage s - NS, which follows this CTA's wait on full(s - NS)).  Both CTAs
+// walk the same sequence of tile pairs, so they run the same stages.  A
+// cluster barrier after the barrier set-up and another before exit keep
+// either CTA from sending into the other's shared memory outside its
+// lifetime; before the last one each producer waits for the copies into its
+// own shared memory and for both commits of its last stages.  Mode-0 output
+// is staged per warp, 32 rows x 8 complex values at a time, so that the
+// global stores are row-contiguous.
+namespace tcw {
+constexpr int BN = 256;
+constexpr int NS = 4;
+constexpr int A_TILE = tc::A_TILE;               // 128 rows x 128 bytes
+constexpr int B_TILE = BN * 128;                 // 256 rows x 64 binary16 values
+constexpr int B_HALF = B_TILE / 2;
+constexpr int OFF_A = 0;
+constexpr int OFF_B = NS * A_TILE;
+constexpr int STG_PITCH = 9;                     // float2 per staged row (8 + 1)
+constexpr int STG_WARP = 32 * STG_PITCH * 8;
+constexpr int OFF_STG = OFF_B + NS * B_TILE;
+constexpr int OFF_BAR = OFF_STG + (tc::NLOAD / 32) * STG_WARP;
+constexpr int NBAR = 2 * NS + 5;                 // full, done, accf[2], acce[2], fin
+constexpr int SMEM_BYTES = OFF_BAR + 8 * NBAR + 16 + 1024;   // + TMEM address, abort flag, alignment slack
+constexpr uint32_t TMEM_COLS = 2 * BN;
+// kind::f16: D = F32, A = B = F16, both K-major, N = 256, M = 128
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(tc::BM >> 4) << 24);
+static_assert(OFF_B % 1024 == 0 && OFF_STG % 1024 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+
+// Bulk copy global -> shared into the same offset of every CTA in mask, each
+// completing its bytes on its own mbarrier at offset bar.
+__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+      : "memory");
+}
+// Commit of this CTA's MMAs to the mbarrier at offset bar of every CTA in mask.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          bar),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+}  // namespace tcw
+
+__global__ void __launch_bounds__(tc::THREADS, 1) k_tc_hgemm_w(TcArgs a, const __grid_constant__ CUtensorMap xmap) {
+  using namespace tc;
+  constexpr int NS = tcw::NS, BN = tcw::BN;
+  constexpr uint16_t PAIR = 3;   // both CTAs of the cluster
+  extern __shared__ unsigned char smem_dyn[];
+  // (the same offsets in both CTAs: they run the same layout from the same base)
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t s_base = smem_u32(sm);
+  const uint32_t full0 = s_base + tcw::OFF_BAR, done0 = full0 + 8 * NS;
+  const uint32_t accf0 = done0 + 8 * NS, acce0 = accf0 + 16, fin = acce0 + 16;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + tcw::OFF_BAR + 8 * tcw::NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + tcw::OFF_BAR + 8 * tcw::NBAR + 8);
+  const int q = (int)tcw::cluster_rank();
+  uint32_t cid, ncl;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(ncl));
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tcw::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < NS; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(done0 + 8 * i) : "memory");
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accf0 + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acce0 + 8 * i), "n"(NLOAD / 32) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fin) : "memory");
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  tcw::cluster_sync_all();   // the peer's barriers exist before anything is sent to them
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const bool skipped = a.skip && *a.skip;
+  const int nks = a.nks;
+  const int rtiles = (a.M + BM - 1) / BM;
+  const int total = skipped ? 0 : ((rtiles + 1) / 2) * a.ntiles;   // tile pairs
+
+  if (warp < MMA_WARP) {
+    // ---------------------------------------------------------------- epilogue
+    constexpr int HALF = BN / 2;   // real columns per warp
+    const int lg = warp & 3, chalf = warp >> 2;
+    const int row = lg * 32 + lane;
+    float2* stg = reinterpret_cast<float2*>(sm + tcw::OFF_STG + warp * tcw::STG_WARP);
+    const float es = (a.escale ? (float)*a.escale : 1.0f) * a.oscale;
+    int it = 0;
+    for (int u = (int)cid; u < total; u += (int)ncl, ++it) {
+      const int b = it & 1;
+      const int ctile = u % a.ntiles, m0 = ((u / a.ntiles) * 2 + q) * BM;
+      const int m = m0 + row;
+      const bool mok = m < a.M;
+      const int nq0 = ctile * (BN / 2) + chalf * (HALF / 2);   // first complex column of this warp
+      const int mr = (mok ? m : 0) % a.e_mod;
+      // E of 16 complex columns from column n0 (zeros past Nc)
+      auto load_e = [&](float2 (&e)[16], int n0) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          e[k] = n0 + k < a.Nc ? a.E[(size_t)(n0 + k) * a.e_ld + mr] : make_float2(0.f, 0.f);
+      };
+      float2 ecur[16];
+      if (a.E) load_e(ecur, nq0);   // before the wait: the latency overlaps the MMAs
+      const bool to = !mbar_wait(accf0 + 8 * b, (uint32_t)(it >> 1) & 1u);
+      if (loader_sync_or(to || *abort_flag != 0)) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      size_t cb = 0;
+      bool pad1 = false;
+      if (a.mode == 1 && mok) {
+        const int p = m / a.MB, r = m - p * a.MB;
+        cb = ((size_t)p * a.Nc + nq0) * a.ldc + r;
+        pad1 = r == a.MB - 1 && a.ldc > a.MB;
+      }
+      const uint32_t taddr = tmem + (uint32_t)(b * BN) + ((uint32_t)(lg * 32) << 16) + (uint32_t)(chalf * HALF);
+#pragma unroll 1
+      for (int j0 = 0; j0 < HALF; j0 += 32) {
+        if (a.E && j0 > 0) load_e(ecur, nq0 + j0 / 2);   // (lands during the accumulator read)
+        uint32_t v[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+            "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+            "[%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr + (uint32_t)j0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (j0 + 32 >= HALF) {
+          // this warp's last read of the accumulator: release it to the MMA lane
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        }
+        // complex value k of this chunk, scaled (and times E)
+        auto val = [&](int k) {
+          const float2 x = make_float2(__uint_as_float(v[2 * k]), __uint_as_float(v[2 * k + 1]));
+          if (a.E) {
+            const float2 e = ecur[k];
+            return make_float2(es * (x.x * e.x - x.y * e.y), es * (x.x * e.y + x.y * e.x));
+          }
+          return make_float2(es * x.x, es * x.y);
+        };
+        const int nc0 = nq0 + j0 / 2;   // first complex column of this chunk
+        if (a.mode == 1) {
+          if (mok) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              if (nc0 + k < a.Nc) {
+                put_c(a, cb + (size_t)(j0 / 2 + k) * a.ldc, val(k));
+                if (pad1) put_c(a, cb + (size_t)(j0 / 2 + k) * a.ldc + 1, make_float2(0.f, 0.f));
+              }
+          }
+        } else {
+          // 32 rows x 8 values through the warp's staging area, then row-contiguous stores
+#pragma unroll
+          for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) stg[lane * tcw::STG_PITCH + k] = val(8 * h2 + k);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int rr = 4 * i + (lane >> 3), cc = lane & 7;
+              const int mm = m0 + lg * 32 + rr, n = nc0 + 8 * h2 + cc;
+              if (mm < a.M && n < a.Nc) {
+                put_c(a, (size_t)mm * a.ldc + n, stg[rr * tcw::STG_PITCH + cc]);
+                if (n == a.Nc - 1 && a.ldc > a.Nc) put_c(a, (size_t)mm * a.ldc + a.Nc, make_float2(0.f, 0.f));
+              }
+            }
+            __syncwarp();
+          }
+        }
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      bool any = false, stop = false;
+      int g = 0, it = 0;
+      for (int u = (int)cid; u < total && !stop; u += (int)ncl, ++it) {
+        const int b = it & 1;
+        if (it >= 2 && !mbar_wait(acce0 + 8 * b, (uint32_t)((it >> 1) - 1) & 1u)) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int s = 0; s < nks; ++s, ++g) {
+          const int slot = g % NS;
+          const uint32_t par = (uint32_t)(g / NS) & 1u;
+          if (!mbar_wait(full0 + 8 * slot, par) || *abort_flag) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t aa = s_base + tcw::OFF_A + slot * tcw::A_TILE;
+          const uint32_t bb = s_base + tcw::OFF_B + slot * tcw::B_TILE;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            mma_f16(acc, sdesc_sw128(aa + 32u * ks), sdesc(bb + 256u * ks), tcw::IDESC, (s > 0 || ks > 0) ? 1u : 0u);
+          tcw::mma_commit_mc(done0 + 8 * slot, PAIR);   // the slot is free in both CTAs once both commit
+          any = true;
+        }
+        if (!stop) mma_commit(accf0 + 8 * b);
+      }
+      // tensor memory is freed only after every MMA issued has completed
+      if (any) mma_commit(fin);
+      else mbar_arrive(fin);
+      if (!mbar_wait(fin, 0)) *abort_flag = 1;
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- X and B copies
+    int g = 0;
+    bool stop = false;
+    const unsigned char* Bt = reinterpret_cast<const unsigned char*>(a.Bhi);
+    for (int u = (int)cid; u < total && !stop; u += (int)ncl) {
+      const int ctile = u % a.ntiles, m0 = ((u / a.ntiles) * 2 + q) * BM;
+      for (int s = 0; s < nks; ++s, ++g) {
+        if (g >= NS && !mbar_wait(done0 + 8 * ((g - NS) % NS), (uint32_t)((g - NS) / NS) & 1u)) {
+          *abort_flag = 1;
+          stop = true;
+          break;
+        }
+        if (*abort_flag) {
+          stop = true;
+          break;
+        }
+        const int slot = g % NS;
+        const uint32_t fb = full0 + 8 * slot;
+        // this CTA's X (16 KB) and both B halves (its own and the peer's, 16 KB each)
+        mbar_expect_tx(fb, (uint32_t)(tcw::A_TILE + tcw::B_TILE));
+        tensor_g2s_2d(s_base + tcw::OFF_A + slot * tcw::A_TILE, &xmap, s * 2 * BK, m0, fb);
+        tcw::bulk_g2s_mc(s_base + tcw::OFF_B + slot * tcw::B_TILE + q * tcw::B_HALF,
+                         Bt + ((size_t)ctile * nks + s) * tcw::B_TILE + (size_t)q * tcw::B_HALF,
+                         (uint32_t)tcw::B_HALF, fb, PAIR);
+      }
+    }
+    // before the exit barrier: every copy into this CTA's shared memory has
+    // landed, and both MMA lanes' commits of the last stages have arrived here
+    const int t0 = g > NS ? g - NS : 0;
+    for (int t = t0; t < g; ++t)
+      if (!mbar_wait(full0 + 8 * (t % NS), (uint32_t)(t / NS) & 1u)) *abort_flag = 1;
+    if (!*abort_flag)
+      for (int t = t0; t < g; ++t)
+        if (!mbar_wait(done0 + 8 * (t % NS), (uint32_t)(t / NS) & 1u)) *abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  tcw::cluster_sync_all();
+  if (tid == 0 && *abort_flag) atomicExch(a.err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcw::TMEM_COLS)
+                 : "memory");
+}
+
 // Check of the bounded wait: one warp waits for phase 0 of a barrier that
 // nothing arrives on (count 1, no arrival, no copy), through the same
 // mbar_wait as the transform kernel.  The wait must give up after its limit
@@ -974,12 +1280,21 @@ TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, 
           op.lo[blk + core_off(row, k) / 4] = lo;
         }
     }
-  // binary16 tiles (round to nearest even): K stages of 64 values, the same
-  // 128-byte rows, core matrices of 8 rows x 8 values
+  tc_fill_h16(op, Q, bn);
+  return op;
+}
+
+// Binary16 tiles of the same factor (round to nearest even) for tile width
+// bn (64, 128 or 256): K stages of 64 values, 128-byte rows, core matrices of
+// 8 rows x 8 values.
+void tc_fill_h16(TcOperand& op, const std::vector<std::complex<double>>& Q, int bn) {
+  using namespace tc;
+  const int kdim = op.kdim, ndim = op.ndim;
   op.nks16 = (2 * kdim + 2 * BK - 1) / (2 * BK);
+  const int ntiles = (2 * ndim + bn - 1) / bn;
   const size_t per16 = (size_t)bn * 2 * BK;
-  op.h16.assign(per16 * op.nks16 * op.ntiles, 0);
-  for (int nt = 0; nt < op.ntiles; ++nt)
+  op.h16.assign(per16 * op.nks16 * ntiles, 0);
+  for (int nt = 0; nt < ntiles; ++nt)
     for (int ks = 0; ks < op.nks16; ++ks) {
       const size_t blk = ((size_t)nt * op.nks16 + ks) * per16;
       for (int row = 0; row < bn; ++row)
@@ -998,6 +1313,16 @@ TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, 
           op.h16[blk + off / 2] = bits;
         }
     }
+}
+
+TcOperand tc_make_operand16(const std::vector<std::complex<double>>& Q, int kdim, int ndim, int bn) {
+  TcOperand op;
+  op.kdim = kdim;
+  op.ndim = ndim;
+  op.bn = bn;
+  op.nks = (2 * kdim + tc::BK - 1) / tc::BK;
+  op.ntiles = (2 * ndim + bn - 1) / bn;
+  tc_fill_h16(op, Q, bn);
   return op;
 }
 
@@ -1074,6 +1399,7 @@ static void tc_attributes() {
     cudaFuncSetAttribute(k_tc_cgemm_ps<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<128>::SMEM_BYTES);
     cudaFuncSetAttribute(k_tc_cgemm_ps<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<64>::SMEM_BYTES);
     cudaFuncSetAttribute(k_tc_cgemm_ps<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CfgP<128>::SMEM_BYTES);
+    cudaFuncSetAttribute(k_tc_hgemm_w, cudaFuncAttributeMaxDynamicSharedMemorySize, tcw::SMEM_BYTES);
   });
 }
 
@@ -1206,6 +1532,83 @@ cudaError_t tc_hgemm(const TcDevOperand& B, const void* X, int M, void* C, long 
   cfg.dynamicSmemBytes = B.bn == 128 ? CfgP<128>::SMEM_BYTES : CfgP<64>::SMEM_BYTES;
   const cudaError_t e = B.bn == 128 ? cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<128, true>, a, *xmap)
                                     : cudaLaunchKernelEx(&cfg, k_tc_cgemm_ps<64, true>, a, *xmap);
+  note_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Clusters of two 320-thread CTAs with the paired kernel's shared memory
+// that the GPU holds at once (0 if the query fails).
+static int tc_wide_clusters() {
+  static const int n = [] {
+    tc_attributes();
+    cudaLaunchConfig_t qc = {};
+    qc.gridDim = dim3(2);
+    qc.blockDim = dim3(tc::THREADS);
+    qc.dynamicSmemBytes = tcw::SMEM_BYTES;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    qc.attrs = at;
+    qc.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, k_tc_hgemm_w, &qc) != cudaSuccess) {
+      cudaGetLastError();
+      c = 0;
+    }
+    return c;
+  }();
+  return n;
+}
+
+bool tc_wide_available() { return tc_wide_clusters() > 0; }
+
+cudaError_t tc_hgemm_w(const TcDevOperand& B, const void* X, int M, void* C, long long ldc, int mode, int MB,
+                       const float2* E, int e_ld, int e_mod, const double* escale, float oscale, bool out_half,
+                       const int* skip, int* err, cudaStream_t st, const CUtensorMap* xmap) {
+  if (B.bn != tcw::BN || !B.h16 || !xmap) return cudaErrorInvalidValue;
+  if (mode == 1 && (MB <= 0 || ldc < MB)) return cudaErrorInvalidValue;
+  const int ncl = tc_wide_clusters();
+  if (ncl <= 0) return cudaErrorNotSupported;
+  TcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.X = reinterpret_cast<const float*>(X);
+  a.M = M;
+  a.K2 = 2 * B.kdim;
+  a.nks = B.nks16;
+  a.Bhi = reinterpret_cast<const float*>(B.h16);
+  a.Nc = B.ndim;
+  a.ntiles = B.ntiles;
+  a.C = reinterpret_cast<float2*>(C);
+  a.ldc = ldc;
+  a.mode = mode;
+  a.MB = MB;
+  a.E = E;
+  a.e_ld = e_ld;
+  a.e_mod = e_mod > 0 ? e_mod : 1;
+  a.escale = escale;
+  a.skip = skip;
+  a.err = err;
+  a.out_half = out_half ? 1 : 0;
+  a.oscale = oscale;
+  const long long pairs = (((long long)(M + tc::BM - 1) / tc::BM + 1) / 2) * B.ntiles;
+  if (pairs <= 0 || pairs > 0x3fffffffLL) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(pairs, ncl)));
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.dynamicSmemBytes = tcw::SMEM_BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = SG_TC_PDL;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_hgemm_w, a, *xmap);
   note_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }

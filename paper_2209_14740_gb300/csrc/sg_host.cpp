@@ -194,18 +194,41 @@ namespace sgi {
 // (hi / lo TF32 parts in the MMA's core-matrix order, tile width bn or the
 // rule).  The old operands are freed only once the new ones are in place.
 sg_status tc_build_operands(sg_handle* h, int bn) {
-  if (bn != 0 && bn != 64 && bn != 128) return fail(SG_EINVAL, "transform tile width must be 64 or 128");
-  TcDevOperand fresh[4];
+  if (bn != 0 && bn != 64 && bn != 128 && bn != 256)
+    return fail(SG_EINVAL, "transform tile width must be 64, 128 or 256");
+  const bool wide = bn == 256;
+  if (wide && !tc_wide_available())
+    return fail(SG_EUNSUPPORTED, "the 256-column transforms need clusters of two CTAs, which this GPU cannot hold");
+  TcDevOperand fresh[4], freshW[4];
+  auto free_fresh = [&]() {
+    for (int u = 0; u < 4; ++u) {
+      cudaFree(fresh[u].hi); cudaFree(fresh[u].lo); cudaFree(fresh[u].h16);
+      cudaFree(freshW[u].h16);
+    }
+  };
   for (int t = 0; t < 4; ++t) {
-    if (h->tc_fac[t].empty()) return fail(SG_EUNSUPPORTED, "this problem has no tensor-core transforms");
-    const int w = bn ? bn : tc_tile_width(h->tc_rows[t], h->tc_dim[t], h->num_sms);
+    if (h->tc_fac[t].empty()) {
+      free_fresh();
+      return fail(SG_EUNSUPPORTED, "this problem has no tensor-core transforms");
+    }
+    if (wide) {
+      TcOperand ow = tc_make_operand16(h->tc_fac[t], h->tc_dim[t], h->tc_dim[t], 256);
+      TcDevOperand& d = freshW[t];
+      d.kdim = ow.kdim; d.ndim = ow.ndim; d.nks = ow.nks; d.ntiles = ow.ntiles; d.bn = ow.bn;
+      d.nks16 = ow.nks16;
+      if (upload(&d.h16, ow.h16.data(), ow.h16.size())) {
+        free_fresh();
+        return fail(SG_ENOMEM, "transform operand upload");
+      }
+    }
+    const int w = wide ? 128 : bn ? bn : tc_tile_width(h->tc_rows[t], h->tc_dim[t], h->num_sms);
     TcOperand op = tc_make_operand(h->tc_fac[t], h->tc_dim[t], h->tc_dim[t], w);
     TcDevOperand& d = fresh[t];
     d.kdim = op.kdim; d.ndim = op.ndim; d.nks = op.nks; d.ntiles = op.ntiles; d.bn = op.bn;
     d.nks16 = op.nks16;
     if (upload(&d.hi, op.hi.data(), op.hi.size()) || upload(&d.lo, op.lo.data(), op.lo.size()) ||
         upload(&d.h16, op.h16.data(), op.h16.size())) {
-      for (int u = 0; u <= t; ++u) { cudaFree(fresh[u].hi); cudaFree(fresh[u].lo); cudaFree(fresh[u].h16); }
+      free_fresh();
       return fail(SG_ENOMEM, "transform operand upload");
     }
   }
@@ -216,8 +239,11 @@ sg_status tc_build_operands(sg_handle* h, int bn) {
     cudaFree(h->tcB[t].hi);
     cudaFree(h->tcB[t].lo);
     cudaFree(h->tcB[t].h16);
+    cudaFree(h->tcW[t].h16);
     h->tcB[t] = fresh[t];
+    h->tcW[t] = freshW[t];
   }
+  h->tc_wide = wide;
   return SG_OK;
 }
 }  // namespace sgi
@@ -234,6 +260,7 @@ static void destroy_impl(sg_handle* h) {
   cudaFree(h->d_dyinv); cudaFree(h->d_dyinv32); cudaFree(h->d_tmp); cudaFree(h->d_tmp2);
   cudaFree(h->d_Qy32); cudaFree(h->d_Qyt32); cudaFree(h->d_Linv32[0]); cudaFree(h->d_Linv32[1]);
   for (auto& t : h->tcB) { cudaFree(t.hi); cudaFree(t.lo); cudaFree(t.h16); }
+  for (auto& t : h->tcW) cudaFree(t.h16);
   cudaFree(h->d_fd16s); cudaFree(h->d_fd16part);
   cudaFree(h->d_err);
   cudaFree(h->d_modemax);

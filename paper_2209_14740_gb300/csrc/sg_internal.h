@@ -122,6 +122,9 @@ struct TcDevOperand {
   uint16_t* h16 = nullptr;
 };
 TcOperand tc_make_operand(const std::vector<std::complex<double>>& Q, int kdim, int ndim, int bn);
+// Binary16 tiles only (op.h16, op.nks16) for tile width bn (64, 128 or 256).
+TcOperand tc_make_operand16(const std::vector<std::complex<double>>& Q, int kdim, int ndim, int bn);
+void tc_fill_h16(TcOperand& op, const std::vector<std::complex<double>>& Q, int bn);
 // Tile width (64 or 128 real columns) for a GEMM of `rows` rows and ndim
 // complex output columns on a GPU with num_sms SMs.
 int tc_tile_width(long long rows, int ndim, int num_sms);
@@ -142,6 +145,14 @@ cudaError_t tc_cgemm(const TcDevOperand& B, const float2* X, long long ldx, int 
 cudaError_t tc_hgemm(const TcDevOperand& B, const void* X, int M, void* C, long long ldc, int mode, int MB,
                      const float2* E, int e_ld, int e_mod, const double* escale, float oscale, bool out_half,
                      const int* skip, int* err, cudaStream_t st, const CUtensorMap* xmap);
+// The same product by the paired 256-column kernel (clusters of two CTAs on
+// adjacent row tiles sharing each B stage through multicast copies): B is a
+// 256-wide binary16 operand (tc_make_operand16 with bn = 256).  Not supported
+// when the GPU cannot hold a cluster of two such CTAs.
+cudaError_t tc_hgemm_w(const TcDevOperand& B, const void* X, int M, void* C, long long ldc, int mode, int MB,
+                       const float2* E, int e_ld, int e_mod, const double* escale, float oscale, bool out_half,
+                       const int* skip, int* err, cudaStream_t st, const CUtensorMap* xmap);
+bool tc_wide_available();
 // Tensor map of M rows of kdim binary16 pairs, row pitch ldx pairs (ldx a
 // multiple of 4, X 16-byte aligned): boxes of 64 values x 128 rows in the
 // 128-byte swizzle.
@@ -259,7 +270,10 @@ struct sg_handle {
   // launch shapes chosen by sg_autotune / sg_tune_set (0: built-in rule)
   int tune_cgs_bpsm = 0;             // CGS2 passes: grid of this many blocks per SM
   int tune_op_occ = 0;               // persistent complex64 operator: CTAs per SM (at most its occupancy)
-  int tune_tc_bn = 0;                // plain-TF32 transforms: output tile width (64 or 128)
+  int tune_tc_bn = 0;                // transforms: output tile width (64 or 128; 256: the binary16
+                                     // transforms in the paired 256-column form, the TF32 ones at 128)
+  sgi::TcDevOperand tcW[4];          // binary16 factors for the 256-column form (h16 only)
+  bool tc_wide = false;              // the binary16 transforms run the 256-column form
   int tune_tf32 = 0;                 // 1: the solver's transforms in TF32 even where the binary16 route exists
   double tune_us[3] = {0.0, 0.0, 0.0};   // measured: CGS2 step, operator, TF32 apply (microseconds)
   // host factors of the four tensor-core transforms (kept to rebuild them

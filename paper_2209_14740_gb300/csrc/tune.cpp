@@ -1,6 +1,6 @@
 // Launch-shape tuning (sg_autotune, sg_tune_get, sg_tune_set): the CGS2
 // grid, the persistent operator's CTAs per SM and the transform tile width
-// are timed on the handle's own problem with CUDA events and the fastest of
+// (64, 128, or the paired 256-column form of the binary16 transforms) are timed on the handle's own problem with CUDA events and the fastest of
 // each is kept in the handle.  The candidates change no arithmetic of the
 // operator or the transforms (every output element is formed by one thread
 // or one MMA tile whatever the shape); the CGS2 grid changes only the order
@@ -70,8 +70,10 @@ extern "C" sg_status sg_tune_set(sg_handle* h, const sg_tune* t) {
     if (!h || !t) return fail(SG_EINVAL, "NULL argument");
     if (t->cgs_blocks_per_sm < 0 || t->cgs_blocks_per_sm > 8) return fail(SG_EINVAL, "cgs_blocks_per_sm must be 0 .. 8");
     if (t->op_ctas_per_sm < 0 || t->op_ctas_per_sm > 16) return fail(SG_EINVAL, "op_ctas_per_sm must be 0 .. 16");
-    if (t->tc_tile_n != 0 && t->tc_tile_n != 64 && t->tc_tile_n != 128)
-      return fail(SG_EINVAL, "tc_tile_n must be 0, 64 or 128");
+    if (t->tc_tile_n != 0 && t->tc_tile_n != 64 && t->tc_tile_n != 128 && t->tc_tile_n != 256)
+      return fail(SG_EINVAL, "tc_tile_n must be 0, 64, 128 or 256");
+    if (t->tc_tile_n == 256 && !h->fd16)
+      return fail(SG_EUNSUPPORTED, "tc_tile_n 256 is the binary16 transforms' form; this problem has none");
     if (t->tf32_transforms != 0 && t->tf32_transforms != 1) return fail(SG_EINVAL, "tf32_transforms must be 0 or 1");
     if (t->tc_tile_n != h->tune_tc_bn && h->fd) {
       sg_status s = tc_build_operands(h, t->tc_tile_n);
@@ -155,12 +157,16 @@ extern "C" sg_status sg_autotune(sg_handle* h, int restart, sg_tune* out, void* 
       } free_unit{unit};
       SG_CUDA_TRY(cudaMemcpy(unit, &one, sizeof(double), cudaMemcpyHostToDevice));
       double best = 0.0;
-      int choice = 0, tf32 = 0;
-      for (int bn : {64, 128}) {
+      int choice = 0, tf32 = 0, last = 0;
+      for (int bn : {64, 128, 256}) {
+        // 256: the paired binary16 form (TF32 transforms stay at 128)
+        if (bn == 256 && !(h->fd16 && tc_wide_available())) continue;
         s = tc_build_operands(h, bn);
         if (s != SG_OK) return s;
+        last = bn;
         for (int use_tf32 : {0, 1}) {
           if (!use_tf32 && !h->fd16) continue;
+          if (use_tf32 && bn == 256) continue;
           h->tune_tf32 = use_tf32;
           double us = 0.0;
           s = time_us(st, TUNE_REPS, [&]() { return launch_precond_fast(h, 0, V0, V1, st, nullptr, unit); }, &us);
@@ -172,7 +178,7 @@ extern "C" sg_status sg_autotune(sg_handle* h, int restart, sg_tune* out, void* 
           }
         }
       }
-      if (choice != 128) {
+      if (choice != last) {
         s = tc_build_operands(h, choice);
         if (s != SG_OK) return s;
       }

@@ -19,7 +19,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE_PATH = os.path.join(HERE, "tune_table.json")
 KEY = ("dim", "mx", "my", "s", "r")
-CHOICES = {"cgs_blocks_per_sm": range(0, 9), "op_ctas_per_sm": range(0, 17), "tc_tile_n": (0, 64, 128),
+CHOICES = {"cgs_blocks_per_sm": range(0, 9), "op_ctas_per_sm": range(0, 17), "tc_tile_n": (0, 64, 128, 256),
            "tf32_transforms": (0, 1)}
 
 _cache = None

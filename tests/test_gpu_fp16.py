@@ -125,3 +125,64 @@ def test_fp16_copy_route_scale_invariant(B, g, kind):
         its[e] = info["iters"]
     assert max(its.values()) - min(its.values()) <= 1, its
     op.close()
+
+
+@pytest.mark.parametrize("g,s,r", [(63, 3, 2), (127, 3, 3), (200, 2, 3)])
+def test_paired_256_form_apply(B, g, s, r):
+    """The binary16 transforms in the paired 256-column form (tc_tile_n 256:
+    clusters of two CTAs on adjacent row tiles, each B stage shared by
+    multicast copies) give the 128-column form's apply to FP32 rounding and
+    the FP64 apply within 5e-3; 63^2 with P = 10 has an odd number of row
+    tiles (the last pair's second CTA works on rows past the end) and a
+    single, mostly empty column tile."""
+    op = B.SG(inputs.helmholtz_2d(g, s, r, 20.0, 0.1), tuned=False)
+    assert op.info["fp16_route"] == 1
+    rng = np.random.default_rng(g * 7 + r)
+    x = (rng.standard_normal(op.N) + 1j * rng.standard_normal(op.N)).astype(np.complex64)
+    X = torch.from_numpy(x).to(DEV)
+    for kind in (B.PREC_MEAN, B.PREC_CSL_MEAN):
+        Zr = torch.empty(op.N, dtype=torch.complex128, device=DEV)
+        op.precond(X.to(torch.complex128), Zr, kind, B.FP64)
+        out = {}
+        for tn in (128, 256):
+            op.tune_set({"tc_tile_n": tn})
+            assert op.tune_get()["tc_tile_n"] == tn
+            Z = torch.empty_like(X)
+            op.precond(X, Z, kind, B.FP16)
+            out[tn] = Z
+        d = float(torch.linalg.vector_norm(out[256] - out[128]) / torch.linalg.vector_norm(out[128]))
+        assert d <= 1e-6, (kind, d)
+        e = float(torch.linalg.vector_norm(out[256].to(torch.complex128) - Zr) / torch.linalg.vector_norm(Zr))
+        assert e < 5e-3, (kind, e)
+    op.close()
+
+
+def test_paired_256_form_in_mixed_gmres(B):
+    """Mixed GMRES with the paired form in its flexible cycles (transform 1
+    from the binary16 copy of each new basis vector included) reaches the
+    tolerance in the 128-column form's number of steps (within 1), with the
+    oracle's residual."""
+    pr = inputs.helmholtz_2d(127, 3, 3, 30.0, 0.15)
+    S = sg.assemble_problem(pr)
+    b = torch.from_numpy(S.b).to(DEV)
+    its = {}
+    for tn in (128, 256):
+        op = B.SG(pr, tuned=False)
+        op.tune_set({"tc_tile_n": tn, "tf32_transforms": 0})
+        x = torch.zeros_like(b)
+        info = op.gmres(b, x, restart=50, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000)
+        assert info["status"] == B.SG_OK
+        relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
+        assert relres <= 1e-9, (tn, relres)
+        its[tn] = info["iters"]
+        op.close()
+    assert abs(its[256] - its[128]) <= 1, its
+
+
+def test_paired_256_form_refused_without_fp16_route(B):
+    op = B.SG(inputs.helmholtz_2d(15, 2, 2, 9.0, 0.1), tuned=False)
+    assert op.info["fp16_route"] == 0
+    with pytest.raises(B.SgError) as ei:
+        op.tune_set({"tc_tile_n": 256})
+    assert ei.value.status == B.SG_EUNSUPPORTED
+    op.close()

@@ -475,7 +475,9 @@ sg_status sg_fd_transform(sg_handle* h, sg_prec kind, sg_precision prec, int t, 
  * preconditioner within its ~2e-3 accuracy (the flexible cycles absorb it).
  * The *_us fields are filled by sg_autotune: measured times of one step's
  * CGS2 passes at step restart / 2, one complex64 operator application and
- * one preconditioner apply of the cycles' form (0 where not timed). */
+ * one preconditioner apply of the cycles' form, as an Arnoldi step after
+ * the first runs it (binary16 from the workspace's binary16 copy of the
+ * basis vector where there is one; 0 where not timed). */
 typedef struct {
   int cgs_blocks_per_sm;
   int op_ctas_per_sm;

@@ -939,9 +939,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_tc_cgemm_ps(TcArgs a, const 
 // own shared memory and for both commits of its last stages.  Mode-0 output
 // is staged per warp, 32 rows x 8 complex values at a time, so that the
 // global stores are row-contiguous.
+#ifndef SG_TC_W_STAGES
+#define SG_TC_W_STAGES 4
+#endif
 namespace tcw {
 constexpr int BN = 256;
-constexpr int NS = 4;
+constexpr int NS = SG_TC_W_STAGES;
 constexpr int A_TILE = tc::A_TILE;               // 128 rows x 128 bytes
 constexpr int B_TILE = BN * 128;                 // 256 rows x 64 binary16 values
 constexpr int B_HALF = B_TILE / 2;

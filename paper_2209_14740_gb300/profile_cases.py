@@ -54,6 +54,8 @@ def main(argv=None):
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--inner-tol", type=float, default=0.0, help="mixed solve: inner reduction per refinement")
+    ap.add_argument("--tile-n", type=int, default=-1,
+                    help="transform tile width to set (64, 128, 256; 0: built-in rule); default: as tuned")
     a = ap.parse_args(argv)
 
     B.load()
@@ -62,6 +64,10 @@ def main(argv=None):
         op = B.SG(inputs.helmholtz_1d_c1(n_unknowns=a.g, r=a.r))
     else:
         op = B.SG(inputs.helmholtz_2d(a.g, a.s, a.r, a.kbar, a.sigma))
+    if a.tile_n >= 0:
+        t = op.tune_get()
+        t["tc_tile_n"] = a.tile_n
+        op.tune_set(t)
     prec = {"fp32": B.FP32, "fp64": B.FP64, "tf32": B.TF32, "fp16": B.FP16}[a.prec]
     cdt = torch.complex128 if prec == B.FP64 else torch.complex64
     gen = torch.Generator(device=dev).manual_seed(0)

@@ -19,7 +19,7 @@ def test_committed_table_is_valid_and_covers_the_workloads():
     assert len(tab) == len(doc["entries"]) >= 3
     for e in doc["entries"]:
         assert e["cgs_us"] > 0 and e["op_us"] > 0
-        assert (e["apply_us"] > 0) == (e["tc_tile_n"] in (64, 128))
+        assert (e["apply_us"] > 0) == (e["tc_tile_n"] in (64, 128, 256))
     # the headline, the 127^2 and the 1D workloads have entries
     assert tune_table.lookup(2, 511, 511, 6, 3) is not None
     assert tune_table.lookup(2, 127, 127, 3, 3) is not None

@@ -57,12 +57,18 @@ MATVEC_WORKLOAD = "helmholtz_2d_511x511_s6_deg3 (P=84, 21,934,164 unknowns)"
 # tile (SHA-256 below): a changed kernel reports null.
 MATVEC_TRAFFIC = {"sha256": "0e5a4679d2e0f084f9f73ce6af95304f6010fe7044be5c825df92d9d73acfd2d",
                   "bytes": 183150592 + 123807488}
-# DRAM bytes of one launch of the persistent binary16 transform
-# (k_tc_cgemm_ps<128, true>, transform 2 of an apply at 511 x 511, P = 84) from
-# the ncu capture summarised under profiles/; reported while the kernel source
-# (the persistent section of k_tc_gemm.cu, SHA-256 below) is unchanged.
-TRANSFORM_TRAFFIC = {"sha256": "17314e41f33bc6264a05f8d99e050307a6d6ddc102cc9323a472040d7ea71198",
-                     "bytes": 92218112 + 47893248}
+# DRAM bytes of one launch of the binary16 transform (transform 2 of an apply
+# at 511 x 511, P = 84) from the ncu captures summarised under profiles/: the
+# persistent k_tc_cgemm_ps<128, true> ("ps") and the paired 256-column
+# k_tc_hgemm_w ("wide"); each reported while its kernel source (the section
+# of k_tc_gemm.cu between the markers, SHA-256 below) is unchanged.
+TRANSFORM_TRAFFIC = {
+    "ps": {"begin": "template <int BN>\nstruct CfgP", "end": "// ------------------------------------------------------------------ paired 256-column",
+           "sha256": "17314e41f33bc6264a05f8d99e050307a6d6ddc102cc9323a472040d7ea71198", "bytes": 92218112 + 47893248},
+    "wide": {"begin": "// ------------------------------------------------------------------ paired 256-column",
+             "end": "// Check of the bounded wait",
+             "sha256": "1c3a2958e35b2ae42c1747348c4c3e41e19dee986912c16e3e35e11f04f0d9ed", "bytes": 92444160 + 47176192},
+}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -99,15 +105,20 @@ def matvec_traffic():
     return MATVEC_TRAFFIC["bytes"] if digest == MATVEC_TRAFFIC["sha256"] else None
 
 
-def transform_traffic():
+def transform_section_sha(kind):
     import hashlib
+    t = TRANSFORM_TRAFFIC[kind]
     src = open(os.path.join(ROOT, "paper_2209_14740_gb300", "csrc", "k_tc_gemm.cu")).read()
-    i = src.find("template <int BN>\nstruct CfgP")
-    j = src.find("// Check of the bounded wait")
+    i = src.find(t["begin"])
+    j = src.find(t["end"], i + 1)
     if i < 0 or j < 0:
         return None
-    digest = hashlib.sha256(src[i:j].encode()).hexdigest()
-    return TRANSFORM_TRAFFIC["bytes"] if digest == TRANSFORM_TRAFFIC["sha256"] else None
+    return hashlib.sha256(src[i:j].encode()).hexdigest()
+
+
+def transform_traffic(kind):
+    t = TRANSFORM_TRAFFIC[kind]
+    return t["bytes"] if t["sha256"] and transform_section_sha(kind) == t["sha256"] else None
 
 
 def load_peaks():
@@ -566,14 +577,17 @@ def run_ours(args):
     # ---------------------------------------------------------------- dominant kernel of the step
     # The preconditioner apply of the solve's complex64 cycles is four
     # launches of the tensor-core transform kernel, complex GEMMs of (P my) x
-    # mx by mx x mx (x direction) and (P mx) x my by my x my (y direction):
-    # the first reads the odd-pitch complex64 input with the loader warps
-    # (k_tc_cgemm, TF32), the other three take X by tensor copies in the
-    # persistent form (k_tc_cgemm_ps: binary16 operands where the binary16
-    # route exists and the tuning keeps it, else TF32) -- the step's dominant
-    # kernel.  It is timed alone through sg_fd_transform (transform 2, the
-    # same launch as inside the apply), 20 launches with CUDA events on the
-    # solve's stream; the whole apply and transform 1 beside it.
+    # mx by mx x mx (x direction) and (P mx) x my by my x my (y direction).
+    # On the binary16 route every Arnoldi step after the first of a cycle
+    # runs all four as binary16 GEMMs by tensor copies (transform 1 from the
+    # binary16 copy of the basis vector that the second CGS2 pass writes):
+    # the paired 256-column kernel k_tc_hgemm_w where the tuning selects it,
+    # else the persistent k_tc_cgemm_ps; the first step of a cycle (and
+    # sg_precond) runs transform 1 in TF32 from the complex64 vector.  The
+    # dominant kernel is timed alone through sg_fd_transform (transform 2,
+    # the same launch as inside the apply), 20 launches with CUDA events on
+    # the solve's stream; transforms 3 and 4, the whole apply and the TF32
+    # transform 1 beside it.
     top = None
     if info_h.get("tf32_route"):
         mx, my = info_h["mx"], info_h["my"]
@@ -601,23 +615,39 @@ def run_ours(args):
             op.fd_transform(1, T1, T2, B.PREC_MEAN, form)
             op.fd_transform(0, T1, T2, B.PREC_MEAN, form)
         t_ps = event_ms(torch, stream, lambda: op.fd_transform(1, T1, T2, B.PREC_MEAN, form), reps)
+        t_t3 = event_ms(torch, stream, lambda: op.fd_transform(2, T2, T1, B.PREC_MEAN, form), reps)
+        Yp = torch.empty(N, dtype=torch.complex64, device=dev)
+        t_t4 = event_ms(torch, stream, lambda: op.fd_transform(3, T1, Yp, B.PREC_MEAN, form), reps)
+        del Yp
         t_t1 = event_ms(torch, stream, lambda: op.fd_transform(0, T1, T2, B.PREC_MEAN, form), reps)
         del T1, T2
         flops = 8.0 * P * mx * my * my           # transform 2: (P mx) x my by my x my, complex
         peak_t, peak_kind_t = load_tensor_peak(fp16=f16)
         peak_tf32, _ = load_tensor_peak(fp16=False)
         ach = flops / (t_ps * 1e-3) / 1e12
-        tr = transform_traffic() if f16 else None
-        top = {"kernel": ("k_tc_cgemm_ps<128, true> (persistent binary16 transform, kind::f16" if f16 else
-                          "k_tc_cgemm_ps<128, false> (persistent plain-TF32 transform") +
-                         " of the 2D preconditioner, 3 of the 4 launches per apply)", "bound": "tensor",
+        wide = f16 and op.tune_get().get("tc_tile_n") == 256
+        tr = transform_traffic("wide" if wide else "ps") if f16 else None
+        if wide:
+            kname = ("k_tc_hgemm_w (paired 256-column binary16 transform, kind::f16, clusters of two CTAs "
+                     "sharing B stages by multicast copies; all 4 launches of the apply in the cycles' steps "
+                     "after the first, 3 of 4 in the first)")
+            tsrc = "ncu capture of this kernel source (profiles/tc_hgemm_w_511x511_s6_deg3.md)"
+        elif f16:
+            kname = ("k_tc_cgemm_ps<%d, true> (persistent binary16 transform, kind::f16; all 4 launches of the "
+                     "apply in the cycles' steps after the first, 3 of 4 in the first)" % op.tune_get().get("tc_tile_n"))
+            tsrc = "ncu capture of this kernel source (profiles/tc_hgemm_ps_511x511_s6_deg3.md)"
+        else:
+            kname = "k_tc_cgemm_ps (persistent plain-TF32 transform, 3 of the 4 launches per apply)"
+            tsrc = None
+        top = {"kernel": kname, "bound": "tensor",
                "achieved": ach, "peak": peak_t, "unit": "TFLOP/s", "frac": ach / peak_t, "traffic": tr,
-               "traffic_source": "ncu capture of this kernel source (profiles/tc_cgemm_ps_511x511_s6_deg3.md)"
-               if tr else None,
+               "traffic_source": tsrc if tr else None,
                "peak_kind": peak_kind_t, "us_per_launch": 1000.0 * t_ps, "flops_per_launch": flops,
                "units": "8 P m^3 real flop per launch (complex GEMM of (P m) x m by m x m; m = 511, P = 84)",
-               "transform1_us": 1000.0 * t_t1,
-               "transform1_frac_tf32": flops / (t_t1 * 1e-3) / 1e12 / peak_tf32,
+               "transform3_us": 1000.0 * t_t3, "transform4_us": 1000.0 * t_t4,
+               "frac_mean_of_transforms_2_to_4": flops / (statistics.mean([t_ps, t_t3, t_t4]) * 1e-3) / 1e12 / peak_t,
+               "transform1_complex64_input_us": 1000.0 * t_t1,
+               "transform1_complex64_input_frac_tf32": flops / (t_t1 * 1e-3) / 1e12 / peak_tf32,
                "apply_ms": t_apply}
 
     # ---------------------------------------------------------------- end to end with host buffers

@@ -16,7 +16,8 @@ Beside it the line reports: the plain FP64 GPU GMRES(30) on the same system
 (`fp64`, with the FP64 kernels against the measured FP64 FMA rate), the error
 of every mixed result against an FP64 GPU solve to 1e-12 (`error`), the
 end-to-end number through the C ABI with host buffers (`e2e`), the roofline
-of the dominant kernel (`roofline`), the SG matvec bandwidth (`matvec`), the
+of the dominant kernel (`roofline`: CGS2 pass 2, HBM) and of the tensor-core
+transform (`roofline_tensor`), the SG matvec bandwidth (`matvec`), the
 127 x 127 workload (`cfg2_127`), the 1D workload, the batched and learned
 warm-start legs, clocks sampled during the timed region, and the CPU oracle
 (`cpu_baseline`) on a bounded sample.
@@ -69,6 +70,17 @@ TRANSFORM_TRAFFIC = {
              "end": "// Check of the bounded wait",
              "sha256": "1c3a2958e35b2ae42c1747348c4c3e41e19dee986912c16e3e35e11f04f0d9ed", "bytes": 92444160 + 47176192},
 }
+# Arnoldi step of the CGS2 passes timed for the roofline (the mean step index
+# of the 511^2 solve's 39 steps is 9.3)
+CGS2_STEP = 10
+# DRAM bytes of one launch of CGS2 pass 2 (k_cgs2_second<float>, flexible form
+# with the binary16 copy, step 10) at 255^2, P = 84 (N_255 unknowns), from the
+# ncu capture summarised under profiles/, scaled to N unknowns (every term of
+# the pass's traffic is a multiple of N); reported while the pass's source (the
+# section of solver.cu between the markers, SHA-256 below) is unchanged.
+CGS2_TRAFFIC = {"begin": "// Two-pass form, pass 2 (flexible cycles)", "end": "// r = b - Ax (or r = b when Ax",
+                "sha256": "5fa2f8270ce484fa506ac992b24bcecc215091967a5baa854aeadf15196accfd",
+                "bytes": 526924288 + 93886208, "n": 255 * 255 * 84}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -119,6 +131,23 @@ def transform_section_sha(kind):
 def transform_traffic(kind):
     t = TRANSFORM_TRAFFIC[kind]
     return t["bytes"] if t["sha256"] and transform_section_sha(kind) == t["sha256"] else None
+
+
+def cgs2_section_sha():
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2209_14740_gb300", "csrc", "solver.cu")).read()
+    i = src.find(CGS2_TRAFFIC["begin"])
+    j = src.find(CGS2_TRAFFIC["end"], i + 1)
+    if i < 0 or j < 0:
+        return None
+    return hashlib.sha256(src[i:j].encode()).hexdigest()
+
+
+def cgs2_traffic(n):
+    t = CGS2_TRAFFIC
+    if not t["sha256"] or not t["bytes"] or cgs2_section_sha() != t["sha256"]:
+        return None
+    return t["bytes"] * n / t["n"]
 
 
 def load_peaks():
@@ -589,6 +618,7 @@ def run_ours(args):
     # the solve's stream; transforms 3 and 4, the whole apply and the TF32
     # transform 1 beside it.
     top = None
+    cgs = None
     if info_h.get("tf32_route"):
         mx, my = info_h["mx"], info_h["my"]
         f16 = bool(info_h.get("fp16_route")) and not op.tune_get().get("tf32_transforms")
@@ -649,6 +679,37 @@ def run_ours(args):
                "transform1_complex64_input_us": 1000.0 * t_t1,
                "transform1_complex64_input_frac_tf32": flops / (t_t1 * 1e-3) / 1e12 / peak_tf32,
                "apply_ms": t_apply}
+        # The CGS2 passes of one Arnoldi step of the flexible cycles, the
+        # step's largest kernels (pass 2 the largest share of the solve):
+        # step j = CGS2_STEP on a zeroed workspace through sg_cgs2_pass, 20
+        # launches each with CUDA events on the solve's stream (each preceded
+        # by the pass's 64-byte clear of the done flag).  Algorithmic bytes:
+        # pass 1 reads V_0..V_j and w; pass 2 reads V_0..V_{j-1}, slot j and
+        # w, writes slots j and j+1 and, on the binary16 route, the binary16
+        # copy of slot j+1.
+        jc = CGS2_STEP
+        op.cgs2_pass(jc, 0, restart=solve["restart"])
+        for _ in range(3):
+            op.cgs2_pass(jc, 1)
+            op.cgs2_pass(jc, 2)
+        t_p1 = event_ms(torch, stream, lambda: op.cgs2_pass(jc, 1), reps)
+        t_p2 = event_ms(torch, stream, lambda: op.cgs2_pass(jc, 2), reps)
+        b_p1 = (jc + 2) * N * 8
+        b_p2 = (jc + 4) * N * 8 + (N * 4 if f16 else 0)
+        hbm_peak, hbm_kind = load_peaks()
+        tr2 = cgs2_traffic(N) if f16 else None
+        cgs = {"kernel": "k_cgs2_second<float> (CGS2 pass 2 of a flexible complex64 Arnoldi step, j = %d: "
+                         "projection update of slots j and j+1%s, ||w||^2, Givens column)"
+                         % (jc, ", binary16 copy of slot j+1" if f16 else ""),
+               "bound": "hbm", "achieved": b_p2 / (t_p2 * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+               "frac": b_p2 / (t_p2 * 1e-3) / 1e9 / hbm_peak, "traffic": tr2,
+               "traffic_source": ("ncu capture of this kernel source at 255^2 (P = 84), step %d, scaled by "
+                                  "the unknowns (profiles/cgs2_step10_255x255_s6_deg3.md)" % jc) if tr2 else None,
+               "peak_kind": hbm_kind, "us_per_launch": 1000.0 * t_p2, "bytes_per_launch": b_p2,
+               "units": "(j + 4) N 8 B + N 4 B (binary16 copy) per launch, j = %d, N = %d" % (jc, N),
+               "pass1": {"kernel": "k_cgs_dots<float>", "us_per_launch": 1000.0 * t_p1, "bytes_per_launch": b_p1,
+                         "gbs": b_p1 / (t_p1 * 1e-3) / 1e9, "frac": b_p1 / (t_p1 * 1e-3) / 1e9 / hbm_peak},
+               "both_passes_model_frac": 2 * (jc + 1) * N * 8 / ((t_p1 + t_p2) * 1e-3) / 1e9 / hbm_peak}
 
     # ---------------------------------------------------------------- end to end with host buffers
     bh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
@@ -770,7 +831,13 @@ def run_ours(args):
         "clocks": clocks,
         "tuning": tuning,
     }
-    if top:
+    # the dominant kernel of the step by share of the solve's kernel time is
+    # CGS2 pass 2 (HBM); the tensor-core transform's roofline beside it
+    if cgs:
+        line["roofline"] = cgs
+        if top:
+            line["roofline_tensor"] = top
+    elif top:
         line["roofline"] = top
     if mv:
         line["matvec"] = mv

@@ -30,7 +30,7 @@ EXPORTED = ["sg_assemble", "sg_destroy", "sg_get_info", "sg_rhs", "sg_matvec", "
             "sg_mlp_forward", "sg_mlp_loss_grad", "sg_mlp_train", "sg_cgemm_hn", "sg_cgemm_nn",
             "sg_selftest_wait_timeout", "sg_alu_peak", "sg_stationary", "sg_statistics",
             "sg_warmstart_create", "sg_warmstart_destroy", "sg_warmstart_predict", "sg_autotune", "sg_tune_get",
-            "sg_tune_set", "sg_fd_transform"]
+            "sg_tune_set", "sg_fd_transform", "sg_cgs2_pass"]
 NOALLOC_MAX_N = 524288   # SG_NOALLOC_MAX_N in include/sg.h
 
 
@@ -147,6 +147,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.sg_alu_peak.restype = i
     lib.sg_fd_transform.argtypes = [vp, i, i, i, vp, vp, vp]
     lib.sg_fd_transform.restype = i
+    lib.sg_cgs2_pass.argtypes = [vp, i, i, i, vp]
+    lib.sg_cgs2_pass.restype = i
     lib.sg_autotune.argtypes = [vp, i, C.POINTER(SgTune), vp]
     lib.sg_autotune.restype = i
     lib.sg_tune_get.argtypes = [vp, C.POINTER(SgTune)]
@@ -335,6 +337,11 @@ class SG:
         """sg_fd_transform: transform t (0 .. 3) of the fast diagonalisation
         (SG_TF32 or SG_FP16 form), X -> Y (device tensors, layouts in sg.h)."""
         _check(load().sg_fd_transform(self.h, kind, prec, t, _ptr(X), _ptr(Y), _stream(stream)))
+
+    def cgs2_pass(self, j, pass_, restart=30, stream=None):
+        """sg_cgs2_pass: pass 0 prepares the workspace, 1 / 2 launch that CGS2
+        pass of Arnoldi step j of the flexible complex64 cycles."""
+        _check(load().sg_cgs2_pass(self.h, restart, j, pass_, _stream(stream)))
 
     def autotune(self, restart=30, stream=None) -> dict:
         """sg_autotune: time the candidate launch shapes on this problem and

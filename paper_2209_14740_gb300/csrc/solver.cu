@@ -1220,7 +1220,7 @@ HalfCopy half_copy(const sg_handle* h) {
 }
 
 template <typename T>
-cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j);
+cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j, int only = 0);
 
 // One Arnoldi step j with CGS2 on the inner-precision basis.
 template <typename T>
@@ -1258,9 +1258,10 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   return cgs_passes<T>(c, prec, j);
 }
 
-// The CGS2 passes of Arnoldi step j (w = V_{j+1} against V_0 .. V_j).
+// The CGS2 passes of Arnoldi step j (w = V_{j+1} against V_0 .. V_j); only =
+// 1 or 2 launches just that pass of the flexible two-pass form (timing).
 template <typename T>
-cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j) {
+cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j, int only) {
   GmresWork& w = c.h->gw;
   const long long N = c.h->N;
   C2<T>* V = reinterpret_cast<C2<T>*>(w.V);
@@ -1277,15 +1278,20 @@ cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j) {
     // input, at a scale pass 1 derives from ||w||
     HalfCopy hc{};
     if (sizeof(T) == sizeof(float) && use_half_copy(c)) hc = half_copy(c.h);
-    k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
-                                                      D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.c2,
-                                                      hc.p ? D + c.L.sc : nullptr); note_launch();
-    k_cgs2_second<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, D + c.L.c1, D + c.L.c2, w.part, w.counter,
-                                                         D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl, c.L,
-                                                         hc);
-    note_launch();
+    if (only != 2) {
+      k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
+                                                        D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.c2,
+                                                        hc.p ? D + c.L.sc : nullptr); note_launch();
+    }
+    if (only != 1) {
+      k_cgs2_second<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, D + c.L.c1, D + c.L.c2, w.part, w.counter,
+                                                           D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl,
+                                                           c.L, hc);
+      note_launch();
+    }
     return cudaGetLastError();
   }
+  if (only) return cudaErrorNotSupported;
   k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
                                                     D + c.L.d1, D + c.L.c1, w.dctl, nullptr, nullptr); note_launch();
   k_cgs_update<T, true><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, w.counter,
@@ -1731,6 +1737,42 @@ sg_status time_cgs_passes(sg_handle* h, sg_prec prec, int j, int reps, cudaStrea
 }
 
 }  // namespace sgi
+
+extern "C" sg_status sg_cgs2_pass(sg_handle* h, int restart, int j, int pass, void* stream) {
+  using namespace sgi;
+  return guarded([&]() -> sg_status {
+    if (!h) return fail(SG_EINVAL, "NULL handle");
+    if (pass < 0 || pass > 2) return fail(SG_EINVAL, "pass must be 0, 1 or 2");
+    cudaStream_t st = (cudaStream_t)stream;
+    const sg_prec pk = SG_PREC_MEAN;
+    if (pass == 0) {
+      sg_gmres_opts o{};
+      o.restart = restart <= 0 ? 30 : restart;
+      o.mode = SG_MIXED;
+      o.prec = pk;
+      sg_status s = sgi_prepare_workspace(h, &o);
+      if (s != SG_OK) return s;
+    }
+    GmresWork& w = h->gw;
+    if (!w.V || w.prec_bytes != (int)sizeof(float2) || j < 0 || j + 1 > w.restart)
+      return fail(SG_EINVAL, "needs a complex64 workspace (pass 0) with room for step j");
+    Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+    if (!flexible<float>(c, pk) || !prec_available(h, pk))
+      return fail(SG_EUNSUPPORTED, "the two-pass CGS2 form runs in the flexible cycles of 2D separable problems");
+    if (pass == 0) {
+      // zero basis and scalars: the passes read and write the same amount
+      // whatever the values
+      SG_CUDA_TRY(cudaMemsetAsync(w.V, 0, (size_t)(j + 2) * h->N * sizeof(float2), st));
+      SG_CUDA_TRY(cudaMemsetAsync(w.dscal, 0, (size_t)c.L.total * sizeof(double), st));
+      return SG_OK;
+    }
+    // the done flag (set by a zero basis's breakdown) is cleared first, so
+    // that the pass does its work
+    SG_CUDA_TRY(cudaMemsetAsync(w.dctl, 0, 16 * sizeof(int), st));
+    SG_CUDA_TRY(cgs_passes<float>(c, pk, j, pass));
+    return SG_OK;
+  });
+}
 
 // ------------------------------------------------------------------ stationary iteration
 // The stationary iteration of Sec. 5 with the mean-value (or CSL mean-value)

@@ -9,7 +9,8 @@ named "profiled", so a profiler can restrict itself to those launches:
         python -m paper_2209_14740_gb300.profile_cases solve --mode mixed
 
 Cases: matvec (the SG operator), precond (the mean-value preconditioner),
-solve (one preconditioned GMRES solve).  Prints one JSON line with the
+solve (one preconditioned GMRES solve), cgs2 (the two CGS2 passes of Arnoldi
+step --step of the flexible complex64 cycles, on a zeroed workspace).  Prints one JSON line with the
 CUDA-event time per repetition (meaningless under a profiler).
 """
 from __future__ import annotations
@@ -40,7 +41,7 @@ def main(argv=None):
     import torch
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["matvec", "precond", "solve"])
+    ap.add_argument("case", choices=["matvec", "precond", "solve", "cgs2"])
     ap.add_argument("--dim", type=int, default=2, choices=[1, 2], help="1: the 1D workload with --g unknowns")
     ap.add_argument("--g", type=int, default=127)
     ap.add_argument("--s", type=int, default=3)
@@ -54,6 +55,7 @@ def main(argv=None):
     ap.add_argument("--restart", type=int, default=50)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--inner-tol", type=float, default=0.0, help="mixed solve: inner reduction per refinement")
+    ap.add_argument("--step", type=int, default=10, help="cgs2: Arnoldi step j of the timed passes")
     ap.add_argument("--tile-n", type=int, default=-1,
                     help="transform tile width to set (64, 128, 256; 0: built-in rule); default: as tuned")
     a = ap.parse_args(argv)
@@ -83,6 +85,12 @@ def main(argv=None):
         def call():
             return op.gmres(b, x, restart=a.restart, tol=1e-8 if mode != B.FP32 else 1e-5, prec=B.PREC_MEAN,
                             mode=mode, inner_tol=a.inner_tol)
+    elif a.case == "cgs2":
+        op.cgs2_pass(a.step, 0, restart=max(a.restart, a.step + 1))
+
+        def call():
+            op.cgs2_pass(a.step, 1)
+            op.cgs2_pass(a.step, 2)
     else:
         X = torch.randn(op.N, dtype=cdt, device=dev, generator=gen)
         Y = torch.empty_like(X)

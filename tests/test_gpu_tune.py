@@ -159,3 +159,36 @@ def test_retuning_after_solves_drops_captured_graphs(B):
     op.tune_set({"tf32_transforms": 0})
     assert torch.equal(solve(), x16)            # back to the binary16 route, same bits
     op.close()
+
+
+def test_cgs2_pass_entry_point(B):
+    """sg_cgs2_pass: prepares the workspace, runs either pass of a flexible
+    step without error (graph-free, on the caller's stream), rejects steps
+    outside the workspace and problems without the two-pass form, and leaves
+    the handle usable for a solve."""
+    from oracle import sg
+    pr = inputs.helmholtz_2d(63, 2, 2, 15.0, 0.1)
+    op = B.SG(pr, tuned=False)
+    op.cgs2_pass(5, 0, restart=20)
+    for _ in range(2):
+        op.cgs2_pass(5, 1)
+        op.cgs2_pass(5, 2)
+    torch.cuda.synchronize()
+    with pytest.raises(B.SgError) as ei:
+        op.cgs2_pass(20, 1)
+    assert ei.value.status == B.SG_EINVAL
+    with pytest.raises(B.SgError) as ei:
+        op.cgs2_pass(5, 3)
+    assert ei.value.status == B.SG_EINVAL
+    S = sg.assemble_problem(pr)
+    b = torch.from_numpy(S.b).to(DEV)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=20, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=2000)
+    assert info["status"] == B.SG_OK
+    assert np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b) <= 1e-9
+    op.close()
+    op1 = B.SG(inputs.helmholtz_1d_c1(), tuned=False)
+    with pytest.raises(B.SgError) as ei:
+        op1.cgs2_pass(3, 0)
+    assert ei.value.status == B.SG_EUNSUPPORTED
+    op1.close()

@@ -40,6 +40,7 @@ constexpr int MAXV = 512;   // maximum basis vectors handled by the coefficient 
 struct DevLayout {
   int m;                    // restart capacity
   size_t H, cs, sn, g, vscale, d1, c1, d2, c2, yc, sc;   // offsets in doubles
+  size_t R;                 // flexible cycles' basis factor, (m+1) x (m+1) complex, column-major
   size_t total;
   // Every array starts on a 16-byte boundary (an even double offset) because
   // the complex ones are accessed as double2.
@@ -61,6 +62,7 @@ struct DevLayout {
     c2 = take(2 * (size_t)(m + 1));
     yc = take(2 * (size_t)(m + 1));
     sc = take(16);
+    R = take(2 * (size_t)(m + 1) * (m + 1));
     total = o;
   }
 };
@@ -152,9 +154,10 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 //   k_cgs_update<DOTS>     w -= V c1, then d2 = V^H w      (c2 = vscale^2 d2)
 //   k_cgs_update<GIVENS>   w -= V c2, ||w||^2, then the Givens update of
 //                          column j in the last block to finish.
-// Flexible complex64 cycles take two passes instead (k_cgs_dots with the
-// correction of the newest slot, then k_cgs2_second): the third pass's update
-// is folded into the next step's second pass.
+// Flexible complex64 cycles take two passes instead (k_cgs_dots, then
+// k_cgs2_second) over slots that are never finalised in place: the second
+// projection of each new vector is kept as a column of a small triangular
+// factor R that both passes apply to their coefficients (see tri_forward_h).
 // Each block walks chunks of RED_THREADS * CG_EPT consecutive elements (grid
 // stride), a thread keeps its CG_EPT elements of w in registers, and every
 // pass reads each V_i element once (the DOTS re-read of the chunk it just
@@ -334,11 +337,83 @@ __device__ __forceinline__ bool finish_dots(int nv, const double2* red, double* 
   return true;
 }
 
+// The flexible cycles never finalise a basis slot in place: slot k keeps
+// u_k, the step's w after one projection, and the orthogonal directions are
+// V_k = u_k - sum_{i<k} V_i R_ik, i.e. U = V R with R unit upper triangular,
+// column k holding the second-pass coefficients of slot k (written by step
+// k-1's pass 2).  Dots with V come from dots with U by forward substitution,
+// V^H x = R^-H U^H x, and an update by V is one by U with back-substituted
+// coefficients, V c = U (R^-1 c).  (R's off-diagonal entries are of the size
+// of the first pass's rounding, so neither solve loses anything.)  One warp,
+// t[0 .. nv) in shared memory.  R is read through `at` (R_kl, k < l): the
+// device array (column-major, leading dimension ldr) or, for nv <=
+// TRI_SMEM_MAX, a copy of its strict upper triangle that the whole block
+// stages in shared memory first (the solves' steps are sequential, so each
+// one waiting on a global load would cost a load latency per step).
+constexpr int TRI_SMEM_MAX = 64;
+struct RGlobal {
+  const double* R;
+  int ldr;
+  __device__ double2 operator()(int k, int l) const {
+    return *reinterpret_cast<const double2*>(R + 2 * ((size_t)l * ldr + k));
+  }
+};
+struct RShared {
+  const double2* rt;   // column l at rt[l (l - 1) / 2 + k], k < l
+  __device__ double2 operator()(int k, int l) const { return rt[l * (l - 1) / 2 + k]; }
+};
+// All threads of the block: rt <- the strict upper triangle of R (nv columns),
+// entry idx = l (l - 1) / 2 + k with l = floor((1 + sqrt(1 + 8 idx)) / 2)
+// (corrected by one where the square root rounds): every load independent,
+// so the block waits for one load latency, not one per column.
+__device__ __forceinline__ void tri_stage(double2* rt, const double* __restrict__ R, int ldr, int nv) {
+  const int ntri = nv * (nv - 1) / 2;
+  for (int idx = threadIdx.x; idx < ntri; idx += blockDim.x) {
+    int l = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)idx)) * 0.5f);
+    if (l * (l - 1) / 2 > idx) --l;
+    else if ((l + 1) * l / 2 <= idx) ++l;
+    const int k = idx - l * (l - 1) / 2;
+    rt[idx] = *reinterpret_cast<const double2*>(R + 2 * ((size_t)l * ldr + k));
+  }
+}
+template <typename At>
+__device__ __forceinline__ void tri_forward_h(double2* t, const At& at, int nv) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k + 1 < nv; ++k) {
+    const double2 dk = t[k];
+    for (int l = k + 1 + lane; l < nv; l += 32) {   // t_l -= conj(R_kl) t_k
+      const double2 r = at(k, l);
+      t[l].x -= r.x * dk.x + r.y * dk.y;
+      t[l].y -= r.x * dk.y - r.y * dk.x;
+    }
+    __syncwarp();
+  }
+}
+template <typename At>
+__device__ __forceinline__ void tri_back(double2* t, const At& at, int nv) {
+  const int lane = threadIdx.x & 31;
+  for (int l = nv - 1; l > 0; --l) {
+    const double2 cl = t[l];
+    for (int k = lane; k < l; k += 32) {            // t_k -= R_kl t_l
+      const double2 r = at(k, l);
+      t[k].x -= r.x * cl.x - r.y * cl.y;
+      t[k].y -= r.x * cl.y + r.y * cl.x;
+    }
+    __syncwarp();
+  }
+}
+// double2 entries of dynamic shared memory a flexible CGS2 pass needs: the per-warp
+// table, or the solves' vector and R's staged triangle if larger.
+__host__ __device__ constexpr size_t cgs_flex_smem_entries(int nv, int warps) {
+  return nv <= TRI_SMEM_MAX && (size_t)nv + (size_t)nv * (nv - 1) / 2 > (size_t)warps * nv
+             ? (size_t)nv + (size_t)nv * (nv - 1) / 2
+             : (size_t)warps * nv;
+}
+
 // Pass 1: d = V^H w, c = vscale^2 d.  Dynamic shared memory: CG_WARPS * nv double2.
-// Two-pass form (c2prev != null): slot nv-1 still holds u, the previous
-// step's w after one projection, whose final form is u_hat = u - sum_{i<nv-1}
-// c2prev_i V_i; the last block turns u^H w into u_hat^H w = u^H w -
-// sum_i conj(c2prev_i) d_i before forming c.
+// Two-pass form (R != null): V holds the unfinalised slots u_0 .. u_j; the
+// last block turns the sums U^H w into d = V^H w (forward substitution), c =
+// vscale^2 d, and stores the U-basis coefficients R^-1 c that pass 2 applies.
 // With sc (the binary16 route) it also sums ||w||^2 and stores in
 // sc[SC_H16] the scale of pass 2's binary16 copy of w - sum_i c_i V_i:
 // sqrt(N) / 4 over that vector's norm, which Pythagoras gives from the dots
@@ -348,8 +423,8 @@ __device__ __forceinline__ bool finish_dots(int nv, const double2* red, double* 
 template <typename T>
 __device__ __forceinline__ void cgs_dots_body(
     const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev,
-    double* sc) {
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R,
+    int ldr, double* sc) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   __shared__ double sm[32];
@@ -378,21 +453,35 @@ __device__ __forceinline__ void cgs_dots_body(
     if (threadIdx.x == 0) part[(size_t)(2 * nv) * G + blockIdx.x] = dv[0];
   }
   if (!finish_dots(nv, red, part, counter, vscale, d_out, c_out)) return;
-  if (c2prev) {
+  if (R) {
+    // (the per-warp table is no longer needed: its first nv entries hold
+    // the solves' vector, the rest R's staged triangle)
     __syncthreads();
-    if (threadIdx.x == 0) {
-      const int jn = nv - 1;
-      double sx = d_out[2 * jn], sy = d_out[2 * jn + 1];
-      for (int i = 0; i < jn; ++i) {
-        const double cx = c2prev[2 * i], cy = c2prev[2 * i + 1], dx = d_out[2 * i], dy = d_out[2 * i + 1];
-        sx -= cx * dx + cy * dy;   // conj(c) d
-        sy -= cx * dy - cy * dx;
+    const bool staged = nv <= TRI_SMEM_MAX;
+    if (staged) {
+      tri_stage(red + nv, R, ldr, nv);
+      __syncthreads();
+    }
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int l = lane; l < nv; l += 32) red[l] = make_double2(d_out[2 * l], d_out[2 * l + 1]);
+      __syncwarp();
+      if (staged) tri_forward_h(red, RShared{red + nv}, nv);
+      else tri_forward_h(red, RGlobal{R, ldr}, nv);
+      for (int l = lane; l < nv; l += 32) {
+        const double2 d = red[l];
+        d_out[2 * l] = d.x;
+        d_out[2 * l + 1] = d.y;
+        const double vs2 = vscale[l] * vscale[l];
+        red[l] = make_double2(vs2 * d.x, vs2 * d.y);
       }
-      d_out[2 * jn] = sx;
-      d_out[2 * jn + 1] = sy;
-      const double vs = vscale[jn];
-      c_out[2 * jn] = vs * vs * sx;
-      c_out[2 * jn + 1] = vs * vs * sy;
+      __syncwarp();
+      if (staged) tri_back(red, RShared{red + nv}, nv);
+      else tri_back(red, RGlobal{R, ldr}, nv);
+      for (int l = lane; l < nv; l += 32) {
+        c_out[2 * l] = red[l].x;
+        c_out[2 * l + 1] = red[l].y;
+      }
     }
   }
   if (sc) {
@@ -420,16 +509,16 @@ __device__ __forceinline__ void cgs_dots_body(
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(
     const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev,
-    double* sc) {
-  cgs_dots_body<T>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev, sc);
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R,
+    int ldr, double* sc) {
+  cgs_dots_body<T>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, R, ldr, sc);
 }
 template <>
 __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_dots<float>(
     const C2<float>* __restrict__ V, long long N, int nv, const C2<float>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* c2prev,
-    double* sc) {
-  cgs_dots_body<float>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, c2prev, sc);
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R,
+    int ldr, double* sc) {
+  cgs_dots_body<float>(V, N, nv, w, part, counter, vscale, d_out, c_out, ctl, R, ldr, sc);
 }
 
 __device__ void givens_column(double* D, int* ctl, const DevLayout& L, int j);
@@ -535,14 +624,15 @@ __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs_update<f
   cgs_update_body<float, false>(V, N, nv, w, c, part, counter, vscale, d_out, c_out, D, ctl, L, j);
 }
 
-// Two-pass form, pass 2 (flexible cycles): with j = nv - 1,
-//   u_hat = u - sum_{i<j} c2prev_i V_i           (finalises slot j)
-//   w    -= sum_{i<j} c1_i V_i + c1_j u_hat       (slot j+1)
-// then d2 = V^H w over slots 0..j, ||w||^2, and in the last block
-// c2 = vscale^2 d2, ||w - sum_i c2_i V_i||^2 = ||w||^2 - sum_i vscale_i^2 |d2_i|^2
-// (the basis is orthogonal, and the second-pass coefficients are tiny, so
-// the difference loses nothing) and the Givens update of column j.  The
-// vector w - sum c2_i V_i itself is formed by the next step's pass 2.
+// Two-pass form, pass 2 (flexible cycles): with j = nv - 1 and c1 the U-basis
+// coefficients from pass 1,
+//   w -= sum_{i<=j} c1_i u_i                      (slot j+1, once projected)
+// then the sums U^H w over slots 0..j and ||w||^2; the last block turns the
+// sums into d2 = V^H w (forward substitution), stores c2 = vscale^2 d2 as
+// column j+1 of R (w = V_{j+1} + sum_i V_i c2_i: the second projection is
+// never applied to the stored vector), ||V_{j+1}||^2 = ||w||^2 -
+// sum_i vscale_i^2 |d2_i|^2 (the directions are orthogonal) and runs the
+// Givens update of column j.
 // With a half copy (hc.p), w is also written, times pass 1's scale
 // D[sc + SC_H16], as binary16 pairs in rows of mx4 pairs (the input of the
 // next step's binary16 transform 1): element e = row mx + col goes to row
@@ -559,56 +649,48 @@ struct HalfCopy {
 };
 template <typename T>
 __device__ __forceinline__ void cgs2_second_body(
-    C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
-    const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* c_out, double* D, int* ctl, DevLayout L, HalfCopy hc) {
+    C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1, const double* __restrict__ R,
+    int ldr, double* part, unsigned* counter, const double* vscale, double* d_out, double* D, int* ctl,
+    DevLayout L, HalfCopy hc) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   __shared__ C2<T> cs1[MAXV];
-  __shared__ C2<T> cs2[MAXV];
   __shared__ double sm[32];
   const int j = nv - 1;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    cs1[i] = mkc<T>((T)c1[2 * i], (T)c1[2 * i + 1]);
-    cs2[i] = i < j ? mkc<T>((T)c2prev[2 * i], (T)c2prev[2 * i + 1]) : mkc<T>(T(0), T(0));
-  }
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs1[i] = mkc<T>((T)c1[2 * i], (T)c1[2 * i + 1]);
   for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
   __syncthreads();
-  C2<T>* uj = V + (size_t)j * N;
   C2<T>* w = V + (size_t)(j + 1) * N;
   const float hs = hc.p ? (float)D[L.sc + SC_H16] : 0.0f;
   const long long chunk = (long long)RED_THREADS * CG_EPT;
   T nacc = T(0);
   for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
-    C2<T> wk[CG_EPT], uk[CG_EPT];
+    C2<T> wk[CG_EPT];
 #pragma unroll
     for (int k = 0; k < CG_EPT; ++k) {
       const long long e = base + k * RED_THREADS;
       wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
-      uk[k] = e < N ? uj[e] : mkc<T>(T(0), T(0));
     }
     if constexpr (sizeof(T) == 4) {
-      for (int i0 = 0; i0 < j; i0 += CG_QB) {
+      for (int i0 = 0; i0 < nv; i0 += CG_QB) {
         C2<T> v[CG_QB][CG_EPT];
-        load_group<T>(V, N, j, i0, base, v);
+        load_group<T>(V, N, nv, i0, base, v);
 #pragma unroll
         for (int q = 0; q < CG_QB; ++q) {
-          if (i0 + q >= j) break;
-          const C2<T> a = cs1[i0 + q], b = cs2[i0 + q];
+          if (i0 + q >= nv) break;
+          const C2<T> a = cs1[i0 + q];
 #pragma unroll
           for (int k = 0; k < CG_EPT; ++k) {
             wk[k].x -= a.x * v[q][k].x - a.y * v[q][k].y;
             wk[k].y -= a.x * v[q][k].y + a.y * v[q][k].x;
-            uk[k].x -= b.x * v[q][k].x - b.y * v[q][k].y;
-            uk[k].y -= b.x * v[q][k].y + b.y * v[q][k].x;
           }
         }
       }
     } else {
 #pragma unroll 4
-      for (int i = 0; i < j; ++i) {
+      for (int i = 0; i < nv; ++i) {
         const C2<T>* Vi = V + (size_t)i * N;
-        const C2<T> a = cs1[i], b = cs2[i];
+        const C2<T> a = cs1[i];
 #pragma unroll
         for (int k = 0; k < CG_EPT; ++k) {
           const long long e = base + k * RED_THREADS;
@@ -616,46 +698,25 @@ __device__ __forceinline__ void cgs2_second_body(
             const C2<T> v = __ldg(Vi + e);
             wk[k].x -= a.x * v.x - a.y * v.y;
             wk[k].y -= a.x * v.y + a.y * v.x;
-            uk[k].x -= b.x * v.x - b.y * v.y;
-            uk[k].y -= b.x * v.y + b.y * v.x;
           }
         }
       }
     }
-    const C2<T> a = cs1[j];
 #pragma unroll
     for (int k = 0; k < CG_EPT; ++k) {
       const long long e = base + k * RED_THREADS;
       if (e < N) {
-        wk[k].x -= a.x * uk[k].x - a.y * uk[k].y;
-        wk[k].y -= a.x * uk[k].y + a.y * uk[k].x;
-        uj[e] = uk[k];
         w[e] = wk[k];
         nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
         if (hc.p) {
           const unsigned long long row = ((unsigned long long)e * hc.mul) >> hc.shift;
           const long long col = e - (long long)row * hc.mx;
-          hc.p[(size_t)row * hc.mx4 + col] =
-              __floats2half2_rn(hs * (float)wk[k].x, hs * (float)wk[k].y);
+          hc.p[(size_t)row * hc.mx4 + col] = __floats2half2_rn(hs * (float)wk[k].x, hs * (float)wk[k].y);
         }
       }
     }
-    // dots with the unchanged slots 0..j-1 (read-only path), and with the
-    // finalised slot j from registers (it was written by this kernel)
-    chunk_dots<T>(V, N, j, base, wk, red, nv);
-    T ax = T(0), ay = T(0);
-#pragma unroll
-    for (int k = 0; k < CG_EPT; ++k) {
-      ax += uk[k].x * wk[k].x + uk[k].y * wk[k].y;
-      ay += uk[k].x * wk[k].y - uk[k].y * wk[k].x;
-    }
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    if ((threadIdx.x & 31) == 0) {
-      double2& r = red[(threadIdx.x >> 5) * nv + j];
-      r.x += (double)ax;
-      r.y += (double)ay;
-    }
+    // dots with slots 0..j (read-only path: the chunk was just read above)
+    chunk_dots<T>(V, N, nv, base, wk, red, nv);
   }
   // block sums of the dots (as finish_dots) and of ||w||^2 in one table
   const int G = gridDim.x;
@@ -675,6 +736,7 @@ __device__ __forceinline__ void cgs2_second_body(
   if (!last_block(counter)) return;
   __shared__ double wn2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // (the per-warp table is free now: its first nv entries take the sums)
   for (int k = warp; k <= 2 * nv; k += CG_WARPS) {
     const double* pk = part + (size_t)k * G;
     double s0 = 0.0, s1 = 0.0;
@@ -689,44 +751,57 @@ __device__ __forceinline__ void cgs2_second_body(
     for (int o = 16; o > 0; o >>= 1) ssum += __shfl_down_sync(0xffffffffu, ssum, o);
     if (lane == 0) {
       if (k < 2 * nv) {
-        d_out[k] = ssum;
-        const double vs = vscale[k >> 1];
-        c_out[k] = vs * vs * ssum;
+        if (k & 1) red[k >> 1].y = ssum;
+        else red[k >> 1].x = ssum;
       } else {
         wn2 = ssum;
       }
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double corr = 0.0;
-    for (int i = 0; i < nv; ++i) {
-      const double vs = vscale[i];
-      corr += vs * vs * (d_out[2 * i] * d_out[2 * i] + d_out[2 * i + 1] * d_out[2 * i + 1]);
-    }
-    const double r = wn2 - corr;
-    D[L.sc + SC_NORMSQ] = r > 0.0 ? r : 0.0;
-    *counter = 0;
+  const bool staged = nv <= TRI_SMEM_MAX;
+  if (staged) {
+    tri_stage(red + nv, R, ldr, nv);
+    __syncthreads();
   }
-  __syncthreads();
   if (threadIdx.x < 32) {
+    if (staged) tri_forward_h(red, RShared{red + nv}, nv);
+    else tri_forward_h(red, RGlobal{R, ldr}, nv);
+    double2* rcol = reinterpret_cast<double2*>(D + L.R) + (size_t)(j + 1) * ldr;
+    double corr = 0.0;
+    for (int l = lane; l < nv; l += 32) {
+      const double2 d = red[l];
+      d_out[2 * l] = d.x;
+      d_out[2 * l + 1] = d.y;
+      const double vs2 = vscale[l] * vscale[l];
+      rcol[l] = make_double2(vs2 * d.x, vs2 * d.y);
+      corr += vs2 * (d.x * d.x + d.y * d.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) corr += __shfl_down_sync(0xffffffffu, corr, o);
+    if (lane == 0) {
+      const double r = wn2 - corr;
+      D[L.sc + SC_NORMSQ] = r > 0.0 ? r : 0.0;
+      *counter = 0;
+    }
+    __syncwarp();
     givens_column(D, ctl, L, j);
-    if (hc.p && threadIdx.x == 0) D[L.sc + SC_H16IN] = D[L.vscale + j + 1] * sqrt((double)N) / (double)hs;
+    if (hc.p && lane == 0) D[L.sc + SC_H16IN] = D[L.vscale + j + 1] * sqrt((double)N) / (double)hs;
   }
 }
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cgs2_second(
-    C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
-    const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* c_out, double* D, int* ctl, DevLayout L, HalfCopy hc) {
-  cgs2_second_body<T>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L, hc);
+    C2<T>* __restrict__ V, long long N, int nv, const double* __restrict__ c1, const double* __restrict__ R,
+    int ldr, double* part, unsigned* counter, const double* vscale, double* d_out, double* D, int* ctl,
+    DevLayout L, HalfCopy hc) {
+  cgs2_second_body<T>(V, N, nv, c1, R, ldr, part, counter, vscale, d_out, D, ctl, L, hc);
 }
 template <>
 __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs2_second<float>(
-    C2<float>* __restrict__ V, long long N, int nv, const double* __restrict__ c1,
-    const double* __restrict__ c2prev, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* c_out, double* D, int* ctl, DevLayout L, HalfCopy hc) {
-  cgs2_second_body<float>(V, N, nv, c1, c2prev, part, counter, vscale, d_out, c_out, D, ctl, L, hc);
+    C2<float>* __restrict__ V, long long N, int nv, const double* __restrict__ c1, const double* __restrict__ R,
+    int ldr, double* part, unsigned* counter, const double* vscale, double* d_out, double* D, int* ctl,
+    DevLayout L, HalfCopy hc) {
+  cgs2_second_body<float>(V, N, nv, c1, R, ldr, part, counter, vscale, d_out, D, ctl, L, hc);
 }
 
 // r = b - Ax (or r = b when Ax == nullptr) written in the inner precision;
@@ -1268,24 +1343,24 @@ cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j, int only) {
   C2<T>* wv = V + (size_t)(j + 1) * N;
   double* D = w.dscal;
   const int nv = j + 1;
-  const size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
+  size_t red_bytes = (size_t)CG_WARPS * nv * sizeof(double2);
   const int G = c.cg_grid;
   if (flexible<T>(c, prec)) {
-    // two passes: the reorthogonalisation of slot j is folded into this
-    // step's second pass (flexible GMRES lets the preconditioner take the
-    // once-projected vector)
+    red_bytes = cgs_flex_smem_entries(nv, CG_WARPS) * sizeof(double2);
+    // two passes over unfinalised slots (the second projection kept in R;
+    // flexible GMRES lets the preconditioner take the once-projected vector)
     // the binary16 route: pass 2 also writes w as the next step's binary16
     // input, at a scale pass 1 derives from ||w||
     HalfCopy hc{};
     if (sizeof(T) == sizeof(float) && use_half_copy(c)) hc = half_copy(c.h);
     if (only != 2) {
       k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
-                                                        D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.c2,
+                                                        D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.R, c.L.m + 1,
                                                         hc.p ? D + c.L.sc : nullptr); note_launch();
     }
     if (only != 1) {
-      k_cgs2_second<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, D + c.L.c1, D + c.L.c2, w.part, w.counter,
-                                                           D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl,
+      k_cgs2_second<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, D + c.L.c1, D + c.L.R, c.L.m + 1, w.part,
+                                                           w.counter, D + c.L.vscale, D + c.L.d2, D, w.dctl,
                                                            c.L, hc);
       note_launch();
     }
@@ -1293,7 +1368,8 @@ cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j, int only) {
   }
   if (only) return cudaErrorNotSupported;
   k_cgs_dots<T><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, w.part, w.counter, D + c.L.vscale,
-                                                    D + c.L.d1, D + c.L.c1, w.dctl, nullptr, nullptr); note_launch();
+                                                    D + c.L.d1, D + c.L.c1, w.dctl, nullptr, 0, nullptr);
+  note_launch();
   k_cgs_update<T, true><<<G, RED_THREADS, red_bytes, c.st>>>(V, N, nv, wv, D + c.L.c1, w.part, w.counter,
                                                             D + c.L.vscale, D + c.L.d2, D + c.L.c2, D, w.dctl,
                                                             c.L, j); note_launch();

@@ -1,14 +1,16 @@
 """CPU checks of the algebra behind the complex64 GMRES cycles (no GPU).
 
 1. The two-pass CGS2 of the flexible cycles, restated in numpy with the same
-   quantities the kernels keep (raw basis slots, their inverse norms, the
-   coefficients c1 = vscale^2 d1 and c2 = vscale^2 d2 of the previous step):
-   the newest slot holds the once-projected vector u; the next step's first
-   pass corrects u^H w to u_hat^H w with u_hat = u - sum_i c2_i V_i, its
-   second pass finalises u_hat, and the new norm comes from
-   ||w1||^2 - sum_i vscale_i^2 |d2_i|^2.  Checked: the flexible Arnoldi
-   relation A Z = V H to rounding, an orthonormal basis, and the Hessenberg
-   columns equal to those of a plain CGS2 projection of the same A z_j.
+   quantities the kernels keep: unfinalised slots u_k (each step's vector
+   after one projection), the inverse norms vscale_k of the orthogonal
+   directions V_k, and the unit upper triangular R with U = V R whose column
+   k holds slot k's second-pass coefficients.  Pass 1 forms d1 = V^H w =
+   R^-H U^H w, c1 = vscale^2 d1 and updates by U with R^-1 c1; pass 2 forms
+   d2 = R^-H U^H w1, stores c2 = vscale^2 d2 as the next column of R and the
+   new norm as ||w1||^2 - sum_i vscale_i^2 |d2_i|^2.  Checked: the flexible
+   Arnoldi relation A Z = V H to rounding, orthonormal directions, and the
+   Hessenberg columns equal to those of a plain CGS2 projection of the same
+   A z_j.
 2. The accuracy bound of the plain-TF32 preconditioner the GPU tests use
    (5e-3): the four fast-diagonalisation transforms emulated with TF32
    inputs (data truncated to 10 mantissa bits, factors rounded) and FP32
@@ -18,48 +20,60 @@ import numpy as np
 import pytest
 
 
+def _fwd_h(R, e):
+    """d with R^H d = e (R unit upper triangular): forward substitution."""
+    d = e.astype(complex).copy()
+    for k in range(len(d)):
+        d[k + 1:] -= np.conj(R[k, k + 1:]) * d[k]
+    return d
+
+
+def _back(R, c):
+    """x with R x = c (R unit upper triangular): back substitution."""
+    x = c.astype(complex).copy()
+    for l in range(len(x) - 1, 0, -1):
+        x[:l] -= R[:l, l] * x[l]
+    return x
+
+
 def two_pass_flexible_arnoldi(A, minv, r0, m, leak=0.0, seed=0):
-    """m steps; returns (V (n x m+1, finalised, orthonormal), Z, H).  leak > 0
-    perturbs the first-pass coefficients by that relative amount (used for
-    both the projection and H, so A Z = V H stays exact): the once-projected
-    vector then keeps a component along the basis, as the rounding of the
-    complex64 first pass leaves one on the GPU, and only the second pass, the
-    correction of the newest coefficient and the Pythagorean norm remove it."""
+    """m steps; returns (V (n x m+1, the orthonormal directions), Z, H).  leak
+    > 0 perturbs the first-pass dots by that relative amount (used for both
+    the projection and H, so A Z = V H stays exact): the once-projected vector
+    then keeps a component along the basis, as the rounding of the complex64
+    first pass leaves one on the GPU, and only the second pass (kept in R)
+    and the Pythagorean norm account for it."""
     rng = np.random.default_rng(seed)
     n = r0.size
-    slots = np.zeros((m + 1, n), dtype=complex)   # raw slot vectors
+    U = np.zeros((m + 1, n), dtype=complex)        # stored slots, never finalised
     vs = np.zeros(m + 1)
-    slots[0] = r0
+    R = np.eye(m + 1, dtype=complex)
+    U[0] = r0
     vs[0] = 1.0 / np.linalg.norm(r0)
-    c2prev = np.zeros(0, dtype=complex)
     Z = np.zeros((m, n), dtype=complex)
     H = np.zeros((m + 1, m), dtype=complex)
     for j in range(m):
-        u = slots[j].copy()
-        Z[j] = minv(vs[j] * u)
+        Z[j] = minv(vs[j] * U[j])
         w = A @ Z[j]
-        # first pass: dots with slots 0..j (slot j still u), correction of the last
-        d1 = slots[: j + 1].conj() @ w
-        d1[j] -= np.dot(c2prev.conj(), d1[:j])
+        Rj = R[: j + 1, : j + 1]
+        # pass 1: U^H w, d1 = R^-H U^H w, U-basis coefficients R^-1 c1
+        d1 = _fwd_h(Rj, U[: j + 1].conj() @ w)
         if leak:
             e = rng.standard_normal(j + 1) + 1j * rng.standard_normal(j + 1)
             d1 = d1 + leak * np.linalg.norm(d1) * e / np.sqrt(2 * (j + 1))
         c1 = vs[: j + 1] ** 2 * d1
-        # second pass: finalise slot j, project w once, dots, norm
-        u_hat = u - c2prev @ slots[:j]
-        slots[j] = u_hat
-        w1 = w - c1[:j] @ slots[:j] - c1[j] * u_hat
-        d2 = slots[: j + 1].conj() @ w1
+        # pass 2: project once by U, dots, the next column of R, norm
+        w1 = w - _back(Rj, c1) @ U[: j + 1]
+        d2 = _fwd_h(Rj, U[: j + 1].conj() @ w1)
         c2 = vs[: j + 1] ** 2 * d2
         nsq = np.vdot(w1, w1).real - np.sum(vs[: j + 1] ** 2 * np.abs(d2) ** 2)
         H[: j + 1, j] = vs[: j + 1] * (d1 + d2)
         H[j + 1, j] = np.sqrt(nsq)
         vs[j + 1] = 1.0 / np.sqrt(nsq)
-        slots[j + 1] = w1
-        c2prev = c2
-    # the last slot is finalised by what would be the next step's second pass
-    slots[m] = slots[m] - c2prev @ slots[:m]
-    V = (slots * vs[:, None]).T
+        U[j + 1] = w1
+        R[: j + 1, j + 1] = c2
+    Vraw = U.T @ np.linalg.inv(R)                  # V = U R^-1, column k the direction of slot k
+    V = Vraw * vs[None, :]
     return V, Z.T, H
 
 

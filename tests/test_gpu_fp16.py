@@ -186,3 +186,23 @@ def test_paired_256_form_refused_without_fp16_route(B):
         op.tune_set({"tc_tile_n": 256})
     assert ei.value.status == B.SG_EUNSUPPORTED
     op.close()
+
+
+@pytest.mark.parametrize("sigma", [0.25, 0.35])
+def test_flexible_long_cycles(B, sigma):
+    """Flexible cycles longer than 64 steps (the CGS2 passes then read the
+    basis factor R from device memory instead of staging it in shared
+    memory): a strongly varying wavenumber and a tight inner reduction make
+    the cycles long; the solve still reaches the tolerance with the oracle's
+    residual."""
+    pr = inputs.helmholtz_2d(63, 3, 3, 25.0, sigma)
+    S = sg.assemble_problem(pr)
+    b = torch.from_numpy(S.b).to(DEV)
+    op = B.SG(pr, tuned=False)
+    x = torch.zeros_like(b)
+    info = op.gmres(b, x, restart=120, tol=1e-10, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000, inner_tol=1e-7)
+    assert info["status"] == B.SG_OK, info
+    relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
+    assert relres <= 1e-10, relres
+    print("long cycles: sigma %.2f iters %d outer %d" % (sigma, info["iters"], info["outer"]))
+    op.close()

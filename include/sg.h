@@ -235,7 +235,8 @@ typedef struct {
   int max_outer;        /* SG_MIXED: cap on refinement steps; <= 0 means 20 */
   double tol;           /* stop when ||b - A x||_2 / ||b||_2 <= tol (Sec. 6.3) */
   double inner_tol;     /* SG_MIXED: inner relative reduction per refinement step (a step that can
-                           reach tol within 20x of it aims at tol directly); <= 0 means 1e-5 */
+                           reach tol within 20x of it aims at tol directly); <= 0 means 1e-5
+                           (1e-3 with the binary16 basis, see basis16) */
   sg_prec prec;         /* right preconditioner M: A M^-1 y = b, x = M^-1 y (Sec. 6.3) */
   sg_precision mode;    /* SG_FP64, SG_FP32 or SG_MIXED */
   const void* x0;       /* initial guess (same memory space and precision as x); NULL = zero */
@@ -246,6 +247,12 @@ typedef struct {
                            ||b - A x|| / ||b||; 1: left, M^-1 A x = M^-1 b, stopping on
                            ||M^-1 (b - A x)|| / ||M^-1 b|| (Sec. 6.3 compares both; SG_FP64 and
                            SG_FP32 only) */
+  int basis16;          /* SG_MIXED with right preconditioning on a problem whose binary16 route
+                           runs (sg_info.fp16_route, transforms not tuned to TF32): 0 (default)
+                           stores the cycles' Krylov basis as binary16 pairs (half the
+                           orthogonalisation traffic; each cycle then reduces the residual by
+                           about 1e-3, so inner_tol <= 0 means 1e-3 there, and the FP64
+                           refinement takes one more step); -1 keeps it in complex64 */
 } sg_gmres_opts;
 
 typedef struct {

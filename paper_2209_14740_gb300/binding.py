@@ -52,7 +52,8 @@ class SgInfo(C.Structure):
 class SgGmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int), ("maxit", C.c_int), ("max_outer", C.c_int), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("prec", C.c_int), ("mode", C.c_int), ("x0", C.c_void_p),
-                ("host_io", C.c_int), ("check_every", C.c_int), ("x0_policy", C.c_int), ("side", C.c_int)]
+                ("host_io", C.c_int), ("check_every", C.c_int), ("x0_policy", C.c_int), ("side", C.c_int),
+                ("basis16", C.c_int)]
 
 
 class SgGmresInfo(C.Structure):
@@ -409,10 +410,11 @@ class SG:
 
     def gmres(self, b, x, *, restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, x0=None, max_outer=0,
               inner_tol=0.0, host_io=False, check_every=0, stream=None, raise_on_notconv=False,
-              x0_policy=0, side=0):
+              x0_policy=0, side=0, basis16=0):
         o = SgGmresOpts()
         o.x0_policy = x0_policy
         o.side = side
+        o.basis16 = basis16
         o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
         o.prec, o.mode = prec, mode
         o.x0 = _ptr(x0) if x0 is not None else None
@@ -428,9 +430,10 @@ class SG:
 
 
 def _opts(restart=0, maxit=0, tol=1e-8, prec=PREC_MEAN, mode=FP64, max_outer=0, inner_tol=0.0, host_io=False,
-          check_every=0, x0_policy=0, side=0):
+          check_every=0, x0_policy=0, side=0, basis16=0):
     o = SgGmresOpts()
     o.side = side
+    o.basis16 = basis16
     o.restart, o.maxit, o.max_outer, o.tol, o.inner_tol = restart, maxit, max_outer, tol, inner_tol
     o.prec, o.mode = prec, mode
     o.x0 = None

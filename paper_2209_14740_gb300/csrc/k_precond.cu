@@ -608,13 +608,14 @@ static cudaError_t fd16_tail(const sg_handle* h, int which, float2* Z, cudaStrea
 }
 
 cudaError_t launch_precond_f16_copy(const sg_handle* h, int which, const void* X16, const CUtensorMap* xmap,
-                                    float2* Z, cudaStream_t st, const int* skip, const double* in_scale) {
+                                    float2* Z, cudaStream_t st, const int* skip, const double* in_scale,
+                                    float oscale) {
   if (h->dim != 2 || !h->fd || !h->fd16 || !h->blk[which].ready || !h->tcB[0].h16 || !X16 || !xmap || !in_scale)
     return cudaErrorNotSupported;
   // transform 1 as a binary16 GEMM: the copy's rows (K = mx) against Qhat_x,
   // per-batch transposed into d_tmp as fd_apply_h's transform 1 writes it
   const cudaError_t e = hgemm(h, 0, X16, h->P * h->my, h->d_tmp, (h->my + 3) & ~3, 1, h->my, nullptr, 0, 1,
-                                 in_scale, 1.0f, true, skip, h->d_err, st, xmap);
+                                 in_scale, oscale, true, skip, h->d_err, st, xmap);
   return e ? e : fd16_tail(h, which, Z, st, skip, nullptr);
 }
 

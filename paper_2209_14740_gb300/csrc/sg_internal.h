@@ -179,6 +179,11 @@ struct GmresWork {
                            // pairs, P my rows of mx4 (mx rounded up to a multiple of 4) pairs, written
                            // by the second CGS2 pass, read by the next step's transform 1 through v16map
   CUtensorMap v16map;
+  void* Vh = nullptr;      // SG_MIXED flexible cycles on the binary16 route: the Krylov basis as binary16
+                           // pairs, (restart+1) slots of vh_np pairs (P my rows of mx4), slot i read by
+                           // the preconditioner's transform 1 through vhmaps[i]
+  long long vh_np = 0;
+  std::vector<CUtensorMap> vhmaps;
   void* R64 = nullptr;     // N complex128 (mixed: outer residual; fp64: A x)
   void* X64 = nullptr;     // N complex128 staging for host_io / x0
   void* B64 = nullptr;     // N complex128 staging for host_io
@@ -319,11 +324,12 @@ constexpr int kFd16Blocks = 1024;
 // The solver's fast apply: binary16 where available (and not switched off by
 // the tuner), else TF32.
 // The binary16 apply from a binary16 copy X16 (P my rows of mx4 pairs,
-// read through xmap): Z = M^-1 (s X16) with s = *in_scale, which must turn
-// the copy into sqrt(N) times the unit vector to precondition (the scale the
-// binary16 transforms expect).
+// read through xmap): Z = M^-1 (s X16) with s = *in_scale * oscale, which
+// must turn the copy into sqrt(N) times the unit vector to precondition (the
+// scale the binary16 transforms expect).
 cudaError_t launch_precond_f16_copy(const sg_handle* h, int which, const void* X16, const CUtensorMap* xmap,
-                                    float2* Z, cudaStream_t st, const int* skip, const double* in_scale);
+                                    float2* Z, cudaStream_t st, const int* skip, const double* in_scale,
+                                    float oscale = 1.0f);
 cudaError_t launch_precond_fast(const sg_handle* h, int which, const float2* R, float2* Z, cudaStream_t st,
                                 const int* skip, const double* in_scale);
 

@@ -420,35 +420,16 @@ __host__ __device__ constexpr size_t cgs_flex_smem_entries(int nv, int warps) {
 // (||w||^2 - sum_i vscale_i^2 |d_i|^2; taken as at least 1e-8 ||w||^2, as the
 // difference cancels when w is nearly in the span).  The copy's entries then
 // have a root mean square near 1/4, far inside the binary16 range.
-template <typename T>
-__device__ __forceinline__ void cgs_dots_body(
-    const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
-    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R,
-    int ldr, double* sc) {
-  if (ctl[CTL_DONE]) return;
-  extern __shared__ double2 red[];
-  __shared__ double sm[32];
-  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
-  __syncthreads();
-  const long long chunk = (long long)RED_THREADS * CG_EPT;
-  T nacc = T(0);
-  for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
-    C2<T> wk[CG_EPT];
-#pragma unroll
-    for (int k = 0; k < CG_EPT; ++k) {
-      const long long e = base + k * RED_THREADS;
-      wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
-    }
-    if (sc) {
-#pragma unroll
-      for (int k = 0; k < CG_EPT; ++k) nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
-    }
-    chunk_dots<T>(V, N, nv, base, wk, red, nv);
-  }
+// The end of pass 1 for every block (its ||w||^2 when sc is set, the dots'
+// block sums) and, in the last block, the sums over blocks, the two-pass
+// form's triangular solves (R set) and the binary16 scale (sc set).
+__device__ __forceinline__ void pass1_finish(double nacc, int nv, double2* red, double* sm, double* part,
+                                             unsigned* counter, const double* vscale, double* d_out,
+                                             double* c_out, const double* R, int ldr, double* sc, long long N) {
   const int G = gridDim.x;
   if (sc) {
     // this block's ||w||^2 in the row after the dots' 2 nv rows
-    double dv[1] = {(double)nacc};
+    double dv[1] = {nacc};
     block_sum<1>(dv, sm);
     if (threadIdx.x == 0) part[(size_t)(2 * nv) * G + blockIdx.x] = dv[0];
   }
@@ -505,6 +486,34 @@ __device__ __forceinline__ void cgs_dots_body(
       }
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void cgs_dots_body(
+    const C2<T>* __restrict__ V, long long N, int nv, const C2<T>* __restrict__ w, double* part,
+    unsigned* counter, const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R,
+    int ldr, double* sc) {
+  if (ctl[CTL_DONE]) return;
+  extern __shared__ double2 red[];
+  __shared__ double sm[32];
+  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const long long chunk = (long long)RED_THREADS * CG_EPT;
+  T nacc = T(0);
+  for (long long base = blockIdx.x * chunk + threadIdx.x; base - threadIdx.x < N; base += gridDim.x * chunk) {
+    C2<T> wk[CG_EPT];
+#pragma unroll
+    for (int k = 0; k < CG_EPT; ++k) {
+      const long long e = base + k * RED_THREADS;
+      wk[k] = e < N ? w[e] : mkc<T>(T(0), T(0));
+    }
+    if (sc) {
+#pragma unroll
+      for (int k = 0; k < CG_EPT; ++k) nacc += wk[k].x * wk[k].x + wk[k].y * wk[k].y;
+    }
+    chunk_dots<T>(V, N, nv, base, wk, red, nv);
+  }
+  pass1_finish((double)nacc, nv, red, sm, part, counter, vscale, d_out, c_out, R, ldr, sc, N);
 }
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cgs_dots(
@@ -802,6 +811,316 @@ __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_cgs2_second<
     int ldr, double* part, unsigned* counter, const double* vscale, double* d_out, double* D, int* ctl,
     DevLayout L, HalfCopy hc) {
   cgs2_second_body<float>(V, N, nv, c1, R, ldr, part, counter, vscale, d_out, D, ctl, L, hc);
+}
+
+// ------------------------------------------------------------------ binary16 basis
+// The mixed solver's flexible cycles on the binary16 route keep their basis
+// slots as binary16 pairs (the storage idea of compressed-basis GMRES,
+// Aliaga et al.: the orthogonalisation is bound by reading the basis, and
+// the FP64 refinement around the cycles absorbs the coarser storage).  A slot
+// has the layout the binary16 transform 1 reads by tensor copies: P my rows
+// of mx values padded with zeros to mx4 pairs, so the preconditioner of the
+// next step reads the slot itself.  The passes walk a slot in quads of 4
+// positions (16 bytes, never across a row since mx4 is a multiple of 4), two
+// per thread, so that a thread keeps as many bytes in flight as the
+// complex64 passes; w (the operator's output, complex64, unpadded) is read
+// at the quad's unknowns and is zero at the pads.  Arithmetic stays FP32
+// with FP64 sums.  A slot's scale (pass 1's, for the new vector) is never
+// needed by the basis arithmetic, because the directions' inverse norms
+// vscale are taken from the stored values; only the Hessenberg column
+// converts the stored units back to w's (see k_hb_second).
+constexpr int HB_QPT = 2;   // quads per thread and chunk
+constexpr int HB_EPT = 4 * HB_QPT;
+struct HalfBasis {
+  __half2* V;              // slot i at V + i np
+  long long np;            // pairs per slot: P my mx4 (a multiple of 4, below 2^31)
+  unsigned long long mulq; // row = quad / (mx4 / 4) by multiply-shift: ceil(2^(32+s) / (mx4/4))
+  int shiftq, mx, mx4;
+};
+__device__ __forceinline__ float2 hb_f2(unsigned u) {
+  __half2 h;
+  memcpy(&h, &u, sizeof(h));
+  return __half22float2(h);
+}
+__device__ __forceinline__ unsigned hb_h2(float x, float y) {
+  const __half2 h = __floats2half2_rn(x, y);
+  unsigned u;
+  memcpy(&u, &h, sizeof(u));
+  return u;
+}
+// First column of quad qd within its row, and the row.
+__device__ __forceinline__ int hb_quad_col(const HalfBasis& hb, long long qd, long long* row) {
+  const long long r = (long long)(((unsigned long long)qd * hb.mulq) >> hb.shiftq);
+  *row = r;
+  return (int)(4 * (qd - r * (hb.mx4 >> 2)));
+}
+// The thread's elements of w at its quads qbase + k RED_THREADS (zero at pads
+// and past the end).
+__device__ __forceinline__ void hb_load_w(const HalfBasis& hb, const float2* __restrict__ w, long long qbase,
+                                          long long nq, float2 (&wk)[HB_EPT]) {
+#pragma unroll
+  for (int k = 0; k < HB_QPT; ++k) {
+    const long long qd = qbase + k * RED_THREADS;
+    long long row = 0;
+    const int c0 = qd < nq ? hb_quad_col(hb, qd, &row) : hb.mx;
+    const long long e0 = row * hb.mx + c0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wk[4 * k + t] = c0 + t < hb.mx ? w[e0 + t] : make_float2(0.f, 0.f);
+  }
+}
+// v[q][k] = quad qbase + k RED_THREADS of slot i0 + q (zero for slots >= nv
+// or quads past the end); every load is issued before any is used.
+__device__ __forceinline__ void hb_load_group(const HalfBasis& hb, int nv, int i0, long long qbase, long long nq,
+                                              uint4 (&v)[CG_QB][HB_QPT]) {
+#pragma unroll
+  for (int q = 0; q < CG_QB; ++q) {
+    const bool live = i0 + q < nv;
+    const uint4* Vi = reinterpret_cast<const uint4*>(hb.V + (size_t)(live ? i0 + q : 0) * hb.np);
+#pragma unroll
+    for (int k = 0; k < HB_QPT; ++k) {
+      const long long qd = qbase + k * RED_THREADS;
+      v[q][k] = live && qd < nq ? __ldg(Vi + qd) : make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+}
+__device__ __forceinline__ float2 hb_elem(const uint4 (&v)[HB_QPT], int m) {
+  const uint4 u = v[m >> 2];
+  const int t = m & 3;
+  return hb_f2(t == 0 ? u.x : t == 1 ? u.y : t == 2 ? u.z : u.w);
+}
+// red[warp * ld + i] += warp sum of conj(U_i) w over the thread's elements,
+// eight slots at a time (chunk_dots on the binary16 basis).
+__device__ __forceinline__ void hb_chunk_dots(const HalfBasis& hb, int nv, long long qbase, long long nq,
+                                              const float2 (&wk)[HB_EPT], double2* red, int ld) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    float acc[16];
+#pragma unroll
+    for (int qb = 0; qb < 8; qb += CG_QB) {
+      if (i0 + qb >= nv) {   // warp-uniform: a group with no slot left
+#pragma unroll
+        for (int q = 0; q < 2 * CG_QB; ++q) acc[2 * qb + q] = 0.f;
+        continue;
+      }
+      uint4 v[CG_QB][HB_QPT];
+      hb_load_group(hb, nv, i0 + qb, qbase, nq, v);
+#pragma unroll
+      for (int q = 0; q < CG_QB; ++q) {
+        float ax = 0.f, ay = 0.f;
+#pragma unroll
+        for (int m = 0; m < HB_EPT; ++m) {
+          const float2 x = hb_elem(v[q], m);
+          ax += x.x * wk[m].x + x.y * wk[m].y;
+          ay += x.x * wk[m].y - x.y * wk[m].x;
+        }
+        acc[2 * (qb + q)] = ax;
+        acc[2 * (qb + q) + 1] = ay;
+      }
+    }
+    const float sum = warp_sum16(acc);
+    if ((lane & 1) == 0) {
+      const int val = cg_value_of_lane(lane), i = i0 + (val >> 1);
+      if (i < nv) {
+        double2& r = red[warp * ld + i];
+        if (val & 1) r.y += (double)sum; else r.x += (double)sum;
+      }
+    }
+  }
+}
+
+// Slot 0 of a cycle: the starting residual r (complex64, in the workspace's
+// complex64 slot 0) stored as binary16 times sqrt(N) / 4 / ||r|| (||r||^2 in
+// sc[SC_RNORM2]); the last block sets vscale_0 = 1 / ||stored slot 0||.
+__global__ void __launch_bounds__(RED_THREADS) k_hb_slot0(const float2* __restrict__ r, HalfBasis hb, double* D,
+                                                         const int* ctl, DevLayout L, double* part, int pstride,
+                                                         unsigned* counter, long long N) {
+  if (ctl[CTL_DONE]) return;
+  __shared__ double sm[32];
+  const double rn2 = D[L.sc + SC_RNORM2];
+  const float s0 = rn2 > 0.0 && rn2 < 1e300 ? (float)(0.25 * sqrt((double)N) / sqrt(rn2)) : 1.0f;
+  const long long nq = hb.np / 4;
+  float acc = 0.f;
+  uint4* out = reinterpret_cast<uint4*>(hb.V);
+  for (long long qd = blockIdx.x * (long long)blockDim.x + threadIdx.x; qd < nq; qd += (long long)gridDim.x * blockDim.x) {
+    long long row = 0;
+    const int c0 = hb_quad_col(hb, qd, &row);
+    const long long e0 = row * hb.mx + c0;
+    unsigned u[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 v = c0 + t < hb.mx ? r[e0 + t] : make_float2(0.f, 0.f);
+      u[t] = hb_h2(s0 * v.x, s0 * v.y);
+      const float2 f = hb_f2(u[t]);
+      acc += f.x * f.x + f.y * f.y;
+    }
+    out[qd] = make_uint4(u[0], u[1], u[2], u[3]);
+  }
+  double dv[1] = {(double)acc};
+  block_sum<1>(dv, sm);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.x * pstride] = dv[0];
+  if (last_block(counter)) {
+    sum_block_partials(part, pstride, 1, [&](int, double t) { D[L.vscale] = t > 0.0 ? 1.0 / sqrt(t) : 0.0; });
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+// Pass 1 on the binary16 basis: as the two-pass form of k_cgs_dots (dots
+// U^H w, the triangular solves, the scale of the new slot), with U_0 .. U_j
+// read as binary16 quads and w = A z_j (complex64) from its own buffer.
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_hb_dots(
+    HalfBasis hb, long long N, int nv, const float2* __restrict__ w, double* part, unsigned* counter,
+    const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R, int ldr, double* sc) {
+  if (ctl[CTL_DONE]) return;
+  extern __shared__ double2 red[];
+  __shared__ double sm[32];
+  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const long long nq = hb.np / 4, chunk = (long long)RED_THREADS * HB_QPT;
+  float nacc = 0.f;
+  for (long long qbase = blockIdx.x * chunk + threadIdx.x; qbase - threadIdx.x < nq; qbase += gridDim.x * chunk) {
+    float2 wk[HB_EPT];
+    hb_load_w(hb, w, qbase, nq, wk);
+#pragma unroll
+    for (int m = 0; m < HB_EPT; ++m) nacc += wk[m].x * wk[m].x + wk[m].y * wk[m].y;
+    hb_chunk_dots(hb, nv, qbase, nq, wk, red, nv);
+  }
+  pass1_finish((double)nacc, nv, red, sm, part, counter, vscale, d_out, c_out, R, ldr, sc, N);
+}
+
+// Pass 2 on the binary16 basis, step j = nv - 1: w' = w - sum_{i<=j} c1_i U_i
+// (c1 the U-basis coefficients from pass 1), stored as slot j+1 = s w'
+// rounded to binary16 (s = pass 1's scale, D[sc + SC_H16]).  The sums that
+// follow use the stored values, so slot j+1 is exactly what later steps
+// read: U^H u_{j+1} and ||u_{j+1}||^2.  The last block solves for d2 =
+// V^H u_{j+1}, stores c2 = vscale^2 d2 as column j+1 of R, and with
+// nsq = ||u_{j+1}||^2 - sum_i vscale_i^2 |d2_i|^2 (the squared norm of the
+// new direction, stored units) sets vscale_{j+1} = 1 / sqrt(nsq).  Since
+// w = sum_i V_i c1_i + u_{j+1} / s, the Hessenberg column in w's units is
+// h_ij = vscale_i (d1_i + d2_i / s) and h_{j+1,j} = sqrt(nsq) / s: d2 / s
+// goes to d_out and nsq / s^2 to the Givens step.
+__global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_hb_second(
+    HalfBasis hb, long long N, int nv, const float2* __restrict__ w, const double* __restrict__ c1,
+    const double* __restrict__ R, int ldr, double* part, unsigned* counter, const double* vscale, double* d_out,
+    double* D, int* ctl, DevLayout L) {
+  if (ctl[CTL_DONE]) return;
+  extern __shared__ double2 red[];
+  __shared__ float2 cs1[MAXV];
+  __shared__ double sm[32];
+  const int j = nv - 1;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs1[i] = make_float2((float)c1[2 * i], (float)c1[2 * i + 1]);
+  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const double sd = D[L.sc + SC_H16];
+  const float hs = (float)sd;
+  uint4* wout = reinterpret_cast<uint4*>(hb.V + (size_t)(j + 1) * hb.np);
+  const long long nq = hb.np / 4, chunk = (long long)RED_THREADS * HB_QPT;
+  float nacc = 0.f;
+  for (long long qbase = blockIdx.x * chunk + threadIdx.x; qbase - threadIdx.x < nq; qbase += gridDim.x * chunk) {
+    float2 wk[HB_EPT];
+    hb_load_w(hb, w, qbase, nq, wk);
+    for (int i0 = 0; i0 < nv; i0 += CG_QB) {
+      uint4 v[CG_QB][HB_QPT];
+      hb_load_group(hb, nv, i0, qbase, nq, v);
+#pragma unroll
+      for (int q = 0; q < CG_QB; ++q) {
+        if (i0 + q >= nv) break;
+        const float2 a = cs1[i0 + q];
+#pragma unroll
+        for (int m = 0; m < HB_EPT; ++m) {
+          const float2 x = hb_elem(v[q], m);
+          wk[m].x -= a.x * x.x - a.y * x.y;
+          wk[m].y -= a.x * x.y + a.y * x.x;
+        }
+      }
+    }
+    // the new slot (pads stay zero: w and every slot are zero there), and
+    // its stored values for the sums
+#pragma unroll
+    for (int k = 0; k < HB_QPT; ++k) {
+      const long long qd = qbase + k * RED_THREADS;
+      unsigned u[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        u[t] = hb_h2(hs * wk[4 * k + t].x, hs * wk[4 * k + t].y);
+        wk[4 * k + t] = hb_f2(u[t]);
+        nacc += wk[4 * k + t].x * wk[4 * k + t].x + wk[4 * k + t].y * wk[4 * k + t].y;
+      }
+      if (qd < nq) wout[qd] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    hb_chunk_dots(hb, nv, qbase, nq, wk, red, nv);
+  }
+  // block sums of the dots and of ||u_{j+1}||^2 in one table
+  const int G = gridDim.x;
+  double dv[1] = {(double)nacc};
+  block_sum<1>(dv, sm);
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < CG_WARPS; ++ww) {
+      sx += red[ww * nv + i].x;
+      sy += red[ww * nv + i].y;
+    }
+    part[(size_t)(2 * i) * G + blockIdx.x] = sx;
+    part[(size_t)(2 * i + 1) * G + blockIdx.x] = sy;
+  }
+  if (threadIdx.x == 0) part[(size_t)(2 * nv) * G + blockIdx.x] = dv[0];
+  if (!last_block(counter)) return;
+  __shared__ double un2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = warp; k <= 2 * nv; k += CG_WARPS) {
+    const double* pk = part + (size_t)k * G;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < G; b += 64) {
+      s0 += __ldcg(pk + b);
+      s1 += __ldcg(pk + b + 32);
+    }
+    if (b < G) s0 += __ldcg(pk + b);
+    double ssum = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ssum += __shfl_down_sync(0xffffffffu, ssum, o);
+    if (lane == 0) {
+      if (k < 2 * nv) {
+        if (k & 1) red[k >> 1].y = ssum;
+        else red[k >> 1].x = ssum;
+      } else {
+        un2 = ssum;
+      }
+    }
+  }
+  __syncthreads();
+  const bool staged = nv <= TRI_SMEM_MAX;
+  if (staged) {
+    tri_stage(red + nv, R, ldr, nv);
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) {
+    if (staged) tri_forward_h(red, RShared{red + nv}, nv);
+    else tri_forward_h(red, RGlobal{R, ldr}, nv);
+    double2* rcol = reinterpret_cast<double2*>(D + L.R) + (size_t)(j + 1) * ldr;
+    const double is = 1.0 / sd;
+    double corr = 0.0;
+    for (int l = lane; l < nv; l += 32) {
+      const double2 d = red[l];
+      const double vs2 = vscale[l] * vscale[l];
+      rcol[l] = make_double2(vs2 * d.x, vs2 * d.y);
+      d_out[2 * l] = d.x * is;
+      d_out[2 * l + 1] = d.y * is;
+      corr += vs2 * (d.x * d.x + d.y * d.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) corr += __shfl_down_sync(0xffffffffu, corr, o);
+    double nsq = 0.0;
+    if (lane == 0) {
+      nsq = un2 - corr;
+      nsq = nsq > 0.0 ? nsq : 0.0;
+      D[L.sc + SC_NORMSQ] = nsq * is * is;
+      *counter = 0;
+    }
+    __syncwarp();
+    givens_column(D, ctl, L, j);
+    if (lane == 0) D[L.vscale + j + 1] = nsq > 0.0 ? 1.0 / sqrt(nsq) : 0.0;
+  }
 }
 
 // r = b - Ax (or r = b when Ax == nullptr) written in the inner precision;
@@ -1149,7 +1468,7 @@ void sgi_free_gmres_work(sg_handle* h) {
   for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second.exec);
   if (w.stream) cudaStreamDestroy(w.stream);
   if (w.ev) cudaEventDestroy(w.ev);
-  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.Zb); cudaFree(w.V16); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
+  cudaFree(w.V); cudaFree(w.Z); cudaFree(w.Zb); cudaFree(w.V16); cudaFree(w.Vh); cudaFree(w.R64); cudaFree(w.X64); cudaFree(w.B64);
   cudaFree(w.dscal); cudaFree(w.dctl); cudaFree(w.part); cudaFree(w.counter);
   w = GmresWork{};
 }
@@ -1161,6 +1480,8 @@ static void cgs_attributes() {
   std::call_once(once, [] {
     const int bytes = CG_WARPS * MAXV * (int)sizeof(double2);
     cudaFuncSetAttribute(k_cgs_dots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_hb_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_hb_second, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_dots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1207,6 +1528,25 @@ static sg_status ensure_work(sg_handle* h, int m, int elem_bytes) {
       cudaFree(w.V16);   // no tensor map: the step keeps the complex64 transform 1
       w.V16 = nullptr;
     }
+    // the binary16 basis of the mixed solver's cycles (positions within a
+    // slot are ints)
+    const long long np = (long long)rows * (long long)mx4;
+    if (!e && w.V16 && np < (1LL << 31)) {
+      e = cudaMalloc(&w.Vh, (size_t)(m + 1) * np * sizeof(__half2));
+      if (!e) e = cudaMemset(w.Vh, 0, (size_t)(m + 1) * np * sizeof(__half2));
+      if (!e) {
+        w.vh_np = np;
+        w.vhmaps.resize(m + 1);
+        for (int i = 0; i <= m; ++i)
+          if (!tc_make_xmap16(&w.vhmaps[i], reinterpret_cast<__half2*>(w.Vh) + (size_t)i * np, (long long)mx4,
+                              (int)rows, h->mx)) {
+            cudaFree(w.Vh);   // no tensor maps: the cycles keep the complex64 basis
+            w.Vh = nullptr;
+            w.vhmaps.clear();
+            break;
+          }
+      }
+    }
   }
   if (!e) e = cudaMalloc(&w.R64, N * sizeof(double2));
   if (!e) e = cudaMalloc(&w.X64, N * sizeof(double2));
@@ -1245,7 +1585,27 @@ struct Ctx {
   int pstride;
   int cg_grid;   // blocks of the CGS2 passes
   bool left = false;   // left preconditioning: Arnoldi on M^-1 A
+  bool hb = false;     // flexible cycles on the binary16 basis (SG_MIXED, basis16 = 0)
 };
+
+// The workspace holds the binary16 basis and the binary16 route is in use.
+bool hb_available(const sg_handle* h) {
+  const GmresWork& w = h->gw;
+  return h->fd16 && !h->tune_tf32 && w.Vh && (int)w.vhmaps.size() == w.restart + 1 && w.prec_bytes == 8;
+}
+HalfBasis half_basis(const sg_handle* h) {
+  HalfBasis hb{};
+  const int mx = h->mx, mq = ((mx + 3) & ~3) / 4;   // quads per row
+  int sft = 0;
+  while ((1 << sft) < mq) ++sft;
+  hb.V = reinterpret_cast<__half2*>(h->gw.Vh);
+  hb.np = h->gw.vh_np;
+  hb.mulq = ((1ULL << (32 + sft)) + (unsigned long long)mq - 1) / (unsigned long long)mq;
+  hb.shiftq = 32 + sft;
+  hb.mx = mx;
+  hb.mx4 = 4 * mq;
+  return hb;
+}
 
 // Z = M^-1 (s R) with s = *in_scale (1 if null).
 template <typename T>
@@ -1310,6 +1670,28 @@ cudaError_t arnoldi_step(Ctx& c, sg_prec prec, int j) {
   // z = M^-1 v_j with v_j = vscale_j V_j (normalised on the fly, so the raw
   // basis norms stay of the size of h_{j+1,j})
   C2<T>* Z;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (c.hb && flexible<T>(c, prec)) {
+      // the binary16 basis: slot 0 converted from the cycle's residual at
+      // the first step, the preconditioner reading slot j itself
+      // (sqrt(N) v_j = sqrt(N) vscale_j u_j), w = A z_j into its own buffer
+      const HalfBasis hb = half_basis(c.h);
+      if (j == 0) {
+        k_hb_slot0<<<c.grid, RED_THREADS, 0, c.st>>>(reinterpret_cast<const float2*>(w.V), hb, D, w.dctl, c.L,
+                                                     w.part, c.pstride, w.counter, N);
+        note_launch();
+        if ((e = cudaGetLastError())) return e;
+      }
+      Z = reinterpret_cast<C2<T>*>(w.Zb) + (size_t)j * N;
+      const int which = prec == SG_PREC_MEAN ? 0 : 1;
+      if ((e = launch_precond_f16_copy(c.h, which, reinterpret_cast<const __half2*>(w.Vh) + (size_t)j * hb.np,
+                                       &w.vhmaps[j], Z, c.st, w.dctl, D + c.L.vscale + j,
+                                       (float)std::sqrt((double)N))))
+        return e;
+      if ((e = launch_matvec<T>(c.h, Z, reinterpret_cast<C2<T>*>(w.Z), c.st, w.dctl))) return e;
+      return cgs_passes<T>(c, prec, j);
+    }
+  }
   if (flexible<T>(c, prec)) {
     Z = reinterpret_cast<C2<T>*>(w.Zb) + (size_t)j * N;
     if constexpr (sizeof(T) == sizeof(float)) {
@@ -1347,6 +1729,22 @@ cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j, int only) {
   const int G = c.cg_grid;
   if (flexible<T>(c, prec)) {
     red_bytes = cgs_flex_smem_entries(nv, CG_WARPS) * sizeof(double2);
+    if (sizeof(T) == sizeof(float) && c.hb) {
+      const HalfBasis hb = half_basis(c.h);
+      const float2* wz = reinterpret_cast<const float2*>(w.Z);
+      if (only != 2) {
+        k_hb_dots<<<G, RED_THREADS, red_bytes, c.st>>>(hb, N, nv, wz, w.part, w.counter, D + c.L.vscale,
+                                                       D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.R, c.L.m + 1,
+                                                       D + c.L.sc);
+        note_launch();
+      }
+      if (only != 1) {
+        k_hb_second<<<G, RED_THREADS, red_bytes, c.st>>>(hb, N, nv, wz, D + c.L.c1, D + c.L.R, c.L.m + 1, w.part,
+                                                         w.counter, D + c.L.vscale, D + c.L.d2, D, w.dctl, c.L);
+        note_launch();
+      }
+      return cudaGetLastError();
+    }
     // two passes over unfinalised slots (the second projection kept in R;
     // flexible GMRES lets the preconditioner take the once-projected vector)
     // the binary16 route: pass 2 also writes w as the next step's binary16
@@ -1387,7 +1785,8 @@ template <typename T>
 cudaError_t arnoldi_steps(Ctx& c, sg_prec prec, int j0, int len) {
   GmresWork& w = c.h->gw;
   const unsigned long long key = ((unsigned long long)(sizeof(T) == 4) << 60) |
-                                 ((unsigned long long)(c.left ? 1 : 0) << 59) | ((unsigned long long)prec << 56) |
+                                 ((unsigned long long)(c.left ? 1 : 0) << 59) |
+                                 ((unsigned long long)(c.hb ? 1 : 0) << 58) | ((unsigned long long)prec << 55) |
                                  ((unsigned long long)j0 << 28) | (unsigned long long)len;
   auto it = w.graphs.find(key);
   if (it == w.graphs.end()) {
@@ -1556,6 +1955,8 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
     Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
     c.L = DevLayout(w.restart);
     c.left = left;
+    if (opts->basis16 != 0 && opts->basis16 != -1) return fail(SG_EINVAL, "basis16 must be 0 or -1");
+    c.hb = mixed && !left && opts->basis16 == 0 && flexible<float>(c, opts->prec) && hb_available(h);
     // the Hessenberg layout uses the allocated capacity; cycles use m <= capacity
     const size_t obytes = (size_t)N * (f32 ? sizeof(float2) : sizeof(double2));
 
@@ -1635,7 +2036,8 @@ extern "C" sg_status sg_gmres(sg_handle* h, const sg_gmres_opts* opts, const voi
       if (!(bnorm_ref > 0.0) || !std::isfinite(bnorm_ref)) return fail(SG_EBREAKDOWN, "||M^-1 b|| is zero or not finite");
     }
     const int max_outer = mixed ? (opts->max_outer <= 0 ? 20 : opts->max_outer) : 1 << 30;
-    const double inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
+    // (the binary16 basis limits a cycle's reduction to about 1e-3)
+    const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : c.hb ? 1e-3 : 1e-5;
     int iters = 0, cycles = 0, outer = 0;
     double relres = 1.0, relres_p = 1.0;
     int ctl[16];
@@ -1782,6 +2184,7 @@ sg_status time_cgs_passes(sg_handle* h, sg_prec prec, int j, int reps, cudaStrea
   if (!w.V || w.prec_bytes != (int)sizeof(float2) || j < 0 || j + 1 > w.restart || reps < 1)
     return fail(SG_EINVAL, "CGS2 timing needs a complex64 workspace with room for step j");
   Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+  c.hb = flexible<float>(c, prec) && hb_available(h);   // as the mixed solver's cycles run them
   // zero basis and scalars: the passes read and write the same amount
   // whatever the values; the done flag is cleared before every step so that
   // no pass skips its work
@@ -1833,6 +2236,7 @@ extern "C" sg_status sg_cgs2_pass(sg_handle* h, int restart, int j, int pass, vo
     if (!w.V || w.prec_bytes != (int)sizeof(float2) || j < 0 || j + 1 > w.restart)
       return fail(SG_EINVAL, "needs a complex64 workspace (pass 0) with room for step j");
     Ctx c{h, st, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+    c.hb = flexible<float>(c, pk) && hb_available(h);   // the mixed solver's default form
     if (!flexible<float>(c, pk) || !prec_available(h, pk))
       return fail(SG_EUNSUPPORTED, "the two-pass CGS2 form runs in the flexible cycles of 2D separable problems");
     if (pass == 0) {
@@ -2152,12 +2556,14 @@ cudaError_t bg_build(sg_handle* const* h, int count, const sg_gmres_opts* opts, 
   G.k_last.assign(count, 0);
   cudaError_t e = cudaGraphCreate(&G.graph, 0);
   if (!e) e = cudaMalloc((void**)&G.rec, (size_t)count * sizeof(BgRecord));
-  const double tol = opts->tol, inner_tol = opts->inner_tol <= 0 ? 1e-5 : opts->inner_tol;
+  const double tol = opts->tol;
   const int nch = (m + BG_CHUNK - 1) / BG_CHUNK;
   for (int s = 0; s < count && !e; ++s) {
     sg_handle* hs = h[s];
     GmresWork& w = hs->gw;
     Ctx c{hs, w.stream, DevLayout(w.restart), w.nblk, 2 * (MAXV + 2), w.cg_nblk};
+    c.hb = opts->basis16 == 0 && flexible<float>(c, opts->prec) && hb_available(hs);
+    const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : c.hb ? 1e-3 : 1e-5;
     const long long N = hs->N;
     const sg_prec prec = opts->prec;
     BgRecord* rec = G.rec + s;
@@ -2286,6 +2692,7 @@ bool sgi_batched_graph_eligible(const sg_gmres_opts* opts, const void* const* x0
   (void)x0;
   (void)count;
   if (opts->mode != SG_MIXED || opts->host_io || opts->x0 || opts->side != 0) return false;
+  if (opts->basis16 != 0 && opts->basis16 != -1) return false;   // (the per-system route reports it)
   if (opts->x0_policy != SG_X0_AS_GIVEN && opts->x0_policy != SG_X0_FALLBACK && opts->x0_policy != SG_X0_SCALED)
     return false;
   return opts->prec == SG_PREC_NONE || opts->prec == SG_PREC_MEAN || opts->prec == SG_PREC_CSL_MEAN;
@@ -2337,7 +2744,7 @@ sg_status sgi_batched_graph(sg_handle* const* h, int count, const sg_gmres_opts*
   std::memcpy(&ib, &itol, 8);
   key.push_back((uintptr_t)tb);
   key.push_back((uintptr_t)ib);
-  key.push_back((uintptr_t)opts->x0_policy);
+  key.push_back((uintptr_t)opts->x0_policy | ((uintptr_t)(opts->basis16 != 0) << 8));
   for (int k = 0; k < count; ++k) {
     key.push_back((uintptr_t)h[k]->gw.uid);
     key.push_back((uintptr_t)b[k]);

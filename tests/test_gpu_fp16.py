@@ -81,7 +81,8 @@ def test_fp16_route_in_mixed_gmres(B, g):
         op = B.SG(pr, tuned=False)
         op.tune_set({"tf32_transforms": tf32})
         x = torch.zeros_like(b)
-        info = op.gmres(b, x, restart=50, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000)
+        # (the complex64 basis in both, so that only the transforms differ)
+        info = op.gmres(b, x, restart=50, tol=1e-9, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000, basis16=-1)
         assert info["status"] == B.SG_OK
         relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
         assert relres <= 1e-9, (tf32, relres)
@@ -100,13 +101,15 @@ def test_fp16_route_absent_on_small_grids(B):
     op.close()
 
 
-@pytest.mark.parametrize("g,kind", [(96, "csl"), (129, "mean")])
-def test_fp16_copy_route_scale_invariant(B, g, kind):
-    """The flexible cycles' binary16 copy of each new basis vector (written by
-    the second CGS2 pass, read by the next step's binary16 transform 1) takes
-    its scale from that vector's norm: a right-hand side scaled by 2^-40 or
-    2^40 converges in the same number of steps (within 1) to the same
-    tolerance, and the result is the scaled solution."""
+@pytest.mark.parametrize("g,kind,basis16", [(96, "csl", -1), (129, "mean", -1), (96, "csl", 0), (129, "mean", 0)])
+def test_fp16_copy_route_scale_invariant(B, g, kind, basis16):
+    """The binary16 values of the flexible cycles take their scales from the
+    vectors' norms: the copy of each new basis vector that the second CGS2
+    pass writes beside the complex64 basis (basis16 = -1), and the binary16
+    basis itself (basis16 = 0, slot 0 scaled from the residual's norm).  A
+    right-hand side scaled by 2^-40 or 2^40 converges in the same number of
+    steps (within 1) to the same tolerance, and the result is the scaled
+    solution."""
     pr = inputs.helmholtz_2d(g, 3, 2, 25.0, 0.1)
     S = sg.assemble_problem(pr)
     prec = B.PREC_CSL_MEAN if kind == "csl" else B.PREC_MEAN
@@ -117,7 +120,7 @@ def test_fp16_copy_route_scale_invariant(B, g, kind):
         f = 2.0 ** e
         b = torch.from_numpy(S.b * f).to(DEV)
         x = torch.zeros_like(b)
-        info = op.gmres(b, x, restart=40, tol=1e-9, prec=prec, mode=B.MIXED, maxit=4000)
+        info = op.gmres(b, x, restart=40, tol=1e-9, prec=prec, mode=B.MIXED, maxit=4000, basis16=basis16)
         assert info["status"] == B.SG_OK, (e, info)
         xs = x.cpu().numpy() / f
         relres = np.linalg.norm(S.b - S.A @ xs) / np.linalg.norm(S.b)
@@ -205,4 +208,44 @@ def test_flexible_long_cycles(B, sigma):
     relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
     assert relres <= 1e-10, relres
     print("long cycles: sigma %.2f iters %d outer %d" % (sigma, info["iters"], info["outer"]))
+    op.close()
+
+
+@pytest.mark.parametrize("g,kind", [(96, "mean"), (127, "csl"), (160, "mean")])
+def test_binary16_basis_against_complex64(B, g, kind):
+    """SG_MIXED with the flexible cycles' Krylov basis stored as binary16
+    (basis16 = 0, the default on the binary16 route) against the complex64
+    basis (basis16 = -1): both reach the tolerance with the oracle's
+    residual; the binary16 basis limits a cycle's reduction to about 1e-3, so
+    it may take up to two more refinement steps, but no more than a third
+    more Arnoldi steps (plus 3)."""
+    pr = inputs.helmholtz_2d(g, 4, 3, 30.0, 0.15)
+    S = sg.assemble_problem(pr)
+    prec = B.PREC_CSL_MEAN if kind == "csl" else B.PREC_MEAN
+    b = torch.from_numpy(S.b).to(DEV)
+    res = {}
+    for basis16 in (-1, 0):
+        op = B.SG(pr, tuned=False)
+        assert op.info["fp16_route"] == 1
+        x = torch.zeros_like(b)
+        info = op.gmres(b, x, restart=40, tol=1e-9, prec=prec, mode=B.MIXED, maxit=4000, basis16=basis16)
+        assert info["status"] == B.SG_OK, (basis16, info)
+        relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
+        assert relres <= 1e-9, (basis16, relres)
+        assert abs(info["relres"] - relres) <= 1e-3 * relres + 1e-15
+        res[basis16] = info
+        op.close()
+    print("basis16: complex64 %d steps / %d refinements, binary16 %d / %d" %
+          (res[-1]["iters"], res[-1]["outer"], res[0]["iters"], res[0]["outer"]))
+    assert res[0]["iters"] <= (4 * res[-1]["iters"]) // 3 + 3, res
+    assert res[0]["outer"] <= res[-1]["outer"] + 2, res
+
+
+def test_binary16_basis_option_checked(B):
+    op = B.SG(inputs.helmholtz_2d(63, 2, 2, 15.0, 0.1), tuned=False)
+    b = torch.zeros(op.N, dtype=torch.complex128, device=DEV)
+    op.rhs(b, B.FP64)
+    with pytest.raises(B.SgError) as ei:
+        op.gmres(b, torch.zeros_like(b), restart=20, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, basis16=3)
+    assert ei.value.status == B.SG_EINVAL
     op.close()

@@ -16,8 +16,8 @@ Beside it the line reports: the plain FP64 GPU GMRES(30) on the same system
 (`fp64`, with the FP64 kernels against the measured FP64 FMA rate), the error
 of every mixed result against an FP64 GPU solve to 1e-12 (`error`), the
 end-to-end number through the C ABI with host buffers (`e2e`), the roofline
-of the dominant kernel (`roofline`: CGS2 pass 2, HBM) and of the tensor-core
-transform (`roofline_tensor`), the SG matvec bandwidth (`matvec`), the
+of the dominant kernel (`roofline`: the tensor-core transform) and of CGS2
+pass 2 (`roofline_cgs2`, HBM), the SG matvec bandwidth (`matvec`), the
 127 x 127 workload (`cfg2_127`), the 1D workload, the batched and learned
 warm-start legs, clocks sampled during the timed region, and the CPU oracle
 (`cpu_baseline`) on a bounded sample.
@@ -70,17 +70,18 @@ TRANSFORM_TRAFFIC = {
              "end": "// Check of the bounded wait",
              "sha256": "1c3a2958e35b2ae42c1747348c4c3e41e19dee986912c16e3e35e11f04f0d9ed", "bytes": 92444160 + 47176192},
 }
-# Arnoldi step of the CGS2 passes timed for the roofline (the mean step index
-# of the 511^2 solve's 39 steps is 9.3)
+# Arnoldi step of the CGS2 passes timed for their roofline (the step of the
+# traffic capture below; the 511^2 solve's 41 steps have mean index 6.4)
 CGS2_STEP = 10
-# DRAM bytes of one launch of CGS2 pass 2 (k_cgs2_second<float>, flexible form
-# with the binary16 copy, step 10) at 255^2, P = 84 (N_255 unknowns), from the
-# ncu capture summarised under profiles/, scaled to N unknowns (every term of
-# the pass's traffic is a multiple of N); reported while the pass's source (the
-# section of solver.cu between the markers, SHA-256 below) is unchanged.
-CGS2_TRAFFIC = {"begin": "// Two-pass form, pass 2 (flexible cycles)", "end": "// r = b - Ax (or r = b when Ax",
-                "sha256": "5fa2f8270ce484fa506ac992b24bcecc215091967a5baa854aeadf15196accfd",
-                "bytes": 526924288 + 93886208, "n": 255 * 255 * 84}
+# DRAM bytes of one launch of CGS2 pass 2 on the binary16 basis (k_hb_second,
+# step 10) at 255^2, P = 84 (np_255 binary16 pairs per basis slot), from the
+# ncu capture summarised under profiles/, scaled to the slot size np (every
+# term of the pass's traffic is a multiple of the unknowns); reported while
+# the pass's source (the section of solver.cu between the markers, SHA-256
+# below) is unchanged.
+CGS2_TRAFFIC = {"begin": "// Pass 2 on the binary16 basis", "end": "// r = b - Ax (or r = b when Ax",
+                "sha256": "366ae25281eb694f4b4d07fcf3115329a54a908cd46b8b114424f9a792927918",
+                "bytes": 286311168 + 18448384, "np": 84 * 255 * 256}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -143,11 +144,11 @@ def cgs2_section_sha():
     return hashlib.sha256(src[i:j].encode()).hexdigest()
 
 
-def cgs2_traffic(n):
+def cgs2_traffic(np_):
     t = CGS2_TRAFFIC
     if not t["sha256"] or not t["bytes"] or cgs2_section_sha() != t["sha256"]:
         return None
-    return t["bytes"] * n / t["n"]
+    return t["bytes"] * np_ / t["np"]
 
 
 def load_peaks():
@@ -681,12 +682,14 @@ def run_ours(args):
                "apply_ms": t_apply}
         # The CGS2 passes of one Arnoldi step of the flexible cycles, the
         # step's largest kernels (pass 2 the largest share of the solve):
-        # step j = CGS2_STEP on a zeroed workspace through sg_cgs2_pass, 20
-        # launches each with CUDA events on the solve's stream (each preceded
-        # by the pass's 64-byte clear of the done flag).  Algorithmic bytes:
-        # pass 1 reads V_0..V_j and w; pass 2 reads V_0..V_{j-1}, slot j and
-        # w, writes slots j and j+1 and, on the binary16 route, the binary16
-        # copy of slot j+1.
+        # step j = CGS2_STEP on a zeroed workspace through sg_cgs2_pass (the
+        # form the mixed solver runs: on the binary16 route the binary16
+        # basis), 20 launches each with CUDA events on the solve's stream
+        # (each preceded by the pass's 64-byte clear of the done flag).
+        # Algorithmic bytes with the binary16 basis (np pairs per slot, the
+        # padded rows): pass 1 reads slots 0..j and w (complex64); pass 2
+        # reads the same and writes slot j+1.  With the complex64 basis: pass
+        # 1 reads V_0..V_j and w, pass 2 reads V_0..V_j and w and writes w.
         jc = CGS2_STEP
         op.cgs2_pass(jc, 0, restart=solve["restart"])
         for _ in range(3):
@@ -694,22 +697,32 @@ def run_ours(args):
             op.cgs2_pass(jc, 2)
         t_p1 = event_ms(torch, stream, lambda: op.cgs2_pass(jc, 1), reps)
         t_p2 = event_ms(torch, stream, lambda: op.cgs2_pass(jc, 2), reps)
-        b_p1 = (jc + 2) * N * 8
-        b_p2 = (jc + 4) * N * 8 + (N * 4 if f16 else 0)
+        np_ = P * my * ((mx + 3) // 4 * 4)
+        if f16:
+            b_p1 = (jc + 1) * np_ * 4 + N * 8
+            b_p2 = (jc + 1) * np_ * 4 + N * 8 + np_ * 4
+            b_model = 2 * (jc + 1) * np_ * 4
+            kname = ("k_hb_second (CGS2 pass 2 of a flexible Arnoldi step on the binary16 basis, j = %d: "
+                     "projection update, the new slot in binary16, its dots and norm, Givens column)" % jc)
+            units = "(j + 2) np 4 B + N 8 B per launch (binary16 slots of np pairs), j = %d, np = %d, N = %d" % (
+                jc, np_, N)
+        else:
+            b_p1 = (jc + 2) * N * 8
+            b_p2 = (jc + 2) * N * 8 + N * 8
+            b_model = 2 * (jc + 1) * N * 8
+            kname = "k_cgs2_second<float> (CGS2 pass 2 of a flexible complex64 Arnoldi step, j = %d)" % jc
+            units = "(j + 3) N 8 B per launch, j = %d, N = %d" % (jc, N)
         hbm_peak, hbm_kind = load_peaks()
-        tr2 = cgs2_traffic(N) if f16 else None
-        cgs = {"kernel": "k_cgs2_second<float> (CGS2 pass 2 of a flexible complex64 Arnoldi step, j = %d: "
-                         "projection update of slots j and j+1%s, ||w||^2, Givens column)"
-                         % (jc, ", binary16 copy of slot j+1" if f16 else ""),
-               "bound": "hbm", "achieved": b_p2 / (t_p2 * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-               "frac": b_p2 / (t_p2 * 1e-3) / 1e9 / hbm_peak, "traffic": tr2,
+        tr2 = cgs2_traffic(np_) if f16 else None
+        cgs = {"kernel": kname, "bound": "hbm", "achieved": b_p2 / (t_p2 * 1e-3) / 1e9, "peak": hbm_peak,
+               "unit": "GB/s", "frac": b_p2 / (t_p2 * 1e-3) / 1e9 / hbm_peak, "traffic": tr2,
                "traffic_source": ("ncu capture of this kernel source at 255^2 (P = 84), step %d, scaled by "
-                                  "the unknowns (profiles/cgs2_step10_255x255_s6_deg3.md)" % jc) if tr2 else None,
-               "peak_kind": hbm_kind, "us_per_launch": 1000.0 * t_p2, "bytes_per_launch": b_p2,
-               "units": "(j + 4) N 8 B + N 4 B (binary16 copy) per launch, j = %d, N = %d" % (jc, N),
-               "pass1": {"kernel": "k_cgs_dots<float>", "us_per_launch": 1000.0 * t_p1, "bytes_per_launch": b_p1,
-                         "gbs": b_p1 / (t_p1 * 1e-3) / 1e9, "frac": b_p1 / (t_p1 * 1e-3) / 1e9 / hbm_peak},
-               "both_passes_model_frac": 2 * (jc + 1) * N * 8 / ((t_p1 + t_p2) * 1e-3) / 1e9 / hbm_peak}
+                                  "the slot size (profiles/cgs2_step10_255x255_s6_deg3.md)" % jc) if tr2 else None,
+               "peak_kind": hbm_kind, "us_per_launch": 1000.0 * t_p2, "bytes_per_launch": b_p2, "units": units,
+               "pass1": {"kernel": "k_hb_dots" if f16 else "k_cgs_dots<float>", "us_per_launch": 1000.0 * t_p1,
+                         "bytes_per_launch": b_p1, "gbs": b_p1 / (t_p1 * 1e-3) / 1e9,
+                         "frac": b_p1 / (t_p1 * 1e-3) / 1e9 / hbm_peak},
+               "both_passes_basis_model_frac": b_model / ((t_p1 + t_p2) * 1e-3) / 1e9 / hbm_peak}
 
     # ---------------------------------------------------------------- end to end with host buffers
     bh = torch.empty(N, dtype=torch.complex128, pin_memory=True)
@@ -832,13 +845,13 @@ def run_ours(args):
         "tuning": tuning,
     }
     # the dominant kernel of the step by share of the solve's kernel time is
-    # CGS2 pass 2 (HBM); the tensor-core transform's roofline beside it
-    if cgs:
-        line["roofline"] = cgs
-        if top:
-            line["roofline_tensor"] = top
-    elif top:
+    # the tensor-core transform (28.8 % of the 511^2 solve with the binary16
+    # basis, against 19.6 % for CGS2 pass 2, the largest HBM-bound kernel,
+    # whose roofline is reported beside it)
+    if top:
         line["roofline"] = top
+    if cgs:
+        line["roofline_cgs2"] = cgs
     if mv:
         line["matvec"] = mv
     if cfg2:

@@ -888,45 +888,6 @@ __device__ __forceinline__ float2 hb_elem(const uint4 (&v)[HB_QPT], int m) {
   const int t = m & 3;
   return hb_f2(t == 0 ? u.x : t == 1 ? u.y : t == 2 ? u.z : u.w);
 }
-// red[warp * ld + i] += warp sum of conj(U_i) w over the thread's elements,
-// eight slots at a time (chunk_dots on the binary16 basis).
-__device__ __forceinline__ void hb_chunk_dots(const HalfBasis& hb, int nv, long long qbase, long long nq,
-                                              const float2 (&wk)[HB_EPT], double2* red, int ld) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 < nv; i0 += 8) {
-    float acc[16];
-#pragma unroll
-    for (int qb = 0; qb < 8; qb += CG_QB) {
-      if (i0 + qb >= nv) {   // warp-uniform: a group with no slot left
-#pragma unroll
-        for (int q = 0; q < 2 * CG_QB; ++q) acc[2 * qb + q] = 0.f;
-        continue;
-      }
-      uint4 v[CG_QB][HB_QPT];
-      hb_load_group(hb, nv, i0 + qb, qbase, nq, v);
-#pragma unroll
-      for (int q = 0; q < CG_QB; ++q) {
-        float ax = 0.f, ay = 0.f;
-#pragma unroll
-        for (int m = 0; m < HB_EPT; ++m) {
-          const float2 x = hb_elem(v[q], m);
-          ax += x.x * wk[m].x + x.y * wk[m].y;
-          ay += x.x * wk[m].y - x.y * wk[m].x;
-        }
-        acc[2 * (qb + q)] = ax;
-        acc[2 * (qb + q) + 1] = ay;
-      }
-    }
-    const float sum = warp_sum16(acc);
-    if ((lane & 1) == 0) {
-      const int val = cg_value_of_lane(lane), i = i0 + (val >> 1);
-      if (i < nv) {
-        double2& r = red[warp * ld + i];
-        if (val & 1) r.y += (double)sum; else r.x += (double)sum;
-      }
-    }
-  }
-}
 
 // Slot 0 of a cycle: the starting residual r (complex64, in the workspace's
 // complex64 slot 0) stored as binary16 times sqrt(N) / 4 / ||r|| (||r||^2 in
@@ -964,51 +925,223 @@ __global__ void __launch_bounds__(RED_THREADS) k_hb_slot0(const float2* __restri
   }
 }
 
-// Pass 1 on the binary16 basis: as the two-pass form of k_cgs_dots (dots
-// U^H w, the triangular solves, the scale of the new slot), with U_0 .. U_j
-// read as binary16 quads and w = A z_j (complex64) from its own buffer.
+// red[warp * ld + i] += warp sums of conj(U_i) w and, at red[warp * ld + nv
+// + i], of conj(U_i) u (u = the newest slot's values) over the thread's
+// elements, for slots i < ns, four slots at a time.
+__device__ __forceinline__ void hb_chunk_dots2(const HalfBasis& hb, int ns, int nv, long long qbase, long long nq,
+                                               const float2 (&wk)[HB_EPT], const float2 (&uk)[HB_EPT],
+                                               double2* red, int ld) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < ns; i0 += CG_QB) {
+    uint4 v[CG_QB][HB_QPT];
+    hb_load_group(hb, ns, i0, qbase, nq, v);
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < CG_QB; ++q) {
+      float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll
+      for (int m = 0; m < HB_EPT; ++m) {
+        const float2 x = hb_elem(v[q], m);
+        ax += x.x * wk[m].x + x.y * wk[m].y;
+        ay += x.x * wk[m].y - x.y * wk[m].x;
+        bx += x.x * uk[m].x + x.y * uk[m].y;
+        by += x.x * uk[m].y - x.y * uk[m].x;
+      }
+      acc[4 * q] = ax;
+      acc[4 * q + 1] = ay;
+      acc[4 * q + 2] = bx;
+      acc[4 * q + 3] = by;
+    }
+    const float sum = warp_sum16(acc);
+    if ((lane & 1) == 0) {
+      const int val = cg_value_of_lane(lane), i = i0 + (val >> 2);
+      if (i < ns) {
+        double2& r = red[warp * ld + ((val >> 1) & 1) * nv + i];
+        if (val & 1) r.y += (double)sum; else r.x += (double)sum;
+      }
+    }
+  }
+}
+
+// Pass 1 on the binary16 basis, step j = nv - 1.  Slot j holds u_j, the
+// previous step's vector after one projection, stored as pass 2 left it:
+// its second projection is computed here, from the same reads, instead of in
+// pass 2 (delayed reorthogonalisation).  Sums: U_i^H w for i <= j, U_i^H u_j
+// for i < j, ||w||^2.  The last block
+//   1. turns U_{<j}^H u_j into d2 = V_{<j}^H u_j (forward substitution over
+//      R's first j columns), stores c2 = vscale^2 d2 as column j of R and
+//      vscale_j = 1 / sqrt(||u_j||^2 - sum_i vscale_i^2 |d2_i|^2), with
+//      ||u_j||^2 = 1 / vscale_j^2 as pass 2 stored it;
+//   2. turns U^H w into d1 = V^H w with all of R, c1 = vscale^2 d1, and
+//      stores the U-basis coefficients R^-1 c1 that pass 2 applies;
+//   3. stores the scale of the new slot, sqrt(N) / 4 over the projected norm
+//      of w (Pythagoras from d1, as in the complex64 form).
+// Dynamic shared memory: hb_dots_smem_entries(nv) double2.
+__host__ __device__ constexpr size_t hb_dots_smem_entries(int nv, int warps) {
+  return nv <= TRI_SMEM_MAX && (size_t)2 * nv + (size_t)nv * (nv - 1) / 2 > (size_t)warps * 2 * nv
+             ? (size_t)2 * nv + (size_t)nv * (nv - 1) / 2
+             : (size_t)warps * 2 * nv;
+}
 __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_hb_dots(
     HalfBasis hb, long long N, int nv, const float2* __restrict__ w, double* part, unsigned* counter,
-    const double* vscale, double* d_out, double* c_out, const int* ctl, const double* R, int ldr, double* sc) {
+    double* vscale, double* d_out, double* c_out, const int* ctl, double* R, int ldr, double* sc) {
   if (ctl[CTL_DONE]) return;
   extern __shared__ double2 red[];
   __shared__ double sm[32];
-  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
+  const int j = nv - 1, ld = 2 * nv;
+  for (int i = threadIdx.x; i < CG_WARPS * ld; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
   __syncthreads();
   const long long nq = hb.np / 4, chunk = (long long)RED_THREADS * HB_QPT;
-  float nacc = 0.f;
+  const uint4* uj = reinterpret_cast<const uint4*>(hb.V + (size_t)j * hb.np);
+  float nacc = 0.f, ex = 0.f, ey = 0.f;
   for (long long qbase = blockIdx.x * chunk + threadIdx.x; qbase - threadIdx.x < nq; qbase += gridDim.x * chunk) {
-    float2 wk[HB_EPT];
+    float2 wk[HB_EPT], uk[HB_EPT];
     hb_load_w(hb, w, qbase, nq, wk);
 #pragma unroll
-    for (int m = 0; m < HB_EPT; ++m) nacc += wk[m].x * wk[m].x + wk[m].y * wk[m].y;
-    hb_chunk_dots(hb, nv, qbase, nq, wk, red, nv);
+    for (int k = 0; k < HB_QPT; ++k) {
+      const long long qd = qbase + k * RED_THREADS;
+      const uint4 u = qd < nq ? __ldg(uj + qd) : make_uint4(0u, 0u, 0u, 0u);
+      uk[4 * k] = hb_f2(u.x);
+      uk[4 * k + 1] = hb_f2(u.y);
+      uk[4 * k + 2] = hb_f2(u.z);
+      uk[4 * k + 3] = hb_f2(u.w);
+    }
+#pragma unroll
+    for (int m = 0; m < HB_EPT; ++m) {
+      nacc += wk[m].x * wk[m].x + wk[m].y * wk[m].y;
+      ex += uk[m].x * wk[m].x + uk[m].y * wk[m].y;   // u_j^H w from registers
+      ey += uk[m].x * wk[m].y - uk[m].y * wk[m].x;
+    }
+    hb_chunk_dots2(hb, j, nv, qbase, nq, wk, uk, red, ld);
   }
-  pass1_finish((double)nacc, nv, red, sm, part, counter, vscale, d_out, c_out, R, ldr, sc, N);
+  ex = warp_sum(ex);
+  ey = warp_sum(ey);
+  if ((threadIdx.x & 31) == 0) {
+    double2& r = red[(threadIdx.x >> 5) * ld + j];
+    r.x += (double)ex;
+    r.y += (double)ey;
+  }
+  // block sums: rows 0 .. 2 nv - 1 of the table (U^H w, then U_{<j}^H u_j),
+  // row 2 nv ||w||^2
+  const int G = gridDim.x;
+  double dv[1] = {(double)nacc};
+  block_sum<1>(dv, sm);   // (synchronises the block: the table is complete)
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int ww = 0; ww < CG_WARPS; ++ww) {
+      sx += red[ww * ld + i].x;
+      sy += red[ww * ld + i].y;
+    }
+    part[(size_t)(2 * i) * G + blockIdx.x] = sx;
+    part[(size_t)(2 * i + 1) * G + blockIdx.x] = sy;
+  }
+  if (threadIdx.x == 0) part[(size_t)(2 * ld) * G + blockIdx.x] = dv[0];
+  if (!last_block(counter)) return;
+  __shared__ double wn2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // sums over blocks: e = U^H w into red[0 .. nv), f = U_{<j}^H u_j into
+  // red[nv .. nv + j); R's staged triangle from red[2 nv]
+  for (int k = warp; k <= 2 * ld; k += CG_WARPS) {
+    const double* pk = part + (size_t)k * G;
+    double s0 = 0.0, s1 = 0.0;
+    int b = lane;
+    for (; b + 32 < G; b += 64) {
+      s0 += __ldcg(pk + b);
+      s1 += __ldcg(pk + b + 32);
+    }
+    if (b < G) s0 += __ldcg(pk + b);
+    double ssum = s0 + s1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ssum += __shfl_down_sync(0xffffffffu, ssum, o);
+    if (lane == 0) {
+      if (k < 2 * ld) {
+        if (k & 1) red[k >> 1].y = ssum;
+        else red[k >> 1].x = ssum;
+      } else {
+        wn2 = ssum;
+      }
+    }
+  }
+  __syncthreads();
+  double2* rt = red + 2 * nv;
+  const bool staged = nv <= TRI_SMEM_MAX;
+  if (staged) {
+    tri_stage(rt, R, ldr, j);   // columns 1 .. j-1; column j follows from step 1
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) {
+    double2* t = red;          // e
+    double2* f = red + nv;     // f
+    if (j > 0) {
+      if (staged) tri_forward_h(f, RShared{rt}, j);
+      else tri_forward_h(f, RGlobal{R, ldr}, j);
+      double2* rcol = reinterpret_cast<double2*>(R) + (size_t)j * ldr;
+      double corr = 0.0;
+      for (int l = lane; l < j; l += 32) {
+        const double2 d = f[l];
+        const double vs2 = vscale[l] * vscale[l];
+        const double2 c = make_double2(vs2 * d.x, vs2 * d.y);
+        rcol[l] = c;
+        if (staged) rt[j * (j - 1) / 2 + l] = c;
+        corr += vs2 * (d.x * d.x + d.y * d.y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) corr += __shfl_xor_sync(0xffffffffu, corr, o);
+      const double vj = vscale[j];
+      const double un2 = vj > 0.0 ? 1.0 / (vj * vj) : 0.0;
+      const double nsq = un2 - corr;
+      __syncwarp();
+      if (lane == 0) vscale[j] = nsq > 0.0 ? 1.0 / sqrt(nsq) : vj;
+      __syncwarp();
+    }
+    if (staged) tri_forward_h(t, RShared{rt}, nv);
+    else tri_forward_h(t, RGlobal{R, ldr}, nv);
+    double corr1 = 0.0;
+    for (int l = lane; l < nv; l += 32) {
+      const double2 d = t[l];
+      d_out[2 * l] = d.x;
+      d_out[2 * l + 1] = d.y;
+      const double vs2 = vscale[l] * vscale[l];
+      t[l] = make_double2(vs2 * d.x, vs2 * d.y);
+      corr1 += vs2 * (d.x * d.x + d.y * d.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) corr1 += __shfl_xor_sync(0xffffffffu, corr1, o);
+    __syncwarp();
+    if (staged) tri_back(t, RShared{rt}, nv);
+    else tri_back(t, RGlobal{R, ldr}, nv);
+    for (int l = lane; l < nv; l += 32) {
+      c_out[2 * l] = t[l].x;
+      c_out[2 * l + 1] = t[l].y;
+    }
+    if (lane == 0) {
+      const double est2 = fmax(wn2 - corr1, 1e-8 * wn2);
+      const double q = 0.25 * sqrt((double)N);
+      sc[SC_H16] = est2 > 0.0 && est2 < 1e300 ? q / sqrt(est2) : 1.0;
+      *counter = 0;
+    }
+  }
 }
 
 // Pass 2 on the binary16 basis, step j = nv - 1: w' = w - sum_{i<=j} c1_i U_i
 // (c1 the U-basis coefficients from pass 1), stored as slot j+1 = s w'
-// rounded to binary16 (s = pass 1's scale, D[sc + SC_H16]).  The sums that
-// follow use the stored values, so slot j+1 is exactly what later steps
-// read: U^H u_{j+1} and ||u_{j+1}||^2.  The last block solves for d2 =
-// V^H u_{j+1}, stores c2 = vscale^2 d2 as column j+1 of R, and with
-// nsq = ||u_{j+1}||^2 - sum_i vscale_i^2 |d2_i|^2 (the squared norm of the
-// new direction, stored units) sets vscale_{j+1} = 1 / sqrt(nsq).  Since
-// w = sum_i V_i c1_i + u_{j+1} / s, the Hessenberg column in w's units is
-// h_ij = vscale_i (d1_i + d2_i / s) and h_{j+1,j} = sqrt(nsq) / s: d2 / s
-// goes to d_out and nsq / s^2 to the Givens step.
+// rounded to binary16 (s = pass 1's scale, D[sc + SC_H16]), and the squared
+// norm of the stored slot, ||u_{j+1}||^2.  No dots: the second projection of
+// slot j+1 comes from the next step's pass 1.  The Hessenberg column takes
+// the first projection only, h_ij = vscale_i d1_i and h_{j+1,j} =
+// ||u_{j+1}|| / s: the second projection's part, vscale_i d2_i / s, is of the
+// size of the FP32 first pass's rounding, far below the binary16 storage's
+// (about 5e-4 of the slot), which bounds the cycle's Arnoldi relation
+// anyway.  vscale_{j+1} = 1 / ||u_{j+1}|| until the next pass 1 refines it.
 __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_hb_second(
     HalfBasis hb, long long N, int nv, const float2* __restrict__ w, const double* __restrict__ c1,
-    const double* __restrict__ R, int ldr, double* part, unsigned* counter, const double* vscale, double* d_out,
-    double* D, int* ctl, DevLayout L) {
+    double* part, unsigned* counter, double* d_out, double* D, int* ctl, DevLayout L) {
   if (ctl[CTL_DONE]) return;
-  extern __shared__ double2 red[];
   __shared__ float2 cs1[MAXV];
   __shared__ double sm[32];
   const int j = nv - 1;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) cs1[i] = make_float2((float)c1[2 * i], (float)c1[2 * i + 1]);
-  for (int i = threadIdx.x; i < CG_WARPS * nv; i += blockDim.x) red[i] = make_double2(0.0, 0.0);
   __syncthreads();
   const double sd = D[L.sc + SC_H16];
   const float hs = (float)sd;
@@ -1033,8 +1166,7 @@ __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_hb_second(
         }
       }
     }
-    // the new slot (pads stay zero: w and every slot are zero there), and
-    // its stored values for the sums
+    // the new slot (pads stay zero: w and every slot are zero there)
 #pragma unroll
     for (int k = 0; k < HB_QPT; ++k) {
       const long long qd = qbase + k * RED_THREADS;
@@ -1042,84 +1174,33 @@ __global__ void __launch_bounds__(RED_THREADS, CG_MIN_BLOCKS_C64) k_hb_second(
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         u[t] = hb_h2(hs * wk[4 * k + t].x, hs * wk[4 * k + t].y);
-        wk[4 * k + t] = hb_f2(u[t]);
-        nacc += wk[4 * k + t].x * wk[4 * k + t].x + wk[4 * k + t].y * wk[4 * k + t].y;
+        const float2 f = hb_f2(u[t]);
+        nacc += f.x * f.x + f.y * f.y;
       }
       if (qd < nq) wout[qd] = make_uint4(u[0], u[1], u[2], u[3]);
     }
-    hb_chunk_dots(hb, nv, qbase, nq, wk, red, nv);
   }
-  // block sums of the dots and of ||u_{j+1}||^2 in one table
-  const int G = gridDim.x;
   double dv[1] = {(double)nacc};
   block_sum<1>(dv, sm);
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    double sx = 0.0, sy = 0.0;
-#pragma unroll
-    for (int ww = 0; ww < CG_WARPS; ++ww) {
-      sx += red[ww * nv + i].x;
-      sy += red[ww * nv + i].y;
-    }
-    part[(size_t)(2 * i) * G + blockIdx.x] = sx;
-    part[(size_t)(2 * i + 1) * G + blockIdx.x] = sy;
-  }
-  if (threadIdx.x == 0) part[(size_t)(2 * nv) * G + blockIdx.x] = dv[0];
+  if (threadIdx.x == 0) part[blockIdx.x] = dv[0];
   if (!last_block(counter)) return;
   __shared__ double un2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = warp; k <= 2 * nv; k += CG_WARPS) {
-    const double* pk = part + (size_t)k * G;
-    double s0 = 0.0, s1 = 0.0;
-    int b = lane;
-    for (; b + 32 < G; b += 64) {
-      s0 += __ldcg(pk + b);
-      s1 += __ldcg(pk + b + 32);
-    }
-    if (b < G) s0 += __ldcg(pk + b);
-    double ssum = s0 + s1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ssum += __shfl_down_sync(0xffffffffu, ssum, o);
-    if (lane == 0) {
-      if (k < 2 * nv) {
-        if (k & 1) red[k >> 1].y = ssum;
-        else red[k >> 1].x = ssum;
-      } else {
-        un2 = ssum;
-      }
-    }
-  }
+  sum_block_partials(part, 1, 1, [&](int, double t) { un2 = t; });
   __syncthreads();
-  const bool staged = nv <= TRI_SMEM_MAX;
-  if (staged) {
-    tri_stage(red + nv, R, ldr, nv);
-    __syncthreads();
-  }
   if (threadIdx.x < 32) {
-    if (staged) tri_forward_h(red, RShared{red + nv}, nv);
-    else tri_forward_h(red, RGlobal{R, ldr}, nv);
-    double2* rcol = reinterpret_cast<double2*>(D + L.R) + (size_t)(j + 1) * ldr;
-    const double is = 1.0 / sd;
-    double corr = 0.0;
+    const int lane = threadIdx.x;
     for (int l = lane; l < nv; l += 32) {
-      const double2 d = red[l];
-      const double vs2 = vscale[l] * vscale[l];
-      rcol[l] = make_double2(vs2 * d.x, vs2 * d.y);
-      d_out[2 * l] = d.x * is;
-      d_out[2 * l + 1] = d.y * is;
-      corr += vs2 * (d.x * d.x + d.y * d.y);
+      d_out[2 * l] = 0.0;
+      d_out[2 * l + 1] = 0.0;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) corr += __shfl_down_sync(0xffffffffu, corr, o);
-    double nsq = 0.0;
+    const double is = sd > 0.0 ? 1.0 / sd : 0.0;
     if (lane == 0) {
-      nsq = un2 - corr;
-      nsq = nsq > 0.0 ? nsq : 0.0;
-      D[L.sc + SC_NORMSQ] = nsq * is * is;
+      D[L.sc + SC_NORMSQ] = un2 * is * is;
       *counter = 0;
     }
     __syncwarp();
     givens_column(D, ctl, L, j);
-    if (lane == 0) D[L.vscale + j + 1] = nsq > 0.0 ? 1.0 / sqrt(nsq) : 0.0;
+    if (lane == 0) D[L.vscale + j + 1] = un2 > 0.0 ? 1.0 / sqrt(un2) : 0.0;
   }
 }
 
@@ -1480,8 +1561,7 @@ static void cgs_attributes() {
   std::call_once(once, [] {
     const int bytes = CG_WARPS * MAXV * (int)sizeof(double2);
     cudaFuncSetAttribute(k_cgs_dots<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_hb_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_hb_second, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_hb_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * bytes);   // (two dot sets)
     cudaFuncSetAttribute(k_cgs_dots<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_cgs_update<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -1733,14 +1813,14 @@ cudaError_t cgs_passes(Ctx& c, sg_prec prec, int j, int only) {
       const HalfBasis hb = half_basis(c.h);
       const float2* wz = reinterpret_cast<const float2*>(w.Z);
       if (only != 2) {
-        k_hb_dots<<<G, RED_THREADS, red_bytes, c.st>>>(hb, N, nv, wz, w.part, w.counter, D + c.L.vscale,
-                                                       D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.R, c.L.m + 1,
-                                                       D + c.L.sc);
+        k_hb_dots<<<G, RED_THREADS, hb_dots_smem_entries(nv, CG_WARPS) * sizeof(double2), c.st>>>(
+            hb, N, nv, wz, w.part, w.counter, D + c.L.vscale, D + c.L.d1, D + c.L.c1, w.dctl, D + c.L.R,
+            c.L.m + 1, D + c.L.sc);
         note_launch();
       }
       if (only != 1) {
-        k_hb_second<<<G, RED_THREADS, red_bytes, c.st>>>(hb, N, nv, wz, D + c.L.c1, D + c.L.R, c.L.m + 1, w.part,
-                                                         w.counter, D + c.L.vscale, D + c.L.d2, D, w.dctl, c.L);
+        k_hb_second<<<G, RED_THREADS, 0, c.st>>>(hb, N, nv, wz, D + c.L.c1, w.part, w.counter, D + c.L.d2, D,
+                                                 w.dctl, c.L);
         note_launch();
       }
       return cudaGetLastError();

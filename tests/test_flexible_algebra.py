@@ -237,10 +237,14 @@ def half_basis_flexible_arnoldi(A, minv, r0, m, store):
     on the binary16 route), with the quantities its kernels keep: stored
     slots u_k = store(s_k w_k') at a per-slot scale s_k (pass 1's, from the
     projected norm), vscale_k of the stored directions, R of the stored
-    slots; the Hessenberg column in w's units h_ij = vscale_i (d1_i + d2_i /
-    s) and h_{j+1,j} = sqrt(nsq) / s, nsq = ||u_{j+1}||^2 - sum vscale_i^2
-    |d2_i|^2 from the stored values.  Returns (V, Z, H) with V = U R^-1
-    scaled by vscale (the stored directions, normalised)."""
+    slots.  Pass 2 only projects once and stores: the Hessenberg column in
+    w's units is h_ij = vscale_i d1_i, h_{j+1,j} = ||u_{j+1}|| / s, and
+    vscale_{j+1} = 1 / ||u_{j+1}||.  The next step's pass 1 computes the new
+    slot's second projection from the same reads: d2 = R^-H U^H u_j over the
+    first j slots, column j of R = vscale^2 d2, and vscale_j = 1 / sqrt(
+    ||u_j||^2 - sum vscale_i^2 |d2_i|^2).  Returns (V, Z, H) with V = U R^-1
+    scaled by vscale (the stored directions, normalised; the last slot's
+    second projection applied at the end, as the next pass 1 would)."""
     n = r0.size
     U = np.zeros((m + 1, n), dtype=complex)
     vs = np.zeros(m + 1)
@@ -248,11 +252,19 @@ def half_basis_flexible_arnoldi(A, minv, r0, m, store):
     s0 = 0.25 * np.sqrt(n) / np.linalg.norm(r0)
     U[0] = store(s0 * r0)
     vs[0] = 1.0 / np.linalg.norm(U[0])
+
+    def second_projection(j):
+        d2 = _fwd_h(R[:j, :j], U[:j].conj() @ U[j])
+        R[:j, j] = vs[:j] ** 2 * d2
+        vs[j] = 1.0 / np.sqrt(1.0 / vs[j] ** 2 - np.sum(vs[:j] ** 2 * np.abs(d2) ** 2))
+
     Z = np.zeros((m, n), dtype=complex)
     H = np.zeros((m + 1, m), dtype=complex)
     for j in range(m):
         Z[j] = minv(vs[j] * U[j])
         w = A @ Z[j]
+        if j > 0:
+            second_projection(j)
         Rj = R[: j + 1, : j + 1]
         d1 = _fwd_h(Rj, U[: j + 1].conj() @ w)
         c1 = vs[: j + 1] ** 2 * d1
@@ -260,13 +272,12 @@ def half_basis_flexible_arnoldi(A, minv, r0, m, store):
         s = 0.25 * np.sqrt(n) / np.sqrt(est2)
         w1 = w - _back(Rj, c1) @ U[: j + 1]
         u = store(s * w1)
-        d2 = _fwd_h(Rj, U[: j + 1].conj() @ u)
-        nsq = np.vdot(u, u).real - np.sum(vs[: j + 1] ** 2 * np.abs(d2) ** 2)
-        H[: j + 1, j] = vs[: j + 1] * (d1 + d2 / s)
-        H[j + 1, j] = np.sqrt(nsq) / s
-        vs[j + 1] = 1.0 / np.sqrt(nsq)
+        un = np.linalg.norm(u)
+        H[: j + 1, j] = vs[: j + 1] * d1
+        H[j + 1, j] = un / s
+        vs[j + 1] = 1.0 / un
         U[j + 1] = u
-        R[: j + 1, j + 1] = vs[: j + 1] ** 2 * d2
+    second_projection(m)
     V = (U.T @ np.linalg.inv(R)) * vs[None, :]
     return V, Z.T, H
 
@@ -278,10 +289,10 @@ def _round_h16(v):
 def test_half_basis_units():
     """Exact storage at scales far from 1: the stored-unit bookkeeping gives
     the flexible Arnoldi relation to rounding and orthonormal directions, so
-    a slip in a scale factor (d2 / s, sqrt(nsq) / s, vscale from the stored
-    slot) fails here.  Binary16 storage: the relation holds to the storage's
-    rounding (about 5e-4 of the scale) and the directions stay orthonormal to
-    the same order."""
+    a slip in a scale factor (||u|| / s, vscale from the stored slot, the
+    delayed second projection) fails here.  Binary16 storage: the relation
+    holds to the storage's rounding (about 5e-4 of the scale), and the
+    directions of the stored slots are orthonormal."""
     rng = np.random.default_rng(11)
     n, m = 150, 20
     A = np.eye(n) * 4 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)

@@ -932,25 +932,33 @@ __device__ __forceinline__ void hb_chunk_dots2(const HalfBasis& hb, int ns, int 
                                                const float2 (&wk)[HB_EPT], const float2 (&uk)[HB_EPT],
                                                double2* red, int ld) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float2 ws[HB_EPT], us[HB_EPT];
+#pragma unroll
+  for (int m = 0; m < HB_EPT; ++m) {
+    ws[m] = make_float2(wk[m].y, -wk[m].x);
+    us[m] = make_float2(uk[m].y, -uk[m].x);
+  }
   for (int i0 = 0; i0 < ns; i0 += CG_QB) {
     uint4 v[CG_QB][HB_QPT];
     hb_load_group(hb, ns, i0, qbase, nq, v);
     float acc[16];
 #pragma unroll
     for (int q = 0; q < CG_QB; ++q) {
-      float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+      // packed FP32 FMAs: (x.x, x.y) * (w.x, w.y) sums to Re conj(x) w and
+      // (x.x, x.y) * (w.y, -w.x) to Im conj(x) w (ws, us: the swapped pairs)
+      float2 pa = make_float2(0.f, 0.f), pb = pa, pc = pa, pd = pa;
 #pragma unroll
       for (int m = 0; m < HB_EPT; ++m) {
         const float2 x = hb_elem(v[q], m);
-        ax += x.x * wk[m].x + x.y * wk[m].y;
-        ay += x.x * wk[m].y - x.y * wk[m].x;
-        bx += x.x * uk[m].x + x.y * uk[m].y;
-        by += x.x * uk[m].y - x.y * uk[m].x;
+        pa = __ffma2_rn(x, wk[m], pa);
+        pb = __ffma2_rn(x, ws[m], pb);
+        pc = __ffma2_rn(x, uk[m], pc);
+        pd = __ffma2_rn(x, us[m], pd);
       }
-      acc[4 * q] = ax;
-      acc[4 * q + 1] = ay;
-      acc[4 * q + 2] = bx;
-      acc[4 * q + 3] = by;
+      acc[4 * q] = pa.x + pa.y;
+      acc[4 * q + 1] = pb.x + pb.y;
+      acc[4 * q + 2] = pc.x + pc.y;
+      acc[4 * q + 3] = pd.x + pd.y;
     }
     const float sum = warp_sum16(acc);
     if ((lane & 1) == 0) {

@@ -1221,7 +1221,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual(const C2<TO>* __restri
   __shared__ double sm[32];
   const long long stride = (long long)gridDim.x * blockDim.x;
   TO nacc = TO(0);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+  // four elements a thread per round, all loads issued first (the grid is a
+  // few blocks per SM: one load in flight per thread left HBM half idle)
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < N; e += 4 * stride) {
+    C2<TO> v[4], a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = b[e + k * stride];
+      a[k] = Ax ? Ax[e + k * stride] : mkc<TO>(TO(0), TO(0));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k].x -= a[k].x;
+      v[k].y -= a[k].y;
+      if (r) r[e + k * stride] = mkc<TI>((TI)v[k].x, (TI)v[k].y);
+      nacc += v[k].x * v[k].x + v[k].y * v[k].y;
+    }
+  }
+  for (; e < N; e += stride) {
     C2<TO> v = b[e];
     if (Ax) {
       const C2<TO> a = Ax[e];
@@ -1473,7 +1491,23 @@ template <typename TX, typename TZ>
 __global__ void k_axpy(C2<TX>* __restrict__ x, const C2<TZ>* __restrict__ z, long long N, const int* ctl) {
   if (ctl && ctl[CTL_K] == 0) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += stride) {
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < N; e += 4 * stride) {   // four elements a round, loads first
+    C2<TZ> v[4];
+    C2<TX> a[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = z[e + k * stride];
+      a[k] = x[e + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k].x += (TX)v[k].x;
+      a[k].y += (TX)v[k].y;
+      x[e + k * stride] = a[k];
+    }
+  }
+  for (; e < N; e += stride) {
     const C2<TZ> v = z[e];
     C2<TX> a = x[e];
     a.x += (TX)v.x;

@@ -80,8 +80,8 @@ CGS2_STEP = 10
 # the pass's source (the section of solver.cu between the markers, SHA-256
 # below) is unchanged.
 CGS2_TRAFFIC = {"begin": "// Pass 2 on the binary16 basis", "end": "// r = b - Ax (or r = b when Ax",
-                "sha256": "366ae25281eb694f4b4d07fcf3115329a54a908cd46b8b114424f9a792927918",
-                "bytes": 286311168 + 18448384, "np": 84 * 255 * 256}
+                "sha256": "c603c346f722fbd04065f579f7bc9ad3039d8afb2e4c6289954f33d98c9790a7",
+                "bytes": 285044736 + 17458688, "np": 84 * 255 * 256}
 # Dense TF32 / BF16 tensor throughput, nominal (2D preconditioner transforms run on
 # TF32 tensor cores; their peak is the measured BF16 peak times this ratio).
 TF32_PER_BF16 = 1.1 / 2.25
@@ -703,7 +703,7 @@ def run_ours(args):
             b_p2 = (jc + 1) * np_ * 4 + N * 8 + np_ * 4
             b_model = 2 * (jc + 1) * np_ * 4
             kname = ("k_hb_second (CGS2 pass 2 of a flexible Arnoldi step on the binary16 basis, j = %d: "
-                     "projection update, the new slot in binary16, its dots and norm, Givens column)" % jc)
+                     "projection update, the new slot in binary16 and its norm, Givens column)" % jc)
             units = "(j + 2) np 4 B + N 8 B per launch (binary16 slots of np pairs), j = %d, np = %d, N = %d" % (
                 jc, np_, N)
         else:

@@ -458,17 +458,18 @@ sg_status sg_fd_transform(sg_handle* h, sg_prec kind, sg_precision prec, int t, 
 
 /* One pass of the CGS2 orthogonalisation of Arnoldi step j in the complex64
  * flexible cycles that SG_MIXED runs with the mean-value preconditioner on 2D
- * separable problems (the step's largest kernels), launched on `stream` over
- * the handle's GMRES workspace so that a caller can time it with events on
- * that stream:
+ * separable problems (the step's largest kernels), in the form sg_gmres runs
+ * by default (on the binary16 route: the binary16 basis), launched on
+ * `stream` over the handle's GMRES workspace so that a caller can time it
+ * with events on that stream:
  *   pass 0  prepares: sizes the workspace for GMRES(restart) (restart <= 0:
  *           30) as sg_gmres would and zeroes basis slots 0..j+1 and the
  *           device scalars;
- *   pass 1  V_0..V_j^H w (w = slot j+1), and on the binary16 route ||w||^2
- *           for the scale of the basis vector's binary16 copy;
- *   pass 2  the projection update of slots j and j+1, the binary16 copy of
- *           slot j+1 where the route is active, ||w||^2 and the Givens
- *           column of step j.
+ *   pass 1  the dots of w (the operator's output) with slots 0..j and, on
+ *           the binary16 basis, of slot j with slots 0..j-1 (its delayed
+ *           second projection), and the scale of the new slot;
+ *   pass 2  the projection update of w, the new slot j+1 (binary16 on the
+ *           binary16 basis), its norm and the Givens column of step j.
  * Values are meaningless (zeros); the work and the memory traffic are a
  * step's.  Each pass first clears the workspace's done flag (a 64-byte
  * memset on the stream).  SG_EINVAL for j out of the workspace or a pass out

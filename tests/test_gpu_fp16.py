@@ -191,23 +191,25 @@ def test_paired_256_form_refused_without_fp16_route(B):
     op.close()
 
 
-@pytest.mark.parametrize("sigma", [0.25, 0.35])
-def test_flexible_long_cycles(B, sigma):
+@pytest.mark.parametrize("sigma,basis16", [(0.25, 0), (0.35, 0), (0.35, -1), (0.45, 0)])
+def test_flexible_long_cycles(B, sigma, basis16):
     """Flexible cycles longer than 64 steps (the CGS2 passes then read the
     basis factor R from device memory instead of staging it in shared
-    memory): a strongly varying wavenumber and a tight inner reduction make
-    the cycles long; the solve still reaches the tolerance with the oracle's
-    residual."""
+    memory), on the binary16 and the complex64 basis: a strongly varying
+    wavenumber and a tight inner reduction make the cycles long; the solve
+    still reaches the tolerance with the oracle's residual."""
     pr = inputs.helmholtz_2d(63, 3, 3, 25.0, sigma)
     S = sg.assemble_problem(pr)
     b = torch.from_numpy(S.b).to(DEV)
     op = B.SG(pr, tuned=False)
     x = torch.zeros_like(b)
-    info = op.gmres(b, x, restart=120, tol=1e-10, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000, inner_tol=1e-7)
+    info = op.gmres(b, x, restart=120, tol=1e-10, prec=B.PREC_MEAN, mode=B.MIXED, maxit=4000, inner_tol=1e-9,
+                    basis16=basis16)
     assert info["status"] == B.SG_OK, info
     relres = np.linalg.norm(S.b - S.A @ x.cpu().numpy()) / np.linalg.norm(S.b)
     assert relres <= 1e-10, relres
-    print("long cycles: sigma %.2f iters %d outer %d" % (sigma, info["iters"], info["outer"]))
+    print("long cycles: sigma %.2f basis16 %d iters %d outer %d cycles %d" %
+          (sigma, basis16, info["iters"], info["outer"], info["cycles"]))
     op.close()
 
 
@@ -249,3 +251,4 @@ def test_binary16_basis_option_checked(B):
         op.gmres(b, torch.zeros_like(b), restart=20, tol=1e-8, prec=B.PREC_MEAN, mode=B.MIXED, basis16=3)
     assert ei.value.status == B.SG_EINVAL
     op.close()
+

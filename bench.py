@@ -662,11 +662,11 @@ def run_ours(args):
             kname = ("k_tc_hgemm_w (paired 256-column binary16 transform, kind::f16, clusters of two CTAs "
                      "sharing B stages by multicast copies; all 4 launches of the apply in the cycles' steps "
                      "after the first, 3 of 4 in the first)")
-            tsrc = "ncu capture of this kernel source (profiles/tc_hgemm_w_511x511_s6_deg3.md)"
+            tsrc = "ncu capture of this kernel source at 511x511, P = 84 (its summary under profiles/)"
         elif f16:
             kname = ("k_tc_cgemm_ps<%d, true> (persistent binary16 transform, kind::f16; all 4 launches of the "
                      "apply in the cycles' steps after the first, 3 of 4 in the first)" % op.tune_get().get("tc_tile_n"))
-            tsrc = "ncu capture of this kernel source (profiles/tc_hgemm_ps_511x511_s6_deg3.md)"
+            tsrc = "ncu capture of this kernel source at 511x511, P = 84 (its summary under profiles/)"
         else:
             kname = "k_tc_cgemm_ps (persistent plain-TF32 transform, 3 of the 4 launches per apply)"
             tsrc = None
@@ -717,7 +717,7 @@ def run_ours(args):
         cgs = {"kernel": kname, "bound": "hbm", "achieved": b_p2 / (t_p2 * 1e-3) / 1e9, "peak": hbm_peak,
                "unit": "GB/s", "frac": b_p2 / (t_p2 * 1e-3) / 1e9 / hbm_peak, "traffic": tr2,
                "traffic_source": ("ncu capture of this kernel source at 255^2 (P = 84), step %d, scaled by "
-                                  "the slot size (profiles/cgs2_step10_255x255_s6_deg3.md)" % jc) if tr2 else None,
+                                  "the slot size (its summary under profiles/)" % jc) if tr2 else None,
                "peak_kind": hbm_kind, "us_per_launch": 1000.0 * t_p2, "bytes_per_launch": b_p2, "units": units,
                "pass1": {"kernel": "k_hb_dots" if f16 else "k_cgs_dots<float>", "us_per_launch": 1000.0 * t_p1,
                          "bytes_per_launch": b_p1, "gbs": b_p1 / (t_p1 * 1e-3) / 1e9,

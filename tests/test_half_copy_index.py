@@ -27,3 +27,23 @@ def test_row_by_multiply_shift(mx):
     e = e[(e >= 0) & (e <= top)].astype(np.uint64)
     row = (e * np.uint64(mul)) >> np.uint64(shift)
     np.testing.assert_array_equal(row, e // np.uint64(mx))
+
+
+@pytest.mark.parametrize("mx", [32, 33, 63, 95, 127, 255, 256, 511, 1023, 1025, 4095])
+def test_quad_row_by_multiply_shift(mx):
+    """The binary16 basis passes walk a slot in quads of 4 pairs (rows of mx4
+    = 4 mq pairs): row = (quad * mulq) >> (32 + s), s = ceil(log2 mq), mulq =
+    ceil(2^(32+s) / mq), must equal quad // mq for every quad of a slot
+    below 2^31 pairs; a quad's first column 4 (quad - row mq) then never
+    reaches mx4."""
+    mq = (mx + 3) // 4
+    mul, shift = _mul_shift(mq)
+    top = (1 << 29) - 1                 # quads of a slot of < 2^31 pairs
+    rng = np.random.default_rng(mx + 1)
+    qs = np.concatenate([np.arange(0, 2048), rng.integers(0, top // mq, 20000), [top // mq - 1, top // mq]])
+    quad = np.concatenate([qs * mq - 1, qs * mq, qs * mq + 1, qs * mq + mq - 1, [top]])
+    quad = quad[(quad >= 0) & (quad <= top)].astype(np.uint64)
+    row = (quad * np.uint64(mul)) >> np.uint64(shift)
+    np.testing.assert_array_equal(row, quad // np.uint64(mq))
+    col0 = 4 * (quad - row * np.uint64(mq))
+    assert int(col0.max()) <= 4 * mq - 4
